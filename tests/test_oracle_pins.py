@@ -1,0 +1,441 @@
+"""Pins of the FP64 oracle to facts fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than itself: hand-computed
+values, the Stokes equations, closed forms of the Coulomb coefficients, an
+independent power-series expansion of the kernels, convergence rates,
+structural invariants of the tree, exact scaling laws, and the error levels the
+paper prints in its Tables 1 and 2.
+"""
+import os
+
+import numpy as np
+import pytest
+from scipy.special import eval_legendre
+
+import oracle
+from paper_1811_12498_gb300 import inputs
+from tests.jet import kernel_jets
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _rng(s):
+    return np.random.default_rng(1000 + s)
+
+
+# ---------------------------------------------------------------- kernels
+
+def test_kernel_closed_forms():
+    """eqs. (1.2a,b), (1.3): hand-computed single-source velocities."""
+    rows = np.loadtxt(os.path.join(GOLDEN, "kernel_values.txt"))
+    for r in rows:
+        x, f, h, nu, u = r[0:3], r[3:6], r[6:9], r[9:12], r[12:15]
+        src = np.zeros((1, 3))
+        got = oracle.direct(src, f[None], h[None], nu[None], targets=x[None])[0]
+        np.testing.assert_allclose(got, u, rtol=1e-15, atol=1e-16)
+
+
+def test_kernel_symmetries():
+    """S_ij = S_ji and T_ijl fully symmetric (eqs. 1.2a,b)."""
+    rng = _rng(1)
+    for _ in range(20):
+        x, y = rng.standard_normal(3), rng.standard_normal(3)
+        S = oracle.stokeslet(x, y)
+        T = oracle.stresslet(x, y)
+        np.testing.assert_allclose(S, S.T, rtol=0, atol=1e-15 * np.abs(S).max())
+        for perm in [(0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)]:
+            np.testing.assert_allclose(T, T.transpose(perm), rtol=0, atol=1e-15 * np.abs(T).max())
+
+
+def _fd_velocity(src, f, h, nu, x, eps):
+    """Velocity and its first/second central differences at x."""
+    def u_at(p):
+        return oracle.direct(src, f, h, nu, targets=p[None])[0]
+    grad = np.zeros((3, 3))  # grad[k, i] = d u_i / d x_k
+    lap = np.zeros(3)
+    u0 = u_at(x)
+    for k in range(3):
+        e = np.zeros(3)
+        e[k] = eps
+        up, um = u_at(x + e), u_at(x - e)
+        grad[k] = (up - um) / (2 * eps)
+        lap += (up - 2 * u0 + um) / eps ** 2
+    return u0, grad, lap
+
+
+def test_velocity_is_divergence_free():
+    """Stokes flow, eq. (1.1b): div u = 0 away from the sources."""
+    rng = _rng(2)
+    src = rng.uniform(-1, 1, (5, 3))
+    f, h = rng.uniform(-1, 1, (5, 3)), rng.uniform(-1, 1, (5, 3))
+    nu = rng.standard_normal((5, 3))
+    for _ in range(5):
+        x = rng.uniform(2, 3, 3)
+        _, grad, _ = _fd_velocity(src, f, h, nu, x, 1e-5)
+        assert abs(np.trace(grad)) < 1e-8 * np.abs(grad).max()
+
+
+def test_kernels_solve_stokes_equations():
+    """eq. (1.1a): lap u = grad p, with the pressures of a Stokeslet,
+    p = 2 (d.f)/r^3, and of this stresslet, p = 2 (d.h)(d.nu)/r^5 - (2/3)(h.nu)/r^3
+    (both derived by hand for prefactor 1)."""
+    rng = _rng(3)
+    y = np.zeros((1, 3))
+    for kind in ("S", "T"):
+        for _ in range(4):
+            f = rng.uniform(-1, 1, (1, 3)) if kind == "S" else np.zeros((1, 3))
+            h = rng.uniform(-1, 1, (1, 3)) if kind == "T" else np.zeros((1, 3))
+            nu = rng.uniform(-1, 1, (1, 3))
+            x = rng.uniform(0.8, 1.2, 3) * rng.choice([-1, 1], 3)
+
+            def pressure(p):
+                r = np.linalg.norm(p)
+                if kind == "S":
+                    return 2 * (p @ f[0]) / r ** 3
+                return 2 * (p @ h[0]) * (p @ nu[0]) / r ** 5 - (2.0 / 3.0) * (h[0] @ nu[0]) / r ** 3
+
+            _, _, lap = _fd_velocity(y, f, h, nu, x, 2e-3)
+            gp = np.zeros(3)
+            for k in range(3):
+                e = np.zeros(3)
+                e[k] = 1e-5
+                gp[k] = (pressure(x + e) - pressure(x - e)) / 2e-5
+            np.testing.assert_allclose(lap, gp, rtol=0, atol=2e-5 * np.abs(gp).max())
+
+
+def test_direct_sum_superposition_and_exclusion():
+    """eq. (1.3): the sum over n != m is the sum of single-source sums."""
+    rng = _rng(4)
+    x, f, h, nu = inputs.uniform_cube(7, 11)
+    u = oracle.direct(x, f, h, nu)
+    acc = np.zeros_like(u)
+    for n in range(7):
+        others = [m for m in range(7) if m != n]
+        acc[others] += oracle.direct(x[n:n + 1], f[n:n + 1], h[n:n + 1], nu[n:n + 1], targets=x[others])
+    np.testing.assert_allclose(u, acc, rtol=1e-14, atol=1e-14)
+    del rng
+
+
+# ---------------------------------------------------- Coulomb coefficients
+
+def test_coulomb_on_axis_closed_form():
+    """recurrence (3.2): along d = +-R e_a, b^{n e_a} = (+-1)^n R^-(n+1), and
+    coefficients odd in the other two axes vanish (1/|d-t| symmetry)."""
+    P = 12
+    for axis in range(3):
+        for sgn in (1.0, -1.0):
+            R = 0.37
+            d = np.zeros(3)
+            d[axis] = sgn * R
+            b = oracle.coulomb_coeffs(d, P)
+            for n in range(P + 1):
+                k = [0, 0, 0]
+                k[axis] = n
+                np.testing.assert_allclose(b[tuple(k)], sgn ** n * R ** -(n + 1), rtol=1e-13)
+            others = [a for a in range(3) if a != axis]
+            for k1 in range(P + 1):
+                for k2 in range(P + 1 - k1):
+                    for k3 in range(P + 1 - k1 - k2):
+                        k = (k1, k2, k3)
+                        if k[others[0]] % 2 or k[others[1]] % 2:
+                            assert b[k] == 0.0
+
+
+def test_coulomb_legendre_generating_function():
+    """sum_{||k||=n} b^k t^k = |t|^n P_n(cos g) / R^(n+1) (expansion of 1/|d-t|)."""
+    rng = _rng(5)
+    P = 14
+    for _ in range(10):
+        d = rng.standard_normal(3)
+        t = rng.standard_normal(3)
+        b = oracle.coulomb_coeffs(d, P)
+        R, tn = np.linalg.norm(d), np.linalg.norm(t)
+        cg = d @ t / (R * tn)
+        for n in range(P + 1):
+            s = 0.0
+            for k1 in range(n + 1):
+                for k2 in range(n + 1 - k1):
+                    k3 = n - k1 - k2
+                    s += b[k1, k2, k3] * t[0] ** k1 * t[1] ** k2 * t[2] ** k3
+            ref = tn ** n * eval_legendre(n, cg) / R ** (n + 1)
+            scale = tn ** n / R ** (n + 1)
+            assert abs(s - ref) <= 1e-12 * scale
+
+
+# -------------------------------------------- Taylor coefficients of S, T
+
+@pytest.mark.parametrize("p", [0, 1, 3, 6])
+def test_taylor_coefficients_match_power_series(p):
+    """eqs. (3.4), (3.7) equal the power-series expansion of S and T in t."""
+    rng = _rng(6 + p)
+    for _ in range(2):
+        d = rng.standard_normal(3)
+        _, Sj, Tj = kernel_jets(d, p)
+        a = oracle.taylor_stokeslet(d, p)
+        t = oracle.taylor_stresslet(d, p)
+        mask = np.add.outer(np.add.outer(np.arange(p + 1), np.arange(p + 1)), np.arange(p + 1)) <= p
+        for i in range(3):
+            for j in range(3):
+                ref = Sj[i][j].c
+                np.testing.assert_allclose(a[i, j][mask], ref[mask], rtol=1e-11,
+                                           atol=1e-12 * np.abs(ref).max())
+                for l in range(3):
+                    ref = Tj[i][j][l].c
+                    np.testing.assert_allclose(t[i, j, l][mask], ref[mask], rtol=1e-11,
+                                               atol=1e-12 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("p", [0, 2, 5, 8, 10])
+def test_contracted_far_field_equals_explicit(p):
+    """eqs. (4.4) + (4.9) are exact rearrangements of eq. (2.9)."""
+    rng = _rng(20 + p)
+    for _ in range(3):
+        d = rng.standard_normal(3) * 2.0
+        Mf = rng.standard_normal((3,) + (p + 1,) * 3)
+        Mt = rng.standard_normal((3, 3) + (p + 1,) * 3)
+        u1 = oracle.far_contracted(d, p, Mf, Mt)
+        u2 = oracle.far_explicit(d, p, Mf, Mt)
+        np.testing.assert_allclose(u1, u2, rtol=1e-11, atol=1e-13 * np.abs(u2).max())
+
+
+def _cluster(rng, n, radius):
+    v = rng.standard_normal((n, 3))
+    v *= (radius * rng.uniform(0, 1, (n, 1)) ** (1 / 3)) / np.linalg.norm(v, axis=1, keepdims=True)
+    return v
+
+
+def test_far_field_error_decays_like_rho_to_p_plus_one():
+    """Taylor truncation (2.9): error ~ (r/R)^(p+1) for a well-separated cluster."""
+    rng = _rng(30)
+    yc = np.array([0.1, -0.2, 0.3])
+    y = yc + _cluster(rng, 40, 0.1)
+    f, h = rng.uniform(-1, 1, (40, 3)), rng.uniform(-1, 1, (40, 3))
+    nu = rng.standard_normal((40, 3))
+    x = yc + np.array([0.6, 0.5, -0.3])  # R ~ 0.84, rho = r/R ~ 0.12
+    exact = oracle.direct(y, f, h, nu, targets=x[None])[0]
+    errs = []
+    for p in range(0, 9):
+        Mf, Mt = oracle.moments(y, f, h, nu, yc, p)
+        u = oracle.far_contracted(x - yc, p, Mf, Mt)
+        errs.append(np.linalg.norm(u - exact) / np.linalg.norm(exact))
+    errs = np.array(errs)
+    rho = np.max(np.linalg.norm(y - yc, axis=1)) / np.linalg.norm(x - yc)
+    slope = np.polyfit(np.arange(9), np.log(errs), 1)[0]
+    # observed geometric rate lies at or below the bound rho
+    assert slope < np.log(rho) + 0.35
+    assert errs[-1] < 1e-8
+    assert np.all(errs[1:] < errs[:-1] * 1.5)
+
+
+def test_far_field_exact_when_sources_at_centre():
+    """All sources at y_c: moments vanish for ||k|| > 0, the p = 0 far field is exact."""
+    rng = _rng(31)
+    yc = np.array([0.3, 0.2, 0.1])
+    y = np.repeat(yc[None], 6, axis=0)
+    f, h = rng.uniform(-1, 1, (6, 3)), rng.uniform(-1, 1, (6, 3))
+    nu = rng.standard_normal((6, 3))
+    x = np.array([1.5, -0.7, 0.4])
+    exact = oracle.direct(y, f, h, nu, targets=x[None])[0]
+    Mf, Mt = oracle.moments(y, f, h, nu, yc, 0)
+    np.testing.assert_allclose(oracle.far_contracted(x - yc, 0, Mf, Mt), exact, rtol=1e-14)
+
+
+def test_moments_translation_identity():
+    """Moments about c' follow from those about c by the binomial theorem."""
+    rng = _rng(32)
+    from math import comb
+    y = rng.uniform(-1, 1, (9, 3))
+    f, h, nu = rng.uniform(-1, 1, (9, 3)), rng.uniform(-1, 1, (9, 3)), rng.standard_normal((9, 3))
+    p = 4
+    c, c2 = np.array([0.1, 0.2, -0.1]), np.array([-0.3, 0.05, 0.2])
+    Mf, Mt = oracle.moments(y, f, h, nu, c, p)
+    Mf2, Mt2 = oracle.moments(y, f, h, nu, c2, p)
+    s = c - c2
+    for k1 in range(p + 1):
+        for k2 in range(p + 1 - k1):
+            for k3 in range(p + 1 - k1 - k2):
+                acc_f = np.zeros(3)
+                acc_t = np.zeros((3, 3))
+                for j1 in range(k1 + 1):
+                    for j2 in range(k2 + 1):
+                        for j3 in range(k3 + 1):
+                            w = comb(k1, j1) * comb(k2, j2) * comb(k3, j3) * s[0] ** (k1 - j1) * \
+                                s[1] ** (k2 - j2) * s[2] ** (k3 - j3)
+                            acc_f += w * Mf[:, j1, j2, j3]
+                            acc_t += w * Mt[:, :, j1, j2, j3]
+                np.testing.assert_allclose(Mf2[:, k1, k2, k3], acc_f, rtol=1e-12, atol=1e-13)
+                np.testing.assert_allclose(Mt2[:, :, k1, k2, k3], acc_t, rtol=1e-12, atol=1e-13)
+
+
+# ------------------------------------------------------------------ tree
+
+def _check_tree_structure(x, N0, shrink):
+    tree = oracle.Tree(x, N0, shrink)
+    nd = tree.nodes()
+    order = tree.order()
+    q = tree.quantized()
+    lo, side = tree.root()
+    N = x.shape[0]
+    np.testing.assert_array_equal(np.sort(order), np.arange(N))
+    assert nd["count"][0] == N and nd["level"][0] == 0
+    for c in range(tree.num_nodes):
+        b, n, L = nd["begin"][c], nd["count"][c], nd["level"][c]
+        members = order[b:b + n]
+        # every member lies in the node's cell (quantised coordinates)
+        assert np.all((q[members] >> (21 - L)) == nd["cell"][c])
+        # leaf iff at most N0 particles (or depth 21)
+        is_leaf = nd["nchild"][c] == 0
+        assert is_leaf == (n <= N0 or L >= 21)
+        if not is_leaf:
+            ch = nd["child"][c][:nd["nchild"][c]]
+            assert nd["count"][ch].sum() == n
+            assert np.all(nd["level"][ch] == L + 1)
+            assert np.all(nd["count"][ch] > 0)
+            assert np.all(np.diff(nd["begin"][ch]) > 0)
+        pts = x[members]
+        if shrink:
+            yc = (pts.min(0) + pts.max(0)) * 0.5
+        else:
+            cs = side / 2.0 ** L
+            yc = lo + (nd["cell"][c] + 0.5) * cs
+        np.testing.assert_allclose(nd["yc"][c], yc, rtol=1e-15, atol=1e-15)
+        r2 = np.max(np.sum((pts - nd["yc"][c]) ** 2, axis=1))
+        np.testing.assert_allclose(nd["rc2"][c], r2, rtol=1e-14)
+    return tree
+
+
+def test_tree_structure_cube():
+    x, *_ = inputs.uniform_cube(3000, 41)
+    _check_tree_structure(x, 100, True)
+    _check_tree_structure(x, 100, False)
+
+
+def test_tree_structure_sphere_and_duplicates():
+    x, *_ = inputs.fibonacci_sphere(2500, 42)
+    _check_tree_structure(x, 64, True)
+    xd = np.concatenate([x[:300], x[:300], x[:20]])  # coincident points force depth-21 leaves
+    _check_tree_structure(xd, 2, True)
+
+
+def test_quantisation_root_and_clamp():
+    """Root cube: per-axis minimum corner, side = largest extent; the maximum
+    point is clamped into the last cell (Section 5, reading)."""
+    x = np.array([[0.0, 0.0, 0.0], [2.0, 1.0, 0.5], [1.0, 0.25, 0.125]])
+    tree = oracle.Tree(x, 1, True)
+    lo, side = tree.root()
+    np.testing.assert_array_equal(lo, [0, 0, 0])
+    assert side == 2.0
+    q = tree.quantized()
+    np.testing.assert_array_equal(q[0], [0, 0, 0])
+    np.testing.assert_array_equal(q[1], [2 ** 21 - 1, 2 ** 20, 2 ** 19])
+    np.testing.assert_array_equal(q[2], [2 ** 20, 2 ** 18, 2 ** 17])
+
+
+# ------------------------------------------------------------- treecode
+
+def _system(N, seed, kind="cube"):
+    if kind == "cube":
+        return inputs.uniform_cube(N, seed)
+    return inputs.fibonacci_sphere(N, seed)
+
+
+@pytest.mark.parametrize("shrink", [True, False])
+def test_treecode_reduces_to_direct_when_no_cluster_is_accepted(shrink):
+    """theta -> 0: the MAC never holds and Algorithm 1 sums every leaf directly."""
+    x, f, h, nu = _system(900, 51)
+    tree = oracle.Tree(x, 40, shrink)
+    tree.set_moments(f, h, nu, 3)
+    u = tree.treecode(x, 1e-9, 3)
+    np.testing.assert_allclose(u, oracle.direct(x, f, h, nu), rtol=1e-12, atol=1e-12)
+
+
+def test_treecode_single_leaf_is_direct():
+    x, f, h, nu = _system(300, 52)
+    tree = oracle.Tree(x, 300, True)
+    assert tree.num_nodes == 1
+    tree.set_moments(f, h, nu, 4)
+    u, cnt = tree.treecode(x, 0.5, 4, counts=True)
+    np.testing.assert_allclose(u, oracle.direct(x, f, h, nu), rtol=1e-12, atol=1e-12)
+    assert np.all(cnt["far"] == 0)
+
+
+@pytest.mark.parametrize("theta", [0.3, 0.5, 0.8])
+def test_far_and_near_partition_the_sources(theta):
+    """Algorithm 1 visits every source exactly once per target: the far clusters
+    and the near leaves of a target partition the particle set."""
+    x, f, h, nu = _system(4000, 53, "sphere")
+    tree = oracle.Tree(x, 50, True)
+    tree.set_moments(f, h, nu, 2)
+    _, cnt = tree.treecode(x[::7], theta, 2, counts=True)
+    mass = tree.far_mass(x[::7], theta)
+    np.testing.assert_array_equal(mass + cnt["near_pairs"], np.full(mass.shape, 4000))
+    assert cnt["far"].sum() > 0
+
+
+def test_treecode_linearity_and_h_nu_swap():
+    x, f, h, nu = _system(2000, 54)
+    rng = _rng(55)
+    f2, h2 = rng.uniform(-1, 1, f.shape), rng.uniform(-1, 1, h.shape)
+    tree = oracle.Tree(x, 100, True)
+    tgt = x[::13]
+    tree.set_moments(f, h, nu, 5)
+    u1 = tree.treecode(tgt, 0.5)
+    tree.set_moments(f2, h2, nu, 5)
+    u2 = tree.treecode(tgt, 0.5)
+    tree.set_moments(1.5 * f - 0.25 * f2, 1.5 * h - 0.25 * h2, nu, 5)
+    u3 = tree.treecode(tgt, 0.5)
+    np.testing.assert_allclose(u3, 1.5 * u1 - 0.25 * u2, rtol=1e-11, atol=1e-11 * np.abs(u3).max())
+    # T_ijl is symmetric in (j, l): exchanging h and nu leaves u unchanged
+    tree.set_moments(f, nu, h, 5)
+    u4 = tree.treecode(tgt, 0.5)
+    np.testing.assert_allclose(u4, u1, rtol=1e-11, atol=1e-11 * np.abs(u1).max())
+
+
+def test_treecode_exact_power_of_two_scaling():
+    """x -> 2x: the tree is unchanged, the Stokeslet part scales by exactly 1/2
+    and the stresslet part by exactly 1/4 (homogeneity of eqs. 1.2a,b)."""
+    x, f, h, nu = _system(3000, 56)
+    z = np.zeros_like(f)
+    for (ff, hh, power) in ((f, z, 1), (z, h, 2)):
+        t1 = oracle.Tree(x, 80, True)
+        t1.set_moments(ff, hh, nu, 6)
+        t2 = oracle.Tree(2.0 * x, 80, True)
+        t2.set_moments(ff, hh, nu, 6)
+        u1 = t1.treecode(x[::11], 0.5)
+        u2 = t2.treecode(2.0 * x[::11], 0.5)
+        np.testing.assert_array_equal(u2, u1 / 2.0 ** power)
+
+
+def _sampled_E(x, f, h, nu, N0, shrink, theta, ps, nsamp, seed):
+    idx = inputs.sample_indices(x.shape[0], nsamp, seed)
+    ud = oracle.direct(x, f, h, nu, targets=x[idx])
+    tree = oracle.Tree(x, N0, shrink)
+    tree.set_moments(f, h, nu, max(ps))
+    return {p: oracle.rel_l2(tree.treecode(x[idx], theta, p), ud) for p in ps}
+
+
+@pytest.mark.slow
+def test_error_matches_paper_table2_cube():
+    """Table 2(a): random Stokeslets, density 2500, N = 125K, theta = 0.5,
+    N0 = 2000: E = 8.2e-3 (p=2), 1.1e-3 (p=4), 1.7e-4 (p=6), 3.0e-5 (p=8),
+    5.5e-6 (p=10).  E is a statistic of random inputs (600 sampled targets
+    here), so agreement within a factor 2 is required."""
+    x, f, h, nu = inputs.density_cube(125_000, inputs.SEED_BASE + 100)
+    paper = {2: 8.2e-3, 4: 1.1e-3, 6: 1.7e-4, 8: 3.0e-5, 10: 5.5e-6}
+    E = _sampled_E(x, f, h, nu, 2000, False, 0.5, list(paper), 600, 7)
+    for p, e in paper.items():
+        assert e / 2 < E[p] < e * 2, (p, E[p], e)
+
+
+@pytest.mark.slow
+def test_error_matches_paper_table1_sphere():
+    """Table 1(a): icosahedral sphere N = 81920, Stokeslets + stresslets,
+    clusters shrunk to their boxes, theta = 0.5: E = 1.2e-3 (p=2),
+    2.2e-4 (p=4), 5.2e-5 (p=6), 1.2e-5 (p=8), 2.9e-6 (p=10); agreement
+    within a factor 2 (600 sampled targets)."""
+    x, f, h, nu = inputs.icosahedral_sphere(6, inputs.SEED_BASE + 101)
+    assert x.shape[0] == 81920
+    paper = {2: 1.2e-3, 4: 2.2e-4, 6: 5.2e-5, 8: 1.2e-5, 10: 2.9e-6}
+    E = _sampled_E(x, f, h, nu, 2000, True, 0.5, list(paper), 600, 8)
+    for p, e in paper.items():
+        assert e / 2 < E[p] < e * 2, (p, E[p], e)
