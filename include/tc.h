@@ -1,0 +1,193 @@
+/*
+ * tc.h -- C ABI of the GB300 Stokeslet + stresslet treecode.
+ *
+ * The library evaluates the velocity of eq. (1.3) of Wang, Tlupova and
+ * Krasny, "A treecode algorithm for 3D Stokeslets and stresslets"
+ * (arXiv:1811.12498):
+ *
+ *   u_i(x^m) = sum_{n != m} S_ij(x^m, x^n) f_j^n + T_ijl(x^m, x^n) h_j^n nu_l^n
+ *
+ * with S_ij = delta_ij/r + d_i d_j/r^3 and T_ijl = d_i d_j d_l/r^5
+ * (eqs. 1.2a,b, prefactor 1, d = x - y, r = |d|), by the treecode of
+ * Section 5 (Algorithm 1): an octree of particle clusters, the MAC
+ * r/R <= theta (eq. 5.1), an order-p Cartesian Taylor far field built from
+ * the Coulomb-coefficient recurrence (3.2) and contracted as in
+ * eqs. (4.4) and (4.9), and a direct near field (Section 4.1).
+ *
+ * Conventions for every call:
+ *  - Arrays of 3-vectors are FP64 structure-of-arrays in DEVICE memory:
+ *    component a of item n is at ptr[a * count + n].  The caller owns every
+ *    array it passes; the library only reads inputs and writes outputs.
+ *  - The library owns everything reachable from a tc_ctx (tree, moments,
+ *    interaction lists, scratch) and frees it in tc_destroy.
+ *  - Work is enqueued on the context's CUDA stream (tc_config.stream,
+ *    NULL = legacy default stream).  Calls that must size buffers
+ *    (tc_build, tc_eval) synchronise that stream internally.
+ *  - No call aborts or prints.  Every failure returns a status; the message
+ *    is available from tc_last_error.  Device-side failures (a bounded wait
+ *    that ran out, an index check) are reported by the next call that
+ *    synchronises, or by tc_sync.
+ *  - Pairs with |x - y| == 0 contribute nothing.  When targets are the
+ *    sources this is the n != m exclusion of eq. (1.3).
+ */
+#ifndef TC_H
+#define TC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tc_ctx tc_ctx;
+
+typedef enum {
+    TC_OK = 0,
+    TC_EINVAL = 1,   /* an argument is out of range or a pointer is NULL       */
+    TC_ENOMEM = 2,   /* a device or host allocation failed                      */
+    TC_ECUDA = 3,    /* a CUDA runtime call failed (message has the CUDA error) */
+    TC_ESTATE = 4,   /* calls out of order, e.g. tc_eval before tc_moments      */
+    TC_ETIMEOUT = 5, /* a bounded device-side wait ran out                      */
+    TC_EDEVICE = 6   /* a device-side check failed (message says which)        */
+} tc_status;
+
+typedef enum {
+    /* every stage in FP64 */
+    TC_FP64 = 0,
+    /* near field and far-field contraction in FP32 (positions split into
+     * FP32 hi + lo parts, per-tile sums carried in FP64); Coulomb-coefficient
+     * recurrence in FP64 for p >= 8 and FP32 (radius-scaled) below; cluster
+     * moments always FP64 */
+    TC_MIXED = 1
+} tc_precision;
+
+typedef struct {
+    int32_t precision; /* tc_precision                                         */
+    int32_t shrink;    /* 1: cluster centre = centre of the tight bounding box
+                        *    of its particles (test case 1 of Section 6);
+                        * 0: centre of the octree cell                         */
+    void* stream;      /* cudaStream_t the context enqueues on; NULL = default */
+    int32_t reserved0; /* must be 0                                            */
+    int32_t reserved1; /* must be 0                                            */
+} tc_config;
+
+/* Create a context.  cfg may be NULL (TC_MIXED, shrink = 1, default stream).
+ * *out receives the handle, or NULL on failure.  The CUDA device current on
+ * the calling thread is the context's device. */
+tc_status tc_create(tc_ctx** out, const tc_config* cfg);
+
+/* Free a context and every device buffer it owns.  NULL is accepted. */
+tc_status tc_destroy(tc_ctx* ctx);
+
+/* Message of the last failure on ctx (or of the last context-free call on
+ * this thread when ctx is NULL).  Never NULL; valid until the next call. */
+const char* tc_last_error(const tc_ctx* ctx);
+
+/* Wait for the context's stream and report any device-side failure. */
+tc_status tc_sync(tc_ctx* ctx);
+
+/*
+ * Build the octree of Section 5 over N source positions.
+ *  x  : device, 3*N FP64, SoA.  Read during the call only (positions are
+ *       copied into Morton order).
+ *  N  : 1 <= N < 2^31.
+ *  N0 : maximum number of particles in a leaf, >= 1 (Section 6 uses 2000).
+ * Root: the cube with the per-axis minimum corner and side equal to the
+ * largest axis extent.  Cells follow 21-bit quantised coordinates; a cell
+ * is split into its non-empty octants while it holds more than N0 particles
+ * and is above depth 21.  Cluster centres and radii (r = max distance from
+ * the centre to the cluster's particles, Section 2) are computed here.
+ * Invalidates moments and interaction lists.  Synchronises the stream.
+ */
+tc_status tc_build(tc_ctx* ctx, const double* x, int64_t N, int32_t N0);
+
+/*
+ * Cluster moments (Section 2) for every cluster:
+ *   M_j^k = sum_{n in C} (y^n - y_c)^k f_j^n,
+ *   M~_jl^k = sum_{n in C} (y^n - y_c)^k h_j^n nu_l^n,   ||k|| <= p,
+ * computed in FP64 and held in a flattened graded order (Section 6.1.1).
+ *  f, h, nu : device, 3*N FP64 SoA each, in the caller's particle order.
+ *  p        : 0 <= p <= 12.
+ * Requires tc_build.  Enqueued only (no synchronisation).
+ */
+tc_status tc_moments(tc_ctx* ctx, const double* f, const double* h, const double* nu, int32_t p);
+
+/*
+ * Treecode velocity (Algorithm 1) at M targets.
+ *  targets : device, 3*M FP64 SoA, or NULL to evaluate at the sources
+ *            themselves (then M must equal N and u is in the source order).
+ *  theta   : MAC parameter, 0 < theta < 1 (eq. 5.1).
+ *  p       : Taylor order, 0 <= p <= the order given to tc_moments.
+ *  u       : device, 3*M FP64 SoA, written.
+ * Every target makes exactly the far/near decisions of Algorithm 1: the MAC
+ * is tested per target in FP64.  Synchronises the stream once to size the
+ * interaction lists.
+ */
+tc_status tc_eval(tc_ctx* ctx, const double* targets, int64_t M, double theta, int32_t p, double* u);
+
+/*
+ * Direct O(N*M) sum of eq. (1.3) (with the contraction of Section 4.1).
+ *  x, f, h, nu : device, 3*N FP64 SoA.  targets: device 3*M SoA or NULL
+ *  (targets = sources, M must equal N).  u: device 3*M FP64 SoA, written.
+ *  precision   : TC_FP64 or TC_MIXED (FP32 pair terms on hi/lo positions).
+ *  stream      : cudaStream_t or NULL.
+ * Allocates its scratch with stream-ordered cudaMallocAsync and frees it
+ * before returning; enqueued only.
+ */
+tc_status tc_direct(const double* x, const double* f, const double* h, const double* nu, int64_t N,
+                    const double* targets, int64_t M, int32_t precision, void* stream, double* u);
+
+/*
+ * Interaction counts of the last tc_eval (host outputs, any may be NULL):
+ *  near_pairs       : sum over targets of the sizes of the leaves summed directly
+ *  far_interactions : number of (target, cluster) far-field evaluations
+ *  clusters         : number of clusters in the tree
+ */
+tc_status tc_stats(tc_ctx* ctx, int64_t* near_pairs, int64_t* far_interactions, int64_t* clusters);
+
+/*
+ * Per-target counts of the last tc_eval, in the target order of that call
+ * (device int64 arrays of M entries, any may be NULL): number of far
+ * clusters and number of near-field source particles examined.
+ */
+tc_status tc_eval_counts(tc_ctx* ctx, int64_t* nfar, int64_t* nnear_pairs);
+
+/* ---------------------------------------------------------------------- */
+/* Inspection of the tree (host outputs; for tests and tools).            */
+/* ---------------------------------------------------------------------- */
+
+/* Number of clusters and maximum depth of the last tc_build; root corner
+ * lo[3] and side (host pointers, any may be NULL). */
+tc_status tc_tree_info(tc_ctx* ctx, int64_t* nnodes, int32_t* depth, double* lo, double* side);
+
+/*
+ * Copy per-cluster records to host arrays of nnodes entries (any may be
+ * NULL).  Clusters are numbered level by level, children of one parent
+ * consecutively in octant order (x bit most significant).
+ *  begin, count : particle range in Morton order
+ *  level        : depth (root 0); cell: 3*nnodes integer cell coordinates
+ *  parent       : parent index (-1 for the root)
+ *  first_child, nchild : children are first_child .. first_child+nchild-1
+ *  yc           : 3*nnodes cluster centres (x,y,z interleaved per cluster)
+ *  rc2          : squared cluster radius
+ */
+tc_status tc_tree_export(tc_ctx* ctx, int32_t* begin, int32_t* count, int32_t* level, int32_t* cell,
+                         int32_t* parent, int32_t* first_child, int32_t* nchild, double* yc, double* rc2);
+
+/* Morton order of the sources (host int32 array of N): entry i is the
+ * caller's index of the i-th particle in Morton order. */
+tc_status tc_tree_order(tc_ctx* ctx, int32_t* order);
+
+/*
+ * Moments of one cluster as host FP64 cubes of order q = p of tc_moments:
+ * Mf[(j*(q+1) + k1)*(q+1)^2 + k2*(q+1) + k3] = M_j^k (3 cubes) and
+ * Mt[((3j+l)*(q+1) + k1)*(q+1)^2 + ...] = M~_jl^k (9 cubes); entries with
+ * ||k|| > q are 0.
+ */
+tc_status tc_moments_export(tc_ctx* ctx, int64_t node, double* Mf, double* Mt);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TC_H */

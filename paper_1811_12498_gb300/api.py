@@ -1,0 +1,196 @@
+"""Thin Python binding of the C ABI (include/tc.h) over torch CUDA tensors.
+
+Only argument marshalling happens here: every step of the treecode runs in
+the CUDA kernels of libtc.so.  Arrays of 3-vectors are float64 CUDA tensors
+of shape (3, count) (structure of arrays), the layout of the C ABI.
+``soa`` converts an (count, 3) tensor.
+
+    tc = Treecode(precision="mixed", shrink=True)
+    tc.build(x, N0=2000)          # eq. (1.3) sources, Section 5 octree
+    tc.moments(f, h, nu, p=8)     # Section 2 moments
+    u = tc.eval(theta=0.5, p=8)   # Algorithm 1 at the sources
+"""
+import ctypes
+
+import torch
+
+from ._lib import TCConfig, lib
+
+TC_FP64, TC_MIXED = 0, 1
+_STATUS = {0: "TC_OK", 1: "TC_EINVAL", 2: "TC_ENOMEM", 3: "TC_ECUDA", 4: "TC_ESTATE", 5: "TC_ETIMEOUT",
+           6: "TC_EDEVICE"}
+
+
+class TCError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (_STATUS.get(status, status), msg))
+        self.status = status
+
+
+def _prec(precision):
+    if precision in (TC_FP64, "fp64", "FP64"):
+        return TC_FP64
+    if precision in (TC_MIXED, "mixed", "MIXED"):
+        return TC_MIXED
+    raise ValueError("precision must be 'fp64' or 'mixed'")
+
+
+def _check(status, handle=None):
+    if status != 0:
+        msg = lib().tc_last_error(handle)
+        raise TCError(status, msg.decode() if msg else "")
+
+
+def soa(a):
+    """(count, 3) -> contiguous (3, count) float64 on the same device."""
+    return a.t().contiguous().to(torch.float64)
+
+
+def _vec3(a, name, count=None):
+    if a is None:
+        return None
+    if not isinstance(a, torch.Tensor) or not a.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if a.dtype != torch.float64 or a.dim() != 2 or a.shape[0] != 3 or not a.is_contiguous():
+        raise ValueError("%s must be a contiguous float64 tensor of shape (3, n)" % name)
+    if count is not None and a.shape[1] != count:
+        raise ValueError("%s has %d entries, expected %d" % (name, a.shape[1], count))
+    return a
+
+
+def _ptr(a):
+    return None if a is None else ctypes.c_void_p(a.data_ptr())
+
+
+def _stream_ptr(stream):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Treecode:
+    """One treecode context (tc_ctx): tree, moments and interaction lists."""
+
+    def __init__(self, precision="mixed", shrink=True, stream=None):
+        self.precision = _prec(precision)
+        self.stream = torch.cuda.current_stream() if stream is None else stream
+        cfg = TCConfig(self.precision, int(bool(shrink)), _stream_ptr(self.stream), 0, 0)
+        h = ctypes.c_void_p()
+        _check(lib().tc_create(ctypes.byref(h), ctypes.byref(cfg)))
+        self._h = h
+        self.N = 0
+        self.p = None
+        self._keep = ()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().tc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _chk(self, st):
+        _check(st, self._h)
+
+    def build(self, x, N0):
+        x = _vec3(x, "x")
+        self.N = x.shape[1]
+        self._chk(lib().tc_build(self._h, _ptr(x), self.N, int(N0)))
+        return self
+
+    def moments(self, f, h, nu, p):
+        f, h, nu = (_vec3(a, n, self.N) for a, n in ((f, "f"), (h, "h"), (nu, "nu")))
+        self._chk(lib().tc_moments(self._h, _ptr(f), _ptr(h), _ptr(nu), int(p)))
+        self._keep = (f, h, nu)  # inputs must outlive the enqueued kernels
+        self.p = int(p)
+        return self
+
+    def eval(self, theta, p=None, targets=None, out=None):
+        p = self.p if p is None else int(p)
+        t = _vec3(targets, "targets")
+        M = self.N if t is None else t.shape[1]
+        if out is None:
+            with torch.cuda.stream(self.stream):
+                out = torch.empty((3, M), dtype=torch.float64, device="cuda")
+        _vec3(out, "out", M)
+        self._chk(lib().tc_eval(self._h, _ptr(t), M, float(theta), p, _ptr(out)))
+        self._M = M
+        self._keep_t = t
+        return out
+
+    def sync(self):
+        self._chk(lib().tc_sync(self._h))
+
+    def stats(self):
+        near, far, nodes = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        self._chk(lib().tc_stats(self._h, ctypes.byref(near), ctypes.byref(far), ctypes.byref(nodes)))
+        return dict(near_pairs=near.value, far_interactions=far.value, clusters=nodes.value)
+
+    def eval_counts(self):
+        M = self.N if getattr(self, "_M", None) is None else self._M
+        nf = torch.empty(M, dtype=torch.int64, device="cuda")
+        nn = torch.empty(M, dtype=torch.int64, device="cuda")
+        self._chk(lib().tc_eval_counts(self._h, _ptr(nf), _ptr(nn)))
+        return nf, nn
+
+    def tree_info(self):
+        n, d = ctypes.c_int64(), ctypes.c_int32()
+        lo = (ctypes.c_double * 3)()
+        side = ctypes.c_double()
+        self._chk(lib().tc_tree_info(self._h, ctypes.byref(n), ctypes.byref(d), lo, ctypes.byref(side)))
+        return dict(nnodes=n.value, depth=d.value, lo=list(lo), side=side.value)
+
+    def tree_export(self):
+        import numpy as np
+        n = self.tree_info()["nnodes"]
+        out = dict(begin=np.empty(n, np.int32), count=np.empty(n, np.int32), level=np.empty(n, np.int32),
+                   cell=np.empty((n, 3), np.int32), parent=np.empty(n, np.int32), first_child=np.empty(n, np.int32),
+                   nchild=np.empty(n, np.int32), yc=np.empty((n, 3)), rc2=np.empty(n))
+        keys = ("begin", "count", "level", "cell", "parent", "first_child", "nchild", "yc", "rc2")
+        self._chk(lib().tc_tree_export(self._h, *(ctypes.c_void_p(out[k].ctypes.data) for k in keys)))
+        return out
+
+    def tree_order(self):
+        import numpy as np
+        o = np.empty(self.N, np.int32)
+        self._chk(lib().tc_tree_order(self._h, ctypes.c_void_p(o.ctypes.data)))
+        return o
+
+    def moments_export(self, node):
+        import numpy as np
+        q = self.p + 1
+        Mf = np.empty((3, q, q, q))
+        Mt = np.empty((3, 3, q, q, q))
+        self._chk(lib().tc_moments_export(self._h, int(node), ctypes.c_void_p(Mf.ctypes.data),
+                                          ctypes.c_void_p(Mt.ctypes.data)))
+        return Mf, Mt
+
+
+def direct(x, f, h, nu, targets=None, precision="fp64", out=None, stream=None):
+    """Direct sum of eq. (1.3) (tc_direct); returns u of shape (3, M)."""
+    x = _vec3(x, "x")
+    N = x.shape[1]
+    f, h, nu = (_vec3(a, n, N) for a, n in ((f, "f"), (h, "h"), (nu, "nu")))
+    t = _vec3(targets, "targets")
+    M = N if t is None else t.shape[1]
+    if out is None:
+        out = torch.empty((3, M), dtype=torch.float64, device=x.device)
+    _vec3(out, "out", M)
+    _check(lib().tc_direct(_ptr(x), _ptr(f), _ptr(h), _ptr(nu), N, _ptr(t), M, _prec(precision),
+                           _stream_ptr(stream), _ptr(out)))
+    return out
+
+
+def velocity(x, f, h, nu, theta, p, N0, precision="mixed", shrink=True, targets=None):
+    """One-shot treecode velocity (build + moments + eval); u of shape (3, M)."""
+    tc = Treecode(precision, shrink)
+    try:
+        tc.build(x, N0).moments(f, h, nu, p)
+        u = tc.eval(theta, p, targets)
+        tc.sync()
+        return u
+    finally:
+        tc.close()

@@ -1,0 +1,530 @@
+// C ABI entry points (include/tc.h): argument checks, buffer management and
+// the order of kernel launches for tree build, moments and evaluation.
+#include <cstdarg>
+#include <new>
+
+#include "tc_internal.cuh"
+
+namespace tc {
+
+static thread_local std::string g_thread_err = "no error";
+
+void set_thread_error(const char* msg) { g_thread_err = msg; }
+
+tc_status fail(tc_ctx* ctx, tc_status st, const char* fmt, ...)
+{
+    char buf[768];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (ctx)
+        ctx->err = buf;
+    else
+        g_thread_err = buf;
+    return st;
+}
+
+tc_status cuda_fail(tc_ctx* ctx, cudaError_t e, const char* where)
+{
+    if (e == cudaErrorMemoryAllocation)
+        return fail(ctx, TC_ENOMEM, "%s: %s", where, cudaGetErrorString(e));
+    return fail(ctx, TC_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+cudaError_t ensure(DevBuf& b, size_t bytes)
+{
+    if (bytes == 0) bytes = 256;
+    if (b.p && b.cap >= bytes) return cudaSuccess;
+    if (b.p) {
+        cudaError_t e = cudaFree(b.p);
+        b.p = nullptr;
+        b.cap = 0;
+        if (e != cudaSuccess) return e;
+    }
+    size_t want = (bytes + 255) / 256 * 256;
+    cudaError_t e = cudaMalloc(&b.p, want);
+    if (e != cudaSuccess) {
+        b.p = nullptr;
+        return e;
+    }
+    b.cap = want;
+    return cudaSuccess;
+}
+
+// grow keeping the first `keep` bytes
+static cudaError_t grow_keep(DevBuf& b, size_t bytes, size_t keep, cudaStream_t s)
+{
+    if (b.p && b.cap >= bytes) return cudaSuccess;
+    size_t want = (bytes + 255) / 256 * 256;
+    void* np = nullptr;
+    cudaError_t e = cudaMalloc(&np, want);
+    if (e != cudaSuccess) return e;
+    if (b.p && keep) {
+        e = cudaMemcpyAsync(np, b.p, keep, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            cudaFree(np);
+            return e;
+        }
+    }
+    if (b.p) cudaFree(b.p);
+    b.p = np;
+    b.cap = want;
+    return cudaSuccess;
+}
+
+void release(DevBuf& b)
+{
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+}
+
+}  // namespace tc
+
+using namespace tc;
+
+#define TC_CK(call, where)                                  \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where); \
+    } while (0)
+
+static void release_all(tc_ctx* c)
+{
+    DevBuf* bufs[] = {&c->root, &c->bbox_part, &c->keys, &c->keys_alt, &c->perm, &c->perm_alt, &c->hist, &c->xs,
+                      &c->node_topo, &c->node_info, &c->node_key, &c->node_geo, &c->node_invrho, &c->split_cnt,
+                      &c->split_off, &c->scan_tmp, &c->ws, &c->spack, &c->mom, &c->ab64, &c->ab32, &c->tkeys,
+                      &c->tkeys_alt, &c->tperm, &c->tperm_alt, &c->ts, &c->nfar_e, &c->nnear_e,
+                      &c->far_off, &c->near_off, &c->far_list, &c->near_list, &c->cnt_far, &c->cnt_near, &c->u_far,
+                      &c->u_near, &c->flags};
+    for (DevBuf* b : bufs) release(*b);
+}
+
+extern "C" {
+
+tc_status tc_create(tc_ctx** out, const tc_config* cfg)
+{
+    tc_ctx* ctx = nullptr;
+    if (!out) return fail(nullptr, TC_EINVAL, "tc_create: out is NULL");
+    *out = nullptr;
+    tc_config c = {TC_MIXED, 1, nullptr, 0, 0};
+    if (cfg) c = *cfg;
+    if (c.precision != TC_FP64 && c.precision != TC_MIXED)
+        return fail(nullptr, TC_EINVAL, "tc_create: unknown precision %d", c.precision);
+    if (c.shrink != 0 && c.shrink != 1) return fail(nullptr, TC_EINVAL, "tc_create: shrink must be 0 or 1");
+    if (c.reserved0 != 0 || c.reserved1 != 0) return fail(nullptr, TC_EINVAL, "tc_create: reserved fields must be 0");
+    ctx = new (std::nothrow) tc_ctx();
+    if (!ctx) return fail(nullptr, TC_ENOMEM, "tc_create: out of host memory");
+    cudaError_t e = cudaGetDevice(&ctx->device);
+    if (e == cudaSuccess) e = ensure(ctx->flags, 256);
+    if (e == cudaSuccess) e = ensure(ctx->scan_tmp, 256);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->flags.p, 0, 256, (cudaStream_t)c.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)c.stream);
+    if (e != cudaSuccess) {
+        tc_status st = cuda_fail(nullptr, e, "tc_create");
+        release_all(ctx);
+        delete ctx;
+        return st;
+    }
+    ctx->precision = c.precision;
+    ctx->shrink = c.shrink;
+    ctx->stream = (cudaStream_t)c.stream;
+    ctx->err = "no error";
+    *out = ctx;
+    return TC_OK;
+}
+
+tc_status tc_destroy(tc_ctx* ctx)
+{
+    if (!ctx) return TC_OK;
+    cudaStreamSynchronize(ctx->stream);
+    release_all(ctx);
+    delete ctx;
+    return TC_OK;
+}
+
+const char* tc_last_error(const tc_ctx* ctx)
+{
+    if (ctx) return ctx->err.c_str();
+    return g_thread_err.c_str();
+}
+
+static tc_status check_flags(tc_ctx* ctx)
+{
+    int32_t f = 0;
+    TC_CK(cudaMemcpyAsync(&f, ctx->flags.p, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream), "flags");
+    TC_CK(cudaStreamSynchronize(ctx->stream), "flags sync");
+    if (f & kFlagStack) return fail(ctx, TC_EDEVICE, "device check: traversal stack bound exceeded");
+    if (f & kFlagIndex) return fail(ctx, TC_EDEVICE, "device check: index out of range");
+    if (f) return fail(ctx, TC_EDEVICE, "device check: flags 0x%x", f);
+    return TC_OK;
+}
+
+tc_status tc_sync(tc_ctx* ctx)
+{
+    if (!ctx) return fail(nullptr, TC_EINVAL, "tc_sync: ctx is NULL");
+    TC_CK(cudaStreamSynchronize(ctx->stream), "tc_sync");
+    return check_flags(ctx);
+}
+
+tc_status tc_build(tc_ctx* ctx, const double* x, int64_t N, int32_t N0)
+{
+    if (!ctx) return fail(nullptr, TC_EINVAL, "tc_build: ctx is NULL");
+    if (!x) return fail(ctx, TC_EINVAL, "tc_build: x is NULL");
+    if (N < 1 || N >= ((int64_t)1 << 31)) return fail(ctx, TC_EINVAL, "tc_build: N = %lld out of [1, 2^31)", (long long)N);
+    if (N0 < 1) return fail(ctx, TC_EINVAL, "tc_build: N0 = %d must be >= 1", N0);
+    cudaStream_t s = ctx->stream;
+    ctx->built = ctx->have_moments = ctx->have_eval = 0;
+    ctx->ab_p = -1;
+    ctx->N = N;
+    ctx->N0 = N0;
+    int nblk = (int)((N + 255) / 256);
+    if (nblk > 152 * 4) nblk = 152 * 4;
+    int nrad = radix_blocks(N);
+    TC_CK(ensure(ctx->root, 64), "alloc root");
+    TC_CK(ensure(ctx->bbox_part, (size_t)nblk * 6 * sizeof(double)), "alloc bbox");
+    TC_CK(ensure(ctx->keys, (size_t)N * 8), "alloc keys");
+    TC_CK(ensure(ctx->keys_alt, (size_t)N * 8), "alloc keys");
+    TC_CK(ensure(ctx->perm, (size_t)N * 4), "alloc perm");
+    TC_CK(ensure(ctx->perm_alt, (size_t)N * 4), "alloc perm");
+    TC_CK(ensure(ctx->hist, (size_t)256 * nrad * 4), "alloc hist");
+    TC_CK(ensure(ctx->xs, (size_t)3 * N * 8), "alloc xs");
+
+    TC_CK(launch_bbox(x, N, ptr<double>(ctx->bbox_part), nblk, ptr<double>(ctx->root), s), "bbox");
+    TC_CK(launch_keys(x, N, ptr<double>(ctx->root), ptr<uint64_t>(ctx->keys), ptr<int32_t>(ctx->perm), 0, s), "keys");
+    TC_CK(radix_sort(ptr<uint64_t>(ctx->keys), ptr<int32_t>(ctx->perm), ptr<uint64_t>(ctx->keys_alt),
+                     ptr<int32_t>(ctx->perm_alt), ptr<uint32_t>(ctx->hist), N, s),
+          "sort");
+    TC_CK(launch_gather3(x, ptr<int32_t>(ctx->perm), N, ptr<double>(ctx->xs), s), "gather x");
+    double root[6];
+    TC_CK(cudaMemcpyAsync(root, ctx->root.p, sizeof(root), cudaMemcpyDeviceToHost, s), "root copy");
+    TC_CK(cudaStreamSynchronize(s), "root sync");
+    if (root[5] != 0.0) return fail(ctx, TC_EINVAL, "tc_build: x holds a NaN or an infinity");
+    for (int a = 0; a < 3; a++) ctx->lo[a] = root[a];
+    ctx->side = root[3];
+
+    // level-synchronous topology
+    size_t cap = 1024;
+    TC_CK(grow_keep(ctx->node_topo, cap * sizeof(int4), 0, s), "alloc nodes");
+    TC_CK(grow_keep(ctx->node_info, cap * sizeof(int4), 0, s), "alloc nodes");
+    TC_CK(grow_keep(ctx->node_key, cap * sizeof(uint64_t), 0, s), "alloc nodes");
+    TC_CK(launch_init_root(ptr<int4>(ctx->node_topo), ptr<int4>(ctx->node_info), ptr<uint64_t>(ctx->node_key), N, s),
+          "root node");
+    ctx->level_begin.assign(1, 0);
+    int64_t lb = 0, le = 1;
+    for (int level = 0; level < kMaxDepth; level++) {
+        int64_t n = le - lb;
+        TC_CK(ensure(ctx->split_cnt, (size_t)n * 4), "alloc split");
+        TC_CK(ensure(ctx->split_off, (size_t)n * 4), "alloc split");
+        TC_CK(launch_split_count(ptr<int4>(ctx->node_topo), ptr<int4>(ctx->node_info), ptr<uint64_t>(ctx->keys), lb, le,
+                                 N0, ptr<int32_t>(ctx->split_cnt), s),
+              "split count");
+        TC_CK(launch_scan_i32(ptr<int32_t>(ctx->split_cnt), ptr<int32_t>(ctx->split_off), n,
+                              ptr<int32_t>(ctx->scan_tmp), s),
+              "split scan");
+        int32_t total = 0;
+        TC_CK(cudaMemcpyAsync(&total, ctx->scan_tmp.p, 4, cudaMemcpyDeviceToHost, s), "split total");
+        TC_CK(cudaStreamSynchronize(s), "split sync");
+        if (total == 0) break;
+        if ((size_t)(le + total) > cap) {
+            size_t ncap = cap;
+            while (ncap < (size_t)(le + total)) ncap *= 2;
+            TC_CK(grow_keep(ctx->node_topo, ncap * sizeof(int4), (size_t)le * sizeof(int4), s), "grow nodes");
+            TC_CK(grow_keep(ctx->node_info, ncap * sizeof(int4), (size_t)le * sizeof(int4), s), "grow nodes");
+            TC_CK(grow_keep(ctx->node_key, ncap * sizeof(uint64_t), (size_t)le * sizeof(uint64_t), s), "grow nodes");
+            cap = ncap;
+        }
+        TC_CK(launch_split_write(ptr<int4>(ctx->node_topo), ptr<int4>(ctx->node_info), ptr<uint64_t>(ctx->node_key),
+                                 ptr<uint64_t>(ctx->keys), lb, le, N0, ptr<int32_t>(ctx->split_off), s),
+              "split write");
+        ctx->level_begin.push_back(le);
+        lb = le;
+        le += total;
+    }
+    ctx->level_begin.push_back(le);
+    ctx->nnodes = le;
+    ctx->depth = (int)ctx->level_begin.size() - 2;
+    TC_CK(ensure(ctx->node_geo, (size_t)le * sizeof(Geo)), "alloc geo");
+    TC_CK(ensure(ctx->node_invrho, (size_t)le * sizeof(double)), "alloc geo");
+    TC_CK(launch_geometry(ptr<int4>(ctx->node_topo), ptr<int4>(ctx->node_info), ptr<uint64_t>(ctx->node_key),
+                          ptr<double>(ctx->xs), N, le, ptr<double>(ctx->root), ctx->shrink, ptr<Geo>(ctx->node_geo),
+                          ptr<double>(ctx->node_invrho), s),
+          "geometry");
+    ctx->built = 1;
+    return TC_OK;
+}
+
+tc_status tc_moments(tc_ctx* ctx, const double* f, const double* h, const double* nu, int32_t p)
+{
+    if (!ctx) return fail(nullptr, TC_EINVAL, "tc_moments: ctx is NULL");
+    if (!ctx->built) return fail(ctx, TC_ESTATE, "tc_moments: call tc_build first");
+    if (!f || !h || !nu) return fail(ctx, TC_EINVAL, "tc_moments: a weight pointer is NULL");
+    if (p < 0 || p > kPMax) return fail(ctx, TC_EINVAL, "tc_moments: p = %d out of [0, %d]", p, kPMax);
+    cudaStream_t s = ctx->stream;
+    const int64_t N = ctx->N;
+    ctx->have_moments = ctx->have_eval = 0;
+    ctx->ab_p = -1;
+    TC_CK(ensure(ctx->ws, (size_t)9 * N * 8), "alloc weights");
+    TC_CK(ensure(ctx->mom, (size_t)ctx->nnodes * 12 * ncoef(p) * 8), "alloc moments");
+    TC_CK(launch_gather_weights(f, h, nu, ptr<int32_t>(ctx->perm), N, ptr<double>(ctx->ws), s), "gather weights");
+    if (ctx->precision == TC_MIXED) {
+        TC_CK(ensure(ctx->spack, (size_t)N * 64), "alloc pack");
+        TC_CK(launch_source_pack(ptr<double>(ctx->xs), ptr<double>(ctx->ws), N, ptr<float4>(ctx->spack), s), "pack");
+    }
+    TC_CK(launch_moments(ptr<int4>(ctx->node_topo), ptr<Geo>(ctx->node_geo), ptr<double>(ctx->xs),
+                         ptr<double>(ctx->ws), N, ctx->nnodes, p, ptr<double>(ctx->mom), s),
+          "moments");
+    ctx->p_mom = p;
+    ctx->have_moments = 1;
+    return TC_OK;
+}
+
+static tc_status ensure_tables(tc_ctx* ctx, int p)
+{
+    if (ctx->ab_p == p) return TC_OK;
+    cudaStream_t s = ctx->stream;
+    int64_t n = ctx->nnodes * ncoef(p + 2) * 12;
+    double* ab64 = nullptr;
+    float* ab32 = nullptr;
+    if (ctx->precision == TC_FP64) {
+        TC_CK(ensure(ctx->ab64, (size_t)n * 8), "alloc tables");
+        ab64 = ptr<double>(ctx->ab64);
+    } else {
+        TC_CK(ensure(ctx->ab32, (size_t)n * 4), "alloc tables");
+        ab32 = ptr<float>(ctx->ab32);
+    }
+    TC_CK(launch_ab_tables(ptr<double>(ctx->mom), ptr<double>(ctx->node_invrho), ctx->nnodes, ctx->p_mom, p, ab64,
+                           ab32, s),
+          "tables");
+    ctx->ab_p = p;
+    return TC_OK;
+}
+
+tc_status tc_eval(tc_ctx* ctx, const double* targets, int64_t M, double theta, int32_t p, double* u)
+{
+    if (!ctx) return fail(nullptr, TC_EINVAL, "tc_eval: ctx is NULL");
+    if (!ctx->have_moments) return fail(ctx, TC_ESTATE, "tc_eval: call tc_build and tc_moments first");
+    if (!u) return fail(ctx, TC_EINVAL, "tc_eval: u is NULL");
+    if (!(theta > 0.0 && theta < 1.0)) return fail(ctx, TC_EINVAL, "tc_eval: theta = %g out of (0, 1)", theta);
+    if (p < 0 || p > ctx->p_mom)
+        return fail(ctx, TC_EINVAL, "tc_eval: p = %d out of [0, %d] (order of tc_moments)", p, ctx->p_mom);
+    if (!targets && M != ctx->N)
+        return fail(ctx, TC_EINVAL, "tc_eval: targets = NULL requires M = N (%lld)", (long long)ctx->N);
+    if (M < 1 || M >= ((int64_t)1 << 31)) return fail(ctx, TC_EINVAL, "tc_eval: M = %lld out of range", (long long)M);
+    tc_status st = ensure_tables(ctx, p);
+    if (st != TC_OK) return st;
+    cudaStream_t s = ctx->stream;
+    ctx->have_eval = 0;
+    const double* ts;
+    const int32_t* tperm;
+    if (!targets) {
+        ts = ptr<double>(ctx->xs);
+        tperm = ptr<int32_t>(ctx->perm);
+        ctx->eval_self = 1;
+    } else {
+        int nrad = radix_blocks(M);
+        TC_CK(ensure(ctx->tkeys, (size_t)M * 8), "alloc tkeys");
+        TC_CK(ensure(ctx->tkeys_alt, (size_t)M * 8), "alloc tkeys");
+        TC_CK(ensure(ctx->tperm, (size_t)M * 4), "alloc tperm");
+        TC_CK(ensure(ctx->tperm_alt, (size_t)M * 4), "alloc tperm");
+        TC_CK(ensure(ctx->hist, (size_t)256 * nrad * 4), "alloc hist");
+        TC_CK(ensure(ctx->ts, (size_t)3 * M * 8), "alloc ts");
+        TC_CK(launch_keys(targets, M, ptr<double>(ctx->root), ptr<uint64_t>(ctx->tkeys), ptr<int32_t>(ctx->tperm), 1, s),
+              "target keys");
+        TC_CK(radix_sort(ptr<uint64_t>(ctx->tkeys), ptr<int32_t>(ctx->tperm), ptr<uint64_t>(ctx->tkeys_alt),
+                         ptr<int32_t>(ctx->tperm_alt), ptr<uint32_t>(ctx->hist), M, s),
+              "target sort");
+        TC_CK(launch_gather3(targets, ptr<int32_t>(ctx->tperm), M, ptr<double>(ctx->ts), s), "gather targets");
+        ts = ptr<double>(ctx->ts);
+        tperm = ptr<int32_t>(ctx->tperm);
+        ctx->eval_self = 0;
+    }
+    const int64_t nbatch = (M + kBatch - 1) / kBatch;
+    TC_CK(ensure(ctx->nfar_e, (size_t)nbatch * 4), "alloc lists");
+    TC_CK(ensure(ctx->nnear_e, (size_t)nbatch * 4), "alloc lists");
+    TC_CK(ensure(ctx->far_off, (size_t)(nbatch + 1) * 8), "alloc lists");
+    TC_CK(ensure(ctx->near_off, (size_t)(nbatch + 1) * 8), "alloc lists");
+    TC_CK(ensure(ctx->cnt_far, (size_t)M * 8), "alloc counts");
+    TC_CK(ensure(ctx->cnt_near, (size_t)M * 8), "alloc counts");
+    TC_CK(ensure(ctx->u_far, (size_t)3 * M * 8), "alloc u");
+    TC_CK(ensure(ctx->u_near, (size_t)3 * M * 8), "alloc u");
+    TC_CK(cudaMemsetAsync(ctx->flags.p, 0, 4, s), "flags");
+    const int4* topo = ptr<int4>(ctx->node_topo);
+    const Geo* geo = ptr<Geo>(ctx->node_geo);
+    TC_CK(launch_lists(ts, M, topo, geo, theta, 0, ptr<int32_t>(ctx->nfar_e), ptr<int32_t>(ctx->nnear_e), nullptr,
+                       nullptr, nullptr, nullptr, nullptr, nullptr, ptr<int32_t>(ctx->flags), s),
+          "list count");
+    int64_t* far_off = ptr<int64_t>(ctx->far_off);
+    int64_t* near_off = ptr<int64_t>(ctx->near_off);
+    TC_CK(launch_scan_i32_to_i64(ptr<int32_t>(ctx->nfar_e), far_off, nbatch, far_off + nbatch, s), "far scan");
+    TC_CK(launch_scan_i32_to_i64(ptr<int32_t>(ctx->nnear_e), near_off, nbatch, near_off + nbatch, s), "near scan");
+    int64_t tot[2];
+    TC_CK(cudaMemcpyAsync(&tot[0], far_off + nbatch, 8, cudaMemcpyDeviceToHost, s), "list totals");
+    TC_CK(cudaMemcpyAsync(&tot[1], near_off + nbatch, 8, cudaMemcpyDeviceToHost, s), "list totals");
+    st = check_flags(ctx);  // synchronises
+    if (st != TC_OK) return st;
+    TC_CK(ensure(ctx->far_list, (size_t)(tot[0] > 0 ? tot[0] : 1) * sizeof(ListEntry)), "alloc far list");
+    TC_CK(ensure(ctx->near_list, (size_t)(tot[1] > 0 ? tot[1] : 1) * sizeof(ListEntry)), "alloc near list");
+    TC_CK(launch_lists(ts, M, topo, geo, theta, 1, nullptr, nullptr, far_off, near_off,
+                       ptr<ListEntry>(ctx->far_list), ptr<ListEntry>(ctx->near_list), ptr<int64_t>(ctx->cnt_far),
+                       ptr<int64_t>(ctx->cnt_near), ptr<int32_t>(ctx->flags), s),
+          "list write");
+    TC_CK(launch_far(ctx->precision, ts, M, geo, ptr<double>(ctx->node_invrho), ptr<double>(ctx->ab64),
+                     ptr<float>(ctx->ab32), p, far_off, ptr<ListEntry>(ctx->far_list), ptr<double>(ctx->u_far), s),
+          "far field");
+    TC_CK(launch_near(ctx->precision, ts, M, topo, ptr<double>(ctx->xs), ptr<double>(ctx->ws),
+                      ptr<float4>(ctx->spack), ctx->N, near_off, ptr<ListEntry>(ctx->near_list),
+                      ptr<double>(ctx->u_near), s),
+          "near field");
+    TC_CK(launch_finalize(ptr<double>(ctx->u_far), ptr<double>(ctx->u_near), tperm, M, u, s), "finalize");
+    ctx->M = M;
+    ctx->stat_far = tot[0];
+    ctx->have_eval = 1;
+    return TC_OK;
+}
+
+tc_status tc_direct(const double* x, const double* f, const double* h, const double* nu, int64_t N,
+                    const double* targets, int64_t M, int32_t precision, void* stream, double* u)
+{
+    tc_ctx* ctx = nullptr;
+    if (!x || !f || !h || !nu || !u) return fail(nullptr, TC_EINVAL, "tc_direct: a pointer is NULL");
+    if (N < 1 || N >= ((int64_t)1 << 31)) return fail(nullptr, TC_EINVAL, "tc_direct: N out of range");
+    if (!targets && M != N) return fail(nullptr, TC_EINVAL, "tc_direct: targets = NULL requires M = N");
+    if (M < 1 || M >= ((int64_t)1 << 31)) return fail(nullptr, TC_EINVAL, "tc_direct: M out of range");
+    if (precision != TC_FP64 && precision != TC_MIXED) return fail(nullptr, TC_EINVAL, "tc_direct: unknown precision");
+    cudaStream_t s = (cudaStream_t)stream;
+    size_t bytes = direct_scratch_bytes(precision, N, M);
+    void* scratch = nullptr;
+    TC_CK(cudaMallocAsync(&scratch, bytes, s), "tc_direct scratch");
+    cudaError_t e = launch_direct(precision, x, f, h, nu, N, targets ? targets : x, M, u, scratch, bytes, s);
+    cudaError_t e2 = cudaFreeAsync(scratch, s);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "tc_direct");
+    if (e2 != cudaSuccess) return cuda_fail(nullptr, e2, "tc_direct free");
+    return TC_OK;
+}
+
+tc_status tc_stats(tc_ctx* ctx, int64_t* near_pairs, int64_t* far_interactions, int64_t* clusters)
+{
+    if (!ctx) return fail(nullptr, TC_EINVAL, "tc_stats: ctx is NULL");
+    if (clusters) *clusters = ctx->built ? ctx->nnodes : 0;
+    if (!near_pairs && !far_interactions) return TC_OK;
+    if (!ctx->have_eval) return fail(ctx, TC_ESTATE, "tc_stats: no evaluation yet");
+    cudaStream_t s = ctx->stream;
+    int64_t* tmp = ptr<int64_t>(ctx->scan_tmp);
+    TC_CK(launch_sum_i64(ptr<int64_t>(ctx->cnt_near), ctx->M, tmp, s), "stats");
+    TC_CK(launch_sum_i64(ptr<int64_t>(ctx->cnt_far), ctx->M, tmp + 1, s), "stats");
+    int64_t h[2];
+    TC_CK(cudaMemcpyAsync(h, tmp, 16, cudaMemcpyDeviceToHost, s), "stats copy");
+    TC_CK(cudaStreamSynchronize(s), "stats sync");
+    if (near_pairs) *near_pairs = h[0];
+    if (far_interactions) *far_interactions = h[1];
+    return TC_OK;
+}
+
+tc_status tc_eval_counts(tc_ctx* ctx, int64_t* nfar, int64_t* nnear_pairs)
+{
+    if (!ctx) return fail(nullptr, TC_EINVAL, "tc_eval_counts: ctx is NULL");
+    if (!ctx->have_eval) return fail(ctx, TC_ESTATE, "tc_eval_counts: no evaluation yet");
+    const int32_t* perm = ctx->eval_self ? ptr<int32_t>(ctx->perm) : ptr<int32_t>(ctx->tperm);
+    if (nfar) TC_CK(launch_scatter_counts(ptr<int64_t>(ctx->cnt_far), perm, ctx->M, nfar, ctx->stream), "counts");
+    if (nnear_pairs)
+        TC_CK(launch_scatter_counts(ptr<int64_t>(ctx->cnt_near), perm, ctx->M, nnear_pairs, ctx->stream), "counts");
+    return TC_OK;
+}
+
+tc_status tc_tree_info(tc_ctx* ctx, int64_t* nnodes, int32_t* depth, double* lo, double* side)
+{
+    if (!ctx) return fail(nullptr, TC_EINVAL, "tc_tree_info: ctx is NULL");
+    if (!ctx->built) return fail(ctx, TC_ESTATE, "tc_tree_info: no tree");
+    if (nnodes) *nnodes = ctx->nnodes;
+    if (depth) *depth = ctx->depth;
+    if (lo)
+        for (int a = 0; a < 3; a++) lo[a] = ctx->lo[a];
+    if (side) *side = ctx->side;
+    return TC_OK;
+}
+
+static uint32_t host_compact3(uint64_t x)
+{
+    uint32_t v = 0;
+    for (int j = 0; j < 21; j++) v |= (uint32_t)((x >> (3 * j)) & 1u) << j;
+    return v;
+}
+
+tc_status tc_tree_export(tc_ctx* ctx, int32_t* begin, int32_t* count, int32_t* level, int32_t* cell, int32_t* parent,
+                         int32_t* first_child, int32_t* nchild, double* yc, double* rc2)
+{
+    if (!ctx) return fail(nullptr, TC_EINVAL, "tc_tree_export: ctx is NULL");
+    if (!ctx->built) return fail(ctx, TC_ESTATE, "tc_tree_export: no tree");
+    const int64_t n = ctx->nnodes;
+    std::vector<int4> topo(n), info(n);
+    std::vector<uint64_t> key(n);
+    std::vector<Geo> geo(n);
+    cudaStream_t s = ctx->stream;
+    TC_CK(cudaMemcpyAsync(topo.data(), ctx->node_topo.p, n * sizeof(int4), cudaMemcpyDeviceToHost, s), "export");
+    TC_CK(cudaMemcpyAsync(info.data(), ctx->node_info.p, n * sizeof(int4), cudaMemcpyDeviceToHost, s), "export");
+    TC_CK(cudaMemcpyAsync(key.data(), ctx->node_key.p, n * sizeof(uint64_t), cudaMemcpyDeviceToHost, s), "export");
+    TC_CK(cudaMemcpyAsync(geo.data(), ctx->node_geo.p, n * sizeof(Geo), cudaMemcpyDeviceToHost, s), "export");
+    TC_CK(cudaStreamSynchronize(s), "export sync");
+    for (int64_t i = 0; i < n; i++) {
+        if (begin) begin[i] = topo[i].x;
+        if (count) count[i] = topo[i].y;
+        if (first_child) first_child[i] = topo[i].z;
+        if (nchild) nchild[i] = topo[i].w;
+        if (level) level[i] = info[i].x;
+        if (parent) parent[i] = info[i].y;
+        if (cell) {
+            int L = info[i].x;
+            cell[3 * i + 0] = (int32_t)(host_compact3(key[i] >> 2) >> (kMaxDepth - L));
+            cell[3 * i + 1] = (int32_t)(host_compact3(key[i] >> 1) >> (kMaxDepth - L));
+            cell[3 * i + 2] = (int32_t)(host_compact3(key[i]) >> (kMaxDepth - L));
+        }
+        if (yc) {
+            yc[3 * i + 0] = geo[i].x;
+            yc[3 * i + 1] = geo[i].y;
+            yc[3 * i + 2] = geo[i].z;
+        }
+        if (rc2) rc2[i] = geo[i].w;
+    }
+    return TC_OK;
+}
+
+tc_status tc_tree_order(tc_ctx* ctx, int32_t* order)
+{
+    if (!ctx || !order) return fail(ctx, TC_EINVAL, "tc_tree_order: NULL argument");
+    if (!ctx->built) return fail(ctx, TC_ESTATE, "tc_tree_order: no tree");
+    TC_CK(cudaMemcpyAsync(order, ctx->perm.p, ctx->N * 4, cudaMemcpyDeviceToHost, ctx->stream), "order");
+    TC_CK(cudaStreamSynchronize(ctx->stream), "order sync");
+    return TC_OK;
+}
+
+tc_status tc_moments_export(tc_ctx* ctx, int64_t node, double* Mf, double* Mt)
+{
+    if (!ctx) return fail(nullptr, TC_EINVAL, "tc_moments_export: ctx is NULL");
+    if (!ctx->have_moments) return fail(ctx, TC_ESTATE, "tc_moments_export: no moments");
+    if (node < 0 || node >= ctx->nnodes) return fail(ctx, TC_EINVAL, "tc_moments_export: node out of range");
+    const int p = ctx->p_mom, C = ncoef(p), q1 = p + 1;
+    std::vector<double> m((size_t)12 * C);
+    TC_CK(cudaMemcpyAsync(m.data(), ptr<double>(ctx->mom) + node * 12 * C, m.size() * 8, cudaMemcpyDeviceToHost,
+                          ctx->stream),
+          "moments export");
+    TC_CK(cudaStreamSynchronize(ctx->stream), "moments export sync");
+    const size_t cube = (size_t)q1 * q1 * q1;
+    if (Mf) memset(Mf, 0, 3 * cube * 8);
+    if (Mt) memset(Mt, 0, 9 * cube * 8);
+    for (int k1 = 0; k1 <= p; k1++)
+        for (int k2 = 0; k1 + k2 <= p; k2++)
+            for (int k3 = 0; k1 + k2 + k3 <= p; k3++) {
+                int idx = flat_index(k1, k2, k3);
+                size_t o = ((size_t)k1 * q1 + k2) * q1 + k3;
+                for (int c = 0; c < 3; c++)
+                    if (Mf) Mf[c * cube + o] = m[(size_t)c * C + idx];
+                for (int c = 0; c < 9; c++)
+                    if (Mt) Mt[c * cube + o] = m[(size_t)(3 + c) * C + idx];
+            }
+    return TC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,217 @@
+// Direct O(N*M) evaluation of eq. (1.3) in the contracted form of
+// Section 4.1 (the reference u^d of eq. 6.1 for the error E).
+//
+// Warps own 32 targets; the source range is split into `nsplit` chunks along
+// gridDim.y so that few targets (e.g. 10^4 sampled targets against 10^6
+// sources) still fill the GPU.  Each split writes a partial sum to scratch;
+// a second kernel adds the partials in split order (deterministic).
+#include "tc_internal.cuh"
+
+namespace tc {
+
+namespace {
+
+constexpr int kDirWarps = 4;
+constexpr int kDirTargetWarps = 152 * 32;  // aim for about this many warps in flight
+
+__global__ void k_direct_pack(const double* __restrict__ x, const double* __restrict__ f,
+                              const double* __restrict__ h, const double* __restrict__ nu, int64_t N,
+                              float4* __restrict__ pack)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    float hi[3], lo[3];
+    for (int a = 0; a < 3; a++) {
+        double v = x[a * N + i];
+        hi[a] = (float)v;
+        lo[a] = (float)(v - (double)hi[a]);
+    }
+    pack[4 * i + 0] = make_float4(hi[0], hi[1], hi[2], (float)f[i]);
+    pack[4 * i + 1] = make_float4(lo[0], lo[1], lo[2], (float)f[N + i]);
+    pack[4 * i + 2] = make_float4((float)f[2 * N + i], (float)h[i], (float)h[N + i], (float)h[2 * N + i]);
+    pack[4 * i + 3] = make_float4((float)nu[i], (float)nu[N + i], (float)nu[2 * N + i], 0.0f);
+}
+
+__global__ void __launch_bounds__(kDirWarps * 32)
+    k_direct_mixed(const double* __restrict__ t, int64_t M, const float4* __restrict__ pack, int64_t N, int64_t chunk,
+                   double* __restrict__ part)
+{
+    __shared__ float4 tile[kDirWarps][32][4];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t nbatch = (M + 31) / 32;
+    const int64_t b = blockIdx.x * (int64_t)kDirWarps + w;
+    if (b >= nbatch) return;
+    const int64_t m = b * 32 + lane;
+    const bool valid = m < M;
+    float th[3] = {0, 0, 0}, tl[3] = {0, 0, 0};
+    if (valid)
+        for (int a = 0; a < 3; a++) {
+            double v = t[a * M + m];
+            th[a] = (float)v;
+            tl[a] = (float)(v - (double)th[a]);
+        }
+    const int64_t s0 = blockIdx.y * chunk, s1 = min(N, s0 + chunk);
+    double ux = 0.0, uy = 0.0, uz = 0.0;
+    for (int64_t base = s0; base < s1; base += 32) {
+        const int cnt = (int)min((int64_t)32, s1 - base);
+        __syncwarp();
+        if (lane < cnt) {
+            const float4* src = pack + 4 * (base + lane);
+            tile[w][lane][0] = src[0];
+            tile[w][lane][1] = src[1];
+            tile[w][lane][2] = src[2];
+            tile[w][lane][3] = src[3];
+        }
+        __syncwarp();
+        float ax = 0.f, ay = 0.f, az = 0.f;
+        for (int j = 0; j < cnt; j++) {
+            const float4 p0 = tile[w][j][0], p1 = tile[w][j][1], p2 = tile[w][j][2], p3 = tile[w][j][3];
+            const float dx = (th[0] - p0.x) + (tl[0] - p1.x);
+            const float dy = (th[1] - p0.y) + (tl[1] - p1.y);
+            const float dz = (th[2] - p0.z) + (tl[2] - p1.z);
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const float ri = r2 > 0.f ? rsqrtf(r2) : 0.f;
+            const float ri2 = ri * ri;
+            const float ri3 = ri2 * ri;
+            const float df = fmaf(dx, p0.w, fmaf(dy, p1.w, dz * p2.x));
+            const float dh = fmaf(dx, p2.y, fmaf(dy, p2.z, dz * p2.w));
+            const float dn = fmaf(dx, p3.x, fmaf(dy, p3.y, dz * p3.z));
+            const float st = ri3 * fmaf(dh * dn, ri2, df);
+            ax = fmaf(p0.w, ri, fmaf(dx, st, ax));
+            ay = fmaf(p1.w, ri, fmaf(dy, st, ay));
+            az = fmaf(p2.x, ri, fmaf(dz, st, az));
+        }
+        ux += (double)ax;
+        uy += (double)ay;
+        uz += (double)az;
+    }
+    if (valid) {
+        double* o = part + (int64_t)blockIdx.y * 3 * M;
+        o[m] = ux;
+        o[M + m] = uy;
+        o[2 * M + m] = uz;
+    }
+}
+
+__global__ void __launch_bounds__(kDirWarps * 32)
+    k_direct_fp64(const double* __restrict__ t, int64_t M, const double* __restrict__ x, const double* __restrict__ f,
+                  const double* __restrict__ h, const double* __restrict__ nu, int64_t N, int64_t chunk,
+                  double* __restrict__ part)
+{
+    __shared__ double tile[kDirWarps][12][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t nbatch = (M + 31) / 32;
+    const int64_t b = blockIdx.x * (int64_t)kDirWarps + w;
+    if (b >= nbatch) return;
+    const int64_t m = b * 32 + lane;
+    const bool valid = m < M;
+    double tx[3] = {0, 0, 0};
+    if (valid)
+        for (int a = 0; a < 3; a++) tx[a] = t[a * M + m];
+    const int64_t s0 = blockIdx.y * chunk, s1 = min(N, s0 + chunk);
+    double ux = 0.0, uy = 0.0, uz = 0.0;
+    for (int64_t base = s0; base < s1; base += 32) {
+        const int cnt = (int)min((int64_t)32, s1 - base);
+        __syncwarp();
+        if (lane < cnt) {
+            const int64_t i = base + lane;
+            for (int a = 0; a < 3; a++) {
+                tile[w][a][lane] = x[a * N + i];
+                tile[w][3 + a][lane] = f[a * N + i];
+                tile[w][6 + a][lane] = h[a * N + i];
+                tile[w][9 + a][lane] = nu[a * N + i];
+            }
+        }
+        __syncwarp();
+        for (int j = 0; j < cnt; j++) {
+            const double dx = tx[0] - tile[w][0][j], dy = tx[1] - tile[w][1][j], dz = tx[2] - tile[w][2][j];
+            const double r2 = dx * dx + dy * dy + dz * dz;
+            const double ri = r2 > 0.0 ? rsqrt(r2) : 0.0;
+            const double ri2 = ri * ri, ri3 = ri2 * ri;
+            const double f0 = tile[w][3][j], f1 = tile[w][4][j], f2 = tile[w][5][j];
+            const double df = dx * f0 + dy * f1 + dz * f2;
+            const double dh = dx * tile[w][6][j] + dy * tile[w][7][j] + dz * tile[w][8][j];
+            const double dn = dx * tile[w][9][j] + dy * tile[w][10][j] + dz * tile[w][11][j];
+            const double st = ri3 * (df + dh * dn * ri2);
+            ux += f0 * ri + dx * st;
+            uy += f1 * ri + dy * st;
+            uz += f2 * ri + dz * st;
+        }
+    }
+    if (valid) {
+        double* o = part + (int64_t)blockIdx.y * 3 * M;
+        o[m] = ux;
+        o[M + m] = uy;
+        o[2 * M + m] = uz;
+    }
+}
+
+__global__ void k_direct_reduce(const double* __restrict__ part, int nsplit, int64_t M, double* __restrict__ u)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= 3 * M) return;
+    double s = 0.0;
+    for (int k = 0; k < nsplit; k++) s += part[(int64_t)k * 3 * M + i];
+    u[i] = s;
+}
+
+struct DirectPlan {
+    int nsplit;
+    int64_t chunk;
+    size_t pack_bytes, part_bytes;
+};
+
+DirectPlan plan_direct(int precision, int64_t N, int64_t M)
+{
+    DirectPlan pl;
+    int64_t nwarps = (M + 31) / 32;
+    int64_t want = (kDirTargetWarps + nwarps - 1) / nwarps;
+    int64_t maxsplit = N / 512 > 1 ? N / 512 : 1;
+    if (want > maxsplit) want = maxsplit;
+    if (want > 65535) want = 65535;
+    if (want < 1) want = 1;
+    pl.chunk = (N + want - 1) / want;
+    pl.chunk = (pl.chunk + 31) / 32 * 32;
+    pl.nsplit = (int)((N + pl.chunk - 1) / pl.chunk);
+    if (pl.nsplit < 1) pl.nsplit = 1;
+    pl.pack_bytes = precision == TC_FP64 ? 0 : (size_t)N * 64;
+    pl.part_bytes = (size_t)pl.nsplit * 3 * (size_t)M * sizeof(double);
+    return pl;
+}
+
+inline unsigned grid_for(int64_t n, int threads)
+{
+    int64_t g = (n + threads - 1) / threads;
+    return (unsigned)(g > 0 ? g : 1);
+}
+
+}  // namespace
+
+size_t direct_scratch_bytes(int precision, int64_t N, int64_t M)
+{
+    DirectPlan pl = plan_direct(precision, N, M);
+    return ((pl.pack_bytes + 255) / 256) * 256 + pl.part_bytes;
+}
+
+cudaError_t launch_direct(int precision, const double* x, const double* f, const double* h, const double* nu,
+                          int64_t N, const double* t, int64_t M, double* u, void* scratch, size_t scratch_bytes,
+                          cudaStream_t s)
+{
+    DirectPlan pl = plan_direct(precision, N, M);
+    size_t pack_off = ((pl.pack_bytes + 255) / 256) * 256;
+    if (scratch_bytes < pack_off + pl.part_bytes) return cudaErrorInvalidValue;
+    float4* pack = reinterpret_cast<float4*>(scratch);
+    double* part = reinterpret_cast<double*>(reinterpret_cast<char*>(scratch) + pack_off);
+    int64_t nbatch = (M + 31) / 32;
+    dim3 grid((unsigned)((nbatch + kDirWarps - 1) / kDirWarps), (unsigned)pl.nsplit);
+    if (precision == TC_FP64) {
+        k_direct_fp64<<<grid, kDirWarps * 32, 0, s>>>(t, M, x, f, h, nu, N, pl.chunk, part);
+    } else {
+        k_direct_pack<<<grid_for(N, 256), 256, 0, s>>>(x, f, h, nu, N, pack);
+        k_direct_mixed<<<grid, kDirWarps * 32, 0, s>>>(t, M, pack, N, pl.chunk, part);
+    }
+    k_direct_reduce<<<grid_for(3 * M, 256), 256, 0, s>>>(part, pl.nsplit, M, u);
+    return cudaGetLastError();
+}
+
+}  // namespace tc

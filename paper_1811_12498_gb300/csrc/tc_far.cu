@@ -1,0 +1,151 @@
+// Far field: particle-cluster Taylor approximation, eq. (2.9), evaluated in
+// the contracted form of the contraction tables (tc_moments.cu):
+//   u_i += sum_{||k'|| <= p+2} b^{k'}(d') ( Â_i^{k'} + sum_l d'_l B̂_il^{k'} ),
+// with d' = (x - y_c) / rho and the Coulomb coefficients b^{k'}(d') from the
+// recurrence (3.2):
+//   n R'^2 b^k = (2n-1) sum_i d'_i b^{k-e_i} - (n-1) sum_i b^{k-2e_i},  n = ||k||,
+//   b^0 = 1/R',  R' = |d'|.
+//
+// One warp handles a batch of 32 targets (one per lane) and walks the batch's
+// far list; a lane outside an entry's mask idles for that entry.  The
+// recurrence runs level by level; only levels n-2, n-1 and n are live, kept in
+// a per-warp shared-memory ring laid out [slot][position][lane] (no bank
+// conflicts).  Each coefficient is contracted against the cluster's 12 table
+// entries as soon as it is produced.
+//
+// Precision: TR is the recurrence type, TC the table/contraction type.
+// FP64 mode: TR = TC = double.  Mixed: TC = float, TR = double for p >= 8 and
+// float below.  Each cluster's contribution is added to an FP64 per-target
+// accumulator.
+#include "tc_internal.cuh"
+
+namespace tc {
+
+namespace {
+
+constexpr int kFarWarps = 2;
+
+template <typename T>
+__device__ inline T rsqrt_t(double x);
+template <>
+__device__ inline double rsqrt_t<double>(double x) { return rsqrt(x); }
+template <>
+__device__ inline float rsqrt_t<float>(double x) { return rsqrtf((float)x); }
+
+template <typename TC>
+__device__ inline void contract(TC bk, const TC* __restrict__ t, TC* acc)
+{
+#pragma unroll
+    for (int c = 0; c < 12; c++) acc[c] = fma(bk, t[c], acc[c]);
+}
+
+template <typename TR, typename TC>
+__global__ void __launch_bounds__(kFarWarps * 32)
+    k_far(const double* __restrict__ ts, int64_t M, const Geo* __restrict__ geo,
+          const double* __restrict__ invrho, const TC* __restrict__ ab, int p, const int64_t* __restrict__ far_off,
+          const ListEntry* __restrict__ far_list, double* __restrict__ u_far)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t nbatch = (M + kBatch - 1) / kBatch;
+    const int64_t b = blockIdx.x * (int64_t)kFarWarps + w;
+    if (b >= nbatch) return;
+    const int P = p + 2;
+    const int LS = level_size(P);
+    const int C2 = ncoef(P);
+    TR* ring = reinterpret_cast<TR*>(smraw) + (size_t)w * 3 * LS * 32;
+    const int64_t m = b * kBatch + lane;
+    const bool valid = m < M;
+    double x0 = 0, x1 = 0, x2 = 0;
+    if (valid) {
+        x0 = ts[m];
+        x1 = ts[M + m];
+        x2 = ts[2 * M + m];
+    }
+    double ux = 0.0, uy = 0.0, uz = 0.0;
+    const int64_t e0 = far_off[b], e1 = far_off[b + 1];
+    for (int64_t e = e0; e < e1; e++) {
+        const ListEntry le = far_list[e];
+        const bool in = (le.mask >> lane) & 1u;
+        const Geo g = geo[le.node];
+        const double ir = invrho[le.node];
+        const double d0 = (x0 - g.x) * ir, d1 = (x1 - g.y) * ir, d2 = (x2 - g.z) * ir;
+        double R2 = d0 * d0 + d1 * d1 + d2 * d2;
+        if (!in) R2 = 1.0;  // keep idle lanes finite
+        const TR iR2 = (TR)(1.0 / R2);
+        const TR dd0 = (TR)d0, dd1 = (TR)d1, dd2 = (TR)d2;
+        const TC* __restrict__ tab = ab + (int64_t)le.node * C2 * 12;
+        TC acc[12];
+#pragma unroll
+        for (int c = 0; c < 12; c++) acc[c] = (TC)0;
+        TR b0 = rsqrt_t<TR>(R2);
+        ring[lane] = b0;  // slot 0, position 0
+        contract<TC>((TC)b0, tab, acc);
+        for (int n = 1; n <= P; n++) {
+            const TR alpha = (TR)(2 * n - 1) / (TR)n * iR2;
+            const TR beta = (TR)(n - 1) / (TR)n * iR2;
+            TR* Rn = ring + (n % 3) * LS * 32;
+            const TR* R1 = ring + ((n - 1) % 3) * LS * 32;
+            const TR* Rm = ring + ((n + 1) % 3) * LS * 32;  // level n-2
+            const TC* tl = tab + (int64_t)ncoef(n - 1) * 12;
+            for (int a = 0; a <= n; a++) {
+                const int k1 = n - a;
+                const int base = a * (a + 1) / 2;
+                for (int k3 = 0; k3 <= a; k3++) {
+                    const int k2 = a - k3;
+                    const int pos = base + k3;
+                    TR s1 = 0, s2 = 0;
+                    if (k1 >= 1) s1 = dd0 * R1[pos * 32 + lane];
+                    if (k2 >= 1) s1 = fma(dd1, R1[(pos - a) * 32 + lane], s1);
+                    if (k3 >= 1) s1 = fma(dd2, R1[(pos - a - 1) * 32 + lane], s1);
+                    if (k1 >= 2) s2 = Rm[pos * 32 + lane];
+                    if (k2 >= 2) s2 += Rm[(pos - 2 * a + 1) * 32 + lane];
+                    if (k3 >= 2) s2 += Rm[(pos - 2 * a - 1) * 32 + lane];
+                    const TR bk = fma(alpha, s1, -beta * s2);
+                    Rn[pos * 32 + lane] = bk;
+                    contract<TC>((TC)bk, tl + pos * 12, acc);
+                }
+            }
+        }
+        if (in) {
+            const TC e0c = (TC)d0, e1c = (TC)d1, e2c = (TC)d2;
+            const TC v0 = acc[0] + e0c * acc[3] + e1c * acc[4] + e2c * acc[5];
+            const TC v1 = acc[1] + e0c * acc[6] + e1c * acc[7] + e2c * acc[8];
+            const TC v2 = acc[2] + e0c * acc[9] + e1c * acc[10] + e2c * acc[11];
+            ux += (double)v0;
+            uy += (double)v1;
+            uz += (double)v2;
+        }
+    }
+    if (valid) {
+        u_far[m] = ux;
+        u_far[M + m] = uy;
+        u_far[2 * M + m] = uz;
+    }
+}
+
+template <typename TR, typename TC>
+cudaError_t run_far(const double* ts, int64_t M, const Geo* geo, const double* invrho, const TC* ab, int p,
+                    const int64_t* far_off, const ListEntry* far_list, double* u_far, cudaStream_t s)
+{
+    int64_t nbatch = (M + kBatch - 1) / kBatch;
+    unsigned grid = (unsigned)((nbatch + kFarWarps - 1) / kFarWarps);
+    size_t smem = (size_t)kFarWarps * 3 * level_size(p + 2) * 32 * sizeof(TR);
+    cudaError_t e = cudaFuncSetAttribute(k_far<TR, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_far<TR, TC><<<grid, kFarWarps * 32, smem, s>>>(ts, M, geo, invrho, ab, p, far_off, far_list, u_far);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_far(int precision, const double* ts, int64_t M, const Geo* geo, const double* invrho,
+                       const double* ab64, const float* ab32, int p, const int64_t* far_off,
+                       const ListEntry* far_list, double* u_far, cudaStream_t s)
+{
+    if (precision == TC_FP64) return run_far<double, double>(ts, M, geo, invrho, ab64, p, far_off, far_list, u_far, s);
+    if (p >= 8) return run_far<double, float>(ts, M, geo, invrho, ab32, p, far_off, far_list, u_far, s);
+    return run_far<float, float>(ts, M, geo, invrho, ab32, p, far_off, far_list, u_far, s);
+}
+
+}  // namespace tc

@@ -1,0 +1,185 @@
+// Internal declarations shared by the translation units of libtc.
+// Not part of the C ABI (see include/tc.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/tc.h"
+
+namespace tc {
+
+constexpr int kMaxDepth = 21;   // 21-bit quantised coordinates, 63-bit Morton keys
+constexpr int kPMax = 12;       // largest Taylor order accepted
+constexpr int kQMax = kPMax + 2;  // far field needs Coulomb coefficients to p+2
+constexpr int kBatch = 32;      // targets per interaction list (one warp)
+constexpr int kStack = 8 * (kMaxDepth + 1);  // traversal stack bound (7 siblings/level + 8)
+
+// number of multi-indices with ||k|| == n, and with ||k|| <= n
+__host__ __device__ constexpr int level_size(int n) { return (n + 1) * (n + 2) / 2; }
+__host__ __device__ constexpr int ncoef(int n) { return (n + 1) * (n + 2) * (n + 3) / 6; }
+
+// Flattened graded order: level by level; inside a level k1 descending, then
+// k2 descending.  With a = k2 + k3 the position inside level n is
+// a(a+1)/2 + k3, and the flat index is ncoef(n-1) + that.
+__host__ __device__ inline int flat_index(int k1, int k2, int k3)
+{
+    int n = k1 + k2 + k3, a = k2 + k3;
+    return (n > 0 ? ncoef(n - 1) : 0) + a * (a + 1) / 2 + k3;
+}
+
+// Error flags raised by kernels (bit mask in device memory).
+enum DevFlag : int {
+    kFlagStack = 1,     // traversal stack bound exceeded
+    kFlagIndex = 2,     // an index check failed
+};
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t cap = 0;
+};
+
+// Cluster centre y_c and squared radius r^2 (32-byte aligned record).
+struct __align__(32) Geo {
+    double x, y, z, w;
+};
+
+// 8-byte list entry: cluster id and the mask of batch lanes it applies to.
+struct ListEntry {
+    int32_t node;
+    uint32_t mask;
+};
+
+}  // namespace tc
+
+struct tc_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int precision = TC_MIXED;
+    int shrink = 1;
+    std::string err;
+
+    // ---- tree (tc_build)
+    int built = 0;
+    int64_t N = 0;
+    int N0 = 0;
+    int depth = 0;
+    int64_t nnodes = 0;
+    std::vector<int64_t> level_begin;  // node index where each level starts (+ end)
+    double lo[3] = {0, 0, 0}, side = 0;
+    tc::DevBuf root;                    // double[8]: lo[3], side, scale
+    tc::DevBuf bbox_part;               // per-block min/max partials
+    tc::DevBuf keys, keys_alt;          // uint64 Morton keys
+    tc::DevBuf perm, perm_alt;          // int32 permutation (Morton -> caller)
+    tc::DevBuf hist;                    // radix histograms
+    tc::DevBuf xs;                      // 3*N FP64 sorted positions
+    tc::DevBuf node_topo;               // int4 {begin, count, first_child, nchild}
+    tc::DevBuf node_info;               // int4 {level, parent, 0, 0}
+    tc::DevBuf node_key;                // uint64 Morton prefix
+    tc::DevBuf node_geo;                // Geo {yc, rc2}
+    tc::DevBuf node_invrho;             // double 1/rho (rho = r, or 1 if r == 0)
+    tc::DevBuf split_cnt, split_off;    // per-level scan buffers
+    tc::DevBuf scan_tmp;                // device scalar(s)
+
+    // ---- moments (tc_moments)
+    int have_moments = 0;
+    int p_mom = -1;
+    tc::DevBuf ws;                      // 9*N FP64 sorted weights: f(3) h(3) nu(3)
+    tc::DevBuf spack;                   // MIXED source pack: 4 float4 per source
+    tc::DevBuf mom;                     // FP64 [node][12][ncoef(p)]
+    int ab_p = -1;                      // order the contraction tables were built for
+    tc::DevBuf ab64;                    // FP64 [node][ncoef(p+2)][12]
+    tc::DevBuf ab32;                    // FP32 [node][ncoef(p+2)][12]
+
+    // ---- evaluation (tc_eval)
+    int64_t M = 0;
+    int eval_self = 1;
+    tc::DevBuf tkeys, tkeys_alt, tperm, tperm_alt;  // disjoint targets
+    tc::DevBuf ts;                      // 3*M FP64 sorted targets
+    tc::DevBuf nfar_e, nnear_e;         // per batch entry counts (int32)
+    tc::DevBuf far_off, near_off;       // per batch exclusive offsets (int64)
+    tc::DevBuf far_list, near_list;     // ListEntry
+    tc::DevBuf cnt_far, cnt_near;       // per sorted target counts (int64)
+    tc::DevBuf u_far, u_near;           // 3*M FP64 sorted order
+    tc::DevBuf flags;                   // int32 device error flags
+    int64_t stat_near_pairs = 0, stat_far = 0;
+    int have_eval = 0;
+};
+
+namespace tc {
+
+// error helpers (tc_api.cu)
+tc_status fail(tc_ctx* ctx, tc_status st, const char* fmt, ...);
+tc_status cuda_fail(tc_ctx* ctx, cudaError_t e, const char* where);
+void set_thread_error(const char* msg);
+
+// grow a device buffer to hold at least `bytes`; contents are not preserved
+cudaError_t ensure(DevBuf& b, size_t bytes);
+void release(DevBuf& b);
+
+template <typename T>
+inline T* ptr(DevBuf& b) { return reinterpret_cast<T*>(b.p); }
+
+// ---- launchers (each returns cudaGetLastError() after enqueueing)
+// tc_build.cu
+cudaError_t launch_bbox(const double* x, int64_t N, double* part, int nblk, double* root, cudaStream_t s);
+cudaError_t launch_keys(const double* x, int64_t N, const double* root, uint64_t* keys, int32_t* idx,
+                        int clamp_outside, cudaStream_t s);
+int radix_blocks(int64_t N);
+cudaError_t radix_sort(uint64_t* keys, int32_t* vals, uint64_t* keys_alt, int32_t* vals_alt, uint32_t* hist,
+                       int64_t N, cudaStream_t s);
+cudaError_t launch_gather3(const double* src, const int32_t* perm, int64_t N, double* dst, cudaStream_t s);
+cudaError_t launch_init_root(int4* topo, int4* info, uint64_t* nkey, int64_t N, cudaStream_t s);
+cudaError_t launch_split_count(const int4* topo, const int4* info, const uint64_t* keys, int64_t lb, int64_t le,
+                               int N0, int32_t* cnt, cudaStream_t s);
+cudaError_t launch_scan_i32(const int32_t* in, int32_t* out_excl, int64_t n, int32_t* total, cudaStream_t s);
+cudaError_t launch_split_write(int4* topo, int4* info, uint64_t* nkey, const uint64_t* keys, int64_t lb, int64_t le,
+                               int N0, const int32_t* off, cudaStream_t s);
+cudaError_t launch_geometry(const int4* topo, const int4* info, const uint64_t* nkey, const double* xs, int64_t N,
+                            int64_t nnodes, const double* root, int shrink, Geo* geo, double* invrho,
+                            cudaStream_t s);
+
+// tc_moments.cu
+cudaError_t launch_gather_weights(const double* f, const double* h, const double* nu, const int32_t* perm,
+                                  int64_t N, double* ws, cudaStream_t s);
+cudaError_t launch_source_pack(const double* xs, const double* ws, int64_t N, float4* pack, cudaStream_t s);
+cudaError_t launch_moments(const int4* topo, const Geo* geo, const double* xs, const double* ws, int64_t N,
+                           int64_t nnodes, int p, double* mom, cudaStream_t s);
+cudaError_t launch_ab_tables(const double* mom, const double* invrho, int64_t nnodes, int pm, int p, double* ab64,
+                             float* ab32, cudaStream_t s);
+
+// tc_lists.cu
+cudaError_t launch_lists(const double* ts, int64_t M, const int4* topo, const Geo* geo, double theta,
+                         int write, int32_t* nfar_e, int32_t* nnear_e, const int64_t* far_off,
+                         const int64_t* near_off, ListEntry* far_list, ListEntry* near_list, int64_t* cnt_far,
+                         int64_t* cnt_near, int32_t* flags, cudaStream_t s);
+cudaError_t launch_scan_i32_to_i64(const int32_t* in, int64_t* out_excl, int64_t n, int64_t* total,
+                                   cudaStream_t s);
+cudaError_t launch_sum_i64(const int64_t* in, int64_t n, int64_t* out, cudaStream_t s);
+
+// tc_far.cu
+cudaError_t launch_far(int precision, const double* ts, int64_t M, const Geo* geo, const double* invrho,
+                       const double* ab64, const float* ab32, int p, const int64_t* far_off,
+                       const ListEntry* far_list, double* u_far, cudaStream_t s);
+
+// tc_near.cu
+cudaError_t launch_near(int precision, const double* ts, int64_t M, const int4* topo,
+                        const double* xs, const double* ws, const float4* spack, int64_t N,
+                        const int64_t* near_off, const ListEntry* near_list, double* u_near, cudaStream_t s);
+cudaError_t launch_finalize(const double* u_far, const double* u_near, const int32_t* perm, int64_t M, double* u,
+                            cudaStream_t s);
+cudaError_t launch_scatter_counts(const int64_t* cs, const int32_t* perm, int64_t M, int64_t* out,
+                                  cudaStream_t s);
+
+// tc_direct.cu
+cudaError_t launch_direct(int precision, const double* x, const double* f, const double* h, const double* nu,
+                          int64_t N, const double* t, int64_t M, double* u, void* scratch, size_t scratch_bytes,
+                          cudaStream_t s);
+size_t direct_scratch_bytes(int precision, int64_t N, int64_t M);
+
+}  // namespace tc

@@ -1,0 +1,162 @@
+// MAC traversal (Algorithm 1, eq. 5.1) producing per-batch interaction lists.
+//
+// A batch is 32 consecutive Morton-ordered targets, one per lane of a warp.
+// The warp walks the tree with an explicit stack of (cluster, lane mask)
+// entries.  At a cluster every lane still in the mask tests its own MAC in
+// FP64; the lanes that pass get a far-field entry, the lanes that fail
+// descend (or get a near-field entry at a leaf).  Each target therefore meets
+// exactly the clusters, and makes exactly the decisions, of Algorithm 1 run on
+// its own.  Children are pushed so that they are visited in octant order.
+//
+// The kernel runs twice: once to count entries per batch, once (after an
+// exclusive scan of the counts) to write them.
+#include "tc_internal.cuh"
+
+namespace tc {
+
+namespace {
+
+constexpr int kListWarps = 4;
+
+__global__ void __launch_bounds__(kListWarps * 32)
+    k_lists(const double* __restrict__ ts, int64_t M, const int4* __restrict__ topo,
+            const Geo* __restrict__ geo, double theta2, int write, int32_t* __restrict__ nfar_e,
+            int32_t* __restrict__ nnear_e, const int64_t* __restrict__ far_off, const int64_t* __restrict__ near_off,
+            ListEntry* __restrict__ far_list, ListEntry* __restrict__ near_list, int64_t* __restrict__ cnt_far,
+            int64_t* __restrict__ cnt_near, int32_t* __restrict__ flags)
+{
+    __shared__ ListEntry stack[kListWarps][kStack];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t nbatch = (M + kBatch - 1) / kBatch;
+    const int64_t b = blockIdx.x * (int64_t)kListWarps + w;
+    if (b >= nbatch) return;
+    const int64_t m = b * kBatch + lane;
+    const bool valid = m < M;
+    double x0 = 0, x1 = 0, x2 = 0;
+    if (valid) {
+        x0 = ts[m];
+        x1 = ts[M + m];
+        x2 = ts[2 * M + m];
+    }
+    ListEntry* st = stack[w];
+    int sp = 0;
+    const unsigned active = __ballot_sync(0xffffffffu, valid);
+    if (lane == 0) st[0] = ListEntry{0, active};
+    sp = 1;
+    __syncwarp();
+    int64_t nf = 0, nn = 0, my_far = 0, my_near = 0;
+    const int64_t fo = write ? far_off[b] : 0, no = write ? near_off[b] : 0;
+    bool overflow = false;
+    while (sp > 0) {
+        ListEntry e = st[--sp];
+        __syncwarp();
+        int4 t = topo[e.node];
+        Geo g = geo[e.node];
+        bool in = (e.mask >> lane) & 1u;
+        double dx = __dsub_rn(x0, g.x), dy = __dsub_rn(x1, g.y), dz = __dsub_rn(x2, g.z);
+        double R2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+        bool pass = in && (R2 > 0.0) && (g.w <= __dmul_rn(theta2, R2));
+        unsigned pm = __ballot_sync(0xffffffffu, pass);
+        unsigned fm = e.mask & ~pm;
+        if (pm) {
+            if (write && lane == 0) far_list[fo + nf] = ListEntry{e.node, pm};
+            nf++;
+            my_far += pass;
+        }
+        if (fm) {
+            if (t.w == 0) {
+                if (write && lane == 0) near_list[no + nn] = ListEntry{e.node, fm};
+                nn++;
+                if (in && !pass) my_near += t.y;
+            } else {
+                if (sp + t.w > kStack) {
+                    overflow = true;
+                    break;
+                }
+                if (lane == 0)
+                    for (int c = t.w - 1; c >= 0; c--) st[sp + (t.w - 1 - c)] = ListEntry{t.z + c, fm};
+                sp += t.w;
+            }
+        }
+        __syncwarp();
+    }
+    if (overflow && lane == 0) atomicOr(flags, kFlagStack);
+    if (!write && lane == 0) {
+        nfar_e[b] = (int32_t)nf;
+        nnear_e[b] = (int32_t)nn;
+    }
+    if (valid && cnt_far) {
+        cnt_far[m] = my_far;
+        cnt_near[m] = my_near;
+    }
+}
+
+__global__ void k_scan_i32_to_i64(const int32_t* __restrict__ in, int64_t* __restrict__ out, int64_t n,
+                                  int64_t* __restrict__ total)
+{
+    __shared__ int64_t part[1024];
+    int t = threadIdx.x;
+    int64_t chunk = (n + blockDim.x - 1) / blockDim.x;
+    int64_t b = t * chunk, e = b + chunk < n ? b + chunk : n;
+    int64_t s = 0;
+    for (int64_t i = b; i < e; i++) s += in[i];
+    part[t] = s;
+    __syncthreads();
+    for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+        int64_t v = t >= o ? part[t - o] : 0;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    int64_t run = part[t] - s;
+    for (int64_t i = b; i < e; i++) {
+        int64_t v = in[i];
+        out[i] = run;
+        run += v;
+    }
+    if (t == (int)blockDim.x - 1) *total = part[t];
+}
+
+__global__ void k_sum_i64(const int64_t* __restrict__ in, int64_t n, int64_t* __restrict__ out)
+{
+    __shared__ int64_t part[1024];
+    int64_t s = 0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += in[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) part[threadIdx.x] += part[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = part[0];
+}
+
+}  // namespace
+
+cudaError_t launch_lists(const double* ts, int64_t M, const int4* topo, const Geo* geo, double theta,
+                         int write, int32_t* nfar_e, int32_t* nnear_e, const int64_t* far_off,
+                         const int64_t* near_off, ListEntry* far_list, ListEntry* near_list, int64_t* cnt_far,
+                         int64_t* cnt_near, int32_t* flags, cudaStream_t s)
+{
+    int64_t nbatch = (M + kBatch - 1) / kBatch;
+    unsigned grid = (unsigned)((nbatch + kListWarps - 1) / kListWarps);
+    double theta2 = theta * theta;
+    k_lists<<<grid, kListWarps * 32, 0, s>>>(ts, M, topo, geo, theta2, write, nfar_e, nnear_e, far_off, near_off,
+                                             far_list, near_list, cnt_far, cnt_near, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan_i32_to_i64(const int32_t* in, int64_t* out_excl, int64_t n, int64_t* total,
+                                   cudaStream_t s)
+{
+    k_scan_i32_to_i64<<<1, 1024, 0, s>>>(in, out_excl, n, total);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sum_i64(const int64_t* in, int64_t n, int64_t* out, cudaStream_t s)
+{
+    k_sum_i64<<<1, 1024, 0, s>>>(in, n, out);
+    return cudaGetLastError();
+}
+
+}  // namespace tc

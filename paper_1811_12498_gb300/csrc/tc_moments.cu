@@ -1,0 +1,263 @@
+// Cluster moments (Section 2) and the per-cluster contraction tables of the
+// far field.
+//
+// Moments, for every cluster C and ||k|| <= p, in FP64:
+//   M_j^k   = sum_{n in C} (y^n - y_c)^k f_j^n                 (comp j = 0..2)
+//   M~_jl^k = sum_{n in C} (y^n - y_c)^k h_j^n nu_l^n          (comp 3 + 3j + l)
+// stored as mom[node][comp][flat(k)] in the graded order of tc_internal.cuh.
+//
+// Contraction tables.  Substituting eq. (3.4) into sum_k a^k_ij M_j^k and
+// eq. (3.7) into sum_k a~^k_ijl M~_jl^k and collecting by the index k' of the
+// Coulomb coefficient b^{k'} gives, for ||k'|| <= p + 2,
+//   u_i = sum_{k'} b^{k'} ( A_i^{k'} + sum_l d_l B_il^{k'} ),   d = x - y_c,
+// with (terms whose moment index is negative or above p vanish)
+//   A_i^{k'}  = M_i^{k'} - k'_i sum_j M_j^{k'-e_i+e_j}
+//             + 1/3 sum_l k'_l M~_il^{k'-e_l}
+//             - 1/3 sum_{j,l} (k'_i - delta_ij) k'_j M~_jl^{k'-e_i-e_j+e_l}
+//   B_il^{k'} = k'_i M_l^{k'-e_i} + 1/3 sum_j k'_i (k'_j - delta_ij) M~_jl^{k'-e_i-e_j}.
+// This is the same sum as eqs. (4.4) + (4.9) regrouped: every term there is
+// b^{k'} times a cluster constant or times one component of d (sigma^k and
+// tau_j are linear in d), so the per-target work becomes one pass over b.
+//
+// Scaling.  b^{k'} is homogeneous of degree -(||k'||+1) in d, so with
+// rho = cluster radius, d' = d / rho:
+//   u_i = sum_{k'} b^{k'}(d') ( Â_i^{k'} + sum_l d'_l B̂_il^{k'} ),
+//   Â = A rho^-(n+1),  B̂ = B rho^-n,  n = ||k'||.
+// Under the MAC |d'| >= 1/theta, so every b^{k'}(d') is at most about
+// theta^n and the tables stay well inside FP32 range for deep trees.
+#include "tc_internal.cuh"
+
+namespace tc {
+
+namespace {
+
+__device__ inline void unflatten(int idx, int& k1, int& k2, int& k3)
+{
+    int n = 0;
+    while (ncoef(n) <= idx) n++;
+    int pos = idx - (n > 0 ? ncoef(n - 1) : 0);
+    int a = 0;
+    while ((a + 1) * (a + 2) / 2 <= pos) a++;
+    k3 = pos - a * (a + 1) / 2;
+    k2 = a - k3;
+    k1 = n - a;
+}
+
+__global__ void k_gather_weights(const double* __restrict__ f, const double* __restrict__ h,
+                                 const double* __restrict__ nu, const int32_t* __restrict__ perm, int64_t N,
+                                 double* __restrict__ ws)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    int64_t j = perm[i];
+    for (int a = 0; a < 3; a++) {
+        ws[a * N + i] = f[a * N + j];
+        ws[(3 + a) * N + i] = h[a * N + j];
+        ws[(6 + a) * N + i] = nu[a * N + j];
+    }
+}
+
+// FP32 source record for the mixed near field: position split as hi + lo
+// (hi = fl32(x), lo = fl32(x - hi)), then f, h, nu.
+__global__ void k_source_pack(const double* __restrict__ xs, const double* __restrict__ ws, int64_t N,
+                              float4* __restrict__ pack)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    float hi[3], lo[3];
+    for (int a = 0; a < 3; a++) {
+        double v = xs[a * N + i];
+        hi[a] = (float)v;
+        lo[a] = (float)(v - (double)hi[a]);
+    }
+    float w[9];
+    for (int c = 0; c < 9; c++) w[c] = (float)ws[c * N + i];
+    pack[4 * i + 0] = make_float4(hi[0], hi[1], hi[2], w[0]);
+    pack[4 * i + 1] = make_float4(lo[0], lo[1], lo[2], w[1]);
+    pack[4 * i + 2] = make_float4(w[2], w[3], w[4], w[5]);
+    pack[4 * i + 3] = make_float4(w[6], w[7], w[8], 0.0f);
+}
+
+constexpr int kMomThreads = 128;
+constexpr int kMomChunk = 32;
+constexpr int kMomSlots = (ncoef(kPMax) + kMomThreads - 1) / kMomThreads;
+
+// One block per cluster.  Particles are staged in chunks: their powers of
+// (y - y_c) per axis and their 12 weights; each thread owns a few k.
+__global__ void __launch_bounds__(kMomThreads) k_moments(const int4* __restrict__ topo,
+                                                         const Geo* __restrict__ geo,
+                                                         const double* __restrict__ xs,
+                                                         const double* __restrict__ ws, int64_t N, int p,
+                                                         double* __restrict__ mom)
+{
+    __shared__ double pw[3][kMomChunk][kPMax + 1];
+    __shared__ double wt[kMomChunk][12];
+    int64_t node = blockIdx.x;
+    int4 t = topo[node];
+    Geo g = geo[node];
+    const int C = ncoef(p);
+    int kk[kMomSlots][3];
+    double acc[kMomSlots][12];
+    for (int s = 0; s < kMomSlots; s++) {
+        int idx = threadIdx.x + s * kMomThreads;
+        if (idx < C)
+            unflatten(idx, kk[s][0], kk[s][1], kk[s][2]);
+        else
+            kk[s][0] = kk[s][1] = kk[s][2] = 0;
+        for (int c = 0; c < 12; c++) acc[s][c] = 0.0;
+    }
+    for (int base = t.x; base < t.x + t.y; base += kMomChunk) {
+        int nq = min(kMomChunk, t.x + t.y - base);
+        __syncthreads();
+        if (threadIdx.x < nq) {
+            int i = base + threadIdx.x;
+            double d[3] = {xs[i] - g.x, xs[N + i] - g.y, xs[2 * N + i] - g.z};
+            for (int a = 0; a < 3; a++) {
+                double v = 1.0;
+                pw[a][threadIdx.x][0] = 1.0;
+                for (int k = 1; k <= p; k++) {
+                    v *= d[a];
+                    pw[a][threadIdx.x][k] = v;
+                }
+            }
+            double f0 = ws[i], f1 = ws[N + i], f2 = ws[2 * N + i];
+            double h[3] = {ws[3 * N + i], ws[4 * N + i], ws[5 * N + i]};
+            double nu[3] = {ws[6 * N + i], ws[7 * N + i], ws[8 * N + i]};
+            wt[threadIdx.x][0] = f0;
+            wt[threadIdx.x][1] = f1;
+            wt[threadIdx.x][2] = f2;
+            for (int j = 0; j < 3; j++)
+                for (int l = 0; l < 3; l++) wt[threadIdx.x][3 + 3 * j + l] = h[j] * nu[l];
+        }
+        __syncthreads();
+        for (int s = 0; s < kMomSlots; s++) {
+            if (threadIdx.x + s * kMomThreads >= C) break;
+            for (int q = 0; q < nq; q++) {
+                double mono = pw[0][q][kk[s][0]] * pw[1][q][kk[s][1]] * pw[2][q][kk[s][2]];
+                for (int c = 0; c < 12; c++) acc[s][c] = fma(mono, wt[q][c], acc[s][c]);
+            }
+        }
+    }
+    for (int s = 0; s < kMomSlots; s++) {
+        int idx = threadIdx.x + s * kMomThreads;
+        if (idx >= C) break;
+        for (int c = 0; c < 12; c++) mom[(node * 12 + c) * C + idx] = acc[s][c];
+    }
+}
+
+// moment of component c at multi-index (k1,k2,k3); 0 outside 0 <= k, ||k|| <= p
+__device__ inline double mget(const double* m, int C, int p, int c, int k1, int k2, int k3)
+{
+    if (k1 < 0 || k2 < 0 || k3 < 0 || k1 + k2 + k3 > p) return 0.0;
+    return m[c * C + flat_index(k1, k2, k3)];
+}
+
+// One thread per (cluster, k'), ||k'|| <= p + 2.  Output layout
+// [node][flat(k')][12]: A_0..A_2, then B_il at 3 + 3i + l.
+// Moments are stored at order pm >= p; only ||k|| <= p enter the tables.
+__global__ void k_ab_tables(const double* __restrict__ mom, const double* __restrict__ invrho, int64_t nnodes,
+                            int pm, int p, double* __restrict__ ab64, float* __restrict__ ab32)
+{
+    const int C = ncoef(pm), C2 = ncoef(p + 2);
+    int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (gid >= nnodes * C2) return;
+    int64_t node = gid / C2;
+    int kidx = (int)(gid - node * C2);
+    int kp[3];
+    unflatten(kidx, kp[0], kp[1], kp[2]);
+    const int n = kp[0] + kp[1] + kp[2];
+    const double* m = mom + node * 12 * C;
+    double A[3] = {0, 0, 0}, B[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    const double third = 1.0 / 3.0;
+    for (int i = 0; i < 3; i++) {
+        int ei[3] = {i == 0, i == 1, i == 2};
+        // Stokeslet part
+        double a = mget(m, C, p, i, kp[0], kp[1], kp[2]);
+        double s = 0.0;
+        for (int j = 0; j < 3; j++) {
+            int ej[3] = {j == 0, j == 1, j == 2};
+            s += mget(m, C, p, j, kp[0] - ei[0] + ej[0], kp[1] - ei[1] + ej[1], kp[2] - ei[2] + ej[2]);
+        }
+        a -= kp[i] * s;
+        // stresslet part
+        double t3 = 0.0, t2 = 0.0;
+        for (int l = 0; l < 3; l++) {
+            int el[3] = {l == 0, l == 1, l == 2};
+            t3 += kp[l] * mget(m, C, p, 3 + 3 * i + l, kp[0] - el[0], kp[1] - el[1], kp[2] - el[2]);
+        }
+        for (int j = 0; j < 3; j++) {
+            int ej[3] = {j == 0, j == 1, j == 2};
+            double cj = (double)(kp[i] - (i == j)) * kp[j];
+            if (cj == 0.0) continue;
+            for (int l = 0; l < 3; l++) {
+                int el[3] = {l == 0, l == 1, l == 2};
+                t2 += cj * mget(m, C, p, 3 + 3 * j + l, kp[0] - ei[0] - ej[0] + el[0], kp[1] - ei[1] - ej[1] + el[1],
+                                kp[2] - ei[2] - ej[2] + el[2]);
+            }
+        }
+        A[i] = a + third * (t3 - t2);
+        for (int l = 0; l < 3; l++) {
+            double bv = kp[i] * mget(m, C, p, l, kp[0] - ei[0], kp[1] - ei[1], kp[2] - ei[2]);
+            double tb = 0.0;
+            for (int j = 0; j < 3; j++) {
+                int ej[3] = {j == 0, j == 1, j == 2};
+                double cj = (double)kp[i] * (kp[j] - (i == j));
+                if (cj == 0.0) continue;
+                tb += cj * mget(m, C, p, 3 + 3 * j + l, kp[0] - ei[0] - ej[0], kp[1] - ei[1] - ej[1],
+                                kp[2] - ei[2] - ej[2]);
+            }
+            B[i][l] = bv + third * tb;
+        }
+    }
+    double ir = invrho[node];
+    double sB = 1.0;
+    for (int q = 0; q < n; q++) sB *= ir;  // rho^-n
+    double sA = sB * ir;                    // rho^-(n+1)
+    double out[12];
+    for (int i = 0; i < 3; i++) out[i] = A[i] * sA;
+    for (int i = 0; i < 3; i++)
+        for (int l = 0; l < 3; l++) out[3 + 3 * i + l] = B[i][l] * sB;
+    int64_t o = gid * 12;
+    if (ab64)
+        for (int c = 0; c < 12; c++) ab64[o + c] = out[c];
+    if (ab32)
+        for (int c = 0; c < 12; c++) ab32[o + c] = (float)out[c];
+}
+
+inline unsigned grid_for(int64_t n, int threads)
+{
+    int64_t g = (n + threads - 1) / threads;
+    return (unsigned)(g > 0 ? g : 1);
+}
+
+}  // namespace
+
+cudaError_t launch_gather_weights(const double* f, const double* h, const double* nu, const int32_t* perm,
+                                  int64_t N, double* ws, cudaStream_t s)
+{
+    k_gather_weights<<<grid_for(N, 256), 256, 0, s>>>(f, h, nu, perm, N, ws);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_source_pack(const double* xs, const double* ws, int64_t N, float4* pack, cudaStream_t s)
+{
+    k_source_pack<<<grid_for(N, 256), 256, 0, s>>>(xs, ws, N, pack);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_moments(const int4* topo, const Geo* geo, const double* xs, const double* ws, int64_t N,
+                           int64_t nnodes, int p, double* mom, cudaStream_t s)
+{
+    k_moments<<<(unsigned)nnodes, kMomThreads, 0, s>>>(topo, geo, xs, ws, N, p, mom);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ab_tables(const double* mom, const double* invrho, int64_t nnodes, int pm, int p, double* ab64,
+                             float* ab32, cudaStream_t s)
+{
+    int64_t total = nnodes * ncoef(p + 2);
+    k_ab_tables<<<grid_for(total, 128), 128, 0, s>>>(mom, invrho, nnodes, pm, p, ab64, ab32);
+    return cudaGetLastError();
+}
+
+}  // namespace tc

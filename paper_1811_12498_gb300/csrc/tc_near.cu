@@ -1,0 +1,197 @@
+// Near field: direct summation over the leaves that fail the MAC, in the
+// contracted form of Section 4.1:
+//   u_i += f_i / r + d_i (s + t),  s = (d.f) / r^3,  t = (d.h)(d.nu) / r^5,
+// d = x - y, skipping pairs with r == 0 (the n != m exclusion of eq. 1.3).
+//
+// One warp handles a batch of 32 targets and walks the batch's near list.
+// Sources are streamed through a per-warp shared-memory tile of 32 records
+// (one coalesced load per lane, then broadcast reads).
+//
+// Mixed precision: positions are split as x = hi + lo (both FP32) and
+// d = (x_hi - y_hi) + (x_lo - y_lo), so d keeps FP32 relative accuracy even
+// for close pairs; pair terms are FP32; each 32-source tile's partial sum
+// is added to an FP64 per-target accumulator.  FP64 mode computes everything
+// in FP64.
+#include "tc_internal.cuh"
+
+namespace tc {
+
+namespace {
+
+constexpr int kNearWarps = 4;
+
+__global__ void __launch_bounds__(kNearWarps * 32)
+    k_near_mixed(const double* __restrict__ ts, int64_t M, const int4* __restrict__ topo,
+                 const float4* __restrict__ spack, const int64_t* __restrict__ near_off,
+                 const ListEntry* __restrict__ near_list, double* __restrict__ u_near)
+{
+    __shared__ float4 tile[kNearWarps][32][4];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t nbatch = (M + kBatch - 1) / kBatch;
+    const int64_t b = blockIdx.x * (int64_t)kNearWarps + w;
+    if (b >= nbatch) return;
+    const int64_t m = b * kBatch + lane;
+    const bool valid = m < M;
+    float th[3] = {0, 0, 0}, tl[3] = {0, 0, 0};
+    if (valid) {
+        for (int a = 0; a < 3; a++) {
+            double v = ts[a * M + m];
+            th[a] = (float)v;
+            tl[a] = (float)(v - (double)th[a]);
+        }
+    }
+    double ux = 0.0, uy = 0.0, uz = 0.0;
+    const int64_t e0 = near_off[b], e1 = near_off[b + 1];
+    for (int64_t e = e0; e < e1; e++) {
+        const ListEntry le = near_list[e];
+        const bool in = (le.mask >> lane) & 1u;
+        const int4 t = topo[le.node];
+        for (int base = t.x; base < t.x + t.y; base += 32) {
+            const int cnt = min(32, t.x + t.y - base);
+            __syncwarp();
+            if (lane < cnt) {
+                const float4* src = spack + 4 * (int64_t)(base + lane);
+                tile[w][lane][0] = src[0];
+                tile[w][lane][1] = src[1];
+                tile[w][lane][2] = src[2];
+                tile[w][lane][3] = src[3];
+            }
+            __syncwarp();
+            if (!in) continue;
+            float ax = 0.f, ay = 0.f, az = 0.f;
+            for (int j = 0; j < cnt; j++) {
+                const float4 p0 = tile[w][j][0], p1 = tile[w][j][1], p2 = tile[w][j][2], p3 = tile[w][j][3];
+                const float dx = (th[0] - p0.x) + (tl[0] - p1.x);
+                const float dy = (th[1] - p0.y) + (tl[1] - p1.y);
+                const float dz = (th[2] - p0.z) + (tl[2] - p1.z);
+                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                const float ri = r2 > 0.f ? rsqrtf(r2) : 0.f;
+                const float ri2 = ri * ri;
+                const float ri3 = ri2 * ri;
+                const float df = fmaf(dx, p0.w, fmaf(dy, p1.w, dz * p2.x));
+                const float dh = fmaf(dx, p2.y, fmaf(dy, p2.z, dz * p2.w));
+                const float dn = fmaf(dx, p3.x, fmaf(dy, p3.y, dz * p3.z));
+                const float st = ri3 * fmaf(dh * dn, ri2, df);
+                ax = fmaf(p0.w, ri, fmaf(dx, st, ax));
+                ay = fmaf(p1.w, ri, fmaf(dy, st, ay));
+                az = fmaf(p2.x, ri, fmaf(dz, st, az));
+            }
+            ux += (double)ax;
+            uy += (double)ay;
+            uz += (double)az;
+        }
+    }
+    if (valid) {
+        u_near[m] = ux;
+        u_near[M + m] = uy;
+        u_near[2 * M + m] = uz;
+    }
+}
+
+__global__ void __launch_bounds__(kNearWarps * 32)
+    k_near_fp64(const double* __restrict__ ts, int64_t M, const int4* __restrict__ topo,
+                const double* __restrict__ xs, const double* __restrict__ ws, int64_t N,
+                const int64_t* __restrict__ near_off, const ListEntry* __restrict__ near_list,
+                double* __restrict__ u_near)
+{
+    __shared__ double tile[kNearWarps][12][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t nbatch = (M + kBatch - 1) / kBatch;
+    const int64_t b = blockIdx.x * (int64_t)kNearWarps + w;
+    if (b >= nbatch) return;
+    const int64_t m = b * kBatch + lane;
+    const bool valid = m < M;
+    double tx[3] = {0, 0, 0};
+    if (valid)
+        for (int a = 0; a < 3; a++) tx[a] = ts[a * M + m];
+    double ux = 0.0, uy = 0.0, uz = 0.0;
+    const int64_t e0 = near_off[b], e1 = near_off[b + 1];
+    for (int64_t e = e0; e < e1; e++) {
+        const ListEntry le = near_list[e];
+        const bool in = (le.mask >> lane) & 1u;
+        const int4 t = topo[le.node];
+        for (int base = t.x; base < t.x + t.y; base += 32) {
+            const int cnt = min(32, t.x + t.y - base);
+            __syncwarp();
+            if (lane < cnt) {
+                const int64_t i = base + lane;
+                for (int a = 0; a < 3; a++) tile[w][a][lane] = xs[a * N + i];
+                for (int c = 0; c < 9; c++) tile[w][3 + c][lane] = ws[c * N + i];
+            }
+            __syncwarp();
+            if (!in) continue;
+            for (int j = 0; j < cnt; j++) {
+                const double dx = tx[0] - tile[w][0][j], dy = tx[1] - tile[w][1][j], dz = tx[2] - tile[w][2][j];
+                const double r2 = dx * dx + dy * dy + dz * dz;
+                const double ri = r2 > 0.0 ? rsqrt(r2) : 0.0;
+                const double ri2 = ri * ri, ri3 = ri2 * ri;
+                const double f0 = tile[w][3][j], f1 = tile[w][4][j], f2 = tile[w][5][j];
+                const double df = dx * f0 + dy * f1 + dz * f2;
+                const double dh = dx * tile[w][6][j] + dy * tile[w][7][j] + dz * tile[w][8][j];
+                const double dn = dx * tile[w][9][j] + dy * tile[w][10][j] + dz * tile[w][11][j];
+                const double st = ri3 * (df + dh * dn * ri2);
+                ux += f0 * ri + dx * st;
+                uy += f1 * ri + dy * st;
+                uz += f2 * ri + dz * st;
+            }
+        }
+    }
+    if (valid) {
+        u_near[m] = ux;
+        u_near[M + m] = uy;
+        u_near[2 * M + m] = uz;
+    }
+}
+
+__global__ void k_finalize(const double* __restrict__ uf, const double* __restrict__ un,
+                           const int32_t* __restrict__ perm, int64_t M, double* __restrict__ u)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    int64_t d = perm[i];
+    for (int a = 0; a < 3; a++) u[a * M + d] = uf[a * M + i] + un[a * M + i];
+}
+
+__global__ void k_scatter_counts(const int64_t* __restrict__ cs, const int32_t* __restrict__ perm, int64_t M,
+                                 int64_t* __restrict__ out)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    out[perm[i]] = cs[i];
+}
+
+inline unsigned grid_for(int64_t n, int threads)
+{
+    int64_t g = (n + threads - 1) / threads;
+    return (unsigned)(g > 0 ? g : 1);
+}
+
+}  // namespace
+
+cudaError_t launch_near(int precision, const double* ts, int64_t M, const int4* topo,
+                        const double* xs, const double* ws, const float4* spack, int64_t N,
+                        const int64_t* near_off, const ListEntry* near_list, double* u_near, cudaStream_t s)
+{
+    int64_t nbatch = (M + kBatch - 1) / kBatch;
+    unsigned grid = (unsigned)((nbatch + kNearWarps - 1) / kNearWarps);
+    if (precision == TC_FP64)
+        k_near_fp64<<<grid, kNearWarps * 32, 0, s>>>(ts, M, topo, xs, ws, N, near_off, near_list, u_near);
+    else
+        k_near_mixed<<<grid, kNearWarps * 32, 0, s>>>(ts, M, topo, spack, near_off, near_list, u_near);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const double* u_far, const double* u_near, const int32_t* perm, int64_t M, double* u,
+                            cudaStream_t s)
+{
+    k_finalize<<<grid_for(M, 256), 256, 0, s>>>(u_far, u_near, perm, M, u);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_counts(const int64_t* cs, const int32_t* perm, int64_t M, int64_t* out, cudaStream_t s)
+{
+    k_scatter_counts<<<grid_for(M, 256), 256, 0, s>>>(cs, perm, M, out);
+    return cudaGetLastError();
+}
+
+}  // namespace tc

@@ -1,0 +1,68 @@
+"""The C ABI library loads, exports every entry point declared in
+include/tc.h, and its host-side argument checks answer without a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1811_12498_gb300 import _lib
+    if not os.path.exists(_lib.LIB_PATH):
+        from paper_1811_12498_gb300.build import build
+        build()
+    return _lib.lib()
+
+
+def declared_entry_points():
+    src = open(os.path.join(ROOT, "include", "tc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(tc_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_entry_points()
+    assert len(names) >= 14
+    from paper_1811_12498_gb300._lib import SIGNATURES
+    for n in names:
+        assert hasattr(lib, n), n
+        assert n in SIGNATURES, n
+
+
+def test_host_argument_checks_without_gpu(lib):
+    # each of these returns before touching the CUDA runtime
+    assert lib.tc_create(None, None) == 1
+    assert b"out is NULL" in lib.tc_last_error(None)
+    from paper_1811_12498_gb300._lib import TCConfig
+    h = ctypes.c_void_p()
+    bad = TCConfig(7, 1, None, 0, 0)
+    assert lib.tc_create(ctypes.byref(h), ctypes.byref(bad)) == 1
+    assert b"precision" in lib.tc_last_error(None)
+    bad = TCConfig(0, 2, None, 0, 0)
+    assert lib.tc_create(ctypes.byref(h), ctypes.byref(bad)) == 1
+    assert lib.tc_build(None, None, 10, 5) == 1
+    assert lib.tc_moments(None, None, None, None, 4) == 1
+    assert lib.tc_eval(None, None, 10, 0.5, 4, None) == 1
+    assert lib.tc_direct(None, None, None, None, 10, None, 10, 0, None, None) == 1
+    assert b"NULL" in lib.tc_last_error(None)
+    assert lib.tc_destroy(None) == 0
+    assert lib.tc_sync(None) == 1
+
+
+def test_oracle_and_library_share_no_code():
+    """The CUDA sources never include or mention the oracle, and the oracle
+    never includes the CUDA headers."""
+    csrc = os.path.join(ROOT, "paper_1811_12498_gb300", "csrc")
+    for f in os.listdir(csrc):
+        text = open(os.path.join(csrc, f)).read()
+        assert "oracle" not in text.lower(), f
+    otext = open(os.path.join(ROOT, "oracle", "oracle.c")).read()
+    assert "tc_internal" not in otext and "tc.h" not in otext
+    for f in os.listdir(os.path.join(ROOT, "paper_1811_12498_gb300")):
+        if f.endswith(".py"):
+            text = open(os.path.join(ROOT, "paper_1811_12498_gb300", f)).read()
+            assert "import oracle" not in text and "from oracle" not in text, f

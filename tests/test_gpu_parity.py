@@ -1,0 +1,278 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (relative L2 over all compared outputs, eq. 6.1 form):
+  * FP64 path vs oracle treecode: 1e-10 (same tree, same per-target MAC
+    decisions; only summation order and the radius scaling differ);
+  * mixed path vs oracle treecode: 1e-6;
+  * FP64 direct sum vs oracle direct sum: 1e-12; mixed direct: 1e-6.
+Tree topology, per-node particle sets, cluster centres, squared radii and
+per-target interaction counts must match bit for bit.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1811_12498_gb300 import api, inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-10, "mixed": 1e-6}
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(np.asarray(a, dtype=np.float64).T)).cuda()
+
+
+def host(u):
+    return u.cpu().numpy().T
+
+
+def system(kind, N, seed):
+    if kind == "cube":
+        return inputs.uniform_cube(N, seed)
+    if kind == "sphere":
+        return inputs.fibonacci_sphere(N, seed)
+    if kind == "clusters":
+        return inputs.gaussian_clusters(N, seed)
+    if kind == "ico":
+        return inputs.icosahedral_sphere(N, seed)
+    raise ValueError(kind)
+
+
+# ------------------------------------------------------------------ direct
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("mixed", 1e-6)])
+@pytest.mark.parametrize("N", [1, 2, 33, 1500])
+def test_direct_matches_oracle(prec, tol, N):
+    x, f, h, nu = inputs.uniform_cube(N, 7 + N)
+    u = host(api.direct(dev(x), dev(f), dev(h), dev(nu), precision=prec))
+    ref = oracle.direct(x, f, h, nu)
+    if N == 1:
+        assert np.all(u == 0.0)
+    else:
+        assert oracle.rel_l2(u, ref) <= tol
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("mixed", 1e-6)])
+def test_direct_disjoint_targets(prec, tol):
+    x, f, h, nu = inputs.uniform_cube(2000, 17)
+    rng = np.random.default_rng(3)
+    t = np.concatenate([rng.uniform(-0.5, 1.5, (700, 3)), x[:5]])  # includes coincident points
+    u = host(api.direct(dev(x), dev(f), dev(h), dev(nu), targets=dev(t), precision=prec))
+    assert oracle.rel_l2(u, oracle.direct(x, f, h, nu, targets=t)) <= tol
+
+
+# -------------------------------------------------------------------- tree
+
+def _node_map(level, cell):
+    return {(int(level[i]), int(cell[i][0]), int(cell[i][1]), int(cell[i][2])): i for i in range(len(level))}
+
+
+@pytest.mark.parametrize("kind,N,N0", [("cube", 20000, 200), ("sphere", 30000, 300), ("clusters", 20000, 150),
+                                       ("cube", 1000, 1000), ("cube", 777, 1)])
+@pytest.mark.parametrize("shrink", [True, False])
+def test_tree_matches_oracle_bit_for_bit(kind, N, N0, shrink):
+    x, f, h, nu = system(kind, N, 21)
+    tc = api.Treecode("fp64", shrink).build(dev(x), N0)
+    g = tc.tree_export()
+    go = tc.tree_order()
+    ot = oracle.Tree(x, N0, shrink)
+    o = ot.nodes()
+    oo = ot.order()
+    lo, side = ot.root()
+    info = tc.tree_info()
+    assert info["side"] == side and info["lo"] == list(lo)
+    assert info["nnodes"] == ot.num_nodes
+    gm = _node_map(g["level"], g["cell"])
+    om = _node_map(o["level"], o["cell"])
+    assert gm.keys() == om.keys()
+    for key, gi in gm.items():
+        oi = om[key]
+        assert g["count"][gi] == o["count"][oi]
+        assert (g["nchild"][gi] == 0) == (o["nchild"][oi] == 0)
+        gs = np.sort(go[g["begin"][gi]:g["begin"][gi] + g["count"][gi]])
+        os_ = np.sort(oo[o["begin"][oi]:o["begin"][oi] + o["count"][oi]])
+        np.testing.assert_array_equal(gs, os_)
+        np.testing.assert_array_equal(g["yc"][gi], o["yc"][oi])
+        assert g["rc2"][gi] == o["rc2"][oi]
+    # children of a cluster are consecutive, in octant order, and partition it
+    for i in range(info["nnodes"]):
+        if g["nchild"][i]:
+            ch = np.arange(g["first_child"][i], g["first_child"][i] + g["nchild"][i])
+            assert np.all(g["parent"][ch] == i)
+            assert g["count"][ch].sum() == g["count"][i]
+            assert g["begin"][ch[0]] == g["begin"][i]
+    tc.close()
+
+
+def test_tree_with_coincident_points_reaches_depth_21():
+    x = np.repeat(np.array([[0.25, 0.5, 0.75]]), 50, axis=0)
+    x = np.concatenate([x, [[0.0, 0.0, 0.0], [1.0, 1.0, 1.0]]])
+    tc = api.Treecode("fp64", True).build(dev(x), 4)
+    info = tc.tree_info()
+    ot = oracle.Tree(x, 4, True)
+    assert info["nnodes"] == ot.num_nodes and info["depth"] == 21
+    tc.close()
+
+
+def test_nonfinite_positions_are_rejected():
+    x = np.random.default_rng(0).uniform(0, 1, (100, 3))
+    x[17, 1] = np.nan
+    tc = api.Treecode("fp64", True)
+    with pytest.raises(api.TCError) as e:
+        tc.build(dev(x), 10)
+    assert e.value.status == 1
+    tc.close()
+
+
+# ----------------------------------------------------------------- moments
+
+@pytest.mark.parametrize("p", [0, 3, 8, 12])
+def test_moments_match_oracle(p):
+    x, f, h, nu = inputs.uniform_cube(6000, 31)
+    tc = api.Treecode("fp64", True).build(dev(x), 300).moments(dev(f), dev(h), dev(nu), p)
+    g = tc.tree_export()
+    ot = oracle.Tree(x, 300, True)
+    ot.set_moments(f, h, nu, p)
+    om = _node_map(ot.nodes()["level"], ot.nodes()["cell"])
+    for key, gi in _node_map(g["level"], g["cell"]).items():
+        Mf, Mt = tc.moments_export(gi)
+        rf, rt = ot.node_moments(om[key])
+        scale = max(np.abs(rf).max(), np.abs(rt).max())
+        np.testing.assert_allclose(Mf, rf, rtol=1e-11, atol=1e-13 * scale)
+        np.testing.assert_allclose(Mt, rt, rtol=1e-11, atol=1e-13 * scale)
+    tc.close()
+
+
+# ---------------------------------------------------------------- treecode
+
+def _run(prec, x, f, h, nu, N0, p, theta, shrink=True, targets=None, pm=None):
+    tc = api.Treecode(prec, shrink).build(dev(x), N0).moments(dev(f), dev(h), dev(nu), p if pm is None else pm)
+    u = tc.eval(theta, p, None if targets is None else dev(targets))
+    nf, nn = tc.eval_counts()
+    st = tc.stats()
+    tc.sync()
+    out = host(u), nf.cpu().numpy(), nn.cpu().numpy(), st
+    tc.close()
+    return out
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("p,theta", [(0, 0.5), (4, 0.3), (6, 0.5), (8, 0.5), (8, 0.8), (12, 0.6)])
+def test_treecode_matches_oracle(prec, p, theta):
+    x, f, h, nu = inputs.uniform_cube(12345, 41)
+    N0 = 150
+    u, nf, nn, st = _run(prec, x, f, h, nu, N0, p, theta)
+    tree = oracle.Tree(x, N0, True)
+    tree.set_moments(f, h, nu, p)
+    ref, cnt = tree.treecode(x, theta, p, counts=True)
+    np.testing.assert_array_equal(nf, cnt["far"])
+    np.testing.assert_array_equal(nn, cnt["near_pairs"])
+    assert st["far_interactions"] == cnt["far"].sum() and st["near_pairs"] == cnt["near_pairs"].sum()
+    err = oracle.rel_l2(u, ref)
+    assert err <= TOL[prec], err
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("kind,N,N0,shrink", [("sphere", 20000, 200, True), ("clusters", 16384, 256, True),
+                                              ("cube", 9001, 100, False), ("ico", 5, 300, True)])
+def test_treecode_workloads_match_oracle(prec, kind, N, N0, shrink):
+    x, f, h, nu = system(kind, N, 43)
+    u, nf, nn, _ = _run(prec, x, f, h, nu, N0, 7, 0.5, shrink)
+    tree = oracle.Tree(x, N0, shrink)
+    tree.set_moments(f, h, nu, 7)
+    ref, cnt = tree.treecode(x, 0.5, 7, counts=True)
+    np.testing.assert_array_equal(nf, cnt["far"])
+    assert oracle.rel_l2(u, ref) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_treecode_lower_order_than_moments(prec):
+    x, f, h, nu = inputs.uniform_cube(5000, 47)
+    u, *_ = _run(prec, x, f, h, nu, 100, 5, 0.5, pm=9)
+    tree = oracle.Tree(x, 100, True)
+    tree.set_moments(f, h, nu, 9)
+    assert oracle.rel_l2(u, tree.treecode(x, 0.5, 5)) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_treecode_disjoint_targets(prec):
+    x, f, h, nu = inputs.uniform_cube(8000, 53)
+    rng = np.random.default_rng(5)
+    t = np.concatenate([rng.uniform(-0.3, 1.3, (3000, 3)), x[100:140], rng.uniform(0.4, 0.6, (61, 3))])
+    u, nf, nn, _ = _run(prec, x, f, h, nu, 120, 6, 0.5, targets=t)
+    tree = oracle.Tree(x, 120, True)
+    tree.set_moments(f, h, nu, 6)
+    ref, cnt = tree.treecode(t, 0.5, 6, counts=True)
+    np.testing.assert_array_equal(nf, cnt["far"])
+    np.testing.assert_array_equal(nn, cnt["near_pairs"])
+    assert oracle.rel_l2(u, ref) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_edge_cases(prec):
+    # a single particle: nothing to sum
+    x = np.array([[0.1, 0.2, 0.3]])
+    one = np.ones((1, 3))
+    u, *_ = _run(prec, x, one, one, one, 10, 4, 0.5)
+    assert np.all(u == 0.0)
+    # two particles, one leaf
+    x2 = np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0]])
+    f2 = np.array([[1.0, 0, 0], [0, 1.0, 0]])
+    z = np.zeros((2, 3))
+    u, *_ = _run(prec, x2, f2, z, z, 10, 4, 0.5)
+    np.testing.assert_allclose(u, oracle.direct(x2, f2, z, z), rtol=1e-6)
+    # every particle at one point: all pairs coincide, u = 0
+    xs = np.repeat(np.array([[0.3, 0.3, 0.3]]), 100, axis=0)
+    ws = np.random.default_rng(1).uniform(-1, 1, (100, 3))
+    u, *_ = _run(prec, xs, ws, ws, ws, 7, 3, 0.5)
+    assert np.all(u == 0.0)
+    # theta -> 0: everything near field, equals the direct sum
+    x, f, h, nu = inputs.uniform_cube(3000, 59)
+    u, nf, *_ = _run(prec, x, f, h, nu, 64, 4, 1e-9)
+    assert nf.sum() == 0
+    assert oracle.rel_l2(u, oracle.direct(x, f, h, nu)) <= (1e-12 if prec == "fp64" else 1e-6)
+
+
+def test_invalid_arguments_raise():
+    x, f, h, nu = inputs.uniform_cube(100, 61)
+    tc = api.Treecode("mixed", True)
+    with pytest.raises(api.TCError) as e:
+        tc.eval(0.5, 4)
+    assert e.value.status == 4  # TC_ESTATE: no tree yet
+    tc.build(dev(x), 10)
+    with pytest.raises(api.TCError):
+        tc.moments(dev(f), dev(h), dev(nu), 13)
+    tc.moments(dev(f), dev(h), dev(nu), 4)
+    for theta in (0.0, 1.0, -0.5):
+        with pytest.raises(api.TCError):
+            tc.eval(theta, 4)
+    with pytest.raises(api.TCError):
+        tc.eval(0.5, 5)  # above the moment order
+    tc.close()
+
+
+# ---------------------------------------------- full size, sampled outputs
+
+@pytest.fixture(scope="module")
+def million():
+    x, f, h, nu = inputs.uniform_cube(1_000_000, inputs.SEED_BASE + 1)
+    idx = inputs.sample_indices(x.shape[0], 48, 99)
+    tree = oracle.Tree(x, 2000, True)
+    tree.set_moments(f, h, nu, 8)
+    ref, cnt = tree.treecode(x[idx], 0.5, 8, counts=True)
+    return x, f, h, nu, idx, ref, cnt
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_full_size_sampled_targets(million, prec):
+    """N = 10^6 uniform cube, p = 8, theta = 0.5, N0 = 2000 (the benchmark's
+    launch configuration): sampled outputs against the oracle, one by one."""
+    x, f, h, nu, idx, ref, cnt = million
+    u, nf, nn, st = _run(prec, x, f, h, nu, 2000, 8, 0.5)
+    np.testing.assert_array_equal(nf[idx], cnt["far"])
+    np.testing.assert_array_equal(nn[idx], cnt["near_pairs"])
+    assert oracle.rel_l2(u[idx], ref) <= TOL[prec]
+    # every target's far clusters and near leaves partition the sources
+    assert st["near_pairs"] > 0 and st["far_interactions"] > 0
