@@ -1,0 +1,358 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the GB300 Stokeslet + stresslet treecode.
+
+Workload (one "step" = the whole hot path over one particle system):
+  N = 1,000,000 particles uniform in the unit cube, f and h uniform in
+  [-1, 1]^3, nu uniform random unit vectors (seeded); tree build with leaf
+  size N0 = 2000, cluster moments of order p = 8, and the treecode velocity
+  at every particle with MAC theta = 0.5 (Algorithm 1), mixed precision.
+  Metric: targets/s = N / (time of one step), inputs resident in HBM.
+
+Prints ONE JSON line (rank 0).  Usage:
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank solves its own seeded system of the same
+size (replicas, weak scaling); there is no data-path collective.
+"""
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "targets/s at N=1M, p=8 (rel-L2<=1e-6 vs FP64 direct); fwd+adjoint s/step"
+UNIT = "targets/s"
+L2_FLUSH_BYTES = 256 << 20
+# nominal GB300 arithmetic peaks (152 SMs at 2070 MHz): FP64 2 FMA/clk/SM,
+# FP32 128 FMA/clk/SM
+PEAK_FP64_TFLOPS = 1.25
+PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def ncoef(n):
+    return (n + 1) * (n + 2) * (n + 3) // 6
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--N", type=int, default=1_000_000)
+    ap.add_argument("--p", type=int, default=8)
+    ap.add_argument("--theta", type=float, default=0.5)
+    ap.add_argument("--N0", type=int, default=2000)
+    ap.add_argument("--cpu-sample", type=int, default=16384, help="targets the oracle evaluates for cpu_baseline")
+    ap.add_argument("--ref-sample", type=int, default=2048, help="targets per step of the reference arm")
+    ap.add_argument("--error-samples", type=int, default=10000, help="targets of the FP64 direct-sum error check")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-compare", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        sm = [float(r[1]) for r in rows if re.match(r"^[0-9.]+$", r[1])]
+        mx = [float(r[2]) for r in rows if re.match(r"^[0-9.]+$", r[2])]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for k, n in enumerate(names):
+                if r[5 + k].lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def far_traffic(p):
+    """Per-launch DRAM bytes of the far-field kernel from the committed ncu
+    summary, if it was taken on the current kernel source; else None."""
+    src = os.path.join(ROOT, "paper_1811_12498_gb300", "csrc", "tc_far.cu")
+    prof = os.path.join(ROOT, "profiles", "far_field_uniform_cube_1M.md")
+    if not os.path.exists(prof):
+        return None
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    text = open(prof).read()
+    m_sha = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
+    m_b = re.search(r"dram_bytes_per_full_launch:\s*([0-9.eE+]+)", text)
+    if not m_sha or not m_b or m_sha.group(1) != sha:
+        return None
+    return float(m_b.group(1))
+
+
+def cpu_baseline(x, f, h, nu, args, sample):
+    """The oracle as it stands, on this host's cores: tree + moments over all
+    N particles, Algorithm 1 at `sample` seeded targets; eval time scaled to N."""
+    import oracle
+    from paper_1811_12498_gb300 import inputs
+    N = x.shape[0]
+    idx = inputs.sample_indices(N, sample, 4242)
+    t0 = time.perf_counter()
+    tree = oracle.Tree(x, args.N0, True)
+    t1 = time.perf_counter()
+    tree.set_moments(f, h, nu, args.p)
+    t2 = time.perf_counter()
+    u = tree.treecode(x[idx], args.theta, args.p)
+    t3 = time.perf_counter()
+    full = (t1 - t0) + (t2 - t1) + (t3 - t2) * N / len(idx)
+    return {"value": N / full, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": "oracle tree + order-%d moments over all %d particles (%.1f s), Algorithm 1 at %d seeded "
+                      "targets (%.1f s) scaled to %d targets" % (args.p, N, t2 - t0, len(idx), t3 - t2, N),
+            "seconds": t3 - t0}, idx, u
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_1811_12498_gb300 import inputs
+    x, f, h, nu = inputs.uniform_cube(args.N, inputs.SEED_BASE + 1)
+    vals = []
+    for k in range(args.warmup + args.steps):
+        r, _, _ = cpu_baseline(x, f, h, nu, args, args.ref_sample)
+        if k >= args.warmup:
+            vals.append(r)
+    v = statistics.mean(r["value"] for r in vals)
+    ms = args.N / v * 1e3
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config(args),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": vals[0]["cores"], "kind": "oracle",
+                             "sample": vals[0]["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config(args):
+    return {"workload": "uniform cube N=%d, Stokeslet+stresslet, p=%d, theta=%g, N0=%d, %s precision, "
+                        "clusters shrunk to their boxes" % (args.N, args.p, args.theta, args.N0, args.precision),
+            "N": args.N, "p": args.p, "theta": args.theta, "N0": args.N0, "precision": args.precision,
+            "l2": "flushed before every timed step (256 MiB write)", "targets": "all N particles"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+
+    from paper_1811_12498_gb300 import api, inputs
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    N, p, theta, N0 = args.N, args.p, args.theta, args.N0
+    x, f, h, nu = inputs.uniform_cube(N, inputs.SEED_BASE + 1 + rank)
+    hx = [torch.from_numpy(np.ascontiguousarray(a.T)).pin_memory() for a in (x, f, h, nu)]
+    dx = [a.cuda() for a in hx]
+    stream = torch.cuda.current_stream()
+    tc = api.Treecode(args.precision, True, stream)
+    u = torch.empty((3, N), dtype=torch.float64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+
+    def step(inputs_dev):
+        tc.build(inputs_dev[0], N0)
+        tc.moments(inputs_dev[1], inputs_dev[2], inputs_dev[3], p)
+        tc.eval(theta, p, out=u)
+
+    for _ in range(args.warmup):
+        step(dx)
+    torch.cuda.synchronize()
+    tc.profile(True)
+    clocks = Clocks(local)
+    barrier()
+    torch.cuda.synchronize()
+    launches0 = api.kernel_launches()
+    clocks.start()
+    times, phases = [], []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(dx)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        phases.append(tc.phase_times())
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    launches = api.kernel_launches() - launches0
+    ms = statistics.mean(times)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = N * world / (ms / 1e3)
+    st = tc.stats()
+    ph = {k: statistics.mean(pp[k] for pp in phases if pp[k] is not None) for k in phases[0] if phases[0][k] is not None}
+
+    # end to end through the public API: pinned host inputs -> device -> step -> host u
+    uh = torch.empty((3, N), dtype=torch.float64).pin_memory()
+    e2e_times = []
+    for k in range(args.steps + 1):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        dd = [a.to("cuda", non_blocking=True) for a in hx]
+        step(dd)
+        uh.copy_(u, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        if k > 0:
+            e2e_times.append(e0.elapsed_time(e1))
+    e2e_ms = statistics.mean(e2e_times)
+    if dist is not None:
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    if rank != 0:
+        tc.close()
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    # accuracy: E against the FP64 direct sum on sampled targets (eq. 6.1)
+    u_host = u.cpu().numpy().T
+    eidx = inputs.sample_indices(N, args.error_samples, 777)
+    tgt = torch.from_numpy(np.ascontiguousarray(x[eidx].T)).cuda()
+    ud = api.direct(dx[0], dx[1], dx[2], dx[3], targets=tgt, precision="fp64").cpu().numpy().T
+    E = float(np.sqrt(np.sum((u_host[eidx] - ud) ** 2) / np.sum(ud ** 2)))
+
+    # roofline of the dominant kernel (far field): algorithmic flops per launch
+    C2 = ncoef(p + 2)
+    n_far = st["far_interactions"]
+    fp64_rec = args.precision == "fp64" or p >= 8
+    far_ms = ph.get("far")
+    near_ms = ph.get("near")
+    rec_flops = 11.0 * C2 * n_far
+    con_flops = (24.0 * C2 + 18.0) * n_far
+    if fp64_rec:
+        achieved = rec_flops / (far_ms / 1e3) / 1e12
+        peak = PEAK_FP64_TFLOPS
+    else:
+        achieved = (rec_flops + con_flops) / (far_ms / 1e3) / 1e12
+        peak = PEAK_FP32_TFLOPS
+    traffic = far_traffic(p)
+    near_flops = 43.0 * st["near_pairs"]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+        "config": config(args),
+        "roofline": {"bound": "alu", "kernel": "k_far (far field, FP64 Coulomb recurrence)" if fp64_rec else
+                     "k_far (far field)", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "peak_kind": "nominal FP64 (152 SMs x 2 FMA/clk x 2.07 GHz)" if fp64_rec else
+                     "nominal FP32 (152 SMs x 128 FMA/clk x 2.07 GHz)",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "flops_per_launch": rec_flops if fp64_rec else rec_flops + con_flops,
+                     "launch_ms": far_ms},
+        "e2e": {"value": N / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(sum(a.numel() * 8 for a in hx)),
+                "d2h_bytes_per_step": int(uh.numel() * 8), "ms_per_step": e2e_ms},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "phases_ms": ph,
+        "interactions": {"far": n_far, "near_pairs": st["near_pairs"], "clusters": st["clusters"]},
+        "secondary": {"near_fp32_tflops": near_flops / (near_ms / 1e3) / 1e12 if near_ms else None,
+                      "near_fp32_frac": (near_flops / (near_ms / 1e3) / 1e12) / PEAK_FP32_TFLOPS if near_ms else None,
+                      "far_fp32_contraction_tflops": con_flops / (far_ms / 1e3) / 1e12},
+        "accuracy": {"E_vs_fp64_direct": E, "E_samples": int(len(eidx))},
+    }
+    if not args.no_fp64_compare and args.precision == "mixed":
+        tc64 = api.Treecode("fp64", True, stream)
+        tc64.build(dx[0], N0).moments(dx[1], dx[2], dx[3], p)
+        u64 = tc64.eval(theta, p)
+        torch.cuda.synchronize()
+        t64 = []
+        for _ in range(2):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            tc64.build(dx[0], N0).moments(dx[1], dx[2], dx[3], p)
+            tc64.eval(theta, p, out=u64)
+            e1.record(stream)
+            e1.synchronize()
+            t64.append(e0.elapsed_time(e1))
+        u64h = u64.cpu().numpy().T
+        line["fp64_path"] = {"ms_per_step": statistics.mean(t64), "value": N / (statistics.mean(t64) / 1e3),
+                             "mixed_vs_fp64_rel_l2": float(np.sqrt(np.sum((u_host - u64h) ** 2) / np.sum(u64h ** 2)))}
+        tc64.close()
+    if not args.no_cpu_baseline:
+        cb, idx, uo = cpu_baseline(x, f, h, nu, args, args.cpu_sample)
+        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        line["accuracy"]["vs_oracle_treecode"] = float(np.sqrt(np.sum((u_host[idx] - uo) ** 2) / np.sum(uo ** 2)))
+        line["accuracy"]["oracle_samples"] = int(len(idx))
+    print(json.dumps(line), flush=True)
+    tc.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -153,6 +153,35 @@ tc_status tc_stats(tc_ctx* ctx, int64_t* near_pairs, int64_t* far_interactions, 
 tc_status tc_eval_counts(tc_ctx* ctx, int64_t* nfar, int64_t* nnear_pairs);
 
 /* ---------------------------------------------------------------------- */
+/* Tracing.                                                               */
+/* ---------------------------------------------------------------------- */
+
+/* Phases timed with CUDA events on the context's stream. */
+typedef enum {
+    TC_PH_BUILD = 0,    /* tc_build: keys, sort, topology, geometry          */
+    TC_PH_MOMENTS = 1,  /* tc_moments: weight gather, leaf moments, upward pass */
+    TC_PH_TABLES = 2,   /* contraction tables (first tc_eval at an order)    */
+    TC_PH_TARGETS = 3,  /* tc_eval: keys and sort of disjoint targets        */
+    TC_PH_LISTS = 4,    /* tc_eval: MAC traversal, both passes and scans     */
+    TC_PH_FAR = 5,      /* tc_eval: far-field kernel                         */
+    TC_PH_NEAR = 6,     /* tc_eval: near-field kernel                        */
+    TC_PH_FINAL = 7,    /* tc_eval: sum and scatter to the caller's order    */
+    TC_NPHASES = 8
+} tc_phase;
+
+/* Enable (1) or disable (0) per-phase event timing on ctx.  Enabling resets
+ * the recorded phases.  Costs two event records per phase. */
+tc_status tc_profile(tc_ctx* ctx, int32_t enable);
+
+/* Durations in ms of the most recent run of each phase (host array of
+ * TC_NPHASES; -1 for a phase not run since profiling was enabled).
+ * Synchronises the stream. */
+tc_status tc_phase_times(tc_ctx* ctx, double* ms);
+
+/* Number of kernels this library has launched in this process so far. */
+int64_t tc_kernel_launches(void);
+
+/* ---------------------------------------------------------------------- */
 /* Inspection of the tree (host outputs; for tests and tools).            */
 /* ---------------------------------------------------------------------- */
 

@@ -27,7 +27,11 @@ SIGNATURES = {
     "tc_tree_export": (_i32, [_vp] + [_vp] * 9),
     "tc_tree_order": (_i32, [_vp, _vp]),
     "tc_moments_export": (_i32, [_vp, _i64, _vp, _vp]),
+    "tc_profile": (_i32, [_vp, _i32]),
+    "tc_phase_times": (_i32, [_vp, _vp]),
+    "tc_kernel_launches": (_i64, []),
 }
+PHASES = ("build", "moments", "tables", "targets", "lists", "far", "near", "final")
 
 
 class TCConfig(ctypes.Structure):

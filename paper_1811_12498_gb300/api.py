@@ -14,7 +14,7 @@ import ctypes
 
 import torch
 
-from ._lib import TCConfig, lib
+from ._lib import PHASES, TCConfig, lib
 
 TC_FP64, TC_MIXED = 0, 1
 _STATUS = {0: "TC_OK", 1: "TC_EINVAL", 2: "TC_ENOMEM", 3: "TC_ECUDA", 4: "TC_ESTATE", 5: "TC_ETIMEOUT",
@@ -124,6 +124,16 @@ class Treecode:
     def sync(self):
         self._chk(lib().tc_sync(self._h))
 
+    def profile(self, enable=True):
+        """Enable per-phase CUDA-event timing (see phase_times)."""
+        self._chk(lib().tc_profile(self._h, int(bool(enable))))
+
+    def phase_times(self):
+        """ms of the most recent run of each phase (None if not run)."""
+        ms = (ctypes.c_double * len(PHASES))()
+        self._chk(lib().tc_phase_times(self._h, ms))
+        return {k: (v if v >= 0 else None) for k, v in zip(PHASES, ms)}
+
     def stats(self):
         near, far, nodes = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
         self._chk(lib().tc_stats(self._h, ctypes.byref(near), ctypes.byref(far), ctypes.byref(nodes)))
@@ -182,6 +192,11 @@ def direct(x, f, h, nu, targets=None, precision="fp64", out=None, stream=None):
     _check(lib().tc_direct(_ptr(x), _ptr(f), _ptr(h), _ptr(nu), N, _ptr(t), M, _prec(precision),
                            _stream_ptr(stream), _ptr(out)))
     return out
+
+
+def kernel_launches():
+    """Kernels launched by libtc.so in this process so far."""
+    return int(lib().tc_kernel_launches())
 
 
 def velocity(x, f, h, nu, theta, p, N0, precision="mixed", shrink=True, targets=None):

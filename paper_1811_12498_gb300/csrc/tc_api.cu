@@ -1,5 +1,6 @@
 // C ABI entry points (include/tc.h): argument checks, buffer management and
 // the order of kernel launches for tree build, moments and evaluation.
+#include <atomic>
 #include <cstdarg>
 #include <new>
 
@@ -85,6 +86,22 @@ void release(DevBuf& b)
 
 using namespace tc;
 
+static std::atomic<int64_t> g_launches{0};
+void tc::note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// phase timing: events around a phase when profiling is on
+static void ph_begin(tc_ctx* ctx, int ph)
+{
+    if (ctx->profile) cudaEventRecord(ctx->ev[2 * ph], ctx->stream);
+}
+static void ph_end(tc_ctx* ctx, int ph)
+{
+    if (ctx->profile) {
+        cudaEventRecord(ctx->ev[2 * ph + 1], ctx->stream);
+        ctx->ev_recorded[ph] = 1;
+    }
+}
+
 #define TC_CK(call, where)                                  \
     do {                                                    \
         cudaError_t e_ = (call);                            \
@@ -141,9 +158,37 @@ tc_status tc_destroy(tc_ctx* ctx)
     if (!ctx) return TC_OK;
     cudaStreamSynchronize(ctx->stream);
     release_all(ctx);
+    for (cudaEvent_t& e : ctx->ev)
+        if (e) cudaEventDestroy(e);
     delete ctx;
     return TC_OK;
 }
+
+tc_status tc_profile(tc_ctx* ctx, int32_t enable)
+{
+    if (!ctx) return fail(nullptr, TC_EINVAL, "tc_profile: ctx is NULL");
+    if (enable && !ctx->ev[0])
+        for (cudaEvent_t& e : ctx->ev) TC_CK(cudaEventCreate(&e), "tc_profile event");
+    for (int& r : ctx->ev_recorded) r = 0;
+    ctx->profile = enable ? 1 : 0;
+    return TC_OK;
+}
+
+tc_status tc_phase_times(tc_ctx* ctx, double* ms)
+{
+    if (!ctx || !ms) return fail(ctx, TC_EINVAL, "tc_phase_times: NULL argument");
+    TC_CK(cudaStreamSynchronize(ctx->stream), "tc_phase_times sync");
+    for (int ph = 0; ph < TC_NPHASES; ph++) {
+        ms[ph] = -1.0;
+        if (!ctx->ev_recorded[ph]) continue;
+        float t = 0.f;
+        TC_CK(cudaEventElapsedTime(&t, ctx->ev[2 * ph], ctx->ev[2 * ph + 1]), "tc_phase_times");
+        ms[ph] = t;
+    }
+    return TC_OK;
+}
+
+int64_t tc_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
 const char* tc_last_error(const tc_ctx* ctx)
 {
@@ -192,6 +237,7 @@ tc_status tc_build(tc_ctx* ctx, const double* x, int64_t N, int32_t N0)
     TC_CK(ensure(ctx->hist, (size_t)256 * nrad * 4), "alloc hist");
     TC_CK(ensure(ctx->xs, (size_t)3 * N * 8), "alloc xs");
 
+    ph_begin(ctx, TC_PH_BUILD);
     TC_CK(launch_bbox(x, N, ptr<double>(ctx->bbox_part), nblk, ptr<double>(ctx->root), s), "bbox");
     TC_CK(launch_keys(x, N, ptr<double>(ctx->root), ptr<uint64_t>(ctx->keys), ptr<int32_t>(ctx->perm), 0, s), "keys");
     TC_CK(radix_sort(ptr<uint64_t>(ctx->keys), ptr<int32_t>(ctx->perm), ptr<uint64_t>(ctx->keys_alt),
@@ -252,6 +298,7 @@ tc_status tc_build(tc_ctx* ctx, const double* x, int64_t N, int32_t N0)
                           ptr<double>(ctx->xs), N, le, ptr<double>(ctx->root), ctx->shrink, ptr<Geo>(ctx->node_geo),
                           ptr<double>(ctx->node_invrho), s),
           "geometry");
+    ph_end(ctx, TC_PH_BUILD);
     ctx->built = 1;
     return TC_OK;
 }
@@ -268,14 +315,21 @@ tc_status tc_moments(tc_ctx* ctx, const double* f, const double* h, const double
     ctx->ab_p = -1;
     TC_CK(ensure(ctx->ws, (size_t)9 * N * 8), "alloc weights");
     TC_CK(ensure(ctx->mom, (size_t)ctx->nnodes * 12 * ncoef(p) * 8), "alloc moments");
+    if (ctx->precision == TC_MIXED) TC_CK(ensure(ctx->spack, (size_t)N * 64), "alloc pack");
+    ph_begin(ctx, TC_PH_MOMENTS);
     TC_CK(launch_gather_weights(f, h, nu, ptr<int32_t>(ctx->perm), N, ptr<double>(ctx->ws), s), "gather weights");
     if (ctx->precision == TC_MIXED) {
-        TC_CK(ensure(ctx->spack, (size_t)N * 64), "alloc pack");
         TC_CK(launch_source_pack(ptr<double>(ctx->xs), ptr<double>(ctx->ws), N, ptr<float4>(ctx->spack), s), "pack");
     }
     TC_CK(launch_moments(ptr<int4>(ctx->node_topo), ptr<Geo>(ctx->node_geo), ptr<double>(ctx->xs),
                          ptr<double>(ctx->ws), N, ctx->nnodes, p, ptr<double>(ctx->mom), s),
           "moments");
+    // upward pass: level_begin holds the first node of each level and the end
+    for (int L = (int)ctx->level_begin.size() - 3; L >= 0; L--)
+        TC_CK(launch_m2m(ptr<int4>(ctx->node_topo), ptr<Geo>(ctx->node_geo), ctx->level_begin[L],
+                         ctx->level_begin[L + 1], p, ptr<double>(ctx->mom), s),
+              "m2m");
+    ph_end(ctx, TC_PH_MOMENTS);
     ctx->p_mom = p;
     ctx->have_moments = 1;
     return TC_OK;
@@ -295,9 +349,11 @@ static tc_status ensure_tables(tc_ctx* ctx, int p)
         TC_CK(ensure(ctx->ab32, (size_t)n * 4), "alloc tables");
         ab32 = ptr<float>(ctx->ab32);
     }
+    ph_begin(ctx, TC_PH_TABLES);
     TC_CK(launch_ab_tables(ptr<double>(ctx->mom), ptr<double>(ctx->node_invrho), ctx->nnodes, ctx->p_mom, p, ab64,
                            ab32, s),
           "tables");
+    ph_end(ctx, TC_PH_TABLES);
     ctx->ab_p = p;
     return TC_OK;
 }
@@ -331,12 +387,14 @@ tc_status tc_eval(tc_ctx* ctx, const double* targets, int64_t M, double theta, i
         TC_CK(ensure(ctx->tperm_alt, (size_t)M * 4), "alloc tperm");
         TC_CK(ensure(ctx->hist, (size_t)256 * nrad * 4), "alloc hist");
         TC_CK(ensure(ctx->ts, (size_t)3 * M * 8), "alloc ts");
+        ph_begin(ctx, TC_PH_TARGETS);
         TC_CK(launch_keys(targets, M, ptr<double>(ctx->root), ptr<uint64_t>(ctx->tkeys), ptr<int32_t>(ctx->tperm), 1, s),
               "target keys");
         TC_CK(radix_sort(ptr<uint64_t>(ctx->tkeys), ptr<int32_t>(ctx->tperm), ptr<uint64_t>(ctx->tkeys_alt),
                          ptr<int32_t>(ctx->tperm_alt), ptr<uint32_t>(ctx->hist), M, s),
               "target sort");
         TC_CK(launch_gather3(targets, ptr<int32_t>(ctx->tperm), M, ptr<double>(ctx->ts), s), "gather targets");
+        ph_end(ctx, TC_PH_TARGETS);
         ts = ptr<double>(ctx->ts);
         tperm = ptr<int32_t>(ctx->tperm);
         ctx->eval_self = 0;
@@ -353,6 +411,7 @@ tc_status tc_eval(tc_ctx* ctx, const double* targets, int64_t M, double theta, i
     TC_CK(cudaMemsetAsync(ctx->flags.p, 0, 4, s), "flags");
     const int4* topo = ptr<int4>(ctx->node_topo);
     const Geo* geo = ptr<Geo>(ctx->node_geo);
+    ph_begin(ctx, TC_PH_LISTS);
     TC_CK(launch_lists(ts, M, topo, geo, theta, 0, ptr<int32_t>(ctx->nfar_e), ptr<int32_t>(ctx->nnear_e), nullptr,
                        nullptr, nullptr, nullptr, nullptr, nullptr, ptr<int32_t>(ctx->flags), s),
           "list count");
@@ -371,14 +430,21 @@ tc_status tc_eval(tc_ctx* ctx, const double* targets, int64_t M, double theta, i
                        ptr<ListEntry>(ctx->far_list), ptr<ListEntry>(ctx->near_list), ptr<int64_t>(ctx->cnt_far),
                        ptr<int64_t>(ctx->cnt_near), ptr<int32_t>(ctx->flags), s),
           "list write");
+    ph_end(ctx, TC_PH_LISTS);
+    ph_begin(ctx, TC_PH_FAR);
     TC_CK(launch_far(ctx->precision, ts, M, geo, ptr<double>(ctx->node_invrho), ptr<double>(ctx->ab64),
                      ptr<float>(ctx->ab32), p, far_off, ptr<ListEntry>(ctx->far_list), ptr<double>(ctx->u_far), s),
           "far field");
+    ph_end(ctx, TC_PH_FAR);
+    ph_begin(ctx, TC_PH_NEAR);
     TC_CK(launch_near(ctx->precision, ts, M, topo, ptr<double>(ctx->xs), ptr<double>(ctx->ws),
                       ptr<float4>(ctx->spack), ctx->N, near_off, ptr<ListEntry>(ctx->near_list),
                       ptr<double>(ctx->u_near), s),
           "near field");
+    ph_end(ctx, TC_PH_NEAR);
+    ph_begin(ctx, TC_PH_FINAL);
     TC_CK(launch_finalize(ptr<double>(ctx->u_far), ptr<double>(ctx->u_near), tperm, M, u, s), "finalize");
+    ph_end(ctx, TC_PH_FINAL);
     ctx->M = M;
     ctx->stat_far = tot[0];
     ctx->have_eval = 1;

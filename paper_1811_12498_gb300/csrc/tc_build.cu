@@ -385,7 +385,9 @@ inline unsigned grid_for(int64_t n, int threads)
 cudaError_t launch_bbox(const double* x, int64_t N, double* part, int nblk, double* root, cudaStream_t s)
 {
     k_bbox_partial<<<nblk, kBboxThreads, 0, s>>>(x, N, part);
+    note_launch();
     k_bbox_final<<<1, 32, 0, s>>>(part, nblk, root);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -393,6 +395,7 @@ cudaError_t launch_keys(const double* x, int64_t N, const double* root, uint64_t
                         int clamp_outside, cudaStream_t s)
 {
     k_keys<<<grid_for(N, 256), 256, 0, s>>>(x, N, root, keys, idx, clamp_outside);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -408,8 +411,11 @@ cudaError_t radix_sort(uint64_t* keys, int32_t* vals, uint64_t* keys_alt, int32_
     for (int pass = 0; pass < 8; pass++) {
         int shift = 8 * pass;
         k_radix_hist<<<nblk, kRadixThreads, 0, s>>>(ki, N, shift, hist);
+        note_launch();
         k_scan_u32_inplace<<<1, 1024, 0, s>>>(hist, (int64_t)256 * nblk);
+        note_launch();
         k_radix_scatter<<<nblk, kRadixThreads, 0, s>>>(ki, vi, ko, vo, N, shift, hist);
+        note_launch();
         uint64_t* tk = ki;
         ki = ko;
         ko = tk;
@@ -423,12 +429,14 @@ cudaError_t radix_sort(uint64_t* keys, int32_t* vals, uint64_t* keys_alt, int32_
 cudaError_t launch_gather3(const double* src, const int32_t* perm, int64_t N, double* dst, cudaStream_t s)
 {
     k_gather3<<<grid_for(N, 256), 256, 0, s>>>(src, perm, N, dst);
+    note_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_init_root(int4* topo, int4* info, uint64_t* nkey, int64_t N, cudaStream_t s)
 {
     k_init_root<<<1, 1, 0, s>>>(topo, info, nkey, N);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -436,6 +444,7 @@ cudaError_t launch_split_count(const int4* topo, const int4* info, const uint64_
                                int N0, int32_t* cnt, cudaStream_t s)
 {
     k_split_count<<<grid_for(le - lb, 128), 128, 0, s>>>(topo, info, keys, lb, le, N0, cnt);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -470,6 +479,7 @@ __global__ void k_scan_i32(const int32_t* __restrict__ in, int32_t* __restrict__
 cudaError_t launch_scan_i32(const int32_t* in, int32_t* out_excl, int64_t n, int32_t* total, cudaStream_t s)
 {
     k_scan_i32<<<1, 1024, 0, s>>>(in, out_excl, n, total);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -477,6 +487,7 @@ cudaError_t launch_split_write(int4* topo, int4* info, uint64_t* nkey, const uin
                                int N0, const int32_t* off, cudaStream_t s)
 {
     k_split_write<<<grid_for(le - lb, 128), 128, 0, s>>>(topo, info, nkey, keys, lb, le, N0, off);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -485,6 +496,7 @@ cudaError_t launch_geometry(const int4* topo, const int4* info, const uint64_t* 
                             cudaStream_t s)
 {
     k_geometry<<<(unsigned)nnodes, kGeoThreads, 0, s>>>(topo, info, nkey, xs, N, root, shrink, geo, invrho);
+    note_launch();
     return cudaGetLastError();
 }
 

@@ -206,11 +206,15 @@ cudaError_t launch_direct(int precision, const double* x, const double* f, const
     dim3 grid((unsigned)((nbatch + kDirWarps - 1) / kDirWarps), (unsigned)pl.nsplit);
     if (precision == TC_FP64) {
         k_direct_fp64<<<grid, kDirWarps * 32, 0, s>>>(t, M, x, f, h, nu, N, pl.chunk, part);
+        note_launch();
     } else {
         k_direct_pack<<<grid_for(N, 256), 256, 0, s>>>(x, f, h, nu, N, pack);
+        note_launch();
         k_direct_mixed<<<grid, kDirWarps * 32, 0, s>>>(t, M, pack, N, pl.chunk, part);
+        note_launch();
     }
     k_direct_reduce<<<grid_for(3 * M, 256), 256, 0, s>>>(part, pl.nsplit, M, u);
+    note_launch();
     return cudaGetLastError();
 }
 

@@ -1,17 +1,25 @@
 // Far field: particle-cluster Taylor approximation, eq. (2.9), evaluated in
 // the contracted form of the contraction tables (tc_moments.cu):
 //   u_i += sum_{||k'|| <= p+2} b^{k'}(d') ( Â_i^{k'} + sum_l d'_l B̂_il^{k'} ),
-// with d' = (x - y_c) / rho and the Coulomb coefficients b^{k'}(d') from the
+// with d' = (x - y_c) / rho and the Coulomb coefficients b^k of the
 // recurrence (3.2):
-//   n R'^2 b^k = (2n-1) sum_i d'_i b^{k-e_i} - (n-1) sum_i b^{k-2e_i},  n = ||k||,
-//   b^0 = 1/R',  R' = |d'|.
+//   n R^2 b^k = (2n-1) sum_i d_i b^{k-e_i} - (n-1) sum_i b^{k-2e_i},  n = ||k||.
+//
+// The recurrence is run on the unit vector w = d'/R' (R' = |d'|): b^k is
+// homogeneous of degree -(n+1), so b^k(d') = R'^-(n+1) b^k(w), and with
+// |w| = 1 the coefficients (2n-1)/n and (n-1)/n no longer depend on the
+// target.  Writing b^k(w) = lambda_n c^k with lambda_n = prod_{j<=n} (2j-1)/j
+// turns the recurrence into
+//   c^k = sum_i w_i c^{k-e_i} - kappa_n sum_i c^{k-2e_i},
+//   kappa_n = (n-1)^2 / ((2n-1)(2n-3)),  c^0 = 1,
+// six FP64 operations per coefficient, all O(1) in magnitude.  The level
+// factor lambda_n R'^-(n+1) multiplies the level's 12 partial contractions.
 //
 // One warp handles a batch of 32 targets (one per lane) and walks the batch's
-// far list; a lane outside an entry's mask idles for that entry.  The
-// recurrence runs level by level; only levels n-2, n-1 and n are live, kept in
-// a per-warp shared-memory ring laid out [slot][position][lane] (no bank
-// conflicts).  Each coefficient is contracted against the cluster's 12 table
-// entries as soon as it is produced.
+// far list; a lane outside an entry's mask idles for that entry.  Only levels
+// n-2, n-1 and n of c are live, kept in a per-warp shared-memory ring laid out
+// [slot][position][lane] (no bank conflicts).  Each coefficient is
+// contracted against the cluster's 12 table entries as soon as it exists.
 //
 // Precision: TR is the recurrence type, TC the table/contraction type.
 // FP64 mode: TR = TC = double.  Mixed: TC = float, TR = double for p >= 8 and
@@ -25,19 +33,20 @@ namespace {
 
 constexpr int kFarWarps = 2;
 
-template <typename T>
-__device__ inline T rsqrt_t(double x);
-template <>
-__device__ inline double rsqrt_t<double>(double x) { return rsqrt(x); }
-template <>
-__device__ inline float rsqrt_t<float>(double x) { return rsqrtf((float)x); }
-
-template <typename TC>
-__device__ inline void contract(TC bk, const TC* __restrict__ t, TC* acc)
+struct LevelConst {
+    double kappa[kQMax + 1];  // kappa_n
+    double ratio[kQMax + 1];  // (2n-1)/n = lambda_n / lambda_{n-1}
+};
+__host__ __device__ constexpr LevelConst make_level_const()
 {
-#pragma unroll
-    for (int c = 0; c < 12; c++) acc[c] = fma(bk, t[c], acc[c]);
+    LevelConst c{};
+    for (int n = 0; n <= kQMax; n++) {
+        c.kappa[n] = n >= 2 ? (double)((n - 1) * (n - 1)) / (double)((2 * n - 1) * (2 * n - 3)) : 0.0;
+        c.ratio[n] = n >= 1 ? (double)(2 * n - 1) / (double)n : 1.0;
+    }
+    return c;
 }
+__constant__ LevelConst c_lev = make_level_const();
 
 template <typename TR, typename TC>
 __global__ void __launch_bounds__(kFarWarps * 32)
@@ -72,22 +81,26 @@ __global__ void __launch_bounds__(kFarWarps * 32)
         const double d0 = (x0 - g.x) * ir, d1 = (x1 - g.y) * ir, d2 = (x2 - g.z) * ir;
         double R2 = d0 * d0 + d1 * d1 + d2 * d2;
         if (!in) R2 = 1.0;  // keep idle lanes finite
-        const TR iR2 = (TR)(1.0 / R2);
-        const TR dd0 = (TR)d0, dd1 = (TR)d1, dd2 = (TR)d2;
+        const double iR = rsqrt(R2);
+        const TR w0 = (TR)(d0 * iR), w1 = (TR)(d1 * iR), w2 = (TR)(d2 * iR);
         const TC* __restrict__ tab = ab + (int64_t)le.node * C2 * 12;
-        TC acc[12];
+        TC tot[12];
 #pragma unroll
-        for (int c = 0; c < 12; c++) acc[c] = (TC)0;
-        TR b0 = rsqrt_t<TR>(R2);
-        ring[lane] = b0;  // slot 0, position 0
-        contract<TC>((TC)b0, tab, acc);
+        for (int c = 0; c < 12; c++) tot[c] = tab[c];  // level 0: c^0 = 1
+        TC scale = (TC)iR;                             // lambda_0 R'^-1
+#pragma unroll
+        for (int c = 0; c < 12; c++) tot[c] *= scale;
+        ring[lane] = (TR)1;
         for (int n = 1; n <= P; n++) {
-            const TR alpha = (TR)(2 * n - 1) / (TR)n * iR2;
-            const TR beta = (TR)(n - 1) / (TR)n * iR2;
+            const TR kap = (TR)c_lev.kappa[n];
+            scale *= (TC)(c_lev.ratio[n] * iR);
             TR* Rn = ring + (n % 3) * LS * 32;
             const TR* R1 = ring + ((n - 1) % 3) * LS * 32;
             const TR* Rm = ring + ((n + 1) % 3) * LS * 32;  // level n-2
             const TC* tl = tab + (int64_t)ncoef(n - 1) * 12;
+            TC acc[12];
+#pragma unroll
+            for (int c = 0; c < 12; c++) acc[c] = (TC)0;
             for (int a = 0; a <= n; a++) {
                 const int k1 = n - a;
                 const int base = a * (a + 1) / 2;
@@ -95,23 +108,28 @@ __global__ void __launch_bounds__(kFarWarps * 32)
                     const int k2 = a - k3;
                     const int pos = base + k3;
                     TR s1 = 0, s2 = 0;
-                    if (k1 >= 1) s1 = dd0 * R1[pos * 32 + lane];
-                    if (k2 >= 1) s1 = fma(dd1, R1[(pos - a) * 32 + lane], s1);
-                    if (k3 >= 1) s1 = fma(dd2, R1[(pos - a - 1) * 32 + lane], s1);
+                    if (k1 >= 1) s1 = w0 * R1[pos * 32 + lane];
+                    if (k2 >= 1) s1 = fma(w1, R1[(pos - a) * 32 + lane], s1);
+                    if (k3 >= 1) s1 = fma(w2, R1[(pos - a - 1) * 32 + lane], s1);
                     if (k1 >= 2) s2 = Rm[pos * 32 + lane];
                     if (k2 >= 2) s2 += Rm[(pos - 2 * a + 1) * 32 + lane];
                     if (k3 >= 2) s2 += Rm[(pos - 2 * a - 1) * 32 + lane];
-                    const TR bk = fma(alpha, s1, -beta * s2);
-                    Rn[pos * 32 + lane] = bk;
-                    contract<TC>((TC)bk, tl + pos * 12, acc);
+                    const TR ck = fma(-kap, s2, s1);
+                    Rn[pos * 32 + lane] = ck;
+                    const TC cc = (TC)ck;
+                    const TC* t = tl + pos * 12;
+#pragma unroll
+                    for (int c = 0; c < 12; c++) acc[c] = fma(cc, t[c], acc[c]);
                 }
             }
+#pragma unroll
+            for (int c = 0; c < 12; c++) tot[c] = fma(scale, acc[c], tot[c]);
         }
         if (in) {
             const TC e0c = (TC)d0, e1c = (TC)d1, e2c = (TC)d2;
-            const TC v0 = acc[0] + e0c * acc[3] + e1c * acc[4] + e2c * acc[5];
-            const TC v1 = acc[1] + e0c * acc[6] + e1c * acc[7] + e2c * acc[8];
-            const TC v2 = acc[2] + e0c * acc[9] + e1c * acc[10] + e2c * acc[11];
+            const TC v0 = tot[0] + e0c * tot[3] + e1c * tot[4] + e2c * tot[5];
+            const TC v1 = tot[1] + e0c * tot[6] + e1c * tot[7] + e2c * tot[8];
+            const TC v2 = tot[2] + e0c * tot[9] + e1c * tot[10] + e2c * tot[11];
             ux += (double)v0;
             uy += (double)v1;
             uz += (double)v2;
@@ -134,6 +152,7 @@ cudaError_t run_far(const double* ts, int64_t M, const Geo* geo, const double* i
     cudaError_t e = cudaFuncSetAttribute(k_far<TR, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_far<TR, TC><<<grid, kFarWarps * 32, smem, s>>>(ts, M, geo, invrho, ab, p, far_off, far_list, u_far);
+    note_launch();
     return cudaGetLastError();
 }
 

@@ -109,9 +109,17 @@ struct tc_ctx {
     tc::DevBuf flags;                   // int32 device error flags
     int64_t stat_near_pairs = 0, stat_far = 0;
     int have_eval = 0;
+
+    // ---- phase timing (tc_profile / tc_phase_times)
+    int profile = 0;
+    cudaEvent_t ev[2 * TC_NPHASES] = {};
+    int ev_recorded[TC_NPHASES] = {};
 };
 
 namespace tc {
+
+// count one kernel launch (process-wide counter read by tc_kernel_launches)
+void note_launch();
 
 // error helpers (tc_api.cu)
 tc_status fail(tc_ctx* ctx, tc_status st, const char* fmt, ...);
@@ -150,6 +158,7 @@ cudaError_t launch_gather_weights(const double* f, const double* h, const double
 cudaError_t launch_source_pack(const double* xs, const double* ws, int64_t N, float4* pack, cudaStream_t s);
 cudaError_t launch_moments(const int4* topo, const Geo* geo, const double* xs, const double* ws, int64_t N,
                            int64_t nnodes, int p, double* mom, cudaStream_t s);
+cudaError_t launch_m2m(const int4* topo, const Geo* geo, int64_t lb, int64_t le, int p, double* mom, cudaStream_t s);
 cudaError_t launch_ab_tables(const double* mom, const double* invrho, int64_t nnodes, int pm, int p, double* ab64,
                              float* ab32, cudaStream_t s);
 

@@ -143,6 +143,7 @@ cudaError_t launch_lists(const double* ts, int64_t M, const int4* topo, const Ge
     double theta2 = theta * theta;
     k_lists<<<grid, kListWarps * 32, 0, s>>>(ts, M, topo, geo, theta2, write, nfar_e, nnear_e, far_off, near_off,
                                              far_list, near_list, cnt_far, cnt_near, flags);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -150,12 +151,14 @@ cudaError_t launch_scan_i32_to_i64(const int32_t* in, int64_t* out_excl, int64_t
                                    cudaStream_t s)
 {
     k_scan_i32_to_i64<<<1, 1024, 0, s>>>(in, out_excl, n, total);
+    note_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_sum_i64(const int64_t* in, int64_t n, int64_t* out, cudaStream_t s)
 {
     k_sum_i64<<<1, 1024, 0, s>>>(in, n, out);
+    note_launch();
     return cudaGetLastError();
 }
 

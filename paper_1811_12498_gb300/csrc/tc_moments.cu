@@ -82,8 +82,10 @@ constexpr int kMomThreads = 128;
 constexpr int kMomChunk = 32;
 constexpr int kMomSlots = (ncoef(kPMax) + kMomThreads - 1) / kMomThreads;
 
-// One block per cluster.  Particles are staged in chunks: their powers of
-// (y - y_c) per axis and their 12 weights; each thread owns a few k.
+// One block per leaf cluster (P2M, from the definition).  Particles are
+// staged in chunks: their powers of (y - y_c) per axis and their 12 weights;
+// each thread owns a few k.  Internal clusters are skipped here and
+// assembled from their children by k_m2m.
 __global__ void __launch_bounds__(kMomThreads) k_moments(const int4* __restrict__ topo,
                                                          const Geo* __restrict__ geo,
                                                          const double* __restrict__ xs,
@@ -94,6 +96,7 @@ __global__ void __launch_bounds__(kMomThreads) k_moments(const int4* __restrict_
     __shared__ double wt[kMomChunk][12];
     int64_t node = blockIdx.x;
     int4 t = topo[node];
+    if (t.w != 0) return;
     Geo g = geo[node];
     const int C = ncoef(p);
     int kk[kMomSlots][3];
@@ -135,6 +138,84 @@ __global__ void __launch_bounds__(kMomThreads) k_moments(const int4* __restrict_
             for (int q = 0; q < nq; q++) {
                 double mono = pw[0][q][kk[s][0]] * pw[1][q][kk[s][1]] * pw[2][q][kk[s][2]];
                 for (int c = 0; c < 12; c++) acc[s][c] = fma(mono, wt[q][c], acc[s][c]);
+            }
+        }
+    }
+    for (int s = 0; s < kMomSlots; s++) {
+        int idx = threadIdx.x + s * kMomThreads;
+        if (idx >= C) break;
+        for (int c = 0; c < 12; c++) mom[(node * 12 + c) * C + idx] = acc[s][c];
+    }
+}
+
+// Pascal's triangle up to row kPMax.
+struct Binom {
+    double v[kPMax + 1][kPMax + 1];
+};
+__host__ __device__ constexpr Binom make_binom()
+{
+    Binom b{};
+    for (int n = 0; n <= kPMax; n++) {
+        b.v[n][0] = 1.0;
+        for (int k = 1; k <= n; k++) b.v[n][k] = b.v[n - 1][k - 1] + (k <= n - 1 ? b.v[n - 1][k] : 0.0);
+    }
+    return b;
+}
+__constant__ Binom c_binom = make_binom();
+
+// M2M: moments of an internal cluster P from those of its children C by the
+// binomial theorem, (y - c_P)^k = sum_{m <= k} binom(k, m) (y - c_C)^m (c_C - c_P)^(k-m):
+//   M^k(P) = sum_C sum_{m <= k} binom(k, m) (c_C - c_P)^(k-m) M^m(C),
+// the same for all 12 components.  One block per internal cluster of one
+// level; levels are processed from the deepest up.
+__global__ void __launch_bounds__(kMomThreads) k_m2m(const int4* __restrict__ topo, const Geo* __restrict__ geo,
+                                                     int64_t lb, int64_t le, int p, double* __restrict__ mom)
+{
+    __shared__ double sp[3][kPMax + 1];
+    const int64_t node = lb + blockIdx.x;
+    if (node >= le) return;
+    const int4 t = topo[node];
+    if (t.w == 0) return;
+    const Geo gp = geo[node];
+    const int C = ncoef(p);
+    int kk[kMomSlots][3];
+    double acc[kMomSlots][12];
+    for (int s = 0; s < kMomSlots; s++) {
+        int idx = threadIdx.x + s * kMomThreads;
+        if (idx < C)
+            unflatten(idx, kk[s][0], kk[s][1], kk[s][2]);
+        else
+            kk[s][0] = kk[s][1] = kk[s][2] = 0;
+        for (int c = 0; c < 12; c++) acc[s][c] = 0.0;
+    }
+    for (int ci = 0; ci < t.w; ci++) {
+        const int64_t child = t.z + ci;
+        const Geo gc = geo[child];
+        __syncthreads();
+        if (threadIdx.x < 3) {
+            const double sh = threadIdx.x == 0 ? gc.x - gp.x : (threadIdx.x == 1 ? gc.y - gp.y : gc.z - gp.z);
+            double v = 1.0;
+            sp[threadIdx.x][0] = 1.0;
+            for (int k = 1; k <= p; k++) {
+                v *= sh;
+                sp[threadIdx.x][k] = v;
+            }
+        }
+        __syncthreads();
+        const double* mc = mom + child * 12 * C;
+        for (int s = 0; s < kMomSlots; s++) {
+            if (threadIdx.x + s * kMomThreads >= C) break;
+            const int k1 = kk[s][0], k2 = kk[s][1], k3 = kk[s][2];
+            for (int m1 = 0; m1 <= k1; m1++) {
+                const double c1 = c_binom.v[k1][m1] * sp[0][k1 - m1];
+                for (int m2 = 0; m2 <= k2; m2++) {
+                    const double c12 = c1 * c_binom.v[k2][m2] * sp[1][k2 - m2];
+                    for (int m3 = 0; m3 <= k3; m3++) {
+                        const double w = c12 * c_binom.v[k3][m3] * sp[2][k3 - m3];
+                        const int mi = flat_index(m1, m2, m3);
+                        for (int c = 0; c < 12; c++) acc[s][c] = fma(w, mc[c * C + mi], acc[s][c]);
+                    }
+                }
             }
         }
     }
@@ -236,12 +317,14 @@ cudaError_t launch_gather_weights(const double* f, const double* h, const double
                                   int64_t N, double* ws, cudaStream_t s)
 {
     k_gather_weights<<<grid_for(N, 256), 256, 0, s>>>(f, h, nu, perm, N, ws);
+    note_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_source_pack(const double* xs, const double* ws, int64_t N, float4* pack, cudaStream_t s)
 {
     k_source_pack<<<grid_for(N, 256), 256, 0, s>>>(xs, ws, N, pack);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -249,6 +332,15 @@ cudaError_t launch_moments(const int4* topo, const Geo* geo, const double* xs, c
                            int64_t nnodes, int p, double* mom, cudaStream_t s)
 {
     k_moments<<<(unsigned)nnodes, kMomThreads, 0, s>>>(topo, geo, xs, ws, N, p, mom);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_m2m(const int4* topo, const Geo* geo, int64_t lb, int64_t le, int p, double* mom, cudaStream_t s)
+{
+    if (le <= lb) return cudaSuccess;
+    k_m2m<<<(unsigned)(le - lb), kMomThreads, 0, s>>>(topo, geo, lb, le, p, mom);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -257,6 +349,7 @@ cudaError_t launch_ab_tables(const double* mom, const double* invrho, int64_t nn
 {
     int64_t total = nnodes * ncoef(p + 2);
     k_ab_tables<<<grid_for(total, 128), 128, 0, s>>>(mom, invrho, nnodes, pm, p, ab64, ab32);
+    note_launch();
     return cudaGetLastError();
 }
 

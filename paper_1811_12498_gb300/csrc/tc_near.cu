@@ -178,6 +178,7 @@ cudaError_t launch_near(int precision, const double* ts, int64_t M, const int4* 
         k_near_fp64<<<grid, kNearWarps * 32, 0, s>>>(ts, M, topo, xs, ws, N, near_off, near_list, u_near);
     else
         k_near_mixed<<<grid, kNearWarps * 32, 0, s>>>(ts, M, topo, spack, near_off, near_list, u_near);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -185,12 +186,14 @@ cudaError_t launch_finalize(const double* u_far, const double* u_near, const int
                             cudaStream_t s)
 {
     k_finalize<<<grid_for(M, 256), 256, 0, s>>>(u_far, u_near, perm, M, u);
+    note_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_scatter_counts(const int64_t* cs, const int32_t* perm, int64_t M, int64_t* out, cudaStream_t s)
 {
     k_scatter_counts<<<grid_for(M, 256), 256, 0, s>>>(cs, perm, M, out);
+    note_launch();
     return cudaGetLastError();
 }
 
