@@ -138,6 +138,37 @@ tc_status tc_direct(const double* x, const double* f, const double* h, const dou
                     const double* targets, int64_t M, int32_t precision, void* stream, double* u);
 
 /*
+ * tc_direct without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that must not allocate device memory
+ * on their own, for example a host application whose device memory is owned
+ * by a framework pool that forbids allocations from third-party libraries,
+ * or a latency-sensitive caller that cannot pay for an allocator call (an
+ * allocation may wait for the device or grow a memory pool) on its path.
+ *
+ * Same arguments, layouts, results and precision modes as tc_direct.  The
+ * scratch (the FP32 source pack of TC_MIXED, 64 B per source, and the
+ * per-split partial sums, 24 B per target per split) lives in one fixed
+ * array of TC_DIRECT_NOALLOC_SCRATCH_BYTES of device memory that is part of
+ * the library image: every device that loads the library holds it until
+ * the process exits.  A problem whose scratch does not fit even unsplit
+ * (64 B * N, rounded up to 256 B, in TC_MIXED, plus 24 B * M) is rejected
+ * with TC_EINVAL and a message that says so, before anything is enqueued;
+ * otherwise the source range is split into as many chunks as fit.
+ *
+ * No cudaMalloc, cudaFree or other allocating routine is called.  The first
+ * call on a device looks up the array's device address once for that device
+ * (with that device current); make that first call before any stream
+ * capture.  All calls on a device share the one array and it keeps the last
+ * call's contents; every scratch word a call reads is first written by the
+ * same call, so nothing needs clearing, but calls whose kernels overlap on
+ * the GPU (different streams, no ordering between them) race on the array
+ * and give wrong results.  Enqueued only.
+ */
+#define TC_DIRECT_NOALLOC_SCRATCH_BYTES (64ull << 20)
+tc_status tc_direct_noalloc(const double* x, const double* f, const double* h, const double* nu, int64_t N,
+                            const double* targets, int64_t M, int32_t precision, void* stream, double* u);
+
+/*
  * Interaction counts of the last tc_eval (host outputs, any may be NULL):
  *  near_pairs       : sum over targets of the sizes of the leaves summed directly
  *  far_interactions : number of (target, cluster) far-field evaluations

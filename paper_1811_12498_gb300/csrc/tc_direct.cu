@@ -219,3 +219,97 @@ cudaError_t launch_direct(int precision, const double* x, const double* f, const
 }
 
 }  // namespace tc
+
+// ---------------------------------------------------------------------------
+// tc_direct_noalloc: the same direct sum, with its scratch (the FP32 source
+// pack of the mixed path and the per-split partial sums) in one fixed array
+// of device memory that is part of the library image, for callers that may
+// not allocate device memory themselves.  See include/tc.h for the contract.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace tc {
+namespace {
+
+constexpr size_t kNoAllocBytes = (size_t)TC_DIRECT_NOALLOC_SCRATCH_BYTES;
+constexpr int kNoAllocMaxDevices = 64;
+
+// Device-side scratch shared by every tc_direct_noalloc call on a device.
+// Host code must not use this name as an address: it is a host-side stand-in.
+static __device__ __align__(256) unsigned char g_direct_scratch[kNoAllocBytes];
+
+// Device address of g_direct_scratch per device, looked up once per device.
+void* g_noalloc_addr[kNoAllocMaxDevices] = {};
+std::mutex g_noalloc_mu;
+
+cudaError_t noalloc_scratch(int dev, void** out)
+{
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_direct_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace tc
+
+extern "C" tc_status tc_direct_noalloc(const double* x, const double* f, const double* h, const double* nu, int64_t N,
+                                       const double* targets, int64_t M, int32_t precision, void* stream, double* u)
+{
+    using namespace tc;
+    if (!x || !f || !h || !nu || !u) return fail(nullptr, TC_EINVAL, "tc_direct_noalloc: a pointer is NULL");
+    if (N < 1 || N >= ((int64_t)1 << 31)) return fail(nullptr, TC_EINVAL, "tc_direct_noalloc: N out of range");
+    if (!targets && M != N) return fail(nullptr, TC_EINVAL, "tc_direct_noalloc: targets = NULL requires M = N");
+    if (M < 1 || M >= ((int64_t)1 << 31)) return fail(nullptr, TC_EINVAL, "tc_direct_noalloc: M out of range");
+    if (precision != TC_FP64 && precision != TC_MIXED)
+        return fail(nullptr, TC_EINVAL, "tc_direct_noalloc: unknown precision");
+    // size check first: nothing is launched for a problem that does not fit
+    DirectPlan pl = plan_direct(precision, N, M);
+    const size_t pack_off = ((pl.pack_bytes + 255) / 256) * 256;
+    const size_t per_split = (size_t)3 * (size_t)M * sizeof(double);
+    if (pack_off + per_split > kNoAllocBytes)
+        return fail(nullptr, TC_EINVAL,
+                    "tc_direct_noalloc: needs %zu bytes of scratch (64 B per source in mixed precision + 24 B per "
+                    "target), the fixed array holds %zu bytes; use tc_direct for this size",
+                    pack_off + per_split, kNoAllocBytes);
+    const int64_t max_split = (int64_t)((kNoAllocBytes - pack_off) / per_split);
+    if (pl.nsplit > max_split) {
+        pl.chunk = (N + max_split - 1) / max_split;
+        pl.chunk = (pl.chunk + 31) / 32 * 32;
+        pl.nsplit = (int)((N + pl.chunk - 1) / pl.chunk);
+    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "tc_direct_noalloc device");
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(nullptr, TC_EINVAL, "tc_direct_noalloc: device %d", dev);
+    void* base = nullptr;
+    e = noalloc_scratch(dev, &base);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "tc_direct_noalloc scratch address");
+    cudaStream_t s = (cudaStream_t)stream;
+    const double* t = targets ? targets : x;
+    float4* pack = reinterpret_cast<float4*>(base);
+    double* part = reinterpret_cast<double*>(reinterpret_cast<char*>(base) + pack_off);
+    const int64_t nbatch = (M + 31) / 32;
+    dim3 grid((unsigned)((nbatch + kDirWarps - 1) / kDirWarps), (unsigned)pl.nsplit);
+    // every scratch word read below is first written by this call: the pack by
+    // k_direct_pack, each split's partial block by its own k_direct_* launch
+    if (precision == TC_FP64) {
+        k_direct_fp64<<<grid, kDirWarps * 32, 0, s>>>(t, M, x, f, h, nu, N, pl.chunk, part);
+        note_launch();
+    } else {
+        k_direct_pack<<<grid_for(N, 256), 256, 0, s>>>(x, f, h, nu, N, pack);
+        note_launch();
+        k_direct_mixed<<<grid, kDirWarps * 32, 0, s>>>(t, M, pack, N, pl.chunk, part);
+        note_launch();
+    }
+    k_direct_reduce<<<grid_for(3 * M, 256), 256, 0, s>>>(part, pl.nsplit, M, u);
+    note_launch();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "tc_direct_noalloc launch");
+    return TC_OK;
+}
