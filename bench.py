@@ -119,7 +119,7 @@ def far_traffic(p):
     """Per-launch DRAM bytes of the far-field kernel from the committed ncu
     summary, if it was taken on the current kernel source; else None."""
     src = os.path.join(ROOT, "paper_1811_12498_gb300", "csrc", "tc_far.cu")
-    prof = os.path.join(ROOT, "profiles", "far_field_uniform_cube_1M.md")
+    prof = os.path.join(ROOT, "profiles", "far_field_uniform_cube_131k.md")
     if not os.path.exists(prof):
         return None
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()

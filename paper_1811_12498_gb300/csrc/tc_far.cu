@@ -16,22 +16,27 @@
 // factor lambda_n R'^-(n+1) multiplies the level's 12 partial contractions.
 //
 // One warp handles a batch of 32 targets (one per lane) and walks the batch's
-// far list; a lane outside an entry's mask idles for that entry.  Only levels
-// n-2, n-1 and n of c are live, kept in a per-warp shared-memory ring laid out
-// [slot][position][lane] (no bank conflicts).  Each coefficient is
-// contracted against the cluster's 12 table entries as soon as it exists.
+// far list; a lane outside an entry's mask idles for that entry.  The
+// coefficients live in a per-warp shared-memory store of two slots laid out
+// [slot][position][lane] (no bank conflicts): level n overwrites level n-2 in
+// place, positions running downward, which is safe because coefficient k
+// reads level n-2 only at positions <= its own.  Two coefficients are formed
+// per step for instruction-level parallelism.  Each coefficient is contracted
+// against the cluster's 12 table entries as soon as it exists.
 //
 // Precision: TR is the recurrence type, TC the table/contraction type.
 // FP64 mode: TR = TC = double.  Mixed: TC = float, TR = double for p >= 8 and
-// float below.  Each cluster's contribution is added to an FP64 per-target
-// accumulator.
+// float below; the FP64 -> FP32 narrowing of each coefficient is done with
+// integer operations (round to nearest, ties away from zero; magnitudes below
+// 2^-126 flushed to zero) so that it does not occupy the FP64 pipe.  Each
+// cluster's contribution is added to an FP64 per-target accumulator.
 #include "tc_internal.cuh"
 
 namespace tc {
 
 namespace {
 
-constexpr int kFarWarps = 2;
+constexpr int kFarWarps = 1;
 
 struct LevelConst {
     double kappa[kQMax + 1];  // kappa_n
@@ -48,6 +53,54 @@ __host__ __device__ constexpr LevelConst make_level_const()
 }
 __constant__ LevelConst c_lev = make_level_const();
 
+// FP64 -> FP32 by bit manipulation: round the magnitude to 23 mantissa bits
+// (adding half a unit of the last kept bit, ties away from zero; a carry
+// into the exponent is the correct result), re-bias the exponent, keep the
+// sign; values below the FP32 normal range give 0.  The inputs here are the
+// O(1) coefficients c^k, far from FP32 overflow.
+__device__ inline float narrow(double v)
+{
+    const unsigned long long r = (unsigned long long)__double_as_longlong(v) + 0x10000000ull;
+    const unsigned hi = (unsigned)(r >> 32);
+    const unsigned lo = (unsigned)r;
+    const unsigned e = (hi >> 20) & 0x7ffu;
+    const unsigned m = __funnelshift_l(lo, hi, 3);  // top 23 mantissa bits in m & 0x7fffff
+    const unsigned bits = (hi & 0x80000000u) | ((e - 896u) << 23) | (m & 0x7fffffu);
+    return e > 896u ? __uint_as_float(bits) : 0.0f;
+}
+
+template <typename TR, typename TC>
+__device__ inline TC to_tc(TR v)
+{
+    return (TC)v;
+}
+template <>
+__device__ inline float to_tc<double, float>(double v)
+{
+    return narrow(v);
+}
+
+template <typename TR>
+__device__ inline TR coef(const TR* R1, const TR* R2, int pos, int a, int k1, int k2, int k3, TR w0, TR w1, TR w2,
+                          TR kap, int lane)
+{
+    TR s1 = 0, s2 = 0;
+    if (k1 >= 1) s1 = w0 * R1[pos * 32 + lane];
+    if (k2 >= 1) s1 = fma(w1, R1[(pos - a) * 32 + lane], s1);
+    if (k3 >= 1) s1 = fma(w2, R1[(pos - a - 1) * 32 + lane], s1);
+    if (k1 >= 2) s2 = R2[pos * 32 + lane];
+    if (k2 >= 2) s2 += R2[(pos - 2 * a + 1) * 32 + lane];
+    if (k3 >= 2) s2 += R2[(pos - 2 * a - 1) * 32 + lane];
+    return fma(-kap, s2, s1);
+}
+
+template <typename TC>
+__device__ inline void contract(TC c, const TC* __restrict__ t, TC* acc)
+{
+#pragma unroll
+    for (int q = 0; q < 12; q++) acc[q] = fma(c, t[q], acc[q]);
+}
+
 template <typename TR, typename TC>
 __global__ void __launch_bounds__(kFarWarps * 32)
     k_far(const double* __restrict__ ts, int64_t M, const Geo* __restrict__ geo,
@@ -60,9 +113,11 @@ __global__ void __launch_bounds__(kFarWarps * 32)
     const int64_t b = blockIdx.x * (int64_t)kFarWarps + w;
     if (b >= nbatch) return;
     const int P = p + 2;
-    const int LS = level_size(P);
     const int C2 = ncoef(P);
-    TR* ring = reinterpret_cast<TR*>(smraw) + (size_t)w * 3 * LS * 32;
+    // slot of parity P holds levels P, P-2, ...; the other slot P-1, P-3, ...
+    const int LSP = level_size(P), LSQ = level_size(P - 1);
+    TR* slot_p = reinterpret_cast<TR*>(smraw) + (size_t)w * (LSP + LSQ) * 32;
+    TR* slot_q = slot_p + (size_t)LSP * 32;
     const int64_t m = b * kBatch + lane;
     const bool valid = m < M;
     double x0 = 0, x1 = 0, x2 = 0;
@@ -85,45 +140,42 @@ __global__ void __launch_bounds__(kFarWarps * 32)
         const TR w0 = (TR)(d0 * iR), w1 = (TR)(d1 * iR), w2 = (TR)(d2 * iR);
         const TC* __restrict__ tab = ab + (int64_t)le.node * C2 * 12;
         TC tot[12];
+        TC scale = (TC)iR;  // lambda_0 R'^-1; level 0: c^0 = 1
 #pragma unroll
-        for (int c = 0; c < 12; c++) tot[c] = tab[c];  // level 0: c^0 = 1
-        TC scale = (TC)iR;                             // lambda_0 R'^-1
-#pragma unroll
-        for (int c = 0; c < 12; c++) tot[c] *= scale;
-        ring[lane] = (TR)1;
+        for (int q = 0; q < 12; q++) tot[q] = scale * tab[q];
+        ((P & 1) ? slot_q : slot_p)[lane] = (TR)1;  // level 0 has parity 0
+        __syncwarp();
         for (int n = 1; n <= P; n++) {
             const TR kap = (TR)c_lev.kappa[n];
             scale *= (TC)(c_lev.ratio[n] * iR);
-            TR* Rn = ring + (n % 3) * LS * 32;
-            const TR* R1 = ring + ((n - 1) % 3) * LS * 32;
-            const TR* Rm = ring + ((n + 1) % 3) * LS * 32;  // level n-2
+            TR* Rn = ((n ^ P) & 1) ? slot_q : slot_p;  // also holds level n-2
+            const TR* R1 = ((n ^ P) & 1) ? slot_p : slot_q;
             const TC* tl = tab + (int64_t)ncoef(n - 1) * 12;
             TC acc[12];
 #pragma unroll
-            for (int c = 0; c < 12; c++) acc[c] = (TC)0;
-            for (int a = 0; a <= n; a++) {
+            for (int q = 0; q < 12; q++) acc[q] = (TC)0;
+            for (int a = n; a >= 0; a--) {
                 const int k1 = n - a;
                 const int base = a * (a + 1) / 2;
-                for (int k3 = 0; k3 <= a; k3++) {
-                    const int k2 = a - k3;
+                int k3 = a;
+                for (; k3 >= 1; k3 -= 2) {
                     const int pos = base + k3;
-                    TR s1 = 0, s2 = 0;
-                    if (k1 >= 1) s1 = w0 * R1[pos * 32 + lane];
-                    if (k2 >= 1) s1 = fma(w1, R1[(pos - a) * 32 + lane], s1);
-                    if (k3 >= 1) s1 = fma(w2, R1[(pos - a - 1) * 32 + lane], s1);
-                    if (k1 >= 2) s2 = Rm[pos * 32 + lane];
-                    if (k2 >= 2) s2 += Rm[(pos - 2 * a + 1) * 32 + lane];
-                    if (k3 >= 2) s2 += Rm[(pos - 2 * a - 1) * 32 + lane];
-                    const TR ck = fma(-kap, s2, s1);
-                    Rn[pos * 32 + lane] = ck;
-                    const TC cc = (TC)ck;
-                    const TC* t = tl + pos * 12;
-#pragma unroll
-                    for (int c = 0; c < 12; c++) acc[c] = fma(cc, t[c], acc[c]);
+                    const TR ca = coef<TR>(R1, Rn, pos, a, k1, a - k3, k3, w0, w1, w2, kap, lane);
+                    const TR cb = coef<TR>(R1, Rn, pos - 1, a, k1, a - k3 + 1, k3 - 1, w0, w1, w2, kap, lane);
+                    Rn[pos * 32 + lane] = ca;
+                    Rn[(pos - 1) * 32 + lane] = cb;
+                    contract<TC>(to_tc<TR, TC>(ca), tl + pos * 12, acc);
+                    contract<TC>(to_tc<TR, TC>(cb), tl + (pos - 1) * 12, acc);
+                }
+                if (k3 == 0) {
+                    const TR ca = coef<TR>(R1, Rn, base, a, k1, a, 0, w0, w1, w2, kap, lane);
+                    Rn[base * 32 + lane] = ca;
+                    contract<TC>(to_tc<TR, TC>(ca), tl + base * 12, acc);
                 }
             }
+            __syncwarp();
 #pragma unroll
-            for (int c = 0; c < 12; c++) tot[c] = fma(scale, acc[c], tot[c]);
+            for (int q = 0; q < 12; q++) tot[q] = fma(scale, acc[q], tot[q]);
         }
         if (in) {
             const TC e0c = (TC)d0, e1c = (TC)d1, e2c = (TC)d2;
@@ -148,7 +200,7 @@ cudaError_t run_far(const double* ts, int64_t M, const Geo* geo, const double* i
 {
     int64_t nbatch = (M + kBatch - 1) / kBatch;
     unsigned grid = (unsigned)((nbatch + kFarWarps - 1) / kFarWarps);
-    size_t smem = (size_t)kFarWarps * 3 * level_size(p + 2) * 32 * sizeof(TR);
+    size_t smem = (size_t)kFarWarps * (level_size(p + 2) + level_size(p + 1)) * 32 * sizeof(TR);
     cudaError_t e = cudaFuncSetAttribute(k_far<TR, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_far<TR, TC><<<grid, kFarWarps * 32, smem, s>>>(ts, M, geo, invrho, ab, p, far_off, far_list, u_far);
