@@ -126,6 +126,32 @@ tc_status tc_moments(tc_ctx* ctx, const double* f, const double* h, const double
 tc_status tc_eval(tc_ctx* ctx, const double* targets, int64_t M, double theta, int32_t p, double* u);
 
 /*
+ * Adjoint of the last tc_eval with its structure frozen.  For
+ *   L = sum_m g^m . u(x^m)
+ * it returns dL/df, dL/dh, dL/dnu, dL/dx and dL/dt while the tree (cluster
+ * membership, centres y_c and radii), every target's far/near decisions and
+ * the Taylor order p of that tc_eval are held fixed; this is the exact
+ * derivative of the discrete map that tc_eval computes, up to rounding.
+ * (The paper does not differentiate the method; the formulas follow from
+ * eqs. (1.3), (2.9), (3.2) and Section 4.1 by the chain rule.)
+ *  g       : device 3*M FP64 SoA in the target order of the last tc_eval.
+ *  grad_f, grad_h, grad_nu : device 3*N FP64 SoA (caller's source order),
+ *            written; any may be NULL.
+ *  grad_x  : device 3*N FP64 or NULL.  Derivative with respect to the
+ *            source positions; when the last tc_eval had targets = NULL it is
+ *            the total derivative with respect to the particle positions.
+ *  grad_t  : device 3*M FP64 or NULL: derivative with respect to the target
+ *            positions of a tc_eval with disjoint targets; must be NULL when
+ *            the targets were the sources.
+ * The source-side far-field term is accumulated per cluster with FP64
+ * atomics, so repeated calls agree to FP64 rounding, not bit for bit.
+ * Requires tc_eval.  Synchronises the stream the first time after a tc_eval
+ * (its interaction lists are sorted by cluster).
+ */
+tc_status tc_adjoint(tc_ctx* ctx, const double* g, double* grad_f, double* grad_h, double* grad_nu, double* grad_x,
+                     double* grad_t);
+
+/*
  * Direct O(N*M) sum of eq. (1.3) (with the contraction of Section 4.1).
  *  x, f, h, nu : device, 3*N FP64 SoA.  targets: device 3*M SoA or NULL
  *  (targets = sources, M must equal N).  u: device 3*M FP64 SoA, written.
@@ -175,6 +201,17 @@ tc_status tc_direct_noalloc(const double* x, const double* f, const double* h, c
  *  clusters         : number of clusters in the tree
  */
 tc_status tc_stats(tc_ctx* ctx, int64_t* near_pairs, int64_t* far_interactions, int64_t* clusters);
+
+/*
+ * Interaction-list sizes of the last tc_eval (host outputs, any may be NULL):
+ *  far_entries         : (batch, cluster) far-field list entries; a batch is 32
+ *                        targets, so far_interactions / (32 far_entries) is the
+ *                        fraction of far-kernel lanes doing useful work
+ *  near_entries        : (batch, leaf) near-field list entries
+ *  near_entry_sources  : sum over near entries of the leaf size; near_pairs /
+ *                        (32 near_entry_sources) is the near-kernel lane use
+ */
+tc_status tc_list_stats(tc_ctx* ctx, int64_t* far_entries, int64_t* near_entries, int64_t* near_entry_sources);
 
 /*
  * Per-target counts of the last tc_eval, in the target order of that call

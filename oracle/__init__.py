@@ -62,6 +62,7 @@ def _load():
         "orc_tree_export_moments": (None, [vp, c_i64, _d, _d]),
         "orc_treecode": (c_int, [vp, _d, c_i64, c_dbl, c_int, _d, vp, vp, vp, c_int]),
         "orc_far_mass": (None, [vp, _d, c_i64, c_dbl, _i64]),
+        "orc_treecode_frozen": (c_int, [vp, _d, _d, _d, _d, c_int, _d, _d, c_i64, c_dbl, _d, c_int]),
         "orc_max_threads": (c_int, []),
     }
     for name, (res, args) in sig.items():
@@ -234,6 +235,17 @@ class Tree:
             raise ValueError("oracle treecode needs moments of order >= p")
         if counts:
             return u, dict(far=nf, near_leaves=nl, near_pairs=npairs)
+        return u
+
+    def treecode_frozen(self, xe, f, h, nu, p, td, te, theta, nthreads=0):
+        """Frozen-structure velocity: MAC decisions at td, moments and direct
+        sums at the moved sources xe, evaluation at the moved targets te."""
+        xe, f, h, nu, td, te = (_c3(a) for a in (xe, f, h, nu, td, te))
+        u = np.empty((te.shape[0], 3))
+        rc = _load().orc_treecode_frozen(self._h, _ptr(xe), _ptr(f), _ptr(h), _ptr(nu), int(p), _ptr(td), _ptr(te),
+                                         te.shape[0], float(theta), _ptr(u), nthreads)
+        if rc != 0:
+            raise ValueError("oracle frozen treecode rejected p")
         return u
 
     def far_mass(self, targets, theta):

@@ -684,3 +684,83 @@ int orc_max_threads(void)
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------ */
+/* Frozen-structure evaluation, for finite-difference checks of the    */
+/* adjoint.  The tree built from the original positions keeps its      */
+/* cluster membership, centres y_c and radii; every target takes the   */
+/* MAC decisions of Algorithm 1 at its decision position td; the       */
+/* moments (Section 2) and the direct sums (Section 4.1) use the moved  */
+/* source positions xe, and far fields and direct sums are evaluated   */
+/* at the moved target positions te.  With xe = x and td = te this is  */
+/* orc_treecode.                                                       */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    const orc_tree* t;
+    const double *xe, *f, *h, *nu;
+    const double *Mf, *Mt; /* moments at xe, per node */
+    int p, n3;
+    double theta;
+} orc_frozen;
+
+static void compute_velocity_frozen(const orc_frozen* z, int64_t c, const double* xd, const double* xm, double* u)
+{
+    const orc_tree* t = z->t;
+    const orc_node* nd = &t->nodes[c];
+    double dd[3] = {xd[0] - nd->yc[0], xd[1] - nd->yc[1], xd[2] - nd->yc[2]};
+    double R2 = (dd[0] * dd[0] + dd[1] * dd[1]) + dd[2] * dd[2];
+    int mac = (R2 > 0.0) && (nd->rc2 <= (z->theta * z->theta) * R2);
+    if (mac) {
+        double d[3] = {xm[0] - nd->yc[0], xm[1] - nd->yc[1], xm[2] - nd->yc[2]};
+        double uf[3];
+        orc_far_contracted(d, z->p, z->Mf + (size_t)c * 3 * z->n3, z->Mt + (size_t)c * 9 * z->n3, uf);
+        for (int i = 0; i < 3; i++) u[i] += uf[i];
+    } else if (nd->nchild == 0) {
+        for (int64_t q = 0; q < nd->count; q++) {
+            int64_t n = t->order[nd->begin + q];
+            const double* y = z->xe + 3 * n;
+            double d[3] = {xm[0] - y[0], xm[1] - y[1], xm[2] - y[2]};
+            double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            if (r2 == 0.0) continue;
+            double r = sqrt(r2);
+            const double* f = z->f + 3 * n;
+            const double* h = z->h + 3 * n;
+            const double* nu = z->nu + 3 * n;
+            double s = (d[0] * f[0] + d[1] * f[1] + d[2] * f[2]) / (r * r2);
+            double tt = (d[0] * h[0] + d[1] * h[1] + d[2] * h[2]) * (d[0] * nu[0] + d[1] * nu[1] + d[2] * nu[2]) /
+                        (r2 * r2 * r);
+            for (int i = 0; i < 3; i++) u[i] += f[i] / r + d[i] * (s + tt);
+        }
+    } else {
+        for (int o = 0; o < nd->nchild; o++) compute_velocity_frozen(z, nd->child[o], xd, xm, u);
+    }
+}
+
+int orc_treecode_frozen(const orc_tree* t, const double* xe, const double* f, const double* h, const double* nu, int p,
+                        const double* td, const double* te, int64_t M, double theta, double* u, int nthreads)
+{
+    if (p < 0 || p > ORC_PMAX) return -1;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+    (void)nthreads;
+    int n3 = (p + 1) * (p + 1) * (p + 1);
+    double* Mf = (double*)malloc(sizeof(double) * 3 * n3 * (size_t)t->nnodes);
+    double* Mt = (double*)malloc(sizeof(double) * 9 * n3 * (size_t)t->nnodes);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t c = 0; c < t->nnodes; c++) {
+        const orc_node* nd = &t->nodes[c];
+        orc_moments(xe, f, h, nu, t->order + nd->begin, nd->count, nd->yc, p, Mf + (size_t)c * 3 * n3,
+                    Mt + (size_t)c * 9 * n3);
+    }
+    orc_frozen z = {t, xe, f, h, nu, Mf, Mt, p, n3, theta};
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t m = 0; m < M; m++) {
+        double acc[3] = {0, 0, 0};
+        compute_velocity_frozen(&z, 0, td + 3 * m, te + 3 * m, acc);
+        for (int i = 0; i < 3; i++) u[3 * m + i] = acc[i];
+    }
+    free(Mf);
+    free(Mt);
+    return 0;
+}

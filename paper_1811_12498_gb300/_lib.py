@@ -20,10 +20,12 @@ SIGNATURES = {
     "tc_build": (_i32, [_vp, _vp, _i64, _i32]),
     "tc_moments": (_i32, [_vp, _vp, _vp, _vp, _i32]),
     "tc_eval": (_i32, [_vp, _vp, _i64, _dbl, _i32, _vp]),
+    "tc_adjoint": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "tc_direct": (_i32, [_vp, _vp, _vp, _vp, _i64, _vp, _i64, _i32, _vp, _vp]),
     "tc_direct_noalloc": (_i32, [_vp, _vp, _vp, _vp, _i64, _vp, _i64, _i32, _vp, _vp]),
     "tc_stats": (_i32, [_vp, _vp, _vp, _vp]),
     "tc_eval_counts": (_i32, [_vp, _vp, _vp]),
+    "tc_list_stats": (_i32, [_vp, _vp, _vp, _vp]),
     "tc_tree_info": (_i32, [_vp, _vp, _vp, _vp, _vp]),
     "tc_tree_export": (_i32, [_vp] + [_vp] * 9),
     "tc_tree_order": (_i32, [_vp, _vp]),

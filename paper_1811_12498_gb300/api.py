@@ -124,6 +124,23 @@ class Treecode:
     def sync(self):
         self._chk(lib().tc_sync(self._h))
 
+    def adjoint(self, g, f=True, h=True, nu=True, x=True, t=False):
+        """Gradients of L = sum_m g^m . u^m with the structure of the last eval
+        frozen (tc_adjoint).  g: (3, M).  Returns a dict with the requested
+        entries among f, h, nu, x (each (3, N)) and t (targets, (3, M))."""
+        M = self._M
+        g = _vec3(g, "g", M)
+        out = {}
+        with torch.cuda.stream(self.stream):
+            for k, want, n in (("f", f, self.N), ("h", h, self.N), ("nu", nu, self.N), ("x", x, self.N),
+                               ("t", t, M)):
+                if want:
+                    out[k] = torch.empty((3, n), dtype=torch.float64, device="cuda")
+        self._chk(lib().tc_adjoint(self._h, _ptr(g), _ptr(out.get("f")), _ptr(out.get("h")), _ptr(out.get("nu")),
+                                   _ptr(out.get("x")), _ptr(out.get("t"))))
+        self._keep_g = g
+        return out
+
     def profile(self, enable=True):
         """Enable per-phase CUDA-event timing (see phase_times)."""
         self._chk(lib().tc_profile(self._h, int(bool(enable))))
@@ -138,6 +155,16 @@ class Treecode:
         near, far, nodes = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
         self._chk(lib().tc_stats(self._h, ctypes.byref(near), ctypes.byref(far), ctypes.byref(nodes)))
         return dict(near_pairs=near.value, far_interactions=far.value, clusters=nodes.value)
+
+    def list_stats(self):
+        """Interaction-list sizes of the last eval and the fraction of kernel
+        lanes doing useful work in the far and near kernels."""
+        fe, ne, ns = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        self._chk(lib().tc_list_stats(self._h, ctypes.byref(fe), ctypes.byref(ne), ctypes.byref(ns)))
+        st = self.stats()
+        return dict(far_entries=fe.value, near_entries=ne.value, near_entry_sources=ns.value,
+                    far_lane_use=st["far_interactions"] / max(1, 32 * fe.value),
+                    near_lane_use=st["near_pairs"] / max(1, 32 * ns.value))
 
     def eval_counts(self):
         M = self.N if getattr(self, "_M", None) is None else self._M
@@ -192,6 +219,39 @@ def direct(x, f, h, nu, targets=None, precision="fp64", out=None, stream=None):
     _check(lib().tc_direct(_ptr(x), _ptr(f), _ptr(h), _ptr(nu), N, _ptr(t), M, _prec(precision),
                            _stream_ptr(stream), _ptr(out)))
     return out
+
+
+class StokesTreecode(torch.autograd.Function):
+    """u = treecode velocity (eq. 1.3 by Algorithm 1) as a differentiable op.
+
+    forward(x, f, h, nu, theta, p, N0, precision, shrink): x, f, h, nu are
+    (3, N) float64 CUDA tensors; returns u (3, N) at the particles.
+    backward: the adjoint with the tree and interaction lists of the forward
+    pass frozen (tc_adjoint); gradients for x, f, h and nu.
+    """
+
+    @staticmethod
+    def forward(ctx, x, f, h, nu, theta, p, N0, precision="mixed", shrink=True):
+        tc = Treecode(precision, shrink)
+        tc.build(x.detach(), N0).moments(f.detach(), h.detach(), nu.detach(), p)
+        u = tc.eval(theta, p)
+        ctx.tc = tc
+        return u
+
+    @staticmethod
+    def backward(ctx, gu):
+        tc = ctx.tc
+        need = ctx.needs_input_grad
+        gr = tc.adjoint(gu.contiguous(), f=need[1], h=need[2], nu=need[3], x=need[0])
+        tc.sync()
+        tc.close()
+        ctx.tc = None
+        return gr.get("x"), gr.get("f"), gr.get("h"), gr.get("nu"), None, None, None, None, None
+
+
+def stokes_velocity(x, f, h, nu, theta, p, N0, precision="mixed", shrink=True):
+    """Differentiable treecode velocity at the particles (see StokesTreecode)."""
+    return StokesTreecode.apply(x, f, h, nu, theta, p, N0, precision, shrink)
 
 
 def kernel_launches():

@@ -1,0 +1,879 @@
+// Adjoint of the treecode velocity with the structure frozen.
+//
+// For L = sum_m g^m . u(x^m), with the tree (membership, centres y_c, radii),
+// every target's MAC decisions and the order p of the last tc_eval held
+// fixed, this computes dL/df, dL/dh, dL/dnu and dL/dx (source and target
+// positions).  The paper does not differentiate its method; the derivation
+// below is the chain rule applied to its formulas.
+//
+// Near field (Section 4.1 kernel K_i(d) = f_i/r + d_i (s + t), d = x_m - y_n):
+//   g.K = (g.f)/r + (g.d)(s + t),  s = (d.f)/r^3,  t = (d.h)(d.nu)/r^5,
+//   d(g.K)/df_j  = g_j/r + d_j (g.d)/r^3,
+//   d(g.K)/dh_j  = d_j (g.d)(d.nu)/r^5,   d(g.K)/dnu_l = d_l (g.d)(d.h)/r^5,
+//   d(g.K)/dd_a  = d_a c1 + g_a (s + t) + f_a c3 + h_a c4 + nu_a c5,
+//   c1 = -((g.f)/r^3 + (g.d)(3 (d.f)/r^5 + 5 (d.h)(d.nu)/r^7)),
+//   c3 = (g.d)/r^3,  c4 = (g.d)(d.nu)/r^5,  c5 = (g.d)(d.h)/r^5;
+// the target gets +d(g.K)/dd, the source -d(g.K)/dd.
+//
+// Far field, target side: with u_i = sum_k b^k(d') (Â_i^k + d'_q B̂_iq^k),
+// d' = (x - y_c)/rho, and d b^k/d d'_l = -(k_l + 1) b^{k+e_l} (b^k is a
+// Taylor coefficient in y of a function of x - y):
+//   sum_i g_i du_i/dx_l = (1/rho) sum_k [ b^k beta_l^k - (k_l + 1) b^{k+e_l} alpha^k ],
+//   alpha^k = g.(Â^k + d'_q B̂_.q^k),  beta_l^k = sum_i g_i B̂_il^k,
+// so the recurrence runs one level further, to p + 3.
+//
+// Far field, source side: the tables are linear in the moments, so
+//   Ā_i^k = sum_m g_i^m b^k(d'_m),  B̄_iq^k = sum_m g_i^m d'_q b^k(d'_m)
+// summed over the targets m that accept the cluster, give the adjoint moments
+// Lambda_c^k = dL/dM_c^k by the transpose of the table map (k_lambda).  A
+// particle y in clusters C then has dL/dw_c = sum_C sum_k Lambda_c^k(C) (y - y_C)^k;
+// the ancestors' polynomials are re-expanded about the leaf centre by the
+// binomial theorem (k_l2l) and evaluated once per particle (k_leaf_eval),
+// with dL/dy = sum_c w_c grad_y of the same polynomial.  Weights:
+// w = (f_0..2, h_j nu_l), so dL/dh_j = sum_l nu_l dL/dw_{3+3j+l} and
+// dL/dnu_l = sum_j h_j dL/dw_{3+3j+l}.
+//
+// Work decomposition: the target-side kernels are batch-major like the
+// forward ones; the source-side kernels are cluster-major or leaf-major over
+// the forward lists sorted by cluster (stable radix sort, so entries keep
+// their batch order).  The cluster-major far kernel accumulates per warp in
+// shared memory and flushes with FP64 atomics when the cluster changes, so
+// the source-side far gradient is reproducible only up to FP64 rounding.
+#include "tc_recurrence.cuh"
+
+namespace tc {
+
+namespace {
+
+__constant__ LevelConst c_lev = make_level_const();
+
+inline unsigned grid_for(int64_t n, int threads)
+{
+    int64_t g = (n + threads - 1) / threads;
+    return (unsigned)(g > 0 ? g : 1);
+}
+
+__device__ inline void unflatten(int idx, int& k1, int& k2, int& k3)
+{
+    int n = 0;
+    while (ncoef(n) <= idx) n++;
+    int pos = idx - (n > 0 ? ncoef(n - 1) : 0);
+    int a = 0;
+    while ((a + 1) * (a + 2) / 2 <= pos) a++;
+    k3 = pos - a * (a + 1) / 2;
+    k2 = a - k3;
+    k1 = n - a;
+}
+
+// ------------------------------------------------------------ list helpers
+__global__ void k_entry_keys(const ListEntry* __restrict__ list, int64_t n, uint64_t* __restrict__ keys,
+                             int32_t* __restrict__ idx)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    keys[i] = (uint64_t)(uint32_t)list[i].node;
+    idx[i] = (int32_t)i;
+}
+
+// batch of each list entry: largest b with off[b] <= e
+__global__ void k_entry_batch(const int64_t* __restrict__ off, int64_t nbatch, int64_t n, int32_t* __restrict__ eb)
+{
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    int64_t lo = 0, hi = nbatch;  // off[lo] <= e < off[hi]
+    while (hi - lo > 1) {
+        int64_t mid = (lo + hi) >> 1;
+        if (off[mid] <= e)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    eb[e] = (int32_t)lo;
+}
+
+__global__ void k_gather_g(const double* __restrict__ g, const int32_t* __restrict__ perm, int64_t M,
+                           double* __restrict__ gs)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    int64_t j = perm[i];
+    gs[i] = g[j];
+    gs[M + i] = g[M + j];
+    gs[2 * M + i] = g[2 * M + j];
+}
+
+// first index in sorted keys[0, n) that is >= v
+__device__ inline int64_t lower_key(const uint64_t* keys, int64_t n, uint64_t v)
+{
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (keys[mid] < v)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+// ------------------------------------------------------- near, pair terms
+// Writes the five scalar factors of d(g.K)/dd and of the weight gradients.
+template <typename T>
+struct NearTerms {
+    T ri, st, c1, c3, c4, c5;
+};
+
+template <typename T>
+__device__ inline NearTerms<T> near_terms(T dx, T dy, T dz, const T* f, const T* h, const T* nu, const T* g,
+                                          T ri)
+{
+    NearTerms<T> o;
+    const T ri2 = ri * ri, ri3 = ri2 * ri, ri5 = ri3 * ri2, ri7 = ri5 * ri2;
+    const T df = dx * f[0] + dy * f[1] + dz * f[2];
+    const T dh = dx * h[0] + dy * h[1] + dz * h[2];
+    const T dn = dx * nu[0] + dy * nu[1] + dz * nu[2];
+    const T gd = dx * g[0] + dy * g[1] + dz * g[2];
+    const T gf = g[0] * f[0] + g[1] * f[1] + g[2] * f[2];
+    o.ri = ri;
+    o.st = df * ri3 + dh * dn * ri5;
+    o.c1 = -(gf * ri3 + gd * (3 * df * ri5 + 5 * dh * dn * ri7));
+    o.c3 = gd * ri3;
+    o.c4 = gd * dn * ri5;
+    o.c5 = gd * dh * ri5;
+    return o;
+}
+
+constexpr int kNearAdjWarps = 4;
+
+// Target side of the near field, batch-major (one warp per 32 targets).
+template <typename T>
+__global__ void __launch_bounds__(kNearAdjWarps * 32)
+    k_near_adj_target(const double* __restrict__ ts, const double* __restrict__ gs, int64_t M,
+                      const int4* __restrict__ topo, const double* __restrict__ xs, const double* __restrict__ ws,
+                      int64_t N, const int64_t* __restrict__ near_off, const ListEntry* __restrict__ near_list,
+                      double* __restrict__ gt)
+{
+    // source tile: x_hi(3) x_lo(3) f(3) h(3) nu(3) per source
+    __shared__ T tile[kNearAdjWarps][15][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t nbatch = (M + kBatch - 1) / kBatch;
+    const int64_t b = blockIdx.x * (int64_t)kNearAdjWarps + w;
+    if (b >= nbatch) return;
+    const int64_t m = b * kBatch + lane;
+    const bool valid = m < M;
+    T th[3] = {0, 0, 0}, tl[3] = {0, 0, 0}, g[3] = {0, 0, 0};
+    if (valid)
+        for (int a = 0; a < 3; a++) {
+            const double v = ts[a * M + m];
+            th[a] = (T)v;
+            tl[a] = (T)(v - (double)th[a]);
+            g[a] = (T)gs[a * M + m];
+        }
+    double acc[3] = {0, 0, 0};
+    for (int64_t e = near_off[b]; e < near_off[b + 1]; e++) {
+        const ListEntry le = near_list[e];
+        const bool in = (le.mask >> lane) & 1u;
+        const int4 t = topo[le.node];
+        for (int base = t.x; base < t.x + t.y; base += 32) {
+            const int cnt = min(32, t.x + t.y - base);
+            __syncwarp();
+            if (lane < cnt) {
+                const int64_t i = base + lane;
+                for (int a = 0; a < 3; a++) {
+                    const double v = xs[a * N + i];
+                    const T hi = (T)v;
+                    tile[w][a][lane] = hi;
+                    tile[w][3 + a][lane] = (T)(v - (double)hi);
+                }
+                for (int c = 0; c < 9; c++) tile[w][6 + c][lane] = (T)ws[c * N + i];
+            }
+            __syncwarp();
+            if (!in) continue;
+            T a0 = 0, a1 = 0, a2 = 0;
+            for (int j = 0; j < cnt; j++) {
+                const T dx = (th[0] - tile[w][0][j]) + (tl[0] - tile[w][3][j]);
+                const T dy = (th[1] - tile[w][1][j]) + (tl[1] - tile[w][4][j]);
+                const T dz = (th[2] - tile[w][2][j]) + (tl[2] - tile[w][5][j]);
+                const T r2 = dx * dx + dy * dy + dz * dz;
+                const T ri = r2 > (T)0 ? (T)1 / sqrt(r2) : (T)0;
+                const T f[3] = {tile[w][6][j], tile[w][7][j], tile[w][8][j]};
+                const T h[3] = {tile[w][9][j], tile[w][10][j], tile[w][11][j]};
+                const T nu[3] = {tile[w][12][j], tile[w][13][j], tile[w][14][j]};
+                const NearTerms<T> q = near_terms<T>(dx, dy, dz, f, h, nu, g, ri);
+                a0 += dx * q.c1 + g[0] * q.st + f[0] * q.c3 + h[0] * q.c4 + nu[0] * q.c5;
+                a1 += dy * q.c1 + g[1] * q.st + f[1] * q.c3 + h[1] * q.c4 + nu[1] * q.c5;
+                a2 += dz * q.c1 + g[2] * q.st + f[2] * q.c3 + h[2] * q.c4 + nu[2] * q.c5;
+            }
+            acc[0] += (double)a0;
+            acc[1] += (double)a1;
+            acc[2] += (double)a2;
+        }
+    }
+    if (valid)
+        for (int a = 0; a < 3; a++) gt[a * M + m] += acc[a];
+}
+
+// Source side of the near field, leaf-major: a block per leaf, a warp per 32
+// of its sources, looping over the near entries (batch, lane mask) that name
+// the leaf; targets of an entry are staged in shared memory.
+template <typename T>
+__global__ void __launch_bounds__(kNearAdjWarps * 32)
+    k_near_adj_source(const double* __restrict__ ts, const double* __restrict__ gs, int64_t M,
+                      const int4* __restrict__ topo, const double* __restrict__ xs, const double* __restrict__ ws,
+                      int64_t N, const uint64_t* __restrict__ skeys, const int32_t* __restrict__ sidx,
+                      const ListEntry* __restrict__ near_list, const int32_t* __restrict__ ebatch, int64_t nent,
+                      double* __restrict__ gnear)
+{
+    __shared__ T tile[kNearAdjWarps][9][32];  // target x_hi(3) x_lo(3) g(3)
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t node = blockIdx.x;
+    const int4 t = topo[node];
+    if (t.w != 0) return;
+    const int64_t j0 = lower_key(skeys, nent, (uint64_t)node), j1 = lower_key(skeys, nent, (uint64_t)node + 1);
+    for (int tile0 = w * 32; tile0 < t.y; tile0 += kNearAdjWarps * 32) {
+        const int64_t si = t.x + tile0 + lane;
+        const bool valid = tile0 + lane < t.y;
+        T sh[3] = {0, 0, 0}, sl[3] = {0, 0, 0}, f[3] = {0, 0, 0}, h[3] = {0, 0, 0}, nu[3] = {0, 0, 0};
+        if (valid)
+            for (int a = 0; a < 3; a++) {
+                const double v = xs[a * N + si];
+                sh[a] = (T)v;
+                sl[a] = (T)(v - (double)sh[a]);
+                f[a] = (T)ws[a * N + si];
+                h[a] = (T)ws[(3 + a) * N + si];
+                nu[a] = (T)ws[(6 + a) * N + si];
+            }
+        double acc[12];
+        for (int c = 0; c < 12; c++) acc[c] = 0.0;
+        for (int64_t j = j0; j < j1; j++) {
+            const int32_t e = sidx[j];
+            const unsigned mask = near_list[e].mask;
+            const int64_t m = (int64_t)ebatch[e] * kBatch + lane;
+            __syncwarp();
+            if ((mask >> lane) & 1u)
+                for (int a = 0; a < 3; a++) {
+                    const double v = ts[a * M + m];
+                    const T hi = (T)v;
+                    tile[w][a][lane] = hi;
+                    tile[w][3 + a][lane] = (T)(v - (double)hi);
+                    tile[w][6 + a][lane] = (T)gs[a * M + m];
+                }
+            __syncwarp();
+            T a[12];
+            for (int c = 0; c < 12; c++) a[c] = 0;
+            unsigned mm = mask;
+            while (mm) {
+                const int q = __ffs(mm) - 1;
+                mm &= mm - 1;
+                const T dx = (tile[w][0][q] - sh[0]) + (tile[w][3][q] - sl[0]);
+                const T dy = (tile[w][1][q] - sh[1]) + (tile[w][4][q] - sl[1]);
+                const T dz = (tile[w][2][q] - sh[2]) + (tile[w][5][q] - sl[2]);
+                const T g[3] = {tile[w][6][q], tile[w][7][q], tile[w][8][q]};
+                const T r2 = dx * dx + dy * dy + dz * dz;
+                const T ri = r2 > (T)0 ? (T)1 / sqrt(r2) : (T)0;
+                const NearTerms<T> z = near_terms<T>(dx, dy, dz, f, h, nu, g, ri);
+                const T d[3] = {dx, dy, dz};
+                for (int c = 0; c < 3; c++) {
+                    a[c] += g[c] * z.ri + d[c] * z.c3;
+                    a[3 + c] += d[c] * z.c4;
+                    a[6 + c] += d[c] * z.c5;
+                    a[9 + c] -= d[c] * z.c1 + g[c] * z.st + f[c] * z.c3 + h[c] * z.c4 + nu[c] * z.c5;
+                }
+            }
+            for (int c = 0; c < 12; c++) acc[c] += (double)a[c];
+        }
+        if (valid)
+            for (int c = 0; c < 12; c++) gnear[c * N + si] = acc[c];
+    }
+}
+
+// --------------------------------------------------- far, target side
+// Batch-major like k_far; the recurrence runs to P + 1 = p + 3 and the
+// level-(n-1) values alpha^k are kept in a second two-slot store.
+template <typename TR, typename TC>
+__global__ void __launch_bounds__(32)
+    k_far_adj_target(const double* __restrict__ ts, const double* __restrict__ gs, int64_t M,
+                     const Geo* __restrict__ geo, const double* __restrict__ invrho, const TC* __restrict__ ab, int p,
+                     const int64_t* __restrict__ far_off, const ListEntry* __restrict__ far_list,
+                     double* __restrict__ gt)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int lane = threadIdx.x & 31;
+    const int64_t nbatch = (M + kBatch - 1) / kBatch;
+    const int64_t b = blockIdx.x;
+    if (b >= nbatch) return;
+    const int P = p + 2, Q = P + 1;
+    const int C2 = ncoef(P);
+    TR* cs_q = reinterpret_cast<TR*>(smraw);  // parity of Q: levels Q, Q-2, ...
+    TR* cs_o = cs_q + (size_t)level_size(Q) * 32;
+    TC* as_p = reinterpret_cast<TC*>(cs_o + (size_t)level_size(P) * 32);  // parity of P
+    TC* as_o = as_p + (size_t)level_size(P) * 32;
+    const int64_t m = b * kBatch + lane;
+    const bool valid = m < M;
+    double x[3] = {0, 0, 0};
+    TC g[3] = {0, 0, 0};
+    if (valid)
+        for (int a = 0; a < 3; a++) {
+            x[a] = ts[a * M + m];
+            g[a] = (TC)gs[a * M + m];
+        }
+    double G[3] = {0, 0, 0};
+    for (int64_t e = far_off[b]; e < far_off[b + 1]; e++) {
+        const ListEntry le = far_list[e];
+        const bool in = (le.mask >> lane) & 1u;
+        const Geo gc = geo[le.node];
+        const double ir = invrho[le.node];
+        const double d0 = (x[0] - gc.x) * ir, d1 = (x[1] - gc.y) * ir, d2 = (x[2] - gc.z) * ir;
+        double R2 = d0 * d0 + d1 * d1 + d2 * d2;
+        if (!in) R2 = 1.0;
+        const double iR = rsqrt(R2);
+        const TR w0 = (TR)(d0 * iR), w1 = (TR)(d1 * iR), w2 = (TR)(d2 * iR);
+        const TC dd[3] = {(TC)d0, (TC)d1, (TC)d2};
+        const TC* __restrict__ tab = ab + (int64_t)le.node * C2 * 12;
+        TC scale = (TC)iR;
+        TC Gl[3];
+        {  // level 0: c^0 = 1
+            const TC* t = tab;
+            TC v[3], beta[3];
+            for (int i = 0; i < 3; i++) v[i] = t[i] + dd[0] * t[3 + 3 * i] + dd[1] * t[4 + 3 * i] + dd[2] * t[5 + 3 * i];
+            for (int l = 0; l < 3; l++) beta[l] = g[0] * t[3 + l] + g[1] * t[6 + l] + g[2] * t[9 + l];
+            (((0 ^ P) & 1) ? as_o : as_p)[lane] = g[0] * v[0] + g[1] * v[1] + g[2] * v[2];
+            (((0 ^ Q) & 1) ? cs_o : cs_q)[lane] = (TR)1;
+            for (int l = 0; l < 3; l++) Gl[l] = scale * beta[l];
+        }
+        for (int n = 1; n <= Q; n++) {
+            const TR kap = (TR)c_lev.kappa[n];
+            scale *= (TC)(c_lev.ratio[n] * iR);
+            TR* Rn = ((n ^ Q) & 1) ? cs_o : cs_q;
+            const TR* R1 = ((n ^ Q) & 1) ? cs_q : cs_o;
+            TC* An = ((n ^ P) & 1) ? as_o : as_p;
+            const TC* A1 = ((n ^ P) & 1) ? as_p : as_o;
+            const TC* tl = tab + (int64_t)ncoef(n - 1) * 12;
+            TC acc1[3] = {0, 0, 0}, acc2[3] = {0, 0, 0};
+            for (int a = n; a >= 0; a--) {
+                const int k1 = n - a;
+                const int base = a * (a + 1) / 2;
+                for (int k3 = a; k3 >= 0; k3--) {
+                    const int k2 = a - k3;
+                    const int pos = base + k3;
+                    const TR ck = coef<TR>(R1, Rn, pos, a, k1, k2, k3, w0, w1, w2, kap, lane);
+                    Rn[pos * 32 + lane] = ck;
+                    const TC cc = to_tc<TR, TC>(ck);
+                    if (k1 >= 1) acc2[0] += cc * (TC)k1 * A1[pos * 32 + lane];
+                    if (k2 >= 1) acc2[1] += cc * (TC)k2 * A1[(pos - a) * 32 + lane];
+                    if (k3 >= 1) acc2[2] += cc * (TC)k3 * A1[(pos - a - 1) * 32 + lane];
+                    if (n <= P) {
+                        const TC* t = tl + pos * 12;
+                        TC v[3];
+                        for (int i = 0; i < 3; i++)
+                            v[i] = t[i] + dd[0] * t[3 + 3 * i] + dd[1] * t[4 + 3 * i] + dd[2] * t[5 + 3 * i];
+                        An[pos * 32 + lane] = g[0] * v[0] + g[1] * v[1] + g[2] * v[2];
+                        for (int l = 0; l < 3; l++) acc1[l] += cc * (g[0] * t[3 + l] + g[1] * t[6 + l] + g[2] * t[9 + l]);
+                    }
+                }
+            }
+            for (int l = 0; l < 3; l++) Gl[l] += scale * (acc1[l] - acc2[l]);
+        }
+        if (in)
+            for (int l = 0; l < 3; l++) G[l] += ir * (double)Gl[l];
+    }
+    if (valid)
+        for (int l = 0; l < 3; l++) gt[l * M + m] = G[l];
+}
+
+// --------------------------------------------------- far, source side
+// Cluster-major over the far entries sorted by cluster; a warp takes `chunk`
+// consecutive sorted entries.  Per entry the lanes are the batch's targets
+// (g = 0 on lanes outside the mask, so they add nothing).  After each level
+// the scaled coefficients s_n c^k of all lanes sit in a padded buffer and
+// each lane sums, for its own positions, over the 32 targets into the
+// warp's accumulators [coefficient][12]; the accumulators are flushed to the
+// cluster's FP64 adjoint tables with atomics when the cluster changes.
+template <typename TR, typename TC>
+__global__ void __launch_bounds__(32)
+    k_far_adj_source(const double* __restrict__ ts, const double* __restrict__ gs, int64_t M,
+                     const Geo* __restrict__ geo, const double* __restrict__ invrho, int p,
+                     const uint64_t* __restrict__ skeys, const int32_t* __restrict__ sidx,
+                     const ListEntry* __restrict__ far_list, const int32_t* __restrict__ ebatch, int64_t nent,
+                     int chunk, double* __restrict__ abar)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int lane = threadIdx.x & 31;
+    const int64_t j0 = (int64_t)blockIdx.x * chunk;
+    if (j0 >= nent) return;
+    const int64_t j1 = min(nent, j0 + chunk);
+    const int P = p + 2;
+    const int C2 = ncoef(P);
+    const int LSP = level_size(P);
+    TR* cs_p = reinterpret_cast<TR*>(smraw);  // parity of P
+    TR* cs_o = cs_p + (size_t)LSP * 32;
+    TC* sc = reinterpret_cast<TC*>(cs_o + (size_t)level_size(P - 1) * 32);  // [LSP][33]
+    TC* gb = sc + (size_t)LSP * 33;                                           // [32][12]
+    TC* acc = gb + 32 * 12;                                                   // [C2][12]
+    int64_t cur = -1;
+    for (int q = lane; q < C2 * 12; q += 32) acc[q] = (TC)0;
+    for (int64_t j = j0; j < j1; j++) {
+        const int64_t node = (int64_t)skeys[j];
+        if (node != cur) {
+            __syncwarp();
+            if (cur >= 0)
+                for (int q = lane; q < C2 * 12; q += 32) {
+                    atomicAdd(&abar[cur * C2 * 12 + q], (double)acc[q]);
+                    acc[q] = (TC)0;
+                }
+            cur = node;
+            __syncwarp();
+        }
+        const int32_t e = sidx[j];
+        const unsigned mask = far_list[e].mask;
+        const int64_t m = (int64_t)ebatch[e] * kBatch + lane;
+        const bool in = (mask >> lane) & 1u;
+        double x[3] = {0, 0, 0};
+        TC g[3] = {0, 0, 0};
+        if (in)
+            for (int a = 0; a < 3; a++) {
+                x[a] = ts[a * M + m];
+                g[a] = (TC)gs[a * M + m];
+            }
+        const Geo gc = geo[node];
+        const double ir = invrho[node];
+        const double d0 = (x[0] - gc.x) * ir, d1 = (x[1] - gc.y) * ir, d2 = (x[2] - gc.z) * ir;
+        double R2 = d0 * d0 + d1 * d1 + d2 * d2;
+        if (!in) R2 = 1.0;
+        const double iR = rsqrt(R2);
+        const TR w0 = (TR)(d0 * iR), w1 = (TR)(d1 * iR), w2 = (TR)(d2 * iR);
+        const TC dd[3] = {(TC)d0, (TC)d1, (TC)d2};
+        TC scale = (TC)iR;
+        for (int i = 0; i < 3; i++) {
+            gb[lane * 12 + i] = g[i];
+            for (int l = 0; l < 3; l++) gb[lane * 12 + 3 + 3 * i + l] = g[i] * dd[l];
+        }
+        (((0 ^ P) & 1) ? cs_o : cs_p)[lane] = (TR)1;
+        sc[lane] = scale;  // position 0, column lane
+        for (int n = 0; n <= P; n++) {
+            if (n > 0) {
+                const TR kap = (TR)c_lev.kappa[n];
+                scale *= (TC)(c_lev.ratio[n] * iR);
+                TR* Rn = ((n ^ P) & 1) ? cs_o : cs_p;
+                const TR* R1 = ((n ^ P) & 1) ? cs_p : cs_o;
+                for (int a = n; a >= 0; a--) {
+                    const int k1 = n - a;
+                    const int base = a * (a + 1) / 2;
+                    for (int k3 = a; k3 >= 0; k3--) {
+                        const int pos = base + k3;
+                        const TR ck = coef<TR>(R1, Rn, pos, a, k1, a - k3, k3, w0, w1, w2, kap, lane);
+                        Rn[pos * 32 + lane] = ck;
+                        sc[pos * 33 + lane] = scale * to_tc<TR, TC>(ck);
+                    }
+                }
+            }
+            __syncwarp();
+            const int ls = level_size(n);
+            TC* accl = acc + (size_t)(n > 0 ? ncoef(n - 1) : 0) * 12;
+            for (int pos = lane; pos < ls; pos += 32) {
+                TC r[12];
+                for (int c = 0; c < 12; c++) r[c] = (TC)0;
+                for (int t = 0; t < 32; t++) {
+                    const TC v = sc[pos * 33 + t];
+                    for (int c = 0; c < 12; c++) r[c] += v * gb[t * 12 + c];
+                }
+                for (int c = 0; c < 12; c++) accl[pos * 12 + c] += r[c];
+            }
+            __syncwarp();
+        }
+    }
+    __syncwarp();
+    if (cur >= 0)
+        for (int q = lane; q < C2 * 12; q += 32) atomicAdd(&abar[cur * C2 * 12 + q], (double)acc[q]);
+}
+
+// ------------------------------------------- adjoint moments (table transpose)
+// One block per cluster; thread 0 scatters the transpose of the table map of
+// tc_moments.cu (k_ab_tables) into shared memory, so each moment gathers
+//   Lambda_c^k = sum over the table entries that read M_c^k of (entry
+//   coefficient) x (scaled adjoint table entry).
+__global__ void k_lambda(const double* __restrict__ abar, const double* __restrict__ invrho, int p,
+                         double* __restrict__ lam)
+{
+    extern __shared__ double ls[];
+    const int64_t node = blockIdx.x;
+    const int C = ncoef(p), C2 = ncoef(p + 2);
+    for (int q = threadIdx.x; q < 12 * C; q += blockDim.x) ls[q] = 0.0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const double ir = invrho[node];
+        const double third = 1.0 / 3.0;
+        auto add = [&](int c, int k1, int k2, int k3, double v) {
+            if (k1 < 0 || k2 < 0 || k3 < 0 || k1 + k2 + k3 > p) return;
+            ls[c * C + flat_index(k1, k2, k3)] += v;
+        };
+        for (int kidx = 0; kidx < C2; kidx++) {
+            int kp[3];
+            unflatten(kidx, kp[0], kp[1], kp[2]);
+            const int n = kp[0] + kp[1] + kp[2];
+            double sB = 1.0;
+            for (int q = 0; q < n; q++) sB *= ir;
+            const double sA = sB * ir;
+            const double* ab = abar + (node * C2 + kidx) * 12;
+            for (int i = 0; i < 3; i++) {
+                const int ei[3] = {i == 0, i == 1, i == 2};
+                const double Ab = ab[i] * sA;
+                if (Ab != 0.0) {
+                    add(i, kp[0], kp[1], kp[2], Ab);
+                    for (int j = 0; j < 3; j++) {
+                        const int ej[3] = {j == 0, j == 1, j == 2};
+                        add(j, kp[0] - ei[0] + ej[0], kp[1] - ei[1] + ej[1], kp[2] - ei[2] + ej[2], -kp[i] * Ab);
+                    }
+                    for (int l = 0; l < 3; l++) {
+                        const int el[3] = {l == 0, l == 1, l == 2};
+                        add(3 + 3 * i + l, kp[0] - el[0], kp[1] - el[1], kp[2] - el[2], third * kp[l] * Ab);
+                    }
+                    for (int j = 0; j < 3; j++) {
+                        const int ej[3] = {j == 0, j == 1, j == 2};
+                        const double cj = (double)(kp[i] - (i == j)) * kp[j];
+                        if (cj == 0.0) continue;
+                        for (int l = 0; l < 3; l++) {
+                            const int el[3] = {l == 0, l == 1, l == 2};
+                            add(3 + 3 * j + l, kp[0] - ei[0] - ej[0] + el[0], kp[1] - ei[1] - ej[1] + el[1],
+                                kp[2] - ei[2] - ej[2] + el[2], -third * cj * Ab);
+                        }
+                    }
+                }
+                for (int l = 0; l < 3; l++) {
+                    const double Bb = ab[3 + 3 * i + l] * sB;
+                    if (Bb == 0.0) continue;
+                    add(l, kp[0] - ei[0], kp[1] - ei[1], kp[2] - ei[2], kp[i] * Bb);
+                    for (int j = 0; j < 3; j++) {
+                        const int ej[3] = {j == 0, j == 1, j == 2};
+                        const double cj = (double)kp[i] * (kp[j] - (i == j));
+                        if (cj == 0.0) continue;
+                        add(3 + 3 * j + l, kp[0] - ei[0] - ej[0], kp[1] - ei[1] - ej[1], kp[2] - ei[2] - ej[2],
+                            third * cj * Bb);
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < 12 * C; q += blockDim.x) lam[node * 12 * C + q] = ls[q];
+}
+
+// Pascal's triangle up to row kPMax.
+struct Binom {
+    double v[kPMax + 1][kPMax + 1];
+};
+__host__ __device__ constexpr Binom make_binom()
+{
+    Binom b{};
+    for (int n = 0; n <= kPMax; n++) {
+        b.v[n][0] = 1.0;
+        for (int k = 1; k <= n; k++) b.v[n][k] = b.v[n - 1][k - 1] + (k <= n - 1 ? b.v[n - 1][k] : 0.0);
+    }
+    return b;
+}
+__constant__ Binom c_binom = make_binom();
+
+// Downward pass: the adjoint polynomial of the parent, sum_k L^k (y - y_P)^k,
+// re-expanded about the child centre (y - y_P = (y - y_C) + s, s = y_C - y_P):
+//   L'^j = sum_{k >= j} binom(k, j) s^(k-j) L^k,  added to the child's own.
+__global__ void k_l2l(const int4* __restrict__ info, const Geo* __restrict__ geo, int64_t lb, int64_t le, int p,
+                      const double* __restrict__ lam, double* __restrict__ lamacc)
+{
+    __shared__ double sp[3][kPMax + 1];
+    const int64_t node = lb + blockIdx.x;
+    if (node >= le) return;
+    const int C = ncoef(p);
+    const int64_t parent = info[node].y;
+    if (parent < 0) {
+        for (int q = threadIdx.x; q < 12 * C; q += blockDim.x) lamacc[node * 12 * C + q] = lam[node * 12 * C + q];
+        return;
+    }
+    const Geo gc = geo[node], gp = geo[parent];
+    if (threadIdx.x < 3) {
+        const double s = threadIdx.x == 0 ? gc.x - gp.x : (threadIdx.x == 1 ? gc.y - gp.y : gc.z - gp.z);
+        double v = 1.0;
+        sp[threadIdx.x][0] = 1.0;
+        for (int k = 1; k <= p; k++) {
+            v *= s;
+            sp[threadIdx.x][k] = v;
+        }
+    }
+    __syncthreads();
+    const double* lp = lamacc + parent * 12 * C;
+    for (int jdx = threadIdx.x; jdx < C; jdx += blockDim.x) {
+        int j1, j2, j3;
+        unflatten(jdx, j1, j2, j3);
+        double acc[12];
+        for (int c = 0; c < 12; c++) acc[c] = lam[(node * 12 + c) * C + jdx];
+        for (int k1 = j1; k1 <= p; k1++) {
+            const double w1 = c_binom.v[k1][j1] * sp[0][k1 - j1];
+            for (int k2 = j2; k1 + k2 <= p; k2++) {
+                const double w12 = w1 * c_binom.v[k2][j2] * sp[1][k2 - j2];
+                for (int k3 = j3; k1 + k2 + k3 <= p; k3++) {
+                    const double wk = w12 * c_binom.v[k3][j3] * sp[2][k3 - j3];
+                    const int kidx = flat_index(k1, k2, k3);
+                    for (int c = 0; c < 12; c++) acc[c] = fma(wk, lp[c * C + kidx], acc[c]);
+                }
+            }
+        }
+        for (int c = 0; c < 12; c++) lamacc[(node * 12 + c) * C + jdx] = acc[c];
+    }
+}
+
+// Per particle of a leaf: Q_c(y) = sum_k L_c^k (y - y_L)^k and
+// grad_y sum_c w_c Q_c(y); writes dL/df, dL/dh, dL/dnu, dL/dx (far, source side).
+__global__ void k_leaf_eval(const int4* __restrict__ topo, const Geo* __restrict__ geo, const double* __restrict__ xs,
+                            const double* __restrict__ ws, int64_t N, int p, const double* __restrict__ lamacc,
+                            double* __restrict__ gfar)
+{
+    extern __shared__ double ll[];
+    const int64_t node = blockIdx.x;
+    const int4 t = topo[node];
+    if (t.w != 0) return;
+    const int C = ncoef(p);
+    for (int q = threadIdx.x; q < 12 * C; q += blockDim.x) ll[q] = lamacc[node * 12 * C + q];
+    __syncthreads();
+    const Geo gc = geo[node];
+    for (int i = t.x + threadIdx.x; i < t.x + t.y; i += blockDim.x) {
+        const double dl[3] = {xs[i] - gc.x, xs[N + i] - gc.y, xs[2 * N + i] - gc.z};
+        double w[12];
+        for (int c = 0; c < 3; c++) w[c] = ws[c * N + i];
+        for (int j = 0; j < 3; j++)
+            for (int l = 0; l < 3; l++) w[3 + 3 * j + l] = ws[(3 + j) * N + i] * ws[(6 + l) * N + i];
+        double Qv[12], gx[3] = {0, 0, 0};
+        for (int c = 0; c < 12; c++) Qv[c] = 0.0;
+        double p1 = 1.0, p1m = 0.0;
+        for (int k1 = 0; k1 <= p; k1++) {
+            double p2 = 1.0, p2m = 0.0;
+            for (int k2 = 0; k1 + k2 <= p; k2++) {
+                double p3 = 1.0, p3m = 0.0;
+                for (int k3 = 0; k1 + k2 + k3 <= p; k3++) {
+                    const int kidx = flat_index(k1, k2, k3);
+                    const double mono = p1 * p2 * p3;
+                    double R = 0.0;
+                    for (int c = 0; c < 12; c++) {
+                        const double L = ll[c * C + kidx];
+                        Qv[c] = fma(L, mono, Qv[c]);
+                        R = fma(w[c], L, R);
+                    }
+                    gx[0] = fma(R, k1 * p1m * p2 * p3, gx[0]);
+                    gx[1] = fma(R, k2 * p1 * p2m * p3, gx[1]);
+                    gx[2] = fma(R, k3 * p1 * p2 * p3m, gx[2]);
+                    p3m = p3;
+                    p3 *= dl[2];
+                }
+                p2m = p2;
+                p2 *= dl[1];
+            }
+            p1m = p1;
+            p1 *= dl[0];
+        }
+        for (int a = 0; a < 3; a++) {
+            gfar[a * N + i] = Qv[a];
+            double gh = 0.0, gn = 0.0;
+            for (int l = 0; l < 3; l++) gh += ws[(6 + l) * N + i] * Qv[3 + 3 * a + l];
+            for (int j = 0; j < 3; j++) gn += ws[(3 + j) * N + i] * Qv[3 + 3 * j + a];
+            gfar[(3 + a) * N + i] = gh;
+            gfar[(6 + a) * N + i] = gn;
+            gfar[(9 + a) * N + i] = gx[a];
+        }
+    }
+}
+
+// Sum the parts and scatter from Morton order to the caller's order.
+__global__ void k_adj_final(const double* __restrict__ gfar, const double* __restrict__ gnear,
+                            const double* __restrict__ gt, const int32_t* __restrict__ perm, int64_t N, int self,
+                            double* __restrict__ gf, double* __restrict__ gh, double* __restrict__ gnu,
+                            double* __restrict__ gx)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int64_t d = perm[i];
+    for (int a = 0; a < 3; a++) {
+        if (gf) gf[a * N + d] = gfar[a * N + i] + gnear[a * N + i];
+        if (gh) gh[a * N + d] = gfar[(3 + a) * N + i] + gnear[(3 + a) * N + i];
+        if (gnu) gnu[a * N + d] = gfar[(6 + a) * N + i] + gnear[(6 + a) * N + i];
+        if (gx) gx[a * N + d] = gfar[(9 + a) * N + i] + gnear[(9 + a) * N + i] + (self ? gt[a * N + i] : 0.0);
+    }
+}
+
+__global__ void k_scatter3(const double* __restrict__ src, const int32_t* __restrict__ perm, int64_t M,
+                           double* __restrict__ dst)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    const int64_t d = perm[i];
+    for (int a = 0; a < 3; a++) dst[a * M + d] = src[a * M + i];
+}
+
+constexpr int kFarAdjChunk = 48;  // sorted far entries per warp in the cluster-major pass
+
+template <typename TR, typename TC>
+cudaError_t run_far_adj(tc_ctx* ctx, const double* ts, int64_t M, int p, cudaStream_t s)
+{
+    const int P = p + 2, Q = P + 1;
+    const TC* ab = (const TC*)(ctx->precision == TC_FP64 ? ctx->ab64.p : ctx->ab32.p);
+    const int64_t nbatch = (M + kBatch - 1) / kBatch;
+    size_t sm1 = (size_t)(level_size(Q) + level_size(P)) * 32 * sizeof(TR) +
+                 (size_t)(level_size(P) + level_size(P - 1)) * 32 * sizeof(TC);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_far_adj_target<TR, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
+    if (e != cudaSuccess) return e;
+    k_far_adj_target<TR, TC><<<(unsigned)nbatch, 32, sm1, s>>>(
+        ts, ptr<double>(ctx->adj_gs), M, ptr<Geo>(ctx->node_geo), ptr<double>(ctx->node_invrho), ab, p,
+        ptr<int64_t>(ctx->far_off), ptr<ListEntry>(ctx->far_list), ptr<double>(ctx->adj_gt));
+    note_launch();
+    const int64_t nent = ctx->far_entries;
+    if (nent > 0) {
+        size_t sm2 = (size_t)(level_size(P) + level_size(P - 1)) * 32 * sizeof(TR) +
+                     ((size_t)level_size(P) * 33 + 32 * 12 + (size_t)ncoef(P) * 12) * sizeof(TC);
+        e = cudaFuncSetAttribute(k_far_adj_source<TR, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
+        if (e != cudaSuccess) return e;
+        k_far_adj_source<TR, TC><<<grid_for(nent, kFarAdjChunk), 32, sm2, s>>>(
+            ts, ptr<double>(ctx->adj_gs), M, ptr<Geo>(ctx->node_geo), ptr<double>(ctx->node_invrho), p,
+            ptr<uint64_t>(ctx->adj_fkeys), ptr<int32_t>(ctx->adj_fidx), ptr<ListEntry>(ctx->far_list),
+            ptr<int32_t>(ctx->adj_febatch), nent, kFarAdjChunk, ptr<double>(ctx->adj_abar));
+        note_launch();
+    }
+    return cudaGetLastError();
+}
+
+// Sort one of the forward lists by cluster: keys/idx sorted, batch per entry.
+cudaError_t sort_entries(const ListEntry* list, int64_t n, const int64_t* off, int64_t nbatch, int64_t nnodes,
+                         DevBuf& keys, DevBuf& keys_alt, DevBuf& idx, DevBuf& idx_alt, DevBuf& eb, DevBuf& hist,
+                         cudaStream_t s)
+{
+    cudaError_t e;
+    if ((e = ensure(keys, (size_t)n * 8)) != cudaSuccess) return e;
+    if ((e = ensure(keys_alt, (size_t)n * 8)) != cudaSuccess) return e;
+    if ((e = ensure(idx, (size_t)n * 4)) != cudaSuccess) return e;
+    if ((e = ensure(idx_alt, (size_t)n * 4)) != cudaSuccess) return e;
+    if ((e = ensure(eb, (size_t)n * 4)) != cudaSuccess) return e;
+    if ((e = ensure(hist, (size_t)256 * radix_blocks(n) * 4)) != cudaSuccess) return e;
+    if (n == 0) return cudaSuccess;
+    k_entry_keys<<<grid_for(n, 256), 256, 0, s>>>(list, n, ptr<uint64_t>(keys), ptr<int32_t>(idx));
+    note_launch();
+    int bits = 1;
+    while (bits < 32 && ((int64_t)1 << bits) < nnodes) bits++;
+    e = radix_sort_bits(ptr<uint64_t>(keys), ptr<int32_t>(idx), ptr<uint64_t>(keys_alt), ptr<int32_t>(idx_alt),
+                        ptr<uint32_t>(hist), n, bits, s);
+    if (e != cudaSuccess) return e;
+    k_entry_batch<<<grid_for(n, 256), 256, 0, s>>>(off, nbatch, n, ptr<int32_t>(eb));
+    note_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace
+}  // namespace tc
+
+using namespace tc;
+
+#define TC_CK(call, where)                                       \
+    do {                                                         \
+        cudaError_t e_ = (call);                                 \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where); \
+    } while (0)
+
+extern "C" tc_status tc_adjoint(tc_ctx* ctx, const double* g, double* grad_f, double* grad_h, double* grad_nu,
+                                double* grad_x, double* grad_t)
+{
+    if (!ctx) return fail(nullptr, TC_EINVAL, "tc_adjoint: ctx is NULL");
+    if (!ctx->have_eval) return fail(ctx, TC_ESTATE, "tc_adjoint: call tc_eval first");
+    if (!g) return fail(ctx, TC_EINVAL, "tc_adjoint: g is NULL");
+    if (ctx->eval_self && grad_t)
+        return fail(ctx, TC_EINVAL, "tc_adjoint: grad_t must be NULL when targets are the sources (use grad_x)");
+    cudaStream_t s = ctx->stream;
+    const int64_t N = ctx->N, M = ctx->M, nnodes = ctx->nnodes;
+    const int p = ctx->ab_p;
+    const int C = ncoef(p), C2 = ncoef(p + 2);
+    const int64_t nbatch = (M + kBatch - 1) / kBatch;
+    const int32_t* tperm = ctx->eval_self ? ptr<int32_t>(ctx->perm) : ptr<int32_t>(ctx->tperm);
+    const double* ts = ctx->eval_self ? ptr<double>(ctx->xs) : ptr<double>(ctx->ts);
+
+    TC_CK(ensure(ctx->adj_gs, (size_t)3 * M * 8), "alloc adjoint");
+    TC_CK(ensure(ctx->adj_gt, (size_t)3 * M * 8), "alloc adjoint");
+    TC_CK(ensure(ctx->adj_abar, (size_t)nnodes * C2 * 12 * 8), "alloc adjoint");
+    TC_CK(ensure(ctx->adj_lam, (size_t)nnodes * 12 * C * 8), "alloc adjoint");
+    TC_CK(ensure(ctx->adj_lamacc, (size_t)nnodes * 12 * C * 8), "alloc adjoint");
+    TC_CK(ensure(ctx->adj_gfar, (size_t)12 * N * 8), "alloc adjoint");
+    TC_CK(ensure(ctx->adj_gnear, (size_t)12 * N * 8), "alloc adjoint");
+
+    if (!ctx->adj_lists_ready) {
+        TC_CK(sort_entries(ptr<ListEntry>(ctx->far_list), ctx->far_entries, ptr<int64_t>(ctx->far_off), nbatch, nnodes,
+                           ctx->adj_fkeys, ctx->adj_fkeys_alt, ctx->adj_fidx, ctx->adj_fidx_alt, ctx->adj_febatch,
+                           ctx->adj_hist, s),
+              "sort far entries");
+        TC_CK(sort_entries(ptr<ListEntry>(ctx->near_list), ctx->near_entries, ptr<int64_t>(ctx->near_off), nbatch,
+                           nnodes, ctx->adj_nkeys, ctx->adj_nkeys_alt, ctx->adj_nidx, ctx->adj_nidx_alt,
+                           ctx->adj_nebatch, ctx->adj_hist, s),
+              "sort near entries");
+        ctx->adj_lists_ready = 1;
+    }
+    k_gather_g<<<grid_for(M, 256), 256, 0, s>>>(g, tperm, M, ptr<double>(ctx->adj_gs));
+    note_launch();
+    TC_CK(cudaMemsetAsync(ctx->adj_abar.p, 0, (size_t)nnodes * C2 * 12 * 8, s), "zero adjoint tables");
+
+    // far field: target side (writes adj_gt) and source side (adjoint tables)
+    cudaError_t e;
+    if (ctx->precision == TC_FP64)
+        e = run_far_adj<double, double>(ctx, ts, M, p, s);
+    else if (p >= 8)
+        e = run_far_adj<double, float>(ctx, ts, M, p, s);
+    else
+        e = run_far_adj<float, float>(ctx, ts, M, p, s);
+    TC_CK(e, "far adjoint");
+
+    // near field: target side adds to adj_gt; source side writes adj_gnear
+    const unsigned ngrid = (unsigned)((nbatch + kNearAdjWarps - 1) / kNearAdjWarps);
+    if (ctx->precision == TC_FP64) {
+        k_near_adj_target<double><<<ngrid, kNearAdjWarps * 32, 0, s>>>(
+            ts, ptr<double>(ctx->adj_gs), M, ptr<int4>(ctx->node_topo), ptr<double>(ctx->xs), ptr<double>(ctx->ws), N,
+            ptr<int64_t>(ctx->near_off), ptr<ListEntry>(ctx->near_list), ptr<double>(ctx->adj_gt));
+        note_launch();
+        k_near_adj_source<double><<<(unsigned)nnodes, kNearAdjWarps * 32, 0, s>>>(
+            ts, ptr<double>(ctx->adj_gs), M, ptr<int4>(ctx->node_topo), ptr<double>(ctx->xs), ptr<double>(ctx->ws), N,
+            ptr<uint64_t>(ctx->adj_nkeys), ptr<int32_t>(ctx->adj_nidx), ptr<ListEntry>(ctx->near_list),
+            ptr<int32_t>(ctx->adj_nebatch), ctx->near_entries, ptr<double>(ctx->adj_gnear));
+        note_launch();
+    } else {
+        k_near_adj_target<float><<<ngrid, kNearAdjWarps * 32, 0, s>>>(
+            ts, ptr<double>(ctx->adj_gs), M, ptr<int4>(ctx->node_topo), ptr<double>(ctx->xs), ptr<double>(ctx->ws), N,
+            ptr<int64_t>(ctx->near_off), ptr<ListEntry>(ctx->near_list), ptr<double>(ctx->adj_gt));
+        note_launch();
+        k_near_adj_source<float><<<(unsigned)nnodes, kNearAdjWarps * 32, 0, s>>>(
+            ts, ptr<double>(ctx->adj_gs), M, ptr<int4>(ctx->node_topo), ptr<double>(ctx->xs), ptr<double>(ctx->ws), N,
+            ptr<uint64_t>(ctx->adj_nkeys), ptr<int32_t>(ctx->adj_nidx), ptr<ListEntry>(ctx->near_list),
+            ptr<int32_t>(ctx->adj_nebatch), ctx->near_entries, ptr<double>(ctx->adj_gnear));
+        note_launch();
+    }
+    TC_CK(cudaGetLastError(), "near adjoint");
+
+    // adjoint moments, downward pass, per-particle evaluation
+    size_t lsm = (size_t)12 * C * 8;
+    TC_CK(cudaFuncSetAttribute(k_lambda, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm), "lambda attr");
+    k_lambda<<<(unsigned)nnodes, 32, lsm, s>>>(ptr<double>(ctx->adj_abar), ptr<double>(ctx->node_invrho), p,
+                                              ptr<double>(ctx->adj_lam));
+    note_launch();
+    for (size_t L = 0; L + 1 < ctx->level_begin.size(); L++) {
+        const int64_t lb = ctx->level_begin[L], le = ctx->level_begin[L + 1];
+        if (le <= lb) continue;
+        k_l2l<<<(unsigned)(le - lb), 128, 0, s>>>(ptr<int4>(ctx->node_info), ptr<Geo>(ctx->node_geo), lb, le, p,
+                                                  ptr<double>(ctx->adj_lam), ptr<double>(ctx->adj_lamacc));
+        note_launch();
+    }
+    TC_CK(cudaFuncSetAttribute(k_leaf_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm), "leaf attr");
+    k_leaf_eval<<<(unsigned)nnodes, 128, lsm, s>>>(ptr<int4>(ctx->node_topo), ptr<Geo>(ctx->node_geo),
+                                                   ptr<double>(ctx->xs), ptr<double>(ctx->ws), N, p,
+                                                   ptr<double>(ctx->adj_lamacc), ptr<double>(ctx->adj_gfar));
+    note_launch();
+    k_adj_final<<<grid_for(N, 256), 256, 0, s>>>(ptr<double>(ctx->adj_gfar), ptr<double>(ctx->adj_gnear),
+                                                 ptr<double>(ctx->adj_gt), ptr<int32_t>(ctx->perm), N, ctx->eval_self,
+                                                 grad_f, grad_h, grad_nu, grad_x);
+    note_launch();
+    if (!ctx->eval_self && grad_t) {
+        k_scatter3<<<grid_for(M, 256), 256, 0, s>>>(ptr<double>(ctx->adj_gt), tperm, M, grad_t);
+        note_launch();
+    }
+    TC_CK(cudaGetLastError(), "adjoint");
+    return TC_OK;
+}

@@ -115,7 +115,10 @@ static void release_all(tc_ctx* c)
                       &c->split_off, &c->scan_tmp, &c->ws, &c->spack, &c->mom, &c->ab64, &c->ab32, &c->tkeys,
                       &c->tkeys_alt, &c->tperm, &c->tperm_alt, &c->ts, &c->nfar_e, &c->nnear_e,
                       &c->far_off, &c->near_off, &c->far_list, &c->near_list, &c->cnt_far, &c->cnt_near, &c->u_far,
-                      &c->u_near, &c->flags};
+                      &c->u_near, &c->flags, &c->adj_fkeys, &c->adj_fkeys_alt, &c->adj_fidx, &c->adj_fidx_alt,
+                      &c->adj_febatch, &c->adj_nkeys, &c->adj_nkeys_alt, &c->adj_nidx, &c->adj_nidx_alt,
+                      &c->adj_nebatch, &c->adj_hist, &c->adj_gs, &c->adj_gt, &c->adj_abar, &c->adj_lam,
+                      &c->adj_lamacc, &c->adj_gfar, &c->adj_gnear};
     for (DevBuf* b : bufs) release(*b);
 }
 
@@ -373,6 +376,7 @@ tc_status tc_eval(tc_ctx* ctx, const double* targets, int64_t M, double theta, i
     if (st != TC_OK) return st;
     cudaStream_t s = ctx->stream;
     ctx->have_eval = 0;
+    ctx->adj_lists_ready = 0;
     const double* ts;
     const int32_t* tperm;
     if (!targets) {
@@ -446,7 +450,8 @@ tc_status tc_eval(tc_ctx* ctx, const double* targets, int64_t M, double theta, i
     TC_CK(launch_finalize(ptr<double>(ctx->u_far), ptr<double>(ctx->u_near), tperm, M, u, s), "finalize");
     ph_end(ctx, TC_PH_FINAL);
     ctx->M = M;
-    ctx->stat_far = tot[0];
+    ctx->far_entries = tot[0];
+    ctx->near_entries = tot[1];
     ctx->have_eval = 1;
     return TC_OK;
 }
@@ -486,6 +491,23 @@ tc_status tc_stats(tc_ctx* ctx, int64_t* near_pairs, int64_t* far_interactions, 
     TC_CK(cudaStreamSynchronize(s), "stats sync");
     if (near_pairs) *near_pairs = h[0];
     if (far_interactions) *far_interactions = h[1];
+    return TC_OK;
+}
+
+tc_status tc_list_stats(tc_ctx* ctx, int64_t* far_entries, int64_t* near_entries, int64_t* near_entry_sources)
+{
+    if (!ctx) return fail(nullptr, TC_EINVAL, "tc_list_stats: ctx is NULL");
+    if (!ctx->have_eval) return fail(ctx, TC_ESTATE, "tc_list_stats: no evaluation yet");
+    if (far_entries) *far_entries = ctx->far_entries;
+    if (near_entries) *near_entries = ctx->near_entries;
+    if (near_entry_sources) {
+        int64_t* tmp = ptr<int64_t>(ctx->scan_tmp) + 2;
+        TC_CK(launch_sum_entry_sizes(ptr<ListEntry>(ctx->near_list), ctx->near_entries, ptr<int4>(ctx->node_topo), tmp,
+                                     ctx->stream),
+              "list stats");
+        TC_CK(cudaMemcpyAsync(near_entry_sources, tmp, 8, cudaMemcpyDeviceToHost, ctx->stream), "list stats copy");
+        TC_CK(cudaStreamSynchronize(ctx->stream), "list stats sync");
+    }
     return TC_OK;
 }
 

@@ -404,11 +404,22 @@ int radix_blocks(int64_t N) { return (int)((N + kRadixTile - 1) / kRadixTile); }
 cudaError_t radix_sort(uint64_t* keys, int32_t* vals, uint64_t* keys_alt, int32_t* vals_alt, uint32_t* hist,
                        int64_t N, cudaStream_t s)
 {
+    return radix_sort_bits(keys, vals, keys_alt, vals_alt, hist, N, 64, s);
+}
+
+// Sort on the low `bits` key bits only (an even number of 8-bit passes, so
+// the result always ends in keys/vals).
+cudaError_t radix_sort_bits(uint64_t* keys, int32_t* vals, uint64_t* keys_alt, int32_t* vals_alt, uint32_t* hist,
+                            int64_t N, int bits, cudaStream_t s)
+{
     int nblk = radix_blocks(N);
     if (nblk < 1) return cudaSuccess;
+    int passes = (bits + 7) / 8;
+    passes += passes & 1;
+    if (passes > 8) passes = 8;
     uint64_t *ki = keys, *ko = keys_alt;
     int32_t *vi = vals, *vo = vals_alt;
-    for (int pass = 0; pass < 8; pass++) {
+    for (int pass = 0; pass < passes; pass++) {
         int shift = 8 * pass;
         k_radix_hist<<<nblk, kRadixThreads, 0, s>>>(ki, N, shift, hist);
         note_launch();
@@ -423,7 +434,7 @@ cudaError_t radix_sort(uint64_t* keys, int32_t* vals, uint64_t* keys_alt, int32_
         vi = vo;
         vo = tv;
     }
-    return cudaGetLastError();  // 8 passes: result is back in keys/vals
+    return cudaGetLastError();  // even number of passes: result is back in keys/vals
 }
 
 cudaError_t launch_gather3(const double* src, const int32_t* perm, int64_t N, double* dst, cudaStream_t s)

@@ -107,8 +107,18 @@ struct tc_ctx {
     tc::DevBuf cnt_far, cnt_near;       // per sorted target counts (int64)
     tc::DevBuf u_far, u_near;           // 3*M FP64 sorted order
     tc::DevBuf flags;                   // int32 device error flags
-    int64_t stat_near_pairs = 0, stat_far = 0;
+    int64_t far_entries = 0, near_entries = 0;  // list sizes of the last tc_eval
     int have_eval = 0;
+
+    // ---- adjoint (tc_adjoint)
+    tc::DevBuf adj_fkeys, adj_fkeys_alt, adj_fidx, adj_fidx_alt, adj_febatch;  // far entries sorted by cluster
+    tc::DevBuf adj_nkeys, adj_nkeys_alt, adj_nidx, adj_nidx_alt, adj_nebatch;  // near entries sorted by leaf
+    tc::DevBuf adj_hist;
+    tc::DevBuf adj_gs, adj_gt;            // 3*M sorted g and target-position gradient
+    tc::DevBuf adj_abar;                  // FP64 [node][ncoef(p+2)][12] adjoint of the tables
+    tc::DevBuf adj_lam, adj_lamacc;       // FP64 [node][12][ncoef(p)] adjoint moments, accumulated down
+    tc::DevBuf adj_gfar, adj_gnear;       // 12*N FP64 sorted: d/df, d/dh, d/dnu, d/dx
+    int adj_lists_ready = 0;              // sorted lists match the last tc_eval
 
     // ---- phase timing (tc_profile / tc_phase_times)
     int profile = 0;
@@ -141,6 +151,8 @@ cudaError_t launch_keys(const double* x, int64_t N, const double* root, uint64_t
 int radix_blocks(int64_t N);
 cudaError_t radix_sort(uint64_t* keys, int32_t* vals, uint64_t* keys_alt, int32_t* vals_alt, uint32_t* hist,
                        int64_t N, cudaStream_t s);
+cudaError_t radix_sort_bits(uint64_t* keys, int32_t* vals, uint64_t* keys_alt, int32_t* vals_alt, uint32_t* hist,
+                            int64_t N, int bits, cudaStream_t s);
 cudaError_t launch_gather3(const double* src, const int32_t* perm, int64_t N, double* dst, cudaStream_t s);
 cudaError_t launch_init_root(int4* topo, int4* info, uint64_t* nkey, int64_t N, cudaStream_t s);
 cudaError_t launch_split_count(const int4* topo, const int4* info, const uint64_t* keys, int64_t lb, int64_t le,
@@ -170,6 +182,7 @@ cudaError_t launch_lists(const double* ts, int64_t M, const int4* topo, const Ge
 cudaError_t launch_scan_i32_to_i64(const int32_t* in, int64_t* out_excl, int64_t n, int64_t* total,
                                    cudaStream_t s);
 cudaError_t launch_sum_i64(const int64_t* in, int64_t n, int64_t* out, cudaStream_t s);
+cudaError_t launch_sum_entry_sizes(const ListEntry* list, int64_t n, const int4* topo, int64_t* out, cudaStream_t s);
 
 // tc_far.cu
 cudaError_t launch_far(int precision, const double* ts, int64_t M, const Geo* geo, const double* invrho,

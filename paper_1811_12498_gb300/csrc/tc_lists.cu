@@ -131,7 +131,30 @@ __global__ void k_sum_i64(const int64_t* __restrict__ in, int64_t n, int64_t* __
     if (threadIdx.x == 0) *out = part[0];
 }
 
+// sum over list entries of the entry's cluster size
+__global__ void k_sum_entry_sizes(const ListEntry* __restrict__ list, int64_t n, const int4* __restrict__ topo,
+                                  int64_t* __restrict__ out)
+{
+    __shared__ int64_t part[1024];
+    int64_t s = 0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += topo[list[i].node].y;
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) part[threadIdx.x] += part[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = part[0];
+}
+
 }  // namespace
+
+cudaError_t launch_sum_entry_sizes(const ListEntry* list, int64_t n, const int4* topo, int64_t* out, cudaStream_t s)
+{
+    k_sum_entry_sizes<<<1, 1024, 0, s>>>(list, n, topo, out);
+    note_launch();
+    return cudaGetLastError();
+}
 
 cudaError_t launch_lists(const double* ts, int64_t M, const int4* topo, const Geo* geo, double theta,
                          int write, int32_t* nfar_e, int32_t* nnear_e, const int64_t* far_off,

@@ -1,0 +1,184 @@
+"""The adjoint (tc_adjoint) against the FP64 oracle.
+
+L = sum_m g^m . u(x^m) with the structure of the last evaluation frozen.
+* Weights: u is linear in f (and in h for fixed nu, and in nu for fixed h),
+  so <dL/df, phi> must equal sum_m g^m . u_oracle(f = phi, h = 0) exactly up
+  to rounding (and likewise for h and nu).  Tolerances: FP64 path 1e-10,
+  mixed path 1e-6, relative to |dL/df| |phi|.
+* Positions: central finite differences (step 1e-6, FP64) of the oracle's
+  frozen-structure map (decisions at the original positions, moments and sums
+  at the moved ones) on sampled entries; relative L2 over the samples, with
+  each entry's error floored at the RMS of the gradient: <= 1e-5.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1811_12498_gb300 import api, inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL_W = {"fp64": 1e-10, "mixed": 1e-6}
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(np.asarray(a, dtype=np.float64).T)).cuda()
+
+
+def host(t):
+    return t.cpu().numpy().T
+
+
+def _adjoint(prec, x, f, h, nu, g, N0, p, theta, targets=None, shrink=True):
+    tc = api.Treecode(prec, shrink).build(dev(x), N0).moments(dev(f), dev(h), dev(nu), p)
+    tc.eval(theta, p, None if targets is None else dev(targets))
+    gr = tc.adjoint(dev(g), t=targets is not None)
+    tc.sync()
+    out = {k: host(v) for k, v in gr.items()}
+    tc.close()
+    return out
+
+
+def _L_oracle(tree, tgt, g, f, h, nu, p, theta):
+    tree.set_moments(f, h, nu, p)
+    return float(np.sum(g * tree.treecode(tgt, theta, p)))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("kind,N,N0,p,theta", [("cube", 20000, 200, 6, 0.5), ("cube", 12000, 150, 8, 0.5),
+                                               ("sphere", 15000, 150, 4, 0.7)])
+def test_weight_gradients_dot_product(prec, kind, N, N0, p, theta):
+    if kind == "cube":
+        x, f, h, nu = inputs.uniform_cube(N, 301)
+    else:
+        x, f, h, nu = inputs.fibonacci_sphere(N, 302)
+    rng = np.random.default_rng(303)
+    g = rng.standard_normal((N, 3))
+    gr = _adjoint(prec, x, f, h, nu, g, N0, p, theta)
+    tree = oracle.Tree(x, N0, True)
+    z = np.zeros_like(f)
+    phi, psi, chi = (rng.standard_normal((N, 3)) for _ in range(3))
+    checks = [(gr["f"], phi, _L_oracle(tree, x, g, phi, z, nu, p, theta)),
+              (gr["h"], psi, _L_oracle(tree, x, g, z, psi, nu, p, theta)),
+              (gr["nu"], chi, _L_oracle(tree, x, g, z, h, chi, p, theta))]
+    for grad, probe, ref in checks:
+        got = float(np.sum(grad * probe))
+        scale = np.linalg.norm(grad) * np.linalg.norm(probe)
+        assert abs(got - ref) <= TOL_W[prec] * scale, (got, ref, scale)
+
+
+def _fd_positions(x, f, h, nu, g, N0, p, theta, entries, step, targets=None, which="x"):
+    """Central differences of sum g . u_frozen on the listed (index, axis)."""
+    tree = oracle.Tree(x, N0, True)
+    tgt = x if targets is None else targets
+    out = []
+    for (n, a) in entries:
+        vals = []
+        for sgn in (1.0, -1.0):
+            xe = x.copy()
+            te = tgt.copy() if targets is not None else None
+            if which == "x":
+                xe[n, a] += sgn * step
+                if targets is None:
+                    te = xe
+            else:
+                te[n, a] += sgn * step
+            u = tree.treecode_frozen(xe, f, h, nu, p, tgt, te, theta)
+            vals.append(float(np.sum(g * u)))
+        out.append((vals[0] - vals[1]) / (2 * step))
+    return np.array(out)
+
+
+def _fd_error(got, fd, full):
+    floor = np.sqrt(np.mean(full ** 2))
+    return float(np.sqrt(np.sum((got - fd) ** 2) / np.sum(np.maximum(np.abs(fd), floor) ** 2)))
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-5), ("mixed", 1e-4)])
+@pytest.mark.parametrize("kind", ["cube", "clusters"])
+def test_position_gradient_matches_finite_differences(prec, tol, kind):
+    N, N0, p, theta = 3000, 100, 6, 0.5
+    if kind == "cube":
+        x, f, h, nu = inputs.uniform_cube(N, 311)
+    else:
+        x, f, h, nu = inputs.gaussian_clusters(N, 312)
+    rng = np.random.default_rng(313)
+    g = rng.standard_normal((N, 3))
+    gr = _adjoint(prec, x, f, h, nu, g, N0, p, theta)
+    idx = inputs.sample_indices(N, 24, 314)
+    entries = [(int(n), int(k % 3)) for k, n in enumerate(idx)]
+    fd = _fd_positions(x, f, h, nu, g, N0, p, theta, entries, 1e-6)
+    got = np.array([gr["x"][n, a] for n, a in entries])
+    assert _fd_error(got, fd, gr["x"]) <= tol
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_disjoint_targets_source_and_target_gradients(prec):
+    N, N0, p, theta = 2500, 90, 5, 0.5
+    x, f, h, nu = inputs.uniform_cube(N, 321)
+    rng = np.random.default_rng(322)
+    t = np.concatenate([rng.uniform(-0.2, 1.2, (800, 3)), x[:10]])
+    g = rng.standard_normal((t.shape[0], 3))
+    gr = _adjoint(prec, x, f, h, nu, g, N0, p, theta, targets=t)
+    tol = 1e-5 if prec == "fp64" else 1e-4
+    ex = [(int(n), int(k % 3)) for k, n in enumerate(inputs.sample_indices(N, 16, 323))]
+    fd = _fd_positions(x, f, h, nu, g, N0, p, theta, ex, 1e-6, targets=t, which="x")
+    assert _fd_error(np.array([gr["x"][n, a] for n, a in ex]), fd, gr["x"]) <= tol
+    et = [(int(n), int(k % 3)) for k, n in enumerate(inputs.sample_indices(t.shape[0], 16, 324))]
+    fdt = _fd_positions(x, f, h, nu, g, N0, p, theta, et, 1e-6, targets=t, which="t")
+    assert _fd_error(np.array([gr["t"][n, a] for n, a in et]), fdt, gr["t"]) <= tol
+    # weights with disjoint targets
+    tree = oracle.Tree(x, N0, True)
+    phi = rng.standard_normal((N, 3))
+    ref = _L_oracle(tree, t, g, phi, np.zeros_like(f), nu, p, theta)
+    got = float(np.sum(gr["f"] * phi))
+    assert abs(got - ref) <= TOL_W[prec] * np.linalg.norm(gr["f"]) * np.linalg.norm(phi)
+
+
+def test_autograd_function_matches_adjoint():
+    N, N0, p, theta = 4000, 128, 6, 0.5
+    x, f, h, nu = inputs.uniform_cube(N, 331)
+    g = np.random.default_rng(332).standard_normal((N, 3))
+    X, F, H, NU = (dev(a).requires_grad_(True) for a in (x, f, h, nu))
+    u = api.stokes_velocity(X, F, H, NU, theta, p, N0, "fp64")
+    (u * dev(g)).sum().backward()
+    gr = _adjoint("fp64", x, f, h, nu, g, N0, p, theta)
+    for name, T in (("x", X), ("f", F), ("h", H), ("nu", NU)):
+        ref = gr[name]
+        np.testing.assert_allclose(host(T.grad), ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+
+
+def test_adjoint_argument_checks():
+    x, f, h, nu = inputs.uniform_cube(200, 341)
+    tc = api.Treecode("fp64", True).build(dev(x), 20).moments(dev(f), dev(h), dev(nu), 3)
+    with pytest.raises(api.TCError) as e:
+        tc._M = 200
+        tc.adjoint(dev(np.ones((200, 3))))
+    assert e.value.status == 4  # no evaluation yet
+    tc.eval(0.5, 3)
+    with pytest.raises(api.TCError) as e:
+        tc.adjoint(dev(np.ones((200, 3))), t=True)
+    assert e.value.status == 1  # grad_t with targets = sources
+    tc.close()
+
+
+def test_full_size_sampled_weight_gradient():
+    """N = 262,144 in 8 Gaussian clusters (sigma 0.05), p = 8, theta = 0.5,
+    mixed precision: with g nonzero on 64 sampled targets only, L needs the
+    oracle at those targets alone, so the dot-product identity is checked at
+    full size."""
+    N, N0, p, theta = 262_144, 2000, 8, 0.5
+    x, f, h, nu = inputs.gaussian_clusters(N, inputs.SEED_BASE + 4)
+    rng = np.random.default_rng(351)
+    idx = inputs.sample_indices(N, 64, 352)
+    g = np.zeros((N, 3))
+    g[idx] = rng.standard_normal((len(idx), 3))
+    gr = _adjoint("mixed", x, f, h, nu, g, N0, p, theta)
+    tree = oracle.Tree(x, N0, True)
+    z = np.zeros_like(f)
+    phi = rng.standard_normal((N, 3))
+    tree.set_moments(phi, z, nu, p)
+    ref = float(np.sum(g[idx] * tree.treecode(x[idx], theta, p)))
+    got = float(np.sum(gr["f"] * phi))
+    assert abs(got - ref) <= 1e-6 * np.linalg.norm(gr["f"]) * np.linalg.norm(phi)

@@ -439,3 +439,17 @@ def test_error_matches_paper_table1_sphere():
     E = _sampled_E(x, f, h, nu, 2000, True, 0.5, list(paper), 600, 8)
     for p, e in paper.items():
         assert e / 2 < E[p] < e * 2, (p, E[p], e)
+
+
+def test_frozen_structure_map_reduces_to_treecode_and_direct():
+    """The frozen-structure evaluation used for finite differences of the
+    adjoint: unmoved it is Algorithm 1 exactly; with theta -> 0 every pair is
+    summed directly, so moved positions give the direct sum at those positions."""
+    x, f, h, nu = _system(1500, 57)
+    tree = oracle.Tree(x, 60, True)
+    tree.set_moments(f, h, nu, 5)
+    np.testing.assert_array_equal(tree.treecode_frozen(x, f, h, nu, 5, x, x, 0.5), tree.treecode(x, 0.5, 5))
+    rng = _rng(58)
+    xe = x + 1e-3 * rng.standard_normal(x.shape)
+    u = tree.treecode_frozen(xe, f, h, nu, 5, x, xe, 1e-9)
+    np.testing.assert_allclose(u, oracle.direct(xe, f, h, nu), rtol=1e-12, atol=1e-12)
