@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--error-samples", type=int, default=10000, help="targets of the FP64 direct-sum error check")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the forward+adjoint (Gaussian clusters) and batched (64 systems) measurements")
     return ap.parse_args()
 
 
@@ -176,6 +178,94 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _events(stream):
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    return e0, e1
+
+
+def bench_fwd_adjoint(flush, stream, steps=3):
+    """Forward + adjoint step on 262,144 particles in 8 Gaussian clusters
+    (sigma 0.05), p = 8, theta = 0.5, N0 = 2000, mixed precision: tc_build,
+    tc_moments, tc_eval and tc_adjoint for dL/df, dL/dh, dL/dnu, dL/dx."""
+    import numpy as np
+    import torch
+
+    from paper_1811_12498_gb300 import api, inputs
+    N, N0, p, theta = 262_144, 2000, 8, 0.5
+    x, f, h, nu = inputs.gaussian_clusters(N, inputs.SEED_BASE + 4)
+    d = [torch.from_numpy(np.ascontiguousarray(a.T)).cuda() for a in (x, f, h, nu)]
+    g = torch.from_numpy(np.ascontiguousarray(np.random.default_rng(5).standard_normal((N, 3)).T)).cuda()
+    tc = api.Treecode("mixed", True, stream)
+    u = torch.empty((3, N), dtype=torch.float64, device="cuda")
+    fwd, tot = [], []
+    for k in range(steps + 1):
+        flush.fill_(1)
+        e0, e1 = _events(stream)
+        tc.build(d[0], N0).moments(d[1], d[2], d[3], p)
+        tc.eval(theta, p, out=u)
+        em = torch.cuda.Event(enable_timing=True)
+        em.record(stream)
+        tc.adjoint(g)
+        e1.record(stream)
+        e1.synchronize()
+        if k > 0:
+            fwd.append(e0.elapsed_time(em))
+            tot.append(e0.elapsed_time(e1))
+    tc.close()
+    ms = statistics.mean(tot)
+    return {"workload": "8 Gaussian clusters N=262144, sigma=0.05, p=8, theta=0.5, N0=2000, mixed",
+            "s_per_step": ms / 1e3, "fwd_ms": statistics.mean(fwd), "adjoint_ms": ms - statistics.mean(fwd),
+            "steps": steps, "grads": "f, h, nu, x"}
+
+
+def bench_batched(flush, stream, reps=3):
+    """64 independent systems, sizes log-uniform in [1e4, 5e5] (even: uniform
+    cube, odd: Fibonacci sphere), p = 6, theta = 0.6, N0 = 2000, mixed: one
+    batched evaluation (persistent kernels from a CUDA graph, autotuned
+    shapes) against 64 separate tc_eval calls; trees and moments built once."""
+    import numpy as np
+    import torch
+
+    from paper_1811_12498_gb300 import api, inputs
+    sizes = inputs.batch_sizes(64, inputs.SEED_BASE + 5)
+    parts = []
+    for k, n in enumerate(sizes):
+        gen = inputs.uniform_cube if k % 2 == 0 else inputs.fibonacci_sphere
+        parts.append(gen(int(n), inputs.SEED_BASE + 500 + k))
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    seg = [torch.from_numpy(np.ascontiguousarray(np.concatenate([pp[c] for pp in parts]).T)).cuda() for c in range(4)]
+    b = api.Batch("mixed", True, stream)
+    b.build(seg[0], off, 2000).moments(seg[1], seg[2], seg[3], 6)
+    u = b.eval(0.6, 6)  # tunes and captures the graph
+    outs = b.eval_separate(0.6, 6)
+    tb, ts = [], []
+    for _ in range(reps):
+        flush.fill_(1)
+        e0, e1 = _events(stream)
+        b.eval(0.6, 6, out=u)
+        e1.record(stream)
+        e1.synchronize()
+        tb.append(e0.elapsed_time(e1))
+        flush.fill_(1)
+        e0, e1 = _events(stream)
+        b.eval_separate(0.6, 6, outs)
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    same = all(torch.equal(u[:, int(off[s]):int(off[s + 1])], outs[s]) for s in range(len(sizes)))
+    info = b.info()
+    b.close()
+    ntot = int(off[-1])
+    return {"workload": "64 systems, log-uniform N in [1e4, 5e5], cube/sphere, p=6, theta=0.6, N0=2000, mixed",
+            "total_targets": ntot, "batched_ms": statistics.mean(tb), "separate_ms": statistics.mean(ts),
+            "batched_targets_per_s": ntot / (statistics.mean(tb) / 1e3),
+            "separate_targets_per_s": ntot / (statistics.mean(ts) / 1e3),
+            "identical_results": bool(same), "tuned_shape": info}
+
+
 def config(args):
     return {"workload": "uniform cube N=%d, Stokeslet+stresslet, p=%d, theta=%g, N0=%d, %s precision, "
                         "clusters shrunk to their boxes" % (args.N, args.p, args.theta, args.N0, args.precision),
@@ -248,6 +338,7 @@ def main():
         ms = float(t.item())
     value = N * world / (ms / 1e3)
     st = tc.stats()
+    ls = tc.list_stats()
     ph = {k: statistics.mean(pp[k] for pp in phases if pp[k] is not None) for k in phases[0] if phases[0][k] is not None}
 
     # end to end through the public API: pinned host inputs -> device -> step -> host u
@@ -317,7 +408,9 @@ def main():
         "gpu_launches": int(launches),
         "clocks": clk,
         "phases_ms": ph,
-        "interactions": {"far": n_far, "near_pairs": st["near_pairs"], "clusters": st["clusters"]},
+        "interactions": {"far": n_far, "near_pairs": st["near_pairs"], "clusters": st["clusters"],
+                         "far_entries": ls["far_entries"], "near_entries": ls["near_entries"],
+                         "far_lane_use": ls["far_lane_use"], "near_lane_use": ls["near_lane_use"]},
         "secondary": {"near_fp32_tflops": near_flops / (near_ms / 1e3) / 1e12 if near_ms else None,
                       "near_fp32_frac": (near_flops / (near_ms / 1e3) / 1e12) / PEAK_FP32_TFLOPS if near_ms else None,
                       "far_fp32_contraction_tflops": con_flops / (far_ms / 1e3) / 1e12},
@@ -348,6 +441,9 @@ def main():
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
         line["accuracy"]["vs_oracle_treecode"] = float(np.sqrt(np.sum((u_host[idx] - uo) ** 2) / np.sum(uo ** 2)))
         line["accuracy"]["oracle_samples"] = int(len(idx))
+    if not args.no_extras:
+        line["fwd_adjoint"] = bench_fwd_adjoint(flush, stream)
+        line["batched"] = bench_batched(flush, stream)
     print(json.dumps(line), flush=True)
     tc.close()
     if dist is not None:

@@ -221,6 +221,48 @@ tc_status tc_list_stats(tc_ctx* ctx, int64_t* far_entries, int64_t* near_entries
 tc_status tc_eval_counts(tc_ctx* ctx, int64_t* nfar, int64_t* nnear_pairs);
 
 /* ---------------------------------------------------------------------- */
+/* Batches of independent systems.                                        */
+/* ---------------------------------------------------------------------- */
+/*
+ * A batch evaluates many independent particle systems (each its own eq. (1.3)
+ * with targets = sources) together.  Arrays are segmented FP64 SoA in device
+ * memory: with ntot = offsets[nsys], component a of particle i of system s
+ * is at ptr[a * ntot + offsets[s] + i].  offsets is a HOST array of nsys + 1
+ * entries, offsets[0] = 0, strictly increasing.  Every system uses the
+ * batch's tc_config; the batch owns one context per system.
+ *
+ * tc_batch_eval runs, after preparing every system's interaction lists, the
+ * far field, the near field and the final sum of all systems as one
+ * persistent far kernel, one persistent near kernel and one finalize: warps
+ * take (system, batch of 32 targets) items from a device counter until the
+ * queue is empty.  That phase is captured into a CUDA graph on the first call
+ * and replayed while the output pointer, the order p, the launch shapes and
+ * the systems' buffers are unchanged.  Launch shapes come from an autotuner
+ * that times candidate shapes on the first evaluation at each order.
+ */
+typedef struct tc_batch tc_batch;
+
+tc_status tc_batch_create(tc_batch** out, const tc_config* cfg);
+tc_status tc_batch_destroy(tc_batch* b);
+const char* tc_batch_last_error(const tc_batch* b);
+/* autotune (default 1) and CUDA-graph replay (default 1) switches */
+tc_status tc_batch_set(tc_batch* b, int32_t autotune, int32_t use_graph);
+/* tc_build of every system (x segmented, see above); synchronises */
+tc_status tc_batch_build(tc_batch* b, const double* x, int32_t nsys, const int64_t* offsets, int32_t N0);
+/* tc_moments of every system (f, h, nu segmented) */
+tc_status tc_batch_moments(tc_batch* b, const double* f, const double* h, const double* nu, int32_t p);
+/* velocity of every system at its own particles into u (segmented 3 x ntot) */
+tc_status tc_batch_eval(tc_batch* b, double theta, int32_t p, double* u);
+/* the same result by one ordinary tc_eval per system (u_sys: host array of
+ * nsys device pointers, system s writes a 3 x n_s SoA array); for comparison */
+tc_status tc_batch_eval_separate(tc_batch* b, double theta, int32_t p, double* const* u_sys);
+/* chosen launch shapes {far warps/block, far blocks, near warps/block, near
+ * blocks} (0 blocks = occupancy limit) and the tuned kernels' times in ms */
+tc_status tc_batch_info(tc_batch* b, int32_t* shape, float* tune_ms);
+/* context of system s (owned by the batch), e.g. for tc_stats; NULL if out of range */
+tc_ctx* tc_batch_system(tc_batch* b, int32_t s);
+
+/* ---------------------------------------------------------------------- */
 /* Tracing.                                                               */
 /* ---------------------------------------------------------------------- */
 

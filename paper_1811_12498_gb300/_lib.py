@@ -30,6 +30,16 @@ SIGNATURES = {
     "tc_tree_export": (_i32, [_vp] + [_vp] * 9),
     "tc_tree_order": (_i32, [_vp, _vp]),
     "tc_moments_export": (_i32, [_vp, _i64, _vp, _vp]),
+    "tc_batch_create": (_i32, [_c.POINTER(_vp), _vp]),
+    "tc_batch_destroy": (_i32, [_vp]),
+    "tc_batch_last_error": (_c.c_char_p, [_vp]),
+    "tc_batch_set": (_i32, [_vp, _i32, _i32]),
+    "tc_batch_build": (_i32, [_vp, _vp, _i32, _vp, _i32]),
+    "tc_batch_moments": (_i32, [_vp, _vp, _vp, _vp, _i32]),
+    "tc_batch_eval": (_i32, [_vp, _dbl, _i32, _vp]),
+    "tc_batch_eval_separate": (_i32, [_vp, _dbl, _i32, _vp]),
+    "tc_batch_info": (_i32, [_vp, _vp, _vp]),
+    "tc_batch_system": (_vp, [_vp, _i32]),
     "tc_profile": (_i32, [_vp, _i32]),
     "tc_phase_times": (_i32, [_vp, _vp]),
     "tc_kernel_launches": (_i64, []),

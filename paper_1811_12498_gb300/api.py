@@ -221,6 +221,87 @@ def direct(x, f, h, nu, targets=None, precision="fp64", out=None, stream=None):
     return out
 
 
+class Batch:
+    """Many independent systems evaluated together (tc_batch_*).
+
+    Arrays are segmented (3, ntot) float64 CUDA tensors; `offsets` is a list
+    of nsys + 1 particle offsets.  eval() runs all systems' far and near
+    fields as persistent kernels replayed from a CUDA graph."""
+
+    def __init__(self, precision="mixed", shrink=True, stream=None, autotune=True, graph=True):
+        self.stream = torch.cuda.current_stream() if stream is None else stream
+        cfg = TCConfig(_prec(precision), int(bool(shrink)), _stream_ptr(self.stream), 0, 0)
+        h = ctypes.c_void_p()
+        _check(lib().tc_batch_create(ctypes.byref(h), ctypes.byref(cfg)))
+        self._h = h
+        self._chk(lib().tc_batch_set(h, int(bool(autotune)), int(bool(graph))))
+        self.offsets = None
+        self._keep = ()
+
+    def _chk(self, st):
+        if st != 0:
+            msg = lib().tc_batch_last_error(self._h)
+            raise TCError(st, msg.decode() if msg else "")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().tc_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def build(self, x, offsets, N0):
+        x = _vec3(x, "x", int(offsets[-1]))
+        self.offsets = [int(v) for v in offsets]
+        off = (ctypes.c_int64 * len(self.offsets))(*self.offsets)
+        self._chk(lib().tc_batch_build(self._h, _ptr(x), len(self.offsets) - 1, off, int(N0)))
+        self._keep_x = x
+        return self
+
+    def moments(self, f, h, nu, p):
+        n = self.offsets[-1]
+        f, h, nu = (_vec3(a, k, n) for a, k in ((f, "f"), (h, "h"), (nu, "nu")))
+        self._chk(lib().tc_batch_moments(self._h, _ptr(f), _ptr(h), _ptr(nu), int(p)))
+        self._keep = (f, h, nu)
+        return self
+
+    def eval(self, theta, p, out=None):
+        n = self.offsets[-1]
+        if out is None:
+            with torch.cuda.stream(self.stream):
+                out = torch.empty((3, n), dtype=torch.float64, device="cuda")
+        _vec3(out, "out", n)
+        self._chk(lib().tc_batch_eval(self._h, float(theta), int(p), _ptr(out)))
+        return out
+
+    def eval_separate(self, theta, p, outs=None):
+        """One ordinary tc_eval per system; returns the list of (3, n_s) outputs."""
+        sizes = [b - a for a, b in zip(self.offsets[:-1], self.offsets[1:])]
+        if outs is None:
+            with torch.cuda.stream(self.stream):
+                outs = [torch.empty((3, n), dtype=torch.float64, device="cuda") for n in sizes]
+        arr = (ctypes.c_void_p * len(outs))(*[o.data_ptr() for o in outs])
+        self._chk(lib().tc_batch_eval_separate(self._h, float(theta), int(p), arr))
+        return outs
+
+    def info(self):
+        sh = (ctypes.c_int32 * 4)()
+        ms = (ctypes.c_float * 2)()
+        self._chk(lib().tc_batch_info(self._h, sh, ms))
+        return dict(far_warps=sh[0], far_blocks=sh[1], near_warps=sh[2], near_blocks=sh[3],
+                    far_ms=ms[0], near_ms=ms[1])
+
+    def system_stats(self, s):
+        h = lib().tc_batch_system(self._h, int(s))
+        near, far, nodes = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().tc_stats(h, ctypes.byref(near), ctypes.byref(far), ctypes.byref(nodes)), h)
+        return dict(near_pairs=near.value, far_interactions=far.value, clusters=nodes.value)
+
+
 class StokesTreecode(torch.autograd.Function):
     """u = treecode velocity (eq. 1.3 by Algorithm 1) as a differentiable op.
 

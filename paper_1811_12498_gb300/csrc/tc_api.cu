@@ -361,11 +361,13 @@ static tc_status ensure_tables(tc_ctx* ctx, int p)
     return TC_OK;
 }
 
-tc_status tc_eval(tc_ctx* ctx, const double* targets, int64_t M, double theta, int32_t p, double* u)
+}  // extern "C"
+
+// First half of tc_eval: contraction tables, target ordering and the
+// interaction lists (synchronises once to size the lists).
+tc_status tc::eval_prepare(tc_ctx* ctx, const double* targets, int64_t M, double theta, int p)
 {
-    if (!ctx) return fail(nullptr, TC_EINVAL, "tc_eval: ctx is NULL");
     if (!ctx->have_moments) return fail(ctx, TC_ESTATE, "tc_eval: call tc_build and tc_moments first");
-    if (!u) return fail(ctx, TC_EINVAL, "tc_eval: u is NULL");
     if (!(theta > 0.0 && theta < 1.0)) return fail(ctx, TC_EINVAL, "tc_eval: theta = %g out of (0, 1)", theta);
     if (p < 0 || p > ctx->p_mom)
         return fail(ctx, TC_EINVAL, "tc_eval: p = %d out of [0, %d] (order of tc_moments)", p, ctx->p_mom);
@@ -376,6 +378,7 @@ tc_status tc_eval(tc_ctx* ctx, const double* targets, int64_t M, double theta, i
     if (st != TC_OK) return st;
     cudaStream_t s = ctx->stream;
     ctx->have_eval = 0;
+    ctx->prepared = 0;
     ctx->adj_lists_ready = 0;
     const double* ts;
     const int32_t* tperm;
@@ -435,25 +438,53 @@ tc_status tc_eval(tc_ctx* ctx, const double* targets, int64_t M, double theta, i
                        ptr<int64_t>(ctx->cnt_near), ptr<int32_t>(ctx->flags), s),
           "list write");
     ph_end(ctx, TC_PH_LISTS);
+    (void)tperm;
+    ctx->M = M;
+    ctx->far_entries = tot[0];
+    ctx->near_entries = tot[1];
+    ctx->p_eval = p;
+    ctx->prepared = 1;
+    return TC_OK;
+}
+
+// Second half of tc_eval: far field, near field, sum and scatter to u.
+tc_status tc::eval_compute(tc_ctx* ctx, double* u)
+{
+    if (!ctx->prepared) return fail(ctx, TC_ESTATE, "tc_eval: lists are not prepared");
+    cudaStream_t s = ctx->stream;
+    const int64_t M = ctx->M;
+    const int p = ctx->p_eval;
+    const double* ts = ctx->eval_self ? ptr<double>(ctx->xs) : ptr<double>(ctx->ts);
+    const int32_t* tperm = ctx->eval_self ? ptr<int32_t>(ctx->perm) : ptr<int32_t>(ctx->tperm);
     ph_begin(ctx, TC_PH_FAR);
-    TC_CK(launch_far(ctx->precision, ts, M, geo, ptr<double>(ctx->node_invrho), ptr<double>(ctx->ab64),
-                     ptr<float>(ctx->ab32), p, far_off, ptr<ListEntry>(ctx->far_list), ptr<double>(ctx->u_far), s),
+    TC_CK(launch_far(ctx->precision, ts, M, ptr<Geo>(ctx->node_geo), ptr<double>(ctx->node_invrho),
+                     ptr<double>(ctx->ab64), ptr<float>(ctx->ab32), p, ptr<int64_t>(ctx->far_off),
+                     ptr<ListEntry>(ctx->far_list), ptr<double>(ctx->u_far), s),
           "far field");
     ph_end(ctx, TC_PH_FAR);
     ph_begin(ctx, TC_PH_NEAR);
-    TC_CK(launch_near(ctx->precision, ts, M, topo, ptr<double>(ctx->xs), ptr<double>(ctx->ws),
-                      ptr<float4>(ctx->spack), ctx->N, near_off, ptr<ListEntry>(ctx->near_list),
+    TC_CK(launch_near(ctx->precision, ts, M, ptr<int4>(ctx->node_topo), ptr<double>(ctx->xs), ptr<double>(ctx->ws),
+                      ptr<float4>(ctx->spack), ctx->N, ptr<int64_t>(ctx->near_off), ptr<ListEntry>(ctx->near_list),
                       ptr<double>(ctx->u_near), s),
           "near field");
     ph_end(ctx, TC_PH_NEAR);
     ph_begin(ctx, TC_PH_FINAL);
     TC_CK(launch_finalize(ptr<double>(ctx->u_far), ptr<double>(ctx->u_near), tperm, M, u, s), "finalize");
     ph_end(ctx, TC_PH_FINAL);
-    ctx->M = M;
-    ctx->far_entries = tot[0];
-    ctx->near_entries = tot[1];
     ctx->have_eval = 1;
     return TC_OK;
+}
+
+extern "C" {
+
+tc_status tc_eval(tc_ctx* ctx, const double* targets, int64_t M, double theta, int32_t p, double* u)
+{
+    if (!ctx) return fail(nullptr, TC_EINVAL, "tc_eval: ctx is NULL");
+    if (!ctx->have_moments) return fail(ctx, TC_ESTATE, "tc_eval: call tc_build and tc_moments first");
+    if (!u) return fail(ctx, TC_EINVAL, "tc_eval: u is NULL");
+    tc_status st = eval_prepare(ctx, targets, M, theta, p);
+    if (st != TC_OK) return st;
+    return eval_compute(ctx, u);
 }
 
 tc_status tc_direct(const double* x, const double* f, const double* h, const double* nu, int64_t N,

@@ -47,23 +47,17 @@ __device__ inline void contract(TC c, const TC* __restrict__ t, TC* acc)
     for (int q = 0; q < 12; q++) acc[q] = fma(c, t[q], acc[q]);
 }
 
+// The far field of batch b (32 targets, one per lane) on one warp.  slot_p
+// holds the levels of the parity of P = p + 2 (size level_size(P) x 32) and
+// slot_q the others (level_size(P - 1) x 32).
 template <typename TR, typename TC>
-__global__ void __launch_bounds__(kFarWarps * 32)
-    k_far(const double* __restrict__ ts, int64_t M, const Geo* __restrict__ geo,
-          const double* __restrict__ invrho, const TC* __restrict__ ab, int p, const int64_t* __restrict__ far_off,
-          const ListEntry* __restrict__ far_list, double* __restrict__ u_far)
+__device__ inline void far_batch(const double* __restrict__ ts, int64_t M, const Geo* __restrict__ geo,
+                                 const double* __restrict__ invrho, const TC* __restrict__ ab, int p,
+                                 const int64_t* __restrict__ far_off, const ListEntry* __restrict__ far_list,
+                                 double* __restrict__ u_far, int64_t b, TR* slot_p, TR* slot_q, int lane)
 {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t nbatch = (M + kBatch - 1) / kBatch;
-    const int64_t b = blockIdx.x * (int64_t)kFarWarps + w;
-    if (b >= nbatch) return;
     const int P = p + 2;
     const int C2 = ncoef(P);
-    // slot of parity P holds levels P, P-2, ...; the other slot P-1, P-3, ...
-    const int LSP = level_size(P), LSQ = level_size(P - 1);
-    TR* slot_p = reinterpret_cast<TR*>(smraw) + (size_t)w * (LSP + LSQ) * 32;
-    TR* slot_q = slot_p + (size_t)LSP * 32;
     const int64_t m = b * kBatch + lane;
     const bool valid = m < M;
     double x0 = 0, x1 = 0, x2 = 0;
@@ -140,6 +134,82 @@ __global__ void __launch_bounds__(kFarWarps * 32)
     }
 }
 
+template <typename TR>
+__device__ inline void far_slots(unsigned char* smraw, int p, int w, TR*& slot_p, TR*& slot_q)
+{
+    const int LSP = level_size(p + 2), LSQ = level_size(p + 1);
+    slot_p = reinterpret_cast<TR*>(smraw) + (size_t)w * (LSP + LSQ) * 32;
+    slot_q = slot_p + (size_t)LSP * 32;
+}
+
+template <typename TR, typename TC>
+__global__ void __launch_bounds__(kFarWarps * 32)
+    k_far(const double* __restrict__ ts, int64_t M, const Geo* __restrict__ geo,
+          const double* __restrict__ invrho, const TC* __restrict__ ab, int p, const int64_t* __restrict__ far_off,
+          const ListEntry* __restrict__ far_list, double* __restrict__ u_far)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t nbatch = (M + kBatch - 1) / kBatch;
+    const int64_t b = blockIdx.x * (int64_t)kFarWarps + w;
+    if (b >= nbatch) return;
+    TR *slot_p, *slot_q;
+    far_slots<TR>(smraw, p, w, slot_p, slot_q);
+    far_batch<TR, TC>(ts, M, geo, invrho, ab, p, far_off, far_list, u_far, b, slot_p, slot_q, lane);
+}
+
+// Persistent far-field kernel over many systems: every warp repeatedly takes
+// the next (system, batch) item from a device counter until the queue is
+// empty.  Items are numbered system by system (item_off: nsys + 1 offsets).
+template <typename TR, typename TC>
+__global__ void k_far_batched(const SysDesc* __restrict__ sys, int nsys, const int64_t* __restrict__ item_off,
+                              int64_t nitems, int p, unsigned long long* __restrict__ counter)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    TR *slot_p, *slot_q;
+    far_slots<TR>(smraw, p, w, slot_p, slot_q);
+    for (;;) {
+        unsigned long long item = 0;
+        if (lane == 0) item = atomicAdd(counter, 1ull);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if ((int64_t)item >= nitems) break;
+        int lo = 0, hi = nsys;  // item_off[lo] <= item < item_off[hi]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (item_off[mid] <= (int64_t)item)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        const SysDesc& d = sys[lo];
+        far_batch<TR, TC>(d.ts, d.M, d.geo, d.invrho, (const TC*)d.ab, p, d.far_off, d.far_list, d.u_far,
+                          (int64_t)item - item_off[lo], slot_p, slot_q, lane);
+    }
+}
+
+template <typename TR, typename TC>
+cudaError_t run_far_batched(const SysDesc* sys, int nsys, const int64_t* item_off, int64_t nitems, int p,
+                            unsigned long long* counter, int warps_per_block, int blocks, cudaStream_t s)
+{
+    size_t smem = (size_t)warps_per_block * (level_size(p + 2) + level_size(p + 1)) * 32 * sizeof(TR);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_far_batched<TR, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (blocks <= 0) {
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_far_batched<TR, TC>, warps_per_block * 32, smem);
+        if (e != cudaSuccess) return e;
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        blocks = (per_sm > 0 ? per_sm : 1) * sms;
+    }
+    k_far_batched<TR, TC><<<blocks, warps_per_block * 32, smem, s>>>(sys, nsys, item_off, nitems, p, counter);
+    note_launch();
+    return cudaGetLastError();
+}
+
 template <typename TR, typename TC>
 cudaError_t run_far(const double* ts, int64_t M, const Geo* geo, const double* invrho, const TC* ab, int p,
                     const int64_t* far_off, const ListEntry* far_list, double* u_far, cudaStream_t s)
@@ -163,6 +233,16 @@ cudaError_t launch_far(int precision, const double* ts, int64_t M, const Geo* ge
     if (precision == TC_FP64) return run_far<double, double>(ts, M, geo, invrho, ab64, p, far_off, far_list, u_far, s);
     if (p >= 8) return run_far<double, float>(ts, M, geo, invrho, ab32, p, far_off, far_list, u_far, s);
     return run_far<float, float>(ts, M, geo, invrho, ab32, p, far_off, far_list, u_far, s);
+}
+
+cudaError_t launch_far_batched(int precision, const SysDesc* sys, int nsys, const int64_t* item_off, int64_t nitems,
+                               int p, unsigned long long* counter, int warps_per_block, int blocks, cudaStream_t s)
+{
+    if (precision == TC_FP64)
+        return run_far_batched<double, double>(sys, nsys, item_off, nitems, p, counter, warps_per_block, blocks, s);
+    if (p >= 8)
+        return run_far_batched<double, float>(sys, nsys, item_off, nitems, p, counter, warps_per_block, blocks, s);
+    return run_far_batched<float, float>(sys, nsys, item_off, nitems, p, counter, warps_per_block, blocks, s);
 }
 
 }  // namespace tc

@@ -55,6 +55,29 @@ struct ListEntry {
     uint32_t mask;
 };
 
+// Device-side description of one system for the batched (persistent) far,
+// near and finalize kernels: the buffers of its context after eval_prepare.
+struct SysDesc {
+    const double* ts;          // 3*M sorted targets
+    int64_t M;
+    const Geo* geo;
+    const double* invrho;
+    const void* ab;            // contraction tables (double or float)
+    const int64_t* far_off;
+    const ListEntry* far_list;
+    double* u_far;
+    const int4* topo;
+    const float4* spack;
+    const double* xs;
+    const double* ws;
+    int64_t N;
+    const int64_t* near_off;
+    const ListEntry* near_list;
+    double* u_near;
+    const int32_t* tperm;      // sorted target -> caller's target index
+    int64_t out_off;           // first column of this system in the batched output
+};
+
 }  // namespace tc
 
 struct tc_ctx {
@@ -108,6 +131,8 @@ struct tc_ctx {
     tc::DevBuf u_far, u_near;           // 3*M FP64 sorted order
     tc::DevBuf flags;                   // int32 device error flags
     int64_t far_entries = 0, near_entries = 0;  // list sizes of the last tc_eval
+    int p_eval = -1;                            // order of the last tc_eval
+    int prepared = 0;                           // lists ready for the far/near kernels
     int have_eval = 0;
 
     // ---- adjoint (tc_adjoint)
@@ -130,6 +155,10 @@ namespace tc {
 
 // count one kernel launch (process-wide counter read by tc_kernel_launches)
 void note_launch();
+
+// tc_eval in two halves (tc_api.cu): lists, then far/near/finalize
+tc_status eval_prepare(tc_ctx* ctx, const double* targets, int64_t M, double theta, int p);
+tc_status eval_compute(tc_ctx* ctx, double* u);
 
 // error helpers (tc_api.cu)
 tc_status fail(tc_ctx* ctx, tc_status st, const char* fmt, ...);
@@ -189,7 +218,14 @@ cudaError_t launch_far(int precision, const double* ts, int64_t M, const Geo* ge
                        const double* ab64, const float* ab32, int p, const int64_t* far_off,
                        const ListEntry* far_list, double* u_far, cudaStream_t s);
 
+cudaError_t launch_far_batched(int precision, const SysDesc* sys, int nsys, const int64_t* item_off, int64_t nitems,
+                               int p, unsigned long long* counter, int warps_per_block, int blocks, cudaStream_t s);
+
 // tc_near.cu
+cudaError_t launch_near_batched(int precision, const SysDesc* sys, int nsys, const int64_t* item_off, int64_t nitems,
+                                unsigned long long* counter, int warps_per_block, int blocks, cudaStream_t s);
+cudaError_t launch_finalize_batched(const SysDesc* sys, int nsys, const int64_t* moff, int64_t mtotal, double* u,
+                                    int64_t ntot, cudaStream_t s);
 cudaError_t launch_near(int precision, const double* ts, int64_t M, const int4* topo,
                         const double* xs, const double* ws, const float4* spack, int64_t N,
                         const int64_t* near_off, const ListEntry* near_list, double* u_near, cudaStream_t s);

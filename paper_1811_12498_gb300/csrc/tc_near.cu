@@ -19,17 +19,15 @@ namespace tc {
 namespace {
 
 constexpr int kNearWarps = 4;
+constexpr int kNearMaxWarps = 8;  // largest block the batched kernel accepts
 
-__global__ void __launch_bounds__(kNearWarps * 32)
-    k_near_mixed(const double* __restrict__ ts, int64_t M, const int4* __restrict__ topo,
-                 const float4* __restrict__ spack, const int64_t* __restrict__ near_off,
-                 const ListEntry* __restrict__ near_list, double* __restrict__ u_near)
+// Mixed-precision near field of batch b on one warp; tw is the warp's tile
+// of 32 source records (4 float4 each).
+__device__ inline void near_batch_mixed(const double* __restrict__ ts, int64_t M, const int4* __restrict__ topo,
+                                        const float4* __restrict__ spack, const int64_t* __restrict__ near_off,
+                                        const ListEntry* __restrict__ near_list, double* __restrict__ u_near,
+                                        int64_t b, float4* tw, int lane)
 {
-    __shared__ float4 tile[kNearWarps][32][4];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t nbatch = (M + kBatch - 1) / kBatch;
-    const int64_t b = blockIdx.x * (int64_t)kNearWarps + w;
-    if (b >= nbatch) return;
     const int64_t m = b * kBatch + lane;
     const bool valid = m < M;
     float th[3] = {0, 0, 0}, tl[3] = {0, 0, 0};
@@ -51,16 +49,16 @@ __global__ void __launch_bounds__(kNearWarps * 32)
             __syncwarp();
             if (lane < cnt) {
                 const float4* src = spack + 4 * (int64_t)(base + lane);
-                tile[w][lane][0] = src[0];
-                tile[w][lane][1] = src[1];
-                tile[w][lane][2] = src[2];
-                tile[w][lane][3] = src[3];
+                tw[lane * 4 + 0] = src[0];
+                tw[lane * 4 + 1] = src[1];
+                tw[lane * 4 + 2] = src[2];
+                tw[lane * 4 + 3] = src[3];
             }
             __syncwarp();
             if (!in) continue;
             float ax = 0.f, ay = 0.f, az = 0.f;
             for (int j = 0; j < cnt; j++) {
-                const float4 p0 = tile[w][j][0], p1 = tile[w][j][1], p2 = tile[w][j][2], p3 = tile[w][j][3];
+                const float4 p0 = tw[j * 4 + 0], p1 = tw[j * 4 + 1], p2 = tw[j * 4 + 2], p3 = tw[j * 4 + 3];
                 const float dx = (th[0] - p0.x) + (tl[0] - p1.x);
                 const float dy = (th[1] - p0.y) + (tl[1] - p1.y);
                 const float dz = (th[2] - p0.z) + (tl[2] - p1.z);
@@ -88,17 +86,12 @@ __global__ void __launch_bounds__(kNearWarps * 32)
     }
 }
 
-__global__ void __launch_bounds__(kNearWarps * 32)
-    k_near_fp64(const double* __restrict__ ts, int64_t M, const int4* __restrict__ topo,
-                const double* __restrict__ xs, const double* __restrict__ ws, int64_t N,
-                const int64_t* __restrict__ near_off, const ListEntry* __restrict__ near_list,
-                double* __restrict__ u_near)
+// FP64 near field of batch b on one warp; tw is the warp's tile [12][32].
+__device__ inline void near_batch_fp64(const double* __restrict__ ts, int64_t M, const int4* __restrict__ topo,
+                                       const double* __restrict__ xs, const double* __restrict__ ws, int64_t N,
+                                       const int64_t* __restrict__ near_off, const ListEntry* __restrict__ near_list,
+                                       double* __restrict__ u_near, int64_t b, double* tw, int lane)
 {
-    __shared__ double tile[kNearWarps][12][32];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t nbatch = (M + kBatch - 1) / kBatch;
-    const int64_t b = blockIdx.x * (int64_t)kNearWarps + w;
-    if (b >= nbatch) return;
     const int64_t m = b * kBatch + lane;
     const bool valid = m < M;
     double tx[3] = {0, 0, 0};
@@ -115,20 +108,20 @@ __global__ void __launch_bounds__(kNearWarps * 32)
             __syncwarp();
             if (lane < cnt) {
                 const int64_t i = base + lane;
-                for (int a = 0; a < 3; a++) tile[w][a][lane] = xs[a * N + i];
-                for (int c = 0; c < 9; c++) tile[w][3 + c][lane] = ws[c * N + i];
+                for (int a = 0; a < 3; a++) tw[a * 32 + lane] = xs[a * N + i];
+                for (int c = 0; c < 9; c++) tw[(3 + c) * 32 + lane] = ws[c * N + i];
             }
             __syncwarp();
             if (!in) continue;
             for (int j = 0; j < cnt; j++) {
-                const double dx = tx[0] - tile[w][0][j], dy = tx[1] - tile[w][1][j], dz = tx[2] - tile[w][2][j];
+                const double dx = tx[0] - tw[j], dy = tx[1] - tw[32 + j], dz = tx[2] - tw[64 + j];
                 const double r2 = dx * dx + dy * dy + dz * dz;
                 const double ri = r2 > 0.0 ? rsqrt(r2) : 0.0;
                 const double ri2 = ri * ri, ri3 = ri2 * ri;
-                const double f0 = tile[w][3][j], f1 = tile[w][4][j], f2 = tile[w][5][j];
+                const double f0 = tw[96 + j], f1 = tw[128 + j], f2 = tw[160 + j];
                 const double df = dx * f0 + dy * f1 + dz * f2;
-                const double dh = dx * tile[w][6][j] + dy * tile[w][7][j] + dz * tile[w][8][j];
-                const double dn = dx * tile[w][9][j] + dy * tile[w][10][j] + dz * tile[w][11][j];
+                const double dh = dx * tw[192 + j] + dy * tw[224 + j] + dz * tw[256 + j];
+                const double dn = dx * tw[288 + j] + dy * tw[320 + j] + dz * tw[352 + j];
                 const double st = ri3 * (df + dh * dn * ri2);
                 ux += f0 * ri + dx * st;
                 uy += f1 * ri + dy * st;
@@ -143,6 +136,64 @@ __global__ void __launch_bounds__(kNearWarps * 32)
     }
 }
 
+__global__ void __launch_bounds__(kNearWarps * 32)
+    k_near_mixed(const double* __restrict__ ts, int64_t M, const int4* __restrict__ topo,
+                 const float4* __restrict__ spack, const int64_t* __restrict__ near_off,
+                 const ListEntry* __restrict__ near_list, double* __restrict__ u_near)
+{
+    __shared__ float4 tile[kNearWarps][32 * 4];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t nbatch = (M + kBatch - 1) / kBatch;
+    const int64_t b = blockIdx.x * (int64_t)kNearWarps + w;
+    if (b >= nbatch) return;
+    near_batch_mixed(ts, M, topo, spack, near_off, near_list, u_near, b, tile[w], lane);
+}
+
+__global__ void __launch_bounds__(kNearWarps * 32)
+    k_near_fp64(const double* __restrict__ ts, int64_t M, const int4* __restrict__ topo,
+                const double* __restrict__ xs, const double* __restrict__ ws, int64_t N,
+                const int64_t* __restrict__ near_off, const ListEntry* __restrict__ near_list,
+                double* __restrict__ u_near)
+{
+    __shared__ double tile[kNearWarps][12 * 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t nbatch = (M + kBatch - 1) / kBatch;
+    const int64_t b = blockIdx.x * (int64_t)kNearWarps + w;
+    if (b >= nbatch) return;
+    near_batch_fp64(ts, M, topo, xs, ws, N, near_off, near_list, u_near, b, tile[w], lane);
+}
+
+// Persistent near-field kernel over many systems (see k_far_batched).
+template <bool kFp64>
+__global__ void __launch_bounds__(kNearMaxWarps * 32)
+    k_near_batched(const SysDesc* __restrict__ sys, int nsys, const int64_t* __restrict__ item_off, int64_t nitems,
+                   unsigned long long* __restrict__ counter)
+{
+    __shared__ __align__(16) double tile[kNearMaxWarps][12 * 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (;;) {
+        unsigned long long item = 0;
+        if (lane == 0) item = atomicAdd(counter, 1ull);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if ((int64_t)item >= nitems) break;
+        int lo = 0, hi = nsys;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (item_off[mid] <= (int64_t)item)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        const SysDesc& d = sys[lo];
+        const int64_t b = (int64_t)item - item_off[lo];
+        if (kFp64)
+            near_batch_fp64(d.ts, d.M, d.topo, d.xs, d.ws, d.N, d.near_off, d.near_list, d.u_near, b, tile[w], lane);
+        else
+            near_batch_mixed(d.ts, d.M, d.topo, d.spack, d.near_off, d.near_list, d.u_near, b,
+                             reinterpret_cast<float4*>(tile[w]), lane);
+    }
+}
+
 __global__ void k_finalize(const double* __restrict__ uf, const double* __restrict__ un,
                            const int32_t* __restrict__ perm, int64_t M, double* __restrict__ u)
 {
@@ -150,6 +201,27 @@ __global__ void k_finalize(const double* __restrict__ uf, const double* __restri
     if (i >= M) return;
     int64_t d = perm[i];
     for (int a = 0; a < 3; a++) u[a * M + d] = uf[a * M + i] + un[a * M + i];
+}
+
+// Batched finalize: system s writes columns [out_off, out_off + M_s) of the
+// (3, ntot) output.  moff: nsys + 1 offsets of the systems' targets.
+__global__ void k_finalize_batched(const SysDesc* __restrict__ sys, int nsys, const int64_t* __restrict__ moff,
+                                   int64_t mtotal, double* __restrict__ u, int64_t ntot)
+{
+    const int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (gi >= mtotal) return;
+    int lo = 0, hi = nsys;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (moff[mid] <= gi)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    const SysDesc& d = sys[lo];
+    const int64_t i = gi - moff[lo];
+    const int64_t c = d.out_off + d.tperm[i];
+    for (int a = 0; a < 3; a++) u[a * ntot + c] = d.u_far[a * d.M + i] + d.u_near[a * d.M + i];
 }
 
 __global__ void k_scatter_counts(const int64_t* __restrict__ cs, const int32_t* __restrict__ perm, int64_t M,
@@ -182,10 +254,40 @@ cudaError_t launch_near(int precision, const double* ts, int64_t M, const int4* 
     return cudaGetLastError();
 }
 
+cudaError_t launch_near_batched(int precision, const SysDesc* sys, int nsys, const int64_t* item_off, int64_t nitems,
+                                unsigned long long* counter, int warps_per_block, int blocks, cudaStream_t s)
+{
+    if (warps_per_block < 1 || warps_per_block > kNearMaxWarps) return cudaErrorInvalidValue;
+    const void* fn = precision == TC_FP64 ? (const void*)k_near_batched<true> : (const void*)k_near_batched<false>;
+    cudaError_t e;
+    if (blocks <= 0) {
+        int per_sm = 0, dev = 0, sms = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, warps_per_block * 32, 0);
+        if (e != cudaSuccess) return e;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        blocks = (per_sm > 0 ? per_sm : 1) * sms;
+    }
+    if (precision == TC_FP64)
+        k_near_batched<true><<<blocks, warps_per_block * 32, 0, s>>>(sys, nsys, item_off, nitems, counter);
+    else
+        k_near_batched<false><<<blocks, warps_per_block * 32, 0, s>>>(sys, nsys, item_off, nitems, counter);
+    note_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t launch_finalize(const double* u_far, const double* u_near, const int32_t* perm, int64_t M, double* u,
                             cudaStream_t s)
 {
     k_finalize<<<grid_for(M, 256), 256, 0, s>>>(u_far, u_near, perm, M, u);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_batched(const SysDesc* sys, int nsys, const int64_t* moff, int64_t mtotal, double* u,
+                                    int64_t ntot, cudaStream_t s)
+{
+    k_finalize_batched<<<grid_for(mtotal, 256), 256, 0, s>>>(sys, nsys, moff, mtotal, u, ntot);
     note_launch();
     return cudaGetLastError();
 }
