@@ -41,6 +41,27 @@ def ncoef(n):
     return (n + 1) * (n + 2) * (n + 3) // 6
 
 
+def far_flops_per_interaction(p):
+    """Algorithmic flops of one (target, cluster) far-field interaction of the
+    far kernel (FMA = 2): the Coulomb recurrence on the harmonic subset k1 <= 1
+    (first product 1 flop, each further product an FMA, additions of the
+    second sum, the closing FMA) and the FP32 contraction (12 FMA per
+    coefficient, 12 FMA per level for the level factor, 18 for d'.B)."""
+    P = p + 2
+    rec = 0
+    ncoefs = 0
+    for n in range(1, P + 1):
+        for k1 in (0, 1):
+            for k3 in range(0, n - k1 + 1):
+                k2 = n - k1 - k3
+                t1 = sum(1 for v in (k1, k2, k3) if v >= 1)
+                t2 = sum(1 for v in (k2, k3) if v >= 2)
+                rec += (2 * t1 - 1) + max(t2 - 1, 0) + 2
+                ncoefs += 1
+    con = 24 * (ncoefs + 1) + 24 * P + 18
+    return float(rec), float(con)
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -376,13 +397,13 @@ def main():
     E = float(np.sqrt(np.sum((u_host[eidx] - ud) ** 2) / np.sum(ud ** 2)))
 
     # roofline of the dominant kernel (far field): algorithmic flops per launch
-    C2 = ncoef(p + 2)
     n_far = st["far_interactions"]
     fp64_rec = args.precision == "fp64" or p >= 8
     far_ms = ph.get("far")
     near_ms = ph.get("near")
-    rec_flops = 11.0 * C2 * n_far
-    con_flops = (24.0 * C2 + 18.0) * n_far
+    rec_unit, con_unit = far_flops_per_interaction(p)
+    rec_flops = rec_unit * n_far
+    con_flops = con_unit * n_far
     if fp64_rec:
         achieved = rec_flops / (far_ms / 1e3) / 1e12
         peak = PEAK_FP64_TFLOPS

@@ -12,17 +12,21 @@
 // turns the recurrence into
 //   c^k = sum_i w_i c^{k-e_i} - kappa_n sum_i c^{k-2e_i},
 //   kappa_n = (n-1)^2 / ((2n-1)(2n-3)),  c^0 = 1,
-// six FP64 operations per coefficient, all O(1) in magnitude.  The level
-// factor lambda_n R'^-(n+1) multiplies the level's 12 partial contractions.
+// all O(1) in magnitude.  The level factor lambda_n R'^-(n+1) multiplies the
+// level's 12 partial contractions.  Because the tables are folded onto the
+// harmonic subset k1 <= 1 (k_fold_tables: Laplace's equation expresses every
+// b^k with k1 >= 2 through coefficients of smaller k1 on the same level), only
+// the (P+1)^2 coefficients with k1 <= 1 are formed, at most five FP64
+// operations each, and the recurrence never needs any other.
 //
 // One warp handles a batch of 32 targets (one per lane) and walks the batch's
 // far list; a lane outside an entry's mask idles for that entry.  The
 // coefficients live in a per-warp shared-memory store of two slots laid out
 // [slot][position][lane] (no bank conflicts): level n overwrites level n-2 in
-// place, positions running downward, which is safe because coefficient k
+// place, positions running downward, which is safe because a coefficient
 // reads level n-2 only at positions <= its own.  Two coefficients are formed
 // per step for instruction-level parallelism.  Each coefficient is contracted
-// against the cluster's 12 table entries as soon as it exists.
+// against the cluster's 12 folded table entries as soon as it exists.
 //
 // Precision: TR is the recurrence type, TC the table/contraction type.
 // FP64 mode: TR = TC = double.  Mixed: TC = float, TR = double for p >= 8 and
@@ -47,9 +51,38 @@ __device__ inline void contract(TC c, const TC* __restrict__ t, TC* acc)
     for (int q = 0; q < 12; q++) acc[q] = fma(c, t[q], acc[q]);
 }
 
-// The far field of batch b (32 targets, one per lane) on one warp.  slot_p
-// holds the levels of the parity of P = p + 2 (size level_size(P) x 32) and
-// slot_q the others (level_size(P - 1) x 32).
+// One coefficient c^k of the harmonic subset (k1 <= 1) at level n, subset
+// position h (0..2n): k1 = 0 for h <= n (k3 = h), else k1 = 1 (k3 = h-n-1).
+// R1 holds level n-1 and R2 level n-2 of the subset, [position][lane].
+template <typename TR>
+__device__ inline TR hcoef(const TR* R1, const TR* R2, int n, int h, TR w0, TR w1, TR w2, TR kap, int lane)
+{
+    TR s1, s2 = 0;
+    if (h <= n) {  // k = (0, n - h, h)
+        const int k3 = h, k2 = n - h;
+        s1 = 0;
+        if (k2 >= 1) s1 = w1 * R1[k3 * 32 + lane];
+        if (k3 >= 1) s1 = fma(w2, R1[(k3 - 1) * 32 + lane], s1);
+        if (k2 >= 2) s2 = R2[k3 * 32 + lane];
+        if (k3 >= 2) s2 += R2[(k3 - 2) * 32 + lane];
+    } else {  // k = (1, n - 1 - k3, k3)
+        const int k3 = h - n - 1, k2 = n - 1 - k3;
+        s1 = w0 * R1[k3 * 32 + lane];
+        if (k2 >= 1) s1 = fma(w1, R1[(n + k3) * 32 + lane], s1);
+        if (k3 >= 1) s1 = fma(w2, R1[(n + k3 - 1) * 32 + lane], s1);
+        if (k2 >= 2) s2 = R2[(n - 1 + k3) * 32 + lane];
+        if (k3 >= 2) s2 += R2[(n - 3 + k3) * 32 + lane];
+    }
+    return fma(-kap, s2, s1);
+}
+
+// The far field of batch b (32 targets, one per lane) on one warp, with the
+// folded tables of the harmonic subset (tc_moments.cu, k_fold_tables): only
+// the (P+1)^2 coefficients with k1 <= 1 are formed, 2n+1 per level.  slot_p
+// holds the levels of the parity of P = p + 2 (2P+1 entries x 32 lanes) and
+// slot_q the others (2P-1 x 32); level n overwrites level n-2 in place,
+// positions running downward (a coefficient reads level n-2 only at
+// positions <= its own).
 template <typename TR, typename TC>
 __device__ inline void far_batch(const double* __restrict__ ts, int64_t M, const Geo* __restrict__ geo,
                                  const double* __restrict__ invrho, const TC* __restrict__ ab, int p,
@@ -57,7 +90,7 @@ __device__ inline void far_batch(const double* __restrict__ ts, int64_t M, const
                                  double* __restrict__ u_far, int64_t b, TR* slot_p, TR* slot_q, int lane)
 {
     const int P = p + 2;
-    const int C2 = ncoef(P);
+    const int H = hsize(P);
     const int64_t m = b * kBatch + lane;
     const bool valid = m < M;
     double x0 = 0, x1 = 0, x2 = 0;
@@ -78,7 +111,7 @@ __device__ inline void far_batch(const double* __restrict__ ts, int64_t M, const
         if (!in) R2 = 1.0;  // keep idle lanes finite
         const double iR = rsqrt(R2);
         const TR w0 = (TR)(d0 * iR), w1 = (TR)(d1 * iR), w2 = (TR)(d2 * iR);
-        const TC* __restrict__ tab = ab + (int64_t)le.node * C2 * 12;
+        const TC* __restrict__ tab = ab + (int64_t)le.node * H * 12;
         TC tot[12];
         TC scale = (TC)iR;  // lambda_0 R'^-1; level 0: c^0 = 1
 #pragma unroll
@@ -90,28 +123,23 @@ __device__ inline void far_batch(const double* __restrict__ ts, int64_t M, const
             scale *= (TC)(c_lev.ratio[n] * iR);
             TR* Rn = ((n ^ P) & 1) ? slot_q : slot_p;  // also holds level n-2
             const TR* R1 = ((n ^ P) & 1) ? slot_p : slot_q;
-            const TC* tl = tab + (int64_t)ncoef(n - 1) * 12;
+            const TC* tl = tab + (int64_t)n * n * 12;
             TC acc[12];
 #pragma unroll
             for (int q = 0; q < 12; q++) acc[q] = (TC)0;
-            for (int a = n; a >= 0; a--) {
-                const int k1 = n - a;
-                const int base = a * (a + 1) / 2;
-                int k3 = a;
-                for (; k3 >= 1; k3 -= 2) {
-                    const int pos = base + k3;
-                    const TR ca = coef<TR>(R1, Rn, pos, a, k1, a - k3, k3, w0, w1, w2, kap, lane);
-                    const TR cb = coef<TR>(R1, Rn, pos - 1, a, k1, a - k3 + 1, k3 - 1, w0, w1, w2, kap, lane);
-                    Rn[pos * 32 + lane] = ca;
-                    Rn[(pos - 1) * 32 + lane] = cb;
-                    contract<TC>(to_tc<TR, TC>(ca), tl + pos * 12, acc);
-                    contract<TC>(to_tc<TR, TC>(cb), tl + (pos - 1) * 12, acc);
-                }
-                if (k3 == 0) {
-                    const TR ca = coef<TR>(R1, Rn, base, a, k1, a, 0, w0, w1, w2, kap, lane);
-                    Rn[base * 32 + lane] = ca;
-                    contract<TC>(to_tc<TR, TC>(ca), tl + base * 12, acc);
-                }
+            int h = 2 * n;
+            for (; h >= 1; h -= 2) {
+                const TR ca = hcoef<TR>(R1, Rn, n, h, w0, w1, w2, kap, lane);
+                const TR cb = hcoef<TR>(R1, Rn, n, h - 1, w0, w1, w2, kap, lane);
+                Rn[h * 32 + lane] = ca;
+                Rn[(h - 1) * 32 + lane] = cb;
+                contract<TC>(to_tc<TR, TC>(ca), tl + h * 12, acc);
+                contract<TC>(to_tc<TR, TC>(cb), tl + (h - 1) * 12, acc);
+            }
+            if (h == 0) {
+                const TR ca = hcoef<TR>(R1, Rn, n, 0, w0, w1, w2, kap, lane);
+                Rn[lane] = ca;
+                contract<TC>(to_tc<TR, TC>(ca), tl, acc);
             }
             __syncwarp();
 #pragma unroll
@@ -134,12 +162,15 @@ __device__ inline void far_batch(const double* __restrict__ ts, int64_t M, const
     }
 }
 
+// per-warp coefficient store: 2P+1 and 2P-1 entries (P = p + 2) of 32 lanes
+__host__ __device__ inline size_t far_store_entries(int p) { return (size_t)4 * (p + 2); }
+
 template <typename TR>
 __device__ inline void far_slots(unsigned char* smraw, int p, int w, TR*& slot_p, TR*& slot_q)
 {
-    const int LSP = level_size(p + 2), LSQ = level_size(p + 1);
-    slot_p = reinterpret_cast<TR*>(smraw) + (size_t)w * (LSP + LSQ) * 32;
-    slot_q = slot_p + (size_t)LSP * 32;
+    const int P = p + 2;
+    slot_p = reinterpret_cast<TR*>(smraw) + (size_t)w * far_store_entries(p) * 32;
+    slot_q = slot_p + (size_t)(2 * P + 1) * 32;
 }
 
 template <typename TR, typename TC>
@@ -192,7 +223,7 @@ template <typename TR, typename TC>
 cudaError_t run_far_batched(const SysDesc* sys, int nsys, const int64_t* item_off, int64_t nitems, int p,
                             unsigned long long* counter, int warps_per_block, int blocks, cudaStream_t s)
 {
-    size_t smem = (size_t)warps_per_block * (level_size(p + 2) + level_size(p + 1)) * 32 * sizeof(TR);
+    size_t smem = (size_t)warps_per_block * far_store_entries(p) * 32 * sizeof(TR);
     cudaError_t e =
         cudaFuncSetAttribute(k_far_batched<TR, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -216,7 +247,7 @@ cudaError_t run_far(const double* ts, int64_t M, const Geo* geo, const double* i
 {
     int64_t nbatch = (M + kBatch - 1) / kBatch;
     unsigned grid = (unsigned)((nbatch + kFarWarps - 1) / kFarWarps);
-    size_t smem = (size_t)kFarWarps * (level_size(p + 2) + level_size(p + 1)) * 32 * sizeof(TR);
+    size_t smem = (size_t)kFarWarps * far_store_entries(p) * 32 * sizeof(TR);
     cudaError_t e = cudaFuncSetAttribute(k_far<TR, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_far<TR, TC><<<grid, kFarWarps * 32, smem, s>>>(ts, M, geo, invrho, ab, p, far_off, far_list, u_far);

@@ -118,6 +118,7 @@ struct tc_ctx {
     int ab_p = -1;                      // order the contraction tables were built for
     tc::DevBuf ab64;                    // FP64 [node][ncoef(p+2)][12]
     tc::DevBuf ab32;                    // FP32 [node][ncoef(p+2)][12]
+    tc::DevBuf abf64, abf32;            // folded tables [node][(p+3)^2][12]
 
     // ---- evaluation (tc_eval)
     int64_t M = 0;
@@ -202,6 +203,13 @@ cudaError_t launch_moments(const int4* topo, const Geo* geo, const double* xs, c
 cudaError_t launch_m2m(const int4* topo, const Geo* geo, int64_t lb, int64_t le, int p, double* mom, cudaStream_t s);
 cudaError_t launch_ab_tables(const double* mom, const double* invrho, int64_t nnodes, int pm, int p, double* ab64,
                              float* ab32, cudaStream_t s);
+cudaError_t launch_fold_tables(const double* ab64, int64_t nnodes, int p, double* abf64, float* abf32,
+                               cudaStream_t s);
+
+// Subset of multi-indices with k1 <= 1 ("harmonic basis"): level n has 2n+1
+// of them, level n starts at n^2; inside a level, (0, n-k3, k3) is at k3 and
+// (1, n-1-k3, k3) at n+1+k3.
+__host__ __device__ constexpr int hsize(int P) { return (P + 1) * (P + 1); }
 
 // tc_lists.cu
 cudaError_t launch_lists(const double* ts, int64_t M, const int4* topo, const Geo* geo, double theta,

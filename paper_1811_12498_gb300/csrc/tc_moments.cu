@@ -305,6 +305,66 @@ __global__ void k_ab_tables(const double* __restrict__ mom, const double* __rest
         for (int c = 0; c < 12; c++) ab32[o + c] = (float)out[c];
 }
 
+// Harmonic folding of the tables.  The b^k are the Taylor coefficients of
+// 1/|d - t| in t, a harmonic function, so (Laplace's equation)
+//   sum_i (k_i + 2)(k_i + 1) b^{k + 2 e_i} = 0,
+// i.e. within a level every b^k with k1 >= 2 is
+//   b^k = -[(k2+2)(k2+1) b^{k-2e1+2e2} + (k3+2)(k3+1) b^{k-2e1+2e3}] / (k1 (k1-1)).
+// Substituting this row by row, from k1 = n down to 2, into sum_k b^k T^k
+// moves each table entry with k1 >= 2 onto two entries with k1 smaller by 2;
+// at the end only k1 in {0, 1} carry weight, and
+//   sum_{|k| <= P} b^k T^k = sum_{|k| <= P, k1 <= 1} b^k T'^k
+// exactly, for every d.  The far field then needs the (P+1)^2 coefficients
+// with k1 <= 1 only (2n+1 per level instead of (n+1)(n+2)/2), and those obey
+// recurrence (3.2) among themselves (it never raises k1).  One block per
+// cluster; the folding is done in FP64 and then stored in the working type.
+__global__ void k_fold_tables(const double* __restrict__ ab64, int64_t nnodes, int p, double* __restrict__ abf64,
+                              float* __restrict__ abf32)
+{
+    extern __shared__ double lv[];  // one level: [position][12]
+    const int64_t node = blockIdx.x;
+    const int P = p + 2;
+    const int C2 = ncoef(P), H = hsize(P);
+    for (int n = 0; n <= P; n++) {
+        const int L = level_size(n);
+        const int base = n > 0 ? ncoef(n - 1) : 0;
+        for (int q = threadIdx.x; q < L * 12; q += blockDim.x) lv[q] = ab64[((int64_t)node * C2 + base) * 12 + q];
+        __syncthreads();
+        for (int k1 = n; k1 >= 2; k1--) {
+            const int a = n - k1;  // row k1 holds positions a(a+1)/2 + k3, k3 = 0..a
+            const double inv = 1.0 / ((double)k1 * (k1 - 1));
+            // pushes along e2, then along e3 (each phase writes distinct entries)
+            for (int ph = 0; ph < 2; ph++) {
+                for (int q = threadIdx.x; q < (a + 1) * 12; q += blockDim.x) {
+                    const int k3 = q / 12, c = q % 12, k2 = a - k3;
+                    const int src = a * (a + 1) / 2 + k3;
+                    const int a2 = a + 2;
+                    int dst;
+                    double fct;
+                    if (ph == 0) {
+                        dst = a2 * (a2 + 1) / 2 + k3;  // (k1-2, k2+2, k3)
+                        fct = -(double)((k2 + 2) * (k2 + 1)) * inv;
+                    } else {
+                        dst = a2 * (a2 + 1) / 2 + k3 + 2;  // (k1-2, k2, k3+2)
+                        fct = -(double)((k3 + 2) * (k3 + 1)) * inv;
+                    }
+                    lv[dst * 12 + c] += fct * lv[src * 12 + c];
+                }
+                __syncthreads();
+            }
+        }
+        // keep k1 = 0 (positions n(n+1)/2 + k3) and k1 = 1 ((n-1)n/2 + k3)
+        for (int q = threadIdx.x; q < (2 * n + 1) * 12; q += blockDim.x) {
+            const int h = q / 12, c = q % 12;
+            const int src = h <= n ? n * (n + 1) / 2 + h : (n - 1) * n / 2 + (h - n - 1);
+            const int64_t o = ((int64_t)node * H + n * n + h) * 12 + c;
+            if (abf64) abf64[o] = lv[src * 12 + c];
+            if (abf32) abf32[o] = (float)lv[src * 12 + c];
+        }
+        __syncthreads();
+    }
+}
+
 inline unsigned grid_for(int64_t n, int threads)
 {
     int64_t g = (n + threads - 1) / threads;
@@ -340,6 +400,17 @@ cudaError_t launch_m2m(const int4* topo, const Geo* geo, int64_t lb, int64_t le,
 {
     if (le <= lb) return cudaSuccess;
     k_m2m<<<(unsigned)(le - lb), kMomThreads, 0, s>>>(topo, geo, lb, le, p, mom);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fold_tables(const double* ab64, int64_t nnodes, int p, double* abf64, float* abf32,
+                               cudaStream_t s)
+{
+    const size_t smem = (size_t)level_size(p + 2) * 12 * sizeof(double);
+    cudaError_t e = cudaFuncSetAttribute(k_fold_tables, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_fold_tables<<<(unsigned)nnodes, 128, smem, s>>>(ab64, nnodes, p, abf64, abf32);
     note_launch();
     return cudaGetLastError();
 }
