@@ -113,7 +113,7 @@ static void release_all(tc_ctx* c)
     DevBuf* bufs[] = {&c->root, &c->bbox_part, &c->keys, &c->keys_alt, &c->perm, &c->perm_alt, &c->hist, &c->xs,
                       &c->node_topo, &c->node_info, &c->node_key, &c->node_geo, &c->node_invrho, &c->split_cnt,
                       &c->split_off, &c->scan_tmp, &c->ws, &c->spack, &c->mom, &c->ab64, &c->ab32, &c->abf64,
-                      &c->abf32, &c->tkeys,
+                      &c->abf32, &c->geo32, &c->tkeys,
                       &c->tkeys_alt, &c->tperm, &c->tperm_alt, &c->ts, &c->nfar_e, &c->nnear_e,
                       &c->far_off, &c->near_off, &c->far_list, &c->near_list, &c->cnt_far, &c->cnt_near, &c->u_far,
                       &c->u_near, &c->flags, &c->adj_fkeys, &c->adj_fkeys_alt, &c->adj_fidx, &c->adj_fidx_alt,
@@ -354,6 +354,7 @@ static tc_status ensure_tables(tc_ctx* ctx, int p)
         TC_CK(ensure(ctx->ab32, (size_t)n * 4), "alloc tables");
         ab32 = ptr<float>(ctx->ab32);
         TC_CK(ensure(ctx->abf32, (size_t)nf * 4), "alloc tables");
+        TC_CK(ensure(ctx->geo32, (size_t)ctx->nnodes * 2 * sizeof(float4)), "alloc tables");
     } else {
         TC_CK(ensure(ctx->abf64, (size_t)nf * 8), "alloc tables");
     }
@@ -363,7 +364,9 @@ static tc_status ensure_tables(tc_ctx* ctx, int p)
           "tables");
     TC_CK(launch_fold_tables(ptr<double>(ctx->ab64), ctx->nnodes, p,
                              ctx->precision == TC_FP64 ? ptr<double>(ctx->abf64) : nullptr,
-                             ctx->precision == TC_FP64 ? nullptr : ptr<float>(ctx->abf32), s),
+                             ctx->precision == TC_FP64 ? nullptr : ptr<float>(ctx->abf32),
+                             ptr<Geo>(ctx->node_geo), ptr<double>(ctx->node_invrho),
+                             ctx->precision == TC_FP64 ? nullptr : ptr<float4>(ctx->geo32), s),
           "fold tables");
     ph_end(ctx, TC_PH_TABLES);
     ctx->ab_p = p;
@@ -467,7 +470,8 @@ tc_status tc::eval_compute(tc_ctx* ctx, double* u)
     const int32_t* tperm = ctx->eval_self ? ptr<int32_t>(ctx->perm) : ptr<int32_t>(ctx->tperm);
     ph_begin(ctx, TC_PH_FAR);
     TC_CK(launch_far(ctx->precision, ts, M, ptr<Geo>(ctx->node_geo), ptr<double>(ctx->node_invrho),
-                     ptr<double>(ctx->abf64), ptr<float>(ctx->abf32), p, ptr<int64_t>(ctx->far_off),
+                     ptr<float4>(ctx->geo32), ptr<double>(ctx->abf64), ptr<float>(ctx->abf32), p,
+                     ptr<int64_t>(ctx->far_off),
                      ptr<ListEntry>(ctx->far_list), ptr<double>(ctx->u_far), s),
           "far field");
     ph_end(ctx, TC_PH_FAR);

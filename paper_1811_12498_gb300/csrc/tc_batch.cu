@@ -364,6 +364,7 @@ tc_status tc_batch_eval(tc_batch* b, double theta, int32_t p, double* u)
         d.geo = ptr<Geo>(c->node_geo);
         d.invrho = ptr<double>(c->node_invrho);
         d.ab = c->precision == TC_FP64 ? c->abf64.p : c->abf32.p;  // folded tables
+        d.geo32 = ptr<float4>(c->geo32);
         d.far_off = ptr<int64_t>(c->far_off);
         d.far_list = ptr<ListEntry>(c->far_list);
         d.u_far = ptr<double>(c->u_far);

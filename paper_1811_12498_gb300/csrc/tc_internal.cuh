@@ -62,7 +62,8 @@ struct SysDesc {
     int64_t M;
     const Geo* geo;
     const double* invrho;
-    const void* ab;            // contraction tables (double or float)
+    const void* ab;            // folded contraction tables (double or float)
+    const float4* geo32;       // FP32 cluster geometry of the mixed far kernel
     const int64_t* far_off;
     const ListEntry* far_list;
     double* u_far;
@@ -118,7 +119,8 @@ struct tc_ctx {
     int ab_p = -1;                      // order the contraction tables were built for
     tc::DevBuf ab64;                    // FP64 [node][ncoef(p+2)][12]
     tc::DevBuf ab32;                    // FP32 [node][ncoef(p+2)][12]
-    tc::DevBuf abf64, abf32;            // folded tables [node][(p+3)^2][12]
+    tc::DevBuf abf64, abf32;            // folded tables [node][(p+3)^2][12], level n times lambda_n
+    tc::DevBuf geo32;                   // mixed: per node (y_c hi, 1/rho), (y_c lo, 0) as float4
 
     // ---- evaluation (tc_eval)
     int64_t M = 0;
@@ -204,7 +206,7 @@ cudaError_t launch_m2m(const int4* topo, const Geo* geo, int64_t lb, int64_t le,
 cudaError_t launch_ab_tables(const double* mom, const double* invrho, int64_t nnodes, int pm, int p, double* ab64,
                              float* ab32, cudaStream_t s);
 cudaError_t launch_fold_tables(const double* ab64, int64_t nnodes, int p, double* abf64, float* abf32,
-                               cudaStream_t s);
+                               const Geo* geo, const double* invrho, float4* geo32, cudaStream_t s);
 
 // Subset of multi-indices with k1 <= 1 ("harmonic basis"): level n has 2n+1
 // of them, level n starts at n^2; inside a level, (0, n-k3, k3) is at k3 and
@@ -223,7 +225,7 @@ cudaError_t launch_sum_entry_sizes(const ListEntry* list, int64_t n, const int4*
 
 // tc_far.cu
 cudaError_t launch_far(int precision, const double* ts, int64_t M, const Geo* geo, const double* invrho,
-                       const double* ab64, const float* ab32, int p, const int64_t* far_off,
+                       const float4* geo32, const double* ab64, const float* ab32, int p, const int64_t* far_off,
                        const ListEntry* far_list, double* u_far, cudaStream_t s);
 
 cudaError_t launch_far_batched(int precision, const SysDesc* sys, int nsys, const int64_t* item_off, int64_t nitems,

@@ -317,15 +317,29 @@ __global__ void k_ab_tables(const double* __restrict__ mom, const double* __rest
 // exactly, for every d.  The far field then needs the (P+1)^2 coefficients
 // with k1 <= 1 only (2n+1 per level instead of (n+1)(n+2)/2), and those obey
 // recurrence (3.2) among themselves (it never raises k1).  One block per
-// cluster; the folding is done in FP64 and then stored in the working type.
+// cluster; the folding is done in FP64 and then stored in the working type,
+// level n multiplied by lambda_n = prod_{j<=n} (2j-1)/j, the factor that the
+// far kernels' scale-free recurrence leaves out (tc_far.cu).  In mixed
+// precision the block also writes the cluster's FP32 geometry for the far
+// kernel: (y_c hi, 1/rho) and (y_c lo, 0), hi = fl32(y_c), lo = fl32(y_c - hi).
 __global__ void k_fold_tables(const double* __restrict__ ab64, int64_t nnodes, int p, double* __restrict__ abf64,
-                              float* __restrict__ abf32)
+                              float* __restrict__ abf32, const Geo* __restrict__ geo,
+                              const double* __restrict__ invrho, float4* __restrict__ geo32)
 {
     extern __shared__ double lv[];  // one level: [position][12]
     const int64_t node = blockIdx.x;
     const int P = p + 2;
     const int C2 = ncoef(P), H = hsize(P);
+    if (geo32 && threadIdx.x == 0) {
+        const Geo g = geo[node];
+        const float hx = __double2float_rn(g.x), hy = __double2float_rn(g.y), hz = __double2float_rn(g.z);
+        geo32[2 * node] = make_float4(hx, hy, hz, __double2float_rn(invrho[node]));
+        geo32[2 * node + 1] = make_float4(__double2float_rn(g.x - (double)hx), __double2float_rn(g.y - (double)hy),
+                                          __double2float_rn(g.z - (double)hz), 0.0f);
+    }
+    double lambda = 1.0;  // lambda_n
     for (int n = 0; n <= P; n++) {
+        if (n > 0) lambda *= (double)(2 * n - 1) / (double)n;
         const int L = level_size(n);
         const int base = n > 0 ? ncoef(n - 1) : 0;
         for (int q = threadIdx.x; q < L * 12; q += blockDim.x) lv[q] = ab64[((int64_t)node * C2 + base) * 12 + q];
@@ -358,8 +372,9 @@ __global__ void k_fold_tables(const double* __restrict__ ab64, int64_t nnodes, i
             const int h = q / 12, c = q % 12;
             const int src = h <= n ? n * (n + 1) / 2 + h : (n - 1) * n / 2 + (h - n - 1);
             const int64_t o = ((int64_t)node * H + n * n + h) * 12 + c;
-            if (abf64) abf64[o] = lv[src * 12 + c];
-            if (abf32) abf32[o] = (float)lv[src * 12 + c];
+            const double v = lambda * lv[src * 12 + c];
+            if (abf64) abf64[o] = v;
+            if (abf32) abf32[o] = (float)v;
         }
         __syncthreads();
     }
@@ -405,12 +420,12 @@ cudaError_t launch_m2m(const int4* topo, const Geo* geo, int64_t lb, int64_t le,
 }
 
 cudaError_t launch_fold_tables(const double* ab64, int64_t nnodes, int p, double* abf64, float* abf32,
-                               cudaStream_t s)
+                               const Geo* geo, const double* invrho, float4* geo32, cudaStream_t s)
 {
     const size_t smem = (size_t)level_size(p + 2) * 12 * sizeof(double);
     cudaError_t e = cudaFuncSetAttribute(k_fold_tables, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_fold_tables<<<(unsigned)nnodes, 128, smem, s>>>(ab64, nnodes, p, abf64, abf32);
+    k_fold_tables<<<(unsigned)nnodes, 128, smem, s>>>(ab64, nnodes, p, abf64, abf32, geo, invrho, geo32);
     note_launch();
     return cudaGetLastError();
 }
