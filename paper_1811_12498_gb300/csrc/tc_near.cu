@@ -3,15 +3,21 @@
 //   u_i += f_i / r + d_i (s + t),  s = (d.f) / r^3,  t = (d.h)(d.nu) / r^5,
 // d = x - y, skipping pairs with r == 0 (the n != m exclusion of eq. 1.3).
 //
-// One warp handles a batch of 32 targets and walks the batch's near list.
 // Sources are streamed through a per-warp shared-memory tile of 32 records
 // (one coalesced load per lane, then broadcast reads).
 //
 // Mixed precision: positions are split as x = hi + lo (both FP32) and
 // d = (x_hi - y_hi) + (x_lo - y_lo), so d keeps FP32 relative accuracy even
 // for close pairs; pair terms are FP32; each 32-source tile's partial sum
-// is added to an FP64 per-target accumulator.  FP64 mode computes everything
-// in FP64.
+// is added to an FP64 per-target accumulator.  One warp handles two
+// consecutive batches (64 targets, two per lane) and walks the merge of their
+// two near lists (both are in tree order, i.e. by the leaf's first source), so
+// a leaf that both batches need is staged once and every broadcast source
+// value feeds two targets.  The tile holds the sources in pairs, field by
+// field ((y_2q.f, y_2q+1.f) adjacent), and the pair terms run on packed
+// FP32x2 arithmetic, two sources per instruction.
+//
+// FP64 mode computes everything in FP64, one batch per warp.
 #include "tc_internal.cuh"
 
 namespace tc {
@@ -21,70 +27,197 @@ namespace {
 constexpr int kNearWarps = 4;
 constexpr int kNearMaxWarps = 8;  // largest block the batched kernel accepts
 
-// Mixed-precision near field of batch b on one warp; tw is the warp's tile
-// of 32 source records (4 float4 each).
-__device__ inline void near_batch_mixed(const double* __restrict__ ts, int64_t M, const int4* __restrict__ topo,
-                                        const float4* __restrict__ spack, const int64_t* __restrict__ near_off,
-                                        const ListEntry* __restrict__ near_list, double* __restrict__ u_near,
-                                        int64_t b, float4* tw, int lane)
+// ---------------------------------------------------------------------------
+// mixed precision: packed FP32x2 arithmetic
+
+__device__ __forceinline__ float2 sub2(float2 a, float2 b)
 {
-    const int64_t m = b * kBatch + lane;
-    const bool valid = m < M;
-    float th[3] = {0, 0, 0}, tl[3] = {0, 0, 0};
-    if (valid) {
-        for (int a = 0; a < 3; a++) {
-            double v = ts[a * M + m];
-            th[a] = (float)v;
-            tl[a] = (float)(v - (double)th[a]);
-        }
+    float2 r;
+    asm("{\n\t.reg .b64 ta, tb, td;\n\tmov.b64 ta, {%2, %3};\n\tmov.b64 tb, {%4, %5};\n\t"
+        "sub.rn.f32x2 td, ta, tb;\n\tmov.b64 {%0, %1}, td;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+
+// A source record is 16 FP32 fields: x_hi (3), f0, x_lo (3), f1, f2, h (3),
+// nu (3), pad.  The tile stores source pair q (sources 2q, 2q+1) as 8 float4,
+// float4 k = (y_2q.f_2k, y_2q+1.f_2k, y_2q.f_2k+1, y_2q+1.f_2k+1), with a
+// stride of 9 float4 per pair so that the staging stores are free of bank
+// conflicts.
+constexpr int kPairStride = 9;
+constexpr int kTileFloat4 = 16 * kPairStride;
+
+// Stage sources [base, base + cnt), cnt <= 32, into the tile.  Lanes past cnt
+// contribute a source at 1e30 with zero weights (its terms are exactly 0:
+// r^2 overflows to inf, 1/r = 0, and every weight is 0).
+__device__ inline void stage_pairs(const float4* __restrict__ spack, int64_t base, int cnt, float4* tw, int lane)
+{
+    float f[16];
+    if (lane < cnt) {
+        const float4* src = spack + 4 * (base + lane);
+        const float4 a = src[0], b = src[1], c = src[2], d = src[3];
+        f[0] = a.x, f[1] = a.y, f[2] = a.z, f[3] = a.w;
+        f[4] = b.x, f[5] = b.y, f[6] = b.z, f[7] = b.w;
+        f[8] = c.x, f[9] = c.y, f[10] = c.z, f[11] = c.w;
+        f[12] = d.x, f[13] = d.y, f[14] = d.z, f[15] = d.w;
+    } else {
+#pragma unroll
+        for (int k = 0; k < 16; k++) f[k] = k < 3 ? 1e30f : 0.0f;
     }
-    double ux = 0.0, uy = 0.0, uz = 0.0;
-    const int64_t e0 = near_off[b], e1 = near_off[b + 1];
-    for (int64_t e = e0; e < e1; e++) {
-        const ListEntry le = near_list[e];
-        const bool in = (le.mask >> lane) & 1u;
-        const int4 t = topo[le.node];
+    const int par = lane & 1;
+    float recv[8];
+#pragma unroll
+    for (int k = 0; k < 8; k++) recv[k] = __shfl_xor_sync(0xffffffffu, par ? f[k] : f[8 + k], 1);
+    float4* dst = tw + (lane >> 1) * kPairStride;
+    if (!par) {
+#pragma unroll
+        for (int j = 0; j < 4; j++) dst[j] = make_float4(f[2 * j], recv[2 * j], f[2 * j + 1], recv[2 * j + 1]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+            dst[4 + j] = make_float4(recv[2 * j], f[8 + 2 * j], recv[2 * j + 1], f[9 + 2 * j]);
+    }
+}
+
+// one target, replicated into both halves of each pair
+struct Tgt2 {
+    float2 h0, h1, h2, l0, l1, l2;
+};
+
+__device__ inline Tgt2 load_target(const double* __restrict__ ts, int64_t M, int64_t m, bool valid)
+{
+    float h[3] = {0, 0, 0}, l[3] = {0, 0, 0};
+    if (valid)
+        for (int a = 0; a < 3; a++) {
+            const double v = ts[a * M + m];
+            h[a] = __double2float_rn(v);
+            l[a] = __double2float_rn(v - (double)h[a]);
+        }
+    Tgt2 t;
+    t.h0 = make_float2(h[0], h[0]), t.h1 = make_float2(h[1], h[1]), t.h2 = make_float2(h[2], h[2]);
+    t.l0 = make_float2(l[0], l[0]), t.l1 = make_float2(l[1], l[1]), t.l2 = make_float2(l[2], l[2]);
+    return t;
+}
+
+// Stokeslet + stresslet terms of one target against source pair tp, both
+// sources at once
+__device__ __forceinline__ void pair_terms(const Tgt2& t, const float4* tp, float2& ax, float2& ay, float2& az)
+{
+    const float4 A = tp[0], B = tp[1], C = tp[2], D = tp[3], E = tp[4], F = tp[5], G = tp[6], Q = tp[7];
+    const float2 dx = __fadd2_rn(sub2(t.h0, make_float2(A.x, A.y)), sub2(t.l0, make_float2(C.x, C.y)));
+    const float2 dy = __fadd2_rn(sub2(t.h1, make_float2(A.z, A.w)), sub2(t.l1, make_float2(C.z, C.w)));
+    const float2 dz = __fadd2_rn(sub2(t.h2, make_float2(B.x, B.y)), sub2(t.l2, make_float2(D.x, D.y)));
+    const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+    float2 ri;
+    ri.x = r2.x > 0.f ? rsqrtf(r2.x) : 0.f;
+    ri.y = r2.y > 0.f ? rsqrtf(r2.y) : 0.f;
+    const float2 ri2 = __fmul2_rn(ri, ri);
+    const float2 ri3 = __fmul2_rn(ri2, ri);
+    const float2 f0 = make_float2(B.z, B.w), f1 = make_float2(D.z, D.w), f2 = make_float2(E.x, E.y);
+    const float2 df = __ffma2_rn(dx, f0, __ffma2_rn(dy, f1, __fmul2_rn(dz, f2)));
+    const float2 dh = __ffma2_rn(dx, make_float2(E.z, E.w),
+                                 __ffma2_rn(dy, make_float2(F.x, F.y), __fmul2_rn(dz, make_float2(F.z, F.w))));
+    const float2 dn = __ffma2_rn(dx, make_float2(G.x, G.y),
+                                 __ffma2_rn(dy, make_float2(G.z, G.w), __fmul2_rn(dz, make_float2(Q.x, Q.y))));
+    const float2 st = __fmul2_rn(ri3, __ffma2_rn(__fmul2_rn(dh, dn), ri2, df));
+    ax = __ffma2_rn(f0, ri, __ffma2_rn(dx, st, ax));
+    ay = __ffma2_rn(f1, ri, __ffma2_rn(dy, st, ay));
+    az = __ffma2_rn(f2, ri, __ffma2_rn(dz, st, az));
+}
+
+// Near field of batches 2B and 2B+1 (the second may not exist) on one warp;
+// tw is the warp's tile of kTileFloat4 float4.
+__device__ inline void near_pair_mixed(const double* __restrict__ ts, int64_t M, const int4* __restrict__ topo,
+                                       const float4* __restrict__ spack, const int64_t* __restrict__ near_off,
+                                       const ListEntry* __restrict__ near_list, double* __restrict__ u_near,
+                                       int64_t B, float4* tw, int lane)
+{
+    const int64_t nbatch = (M + kBatch - 1) / kBatch;
+    const int64_t ba = 2 * B, bb = 2 * B + 1;
+    const int64_t ma = ba * kBatch + lane, mb = bb * kBatch + lane;
+    const bool va = ma < M, vb = mb < M;
+    const Tgt2 ta = load_target(ts, M, ma, va), tb = load_target(ts, M, mb, vb);
+    double ua0 = 0, ua1 = 0, ua2 = 0, ub0 = 0, ub1 = 0, ub2 = 0;
+    int64_t ia = near_off[ba], ea = near_off[ba + 1], ib = 0, eb = 0;
+    if (bb < nbatch) {
+        ib = near_off[bb];
+        eb = near_off[bb + 1];
+    }
+    constexpr int kEnd = 0x7fffffff;
+    ListEntry la{0, 0}, lb{0, 0};
+    int4 qa = make_int4(kEnd, 0, 0, 0), qb = make_int4(kEnd, 0, 0, 0);
+    if (ia < ea) {
+        la = near_list[ia];
+        qa = topo[la.node];
+    }
+    if (ib < eb) {
+        lb = near_list[ib];
+        qb = topo[lb.node];
+    }
+    while (ia < ea || ib < eb) {
+        // merge by the leaf's first source; equal keys are the same leaf
+        const bool takeA = ia < ea && qa.x <= qb.x;
+        const bool takeB = ib < eb && (qb.x < qa.x || (qb.x == qa.x && lb.node == la.node));
+        const int4 t = takeA ? qa : qb;
+        const unsigned mA = takeA ? la.mask : 0u, mB = takeB ? lb.mask : 0u;
+        const bool inA = (mA >> lane) & 1u, inB = (mB >> lane) & 1u;
         for (int base = t.x; base < t.x + t.y; base += 32) {
             const int cnt = min(32, t.x + t.y - base);
             __syncwarp();
-            if (lane < cnt) {
-                const float4* src = spack + 4 * (int64_t)(base + lane);
-                tw[lane * 4 + 0] = src[0];
-                tw[lane * 4 + 1] = src[1];
-                tw[lane * 4 + 2] = src[2];
-                tw[lane * 4 + 3] = src[3];
-            }
+            stage_pairs(spack, base, cnt, tw, lane);
             __syncwarp();
-            if (!in) continue;
-            float ax = 0.f, ay = 0.f, az = 0.f;
-            for (int j = 0; j < cnt; j++) {
-                const float4 p0 = tw[j * 4 + 0], p1 = tw[j * 4 + 1], p2 = tw[j * 4 + 2], p3 = tw[j * 4 + 3];
-                const float dx = (th[0] - p0.x) + (tl[0] - p1.x);
-                const float dy = (th[1] - p0.y) + (tl[1] - p1.y);
-                const float dz = (th[2] - p0.z) + (tl[2] - p1.z);
-                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                const float ri = r2 > 0.f ? rsqrtf(r2) : 0.f;
-                const float ri2 = ri * ri;
-                const float ri3 = ri2 * ri;
-                const float df = fmaf(dx, p0.w, fmaf(dy, p1.w, dz * p2.x));
-                const float dh = fmaf(dx, p2.y, fmaf(dy, p2.z, dz * p2.w));
-                const float dn = fmaf(dx, p3.x, fmaf(dy, p3.y, dz * p3.z));
-                const float st = ri3 * fmaf(dh * dn, ri2, df);
-                ax = fmaf(p0.w, ri, fmaf(dx, st, ax));
-                ay = fmaf(p1.w, ri, fmaf(dy, st, ay));
-                az = fmaf(p2.x, ri, fmaf(dz, st, az));
+            const int npairs = (cnt + 1) >> 1;
+            float2 axa = make_float2(0.f, 0.f), aya = axa, aza = axa, axb = axa, ayb = axa, azb = axa;
+            if (mA && mB) {
+                for (int q = 0; q < npairs; q++) {
+                    const float4* tp = tw + q * kPairStride;
+                    pair_terms(ta, tp, axa, aya, aza);
+                    pair_terms(tb, tp, axb, ayb, azb);
+                }
+            } else if (mA) {
+                for (int q = 0; q < npairs; q++) pair_terms(ta, tw + q * kPairStride, axa, aya, aza);
+            } else {
+                for (int q = 0; q < npairs; q++) pair_terms(tb, tw + q * kPairStride, axb, ayb, azb);
             }
-            ux += (double)ax;
-            uy += (double)ay;
-            uz += (double)az;
+            if (inA) {
+                ua0 += (double)(axa.x + axa.y);
+                ua1 += (double)(aya.x + aya.y);
+                ua2 += (double)(aza.x + aza.y);
+            }
+            if (inB) {
+                ub0 += (double)(axb.x + axb.y);
+                ub1 += (double)(ayb.x + ayb.y);
+                ub2 += (double)(azb.x + azb.y);
+            }
+        }
+        if (takeA && ++ia < ea) {
+            la = near_list[ia];
+            qa = topo[la.node];
+        } else if (takeA) {
+            qa.x = kEnd;
+        }
+        if (takeB && ++ib < eb) {
+            lb = near_list[ib];
+            qb = topo[lb.node];
+        } else if (takeB) {
+            qb.x = kEnd;
         }
     }
-    if (valid) {
-        u_near[m] = ux;
-        u_near[M + m] = uy;
-        u_near[2 * M + m] = uz;
+    if (va) {
+        u_near[ma] = ua0;
+        u_near[M + ma] = ua1;
+        u_near[2 * M + ma] = ua2;
+    }
+    if (vb) {
+        u_near[mb] = ub0;
+        u_near[M + mb] = ub1;
+        u_near[2 * M + mb] = ub2;
     }
 }
+
+// ---------------------------------------------------------------------------
+// FP64
 
 // FP64 near field of batch b on one warp; tw is the warp's tile [12][32].
 __device__ inline void near_batch_fp64(const double* __restrict__ ts, int64_t M, const int4* __restrict__ topo,
@@ -141,12 +274,12 @@ __global__ void __launch_bounds__(kNearWarps * 32)
                  const float4* __restrict__ spack, const int64_t* __restrict__ near_off,
                  const ListEntry* __restrict__ near_list, double* __restrict__ u_near)
 {
-    __shared__ float4 tile[kNearWarps][32 * 4];
+    __shared__ float4 tile[kNearWarps][kTileFloat4];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t nbatch = (M + kBatch - 1) / kBatch;
-    const int64_t b = blockIdx.x * (int64_t)kNearWarps + w;
-    if (b >= nbatch) return;
-    near_batch_mixed(ts, M, topo, spack, near_off, near_list, u_near, b, tile[w], lane);
+    const int64_t nsuper = ((M + kBatch - 1) / kBatch + 1) / 2;
+    const int64_t B = blockIdx.x * (int64_t)kNearWarps + w;
+    if (B >= nsuper) return;
+    near_pair_mixed(ts, M, topo, spack, near_off, near_list, u_near, B, tile[w], lane);
 }
 
 __global__ void __launch_bounds__(kNearWarps * 32)
@@ -163,13 +296,16 @@ __global__ void __launch_bounds__(kNearWarps * 32)
     near_batch_fp64(ts, M, topo, xs, ws, N, near_off, near_list, u_near, b, tile[w], lane);
 }
 
-// Persistent near-field kernel over many systems (see k_far_batched).
+// Persistent near-field kernel over many systems (see k_far32_batched).  An
+// item is a batch in FP64 mode and a pair of batches in mixed precision
+// (item_off counts accordingly).
 template <bool kFp64>
 __global__ void __launch_bounds__(kNearMaxWarps * 32)
     k_near_batched(const SysDesc* __restrict__ sys, int nsys, const int64_t* __restrict__ item_off, int64_t nitems,
                    unsigned long long* __restrict__ counter)
 {
-    __shared__ __align__(16) double tile[kNearMaxWarps][12 * 32];
+    constexpr int kTileBytes = 12 * 32 * 8 > kTileFloat4 * 16 ? 12 * 32 * 8 : kTileFloat4 * 16;
+    __shared__ __align__(16) double tile[kNearMaxWarps][kTileBytes / 8];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (;;) {
         unsigned long long item = 0;
@@ -189,8 +325,8 @@ __global__ void __launch_bounds__(kNearMaxWarps * 32)
         if (kFp64)
             near_batch_fp64(d.ts, d.M, d.topo, d.xs, d.ws, d.N, d.near_off, d.near_list, d.u_near, b, tile[w], lane);
         else
-            near_batch_mixed(d.ts, d.M, d.topo, d.spack, d.near_off, d.near_list, d.u_near, b,
-                             reinterpret_cast<float4*>(tile[w]), lane);
+            near_pair_mixed(d.ts, d.M, d.topo, d.spack, d.near_off, d.near_list, d.u_near, b,
+                            reinterpret_cast<float4*>(tile[w]), lane);
     }
 }
 
@@ -244,12 +380,16 @@ cudaError_t launch_near(int precision, const double* ts, int64_t M, const int4* 
                         const double* xs, const double* ws, const float4* spack, int64_t N,
                         const int64_t* near_off, const ListEntry* near_list, double* u_near, cudaStream_t s)
 {
-    int64_t nbatch = (M + kBatch - 1) / kBatch;
-    unsigned grid = (unsigned)((nbatch + kNearWarps - 1) / kNearWarps);
-    if (precision == TC_FP64)
+    if (M <= 0) return cudaSuccess;
+    const int64_t nbatch = (M + kBatch - 1) / kBatch;
+    if (precision == TC_FP64) {
+        const unsigned grid = (unsigned)((nbatch + kNearWarps - 1) / kNearWarps);
         k_near_fp64<<<grid, kNearWarps * 32, 0, s>>>(ts, M, topo, xs, ws, N, near_off, near_list, u_near);
-    else
+    } else {
+        const int64_t nsuper = (nbatch + 1) / 2;
+        const unsigned grid = (unsigned)((nsuper + kNearWarps - 1) / kNearWarps);
         k_near_mixed<<<grid, kNearWarps * 32, 0, s>>>(ts, M, topo, spack, near_off, near_list, u_near);
+    }
     note_launch();
     return cudaGetLastError();
 }
