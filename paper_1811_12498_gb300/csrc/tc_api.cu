@@ -469,7 +469,8 @@ tc_status tc::eval_compute(tc_ctx* ctx, double* u)
     const double* ts = ctx->eval_self ? ptr<double>(ctx->xs) : ptr<double>(ctx->ts);
     const int32_t* tperm = ctx->eval_self ? ptr<int32_t>(ctx->perm) : ptr<int32_t>(ctx->tperm);
     ph_begin(ctx, TC_PH_FAR);
-    TC_CK(launch_far(ctx->precision, ts, M, ptr<Geo>(ctx->node_geo), ptr<double>(ctx->node_invrho),
+    TC_CK(launch_far(ctx->precision, ts, M, ptr<int4>(ctx->node_topo), ptr<Geo>(ctx->node_geo),
+                     ptr<double>(ctx->node_invrho),
                      ptr<float4>(ctx->geo32), ptr<double>(ctx->abf64), ptr<float>(ctx->abf32), p,
                      ptr<int64_t>(ctx->far_off),
                      ptr<ListEntry>(ctx->far_list), ptr<double>(ctx->u_far), s),

@@ -63,7 +63,7 @@ struct tc_batch {
     DevBuf d_off;                      // device copy of off
     DevBuf xseg, fseg, hseg, nuseg;    // per-system copies
     DevBuf desc;                       // SysDesc[nsys]
-    DevBuf item_off;                   // far items (batches), then near items: 2 x (nsys + 1) offsets
+    DevBuf item_off;                   // nsys + 1 item offsets (items: batches in FP64, batch pairs in mixed)
     DevBuf counters;                   // two queue counters
     std::vector<SysDesc> hdesc;
     std::vector<int64_t> hitem;
@@ -132,12 +132,9 @@ static tc_status launch_compute(tc_batch* b, const Shape& sh, int p, int64_t nit
     TB_CK(cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), s), "reset queue");
     const SysDesc* d = ptr<SysDesc>(b->desc);
     const int64_t* io = ptr<int64_t>(b->item_off);
-    const int64_t* io_near = io + b->nsys + 1;
-    const int64_t nitems_near = b->hitem[2 * b->nsys + 1];
     TB_CK(launch_far_batched(b->cfg.precision, d, b->nsys, io, nitems, p, cnt, sh.far_warps, sh.far_blocks, s),
           "batched far field");
-    TB_CK(launch_near_batched(b->cfg.precision, d, b->nsys, io_near, nitems_near, cnt + 1, sh.near_warps,
-                              sh.near_blocks, s),
+    TB_CK(launch_near_batched(b->cfg.precision, d, b->nsys, io, nitems, cnt + 1, sh.near_warps, sh.near_blocks, s),
           "batched near field");
     TB_CK(launch_finalize_batched(d, b->nsys, ptr<int64_t>(b->d_off), b->ntot, u, b->ntot, s), "batched finalize");
     return TC_OK;
@@ -162,8 +159,6 @@ static tc_status tune(tc_batch* b, int p, int64_t nitems, double* u)
     unsigned long long* cnt = ptr<unsigned long long>(b->counters);
     const SysDesc* d = ptr<SysDesc>(b->desc);
     const int64_t* io = ptr<int64_t>(b->item_off);
-    const int64_t* io_near = io + b->nsys + 1;
-    const int64_t nitems_near = b->hitem[2 * b->nsys + 1];
     Shape best;
     float best_far = 1e30f, best_near = 1e30f;
     // far: warps per block x blocks per SM (0 = occupancy limit)
@@ -196,8 +191,7 @@ static tc_status tune(tc_batch* b, int p, int64_t nitems, double* u)
             const int blocks = nb ? nb * sms : 0;
             cudaMemsetAsync(cnt + 1, 0, sizeof(unsigned long long), s);
             cudaEventRecord(e0, s);
-            cudaError_t e =
-                launch_near_batched(b->cfg.precision, d, b->nsys, io_near, nitems_near, cnt + 1, nw, blocks, s);
+            cudaError_t e = launch_near_batched(b->cfg.precision, d, b->nsys, io, nitems, cnt + 1, nw, blocks, s);
             cudaEventRecord(e1, s);
             if (e != cudaSuccess) {
                 cudaGetLastError();
@@ -361,8 +355,7 @@ tc_status tc_batch_eval(tc_batch* b, double theta, int32_t p, double* u)
     }
     // 2. descriptors and the item numbering
     b->hdesc.resize(b->nsys);
-    b->hitem.assign(2 * (b->nsys + 1), 0);
-    int64_t* hnear = b->hitem.data() + b->nsys + 1;  // near items: batch pairs in mixed precision
+    b->hitem.assign(b->nsys + 1, 0);
     for (int s = 0; s < b->nsys; s++) {
         tc_ctx* c = b->ctx[s];
         SysDesc& d = b->hdesc[s];
@@ -386,15 +379,14 @@ tc_status tc_batch_eval(tc_batch* b, double theta, int32_t p, double* u)
         d.tperm = ptr<int32_t>(c->perm);
         d.out_off = b->off[s];
         const int64_t nb = (c->M + kBatch - 1) / kBatch;
-        b->hitem[s + 1] = b->hitem[s] + nb;
-        hnear[s + 1] = hnear[s] + (b->cfg.precision == TC_FP64 ? nb : (nb + 1) / 2);
+        b->hitem[s + 1] = b->hitem[s] + (b->cfg.precision == TC_FP64 ? nb : (nb + 1) / 2);
     }
     const int64_t nitems = b->hitem[b->nsys];
     TB_CK(ensure(b->desc, sizeof(SysDesc) * b->nsys), "alloc descriptors");
-    TB_CK(ensure(b->item_off, (size_t)2 * (b->nsys + 1) * 8), "alloc items");
+    TB_CK(ensure(b->item_off, (size_t)(b->nsys + 1) * 8), "alloc items");
     TB_CK(cudaMemcpyAsync(b->desc.p, b->hdesc.data(), sizeof(SysDesc) * b->nsys, cudaMemcpyHostToDevice, st),
           "copy descriptors");
-    TB_CK(cudaMemcpyAsync(b->item_off.p, b->hitem.data(), (size_t)2 * (b->nsys + 1) * 8, cudaMemcpyHostToDevice, st),
+    TB_CK(cudaMemcpyAsync(b->item_off.p, b->hitem.data(), (size_t)(b->nsys + 1) * 8, cudaMemcpyHostToDevice, st),
           "copy items");
     TB_CK(cudaStreamSynchronize(st), "descriptor sync");  // host arrays are reused next call
     // 3. launch shapes

@@ -19,29 +19,33 @@
 // coefficients with k1 <= 1 are formed, 2n+1 per level, at most five
 // operations each, and the recurrence never needs any other.
 //
-// One warp handles a batch of 32 targets (one per lane) and walks the batch's
-// far list; a lane outside an entry's mask idles for that entry.  Each
-// coefficient is contracted against the cluster's 12 folded table entries as
-// soon as it exists (12 FMA into the per-lane totals).
+// A batch is 32 targets (one per lane) with one far list; a lane outside an
+// entry's mask idles for that entry.  Each coefficient is contracted against
+// the cluster's 12 folded table entries as soon as it exists (12 FMA into the
+// per-lane totals).
 //
 // Two implementations:
 //  * FP32 (mixed precision), order known at compile time (P = p + 2 is a
 //    template parameter, one instantiation per order 0..12): every loop is
 //    unrolled, the two live levels of coefficients are registers, the tables
-//    are read as float4.  d' is formed from FP32 hi/lo splits of the target
-//    and the cluster centre (x_hi - y_hi is computed with one rounding, so d'
-//    carries FP32 relative accuracy however close x and y_c are in absolute
-//    terms), with no FP64 operation per entry except the FP64 accumulation of
-//    the three velocity components.  On the folded tables an FP32 recurrence
-//    is as accurate as an FP64 one (at p = 6, 8, 10 on a uniform cube the
-//    mixed result differs from FP64 by the same 1.8e-7, set by the FP32 near
-//    field).
-//  * FP64, any order at run time: the coefficients live in a per-warp shared
-//    memory store of two slots laid out [slot][position][lane] (no bank
-//    conflicts); level n overwrites level n-2 in place, positions running
-//    downward, which is safe because a coefficient reads level n-2 only at
-//    positions <= its own.  Two coefficients per step for instruction-level
-//    parallelism.
+//    are read as float4.  One warp takes two consecutive batches (two targets
+//    per lane) and walks the merge of their far lists, so every table value
+//    the warp loads serves both targets of a lane wherever the lists share a
+//    cluster: the broadcast table loads, not the arithmetic, bound this
+//    kernel (4 B of L1 bandwidth per FMA at one target per lane).  d' is
+//    formed from FP32 hi/lo splits of the target and the cluster centre
+//    (x_hi - y_hi is computed with one rounding, so d' carries FP32 relative
+//    accuracy however close x and y_c are in absolute terms), with no FP64
+//    operation per entry except the FP64 accumulation of the three velocity
+//    components.  On the folded tables an FP32 recurrence is as accurate as
+//    an FP64 one (at p = 6, 8, 10 on a uniform cube the mixed result differs
+//    from FP64 by the same 1.8e-7, set by the FP32 near field).
+//  * FP64, any order at run time, one batch per warp: the coefficients live
+//    in a per-warp shared memory store of two slots laid out
+//    [slot][position][lane] (no bank conflicts); level n overwrites level n-2
+//    in place, positions running downward, which is safe because a
+//    coefficient reads level n-2 only at positions <= its own.  Two
+//    coefficients per step for instruction-level parallelism.
 #include "tc_recurrence.cuh"
 
 namespace tc {
@@ -237,74 +241,188 @@ __device__ __forceinline__ void contract12f(float c, const float4* __restrict__ 
     tot[11] = fmaf(c, d.w, tot[11]);
 }
 
-// geo32 holds per node (y_c hi xyz, 1/rho) and (y_c lo xyz, 0) in FP32
-template <int P>
-__device__ __forceinline__ void far_batch32(const double* __restrict__ ts, int64_t M,
-                                            const float4* __restrict__ geo32, const float* __restrict__ ab,
-                                            const int64_t* __restrict__ far_off,
-                                            const ListEntry* __restrict__ far_list, double* __restrict__ u_far,
-                                            int64_t b, int lane)
+// A target as FP32 hi/lo splits of its FP64 coordinates.
+struct Tgt32 {
+    float h0, h1, h2, l0, l1, l2;
+};
+
+__device__ inline Tgt32 load_tgt32(const double* __restrict__ ts, int64_t M, int64_t m, bool valid)
 {
-    constexpr int H = (P + 1) * (P + 1);
-    const int64_t m = b * kBatch + lane;
-    const bool valid = m < M;
-    float xh0 = 0, xh1 = 0, xh2 = 0, xl0 = 0, xl1 = 0, xl2 = 0;
+    Tgt32 t{0, 0, 0, 0, 0, 0};
     if (valid) {
         const double x0 = ts[m], x1 = ts[M + m], x2 = ts[2 * M + m];
-        xh0 = __double2float_rn(x0);
-        xh1 = __double2float_rn(x1);
-        xh2 = __double2float_rn(x2);
-        xl0 = __double2float_rn(x0 - (double)xh0);
-        xl1 = __double2float_rn(x1 - (double)xh1);
-        xl2 = __double2float_rn(x2 - (double)xh2);
+        t.h0 = __double2float_rn(x0);
+        t.h1 = __double2float_rn(x1);
+        t.h2 = __double2float_rn(x2);
+        t.l0 = __double2float_rn(x0 - (double)t.h0);
+        t.l1 = __double2float_rn(x1 - (double)t.h1);
+        t.l2 = __double2float_rn(x2 - (double)t.h2);
     }
-    double ux = 0.0, uy = 0.0, uz = 0.0;
-    const int64_t e0 = far_off[b], e1 = far_off[b + 1];
-    for (int64_t e = e0; e < e1; e++) {
-        const ListEntry le = far_list[e];
-        const bool in = (le.mask >> lane) & 1u;
-        const float4 gh = __ldg(geo32 + 2 * (int64_t)le.node);
-        const float4 gl = __ldg(geo32 + 2 * (int64_t)le.node + 1);
-        const float d0 = ((xh0 - gh.x) + (xl0 - gl.x)) * gh.w;
-        const float d1 = ((xh1 - gh.y) + (xl1 - gl.y)) * gh.w;
-        const float d2 = ((xh2 - gh.z) + (xl2 - gl.z)) * gh.w;
-        float R2 = fmaf(d0, d0, fmaf(d1, d1, d2 * d2));
-        if (!in) R2 = 1.0f;  // keep idle lanes finite
-        const float iR = rsqrtf(R2);
-        const float iR2 = iR * iR;
-        const float v0 = d0 * iR2, v1 = d1 * iR2, v2 = d2 * iR2;
-        const float4* __restrict__ tab = reinterpret_cast<const float4*>(ab + (int64_t)le.node * H * 12);
-        float tot[12];
-        {
-            const float4 a = __ldg(tab), bb = __ldg(tab + 1), d = __ldg(tab + 2);  // level 0: c^0 = 1
-            tot[0] = a.x, tot[1] = a.y, tot[2] = a.z, tot[3] = a.w;
-            tot[4] = bb.x, tot[5] = bb.y, tot[6] = bb.z, tot[7] = bb.w;
-            tot[8] = d.x, tot[9] = d.y, tot[10] = d.z, tot[11] = d.w;
+    return t;
+}
+
+// Far-field contribution of one cluster (folded FP32 tables tab, geometry
+// gh = (y_c hi, 1/rho), gl = (y_c lo, 0)) to NT targets held by this lane.
+// The NT recurrences run side by side and share every table load, so a
+// table value broadcast to the warp feeds NT x 32 products.  Lanes for which
+// in[t] is false get finite garbage, discarded by the caller.
+template <int P, int NT>
+__device__ __forceinline__ void far_entry32(const Tgt32 (&tg)[NT], const bool (&in)[NT], const float4 gh,
+                                            const float4 gl, const float4* __restrict__ tab, float (&res)[NT][3])
+{
+    float d0[NT], d1[NT], d2[NT], iR[NT], iR2[NT], v0[NT], v1[NT], v2[NT];
+#pragma unroll
+    for (int t = 0; t < NT; t++) {
+        d0[t] = ((tg[t].h0 - gh.x) + (tg[t].l0 - gl.x)) * gh.w;
+        d1[t] = ((tg[t].h1 - gh.y) + (tg[t].l1 - gl.y)) * gh.w;
+        d2[t] = ((tg[t].h2 - gh.z) + (tg[t].l2 - gl.z)) * gh.w;
+        float R2 = fmaf(d0[t], d0[t], fmaf(d1[t], d1[t], d2[t] * d2[t]));
+        if (!in[t]) R2 = 1.0f;  // keep idle lanes finite
+        iR[t] = rsqrtf(R2);
+        iR2[t] = iR[t] * iR[t];
+        v0[t] = d0[t] * iR2[t];
+        v1[t] = d1[t] * iR2[t];
+        v2[t] = d2[t] * iR2[t];
+    }
+    float tot[NT][12];
+    {
+        const float4 a = __ldg(tab), b = __ldg(tab + 1), c = __ldg(tab + 2);  // level 0: c^0 = 1
+#pragma unroll
+        for (int t = 0; t < NT; t++) {
+            tot[t][0] = a.x, tot[t][1] = a.y, tot[t][2] = a.z, tot[t][3] = a.w;
+            tot[t][4] = b.x, tot[t][5] = b.y, tot[t][6] = b.z, tot[t][7] = b.w;
+            tot[t][8] = c.x, tot[t][9] = c.y, tot[t][10] = c.z, tot[t][11] = c.w;
         }
-        float c[2][2 * P + 1];
-        c[0][0] = 1.0f;
+    }
+    float cs[NT][2][2 * P + 1];
 #pragma unroll
-        for (int n = 1; n <= P; n++) {
-            const float kap = c_lev32.kappa[n] * iR2;
-            float* Rn = c[n & 1];  // also holds level n-2
-            const float* R1 = c[(n - 1) & 1];
+    for (int t = 0; t < NT; t++) cs[t][0][0] = 1.0f;
 #pragma unroll
-            for (int h = 2 * n; h >= 0; h--) {
-                const float cf = hcoef_r(R1, Rn, n, h, v0, v1, v2, kap);
-                Rn[h] = cf;
-                contract12f(cf, tab + 3 * (n * n + h), tot);
+    for (int n = 1; n <= P; n++) {
+        float kap[NT];
+#pragma unroll
+        for (int t = 0; t < NT; t++) kap[t] = c_lev32.kappa[n] * iR2[t];
+#pragma unroll
+        for (int h = 2 * n; h >= 0; h--) {
+            const float4* tl = tab + 3 * (n * n + h);
+            const float4 a = __ldg(tl), b = __ldg(tl + 1), c = __ldg(tl + 2);
+#pragma unroll
+            for (int t = 0; t < NT; t++) {
+                const float cf = hcoef_r(cs[t][(n - 1) & 1], cs[t][n & 1], n, h, v0[t], v1[t], v2[t], kap[t]);
+                cs[t][n & 1][h] = cf;  // level n overwrites level n-2
+                tot[t][0] = fmaf(cf, a.x, tot[t][0]);
+                tot[t][1] = fmaf(cf, a.y, tot[t][1]);
+                tot[t][2] = fmaf(cf, a.z, tot[t][2]);
+                tot[t][3] = fmaf(cf, a.w, tot[t][3]);
+                tot[t][4] = fmaf(cf, b.x, tot[t][4]);
+                tot[t][5] = fmaf(cf, b.y, tot[t][5]);
+                tot[t][6] = fmaf(cf, b.z, tot[t][6]);
+                tot[t][7] = fmaf(cf, b.w, tot[t][7]);
+                tot[t][8] = fmaf(cf, c.x, tot[t][8]);
+                tot[t][9] = fmaf(cf, c.y, tot[t][9]);
+                tot[t][10] = fmaf(cf, c.z, tot[t][10]);
+                tot[t][11] = fmaf(cf, c.w, tot[t][11]);
+            }
+            // keep the table loads of later coefficients from being hoisted
+            // here: with two targets per lane that would exhaust the registers
+            if (NT > 1) asm volatile("" ::: "memory");
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < NT; t++) {
+        res[t][0] = fmaf(d0[t], tot[t][3], fmaf(d1[t], tot[t][4], fmaf(d2[t], tot[t][5], tot[t][0]))) * iR[t];
+        res[t][1] = fmaf(d0[t], tot[t][6], fmaf(d1[t], tot[t][7], fmaf(d2[t], tot[t][8], tot[t][1]))) * iR[t];
+        res[t][2] = fmaf(d0[t], tot[t][9], fmaf(d1[t], tot[t][10], fmaf(d2[t], tot[t][11], tot[t][2]))) * iR[t];
+    }
+}
+
+// Far field of batches 2B and 2B+1 (the second may not exist) on one warp,
+// two targets per lane, over the merge of the two far lists.  Both lists are
+// in tree preorder, which orders clusters by (first source ascending, size
+// descending, index ascending: a parent is numbered before its children);
+// equal entries are the same cluster and are evaluated once for both batches.
+template <int P>
+__device__ __forceinline__ void far_pair32(const double* __restrict__ ts, int64_t M, const int4* __restrict__ topo,
+                                           const float4* __restrict__ geo32, const float* __restrict__ ab,
+                                           const int64_t* __restrict__ far_off,
+                                           const ListEntry* __restrict__ far_list, double* __restrict__ u_far,
+                                           int64_t B, int lane)
+{
+    constexpr int H = (P + 1) * (P + 1);
+    const int64_t nbatch = (M + kBatch - 1) / kBatch;
+    const int64_t ba = 2 * B, bb = 2 * B + 1;
+    const int64_t ma = ba * kBatch + lane, mb = bb * kBatch + lane;
+    const bool va = ma < M, vb = mb < M;
+    const Tgt32 ta = load_tgt32(ts, M, ma, va), tb = load_tgt32(ts, M, mb, vb);
+    double ua0 = 0, ua1 = 0, ua2 = 0, ub0 = 0, ub1 = 0, ub2 = 0;
+    int64_t ia = far_off[ba], ea = far_off[ba + 1], ib = 0, eb = 0;
+    if (bb < nbatch) {
+        ib = far_off[bb];
+        eb = far_off[bb + 1];
+    }
+    ListEntry la{0, 0}, lb{0, 0};
+    int4 qa = make_int4(0, 0, 0, 0), qb = make_int4(0, 0, 0, 0);
+    if (ia < ea) {
+        la = far_list[ia];
+        qa = topo[la.node];
+    }
+    if (ib < eb) {
+        lb = far_list[ib];
+        qb = topo[lb.node];
+    }
+    while (ia < ea || ib < eb) {
+        bool takeA, takeB;
+        if (ia >= ea) {
+            takeA = false, takeB = true;
+        } else if (ib >= eb) {
+            takeA = true, takeB = false;
+        } else if (la.node == lb.node) {
+            takeA = takeB = true;
+        } else {
+            takeA = qa.x < qb.x || (qa.x == qb.x && (qa.y > qb.y || (qa.y == qb.y && la.node < lb.node)));
+            takeB = !takeA;
+        }
+        const int node = takeA ? la.node : lb.node;
+        const unsigned mA = takeA ? la.mask : 0u, mB = takeB ? lb.mask : 0u;
+        const float4 gh = __ldg(geo32 + 2 * (int64_t)node), gl = __ldg(geo32 + 2 * (int64_t)node + 1);
+        const float4* tab = reinterpret_cast<const float4*>(ab + (int64_t)node * H * 12);
+        const bool inA = (mA >> lane) & 1u, inB = (mB >> lane) & 1u;
+        {
+            // both targets of the lane in one pass (a lane whose target is not
+            // in the entry computes finite garbage for it, discarded here)
+            const Tgt32 tg[2] = {ta, tb};
+            const bool in[2] = {inA, inB};
+            float r[2][3];
+            far_entry32<P, 2>(tg, in, gh, gl, tab, r);
+            if (inA) {
+                ua0 += (double)r[0][0];
+                ua1 += (double)r[0][1];
+                ua2 += (double)r[0][2];
+            }
+            if (inB) {
+                ub0 += (double)r[1][0];
+                ub1 += (double)r[1][1];
+                ub2 += (double)r[1][2];
             }
         }
-        if (in) {
-            ux += (double)(fmaf(d0, tot[3], fmaf(d1, tot[4], fmaf(d2, tot[5], tot[0]))) * iR);
-            uy += (double)(fmaf(d0, tot[6], fmaf(d1, tot[7], fmaf(d2, tot[8], tot[1]))) * iR);
-            uz += (double)(fmaf(d0, tot[9], fmaf(d1, tot[10], fmaf(d2, tot[11], tot[2]))) * iR);
+        if (takeA && ++ia < ea) {
+            la = far_list[ia];
+            qa = topo[la.node];
+        }
+        if (takeB && ++ib < eb) {
+            lb = far_list[ib];
+            qb = topo[lb.node];
         }
     }
-    if (valid) {
-        u_far[m] = ux;
-        u_far[M + m] = uy;
-        u_far[2 * M + m] = uz;
+    if (va) {
+        u_far[ma] = ua0;
+        u_far[M + ma] = ua1;
+        u_far[2 * M + ma] = ua2;
+    }
+    if (vb) {
+        u_far[mb] = ub0;
+        u_far[M + mb] = ub1;
+        u_far[2 * M + mb] = ub2;
     }
 }
 
@@ -328,19 +446,21 @@ __global__ void __launch_bounds__(32)
 
 template <int P>
 __global__ void __launch_bounds__(32)
-    k_far32(const double* __restrict__ ts, int64_t M, const float4* __restrict__ geo32, const float* __restrict__ ab,
-            const int64_t* __restrict__ far_off, const ListEntry* __restrict__ far_list, double* __restrict__ u_far)
+    k_far32(const double* __restrict__ ts, int64_t M, const int4* __restrict__ topo,
+            const float4* __restrict__ geo32, const float* __restrict__ ab, const int64_t* __restrict__ far_off,
+            const ListEntry* __restrict__ far_list, double* __restrict__ u_far)
 {
     const int lane = threadIdx.x & 31;
-    const int64_t nbatch = (M + kBatch - 1) / kBatch;
-    const int64_t b = blockIdx.x;
-    if (b >= nbatch) return;
-    far_batch32<P>(ts, M, geo32, ab, far_off, far_list, u_far, b, lane);
+    const int64_t nsuper = ((M + kBatch - 1) / kBatch + 1) / 2;
+    const int64_t B = blockIdx.x;
+    if (B >= nsuper) return;
+    far_pair32<P>(ts, M, topo, geo32, ab, far_off, far_list, u_far, B, lane);
 }
 
 // Persistent far-field kernels over many systems: every warp repeatedly takes
-// the next (system, batch) item from a device counter until the queue is
-// empty.  Items are numbered system by system (item_off: nsys + 1 offsets).
+// the next (system, item) from a device counter until the queue is empty.
+// Items are numbered system by system (item_off: nsys + 1 offsets); an item
+// is a batch in FP64 mode and a pair of batches in mixed precision.
 __device__ inline int64_t next_item(const int64_t* __restrict__ item_off, int nsys, int64_t nitems,
                                     unsigned long long* counter, int lane, int& sys)
 {
@@ -372,9 +492,9 @@ __device__ __noinline__ void far_batch64_call(const SysDesc* d, int p, int64_t b
 }
 
 template <int P>
-__device__ __noinline__ void far_batch32_call(const SysDesc* d, int64_t b, int lane)
+__device__ __noinline__ void far_pair32_call(const SysDesc* d, int64_t B, int lane)
 {
-    far_batch32<P>(d->ts, d->M, d->geo32, (const float*)d->ab, d->far_off, d->far_list, d->u_far, b, lane);
+    far_pair32<P>(d->ts, d->M, d->topo, d->geo32, (const float*)d->ab, d->far_off, d->far_list, d->u_far, B, lane);
 }
 
 __global__ void k_far64_batched(const SysDesc* __restrict__ sys, int nsys, const int64_t* __restrict__ item_off,
@@ -401,7 +521,7 @@ __global__ void k_far32_batched(const SysDesc* __restrict__ sys, int nsys, const
         int s = 0;
         const int64_t b = next_item(item_off, nsys, nitems, counter, lane, s);
         if (b < 0) break;
-        far_batch32_call<P>(sys + s, b, lane);
+        far_pair32_call<P>(sys + s, b, lane);
     }
 }
 
@@ -428,11 +548,11 @@ cudaError_t persistent_grid(K kernel, int warps_per_block, size_t smem, int& blo
 }
 
 template <int P>
-cudaError_t run_far32(const double* ts, int64_t M, const float4* geo32, const float* ab, const int64_t* far_off,
-                      const ListEntry* far_list, double* u_far, cudaStream_t s)
+cudaError_t run_far32(const double* ts, int64_t M, const int4* topo, const float4* geo32, const float* ab,
+                      const int64_t* far_off, const ListEntry* far_list, double* u_far, cudaStream_t s)
 {
-    const int64_t nbatch = (M + kBatch - 1) / kBatch;
-    k_far32<P><<<(unsigned)nbatch, 32, 0, s>>>(ts, M, geo32, ab, far_off, far_list, u_far);
+    const int64_t nsuper = ((M + kBatch - 1) / kBatch + 1) / 2;
+    k_far32<P><<<(unsigned)nsuper, 32, 0, s>>>(ts, M, topo, geo32, ab, far_off, far_list, u_far);
     note_launch();
     return cudaGetLastError();
 }
@@ -450,9 +570,9 @@ cudaError_t run_far32_batched(const SysDesc* sys, int nsys, const int64_t* item_
 
 }  // namespace
 
-cudaError_t launch_far(int precision, const double* ts, int64_t M, const Geo* geo, const double* invrho,
-                       const float4* geo32, const double* ab64, const float* ab32, int p, const int64_t* far_off,
-                       const ListEntry* far_list, double* u_far, cudaStream_t s)
+cudaError_t launch_far(int precision, const double* ts, int64_t M, const int4* topo, const Geo* geo,
+                       const double* invrho, const float4* geo32, const double* ab64, const float* ab32, int p,
+                       const int64_t* far_off, const ListEntry* far_list, double* u_far, cudaStream_t s)
 {
     if (M <= 0) return cudaSuccess;
     if (precision == TC_FP64) {
@@ -466,7 +586,7 @@ cudaError_t launch_far(int precision, const double* ts, int64_t M, const Geo* ge
     }
     switch (p + 2) {
 #define TC_FAR32_CASE(P) \
-    case P: return run_far32<P>(ts, M, geo32, ab32, far_off, far_list, u_far, s);
+    case P: return run_far32<P>(ts, M, topo, geo32, ab32, far_off, far_list, u_far, s);
         TC_FAR32_CASE(2) TC_FAR32_CASE(3) TC_FAR32_CASE(4) TC_FAR32_CASE(5) TC_FAR32_CASE(6)
         TC_FAR32_CASE(7) TC_FAR32_CASE(8) TC_FAR32_CASE(9) TC_FAR32_CASE(10) TC_FAR32_CASE(11)
         TC_FAR32_CASE(12) TC_FAR32_CASE(13) TC_FAR32_CASE(14)

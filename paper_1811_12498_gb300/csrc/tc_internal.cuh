@@ -224,8 +224,9 @@ cudaError_t launch_sum_i64(const int64_t* in, int64_t n, int64_t* out, cudaStrea
 cudaError_t launch_sum_entry_sizes(const ListEntry* list, int64_t n, const int4* topo, int64_t* out, cudaStream_t s);
 
 // tc_far.cu
-cudaError_t launch_far(int precision, const double* ts, int64_t M, const Geo* geo, const double* invrho,
-                       const float4* geo32, const double* ab64, const float* ab32, int p, const int64_t* far_off,
+cudaError_t launch_far(int precision, const double* ts, int64_t M, const int4* topo, const Geo* geo,
+                       const double* invrho, const float4* geo32, const double* ab64, const float* ab32, int p,
+                       const int64_t* far_off,
                        const ListEntry* far_list, double* u_far, cudaStream_t s);
 
 cudaError_t launch_far_batched(int precision, const SysDesc* sys, int nsys, const int64_t* item_off, int64_t nitems,
