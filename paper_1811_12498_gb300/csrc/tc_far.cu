@@ -32,7 +32,10 @@
 //    per lane) and walks the merge of their far lists, so every table value
 //    the warp loads serves both targets of a lane wherever the lists share a
 //    cluster: the broadcast table loads, not the arithmetic, bound this
-//    kernel (4 B of L1 bandwidth per FMA at one target per lane).  d' is
+//    kernel (4 B of L1 bandwidth per FMA at one target per lane).  The
+//    contraction runs on packed FP32x2 FMAs over pairs of table columns,
+//    which halves the instructions of the fully unrolled body (its size, not
+//    only its arithmetic, limits the kernel: instruction fetch stalls).  d' is
 //    formed from FP32 hi/lo splits of the target and the cluster centre
 //    (x_hi - y_hi is computed with one rounding, so d' carries FP32 relative
 //    accuracy however close x and y_c are in absolute terms), with no FP64
@@ -284,14 +287,14 @@ __device__ __forceinline__ void far_entry32(const Tgt32 (&tg)[NT], const bool (&
         v1[t] = d1[t] * iR2[t];
         v2[t] = d2[t] * iR2[t];
     }
-    float tot[NT][12];
+    float2 tot[NT][6];
     {
         const float4 a = __ldg(tab), b = __ldg(tab + 1), c = __ldg(tab + 2);  // level 0: c^0 = 1
 #pragma unroll
         for (int t = 0; t < NT; t++) {
-            tot[t][0] = a.x, tot[t][1] = a.y, tot[t][2] = a.z, tot[t][3] = a.w;
-            tot[t][4] = b.x, tot[t][5] = b.y, tot[t][6] = b.z, tot[t][7] = b.w;
-            tot[t][8] = c.x, tot[t][9] = c.y, tot[t][10] = c.z, tot[t][11] = c.w;
+            tot[t][0] = make_float2(a.x, a.y), tot[t][1] = make_float2(a.z, a.w);
+            tot[t][2] = make_float2(b.x, b.y), tot[t][3] = make_float2(b.z, b.w);
+            tot[t][4] = make_float2(c.x, c.y), tot[t][5] = make_float2(c.z, c.w);
         }
     }
     float cs[NT][2][2 * P + 1];
@@ -310,18 +313,13 @@ __device__ __forceinline__ void far_entry32(const Tgt32 (&tg)[NT], const bool (&
             for (int t = 0; t < NT; t++) {
                 const float cf = hcoef_r(cs[t][(n - 1) & 1], cs[t][n & 1], n, h, v0[t], v1[t], v2[t], kap[t]);
                 cs[t][n & 1][h] = cf;  // level n overwrites level n-2
-                tot[t][0] = fmaf(cf, a.x, tot[t][0]);
-                tot[t][1] = fmaf(cf, a.y, tot[t][1]);
-                tot[t][2] = fmaf(cf, a.z, tot[t][2]);
-                tot[t][3] = fmaf(cf, a.w, tot[t][3]);
-                tot[t][4] = fmaf(cf, b.x, tot[t][4]);
-                tot[t][5] = fmaf(cf, b.y, tot[t][5]);
-                tot[t][6] = fmaf(cf, b.z, tot[t][6]);
-                tot[t][7] = fmaf(cf, b.w, tot[t][7]);
-                tot[t][8] = fmaf(cf, c.x, tot[t][8]);
-                tot[t][9] = fmaf(cf, c.y, tot[t][9]);
-                tot[t][10] = fmaf(cf, c.z, tot[t][10]);
-                tot[t][11] = fmaf(cf, c.w, tot[t][11]);
+                const float2 c2 = make_float2(cf, cf);
+                tot[t][0] = __ffma2_rn(c2, make_float2(a.x, a.y), tot[t][0]);
+                tot[t][1] = __ffma2_rn(c2, make_float2(a.z, a.w), tot[t][1]);
+                tot[t][2] = __ffma2_rn(c2, make_float2(b.x, b.y), tot[t][2]);
+                tot[t][3] = __ffma2_rn(c2, make_float2(b.z, b.w), tot[t][3]);
+                tot[t][4] = __ffma2_rn(c2, make_float2(c.x, c.y), tot[t][4]);
+                tot[t][5] = __ffma2_rn(c2, make_float2(c.z, c.w), tot[t][5]);
             }
             // keep the table loads of later coefficients from being hoisted
             // here: with two targets per lane that would exhaust the registers
@@ -330,9 +328,12 @@ __device__ __forceinline__ void far_entry32(const Tgt32 (&tg)[NT], const bool (&
     }
 #pragma unroll
     for (int t = 0; t < NT; t++) {
-        res[t][0] = fmaf(d0[t], tot[t][3], fmaf(d1[t], tot[t][4], fmaf(d2[t], tot[t][5], tot[t][0]))) * iR[t];
-        res[t][1] = fmaf(d0[t], tot[t][6], fmaf(d1[t], tot[t][7], fmaf(d2[t], tot[t][8], tot[t][1]))) * iR[t];
-        res[t][2] = fmaf(d0[t], tot[t][9], fmaf(d1[t], tot[t][10], fmaf(d2[t], tot[t][11], tot[t][2]))) * iR[t];
+        const float T0 = tot[t][0].x, T1 = tot[t][0].y, T2 = tot[t][1].x, T3 = tot[t][1].y, T4 = tot[t][2].x,
+                    T5 = tot[t][2].y, T6 = tot[t][3].x, T7 = tot[t][3].y, T8 = tot[t][4].x, T9 = tot[t][4].y,
+                    T10 = tot[t][5].x, T11 = tot[t][5].y;
+        res[t][0] = fmaf(d0[t], T3, fmaf(d1[t], T4, fmaf(d2[t], T5, T0))) * iR[t];
+        res[t][1] = fmaf(d0[t], T6, fmaf(d1[t], T7, fmaf(d2[t], T8, T1))) * iR[t];
+        res[t][2] = fmaf(d0[t], T9, fmaf(d1[t], T10, fmaf(d2[t], T11, T2))) * iR[t];
     }
 }
 

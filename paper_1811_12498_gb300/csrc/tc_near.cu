@@ -113,17 +113,17 @@ __device__ __forceinline__ void pair_terms(const Tgt2& t, const float4* tp, floa
     ri.x = r2.x > 0.f ? rsqrtf(r2.x) : 0.f;
     ri.y = r2.y > 0.f ? rsqrtf(r2.y) : 0.f;
     const float2 ri2 = __fmul2_rn(ri, ri);
-    const float2 ri3 = __fmul2_rn(ri2, ri);
     const float2 f0 = make_float2(B.z, B.w), f1 = make_float2(D.z, D.w), f2 = make_float2(E.x, E.y);
     const float2 df = __ffma2_rn(dx, f0, __ffma2_rn(dy, f1, __fmul2_rn(dz, f2)));
     const float2 dh = __ffma2_rn(dx, make_float2(E.z, E.w),
                                  __ffma2_rn(dy, make_float2(F.x, F.y), __fmul2_rn(dz, make_float2(F.z, F.w))));
     const float2 dn = __ffma2_rn(dx, make_float2(G.x, G.y),
                                  __ffma2_rn(dy, make_float2(G.z, G.w), __fmul2_rn(dz, make_float2(Q.x, Q.y))));
-    const float2 st = __fmul2_rn(ri3, __ffma2_rn(__fmul2_rn(dh, dn), ri2, df));
-    ax = __ffma2_rn(f0, ri, __ffma2_rn(dx, st, ax));
-    ay = __ffma2_rn(f1, ri, __ffma2_rn(dy, st, ay));
-    az = __ffma2_rn(f2, ri, __ffma2_rn(dz, st, az));
+    // u += (1/r) (f + d s),  s = (d.f + (d.h)(d.nu) / r^2) / r^2
+    const float2 st = __fmul2_rn(ri2, __ffma2_rn(__fmul2_rn(dh, dn), ri2, df));
+    ax = __ffma2_rn(ri, __ffma2_rn(dx, st, f0), ax);
+    ay = __ffma2_rn(ri, __ffma2_rn(dy, st, f1), ay);
+    az = __ffma2_rn(ri, __ffma2_rn(dz, st, f2), az);
 }
 
 // Near field of batches 2B and 2B+1 (the second may not exist) on one warp;

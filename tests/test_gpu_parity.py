@@ -211,6 +211,20 @@ def test_treecode_disjoint_targets(prec):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_offset_and_duplicated_points(prec):
+    # coordinates far from the origin (FP32 keeps only ~1e-4 absolute there)
+    # and exact duplicates: every coincident pair must still be skipped and
+    # the mixed path keep its accuracy
+    x, f, h, nu = inputs.uniform_cube(4000, 67)
+    x = x + np.array([1000.0, -2000.0, 500.0])
+    x[3500:] = x[:500]
+    u, *_ = _run(prec, x, f, h, nu, 100, 6, 0.5)
+    tree = oracle.Tree(x, 100, True)
+    tree.set_moments(f, h, nu, 6)
+    assert oracle.rel_l2(u, tree.treecode(x, 0.5, 6)) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_edge_cases(prec):
     # a single particle: nothing to sum
     x = np.array([[0.1, 0.2, 0.3]])
