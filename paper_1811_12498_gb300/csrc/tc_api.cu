@@ -1,6 +1,8 @@
 // C ABI entry points (include/tc.h): argument checks, buffer management and
 // the order of kernel launches for tree build, moments and evaluation.
+#include <algorithm>
 #include <atomic>
+#include <cmath>
 #include <cstdarg>
 #include <new>
 
@@ -111,7 +113,8 @@ static void ph_end(tc_ctx* ctx, int ph)
 static void release_all(tc_ctx* c)
 {
     DevBuf* bufs[] = {&c->root, &c->bbox_part, &c->keys, &c->keys_alt, &c->perm, &c->perm_alt, &c->hist, &c->xs,
-                      &c->node_topo, &c->node_info, &c->node_key, &c->node_geo, &c->node_invrho, &c->split_cnt,
+                      &c->node_topo, &c->node_info, &c->node_key, &c->node_geo, &c->node_invrho, &c->node_geof, &c->geo_tmp,
+                      &c->split_cnt,
                       &c->split_off, &c->scan_tmp, &c->ws, &c->spack, &c->mom, &c->ab64, &c->ab32, &c->abf64,
                       &c->abf32, &c->geo32, &c->tkeys,
                       &c->tkeys_alt, &c->tperm, &c->tperm_alt, &c->ts, &c->nfar_e, &c->nnear_e,
@@ -298,9 +301,11 @@ tc_status tc_build(tc_ctx* ctx, const double* x, int64_t N, int32_t N0)
     ctx->depth = (int)ctx->level_begin.size() - 2;
     TC_CK(ensure(ctx->node_geo, (size_t)le * sizeof(Geo)), "alloc geo");
     TC_CK(ensure(ctx->node_invrho, (size_t)le * sizeof(double)), "alloc geo");
+    TC_CK(ensure(ctx->geo_tmp, geometry_scratch_bytes(le)), "alloc geo");
+    TC_CK(ensure(ctx->node_geof, (size_t)le * 2 * sizeof(float4)), "alloc geo");
     TC_CK(launch_geometry(ptr<int4>(ctx->node_topo), ptr<int4>(ctx->node_info), ptr<uint64_t>(ctx->node_key),
                           ptr<double>(ctx->xs), N, le, ptr<double>(ctx->root), ctx->shrink, ptr<Geo>(ctx->node_geo),
-                          ptr<double>(ctx->node_invrho), s),
+                          ptr<double>(ctx->node_invrho), ptr<float4>(ctx->node_geof), ctx->geo_tmp.p, s),
           "geometry");
     ph_end(ctx, TC_PH_BUILD);
     ctx->built = 1;
@@ -430,9 +435,15 @@ tc_status tc::eval_prepare(tc_ctx* ctx, const double* targets, int64_t M, double
     TC_CK(cudaMemsetAsync(ctx->flags.p, 0, 4, s), "flags");
     const int4* topo = ptr<int4>(ctx->node_topo);
     const Geo* geo = ptr<Geo>(ctx->node_geo);
+    const float4* geof = ptr<float4>(ctx->node_geof);
+    // squared magnitude bound of the cluster centres (all inside the root box)
+    double S = 0.0;
+    for (int a = 0; a < 3; a++) S = std::max(S, std::max(std::fabs(ctx->lo[a]), std::fabs(ctx->lo[a] + ctx->side)));
+    const float scale2 = (float)(S * S);
     ph_begin(ctx, TC_PH_LISTS);
-    TC_CK(launch_lists(ts, M, topo, geo, theta, 0, ptr<int32_t>(ctx->nfar_e), ptr<int32_t>(ctx->nnear_e), nullptr,
-                       nullptr, nullptr, nullptr, nullptr, nullptr, ptr<int32_t>(ctx->flags), s),
+    TC_CK(launch_lists(ts, M, topo, geo, geof, scale2, theta, 0, ptr<int32_t>(ctx->nfar_e),
+                       ptr<int32_t>(ctx->nnear_e), nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                       ptr<int32_t>(ctx->flags), s),
           "list count");
     int64_t* far_off = ptr<int64_t>(ctx->far_off);
     int64_t* near_off = ptr<int64_t>(ctx->near_off);
@@ -445,7 +456,7 @@ tc_status tc::eval_prepare(tc_ctx* ctx, const double* targets, int64_t M, double
     if (st != TC_OK) return st;
     TC_CK(ensure(ctx->far_list, (size_t)(tot[0] > 0 ? tot[0] : 1) * sizeof(ListEntry)), "alloc far list");
     TC_CK(ensure(ctx->near_list, (size_t)(tot[1] > 0 ? tot[1] : 1) * sizeof(ListEntry)), "alloc near list");
-    TC_CK(launch_lists(ts, M, topo, geo, theta, 1, nullptr, nullptr, far_off, near_off,
+    TC_CK(launch_lists(ts, M, topo, geo, geof, scale2, theta, 1, nullptr, nullptr, far_off, near_off,
                        ptr<ListEntry>(ctx->far_list), ptr<ListEntry>(ctx->near_list), ptr<int64_t>(ctx->cnt_far),
                        ptr<int64_t>(ctx->cnt_near), ptr<int32_t>(ctx->flags), s),
           "list write");

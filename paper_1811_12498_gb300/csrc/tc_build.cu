@@ -64,29 +64,50 @@ __global__ void k_bbox_partial(const double* __restrict__ x, int64_t N, double* 
 
 // root[0..2] = per-axis minimum, root[3] = side (largest extent),
 // root[4] = 2^21 / side (0 if side == 0), root[5] = 1 if an input was not finite.
-__global__ void k_bbox_final(const double* __restrict__ part, int nblk, double* __restrict__ root)
+// One block of kBboxThreads: strided partial min/max, then a block reduction.
+__global__ void __launch_bounds__(kBboxThreads) k_bbox_final(const double* __restrict__ part, int nblk,
+                                                              double* __restrict__ root)
 {
-    if (threadIdx.x != 0) return;
+    __shared__ double sm[6][kBboxThreads / 32];
+    __shared__ int sbad;
     double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
     bool bad = false;
-    for (int b = 0; b < nblk; b++)
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x)
         for (int a = 0; a < 3; a++) {
             double v0 = part[b * 6 + a], v1 = part[b * 6 + 3 + a];
             bad |= isnan(v0) || isnan(v1);
             mn[a] = fmin(mn[a], v0);
             mx[a] = fmax(mx[a], v1);
         }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (threadIdx.x == 0) sbad = 0;
+    __syncthreads();
+    if (__any_sync(0xffffffffu, bad) && lane == 0) sbad = 1;
+    for (int a = 0; a < 3; a++) {
+        double a0 = warp_min(mn[a]), a1 = warp_max(mx[a]);
+        if (lane == 0) {
+            sm[a][w] = a0;
+            sm[3 + a][w] = a1;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    for (int k = 1; k < kBboxThreads / 32; k++)
+        for (int a = 0; a < 3; a++) {
+            sm[a][0] = fmin(sm[a][0], sm[a][k]);
+            sm[3 + a][0] = fmax(sm[3 + a][0], sm[3 + a][k]);
+        }
     double side = 0.0;
     for (int a = 0; a < 3; a++) {
-        double e = __dsub_rn(mx[a], mn[a]);
+        double e = __dsub_rn(sm[3 + a][0], sm[a][0]);
         if (e > side) side = e;
     }
-    root[0] = mn[0];
-    root[1] = mn[1];
-    root[2] = mn[2];
+    root[0] = sm[0][0];
+    root[1] = sm[1][0];
+    root[2] = sm[2][0];
     root[3] = side;
     root[4] = side > 0.0 ? 2097152.0 / side : 0.0;
-    root[5] = bad ? 1.0 : 0.0;
+    root[5] = sbad ? 1.0 : 0.0;
 }
 
 // 21-bit spread: bit j of v goes to bit 3j.
@@ -330,48 +351,145 @@ __device__ inline double block_reduce(double v, bool is_max, double* sm)
     return sm[0];
 }
 
-// One block per cluster: centre (tight box or cell centre) and r^2.
-__global__ void k_geometry(const int4* __restrict__ topo, const int4* __restrict__ info,
-                           const uint64_t* __restrict__ nkey, const double* __restrict__ xs, int64_t N,
-                           const double* __restrict__ root, int shrink, Geo* __restrict__ geo,
-                           double* __restrict__ invrho)
+// Cluster geometry: centre (tight box or cell centre) and r^2 = max |y - y_c|^2.
+// The work is split into items of at most kGeoChunk particles of one cluster,
+// so that the large clusters near the root are spread over the whole GPU;
+// per-item partial results are combined with atomic min/max, which are exact
+// (the result does not depend on the order), on order-preserving integer
+// images of the doubles.
+constexpr int kGeoChunk = 2048;
+
+// double -> uint64 with the same order (a negative value's bits inverted, a
+// non-negative value's sign bit set)
+__device__ inline unsigned long long dorder(double v)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ inline double dunorder(unsigned long long k)
+{
+    return __longlong_as_double((long long)((k >> 63) ? (k ^ 0x8000000000000000ull) : ~k));
+}
+
+// items per cluster; reset of the per-cluster accumulators
+__global__ void k_geo_items(const int4* __restrict__ topo, int64_t nnodes, int32_t* __restrict__ cnt,
+                            unsigned long long* __restrict__ acc)
+{
+    const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (id >= nnodes) return;
+    cnt[id] = (topo[id].y + kGeoChunk - 1) / kGeoChunk;
+    unsigned long long* a = acc + id * 7;
+    for (int c = 0; c < 3; c++) {
+        a[c] = dorder(INFINITY);       // min
+        a[3 + c] = dorder(-INFINITY);  // max
+    }
+    a[6] = 0ull;  // r^2 >= 0: its bits order like the value
+}
+
+// item -> (cluster, particle range)
+__device__ inline int64_t geo_item(const int4* __restrict__ topo, const int32_t* __restrict__ item_off,
+                                   int64_t nnodes, int item, int& b, int& e)
+{
+    int64_t lo = 0, hi = nnodes;  // item_off[lo] <= item < item_off[hi]
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (item_off[mid] <= item)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    const int4 t = topo[lo];
+    b = t.x + (item - item_off[lo]) * kGeoChunk;
+    e = min(b + kGeoChunk, t.x + t.y);
+    return lo;
+}
+
+__global__ void __launch_bounds__(kGeoThreads)
+    k_geo_box(const int4* __restrict__ topo, const int32_t* __restrict__ item_off, const int32_t* __restrict__ nitems,
+              int64_t nnodes, const double* __restrict__ xs, int64_t N, unsigned long long* __restrict__ acc)
 {
     __shared__ double sm[kGeoThreads / 32];
-    int64_t id = blockIdx.x;
-    int4 t = topo[id];
-    int b = t.x, e = t.x + t.y;
-    double yc[3];
-    if (shrink) {
+    const int total = *nitems;
+    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+        int b, e;
+        const int64_t id = geo_item(topo, item_off, nnodes, item, b, e);
         for (int a = 0; a < 3; a++) {
             double mn = INFINITY, mx = -INFINITY;
             for (int i = b + threadIdx.x; i < e; i += blockDim.x) {
-                double v = xs[a * N + i];
+                const double v = xs[a * N + i];
                 mn = fmin(mn, v);
                 mx = fmax(mx, v);
             }
             mn = block_reduce(mn, false, sm);
             mx = block_reduce(mx, true, sm);
-            yc[a] = __dmul_rn(__dadd_rn(mn, mx), 0.5);
+            if (threadIdx.x == 0) {
+                atomicMin(acc + id * 7 + a, dorder(mn));
+                atomicMax(acc + id * 7 + 3 + a, dorder(mx));
+            }
         }
+    }
+}
+
+// centre of each cluster (tight box or cell centre)
+__global__ void k_geo_centre(const int4* __restrict__ info, const uint64_t* __restrict__ nkey, int64_t nnodes,
+                             const double* __restrict__ root, int shrink, const unsigned long long* __restrict__ acc,
+                             Geo* __restrict__ geo)
+{
+    const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (id >= nnodes) return;
+    double yc[3];
+    if (shrink) {
+        for (int a = 0; a < 3; a++)
+            yc[a] = __dmul_rn(__dadd_rn(dunorder(acc[id * 7 + a]), dunorder(acc[id * 7 + 3 + a])), 0.5);
     } else {
-        int L = info[id].x;
-        uint64_t k = nkey[id];
-        uint32_t c[3] = {compact3(k >> 2) >> (kMaxDepth - L), compact3(k >> 1) >> (kMaxDepth - L),
-                         compact3(k) >> (kMaxDepth - L)};
-        double cs = ldexp(root[3], -L);
+        const int L = info[id].x;
+        const uint64_t k = nkey[id];
+        const uint32_t c[3] = {compact3(k >> 2) >> (kMaxDepth - L), compact3(k >> 1) >> (kMaxDepth - L),
+                               compact3(k) >> (kMaxDepth - L)};
+        const double cs = ldexp(root[3], -L);
         for (int a = 0; a < 3; a++) yc[a] = __dadd_rn(root[a], __dmul_rn((double)c[a] + 0.5, cs));
     }
-    double r2 = 0.0;
-    for (int i = b + threadIdx.x; i < e; i += blockDim.x) {
-        double dx = __dsub_rn(xs[i], yc[0]), dy = __dsub_rn(xs[N + i], yc[1]), dz = __dsub_rn(xs[2 * N + i], yc[2]);
-        double s = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-        r2 = fmax(r2, s);
+    geo[id] = Geo{yc[0], yc[1], yc[2], 0.0};
+}
+
+__global__ void __launch_bounds__(kGeoThreads)
+    k_geo_r2(const int4* __restrict__ topo, const int32_t* __restrict__ item_off, const int32_t* __restrict__ nitems,
+             int64_t nnodes, const double* __restrict__ xs, int64_t N, const Geo* __restrict__ geo,
+             unsigned long long* __restrict__ acc)
+{
+    __shared__ double sm[kGeoThreads / 32];
+    const int total = *nitems;
+    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+        int b, e;
+        const int64_t id = geo_item(topo, item_off, nnodes, item, b, e);
+        const Geo g = geo[id];
+        double r2 = 0.0;
+        for (int i = b + threadIdx.x; i < e; i += blockDim.x) {
+            const double dx = __dsub_rn(xs[i], g.x), dy = __dsub_rn(xs[N + i], g.y), dz = __dsub_rn(xs[2 * N + i], g.z);
+            const double s = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+            r2 = fmax(r2, s);
+        }
+        r2 = block_reduce(r2, true, sm);
+        if (threadIdx.x == 0) atomicMax(acc + id * 7 + 6, (unsigned long long)__double_as_longlong(r2));
     }
-    r2 = block_reduce(r2, true, sm);
-    if (threadIdx.x == 0) {
-        geo[id] = Geo{yc[0], yc[1], yc[2], r2};
-        invrho[id] = r2 > 0.0 ? 1.0 / sqrt(r2) : 1.0;
-    }
+}
+
+// r^2, 1/rho, and the FP32 copy of the geometry used by the MAC screen of
+// the list traversal: (fl32(y_c), fl32(r^2)) and (fl32(y_c - fl32(y_c)), 0)
+__global__ void k_geo_final(int64_t nnodes, const unsigned long long* __restrict__ acc, Geo* __restrict__ geo,
+                            double* __restrict__ invrho, float4* __restrict__ geof)
+{
+    const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (id >= nnodes) return;
+    const double r2 = __longlong_as_double((long long)acc[id * 7 + 6]);
+    Geo g = geo[id];
+    g.w = r2;
+    geo[id] = g;
+    invrho[id] = r2 > 0.0 ? 1.0 / sqrt(r2) : 1.0;
+    const float hx = __double2float_rn(g.x), hy = __double2float_rn(g.y), hz = __double2float_rn(g.z);
+    geof[2 * id] = make_float4(hx, hy, hz, __double2float_rn(r2));
+    geof[2 * id + 1] = make_float4(__double2float_rn(g.x - (double)hx), __double2float_rn(g.y - (double)hy),
+                                   __double2float_rn(g.z - (double)hz), 0.0f);
 }
 
 inline unsigned grid_for(int64_t n, int threads)
@@ -386,7 +504,7 @@ cudaError_t launch_bbox(const double* x, int64_t N, double* part, int nblk, doub
 {
     k_bbox_partial<<<nblk, kBboxThreads, 0, s>>>(x, N, part);
     note_launch();
-    k_bbox_final<<<1, 32, 0, s>>>(part, nblk, root);
+    k_bbox_final<<<1, kBboxThreads, 0, s>>>(part, nblk, root);
     note_launch();
     return cudaGetLastError();
 }
@@ -503,12 +621,33 @@ cudaError_t launch_split_write(int4* topo, int4* info, uint64_t* nkey, const uin
 }
 
 cudaError_t launch_geometry(const int4* topo, const int4* info, const uint64_t* nkey, const double* xs, int64_t N,
-                            int64_t nnodes, const double* root, int shrink, Geo* geo, double* invrho,
-                            cudaStream_t s)
+                            int64_t nnodes, const double* root, int shrink, Geo* geo, double* invrho, float4* geof,
+                            void* scratch, cudaStream_t s)
 {
-    k_geometry<<<(unsigned)nnodes, kGeoThreads, 0, s>>>(topo, info, nkey, xs, N, root, shrink, geo, invrho);
+    // scratch: acc [nnodes][7] u64, cnt [nnodes] i32, item_off [nnodes] i32, nitems i32
+    unsigned long long* acc = static_cast<unsigned long long*>(scratch);
+    int32_t* cnt = reinterpret_cast<int32_t*>(acc + nnodes * 7);
+    int32_t* item_off = cnt + nnodes;
+    int32_t* nitems = item_off + nnodes;
+    k_geo_items<<<grid_for(nnodes, 256), 256, 0, s>>>(topo, nnodes, cnt, acc);
+    note_launch();
+    cudaError_t e = launch_scan_i32(cnt, item_off, nnodes, nitems, s);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const unsigned grid = (unsigned)(sms > 0 ? sms : 1) * 4;
+    k_geo_box<<<grid, kGeoThreads, 0, s>>>(topo, item_off, nitems, nnodes, xs, N, acc);
+    note_launch();
+    k_geo_centre<<<grid_for(nnodes, 256), 256, 0, s>>>(info, nkey, nnodes, root, shrink, acc, geo);
+    note_launch();
+    k_geo_r2<<<grid, kGeoThreads, 0, s>>>(topo, item_off, nitems, nnodes, xs, N, geo, acc);
+    note_launch();
+    k_geo_final<<<grid_for(nnodes, 256), 256, 0, s>>>(nnodes, acc, geo, invrho, geof);
     note_launch();
     return cudaGetLastError();
 }
+
+size_t geometry_scratch_bytes(int64_t nnodes) { return (size_t)nnodes * 7 * 8 + (size_t)(2 * nnodes + 1) * 4; }
 
 }  // namespace tc

@@ -107,6 +107,8 @@ struct tc_ctx {
     tc::DevBuf node_key;                // uint64 Morton prefix
     tc::DevBuf node_geo;                // Geo {yc, rc2}
     tc::DevBuf node_invrho;             // double 1/rho (rho = r, or 1 if r == 0)
+    tc::DevBuf node_geof;               // float4 x2: (y_c hi, fl32(rc2)), (y_c lo, 0) for the MAC screen
+    tc::DevBuf geo_tmp;                 // geometry scratch (per-cluster accumulators, item map)
     tc::DevBuf split_cnt, split_off;    // per-level scan buffers
     tc::DevBuf scan_tmp;                // device scalar(s)
 
@@ -193,8 +195,9 @@ cudaError_t launch_scan_i32(const int32_t* in, int32_t* out_excl, int64_t n, int
 cudaError_t launch_split_write(int4* topo, int4* info, uint64_t* nkey, const uint64_t* keys, int64_t lb, int64_t le,
                                int N0, const int32_t* off, cudaStream_t s);
 cudaError_t launch_geometry(const int4* topo, const int4* info, const uint64_t* nkey, const double* xs, int64_t N,
-                            int64_t nnodes, const double* root, int shrink, Geo* geo, double* invrho,
-                            cudaStream_t s);
+                            int64_t nnodes, const double* root, int shrink, Geo* geo, double* invrho, float4* geof,
+                            void* scratch, cudaStream_t s);
+size_t geometry_scratch_bytes(int64_t nnodes);
 
 // tc_moments.cu
 cudaError_t launch_gather_weights(const double* f, const double* h, const double* nu, const int32_t* perm,
@@ -214,10 +217,10 @@ cudaError_t launch_fold_tables(const double* ab64, int64_t nnodes, int p, double
 __host__ __device__ constexpr int hsize(int P) { return (P + 1) * (P + 1); }
 
 // tc_lists.cu
-cudaError_t launch_lists(const double* ts, int64_t M, const int4* topo, const Geo* geo, double theta,
-                         int write, int32_t* nfar_e, int32_t* nnear_e, const int64_t* far_off,
-                         const int64_t* near_off, ListEntry* far_list, ListEntry* near_list, int64_t* cnt_far,
-                         int64_t* cnt_near, int32_t* flags, cudaStream_t s);
+cudaError_t launch_lists(const double* ts, int64_t M, const int4* topo, const Geo* geo, const float4* geof,
+                         float scale2, double theta, int write, int32_t* nfar_e, int32_t* nnear_e,
+                         const int64_t* far_off, const int64_t* near_off, ListEntry* far_list, ListEntry* near_list,
+                         int64_t* cnt_far, int64_t* cnt_near, int32_t* flags, cudaStream_t s);
 cudaError_t launch_scan_i32_to_i64(const int32_t* in, int64_t* out_excl, int64_t n, int64_t* total,
                                    cudaStream_t s);
 cudaError_t launch_sum_i64(const int64_t* in, int64_t n, int64_t* out, cudaStream_t s);

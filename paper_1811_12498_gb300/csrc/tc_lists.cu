@@ -8,6 +8,15 @@
 // exactly the clusters, and makes exactly the decisions, of Algorithm 1 run on
 // its own.  Children are pushed so that they are visited in octant order.
 //
+// The MAC R^2 > 0 && r_c^2 <= theta^2 R^2 is decided in FP64 exactly as the
+// definition reads (every operation rounded to nearest), but most decisions
+// are settled by an FP32 screen first: R^2 from FP32 hi/lo splits of the
+// target and the centre has a relative error below 2e-6 whenever
+// |x - y_c| >= 1e-7 S (S bounds the coordinates' magnitude), so a screened
+// ratio theta^2 R^2 / r_c^2 farther than 2^-12 from 1 gives the FP64 answer;
+// the rest (near-ties, and centres within 1e-7 S of the target) are decided
+// in FP64.  The decisions, and so the lists, are those of the FP64 test.
+//
 // The kernel runs twice: once to count entries per batch, once (after an
 // exclusive scan of the counts) to write them.
 #include "tc_internal.cuh"
@@ -20,7 +29,8 @@ constexpr int kListWarps = 4;
 
 __global__ void __launch_bounds__(kListWarps * 32)
     k_lists(const double* __restrict__ ts, int64_t M, const int4* __restrict__ topo,
-            const Geo* __restrict__ geo, double theta2, int write, int32_t* __restrict__ nfar_e,
+            const Geo* __restrict__ geo, const float4* __restrict__ geof, float tiny2, float th2f, double theta2,
+            int write, int32_t* __restrict__ nfar_e,
             int32_t* __restrict__ nnear_e, const int64_t* __restrict__ far_off, const int64_t* __restrict__ near_off,
             ListEntry* __restrict__ far_list, ListEntry* __restrict__ near_list, int64_t* __restrict__ cnt_far,
             int64_t* __restrict__ cnt_near, int32_t* __restrict__ flags)
@@ -38,6 +48,9 @@ __global__ void __launch_bounds__(kListWarps * 32)
         x1 = ts[M + m];
         x2 = ts[2 * M + m];
     }
+    const float xh0 = __double2float_rn(x0), xh1 = __double2float_rn(x1), xh2 = __double2float_rn(x2);
+    const float xl0 = __double2float_rn(x0 - (double)xh0), xl1 = __double2float_rn(x1 - (double)xh1),
+                xl2 = __double2float_rn(x2 - (double)xh2);
     ListEntry* st = stack[w];
     int sp = 0;
     const unsigned active = __ballot_sync(0xffffffffu, valid);
@@ -51,11 +64,22 @@ __global__ void __launch_bounds__(kListWarps * 32)
         ListEntry e = st[--sp];
         __syncwarp();
         int4 t = topo[e.node];
-        Geo g = geo[e.node];
         bool in = (e.mask >> lane) & 1u;
-        double dx = __dsub_rn(x0, g.x), dy = __dsub_rn(x1, g.y), dz = __dsub_rn(x2, g.z);
-        double R2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-        bool pass = in && (R2 > 0.0) && (g.w <= __dmul_rn(theta2, R2));
+        const float4 gh = geof[2 * (int64_t)e.node], gl = geof[2 * (int64_t)e.node + 1];
+        const float fx = (xh0 - gh.x) + (xl0 - gl.x), fy = (xh1 - gh.y) + (xl1 - gl.y),
+                    fz = (xh2 - gh.z) + (xl2 - gl.z);
+        const float R2f = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
+        const float q = th2f * R2f;
+        const bool screened = R2f > tiny2 && q < 1e37f && gh.w < 1e37f;  // far from FP32 under/overflow
+        bool pass = screened && q >= gh.w * (1.0f + 0x1p-12f);
+        const bool sure = screened && (pass || q <= gh.w * (1.0f - 0x1p-12f));
+        if (in && !sure) {
+            const Geo g = geo[e.node];
+            double dx = __dsub_rn(x0, g.x), dy = __dsub_rn(x1, g.y), dz = __dsub_rn(x2, g.z);
+            double R2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+            pass = (R2 > 0.0) && (g.w <= __dmul_rn(theta2, R2));
+        }
+        pass = pass && in;
         unsigned pm = __ballot_sync(0xffffffffu, pass);
         unsigned fm = e.mask & ~pm;
         if (pm) {
@@ -156,16 +180,19 @@ cudaError_t launch_sum_entry_sizes(const ListEntry* list, int64_t n, const int4*
     return cudaGetLastError();
 }
 
-cudaError_t launch_lists(const double* ts, int64_t M, const int4* topo, const Geo* geo, double theta,
-                         int write, int32_t* nfar_e, int32_t* nnear_e, const int64_t* far_off,
-                         const int64_t* near_off, ListEntry* far_list, ListEntry* near_list, int64_t* cnt_far,
-                         int64_t* cnt_near, int32_t* flags, cudaStream_t s)
+cudaError_t launch_lists(const double* ts, int64_t M, const int4* topo, const Geo* geo, const float4* geof,
+                         float scale2, double theta, int write, int32_t* nfar_e, int32_t* nnear_e,
+                         const int64_t* far_off, const int64_t* near_off, ListEntry* far_list, ListEntry* near_list,
+                         int64_t* cnt_far, int64_t* cnt_near, int32_t* flags, cudaStream_t s)
 {
     int64_t nbatch = (M + kBatch - 1) / kBatch;
     unsigned grid = (unsigned)((nbatch + kListWarps - 1) / kListWarps);
     double theta2 = theta * theta;
-    k_lists<<<grid, kListWarps * 32, 0, s>>>(ts, M, topo, geo, theta2, write, nfar_e, nnear_e, far_off, near_off,
-                                             far_list, near_list, cnt_far, cnt_near, flags);
+    // screen only where |x - y_c|^2 > 1e-14 S^2 (and R^2 is a normal FP32 number)
+    const float tiny2 = fmaxf(1e-14f * scale2, 1e-30f);
+    k_lists<<<grid, kListWarps * 32, 0, s>>>(ts, M, topo, geo, geof, tiny2, (float)theta2, theta2, write, nfar_e,
+                                             nnear_e, far_off, near_off, far_list, near_list, cnt_far, cnt_near,
+                                             flags);
     note_launch();
     return cudaGetLastError();
 }

@@ -166,31 +166,36 @@ __constant__ Binom c_binom = make_binom();
 // M2M: moments of an internal cluster P from those of its children C by the
 // binomial theorem, (y - c_P)^k = sum_{m <= k} binom(k, m) (y - c_C)^m (c_C - c_P)^(k-m):
 //   M^k(P) = sum_C sum_{m <= k} binom(k, m) (c_C - c_P)^(k-m) M^m(C),
-// the same for all 12 components.  One block per internal cluster of one
-// level; levels are processed from the deepest up.
+// the same for all 12 components.  The shift factorises over the axes, so
+// each child's moments are shifted along x, then y, then z: three passes of
+// at most p+1 terms per coefficient instead of one of prod_a (k_a + 1).  One
+// block per internal cluster of one level, the three working arrays [C][12]
+// in shared memory; levels are processed from the deepest up.
 __global__ void __launch_bounds__(kMomThreads) k_m2m(const int4* __restrict__ topo, const Geo* __restrict__ geo,
                                                      int64_t lb, int64_t le, int p, double* __restrict__ mom)
 {
+    extern __shared__ double m2m_sh[];
     __shared__ double sp[3][kPMax + 1];
+    __shared__ unsigned char kidx[ncoef(kPMax)][3];
     const int64_t node = lb + blockIdx.x;
     if (node >= le) return;
     const int4 t = topo[node];
     if (t.w == 0) return;
     const Geo gp = geo[node];
-    const int C = ncoef(p);
-    int kk[kMomSlots][3];
-    double acc[kMomSlots][12];
-    for (int s = 0; s < kMomSlots; s++) {
-        int idx = threadIdx.x + s * kMomThreads;
-        if (idx < C)
-            unflatten(idx, kk[s][0], kk[s][1], kk[s][2]);
-        else
-            kk[s][0] = kk[s][1] = kk[s][2] = 0;
-        for (int c = 0; c < 12; c++) acc[s][c] = 0.0;
+    const int C = ncoef(p), W = C * 12;
+    for (int k = threadIdx.x; k < C; k += blockDim.x) {
+        int k1, k2, k3;
+        unflatten(k, k1, k2, k3);
+        kidx[k][0] = (unsigned char)k1, kidx[k][1] = (unsigned char)k2, kidx[k][2] = (unsigned char)k3;
     }
+    double* A = m2m_sh;
+    double* B = A + W;
+    double* acc = B + W;
+    for (int i = threadIdx.x; i < W; i += blockDim.x) acc[i] = 0.0;
     for (int ci = 0; ci < t.w; ci++) {
         const int64_t child = t.z + ci;
         const Geo gc = geo[child];
+        const double* mc = mom + child * 12 * C;
         __syncthreads();
         if (threadIdx.x < 3) {
             const double sh = threadIdx.x == 0 ? gc.x - gp.x : (threadIdx.x == 1 ? gc.y - gp.y : gc.z - gp.z);
@@ -201,29 +206,27 @@ __global__ void __launch_bounds__(kMomThreads) k_m2m(const int4* __restrict__ to
                 sp[threadIdx.x][k] = v;
             }
         }
+        for (int i = threadIdx.x; i < W; i += blockDim.x) A[i] = mc[(i % 12) * C + i / 12];
         __syncthreads();
-        const double* mc = mom + child * 12 * C;
-        for (int s = 0; s < kMomSlots; s++) {
-            if (threadIdx.x + s * kMomThreads >= C) break;
-            const int k1 = kk[s][0], k2 = kk[s][1], k3 = kk[s][2];
-            for (int m1 = 0; m1 <= k1; m1++) {
-                const double c1 = c_binom.v[k1][m1] * sp[0][k1 - m1];
-                for (int m2 = 0; m2 <= k2; m2++) {
-                    const double c12 = c1 * c_binom.v[k2][m2] * sp[1][k2 - m2];
-                    for (int m3 = 0; m3 <= k3; m3++) {
-                        const double w = c12 * c_binom.v[k3][m3] * sp[2][k3 - m3];
-                        const int mi = flat_index(m1, m2, m3);
-                        for (int c = 0; c < 12; c++) acc[s][c] = fma(w, mc[c * C + mi], acc[s][c]);
-                    }
+#pragma unroll
+        for (int ax = 0; ax < 3; ax++) {
+            const double* src = ax == 1 ? B : A;
+            double* dst = ax == 0 ? B : (ax == 1 ? A : acc);
+            for (int i = threadIdx.x; i < W; i += blockDim.x) {
+                const int k = i / 12, c = i % 12;
+                int kk[3] = {kidx[k][0], kidx[k][1], kidx[k][2]};
+                const int ka = kk[ax];
+                double v = 0.0;
+                for (int m = 0; m <= ka; m++) {
+                    kk[ax] = m;
+                    v = fma(c_binom.v[ka][m] * sp[ax][ka - m], src[flat_index(kk[0], kk[1], kk[2]) * 12 + c], v);
                 }
+                dst[i] = ax == 2 ? dst[i] + v : v;
             }
+            __syncthreads();
         }
     }
-    for (int s = 0; s < kMomSlots; s++) {
-        int idx = threadIdx.x + s * kMomThreads;
-        if (idx >= C) break;
-        for (int c = 0; c < 12; c++) mom[(node * 12 + c) * C + idx] = acc[s][c];
-    }
+    for (int i = threadIdx.x; i < W; i += blockDim.x) mom[(node * 12 + i % 12) * C + i / 12] = acc[i];
 }
 
 // moment of component c at multi-index (k1,k2,k3); 0 outside 0 <= k, ||k|| <= p
@@ -414,7 +417,10 @@ cudaError_t launch_moments(const int4* topo, const Geo* geo, const double* xs, c
 cudaError_t launch_m2m(const int4* topo, const Geo* geo, int64_t lb, int64_t le, int p, double* mom, cudaStream_t s)
 {
     if (le <= lb) return cudaSuccess;
-    k_m2m<<<(unsigned)(le - lb), kMomThreads, 0, s>>>(topo, geo, lb, le, p, mom);
+    const size_t smem = (size_t)3 * ncoef(p) * 12 * sizeof(double);
+    cudaError_t e = cudaFuncSetAttribute(k_m2m, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_m2m<<<(unsigned)(le - lb), kMomThreads, smem, s>>>(topo, geo, lb, le, p, mom);
     note_launch();
     return cudaGetLastError();
 }
