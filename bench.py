@@ -434,25 +434,34 @@ def main():
         "accuracy": {"E_vs_fp64_direct": E, "E_samples": int(len(eidx))},
     }
     if not args.no_fp64_compare and args.precision == "mixed":
-        tc64 = api.Treecode("fp64", True, stream)
-        tc64.build(dx[0], N0).moments(dx[1], dx[2], dx[3], p)
-        u64 = tc64.eval(theta, p)
-        torch.cuda.synchronize()
-        t64 = []
-        for _ in range(2):
-            flush.fill_(1)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            tc64.build(dx[0], N0).moments(dx[1], dx[2], dx[3], p)
-            tc64.eval(theta, p, out=u64)
-            e1.record(stream)
-            e1.synchronize()
-            t64.append(e0.elapsed_time(e1))
-        u64h = u64.cpu().numpy().T
-        line["fp64_path"] = {"ms_per_step": statistics.mean(t64), "value": N / (statistics.mean(t64) / 1e3),
-                             "mixed_vs_fp64_rel_l2": float(np.sqrt(np.sum((u_host - u64h) ** 2) / np.sum(u64h ** 2)))}
-        tc64.close()
+        def other_path(precision, rec64):
+            t2 = api.Treecode(precision, True, stream, rec64=rec64)
+            t2.build(dx[0], N0).moments(dx[1], dx[2], dx[3], p)
+            u2 = t2.eval(theta, p)
+            torch.cuda.synchronize()
+            times = []
+            for _ in range(2):
+                flush.fill_(1)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                t2.build(dx[0], N0).moments(dx[1], dx[2], dx[3], p)
+                t2.eval(theta, p, out=u2)
+                e1.record(stream)
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1))
+            t2.close()
+            return statistics.mean(times), u2.cpu().numpy().T
+
+        def rel(a, b):
+            return float(np.sqrt(np.sum((a - b) ** 2) / np.sum(b ** 2)))
+
+        ms64, u64h = other_path("fp64", False)
+        line["fp64_path"] = {"ms_per_step": ms64, "value": N / (ms64 / 1e3), "mixed_vs_fp64_rel_l2": rel(u_host, u64h)}
+        msr, urh = other_path("mixed", True)
+        line["mixed_fp64_recurrence_path"] = {"ms_per_step": msr, "value": N / (msr / 1e3),
+                                              "vs_fp64_rel_l2": rel(urh, u64h),
+                                              "note": "tc_config.rec64: far-field recurrence in FP64 for p >= 8"}
     if not args.no_cpu_baseline:
         cb, idx, uo = cpu_baseline(x, f, h, nu, args, args.cpu_sample)
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}

@@ -54,10 +54,11 @@ typedef enum {
 typedef enum {
     /* every stage in FP64 */
     TC_FP64 = 0,
-    /* near field and far-field contraction in FP32 (positions split into
-     * FP32 hi + lo parts, per-tile sums carried in FP64); Coulomb-coefficient
-     * recurrence in FP64 for p >= 8 and FP32 (radius-scaled) below; cluster
-     * moments always FP64 */
+    /* near field, far-field Coulomb-coefficient recurrence and contraction
+     * in FP32 (positions split into FP32 hi + lo parts, per-tile and
+     * per-cluster partial sums carried in FP64); cluster moments and
+     * contraction tables always built in FP64.  With tc_config.rec64 the
+     * recurrence runs in FP64 for p >= 8. */
     TC_MIXED = 1
 } tc_precision;
 
@@ -67,7 +68,9 @@ typedef struct {
                         *    of its particles (test case 1 of Section 6);
                         * 0: centre of the octree cell                         */
     void* stream;      /* cudaStream_t the context enqueues on; NULL = default */
-    int32_t reserved0; /* must be 0                                            */
+    int32_t rec64;     /* TC_MIXED only: 1 = far-field recurrence in FP64 for
+                        * p >= 8 (the contraction stays FP32); 0 = FP32, the
+                        * default, as accurate on the folded tables          */
     int32_t reserved1; /* must be 0                                            */
 } tc_config;
 

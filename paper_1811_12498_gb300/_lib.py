@@ -48,7 +48,7 @@ PHASES = ("build", "moments", "tables", "targets", "lists", "far", "near", "fina
 
 
 class TCConfig(ctypes.Structure):
-    _fields_ = [("precision", _i32), ("shrink", _i32), ("stream", _vp), ("reserved0", _i32), ("reserved1", _i32)]
+    _fields_ = [("precision", _i32), ("shrink", _i32), ("stream", _vp), ("rec64", _i32), ("reserved1", _i32)]
 
 
 _lib = None

@@ -70,10 +70,12 @@ def _stream_ptr(stream):
 class Treecode:
     """One treecode context (tc_ctx): tree, moments and interaction lists."""
 
-    def __init__(self, precision="mixed", shrink=True, stream=None):
+    def __init__(self, precision="mixed", shrink=True, stream=None, rec64=False):
+        """rec64: in mixed precision, run the far-field recurrence in FP64 for
+        p >= 8 (tc_config.rec64)."""
         self.precision = _prec(precision)
         self.stream = torch.cuda.current_stream() if stream is None else stream
-        cfg = TCConfig(self.precision, int(bool(shrink)), _stream_ptr(self.stream), 0, 0)
+        cfg = TCConfig(self.precision, int(bool(shrink)), _stream_ptr(self.stream), int(bool(rec64)), 0)
         h = ctypes.c_void_p()
         _check(lib().tc_create(ctypes.byref(h), ctypes.byref(cfg)))
         self._h = h
@@ -228,9 +230,9 @@ class Batch:
     of nsys + 1 particle offsets.  eval() runs all systems' far and near
     fields as persistent kernels replayed from a CUDA graph."""
 
-    def __init__(self, precision="mixed", shrink=True, stream=None, autotune=True, graph=True):
+    def __init__(self, precision="mixed", shrink=True, stream=None, autotune=True, graph=True, rec64=False):
         self.stream = torch.cuda.current_stream() if stream is None else stream
-        cfg = TCConfig(_prec(precision), int(bool(shrink)), _stream_ptr(self.stream), 0, 0)
+        cfg = TCConfig(_prec(precision), int(bool(shrink)), _stream_ptr(self.stream), int(bool(rec64)), 0)
         h = ctypes.c_void_p()
         _check(lib().tc_batch_create(ctypes.byref(h), ctypes.byref(cfg)))
         self._h = h

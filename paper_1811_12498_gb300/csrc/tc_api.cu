@@ -138,7 +138,8 @@ tc_status tc_create(tc_ctx** out, const tc_config* cfg)
     if (c.precision != TC_FP64 && c.precision != TC_MIXED)
         return fail(nullptr, TC_EINVAL, "tc_create: unknown precision %d", c.precision);
     if (c.shrink != 0 && c.shrink != 1) return fail(nullptr, TC_EINVAL, "tc_create: shrink must be 0 or 1");
-    if (c.reserved0 != 0 || c.reserved1 != 0) return fail(nullptr, TC_EINVAL, "tc_create: reserved fields must be 0");
+    if (c.reserved1 != 0) return fail(nullptr, TC_EINVAL, "tc_create: reserved1 must be 0");
+    if (c.rec64 != 0 && c.rec64 != 1) return fail(nullptr, TC_EINVAL, "tc_create: rec64 must be 0 or 1");
     ctx = new (std::nothrow) tc_ctx();
     if (!ctx) return fail(nullptr, TC_ENOMEM, "tc_create: out of host memory");
     cudaError_t e = cudaGetDevice(&ctx->device);
@@ -153,6 +154,7 @@ tc_status tc_create(tc_ctx** out, const tc_config* cfg)
         return st;
     }
     ctx->precision = c.precision;
+    ctx->rec64 = c.precision == TC_MIXED ? c.rec64 : 0;
     ctx->shrink = c.shrink;
     ctx->stream = (cudaStream_t)c.stream;
     ctx->err = "no error";
@@ -480,7 +482,7 @@ tc_status tc::eval_compute(tc_ctx* ctx, double* u)
     const double* ts = ctx->eval_self ? ptr<double>(ctx->xs) : ptr<double>(ctx->ts);
     const int32_t* tperm = ctx->eval_self ? ptr<int32_t>(ctx->perm) : ptr<int32_t>(ctx->tperm);
     ph_begin(ctx, TC_PH_FAR);
-    TC_CK(launch_far(ctx->precision, ts, M, ptr<int4>(ctx->node_topo), ptr<Geo>(ctx->node_geo),
+    TC_CK(launch_far(ctx->precision, ctx->rec64, ts, M, ptr<int4>(ctx->node_topo), ptr<Geo>(ctx->node_geo),
                      ptr<double>(ctx->node_invrho),
                      ptr<float4>(ctx->geo32), ptr<double>(ctx->abf64), ptr<float>(ctx->abf32), p,
                      ptr<int64_t>(ctx->far_off),

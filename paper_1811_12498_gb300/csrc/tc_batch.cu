@@ -132,7 +132,8 @@ static tc_status launch_compute(tc_batch* b, const Shape& sh, int p, int64_t nit
     TB_CK(cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), s), "reset queue");
     const SysDesc* d = ptr<SysDesc>(b->desc);
     const int64_t* io = ptr<int64_t>(b->item_off);
-    TB_CK(launch_far_batched(b->cfg.precision, d, b->nsys, io, nitems, p, cnt, sh.far_warps, sh.far_blocks, s),
+    TB_CK(launch_far_batched(b->cfg.precision, b->cfg.rec64, d, b->nsys, io, nitems, p, cnt, sh.far_warps,
+                             sh.far_blocks, s),
           "batched far field");
     TB_CK(launch_near_batched(b->cfg.precision, d, b->nsys, io, nitems, cnt + 1, sh.near_warps, sh.near_blocks, s),
           "batched near field");
@@ -169,7 +170,8 @@ static tc_status tune(tc_batch* b, int p, int64_t nitems, double* u)
             const int blocks = fb ? fb * sms : 0;
             cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), s);
             cudaEventRecord(e0, s);
-            cudaError_t e = launch_far_batched(b->cfg.precision, d, b->nsys, io, nitems, p, cnt, fw, blocks, s);
+            cudaError_t e =
+                launch_far_batched(b->cfg.precision, b->cfg.rec64, d, b->nsys, io, nitems, p, cnt, fw, blocks, s);
             cudaEventRecord(e1, s);
             if (e != cudaSuccess) {
                 cudaGetLastError();  // a shape that does not fit is skipped
@@ -236,10 +238,12 @@ tc_status tc_batch_create(tc_batch** out, const tc_config* cfg)
     if (c.precision != TC_FP64 && c.precision != TC_MIXED)
         return fail(nullptr, TC_EINVAL, "tc_batch_create: unknown precision %d", c.precision);
     if (c.shrink != 0 && c.shrink != 1) return fail(nullptr, TC_EINVAL, "tc_batch_create: shrink must be 0 or 1");
+    if (c.rec64 != 0 && c.rec64 != 1) return fail(nullptr, TC_EINVAL, "tc_batch_create: rec64 must be 0 or 1");
     tc_batch* b = new (std::nothrow) tc_batch();
     if (!b) return fail(nullptr, TC_ENOMEM, "tc_batch_create: out of host memory");
     b->cfg = c;
-    b->cfg.reserved0 = b->cfg.reserved1 = 0;
+    b->cfg.reserved1 = 0;
+    if (b->cfg.precision != TC_MIXED) b->cfg.rec64 = 0;
     cudaError_t e = ensure(b->counters, 256);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);

@@ -109,8 +109,27 @@ __device__ inline void contract12(double c, const double* __restrict__ t, double
     }
 }
 
+// FP64 coefficient against FP32 tables: the coefficient is narrowed with
+// integer operations (tc_recurrence.cuh), the 12 products are FP32
+__device__ inline void contract12(double c, const float* __restrict__ t, float* tot)
+{
+    const float cf = narrow(c);
+    const float4* t4 = reinterpret_cast<const float4*>(t);
+#pragma unroll
+    for (int q = 0; q < 3; q++) {
+        const float4 a = t4[q];
+        tot[4 * q] = fmaf(cf, a.x, tot[4 * q]);
+        tot[4 * q + 1] = fmaf(cf, a.y, tot[4 * q + 1]);
+        tot[4 * q + 2] = fmaf(cf, a.z, tot[4 * q + 2]);
+        tot[4 * q + 3] = fmaf(cf, a.w, tot[4 * q + 3]);
+    }
+}
+
+// TC = double: the FP64 mode.  TC = float: mixed precision with the FP64
+// recurrence (tc_config.rec64), the FP32 folded tables and FP32 contraction.
+template <typename TC>
 __device__ inline void far_batch64(const double* __restrict__ ts, int64_t M, const Geo* __restrict__ geo,
-                                   const double* __restrict__ invrho, const double* __restrict__ ab, int p,
+                                   const double* __restrict__ invrho, const TC* __restrict__ ab, int p,
                                    const int64_t* __restrict__ far_off, const ListEntry* __restrict__ far_list,
                                    double* __restrict__ u_far, int64_t b, double* slot_p, double* slot_q, int lane)
 {
@@ -137,8 +156,8 @@ __device__ inline void far_batch64(const double* __restrict__ ts, int64_t M, con
         const double iR = rsqrt(R2);
         const double iR2 = iR * iR;
         const double v0 = d0 * iR2, v1 = d1 * iR2, v2 = d2 * iR2;
-        const double* __restrict__ tab = ab + (int64_t)le.node * H * 12;
-        double tot[12];
+        const TC* __restrict__ tab = ab + (int64_t)le.node * H * 12;
+        TC tot[12];
 #pragma unroll
         for (int q = 0; q < 12; q++) tot[q] = tab[q];  // level 0: c^0 = 1
         ((P & 1) ? slot_q : slot_p)[lane] = 1.0;      // level 0 has parity 0
@@ -147,7 +166,7 @@ __device__ inline void far_batch64(const double* __restrict__ ts, int64_t M, con
             const double kap = c_lev.kappa[n] * iR2;
             double* Rn = ((n ^ P) & 1) ? slot_q : slot_p;  // also holds level n-2
             const double* R1 = ((n ^ P) & 1) ? slot_p : slot_q;
-            const double* tl = tab + (int64_t)n * n * 12;
+            const TC* tl = tab + (int64_t)n * n * 12;
             int h = 2 * n;
             for (; h >= 1; h -= 2) {
                 const double ca = hcoef(R1, Rn, n, h, v0, v1, v2, kap, lane);
@@ -165,9 +184,12 @@ __device__ inline void far_batch64(const double* __restrict__ ts, int64_t M, con
             __syncwarp();
         }
         if (in) {
-            ux += (tot[0] + d0 * tot[3] + d1 * tot[4] + d2 * tot[5]) * iR;
-            uy += (tot[1] + d0 * tot[6] + d1 * tot[7] + d2 * tot[8]) * iR;
-            uz += (tot[2] + d0 * tot[9] + d1 * tot[10] + d2 * tot[11]) * iR;
+            double T[12];
+#pragma unroll
+            for (int q = 0; q < 12; q++) T[q] = (double)tot[q];
+            ux += (T[0] + d0 * T[3] + d1 * T[4] + d2 * T[5]) * iR;
+            uy += (T[1] + d0 * T[6] + d1 * T[7] + d2 * T[8]) * iR;
+            uz += (T[2] + d0 * T[9] + d1 * T[10] + d2 * T[11]) * iR;
         }
     }
     if (valid) {
@@ -430,9 +452,10 @@ __device__ __forceinline__ void far_pair32(const double* __restrict__ ts, int64_
 // ---------------------------------------------------------------------------
 // kernels
 
+template <typename TC>
 __global__ void __launch_bounds__(32)
     k_far64(const double* __restrict__ ts, int64_t M, const Geo* __restrict__ geo, const double* __restrict__ invrho,
-            const double* __restrict__ ab, int p, const int64_t* __restrict__ far_off,
+            const TC* __restrict__ ab, int p, const int64_t* __restrict__ far_off,
             const ListEntry* __restrict__ far_list, double* __restrict__ u_far)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -442,7 +465,7 @@ __global__ void __launch_bounds__(32)
     if (b >= nbatch) return;
     double *slot_p, *slot_q;
     far_slots(smraw, p, 0, slot_p, slot_q);
-    far_batch64(ts, M, geo, invrho, ab, p, far_off, far_list, u_far, b, slot_p, slot_q, lane);
+    far_batch64<TC>(ts, M, geo, invrho, ab, p, far_off, far_list, u_far, b, slot_p, slot_q, lane);
 }
 
 template <int P>
@@ -485,11 +508,12 @@ __device__ inline int64_t next_item(const int64_t* __restrict__ item_off, int ns
 // inlined into the work-queue loop they compiled to a body that issued about
 // 1.6x the instructions of the one-batch kernel (measured: 108 ms against
 // 40 ms for the same eight systems); as called functions they match it.
+template <typename TC>
 __device__ __noinline__ void far_batch64_call(const SysDesc* d, int p, int64_t b, double* slot_p, double* slot_q,
                                               int lane)
 {
-    far_batch64(d->ts, d->M, d->geo, d->invrho, (const double*)d->ab, p, d->far_off, d->far_list, d->u_far, b, slot_p,
-                slot_q, lane);
+    far_batch64<TC>(d->ts, d->M, d->geo, d->invrho, (const TC*)d->ab, p, d->far_off, d->far_list, d->u_far, b,
+                    slot_p, slot_q, lane);
 }
 
 template <int P>
@@ -498,6 +522,7 @@ __device__ __noinline__ void far_pair32_call(const SysDesc* d, int64_t B, int la
     far_pair32<P>(d->ts, d->M, d->topo, d->geo32, (const float*)d->ab, d->far_off, d->far_list, d->u_far, B, lane);
 }
 
+template <typename TC>
 __global__ void k_far64_batched(const SysDesc* __restrict__ sys, int nsys, const int64_t* __restrict__ item_off,
                                 int64_t nitems, int p, unsigned long long* __restrict__ counter)
 {
@@ -509,7 +534,13 @@ __global__ void k_far64_batched(const SysDesc* __restrict__ sys, int nsys, const
         int s = 0;
         const int64_t b = next_item(item_off, nsys, nitems, counter, lane, s);
         if (b < 0) break;
-        far_batch64_call(sys + s, p, b, slot_p, slot_q, lane);
+        if (sizeof(TC) == 8) {
+            far_batch64_call<TC>(sys + s, p, b, slot_p, slot_q, lane);
+        } else {  // mixed precision: the item is the batch pair 2b, 2b+1
+            const int64_t nb = (sys[s].M + kBatch - 1) / kBatch;
+            far_batch64_call<TC>(sys + s, p, 2 * b, slot_p, slot_q, lane);
+            if (2 * b + 1 < nb) far_batch64_call<TC>(sys + s, p, 2 * b + 1, slot_p, slot_q, lane);
+        }
     }
 }
 
@@ -569,22 +600,43 @@ cudaError_t run_far32_batched(const SysDesc* sys, int nsys, const int64_t* item_
     return cudaGetLastError();
 }
 
+template <typename TC>
+cudaError_t run_far64(const double* ts, int64_t M, const Geo* geo, const double* invrho, const TC* ab, int p,
+                      const int64_t* far_off, const ListEntry* far_list, double* u_far, cudaStream_t s)
+{
+    const int64_t nbatch = (M + kBatch - 1) / kBatch;
+    const size_t smem = far_store_entries(p) * 32 * sizeof(double);
+    cudaError_t e = cudaFuncSetAttribute(k_far64<TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_far64<TC><<<(unsigned)nbatch, 32, smem, s>>>(ts, M, geo, invrho, ab, p, far_off, far_list, u_far);
+    note_launch();
+    return cudaGetLastError();
+}
+
+template <typename TC>
+cudaError_t run_far64_batched(const SysDesc* sys, int nsys, const int64_t* item_off, int64_t nitems, int p,
+                              unsigned long long* counter, int warps_per_block, int blocks, cudaStream_t s)
+{
+    const size_t smem = (size_t)warps_per_block * far_store_entries(p) * 32 * sizeof(double);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_far64_batched<TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = persistent_grid(k_far64_batched<TC>, warps_per_block, smem, blocks);
+    if (e != cudaSuccess) return e;
+    k_far64_batched<TC><<<blocks, warps_per_block * 32, smem, s>>>(sys, nsys, item_off, nitems, p, counter);
+    note_launch();
+    return cudaGetLastError();
+}
+
 }  // namespace
 
-cudaError_t launch_far(int precision, const double* ts, int64_t M, const int4* topo, const Geo* geo,
+cudaError_t launch_far(int precision, int rec64, const double* ts, int64_t M, const int4* topo, const Geo* geo,
                        const double* invrho, const float4* geo32, const double* ab64, const float* ab32, int p,
                        const int64_t* far_off, const ListEntry* far_list, double* u_far, cudaStream_t s)
 {
     if (M <= 0) return cudaSuccess;
-    if (precision == TC_FP64) {
-        const int64_t nbatch = (M + kBatch - 1) / kBatch;
-        const size_t smem = far_store_entries(p) * 32 * sizeof(double);
-        cudaError_t e = cudaFuncSetAttribute(k_far64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_far64<<<(unsigned)nbatch, 32, smem, s>>>(ts, M, geo, invrho, ab64, p, far_off, far_list, u_far);
-        note_launch();
-        return cudaGetLastError();
-    }
+    if (precision == TC_FP64) return run_far64<double>(ts, M, geo, invrho, ab64, p, far_off, far_list, u_far, s);
+    if (rec64 && p >= 8) return run_far64<float>(ts, M, geo, invrho, ab32, p, far_off, far_list, u_far, s);
     switch (p + 2) {
 #define TC_FAR32_CASE(P) \
     case P: return run_far32<P>(ts, M, topo, geo32, ab32, far_off, far_list, u_far, s);
@@ -596,20 +648,14 @@ cudaError_t launch_far(int precision, const double* ts, int64_t M, const int4* t
     }
 }
 
-cudaError_t launch_far_batched(int precision, const SysDesc* sys, int nsys, const int64_t* item_off, int64_t nitems,
-                               int p, unsigned long long* counter, int warps_per_block, int blocks, cudaStream_t s)
+cudaError_t launch_far_batched(int precision, int rec64, const SysDesc* sys, int nsys, const int64_t* item_off,
+                               int64_t nitems, int p, unsigned long long* counter, int warps_per_block, int blocks,
+                               cudaStream_t s)
 {
-    if (precision == TC_FP64) {
-        const size_t smem = (size_t)warps_per_block * far_store_entries(p) * 32 * sizeof(double);
-        cudaError_t e =
-            cudaFuncSetAttribute(k_far64_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        e = persistent_grid(k_far64_batched, warps_per_block, smem, blocks);
-        if (e != cudaSuccess) return e;
-        k_far64_batched<<<blocks, warps_per_block * 32, smem, s>>>(sys, nsys, item_off, nitems, p, counter);
-        note_launch();
-        return cudaGetLastError();
-    }
+    if (precision == TC_FP64)
+        return run_far64_batched<double>(sys, nsys, item_off, nitems, p, counter, warps_per_block, blocks, s);
+    if (rec64 && p >= 8)
+        return run_far64_batched<float>(sys, nsys, item_off, nitems, p, counter, warps_per_block, blocks, s);
     switch (p + 2) {
 #define TC_FAR32B_CASE(P) \
     case P: return run_far32_batched<P>(sys, nsys, item_off, nitems, counter, warps_per_block, blocks, s);

@@ -85,6 +85,7 @@ struct tc_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     int precision = TC_MIXED;
+    int rec64 = 0;  // mixed: FP64 far-field recurrence for p >= 8
     int shrink = 1;
     std::string err;
 
@@ -227,12 +228,12 @@ cudaError_t launch_sum_i64(const int64_t* in, int64_t n, int64_t* out, cudaStrea
 cudaError_t launch_sum_entry_sizes(const ListEntry* list, int64_t n, const int4* topo, int64_t* out, cudaStream_t s);
 
 // tc_far.cu
-cudaError_t launch_far(int precision, const double* ts, int64_t M, const int4* topo, const Geo* geo,
+cudaError_t launch_far(int precision, int rec64, const double* ts, int64_t M, const int4* topo, const Geo* geo,
                        const double* invrho, const float4* geo32, const double* ab64, const float* ab32, int p,
                        const int64_t* far_off,
                        const ListEntry* far_list, double* u_far, cudaStream_t s);
 
-cudaError_t launch_far_batched(int precision, const SysDesc* sys, int nsys, const int64_t* item_off, int64_t nitems,
+cudaError_t launch_far_batched(int precision, int rec64, const SysDesc* sys, int nsys, const int64_t* item_off, int64_t nitems,
                                int p, unsigned long long* counter, int warps_per_block, int blocks, cudaStream_t s);
 
 // tc_near.cu

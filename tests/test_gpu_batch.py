@@ -55,6 +55,20 @@ def test_batch_matches_separate_calls_and_oracle(prec, tol):
     b.close()
 
 
+def test_batch_fp64_recurrence_option_matches_separate_calls():
+    sizes = [2100, 700, 3300]
+    xs, fs, hs, ns, off = _systems(sizes, 740)
+    b = api.Batch("mixed", True, rec64=True).build(_seg(xs), off, 150).moments(_seg(fs), _seg(hs), _seg(ns), 8)
+    u = b.eval(0.5, 8).cpu().numpy()
+    sep = b.eval_separate(0.5, 8)
+    for s in range(len(sizes)):
+        np.testing.assert_array_equal(u[:, off[s]:off[s + 1]], sep[s].cpu().numpy())
+        tree = oracle.Tree(xs[s], 150, True)
+        tree.set_moments(fs[s], hs[s], ns[s], 8)
+        assert oracle.rel_l2(u[:, off[s]:off[s + 1]].T, tree.treecode(xs[s], 0.5, 8)) <= 1e-6
+    b.close()
+
+
 def test_batch_without_graph_or_tuning_gives_the_same_result():
     sizes = [1500, 2700, 900]
     xs, fs, hs, ns, off = _systems(sizes, 720)

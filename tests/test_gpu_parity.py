@@ -174,6 +174,20 @@ def test_treecode_matches_oracle(prec, p, theta):
     assert err <= TOL[prec], err
 
 
+@pytest.mark.parametrize("p", [6, 8, 10])
+def test_mixed_fp64_recurrence_option(p):
+    # tc_config.rec64: FP64 recurrence for p >= 8 with the FP32 contraction;
+    # the same accuracy bound, and below p = 8 the default kernel runs
+    x, f, h, nu = inputs.uniform_cube(12000, 71)
+    tc = api.Treecode("mixed", True, rec64=True)
+    tc.build(dev(x), 150).moments(dev(f), dev(h), dev(nu), p)
+    u = host(tc.eval(0.5, p))
+    tc.close()
+    tree = oracle.Tree(x, 150, True)
+    tree.set_moments(f, h, nu, p)
+    assert oracle.rel_l2(u, tree.treecode(x, 0.5, p)) <= TOL["mixed"]
+
+
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("kind,N,N0,shrink", [("sphere", 20000, 200, True), ("clusters", 16384, 256, True),
                                               ("cube", 9001, 100, False), ("ico", 5, 300, True)])
