@@ -46,6 +46,7 @@ namespace tc {
 namespace {
 
 __constant__ LevelConst c_lev = make_level_const();
+__constant__ LevelConst32 c_lev32 = make_level_const32();
 
 inline unsigned grid_for(int64_t n, int threads)
 {
@@ -287,6 +288,186 @@ __global__ void __launch_bounds__(kNearAdjWarps * 32)
     }
 }
 
+// ------------------------------------------ near, mixed precision (FP32)
+// The same pair terms in FP32 on hi/lo positions (as the forward near field),
+// 1/r from rsqrtf, and every warp loop uniform: lanes outside an entry's mask
+// carry g = 0, which zeroes all their terms.
+
+struct NearPair32 {
+    float ri, st, c1, c3, c4, c5;
+};
+
+__device__ __forceinline__ NearPair32 near_pair32(float dx, float dy, float dz, float f0, float f1, float f2, float h0,
+                                                  float h1, float h2, float n0, float n1, float n2, float g0, float g1,
+                                                  float g2)
+{
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const float ri = r2 > 0.f ? rsqrtf(r2) : 0.f;
+    const float ri2 = ri * ri, ri3 = ri2 * ri, ri5 = ri3 * ri2;
+    const float df = fmaf(dx, f0, fmaf(dy, f1, dz * f2));
+    const float dh = fmaf(dx, h0, fmaf(dy, h1, dz * h2));
+    const float dn = fmaf(dx, n0, fmaf(dy, n1, dz * n2));
+    const float gd = fmaf(dx, g0, fmaf(dy, g1, dz * g2));
+    const float gf = fmaf(g0, f0, fmaf(g1, f1, g2 * f2));
+    const float t5 = dh * dn * ri5;  // (d.h)(d.nu)/r^5
+    NearPair32 o;
+    o.ri = ri;
+    o.st = fmaf(df, ri3, t5);
+    o.c3 = gd * ri3;
+    o.c1 = -fmaf(gf, ri3, gd * ri2 * fmaf(3.f * df, ri3, 5.f * t5));
+    o.c4 = o.c3 * dn * ri2;
+    o.c5 = o.c3 * dh * ri2;
+    return o;
+}
+
+// target side, batch-major: lanes are targets, the leaf's sources are
+// broadcast from a tile of 32 records (4 float4: x_hi, x_lo, f, h | nu)
+__global__ void __launch_bounds__(kNearAdjWarps * 32)
+    k_near_adj_target32(const double* __restrict__ ts, const double* __restrict__ gs, int64_t M,
+                        const int4* __restrict__ topo, const float4* __restrict__ spack,
+                        const int64_t* __restrict__ near_off, const ListEntry* __restrict__ near_list,
+                        double* __restrict__ gt)
+{
+    __shared__ float4 tile[kNearAdjWarps][32][4];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t nbatch = (M + kBatch - 1) / kBatch;
+    const int64_t b = blockIdx.x * (int64_t)kNearAdjWarps + w;
+    if (b >= nbatch) return;
+    const int64_t m = b * kBatch + lane;
+    const bool valid = m < M;
+    float th[3] = {0, 0, 0}, tl[3] = {0, 0, 0}, g[3] = {0, 0, 0};
+    if (valid)
+        for (int a = 0; a < 3; a++) {
+            const double v = ts[a * M + m];
+            th[a] = __double2float_rn(v);
+            tl[a] = __double2float_rn(v - (double)th[a]);
+            g[a] = __double2float_rn(gs[a * M + m]);
+        }
+    double acc0 = 0, acc1 = 0, acc2 = 0;
+    for (int64_t e = near_off[b]; e < near_off[b + 1]; e++) {
+        const ListEntry le = near_list[e];
+        const bool in = (le.mask >> lane) & 1u;
+        const int4 t = topo[le.node];
+        for (int base = t.x; base < t.x + t.y; base += 32) {
+            const int cnt = min(32, t.x + t.y - base);
+            __syncwarp();
+            if (lane < cnt) {
+                const float4* src = spack + 4 * (int64_t)(base + lane);
+                tile[w][lane][0] = src[0];  // (x_hi, f0)
+                tile[w][lane][1] = src[1];  // (x_lo, f1)
+                tile[w][lane][2] = src[2];  // (f2, h)
+                tile[w][lane][3] = src[3];  // (nu, 0)
+            }
+            __syncwarp();
+            if (!in) continue;
+            float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+            for (int j = 0; j < cnt; j++) {
+                const float4 A = tile[w][j][0], B = tile[w][j][1], C = tile[w][j][2], D = tile[w][j][3];
+                const float dx = (th[0] - A.x) + (tl[0] - B.x);
+                const float dy = (th[1] - A.y) + (tl[1] - B.y);
+                const float dz = (th[2] - A.z) + (tl[2] - B.z);
+                const NearPair32 q = near_pair32(dx, dy, dz, A.w, B.w, C.x, C.y, C.z, C.w, D.x, D.y, D.z, g[0], g[1],
+                                                 g[2]);
+                a0 += fmaf(dx, q.c1, fmaf(g[0], q.st, fmaf(A.w, q.c3, fmaf(C.y, q.c4, D.x * q.c5))));
+                a1 += fmaf(dy, q.c1, fmaf(g[1], q.st, fmaf(B.w, q.c3, fmaf(C.z, q.c4, D.y * q.c5))));
+                a2 += fmaf(dz, q.c1, fmaf(g[2], q.st, fmaf(C.x, q.c3, fmaf(C.w, q.c4, D.z * q.c5))));
+            }
+            acc0 += (double)a0;
+            acc1 += (double)a1;
+            acc2 += (double)a2;
+        }
+    }
+    if (valid) {
+        gt[m] += acc0;
+        gt[M + m] += acc1;
+        gt[2 * M + m] += acc2;
+    }
+}
+
+// source side, leaf-major: a block per leaf, a warp per 32 of its sources;
+// for every near entry naming the leaf the entry's 32 targets (x_hi | g0,
+// x_lo | g1, g2) are staged and every lane runs over all 32 of them
+__global__ void __launch_bounds__(kNearAdjWarps * 32)
+    k_near_adj_source32(const double* __restrict__ ts, const double* __restrict__ gs, int64_t M,
+                        const int4* __restrict__ topo, const float4* __restrict__ spack, int64_t N,
+                        const uint64_t* __restrict__ skeys, const int32_t* __restrict__ sidx,
+                        const ListEntry* __restrict__ near_list, const int32_t* __restrict__ ebatch, int64_t nent,
+                        double* __restrict__ gnear)
+{
+    __shared__ float4 tile[kNearAdjWarps][32][3];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t node = blockIdx.x;
+    const int4 t = topo[node];
+    if (t.w != 0) return;
+    const int64_t j0 = lower_key(skeys, nent, (uint64_t)node), j1 = lower_key(skeys, nent, (uint64_t)node + 1);
+    for (int tile0 = w * 32; tile0 < t.y; tile0 += kNearAdjWarps * 32) {
+        const int64_t si = t.x + tile0 + lane;
+        const bool valid = tile0 + lane < t.y;
+        float4 A = make_float4(0, 0, 0, 0), B = A, C = A, D = A;
+        if (valid) {
+            const float4* src = spack + 4 * si;
+            A = src[0], B = src[1], C = src[2], D = src[3];
+        }
+        const float sh0 = A.x, sh1 = A.y, sh2 = A.z, sl0 = B.x, sl1 = B.y, sl2 = B.z;
+        const float f0 = A.w, f1 = B.w, f2 = C.x, h0 = C.y, h1 = C.z, h2 = C.w, n0 = D.x, n1 = D.y, n2 = D.z;
+        double acc[12];
+#pragma unroll
+        for (int c = 0; c < 12; c++) acc[c] = 0.0;
+        for (int64_t j = j0; j < j1; j++) {
+            const int32_t e = sidx[j];
+            const unsigned mask = near_list[e].mask;
+            const int64_t m = (int64_t)ebatch[e] * kBatch + lane;
+            __syncwarp();
+            {
+                float4 p0 = make_float4(0, 0, 0, 0), p1 = p0, p2 = p0;
+                if ((mask >> lane) & 1u) {
+                    float xh[3], xl[3];
+                    for (int a = 0; a < 3; a++) {
+                        const double v = ts[a * M + m];
+                        xh[a] = __double2float_rn(v);
+                        xl[a] = __double2float_rn(v - (double)xh[a]);
+                    }
+                    p0 = make_float4(xh[0], xh[1], xh[2], __double2float_rn(gs[m]));
+                    p1 = make_float4(xl[0], xl[1], xl[2], __double2float_rn(gs[M + m]));
+                    p2 = make_float4(__double2float_rn(gs[2 * M + m]), 0.f, 0.f, 0.f);
+                }
+                tile[w][lane][0] = p0;
+                tile[w][lane][1] = p1;
+                tile[w][lane][2] = p2;
+            }
+            __syncwarp();
+            float a[12];
+#pragma unroll
+            for (int c = 0; c < 12; c++) a[c] = 0.f;
+#pragma unroll 2
+            for (int q = 0; q < 32; q++) {
+                const float4 T0 = tile[w][q][0], T1 = tile[w][q][1], T2 = tile[w][q][2];
+                const float g0 = T0.w, g1 = T1.w, g2 = T2.x;
+                const float dx = (T0.x - sh0) + (T1.x - sl0);
+                const float dy = (T0.y - sh1) + (T1.y - sl1);
+                const float dz = (T0.z - sh2) + (T1.z - sl2);
+                const NearPair32 z = near_pair32(dx, dy, dz, f0, f1, f2, h0, h1, h2, n0, n1, n2, g0, g1, g2);
+                a[0] += fmaf(g0, z.ri, dx * z.c3);
+                a[1] += fmaf(g1, z.ri, dy * z.c3);
+                a[2] += fmaf(g2, z.ri, dz * z.c3);
+                a[3] = fmaf(dx, z.c4, a[3]);
+                a[4] = fmaf(dy, z.c4, a[4]);
+                a[5] = fmaf(dz, z.c4, a[5]);
+                a[6] = fmaf(dx, z.c5, a[6]);
+                a[7] = fmaf(dy, z.c5, a[7]);
+                a[8] = fmaf(dz, z.c5, a[8]);
+                a[9] -= fmaf(dx, z.c1, fmaf(g0, z.st, fmaf(f0, z.c3, fmaf(h0, z.c4, n0 * z.c5))));
+                a[10] -= fmaf(dy, z.c1, fmaf(g1, z.st, fmaf(f1, z.c3, fmaf(h1, z.c4, n1 * z.c5))));
+                a[11] -= fmaf(dz, z.c1, fmaf(g2, z.st, fmaf(f2, z.c3, fmaf(h2, z.c4, n2 * z.c5))));
+            }
+#pragma unroll
+            for (int c = 0; c < 12; c++) acc[c] += (double)a[c];
+        }
+        if (valid)
+            for (int c = 0; c < 12; c++) gnear[c * N + si] = acc[c];
+    }
+}
+
 // --------------------------------------------------- far, target side
 // Batch-major like k_far; the recurrence runs to P + 1 = p + 3 and the
 // level-(n-1) values alpha^k are kept in a second two-slot store.
@@ -485,6 +666,276 @@ __global__ void __launch_bounds__(32)
     __syncwarp();
     if (cur >= 0)
         for (int q = lane; q < C2 * 12; q += 32) atomicAdd(&abar[cur * C2 * 12 + q], (double)acc[q]);
+}
+
+// ------------------------------------- far, mixed precision, folded tables
+// The forward far field in mixed precision is u_i = (1/R') sum_h c^h(v)
+// (T_i^h + d'_q T_{3+3i+q}^h) over the harmonic subset h (k1 <= 1) with the
+// folded, lambda-scaled FP32 tables T (tc_far.cu).  The folded sum equals the
+// unfolded one for every d', so it is differentiated as it stands.
+
+// Target side.  With b^k = lambda_n c^k / R' and d b^k/d d'_m =
+// -(k_m + 1) b^{k+e_m}:
+//   d(g.u)/dd'_m = (1/R') sum_h [ c^h gB_m^h - (k_m + 1) r_n c^{k+e_m} alpha^h ],
+//   alpha^h = g_i (T_i^h + d'_q T_{3+3i+q}^h),  gB_m^h = g_i T_{3+3i+m}^h,
+//   r_n = lambda_{n+1} / lambda_n = (2n+1)/(n+1),
+// so the recurrence runs to level P + 1.  k + e_1 leaves the subset when
+// k1 = 1; Laplace's identity on level n+1 gives
+//   c^{(2,a,b)} = -[(a+2)(a+1) c^{(0,a+2,b)} + (b+2)(b+1) c^{(0,a,b+2)}] / 2.
+// One warp per batch, one target per lane, three levels in registers.
+template <int P>
+__global__ void __launch_bounds__(32)
+    k_far_adj_target32(const double* __restrict__ ts, const double* __restrict__ gs, int64_t M,
+                       const float4* __restrict__ geo32, const float* __restrict__ ab,
+                       const int64_t* __restrict__ far_off, const ListEntry* __restrict__ far_list,
+                       double* __restrict__ gt)
+{
+    constexpr int H = (P + 1) * (P + 1);
+    const int lane = threadIdx.x & 31;
+    const int64_t b = blockIdx.x;
+    const int64_t m = b * kBatch + lane;
+    const bool valid = m < M;
+    float xh[3] = {0, 0, 0}, xl[3] = {0, 0, 0}, g[3] = {0, 0, 0};
+    if (valid)
+        for (int a = 0; a < 3; a++) {
+            const double v = ts[a * M + m];
+            xh[a] = __double2float_rn(v);
+            xl[a] = __double2float_rn(v - (double)xh[a]);
+            g[a] = __double2float_rn(gs[a * M + m]);
+        }
+    double G0 = 0, G1 = 0, G2 = 0;
+    for (int64_t e = far_off[b]; e < far_off[b + 1]; e++) {
+        const ListEntry le = far_list[e];
+        const bool in = (le.mask >> lane) & 1u;
+        const float4 gh = __ldg(geo32 + 2 * (int64_t)le.node), gl = __ldg(geo32 + 2 * (int64_t)le.node + 1);
+        const float d0 = ((xh[0] - gh.x) + (xl[0] - gl.x)) * gh.w;
+        const float d1 = ((xh[1] - gh.y) + (xl[1] - gl.y)) * gh.w;
+        const float d2 = ((xh[2] - gh.z) + (xl[2] - gl.z)) * gh.w;
+        float R2 = fmaf(d0, d0, fmaf(d1, d1, d2 * d2));
+        if (!in) R2 = 1.0f;
+        const float iR = rsqrtf(R2), iR2 = iR * iR;
+        const float v0 = d0 * iR2, v1 = d1 * iR2, v2 = d2 * iR2;
+        float wb[9];  // g_i d'_q
+        wb[0] = g[0] * d0, wb[1] = g[0] * d1, wb[2] = g[0] * d2;
+        wb[3] = g[1] * d0, wb[4] = g[1] * d1, wb[5] = g[1] * d2;
+        wb[6] = g[2] * d0, wb[7] = g[2] * d1, wb[8] = g[2] * d2;
+        const float4* __restrict__ tab = reinterpret_cast<const float4*>(ab + (int64_t)le.node * H * 12);
+        float cs[3][2 * P + 3];  // levels n-1, n, n+1 (slot = level mod 3)
+        cs[0][0] = 1.0f;
+        cs[1][0] = v1, cs[1][1] = v2, cs[1][2] = v0;  // level 1: (0,1,0), (0,0,1), (1,0,0)
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+#pragma unroll
+        for (int n = 0; n <= P; n++) {
+            if (n >= 1) {  // level n + 1 from levels n and n - 1
+                const float kap = c_lev32.kappa[n + 1] * iR2;
+#pragma unroll
+                for (int h = 2 * n + 2; h >= 0; h--)
+                    cs[(n + 1) % 3][h] = hcoef_r(cs[n % 3], cs[(n + 2) % 3], n + 1, h, v0, v1, v2, kap);
+            }
+            const float rn = (float)(2 * n + 1) / (float)(n + 1);
+            const float* C1 = cs[(n + 1) % 3];
+#pragma unroll
+            for (int h = 0; h <= 2 * n; h++) {
+                const float4 ta = __ldg(tab + 3 * (n * n + h)), tb = __ldg(tab + 3 * (n * n + h) + 1),
+                             tc = __ldg(tab + 3 * (n * n + h) + 2);
+                // T_0..2 = ta.xyz; T_3+3i+q: i = 0 -> ta.w tb.x tb.y, i = 1 -> tb.z tb.w tc.x,
+                // i = 2 -> tc.y tc.z tc.w
+                const float gB0 = fmaf(g[0], ta.w, fmaf(g[1], tb.z, g[2] * tc.y));
+                const float gB1 = fmaf(g[0], tb.x, fmaf(g[1], tb.w, g[2] * tc.z));
+                const float gB2 = fmaf(g[0], tb.y, fmaf(g[1], tc.x, g[2] * tc.w));
+                float al = fmaf(g[0], ta.x, fmaf(g[1], ta.y, g[2] * ta.z));
+                al = fmaf(wb[0], ta.w, fmaf(wb[1], tb.x, fmaf(wb[2], tb.y, al)));
+                al = fmaf(wb[3], tb.z, fmaf(wb[4], tb.w, fmaf(wb[5], tc.x, al)));
+                al = fmaf(wb[6], tc.y, fmaf(wb[7], tc.z, fmaf(wb[8], tc.w, al)));
+                const float c = cs[n % 3][h];
+                a0 = fmaf(c, gB0, a0);
+                a1 = fmaf(c, gB1, a1);
+                a2 = fmaf(c, gB2, a2);
+                float e0, e1, e2;  // (k_m + 1) r_n c^{k+e_m}
+                if (h <= n) {      // k = (0, n-h, h)
+                    const int k2 = n - h, k3 = h;
+                    e0 = rn * C1[n + 2 + h];
+                    e1 = (float)(k2 + 1) * rn * C1[h];
+                    e2 = (float)(k3 + 1) * rn * C1[h + 1];
+                } else {  // k = (1, a, b)
+                    const int bq = h - n - 1, aq = n - 1 - bq;
+                    e0 = -rn * fmaf((float)((aq + 2) * (aq + 1)), C1[bq], (float)((bq + 2) * (bq + 1)) * C1[bq + 2]);
+                    e1 = (float)(aq + 1) * rn * C1[h + 1];
+                    e2 = (float)(bq + 1) * rn * C1[h + 2];
+                }
+                a0 = fmaf(-e0, al, a0);
+                a1 = fmaf(-e1, al, a1);
+                a2 = fmaf(-e2, al, a2);
+            }
+        }
+        if (in) {
+            const float s = iR * gh.w;  // 1/R' and d'/dx = 1/rho
+            G0 += (double)(a0 * s);
+            G1 += (double)(a1 * s);
+            G2 += (double)(a2 * s);
+        }
+    }
+    if (valid) {
+        gt[m] = G0;
+        gt[M + m] = G1;
+        gt[2 * M + m] = G2;
+    }
+}
+
+// Source side.  The forward map is linear in the folded tables:
+//   dL/dT_i^h = sum_m g_i^m c^h(v_m)/R'_m,  dL/dT_{3+3i+q}^h = sum_m g_i^m d'_qm c^h(v_m)/R'_m,
+// over the targets m that accept the cluster.  Cluster-major over the far
+// entries sorted by cluster; per entry every lane (target) computes its
+// coefficients into shared memory, then each lane sums, for the coefficients
+// it owns, over the 32 targets (a 32 x (P+1)^2 by 32 x 12 product); the
+// accumulators go to the cluster's FP64 folded adjoint tables with atomics
+// when the cluster changes.  Lanes outside the mask carry g = 0.
+template <int P>
+__global__ void __launch_bounds__(32)
+    k_far_adj_source32(const double* __restrict__ ts, const double* __restrict__ gs, int64_t M,
+                       const float4* __restrict__ geo32, const uint64_t* __restrict__ skeys,
+                       const int32_t* __restrict__ sidx, const ListEntry* __restrict__ far_list,
+                       const int32_t* __restrict__ ebatch, int64_t nent, int chunk, double* __restrict__ fbar)
+{
+    constexpr int H = (P + 1) * (P + 1);
+    constexpr int NPL = (H + 31) / 32;
+    __shared__ float sc[H][33];
+    __shared__ __align__(16) float wt[32][12];
+    const int lane = threadIdx.x & 31;
+    const int64_t j0 = (int64_t)blockIdx.x * chunk;
+    if (j0 >= nent) return;
+    const int64_t j1 = min(nent, j0 + chunk);
+    float acc[NPL][12];
+#pragma unroll
+    for (int q = 0; q < NPL; q++)
+#pragma unroll
+        for (int c = 0; c < 12; c++) acc[q][c] = 0.f;
+    int64_t cur = -1;
+    for (int64_t j = j0; j <= j1; j++) {
+        const int64_t node = j < j1 ? (int64_t)skeys[j] : -2;
+        if (node != cur) {
+            if (cur >= 0) {
+#pragma unroll
+                for (int q = 0; q < NPL; q++) {
+                    const int h = lane + 32 * q;
+                    if (h < H)
+                        for (int c = 0; c < 12; c++) atomicAdd(&fbar[(cur * H + h) * 12 + c], (double)acc[q][c]);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < NPL; q++)
+#pragma unroll
+                for (int c = 0; c < 12; c++) acc[q][c] = 0.f;
+            cur = node;
+        }
+        if (j == j1) break;
+        const int32_t e = sidx[j];
+        const unsigned mask = far_list[e].mask;
+        const int64_t m = (int64_t)ebatch[e] * kBatch + lane;
+        const bool in = (mask >> lane) & 1u;
+        float xh[3] = {0, 0, 0}, xl[3] = {0, 0, 0}, g[3] = {0, 0, 0};
+        if (in)
+            for (int a = 0; a < 3; a++) {
+                const double v = ts[a * M + m];
+                xh[a] = __double2float_rn(v);
+                xl[a] = __double2float_rn(v - (double)xh[a]);
+                g[a] = __double2float_rn(gs[a * M + m]);
+            }
+        const float4 gh = __ldg(geo32 + 2 * node), gl = __ldg(geo32 + 2 * node + 1);
+        const float d0 = ((xh[0] - gh.x) + (xl[0] - gl.x)) * gh.w;
+        const float d1 = ((xh[1] - gh.y) + (xl[1] - gl.y)) * gh.w;
+        const float d2 = ((xh[2] - gh.z) + (xl[2] - gl.z)) * gh.w;
+        float R2 = fmaf(d0, d0, fmaf(d1, d1, d2 * d2));
+        if (!in) R2 = 1.0f;
+        const float iR = rsqrtf(R2), iR2 = iR * iR;
+        const float v0 = d0 * iR2, v1 = d1 * iR2, v2 = d2 * iR2;
+        __syncwarp();
+        {
+            float* w = wt[lane];
+            w[0] = g[0], w[1] = g[1], w[2] = g[2];
+            w[3] = g[0] * d0, w[4] = g[0] * d1, w[5] = g[0] * d2;
+            w[6] = g[1] * d0, w[7] = g[1] * d1, w[8] = g[1] * d2;
+            w[9] = g[2] * d0, w[10] = g[2] * d1, w[11] = g[2] * d2;
+        }
+        float cs[2][2 * P + 1];
+        cs[0][0] = 1.0f;
+        sc[0][lane] = iR;
+#pragma unroll
+        for (int n = 1; n <= P; n++) {
+            const float kap = c_lev32.kappa[n] * iR2;
+#pragma unroll
+            for (int h = 2 * n; h >= 0; h--) {
+                const float cf = hcoef_r(cs[(n - 1) & 1], cs[n & 1], n, h, v0, v1, v2, kap);
+                cs[n & 1][h] = cf;
+                sc[n * n + h][lane] = cf * iR;
+            }
+        }
+        __syncwarp();
+        for (int t = 0; t < 32; t++) {
+            const float4* w4 = reinterpret_cast<const float4*>(wt[t]);
+            const float4 wa = w4[0], wb = w4[1], wc = w4[2];
+#pragma unroll
+            for (int q = 0; q < NPL; q++) {
+                const int h = lane + 32 * q;
+                const float s = h < H ? sc[h < H ? h : 0][t] : 0.f;
+                acc[q][0] = fmaf(s, wa.x, acc[q][0]);
+                acc[q][1] = fmaf(s, wa.y, acc[q][1]);
+                acc[q][2] = fmaf(s, wa.z, acc[q][2]);
+                acc[q][3] = fmaf(s, wa.w, acc[q][3]);
+                acc[q][4] = fmaf(s, wb.x, acc[q][4]);
+                acc[q][5] = fmaf(s, wb.y, acc[q][5]);
+                acc[q][6] = fmaf(s, wb.z, acc[q][6]);
+                acc[q][7] = fmaf(s, wb.w, acc[q][7]);
+                acc[q][8] = fmaf(s, wc.x, acc[q][8]);
+                acc[q][9] = fmaf(s, wc.y, acc[q][9]);
+                acc[q][10] = fmaf(s, wc.z, acc[q][10]);
+                acc[q][11] = fmaf(s, wc.w, acc[q][11]);
+            }
+        }
+    }
+}
+
+// Adjoint of the folding (k_fold_tables): from the adjoint of the folded,
+// lambda-scaled tables (fbar, [node][(P+1)^2][12]) to the adjoint of the full
+// tables (abar, [node][C(P+3,3)][12]).  The folding pushes row k1 of a level
+// onto rows k1-2 (k1 from n down to 2) and keeps k1 in {0, 1}, scaled by
+// lambda_n; its transpose seeds k1 in {0, 1} with lambda_n fbar and pulls
+// row k1 from rows k1-2, k1 from 2 up to n.  FP64, one block per cluster.
+__global__ void k_unfold_adj(const double* __restrict__ fbar, int64_t nnodes, int p, double* __restrict__ abar)
+{
+    extern __shared__ double lvb[];  // one level: [position][12]
+    const int64_t node = blockIdx.x;
+    const int P = p + 2;
+    const int C2 = ncoef(P), H = hsize(P);
+    double lambda = 1.0;
+    for (int n = 0; n <= P; n++) {
+        if (n > 0) lambda *= (double)(2 * n - 1) / (double)n;
+        const int L = level_size(n);
+        for (int q = threadIdx.x; q < L * 12; q += blockDim.x) lvb[q] = 0.0;
+        __syncthreads();
+        for (int q = threadIdx.x; q < (2 * n + 1) * 12; q += blockDim.x) {
+            const int h = q / 12, c = q % 12;
+            const int pos = h <= n ? n * (n + 1) / 2 + h : (n - 1) * n / 2 + (h - n - 1);
+            lvb[pos * 12 + c] = lambda * fbar[((int64_t)node * H + n * n + h) * 12 + c];
+        }
+        __syncthreads();
+        for (int k1 = 2; k1 <= n; k1++) {
+            const int a = n - k1, a2 = a + 2;
+            const double inv = 1.0 / ((double)k1 * (k1 - 1));
+            for (int q = threadIdx.x; q < (a + 1) * 12; q += blockDim.x) {
+                const int k3 = q / 12, c = q % 12, k2 = a - k3;
+                const int src = a * (a + 1) / 2 + k3;
+                const int dst2 = a2 * (a2 + 1) / 2 + k3, dst3 = dst2 + 2;
+                const double f2 = -(double)((k2 + 2) * (k2 + 1)) * inv, f3 = -(double)((k3 + 2) * (k3 + 1)) * inv;
+                lvb[src * 12 + c] += f2 * lvb[dst2 * 12 + c] + f3 * lvb[dst3 * 12 + c];
+            }
+            __syncthreads();
+        }
+        const int base = n > 0 ? ncoef(n - 1) : 0;
+        for (int q = threadIdx.x; q < L * 12; q += blockDim.x)
+            abar[((int64_t)node * C2 + base) * 12 + q] = lvb[q];
+        __syncthreads();
+    }
 }
 
 // ------------------------------------------- adjoint moments (table transpose)
@@ -738,6 +1189,52 @@ cudaError_t run_far_adj(tc_ctx* ctx, const double* ts, int64_t M, int p, cudaStr
     return cudaGetLastError();
 }
 
+// Mixed precision: the folded-table adjoint (target side, source side into
+// the folded adjoint tables, then their unfolding into adj_abar).
+template <int P>
+cudaError_t run_far_adj32(tc_ctx* ctx, const double* ts, int64_t M, cudaStream_t s)
+{
+    const int p = P - 2;
+    const int64_t nbatch = (M + kBatch - 1) / kBatch;
+    const int64_t nnodes = ctx->nnodes;
+    const int H = hsize(P);
+    k_far_adj_target32<P><<<(unsigned)nbatch, 32, 0, s>>>(ts, ptr<double>(ctx->adj_gs), M, ptr<float4>(ctx->geo32),
+                                                          ptr<float>(ctx->abf32), ptr<int64_t>(ctx->far_off),
+                                                          ptr<ListEntry>(ctx->far_list), ptr<double>(ctx->adj_gt));
+    note_launch();
+    cudaError_t e = ensure(ctx->adj_fbar, (size_t)nnodes * H * 12 * 8);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(ctx->adj_fbar.p, 0, (size_t)nnodes * H * 12 * 8, s);
+    if (e != cudaSuccess) return e;
+    const int64_t nent = ctx->far_entries;
+    if (nent > 0) {
+        k_far_adj_source32<P><<<grid_for(nent, kFarAdjChunk), 32, 0, s>>>(
+            ts, ptr<double>(ctx->adj_gs), M, ptr<float4>(ctx->geo32), ptr<uint64_t>(ctx->adj_fkeys),
+            ptr<int32_t>(ctx->adj_fidx), ptr<ListEntry>(ctx->far_list), ptr<int32_t>(ctx->adj_febatch), nent,
+            kFarAdjChunk, ptr<double>(ctx->adj_fbar));
+        note_launch();
+    }
+    const size_t smem = (size_t)level_size(P) * 12 * sizeof(double);
+    e = cudaFuncSetAttribute(k_unfold_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_unfold_adj<<<(unsigned)nnodes, 128, smem, s>>>(ptr<double>(ctx->adj_fbar), nnodes, p, ptr<double>(ctx->adj_abar));
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_far_adj32(tc_ctx* ctx, const double* ts, int64_t M, int p, cudaStream_t s)
+{
+    switch (p + 2) {
+#define TC_FARADJ_CASE(P) \
+    case P: return run_far_adj32<P>(ctx, ts, M, s);
+        TC_FARADJ_CASE(2) TC_FARADJ_CASE(3) TC_FARADJ_CASE(4) TC_FARADJ_CASE(5) TC_FARADJ_CASE(6)
+        TC_FARADJ_CASE(7) TC_FARADJ_CASE(8) TC_FARADJ_CASE(9) TC_FARADJ_CASE(10) TC_FARADJ_CASE(11)
+        TC_FARADJ_CASE(12) TC_FARADJ_CASE(13) TC_FARADJ_CASE(14)
+#undef TC_FARADJ_CASE
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 // Sort one of the forward lists by cluster: keys/idx sorted, batch per entry.
 cudaError_t sort_entries(const ListEntry* list, int64_t n, const int64_t* off, int64_t nbatch, int64_t nnodes,
                          DevBuf& keys, DevBuf& keys_alt, DevBuf& idx, DevBuf& idx_alt, DevBuf& eb, DevBuf& hist,
@@ -817,10 +1314,8 @@ extern "C" tc_status tc_adjoint(tc_ctx* ctx, const double* g, double* grad_f, do
     cudaError_t e;
     if (ctx->precision == TC_FP64)
         e = run_far_adj<double, double>(ctx, ts, M, p, s);
-    else if (p >= 8)
-        e = run_far_adj<double, float>(ctx, ts, M, p, s);
     else
-        e = run_far_adj<float, float>(ctx, ts, M, p, s);
+        e = launch_far_adj32(ctx, ts, M, p, s);
     TC_CK(e, "far adjoint");
 
     // near field: target side adds to adj_gt; source side writes adj_gnear
@@ -836,12 +1331,12 @@ extern "C" tc_status tc_adjoint(tc_ctx* ctx, const double* g, double* grad_f, do
             ptr<int32_t>(ctx->adj_nebatch), ctx->near_entries, ptr<double>(ctx->adj_gnear));
         note_launch();
     } else {
-        k_near_adj_target<float><<<ngrid, kNearAdjWarps * 32, 0, s>>>(
-            ts, ptr<double>(ctx->adj_gs), M, ptr<int4>(ctx->node_topo), ptr<double>(ctx->xs), ptr<double>(ctx->ws), N,
+        k_near_adj_target32<<<ngrid, kNearAdjWarps * 32, 0, s>>>(
+            ts, ptr<double>(ctx->adj_gs), M, ptr<int4>(ctx->node_topo), ptr<float4>(ctx->spack),
             ptr<int64_t>(ctx->near_off), ptr<ListEntry>(ctx->near_list), ptr<double>(ctx->adj_gt));
         note_launch();
-        k_near_adj_source<float><<<(unsigned)nnodes, kNearAdjWarps * 32, 0, s>>>(
-            ts, ptr<double>(ctx->adj_gs), M, ptr<int4>(ctx->node_topo), ptr<double>(ctx->xs), ptr<double>(ctx->ws), N,
+        k_near_adj_source32<<<(unsigned)nnodes, kNearAdjWarps * 32, 0, s>>>(
+            ts, ptr<double>(ctx->adj_gs), M, ptr<int4>(ctx->node_topo), ptr<float4>(ctx->spack), N,
             ptr<uint64_t>(ctx->adj_nkeys), ptr<int32_t>(ctx->adj_nidx), ptr<ListEntry>(ctx->near_list),
             ptr<int32_t>(ctx->adj_nebatch), ctx->near_entries, ptr<double>(ctx->adj_gnear));
         note_launch();

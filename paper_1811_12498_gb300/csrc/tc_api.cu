@@ -121,7 +121,7 @@ static void release_all(tc_ctx* c)
                       &c->far_off, &c->near_off, &c->far_list, &c->near_list, &c->cnt_far, &c->cnt_near, &c->u_far,
                       &c->u_near, &c->flags, &c->adj_fkeys, &c->adj_fkeys_alt, &c->adj_fidx, &c->adj_fidx_alt,
                       &c->adj_febatch, &c->adj_nkeys, &c->adj_nkeys_alt, &c->adj_nidx, &c->adj_nidx_alt,
-                      &c->adj_nebatch, &c->adj_hist, &c->adj_gs, &c->adj_gt, &c->adj_abar, &c->adj_lam,
+                      &c->adj_nebatch, &c->adj_hist, &c->adj_gs, &c->adj_gt, &c->adj_abar, &c->adj_fbar, &c->adj_lam,
                       &c->adj_lamacc, &c->adj_gfar, &c->adj_gnear};
     for (DevBuf* b : bufs) release(*b);
 }

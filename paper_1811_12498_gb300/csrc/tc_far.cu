@@ -57,17 +57,6 @@ namespace {
 
 __constant__ LevelConst c_lev = make_level_const();
 
-// kappa_n in FP32 for the register kernels
-struct LevelConst32 {
-    float kappa[kQMax + 2];
-};
-__host__ __device__ constexpr LevelConst32 make_level_const32()
-{
-    LevelConst32 c{};
-    for (int n = 0; n <= kQMax + 1; n++)
-        c.kappa[n] = n >= 2 ? (float)((double)((n - 1) * (n - 1)) / (double)((2 * n - 1) * (2 * n - 3))) : 0.0f;
-    return c;
-}
 __constant__ LevelConst32 c_lev32 = make_level_const32();
 
 // ---------------------------------------------------------------------------
@@ -212,42 +201,6 @@ __device__ inline void far_slots(unsigned char* smraw, int p, int w, double*& sl
 
 // ---------------------------------------------------------------------------
 // FP32, compile-time order: coefficients in registers
-
-// c^k at level n, subset position h; R1 = level n-1, R2 = level n-2 (n, h
-// are compile-time constants after unrolling, so every branch folds away)
-__device__ __forceinline__ float hcoef_r(const float* R1, const float* R2, int n, int h, float v0, float v1, float v2,
-                                         float kap)
-{
-    float s1 = 0.0f, s2 = 0.0f;
-    bool any2 = false;
-    if (h <= n) {
-        const int k3 = h, k2 = n - h;
-        if (k2 >= 1) s1 = v1 * R1[k3];
-        if (k3 >= 1) s1 = k2 >= 1 ? fmaf(v2, R1[k3 - 1], s1) : v2 * R1[k3 - 1];
-        if (k2 >= 2) {
-            s2 = R2[k3];
-            any2 = true;
-        }
-        if (k3 >= 2) {
-            s2 = any2 ? s2 + R2[k3 - 2] : R2[k3 - 2];
-            any2 = true;
-        }
-    } else {
-        const int k3 = h - n - 1, k2 = n - 1 - k3;
-        s1 = v0 * R1[k3];
-        if (k2 >= 1) s1 = fmaf(v1, R1[n + k3], s1);
-        if (k3 >= 1) s1 = fmaf(v2, R1[n + k3 - 1], s1);
-        if (k2 >= 2) {
-            s2 = R2[n - 1 + k3];
-            any2 = true;
-        }
-        if (k3 >= 2) {
-            s2 = any2 ? s2 + R2[n - 3 + k3] : R2[n - 3 + k3];
-            any2 = true;
-        }
-    }
-    return any2 ? fmaf(-kap, s2, s1) : s1;
-}
 
 __device__ __forceinline__ void contract12f(float c, const float4* __restrict__ t, float* tot)
 {

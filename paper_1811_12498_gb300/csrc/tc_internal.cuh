@@ -147,6 +147,7 @@ struct tc_ctx {
     tc::DevBuf adj_hist;
     tc::DevBuf adj_gs, adj_gt;            // 3*M sorted g and target-position gradient
     tc::DevBuf adj_abar;                  // FP64 [node][ncoef(p+2)][12] adjoint of the tables
+    tc::DevBuf adj_fbar;                  // FP64 [node][(p+3)^2][12] adjoint of the folded tables (mixed)
     tc::DevBuf adj_lam, adj_lamacc;       // FP64 [node][12][ncoef(p)] adjoint moments, accumulated down
     tc::DevBuf adj_gfar, adj_gnear;       // 12*N FP64 sorted: d/df, d/dh, d/dnu, d/dx
     int adj_lists_ready = 0;              // sorted lists match the last tc_eval

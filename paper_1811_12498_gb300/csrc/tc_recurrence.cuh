@@ -1,6 +1,7 @@
 // Device helpers shared by the far-field kernels (tc_far.cu) and the adjoint
 // (tc_adjoint.cu): the Coulomb-coefficient recurrence (3.2) on a unit
-// direction, the level constants, and the FP64 -> FP32 narrowing.
+// direction (full index set, FP64 or FP32), its scale-free FP32 form on the
+// harmonic subset, the level constants, and the FP64 -> FP32 narrowing.
 //
 // With w = d'/|d'| and b^k(w) = lambda_n c^k, lambda_n = prod_{j<=n} (2j-1)/j,
 // recurrence (3.2) becomes
@@ -25,6 +26,58 @@ __host__ __device__ constexpr LevelConst make_level_const()
         c.ratio[n] = n >= 1 ? (double)(2 * n - 1) / (double)n : 1.0;
     }
     return c;
+}
+
+// kappa_n in FP32 for the register kernels
+struct LevelConst32 {
+    float kappa[kQMax + 2];
+};
+__host__ __device__ constexpr LevelConst32 make_level_const32()
+{
+    LevelConst32 c{};
+    for (int n = 0; n <= kQMax + 1; n++)
+        c.kappa[n] = n >= 2 ? (float)((double)((n - 1) * (n - 1)) / (double)((2 * n - 1) * (2 * n - 3))) : 0.0f;
+    return c;
+}
+
+// The harmonic subset (k1 <= 1) of level n, 2n+1 coefficients, is stored by
+// position h: k = (0, n-h, h) for h <= n, k = (1, n-1-k3, k3) with
+// k3 = h-n-1 above.  hcoef_r: c^k of level n at position h of the
+// subset from R1 = level n-1 and R2 = level n-2 (scale-free recurrence,
+// tc_far.cu); n and h are compile-time constants after unrolling, so every
+// branch folds away.
+__device__ __forceinline__ float hcoef_r(const float* R1, const float* R2, int n, int h, float v0, float v1, float v2,
+                                         float kap)
+{
+    float s1 = 0.0f, s2 = 0.0f;
+    bool any2 = false;
+    if (h <= n) {
+        const int k3 = h, k2 = n - h;
+        if (k2 >= 1) s1 = v1 * R1[k3];
+        if (k3 >= 1) s1 = k2 >= 1 ? fmaf(v2, R1[k3 - 1], s1) : v2 * R1[k3 - 1];
+        if (k2 >= 2) {
+            s2 = R2[k3];
+            any2 = true;
+        }
+        if (k3 >= 2) {
+            s2 = any2 ? s2 + R2[k3 - 2] : R2[k3 - 2];
+            any2 = true;
+        }
+    } else {
+        const int k3 = h - n - 1, k2 = n - 1 - k3;
+        s1 = v0 * R1[k3];
+        if (k2 >= 1) s1 = fmaf(v1, R1[n + k3], s1);
+        if (k3 >= 1) s1 = fmaf(v2, R1[n + k3 - 1], s1);
+        if (k2 >= 2) {
+            s2 = R2[n - 1 + k3];
+            any2 = true;
+        }
+        if (k3 >= 2) {
+            s2 = any2 ? s2 + R2[n - 3 + k3] : R2[n - 3 + k3];
+            any2 = true;
+        }
+    }
+    return any2 ? fmaf(-kap, s2, s1) : s1;
 }
 
 // FP64 -> FP32 by bit manipulation: round the magnitude to 23 mantissa bits
