@@ -384,9 +384,14 @@ __global__ void __launch_bounds__(kNearAdjWarps * 32)
     }
 }
 
-// source side, leaf-major: a block per leaf, a warp per 32 of its sources;
-// for every near entry naming the leaf the entry's 32 targets (x_hi | g0,
-// x_lo | g1, g2) are staged and every lane runs over all 32 of them
+// source side over the near entries sorted by leaf, in chunks of
+// kNearAdjChunk entries (a chunk can straddle leaves): for each leaf segment
+// of its chunk a block runs a warp per 32 of the leaf's sources over the
+// segment's entries; each entry's 32 targets (x_hi | g0, x_lo | g1, g2) are
+// staged and every lane runs over all 32 of them.  Per-segment sums are added
+// to the FP64 source gradients with atomics (gnear is zeroed first).
+constexpr int kNearAdjChunk = 64;
+
 __global__ void __launch_bounds__(kNearAdjWarps * 32)
     k_near_adj_source32(const double* __restrict__ ts, const double* __restrict__ gs, int64_t M,
                         const int4* __restrict__ topo, const float4* __restrict__ spack, int64_t N,
@@ -396,75 +401,79 @@ __global__ void __launch_bounds__(kNearAdjWarps * 32)
 {
     __shared__ float4 tile[kNearAdjWarps][32][3];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t node = blockIdx.x;
-    const int4 t = topo[node];
-    if (t.w != 0) return;
-    const int64_t j0 = lower_key(skeys, nent, (uint64_t)node), j1 = lower_key(skeys, nent, (uint64_t)node + 1);
-    for (int tile0 = w * 32; tile0 < t.y; tile0 += kNearAdjWarps * 32) {
-        const int64_t si = t.x + tile0 + lane;
-        const bool valid = tile0 + lane < t.y;
-        float4 A = make_float4(0, 0, 0, 0), B = A, C = A, D = A;
-        if (valid) {
-            const float4* src = spack + 4 * si;
-            A = src[0], B = src[1], C = src[2], D = src[3];
-        }
-        const float sh0 = A.x, sh1 = A.y, sh2 = A.z, sl0 = B.x, sl1 = B.y, sl2 = B.z;
-        const float f0 = A.w, f1 = B.w, f2 = C.x, h0 = C.y, h1 = C.z, h2 = C.w, n0 = D.x, n1 = D.y, n2 = D.z;
-        double acc[12];
+    const int64_t c0 = (int64_t)blockIdx.x * kNearAdjChunk;
+    const int64_t c1 = min(nent, c0 + kNearAdjChunk);
+    for (int64_t js = c0; js < c1;) {
+        const uint64_t node = skeys[js];
+        const int64_t je = min(c1, lower_key(skeys, nent, node + 1));
+        const int4 t = topo[node];
+        for (int tile0 = w * 32; tile0 < t.y; tile0 += kNearAdjWarps * 32) {
+            const int64_t si = t.x + tile0 + lane;
+            const bool valid = tile0 + lane < t.y;
+            float4 A = make_float4(0, 0, 0, 0), B = A, C = A, D = A;
+            if (valid) {
+                const float4* src = spack + 4 * si;
+                A = src[0], B = src[1], C = src[2], D = src[3];
+            }
+            const float sh0 = A.x, sh1 = A.y, sh2 = A.z, sl0 = B.x, sl1 = B.y, sl2 = B.z;
+            const float f0 = A.w, f1 = B.w, f2 = C.x, h0 = C.y, h1 = C.z, h2 = C.w, n0 = D.x, n1 = D.y, n2 = D.z;
+            double acc[12];
 #pragma unroll
-        for (int c = 0; c < 12; c++) acc[c] = 0.0;
-        for (int64_t j = j0; j < j1; j++) {
-            const int32_t e = sidx[j];
-            const unsigned mask = near_list[e].mask;
-            const int64_t m = (int64_t)ebatch[e] * kBatch + lane;
-            __syncwarp();
-            {
-                float4 p0 = make_float4(0, 0, 0, 0), p1 = p0, p2 = p0;
-                if ((mask >> lane) & 1u) {
-                    float xh[3], xl[3];
-                    for (int a = 0; a < 3; a++) {
-                        const double v = ts[a * M + m];
-                        xh[a] = __double2float_rn(v);
-                        xl[a] = __double2float_rn(v - (double)xh[a]);
+            for (int c = 0; c < 12; c++) acc[c] = 0.0;
+            for (int64_t j = js; j < je; j++) {
+                const int32_t e = sidx[j];
+                const unsigned mask = near_list[e].mask;
+                const int64_t m = (int64_t)ebatch[e] * kBatch + lane;
+                __syncwarp();
+                {
+                    float4 p0 = make_float4(0, 0, 0, 0), p1 = p0, p2 = p0;
+                    if ((mask >> lane) & 1u) {
+                        float xh[3], xl[3];
+                        for (int a = 0; a < 3; a++) {
+                            const double v = ts[a * M + m];
+                            xh[a] = __double2float_rn(v);
+                            xl[a] = __double2float_rn(v - (double)xh[a]);
+                        }
+                        p0 = make_float4(xh[0], xh[1], xh[2], __double2float_rn(gs[m]));
+                        p1 = make_float4(xl[0], xl[1], xl[2], __double2float_rn(gs[M + m]));
+                        p2 = make_float4(__double2float_rn(gs[2 * M + m]), 0.f, 0.f, 0.f);
                     }
-                    p0 = make_float4(xh[0], xh[1], xh[2], __double2float_rn(gs[m]));
-                    p1 = make_float4(xl[0], xl[1], xl[2], __double2float_rn(gs[M + m]));
-                    p2 = make_float4(__double2float_rn(gs[2 * M + m]), 0.f, 0.f, 0.f);
+                    tile[w][lane][0] = p0;
+                    tile[w][lane][1] = p1;
+                    tile[w][lane][2] = p2;
                 }
-                tile[w][lane][0] = p0;
-                tile[w][lane][1] = p1;
-                tile[w][lane][2] = p2;
-            }
-            __syncwarp();
-            float a[12];
+                __syncwarp();
+                float a[12];
 #pragma unroll
-            for (int c = 0; c < 12; c++) a[c] = 0.f;
+                for (int c = 0; c < 12; c++) a[c] = 0.f;
 #pragma unroll 2
-            for (int q = 0; q < 32; q++) {
-                const float4 T0 = tile[w][q][0], T1 = tile[w][q][1], T2 = tile[w][q][2];
-                const float g0 = T0.w, g1 = T1.w, g2 = T2.x;
-                const float dx = (T0.x - sh0) + (T1.x - sl0);
-                const float dy = (T0.y - sh1) + (T1.y - sl1);
-                const float dz = (T0.z - sh2) + (T1.z - sl2);
-                const NearPair32 z = near_pair32(dx, dy, dz, f0, f1, f2, h0, h1, h2, n0, n1, n2, g0, g1, g2);
-                a[0] += fmaf(g0, z.ri, dx * z.c3);
-                a[1] += fmaf(g1, z.ri, dy * z.c3);
-                a[2] += fmaf(g2, z.ri, dz * z.c3);
-                a[3] = fmaf(dx, z.c4, a[3]);
-                a[4] = fmaf(dy, z.c4, a[4]);
-                a[5] = fmaf(dz, z.c4, a[5]);
-                a[6] = fmaf(dx, z.c5, a[6]);
-                a[7] = fmaf(dy, z.c5, a[7]);
-                a[8] = fmaf(dz, z.c5, a[8]);
-                a[9] -= fmaf(dx, z.c1, fmaf(g0, z.st, fmaf(f0, z.c3, fmaf(h0, z.c4, n0 * z.c5))));
-                a[10] -= fmaf(dy, z.c1, fmaf(g1, z.st, fmaf(f1, z.c3, fmaf(h1, z.c4, n1 * z.c5))));
-                a[11] -= fmaf(dz, z.c1, fmaf(g2, z.st, fmaf(f2, z.c3, fmaf(h2, z.c4, n2 * z.c5))));
-            }
+                for (int q = 0; q < 32; q++) {
+                    const float4 T0 = tile[w][q][0], T1 = tile[w][q][1], T2 = tile[w][q][2];
+                    const float g0 = T0.w, g1 = T1.w, g2 = T2.x;
+                    const float dx = (T0.x - sh0) + (T1.x - sl0);
+                    const float dy = (T0.y - sh1) + (T1.y - sl1);
+                    const float dz = (T0.z - sh2) + (T1.z - sl2);
+                    const NearPair32 z = near_pair32(dx, dy, dz, f0, f1, f2, h0, h1, h2, n0, n1, n2, g0, g1, g2);
+                    a[0] += fmaf(g0, z.ri, dx * z.c3);
+                    a[1] += fmaf(g1, z.ri, dy * z.c3);
+                    a[2] += fmaf(g2, z.ri, dz * z.c3);
+                    a[3] = fmaf(dx, z.c4, a[3]);
+                    a[4] = fmaf(dy, z.c4, a[4]);
+                    a[5] = fmaf(dz, z.c4, a[5]);
+                    a[6] = fmaf(dx, z.c5, a[6]);
+                    a[7] = fmaf(dy, z.c5, a[7]);
+                    a[8] = fmaf(dz, z.c5, a[8]);
+                    a[9] -= fmaf(dx, z.c1, fmaf(g0, z.st, fmaf(f0, z.c3, fmaf(h0, z.c4, n0 * z.c5))));
+                    a[10] -= fmaf(dy, z.c1, fmaf(g1, z.st, fmaf(f1, z.c3, fmaf(h1, z.c4, n1 * z.c5))));
+                    a[11] -= fmaf(dz, z.c1, fmaf(g2, z.st, fmaf(f2, z.c3, fmaf(h2, z.c4, n2 * z.c5))));
+                }
 #pragma unroll
-            for (int c = 0; c < 12; c++) acc[c] += (double)a[c];
+                for (int c = 0; c < 12; c++) acc[c] += (double)a[c];
+            }
+            if (valid)
+                for (int c = 0; c < 12; c++) atomicAdd(&gnear[c * N + si], acc[c]);
         }
-        if (valid)
-            for (int c = 0; c < 12; c++) gnear[c * N + si] = acc[c];
+        js = je;
     }
 }
 
@@ -939,8 +948,9 @@ __global__ void k_unfold_adj(const double* __restrict__ fbar, int64_t nnodes, in
 }
 
 // ------------------------------------------- adjoint moments (table transpose)
-// One block per cluster; thread 0 scatters the transpose of the table map of
-// tc_moments.cu (k_ab_tables) into shared memory, so each moment gathers
+// One block per cluster; its threads scatter the transpose of the table map of
+// tc_moments.cu (k_ab_tables) into shared memory (shared-memory FP64 atomics,
+// so the order of the additions varies), so each moment gathers
 //   Lambda_c^k = sum over the table entries that read M_c^k of (entry
 //   coefficient) x (scaled adjoint table entry).
 __global__ void k_lambda(const double* __restrict__ abar, const double* __restrict__ invrho, int p,
@@ -951,14 +961,14 @@ __global__ void k_lambda(const double* __restrict__ abar, const double* __restri
     const int C = ncoef(p), C2 = ncoef(p + 2);
     for (int q = threadIdx.x; q < 12 * C; q += blockDim.x) ls[q] = 0.0;
     __syncthreads();
-    if (threadIdx.x == 0) {
+    {
         const double ir = invrho[node];
         const double third = 1.0 / 3.0;
         auto add = [&](int c, int k1, int k2, int k3, double v) {
             if (k1 < 0 || k2 < 0 || k3 < 0 || k1 + k2 + k3 > p) return;
-            ls[c * C + flat_index(k1, k2, k3)] += v;
+            atomicAdd(&ls[c * C + flat_index(k1, k2, k3)], v);
         };
-        for (int kidx = 0; kidx < C2; kidx++) {
+        for (int kidx = threadIdx.x; kidx < C2; kidx += blockDim.x) {
             int kp[3];
             unflatten(kidx, kp[0], kp[1], kp[2]);
             const int n = kp[0] + kp[1] + kp[2];
@@ -1073,6 +1083,10 @@ __global__ void k_l2l(const int4* __restrict__ info, const Geo* __restrict__ geo
 
 // Per particle of a leaf: Q_c(y) = sum_k L_c^k (y - y_L)^k and
 // grad_y sum_c w_c Q_c(y); writes dL/df, dL/dh, dL/dnu, dL/dx (far, source side).
+// Grid (clusters, kLeafEvalSplit): the particles of a leaf are shared by
+// kLeafEvalSplit blocks.
+constexpr int kLeafEvalSplit = 8;
+
 __global__ void k_leaf_eval(const int4* __restrict__ topo, const Geo* __restrict__ geo, const double* __restrict__ xs,
                             const double* __restrict__ ws, int64_t N, int p, const double* __restrict__ lamacc,
                             double* __restrict__ gfar)
@@ -1085,7 +1099,7 @@ __global__ void k_leaf_eval(const int4* __restrict__ topo, const Geo* __restrict
     for (int q = threadIdx.x; q < 12 * C; q += blockDim.x) ll[q] = lamacc[node * 12 * C + q];
     __syncthreads();
     const Geo gc = geo[node];
-    for (int i = t.x + threadIdx.x; i < t.x + t.y; i += blockDim.x) {
+    for (int i = t.x + blockIdx.y * blockDim.x + threadIdx.x; i < t.x + t.y; i += gridDim.y * blockDim.x) {
         const double dl[3] = {xs[i] - gc.x, xs[N + i] - gc.y, xs[2 * N + i] - gc.z};
         double w[12];
         for (int c = 0; c < 3; c++) w[c] = ws[c * N + i];
@@ -1335,7 +1349,8 @@ extern "C" tc_status tc_adjoint(tc_ctx* ctx, const double* g, double* grad_f, do
             ts, ptr<double>(ctx->adj_gs), M, ptr<int4>(ctx->node_topo), ptr<float4>(ctx->spack),
             ptr<int64_t>(ctx->near_off), ptr<ListEntry>(ctx->near_list), ptr<double>(ctx->adj_gt));
         note_launch();
-        k_near_adj_source32<<<(unsigned)nnodes, kNearAdjWarps * 32, 0, s>>>(
+        TC_CK(cudaMemsetAsync(ctx->adj_gnear.p, 0, (size_t)12 * N * 8, s), "zero near gradients");
+        k_near_adj_source32<<<grid_for(ctx->near_entries, kNearAdjChunk), kNearAdjWarps * 32, 0, s>>>(
             ts, ptr<double>(ctx->adj_gs), M, ptr<int4>(ctx->node_topo), ptr<float4>(ctx->spack), N,
             ptr<uint64_t>(ctx->adj_nkeys), ptr<int32_t>(ctx->adj_nidx), ptr<ListEntry>(ctx->near_list),
             ptr<int32_t>(ctx->adj_nebatch), ctx->near_entries, ptr<double>(ctx->adj_gnear));
@@ -1346,7 +1361,7 @@ extern "C" tc_status tc_adjoint(tc_ctx* ctx, const double* g, double* grad_f, do
     // adjoint moments, downward pass, per-particle evaluation
     size_t lsm = (size_t)12 * C * 8;
     TC_CK(cudaFuncSetAttribute(k_lambda, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm), "lambda attr");
-    k_lambda<<<(unsigned)nnodes, 32, lsm, s>>>(ptr<double>(ctx->adj_abar), ptr<double>(ctx->node_invrho), p,
+    k_lambda<<<(unsigned)nnodes, 128, lsm, s>>>(ptr<double>(ctx->adj_abar), ptr<double>(ctx->node_invrho), p,
                                               ptr<double>(ctx->adj_lam));
     note_launch();
     for (size_t L = 0; L + 1 < ctx->level_begin.size(); L++) {
@@ -1357,9 +1372,9 @@ extern "C" tc_status tc_adjoint(tc_ctx* ctx, const double* g, double* grad_f, do
         note_launch();
     }
     TC_CK(cudaFuncSetAttribute(k_leaf_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm), "leaf attr");
-    k_leaf_eval<<<(unsigned)nnodes, 128, lsm, s>>>(ptr<int4>(ctx->node_topo), ptr<Geo>(ctx->node_geo),
-                                                   ptr<double>(ctx->xs), ptr<double>(ctx->ws), N, p,
-                                                   ptr<double>(ctx->adj_lamacc), ptr<double>(ctx->adj_gfar));
+    k_leaf_eval<<<dim3((unsigned)nnodes, kLeafEvalSplit), 128, lsm, s>>>(
+        ptr<int4>(ctx->node_topo), ptr<Geo>(ctx->node_geo), ptr<double>(ctx->xs), ptr<double>(ctx->ws), N, p,
+        ptr<double>(ctx->adj_lamacc), ptr<double>(ctx->adj_gfar));
     note_launch();
     k_adj_final<<<grid_for(N, 256), 256, 0, s>>>(ptr<double>(ctx->adj_gfar), ptr<double>(ctx->adj_gnear),
                                                  ptr<double>(ctx->adj_gt), ptr<int32_t>(ctx->perm), N, ctx->eval_self,
