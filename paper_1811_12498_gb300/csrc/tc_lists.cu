@@ -57,7 +57,9 @@ __global__ void __launch_bounds__(kListWarps * 32)
     if (lane == 0) st[0] = ListEntry{0, active};
     sp = 1;
     __syncwarp();
-    int64_t nf = 0, nn = 0, my_far = 0, my_near = 0;
+    // 32-bit counters: entries per batch and interactions per target are all
+    // below N < 2^31 (64-bit ones made this kernel measurably slower)
+    int nf = 0, nn = 0, my_far = 0, my_near = 0;
     const int64_t fo = write ? far_off[b] : 0, no = write ? near_off[b] : 0;
     bool overflow = false;
     while (sp > 0) {
@@ -73,7 +75,9 @@ __global__ void __launch_bounds__(kListWarps * 32)
         const bool screened = R2f > tiny2 && q < 1e37f && gh.w < 1e37f;  // far from FP32 under/overflow
         bool pass = screened && q >= gh.w * (1.0f + 0x1p-12f);
         const bool sure = screened && (pass || q <= gh.w * (1.0f - 0x1p-12f));
-        if (in && !sure) {
+        // warp-uniform guard: the FP64 test is rare, and issued predicated for
+        // the whole warp it would keep the FP64 pipe busy on every visit
+        if (__any_sync(0xffffffffu, in && !sure) && in && !sure) {
             const Geo g = geo[e.node];
             double dx = __dsub_rn(x0, g.x), dy = __dsub_rn(x1, g.y), dz = __dsub_rn(x2, g.z);
             double R2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
