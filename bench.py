@@ -138,11 +138,11 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
-def far_traffic(p):
-    """Per-launch DRAM bytes of the far-field kernel from the committed ncu
-    summary, if it was taken on the current kernel source; else None."""
-    src = os.path.join(ROOT, "paper_1811_12498_gb300", "csrc", "tc_far.cu")
-    prof = os.path.join(ROOT, "profiles", "far_field_uniform_cube_131k.md")
+def kernel_traffic(source, profile):
+    """Per-launch DRAM bytes of a kernel from its committed ncu summary, if the
+    summary was taken on the current kernel source (sha256); else None."""
+    src = os.path.join(ROOT, "paper_1811_12498_gb300", "csrc", source)
+    prof = os.path.join(ROOT, "profiles", profile)
     if not os.path.exists(prof):
         return None
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
@@ -396,30 +396,44 @@ def main():
     ud = api.direct(dx[0], dx[1], dx[2], dx[3], targets=tgt, precision="fp64").cpu().numpy().T
     E = float(np.sqrt(np.sum((u_host[eidx] - ud) ** 2) / np.sum(ud ** 2)))
 
-    # roofline of the dominant kernel (far field): algorithmic flops per launch
+    # roofline of the dominant kernel (the near field at this configuration):
+    # algorithmic flops per launch (43 per Stokeslet + stresslet pair: d 3,
+    # r^2 5, 1/r 1, powers 3, three dot products 15, s and t 4, accumulation 12)
+    # over its phase time; the far kernel beside it
     n_far = st["far_interactions"]
     fp64 = args.precision == "fp64"
     far_ms = ph.get("far")
     near_ms = ph.get("near")
+    peak = PEAK_FP64_TFLOPS if fp64 else PEAK_FP32_TFLOPS
+    peak_kind = ("nominal FP64 (152 SMs x 2 FMA/clk x 2.07 GHz)" if fp64 else
+                 "nominal FP32 (152 SMs x 128 FMA/clk x 2.07 GHz)")
+    near_flops = 43.0 * st["near_pairs"]
+    near_tf = near_flops / (near_ms / 1e3) / 1e12
     rec_unit, con_unit = far_flops_per_interaction(p)
     rec_flops = rec_unit * n_far
     con_flops = con_unit * n_far
-    # the recurrence and the contraction run in one type: FP64, or FP32 (mixed)
-    achieved = (rec_flops + con_flops) / (far_ms / 1e3) / 1e12
-    peak = PEAK_FP64_TFLOPS if fp64 else PEAK_FP32_TFLOPS
-    traffic = far_traffic(p)
-    near_flops = 43.0 * st["near_pairs"]
+    far_tf = (rec_flops + con_flops) / (far_ms / 1e3) / 1e12
+    # the unfolded form: recurrence 11 and contraction 24 flops per coefficient
+    # of order <= p+2, plus 18 for d.B
+    unfolded_far_flops = (11 + 24) * ncoef(p + 2) + 18
+    near_kernel = "k_near_fp64" if fp64 else "k_near_mixed"
+    dominant_near = near_ms >= far_ms
+    if dominant_near:
+        roof = {"bound": "alu", "kernel": near_kernel + " (near field, 43 flops per pair)", "achieved": near_tf,
+                "peak": peak, "unit": "TFLOP/s", "peak_kind": peak_kind, "frac": near_tf / peak,
+                "traffic": None if fp64 else kernel_traffic("tc_near.cu", "near_field_uniform_cube_524k.md"),
+                "flops_per_launch": near_flops, "launch_ms": near_ms}
+    else:
+        roof = {"bound": "alu", "kernel": "k_far (far field, folded recurrence + contraction)", "achieved": far_tf,
+                "peak": peak, "unit": "TFLOP/s", "peak_kind": peak_kind, "frac": far_tf / peak,
+                "traffic": None if fp64 else kernel_traffic("tc_far.cu", "far_field_uniform_cube_524k.md"),
+                "flops_per_launch": rec_flops + con_flops, "launch_ms": far_ms}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
         "config": config(args),
-        "roofline": {"bound": "alu", "kernel": "k_far (far field, recurrence + contraction)", "achieved": achieved,
-                     "peak": peak, "unit": "TFLOP/s",
-                     "peak_kind": "nominal FP64 (152 SMs x 2 FMA/clk x 2.07 GHz)" if fp64 else
-                     "nominal FP32 (152 SMs x 128 FMA/clk x 2.07 GHz)",
-                     "frac": achieved / peak, "traffic": traffic,
-                     "flops_per_launch": rec_flops + con_flops, "launch_ms": far_ms},
+        "roofline": roof,
         "e2e": {"value": N / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(sum(a.numel() * 8 for a in hx)),
                 "d2h_bytes_per_step": int(uh.numel() * 8), "ms_per_step": e2e_ms},
         "gpu_launches": int(launches),
@@ -428,9 +442,13 @@ def main():
         "interactions": {"far": n_far, "near_pairs": st["near_pairs"], "clusters": st["clusters"],
                          "far_entries": ls["far_entries"], "near_entries": ls["near_entries"],
                          "far_lane_use": ls["far_lane_use"], "near_lane_use": ls["near_lane_use"]},
-        "secondary": {"near_fp32_tflops": near_flops / (near_ms / 1e3) / 1e12 if near_ms else None,
-                      "near_fp32_frac": (near_flops / (near_ms / 1e3) / 1e12) / PEAK_FP32_TFLOPS if near_ms else None,
-                      "far_fp32_contraction_tflops": con_flops / (far_ms / 1e3) / 1e12},
+        "secondary": {"near_tflops": near_tf, "near_frac": near_tf / peak,
+                      "far_tflops_folded_count": far_tf, "far_frac_folded_count": far_tf / peak,
+                      "far_flops_per_interaction_folded": rec_unit + con_unit,
+                      "far_tflops_unfolded_count": unfolded_far_flops * n_far / (far_ms / 1e3) / 1e12,
+                      "far_flops_per_interaction_unfolded": unfolded_far_flops,
+                      "near_plus_far_frac_unfolded_count":
+                          (near_flops + unfolded_far_flops * n_far) / ((near_ms + far_ms) / 1e3) / 1e12 / peak},
         "accuracy": {"E_vs_fp64_direct": E, "E_samples": int(len(eidx))},
     }
     if not args.no_fp64_compare and args.precision == "mixed":

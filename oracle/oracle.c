@@ -19,8 +19,8 @@
  *     provided as a cross-check of the contracted forms.
  * Multi-indices are held in plain (P+1)^3 cubes, zero outside ||k|| <= P.
  *
- * Readings of points the paper leaves open (all listed in the design doc):
- *   - kernel prefactor 1 (Section 1 gives the kernels "up to a prefactor");
+ * Readings of points the paper leaves open:
+ *   - kernel prefactor 1 (Section 1 defines the kernels up to a constant);
  *   - a pair contributes nothing when |x - y| == 0 exactly (this is the
  *     n != m exclusion of eq. (1.3) when targets are the sources);
  *   - root cell: per-axis minimum corner, side = largest axis extent; cell
@@ -28,8 +28,8 @@
  *     bisection plane belongs to the upper child and the maximum point is
  *     clamped into the last cell (Section 5);
  *   - a cluster is a leaf iff it holds at most N0 particles or is at depth 21
- *     (Section 5 says both "fewer than N0" and "at most N0"; Section 6 fixes
- *     N0 as the maximum leaf size);
+ *     (Section 5 stops splitting below N0 particles, Section 6 treats N0 as
+ *     the maximum leaf size);
  *   - cluster centre: centre of the tight bounding box (shrink = 1, test
  *     case 1) or centre of the octree cell (shrink = 0); radius r = max
  *     distance from the centre to the cluster's particles (Section 2);
