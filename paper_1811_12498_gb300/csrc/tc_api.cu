@@ -92,14 +92,14 @@ static std::atomic<int64_t> g_launches{0};
 void tc::note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 // phase timing: events around a phase when profiling is on
-static void ph_begin(tc_ctx* ctx, int ph)
+static void ph_begin(tc_ctx* ctx, int ph, cudaStream_t s = nullptr)
 {
-    if (ctx->profile) cudaEventRecord(ctx->ev[2 * ph], ctx->stream);
+    if (ctx->profile) cudaEventRecord(ctx->ev[2 * ph], s ? s : ctx->stream);
 }
-static void ph_end(tc_ctx* ctx, int ph)
+static void ph_end(tc_ctx* ctx, int ph, cudaStream_t s = nullptr)
 {
     if (ctx->profile) {
-        cudaEventRecord(ctx->ev[2 * ph + 1], ctx->stream);
+        cudaEventRecord(ctx->ev[2 * ph + 1], s ? s : ctx->stream);
         ctx->ev_recorded[ph] = 1;
     }
 }
@@ -166,9 +166,13 @@ tc_status tc_destroy(tc_ctx* ctx)
 {
     if (!ctx) return TC_OK;
     cudaStreamSynchronize(ctx->stream);
+    if (ctx->stream2) cudaStreamSynchronize(ctx->stream2);
     release_all(ctx);
     for (cudaEvent_t& e : ctx->ev)
         if (e) cudaEventDestroy(e);
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+    if (ctx->stream2) cudaStreamDestroy(ctx->stream2);
     delete ctx;
     return TC_OK;
 }
@@ -481,20 +485,32 @@ tc_status tc::eval_compute(tc_ctx* ctx, double* u)
     const int p = ctx->p_eval;
     const double* ts = ctx->eval_self ? ptr<double>(ctx->xs) : ptr<double>(ctx->ts);
     const int32_t* tperm = ctx->eval_self ? ptr<int32_t>(ctx->perm) : ptr<int32_t>(ctx->tperm);
-    ph_begin(ctx, TC_PH_FAR);
+    // the far and near fields are independent: the far field runs on the
+    // context's second stream, forked from and joined back to the first
+    if (!ctx->stream2) {
+        TC_CK(cudaStreamCreateWithFlags(&ctx->stream2, cudaStreamNonBlocking), "second stream");
+        TC_CK(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming), "fork event");
+        TC_CK(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming), "join event");
+    }
+    cudaStream_t s2 = ctx->stream2;
+    TC_CK(cudaEventRecord(ctx->ev_fork, s), "fork");
+    TC_CK(cudaStreamWaitEvent(s2, ctx->ev_fork, 0), "fork");
+    ph_begin(ctx, TC_PH_FAR, s2);
     TC_CK(launch_far(ctx->precision, ctx->rec64, ts, M, ptr<int4>(ctx->node_topo), ptr<Geo>(ctx->node_geo),
                      ptr<double>(ctx->node_invrho),
                      ptr<float4>(ctx->geo32), ptr<double>(ctx->abf64), ptr<float>(ctx->abf32), p,
                      ptr<int64_t>(ctx->far_off),
-                     ptr<ListEntry>(ctx->far_list), ptr<double>(ctx->u_far), s),
+                     ptr<ListEntry>(ctx->far_list), ptr<double>(ctx->u_far), s2),
           "far field");
-    ph_end(ctx, TC_PH_FAR);
+    ph_end(ctx, TC_PH_FAR, s2);
+    TC_CK(cudaEventRecord(ctx->ev_join, s2), "join");
     ph_begin(ctx, TC_PH_NEAR);
     TC_CK(launch_near(ctx->precision, ts, M, ptr<int4>(ctx->node_topo), ptr<double>(ctx->xs), ptr<double>(ctx->ws),
                       ptr<float4>(ctx->spack), ctx->N, ptr<int64_t>(ctx->near_off), ptr<ListEntry>(ctx->near_list),
                       ptr<double>(ctx->u_near), s),
           "near field");
     ph_end(ctx, TC_PH_NEAR);
+    TC_CK(cudaStreamWaitEvent(s, ctx->ev_join, 0), "join");
     ph_begin(ctx, TC_PH_FINAL);
     TC_CK(launch_finalize(ptr<double>(ctx->u_far), ptr<double>(ctx->u_near), tperm, M, u, s), "finalize");
     ph_end(ctx, TC_PH_FINAL);

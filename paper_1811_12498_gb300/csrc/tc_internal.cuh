@@ -84,6 +84,8 @@ struct SysDesc {
 struct tc_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
+    cudaStream_t stream2 = nullptr;     // far field, concurrent with the near field
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int precision = TC_MIXED;
     int rec64 = 0;  // mixed: FP64 far-field recurrence for p >= 8
     int shrink = 1;
