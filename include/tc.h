@@ -283,7 +283,11 @@ typedef enum {
 } tc_phase;
 
 /* Enable (1) or disable (0) per-phase event timing on ctx.  Enabling resets
- * the recorded phases.  Costs two event records per phase. */
+ * the recorded phases.  Costs two event records per phase.  tc_eval runs the
+ * far field concurrently with the near field (second stream), so their phase
+ * times overlap; enable = 2 times them with the two kernels serialised, so
+ * that each phase time is that kernel's own duration (the result is the
+ * same). */
 tc_status tc_profile(tc_ctx* ctx, int32_t enable);
 
 /* Durations in ms of the most recent run of each phase (host array of

@@ -144,8 +144,10 @@ class Treecode:
         return out
 
     def profile(self, enable=True):
-        """Enable per-phase CUDA-event timing (see phase_times)."""
-        self._chk(lib().tc_profile(self._h, int(bool(enable))))
+        """Enable per-phase CUDA-event timing (see phase_times).  enable=2
+        serialises the far and near fields so that their phase times are each
+        kernel's own duration (by default they run concurrently)."""
+        self._chk(lib().tc_profile(self._h, int(enable) if enable in (0, 1, 2) else int(bool(enable))))
 
     def phase_times(self):
         """ms of the most recent run of each phase (None if not run)."""

@@ -182,8 +182,9 @@ tc_status tc_profile(tc_ctx* ctx, int32_t enable)
     if (!ctx) return fail(nullptr, TC_EINVAL, "tc_profile: ctx is NULL");
     if (enable && !ctx->ev[0])
         for (cudaEvent_t& e : ctx->ev) TC_CK(cudaEventCreate(&e), "tc_profile event");
+    if (enable < 0 || enable > 2) return fail(ctx, TC_EINVAL, "tc_profile: enable must be 0, 1 or 2");
     for (int& r : ctx->ev_recorded) r = 0;
-    ctx->profile = enable ? 1 : 0;
+    ctx->profile = enable;
     return TC_OK;
 }
 
@@ -492,7 +493,8 @@ tc_status tc::eval_compute(tc_ctx* ctx, double* u)
         TC_CK(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming), "fork event");
         TC_CK(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming), "join event");
     }
-    cudaStream_t s2 = ctx->stream2;
+    // profile mode 2: serialised, so that each phase time is one kernel's own
+    cudaStream_t s2 = ctx->profile == 2 ? s : ctx->stream2;
     TC_CK(cudaEventRecord(ctx->ev_fork, s), "fork");
     TC_CK(cudaStreamWaitEvent(s2, ctx->ev_fork, 0), "fork");
     ph_begin(ctx, TC_PH_FAR, s2);
