@@ -78,6 +78,8 @@ def parse():
     ap.add_argument("--error-samples", type=int, default=10000, help="targets of the FP64 direct-sum error check")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true",
+                    help="skip the accuracy-against-time sweep on the 4M-point sphere")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the forward+adjoint (Gaussian clusters) and batched (64 systems) measurements")
     return ap.parse_args()
@@ -240,6 +242,50 @@ def bench_fwd_adjoint(flush, stream, steps=3):
     return {"workload": "8 Gaussian clusters N=262144, sigma=0.05, p=8, theta=0.5, N0=2000, mixed",
             "s_per_step": ms / 1e3, "fwd_ms": statistics.mean(fwd), "adjoint_ms": ms - statistics.mean(fwd),
             "steps": steps, "grads": "f, h, nu, x"}
+
+
+def bench_sphere_sweep(flush, stream):
+    """Accuracy against time on 4,000,000 quasi-uniform points of the unit
+    sphere (nu = outward normal, f, h ~ N(0,1)), p in {4, 6, 8, 10}, theta in
+    {0.5, 0.7}, N0 = 2000: per point, the time of build + moments + eval
+    (mixed, FP32 recurrence; and with the FP64 recurrence for p >= 8) and E
+    against the FP64 direct sum on 10,000 sampled targets."""
+    import numpy as np
+    import torch
+
+    from paper_1811_12498_gb300 import api, inputs
+    N, N0 = 4_000_000, 2000
+    x, f, h, nu = inputs.fibonacci_sphere(N, inputs.SEED_BASE + 3)
+    d = [torch.from_numpy(np.ascontiguousarray(a.T)).cuda() for a in (x, f, h, nu)]
+    eidx = inputs.sample_indices(N, 10_000, 778)
+    tgt = torch.from_numpy(np.ascontiguousarray(x[eidx].T)).cuda()
+    ud = api.direct(d[0], d[1], d[2], d[3], targets=tgt, precision="fp64").cpu().numpy().T
+    u = torch.empty((3, N), dtype=torch.float64, device="cuda")
+    rows = []
+    for rec64 in (False, True):
+        tc = api.Treecode("mixed", True, stream, rec64=rec64)
+        for p in (4, 6, 8, 10):
+            if rec64 and p < 8:
+                continue
+            for theta in (0.5, 0.7):
+                times = []
+                for k in range(3):
+                    flush.fill_(1)
+                    e0, e1 = _events(stream)
+                    tc.build(d[0], N0).moments(d[1], d[2], d[3], p)
+                    tc.eval(theta, p, out=u)
+                    e1.record(stream)
+                    e1.synchronize()
+                    if k > 0:
+                        times.append(e0.elapsed_time(e1))
+                uh = u.cpu().numpy().T[eidx]
+                E = float(np.sqrt(np.sum((uh - ud) ** 2) / np.sum(ud ** 2)))
+                ms = statistics.mean(times)
+                rows.append({"p": p, "theta": theta, "recurrence": "fp64" if rec64 else "fp32", "ms": ms,
+                             "targets_per_s": N / (ms / 1e3), "E_vs_fp64_direct": E})
+        tc.close()
+    return {"workload": "Fibonacci sphere N=4000000, nu = outward normal, f, h ~ N(0,1), N0=2000, mixed",
+            "E_samples": int(len(eidx)), "points": rows}
 
 
 def bench_batched(flush, stream, reps=3):
@@ -504,6 +550,8 @@ def main():
     if not args.no_extras:
         line["fwd_adjoint"] = bench_fwd_adjoint(flush, stream)
         line["batched"] = bench_batched(flush, stream)
+        if not args.no_sweep:
+            line["sphere_sweep"] = bench_sphere_sweep(flush, stream)
     print(json.dumps(line), flush=True)
     tc.close()
     if dist is not None:

@@ -1293,6 +1293,7 @@ extern "C" tc_status tc_adjoint(tc_ctx* ctx, const double* g, double* grad_f, do
     if (!g) return fail(ctx, TC_EINVAL, "tc_adjoint: g is NULL");
     if (ctx->eval_self && grad_t)
         return fail(ctx, TC_EINVAL, "tc_adjoint: grad_t must be NULL when targets are the sources (use grad_x)");
+    TC_CK(join_moments(ctx), "adjoint");
     cudaStream_t s = ctx->stream;
     const int64_t N = ctx->N, M = ctx->M, nnodes = ctx->nnodes;
     const int p = ctx->ab_p;

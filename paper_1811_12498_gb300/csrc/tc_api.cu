@@ -172,6 +172,7 @@ tc_status tc_destroy(tc_ctx* ctx)
         if (e) cudaEventDestroy(e);
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+    if (ctx->ev_mom) cudaEventDestroy(ctx->ev_mom);
     if (ctx->stream2) cudaStreamDestroy(ctx->stream2);
     delete ctx;
     return TC_OK;
@@ -224,6 +225,7 @@ static tc_status check_flags(tc_ctx* ctx)
 tc_status tc_sync(tc_ctx* ctx)
 {
     if (!ctx) return fail(nullptr, TC_EINVAL, "tc_sync: ctx is NULL");
+    TC_CK(join_moments(ctx), "tc_sync");
     TC_CK(cudaStreamSynchronize(ctx->stream), "tc_sync");
     return check_flags(ctx);
 }
@@ -234,6 +236,7 @@ tc_status tc_build(tc_ctx* ctx, const double* x, int64_t N, int32_t N0)
     if (!x) return fail(ctx, TC_EINVAL, "tc_build: x is NULL");
     if (N < 1 || N >= ((int64_t)1 << 31)) return fail(ctx, TC_EINVAL, "tc_build: N = %lld out of [1, 2^31)", (long long)N);
     if (N0 < 1) return fail(ctx, TC_EINVAL, "tc_build: N0 = %d must be >= 1", N0);
+    TC_CK(join_moments(ctx), "tc_build");
     cudaStream_t s = ctx->stream;
     ctx->built = ctx->have_moments = ctx->have_eval = 0;
     ctx->ab_p = -1;
@@ -325,6 +328,8 @@ tc_status tc_moments(tc_ctx* ctx, const double* f, const double* h, const double
     if (!ctx->built) return fail(ctx, TC_ESTATE, "tc_moments: call tc_build first");
     if (!f || !h || !nu) return fail(ctx, TC_EINVAL, "tc_moments: a weight pointer is NULL");
     if (p < 0 || p > kPMax) return fail(ctx, TC_EINVAL, "tc_moments: p = %d out of [0, %d]", p, kPMax);
+    TC_CK(join_moments(ctx), "tc_moments");
+    TC_CK(second_stream(ctx), "second stream");
     cudaStream_t s = ctx->stream;
     const int64_t N = ctx->N;
     ctx->have_moments = ctx->have_eval = 0;
@@ -337,15 +342,30 @@ tc_status tc_moments(tc_ctx* ctx, const double* f, const double* h, const double
     if (ctx->precision == TC_MIXED) {
         TC_CK(launch_source_pack(ptr<double>(ctx->xs), ptr<double>(ctx->ws), N, ptr<float4>(ctx->spack), s), "pack");
     }
+    // The caller's weights are consumed above; the moment passes read only the
+    // library's sorted copies, so they run on the second stream, overlapping
+    // the list traversal of the next tc_eval (FP64 pipe against FP32 and
+    // memory latency), and are joined before anything reads the moments.
+    // Profile mode 2 keeps them on the first stream.
+    const bool async = ctx->profile != 2;
+    cudaStream_t sm = async ? ctx->stream2 : s;
+    if (async) {
+        TC_CK(cudaEventRecord(ctx->ev_fork, s), "fork");
+        TC_CK(cudaStreamWaitEvent(sm, ctx->ev_fork, 0), "fork");
+    }
     TC_CK(launch_moments(ptr<int4>(ctx->node_topo), ptr<Geo>(ctx->node_geo), ptr<double>(ctx->xs),
-                         ptr<double>(ctx->ws), N, ctx->nnodes, p, ptr<double>(ctx->mom), s),
+                         ptr<double>(ctx->ws), N, ctx->nnodes, p, ptr<double>(ctx->mom), sm),
           "moments");
     // upward pass: level_begin holds the first node of each level and the end
     for (int L = (int)ctx->level_begin.size() - 3; L >= 0; L--)
         TC_CK(launch_m2m(ptr<int4>(ctx->node_topo), ptr<Geo>(ctx->node_geo), ctx->level_begin[L],
-                         ctx->level_begin[L + 1], p, ptr<double>(ctx->mom), s),
+                         ctx->level_begin[L + 1], p, ptr<double>(ctx->mom), sm),
               "m2m");
-    ph_end(ctx, TC_PH_MOMENTS);
+    ph_end(ctx, TC_PH_MOMENTS, sm);
+    if (async) {
+        TC_CK(cudaEventRecord(ctx->ev_mom, sm), "moments done");
+        ctx->mom_pending = 1;
+    }
     ctx->p_mom = p;
     ctx->have_moments = 1;
     return TC_OK;
@@ -398,8 +418,7 @@ tc_status tc::eval_prepare(tc_ctx* ctx, const double* targets, int64_t M, double
     if (!targets && M != ctx->N)
         return fail(ctx, TC_EINVAL, "tc_eval: targets = NULL requires M = N (%lld)", (long long)ctx->N);
     if (M < 1 || M >= ((int64_t)1 << 31)) return fail(ctx, TC_EINVAL, "tc_eval: M = %lld out of range", (long long)M);
-    tc_status st = ensure_tables(ctx, p);
-    if (st != TC_OK) return st;
+    tc_status st = TC_OK;
     cudaStream_t s = ctx->stream;
     ctx->have_eval = 0;
     ctx->prepared = 0;
@@ -468,6 +487,11 @@ tc_status tc::eval_prepare(tc_ctx* ctx, const double* targets, int64_t M, double
                        ptr<int64_t>(ctx->cnt_near), ptr<int32_t>(ctx->flags), s),
           "list write");
     ph_end(ctx, TC_PH_LISTS);
+    // the tables read the moments: join the moment passes here, after the
+    // traversal that ran beside them
+    TC_CK(join_moments(ctx), "join moments");
+    st = ensure_tables(ctx, p);
+    if (st != TC_OK) return st;
     (void)tperm;
     ctx->M = M;
     ctx->far_entries = tot[0];
@@ -488,11 +512,7 @@ tc_status tc::eval_compute(tc_ctx* ctx, double* u)
     const int32_t* tperm = ctx->eval_self ? ptr<int32_t>(ctx->perm) : ptr<int32_t>(ctx->tperm);
     // the far and near fields are independent: the far field runs on the
     // context's second stream, forked from and joined back to the first
-    if (!ctx->stream2) {
-        TC_CK(cudaStreamCreateWithFlags(&ctx->stream2, cudaStreamNonBlocking), "second stream");
-        TC_CK(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming), "fork event");
-        TC_CK(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming), "join event");
-    }
+    TC_CK(second_stream(ctx), "second stream");
     // profile mode 2: serialised, so that each phase time is one kernel's own
     cudaStream_t s2 = ctx->profile == 2 ? s : ctx->stream2;
     TC_CK(cudaEventRecord(ctx->ev_fork, s), "fork");
@@ -669,6 +689,7 @@ tc_status tc_moments_export(tc_ctx* ctx, int64_t node, double* Mf, double* Mt)
     if (!ctx) return fail(nullptr, TC_EINVAL, "tc_moments_export: ctx is NULL");
     if (!ctx->have_moments) return fail(ctx, TC_ESTATE, "tc_moments_export: no moments");
     if (node < 0 || node >= ctx->nnodes) return fail(ctx, TC_EINVAL, "tc_moments_export: node out of range");
+    TC_CK(join_moments(ctx), "moments export");
     const int p = ctx->p_mom, C = ncoef(p), q1 = p + 1;
     std::vector<double> m((size_t)12 * C);
     TC_CK(cudaMemcpyAsync(m.data(), ptr<double>(ctx->mom) + node * 12 * C, m.size() * 8, cudaMemcpyDeviceToHost,

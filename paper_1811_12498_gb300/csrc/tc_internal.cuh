@@ -84,8 +84,9 @@ struct SysDesc {
 struct tc_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
-    cudaStream_t stream2 = nullptr;     // far field, concurrent with the near field
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaStream_t stream2 = nullptr;     // moment passes and far field, concurrent with the first stream
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_mom = nullptr;
+    int mom_pending = 0;                // moment passes enqueued on stream2, not yet joined
     int precision = TC_MIXED;
     int rec64 = 0;  // mixed: FP64 far-field recurrence for p >= 8
     int shrink = 1;
@@ -159,6 +160,28 @@ struct tc_ctx {
     cudaEvent_t ev[2 * TC_NPHASES] = {};
     int ev_recorded[TC_NPHASES] = {};
 };
+namespace tc {
+// The second stream and its events, created on first use.
+inline cudaError_t second_stream(tc_ctx* ctx)
+{
+    if (ctx->stream2) return cudaSuccess;
+    cudaError_t e = cudaStreamCreateWithFlags(&ctx->stream2, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_mom, cudaEventDisableTiming);
+    return e;
+}
+// Order the first stream after the moment passes that tc_moments left
+// running on the second stream (before anything reads the moments or
+// rewrites what those passes read).
+inline cudaError_t join_moments(tc_ctx* ctx)
+{
+    if (!ctx->mom_pending) return cudaSuccess;
+    ctx->mom_pending = 0;
+    return cudaStreamWaitEvent(ctx->stream, ctx->ev_mom, 0);
+}
+}  // namespace tc
+
 
 namespace tc {
 
