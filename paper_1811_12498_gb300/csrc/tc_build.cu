@@ -176,15 +176,25 @@ __global__ void k_radix_hist(const uint64_t* __restrict__ keys, int64_t N, int s
     hist[(int64_t)threadIdx.x * gridDim.x + blockIdx.x] = cnt[threadIdx.x];
 }
 
-// Single-block exclusive scan of n uint32 values in place.
-__global__ void k_scan_u32_inplace(uint32_t* __restrict__ a, int64_t n)
+// Single-block exclusive scan of n uint32 values in place.  Each thread owns
+// a contiguous chunk (a multiple of 4 values, so whole uint4 loads) and reads
+// it with independent vector loads, so the chunk's latency is paid a few
+// times rather than once per element.
+__global__ void __launch_bounds__(1024) k_scan_u32_inplace(uint32_t* __restrict__ a, int64_t n)
 {
     __shared__ uint32_t part[1024];
-    int t = threadIdx.x;
+    const int t = threadIdx.x;
     int64_t chunk = (n + blockDim.x - 1) / blockDim.x;
-    int64_t b = t * chunk, e = b + chunk < n ? b + chunk : n;
+    chunk = (chunk + 3) & ~(int64_t)3;
+    const int64_t b = t * chunk, e = b + chunk < n ? b + chunk : n;
+    const int64_t e4 = b + ((e > b ? e - b : 0) & ~(int64_t)3);  // end of the whole uint4 loads
     uint32_t s = 0;
-    for (int64_t i = b; i < e; i++) s += a[i];
+#pragma unroll 4
+    for (int64_t i = b; i < e4; i += 4) {
+        const uint4 v = *reinterpret_cast<const uint4*>(a + i);
+        s += v.x + v.y + v.z + v.w;
+    }
+    for (int64_t i = e4; i < e; i++) s += a[i];
     part[t] = s;
     __syncthreads();
     for (int o = 1; o < (int)blockDim.x; o <<= 1) {
@@ -194,8 +204,19 @@ __global__ void k_scan_u32_inplace(uint32_t* __restrict__ a, int64_t n)
         __syncthreads();
     }
     uint32_t run = part[t] - s;
-    for (int64_t i = b; i < e; i++) {
-        uint32_t v = a[i];
+#pragma unroll 4
+    for (int64_t i = b; i < e4; i += 4) {
+        const uint4 v = *reinterpret_cast<const uint4*>(a + i);
+        uint4 o;
+        o.x = run;
+        o.y = run + v.x;
+        o.z = o.y + v.y;
+        o.w = o.z + v.z;
+        run = o.w + v.w;
+        *reinterpret_cast<uint4*>(a + i) = o;
+    }
+    for (int64_t i = e4; i < e; i++) {
+        const uint32_t v = a[i];
         a[i] = run;
         run += v;
     }
