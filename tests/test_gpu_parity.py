@@ -263,6 +263,32 @@ def test_edge_cases(prec):
     assert oracle.rel_l2(u, oracle.direct(x, f, h, nu)) <= (1e-12 if prec == "fp64" else 1e-6)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_reuse_without_sync_and_profile_modes(prec):
+    # a context reused back to back with no host sync: the moment passes run
+    # on the context's second stream and must be joined before the next build
+    # and before the tables; profile mode 2 serialises the streams and gives
+    # the same result, bit for bit
+    xa, fa, ha, na = inputs.uniform_cube(6000, 73)
+    xb, fb, hb, nb = inputs.fibonacci_sphere(7000, 74)
+    tc = api.Treecode(prec, True)
+    tc.build(dev(xa), 120).moments(dev(fa), dev(ha), dev(na), 6)
+    ua = tc.eval(0.5, 6)
+    tc.build(dev(xb), 120).moments(dev(fb), dev(hb), dev(nb), 6)
+    ub = tc.eval(0.5, 6)
+    tc.profile(2)
+    tc.build(dev(xb), 120).moments(dev(fb), dev(hb), dev(nb), 6)
+    ub2 = tc.eval(0.5, 6)
+    tc.profile(0)
+    tc.sync()
+    np.testing.assert_array_equal(host(ub), host(ub2))
+    tc.close()
+    for x, f, h, nu, u in ((xa, fa, ha, na, ua), (xb, fb, hb, nb, ub)):
+        tree = oracle.Tree(x, 120, True)
+        tree.set_moments(f, h, nu, 6)
+        assert oracle.rel_l2(host(u), tree.treecode(x, 0.5, 6)) <= TOL[prec]
+
+
 def test_invalid_arguments_raise():
     x, f, h, nu = inputs.uniform_cube(100, 61)
     tc = api.Treecode("mixed", True)
