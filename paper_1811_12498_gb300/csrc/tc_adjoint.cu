@@ -39,6 +39,7 @@
 // their batch order).  The cluster-major far kernel accumulates per warp in
 // shared memory and flushes with FP64 atomics when the cluster changes, so
 // the source-side far gradient is reproducible only up to FP64 rounding.
+#include "tc_nearpair.cuh"
 #include "tc_recurrence.cuh"
 
 namespace tc {
@@ -320,68 +321,79 @@ __device__ __forceinline__ NearPair32 near_pair32(float dx, float dy, float dz, 
     return o;
 }
 
-// target side, batch-major: lanes are targets, the leaf's sources are
-// broadcast from a tile of 32 records (4 float4: x_hi, x_lo, f, h | nu)
+// target side: the forward near field's group walk (tc_nearpair.cuh: four
+// batches per warp, the targets of each leaf packed into 32-lane streams, two
+// sources per packed FP32x2 instruction) with the gradient's pair terms;
+// the result is added to the far part already in gt.
+struct NearOpG {
+    struct Tgt {
+        float2 h0, h1, h2, l0, l1, l2, g0, g1, g2;
+    };
+    static constexpr bool kAdd = true;
+    __device__ static Tgt load(const double* ts, const double* gs, int64_t M, int64_t m, bool valid)
+    {
+        float h[3] = {0, 0, 0}, l[3] = {0, 0, 0}, g[3] = {0, 0, 0};
+        if (valid)
+            for (int a = 0; a < 3; a++) {
+                const double v = ts[a * M + m];
+                h[a] = __double2float_rn(v);
+                l[a] = __double2float_rn(v - (double)h[a]);
+                g[a] = __double2float_rn(gs[a * M + m]);
+            }
+        Tgt t;
+        t.h0 = make_float2(h[0], h[0]), t.h1 = make_float2(h[1], h[1]), t.h2 = make_float2(h[2], h[2]);
+        t.l0 = make_float2(l[0], l[0]), t.l1 = make_float2(l[1], l[1]), t.l2 = make_float2(l[2], l[2]);
+        t.g0 = make_float2(g[0], g[0]), t.g1 = make_float2(g[1], g[1]), t.g2 = make_float2(g[2], g[2]);
+        return t;
+    }
+    // d(g.K)/dd_a = d_a c1 + g_a st + f_a c3 + h_a c4 + nu_a c5 for two sources
+    __device__ static void terms(const Tgt& t, const float4* tp, float2& ax, float2& ay, float2& az)
+    {
+        using nearpair::sub2;
+        const float4 A = tp[0], B = tp[1], C = tp[2], D = tp[3], E = tp[4], F = tp[5], G = tp[6], Q = tp[7];
+        const float2 dx = __fadd2_rn(sub2(t.h0, make_float2(A.x, A.y)), sub2(t.l0, make_float2(C.x, C.y)));
+        const float2 dy = __fadd2_rn(sub2(t.h1, make_float2(A.z, A.w)), sub2(t.l1, make_float2(C.z, C.w)));
+        const float2 dz = __fadd2_rn(sub2(t.h2, make_float2(B.x, B.y)), sub2(t.l2, make_float2(D.x, D.y)));
+        const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+        float2 ri;
+        ri.x = r2.x > 0.f ? rsqrtf(r2.x) : 0.f;
+        ri.y = r2.y > 0.f ? rsqrtf(r2.y) : 0.f;
+        const float2 ri2 = __fmul2_rn(ri, ri), ri3 = __fmul2_rn(ri2, ri), ri5 = __fmul2_rn(ri3, ri2);
+        const float2 f0 = make_float2(B.z, B.w), f1 = make_float2(D.z, D.w), f2 = make_float2(E.x, E.y);
+        const float2 h0 = make_float2(E.z, E.w), h1 = make_float2(F.x, F.y), h2 = make_float2(F.z, F.w);
+        const float2 n0 = make_float2(G.x, G.y), n1 = make_float2(G.z, G.w), n2 = make_float2(Q.x, Q.y);
+        const float2 df = __ffma2_rn(dx, f0, __ffma2_rn(dy, f1, __fmul2_rn(dz, f2)));
+        const float2 dh = __ffma2_rn(dx, h0, __ffma2_rn(dy, h1, __fmul2_rn(dz, h2)));
+        const float2 dn = __ffma2_rn(dx, n0, __ffma2_rn(dy, n1, __fmul2_rn(dz, n2)));
+        const float2 gd = __ffma2_rn(dx, t.g0, __ffma2_rn(dy, t.g1, __fmul2_rn(dz, t.g2)));
+        const float2 gf = __ffma2_rn(t.g0, f0, __ffma2_rn(t.g1, f1, __fmul2_rn(t.g2, f2)));
+        const float2 t5 = __fmul2_rn(__fmul2_rn(dh, dn), ri5);
+        const float2 st = __ffma2_rn(df, ri3, t5);
+        const float2 c3 = __fmul2_rn(gd, ri3);
+        const float2 inner = __ffma2_rn(__fmul2_rn(make_float2(3.f, 3.f), df), ri3, __fmul2_rn(make_float2(5.f, 5.f), t5));
+        const float2 c1n = __ffma2_rn(gf, ri3, __fmul2_rn(__fmul2_rn(gd, ri2), inner));  // -c1
+        const float2 c4 = __fmul2_rn(__fmul2_rn(c3, dn), ri2);
+        const float2 c5 = __fmul2_rn(__fmul2_rn(c3, dh), ri2);
+        ax = __ffma2_rn(t.g0, st, __ffma2_rn(f0, c3, __ffma2_rn(h0, c4, __ffma2_rn(n0, c5, nearpair::sub2(ax, __fmul2_rn(dx, c1n))))));
+        ay = __ffma2_rn(t.g1, st, __ffma2_rn(f1, c3, __ffma2_rn(h1, c4, __ffma2_rn(n1, c5, nearpair::sub2(ay, __fmul2_rn(dy, c1n))))));
+        az = __ffma2_rn(t.g2, st, __ffma2_rn(f2, c3, __ffma2_rn(h2, c4, __ffma2_rn(n2, c5, nearpair::sub2(az, __fmul2_rn(dz, c1n))))));
+    }
+};
+
+constexpr int kNearAdjGroup = 4;
+
 __global__ void __launch_bounds__(kNearAdjWarps * 32)
     k_near_adj_target32(const double* __restrict__ ts, const double* __restrict__ gs, int64_t M,
                         const int4* __restrict__ topo, const float4* __restrict__ spack,
                         const int64_t* __restrict__ near_off, const ListEntry* __restrict__ near_list,
                         double* __restrict__ gt)
 {
-    __shared__ float4 tile[kNearAdjWarps][32][4];
+    __shared__ nearpair::NearScratch<kNearAdjGroup> sc[kNearAdjWarps];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t nbatch = (M + kBatch - 1) / kBatch;
-    const int64_t b = blockIdx.x * (int64_t)kNearAdjWarps + w;
-    if (b >= nbatch) return;
-    const int64_t m = b * kBatch + lane;
-    const bool valid = m < M;
-    float th[3] = {0, 0, 0}, tl[3] = {0, 0, 0}, g[3] = {0, 0, 0};
-    if (valid)
-        for (int a = 0; a < 3; a++) {
-            const double v = ts[a * M + m];
-            th[a] = __double2float_rn(v);
-            tl[a] = __double2float_rn(v - (double)th[a]);
-            g[a] = __double2float_rn(gs[a * M + m]);
-        }
-    double acc0 = 0, acc1 = 0, acc2 = 0;
-    for (int64_t e = near_off[b]; e < near_off[b + 1]; e++) {
-        const ListEntry le = near_list[e];
-        const bool in = (le.mask >> lane) & 1u;
-        const int4 t = topo[le.node];
-        for (int base = t.x; base < t.x + t.y; base += 32) {
-            const int cnt = min(32, t.x + t.y - base);
-            __syncwarp();
-            if (lane < cnt) {
-                const float4* src = spack + 4 * (int64_t)(base + lane);
-                tile[w][lane][0] = src[0];  // (x_hi, f0)
-                tile[w][lane][1] = src[1];  // (x_lo, f1)
-                tile[w][lane][2] = src[2];  // (f2, h)
-                tile[w][lane][3] = src[3];  // (nu, 0)
-            }
-            __syncwarp();
-            if (!in) continue;
-            float a0 = 0.f, a1 = 0.f, a2 = 0.f;
-            for (int j = 0; j < cnt; j++) {
-                const float4 A = tile[w][j][0], B = tile[w][j][1], C = tile[w][j][2], D = tile[w][j][3];
-                const float dx = (th[0] - A.x) + (tl[0] - B.x);
-                const float dy = (th[1] - A.y) + (tl[1] - B.y);
-                const float dz = (th[2] - A.z) + (tl[2] - B.z);
-                const NearPair32 q = near_pair32(dx, dy, dz, A.w, B.w, C.x, C.y, C.z, C.w, D.x, D.y, D.z, g[0], g[1],
-                                                 g[2]);
-                a0 += fmaf(dx, q.c1, fmaf(g[0], q.st, fmaf(A.w, q.c3, fmaf(C.y, q.c4, D.x * q.c5))));
-                a1 += fmaf(dy, q.c1, fmaf(g[1], q.st, fmaf(B.w, q.c3, fmaf(C.z, q.c4, D.y * q.c5))));
-                a2 += fmaf(dz, q.c1, fmaf(g[2], q.st, fmaf(C.x, q.c3, fmaf(C.w, q.c4, D.z * q.c5))));
-            }
-            acc0 += (double)a0;
-            acc1 += (double)a1;
-            acc2 += (double)a2;
-        }
-    }
-    if (valid) {
-        gt[m] += acc0;
-        gt[M + m] += acc1;
-        gt[2 * M + m] += acc2;
-    }
+    const int64_t ngroup = ((M + kBatch - 1) / kBatch + kNearAdjGroup - 1) / kNearAdjGroup;
+    const int64_t B = blockIdx.x * (int64_t)kNearAdjWarps + w;
+    if (B >= ngroup) return;
+    nearpair::near_group<kNearAdjGroup, NearOpG>(ts, gs, M, topo, spack, near_off, near_list, gt, B, sc[w], lane);
 }
 
 // source side over the near entries sorted by leaf, in chunks of
@@ -399,7 +411,9 @@ __global__ void __launch_bounds__(kNearAdjWarps * 32)
                         const ListEntry* __restrict__ near_list, const int32_t* __restrict__ ebatch, int64_t nent,
                         double* __restrict__ gnear)
 {
-    __shared__ float4 tile[kNearAdjWarps][32][3];
+    // staged targets, field-major: x_hi (3), x_lo (3), g (3); targets q, q+1
+    // are read together as one float2 per field
+    __shared__ __align__(8) float tile[kNearAdjWarps][9][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t c0 = (int64_t)blockIdx.x * kNearAdjChunk;
     const int64_t c1 = min(nent, c0 + kNearAdjChunk);
@@ -415,8 +429,12 @@ __global__ void __launch_bounds__(kNearAdjWarps * 32)
                 const float4* src = spack + 4 * si;
                 A = src[0], B = src[1], C = src[2], D = src[3];
             }
-            const float sh0 = A.x, sh1 = A.y, sh2 = A.z, sl0 = B.x, sl1 = B.y, sl2 = B.z;
-            const float f0 = A.w, f1 = B.w, f2 = C.x, h0 = C.y, h1 = C.z, h2 = C.w, n0 = D.x, n1 = D.y, n2 = D.z;
+            // this lane's source, replicated into both halves of each pair
+            const float2 sh0 = make_float2(A.x, A.x), sh1 = make_float2(A.y, A.y), sh2 = make_float2(A.z, A.z);
+            const float2 sl0 = make_float2(B.x, B.x), sl1 = make_float2(B.y, B.y), sl2 = make_float2(B.z, B.z);
+            const float2 f0 = make_float2(A.w, A.w), f1 = make_float2(B.w, B.w), f2 = make_float2(C.x, C.x);
+            const float2 h0 = make_float2(C.y, C.y), h1 = make_float2(C.z, C.z), h2 = make_float2(C.w, C.w);
+            const float2 n0 = make_float2(D.x, D.x), n1 = make_float2(D.y, D.y), n2 = make_float2(D.z, D.z);
             double acc[12];
 #pragma unroll
             for (int c = 0; c < 12; c++) acc[c] = 0.0;
@@ -426,49 +444,69 @@ __global__ void __launch_bounds__(kNearAdjWarps * 32)
                 const int64_t m = (int64_t)ebatch[e] * kBatch + lane;
                 __syncwarp();
                 {
-                    float4 p0 = make_float4(0, 0, 0, 0), p1 = p0, p2 = p0;
-                    if ((mask >> lane) & 1u) {
-                        float xh[3], xl[3];
+                    float v[9];
+#pragma unroll
+                    for (int k = 0; k < 9; k++) v[k] = 0.f;
+                    if ((mask >> lane) & 1u)
                         for (int a = 0; a < 3; a++) {
-                            const double v = ts[a * M + m];
-                            xh[a] = __double2float_rn(v);
-                            xl[a] = __double2float_rn(v - (double)xh[a]);
+                            const double x = ts[a * M + m];
+                            v[a] = __double2float_rn(x);
+                            v[3 + a] = __double2float_rn(x - (double)v[a]);
+                            v[6 + a] = __double2float_rn(gs[a * M + m]);
                         }
-                        p0 = make_float4(xh[0], xh[1], xh[2], __double2float_rn(gs[m]));
-                        p1 = make_float4(xl[0], xl[1], xl[2], __double2float_rn(gs[M + m]));
-                        p2 = make_float4(__double2float_rn(gs[2 * M + m]), 0.f, 0.f, 0.f);
-                    }
-                    tile[w][lane][0] = p0;
-                    tile[w][lane][1] = p1;
-                    tile[w][lane][2] = p2;
+#pragma unroll
+                    for (int k = 0; k < 9; k++) tile[w][k][lane] = v[k];
                 }
                 __syncwarp();
-                float a[12];
+                float2 a[12];
 #pragma unroll
-                for (int c = 0; c < 12; c++) a[c] = 0.f;
-#pragma unroll 2
-                for (int q = 0; q < 32; q++) {
-                    const float4 T0 = tile[w][q][0], T1 = tile[w][q][1], T2 = tile[w][q][2];
-                    const float g0 = T0.w, g1 = T1.w, g2 = T2.x;
-                    const float dx = (T0.x - sh0) + (T1.x - sl0);
-                    const float dy = (T0.y - sh1) + (T1.y - sl1);
-                    const float dz = (T0.z - sh2) + (T1.z - sl2);
-                    const NearPair32 z = near_pair32(dx, dy, dz, f0, f1, f2, h0, h1, h2, n0, n1, n2, g0, g1, g2);
-                    a[0] += fmaf(g0, z.ri, dx * z.c3);
-                    a[1] += fmaf(g1, z.ri, dy * z.c3);
-                    a[2] += fmaf(g2, z.ri, dz * z.c3);
-                    a[3] = fmaf(dx, z.c4, a[3]);
-                    a[4] = fmaf(dy, z.c4, a[4]);
-                    a[5] = fmaf(dz, z.c4, a[5]);
-                    a[6] = fmaf(dx, z.c5, a[6]);
-                    a[7] = fmaf(dy, z.c5, a[7]);
-                    a[8] = fmaf(dz, z.c5, a[8]);
-                    a[9] -= fmaf(dx, z.c1, fmaf(g0, z.st, fmaf(f0, z.c3, fmaf(h0, z.c4, n0 * z.c5))));
-                    a[10] -= fmaf(dy, z.c1, fmaf(g1, z.st, fmaf(f1, z.c3, fmaf(h1, z.c4, n1 * z.c5))));
-                    a[11] -= fmaf(dz, z.c1, fmaf(g2, z.st, fmaf(f2, z.c3, fmaf(h2, z.c4, n2 * z.c5))));
+                for (int c = 0; c < 12; c++) a[c] = make_float2(0.f, 0.f);
+                for (int q = 0; q < 32; q += 2) {
+                    float2 T[9];
+#pragma unroll
+                    for (int k = 0; k < 9; k++) T[k] = *reinterpret_cast<const float2*>(&tile[w][k][q]);
+                    using nearpair::sub2;
+                    const float2 dx = __fadd2_rn(sub2(T[0], sh0), sub2(T[3], sl0));
+                    const float2 dy = __fadd2_rn(sub2(T[1], sh1), sub2(T[4], sl1));
+                    const float2 dz = __fadd2_rn(sub2(T[2], sh2), sub2(T[5], sl2));
+                    const float2 g0 = T[6], g1 = T[7], g2 = T[8];
+                    const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+                    float2 ri;
+                    ri.x = r2.x > 0.f ? rsqrtf(r2.x) : 0.f;
+                    ri.y = r2.y > 0.f ? rsqrtf(r2.y) : 0.f;
+                    const float2 ri2 = __fmul2_rn(ri, ri), ri3 = __fmul2_rn(ri2, ri), ri5 = __fmul2_rn(ri3, ri2);
+                    const float2 df = __ffma2_rn(dx, f0, __ffma2_rn(dy, f1, __fmul2_rn(dz, f2)));
+                    const float2 dh = __ffma2_rn(dx, h0, __ffma2_rn(dy, h1, __fmul2_rn(dz, h2)));
+                    const float2 dn = __ffma2_rn(dx, n0, __ffma2_rn(dy, n1, __fmul2_rn(dz, n2)));
+                    const float2 gd = __ffma2_rn(dx, g0, __ffma2_rn(dy, g1, __fmul2_rn(dz, g2)));
+                    const float2 gf = __ffma2_rn(g0, f0, __ffma2_rn(g1, f1, __fmul2_rn(g2, f2)));
+                    const float2 t5 = __fmul2_rn(__fmul2_rn(dh, dn), ri5);
+                    const float2 st = __ffma2_rn(df, ri3, t5);
+                    const float2 c3 = __fmul2_rn(gd, ri3);
+                    const float2 inner =
+                        __ffma2_rn(__fmul2_rn(make_float2(3.f, 3.f), df), ri3, __fmul2_rn(make_float2(5.f, 5.f), t5));
+                    const float2 c1n = __ffma2_rn(gf, ri3, __fmul2_rn(__fmul2_rn(gd, ri2), inner));  // -c1
+                    const float2 c4 = __fmul2_rn(__fmul2_rn(c3, dn), ri2);
+                    const float2 c5 = __fmul2_rn(__fmul2_rn(c3, dh), ri2);
+                    a[0] = __ffma2_rn(g0, ri, __ffma2_rn(dx, c3, a[0]));
+                    a[1] = __ffma2_rn(g1, ri, __ffma2_rn(dy, c3, a[1]));
+                    a[2] = __ffma2_rn(g2, ri, __ffma2_rn(dz, c3, a[2]));
+                    a[3] = __ffma2_rn(dx, c4, a[3]);
+                    a[4] = __ffma2_rn(dy, c4, a[4]);
+                    a[5] = __ffma2_rn(dz, c4, a[5]);
+                    a[6] = __ffma2_rn(dx, c5, a[6]);
+                    a[7] = __ffma2_rn(dy, c5, a[7]);
+                    a[8] = __ffma2_rn(dz, c5, a[8]);
+                    // dL/dy = -d(g.K)/dd = -(d c1 + g st + f c3 + h c4 + nu c5)
+                    a[9] = __ffma2_rn(dx, c1n, sub2(a[9], __ffma2_rn(g0, st, __ffma2_rn(f0, c3,
+                                                       __ffma2_rn(h0, c4, __fmul2_rn(n0, c5))))));
+                    a[10] = __ffma2_rn(dy, c1n, sub2(a[10], __ffma2_rn(g1, st, __ffma2_rn(f1, c3,
+                                                        __ffma2_rn(h1, c4, __fmul2_rn(n1, c5))))));
+                    a[11] = __ffma2_rn(dz, c1n, sub2(a[11], __ffma2_rn(g2, st, __ffma2_rn(f2, c3,
+                                                        __ffma2_rn(h2, c4, __fmul2_rn(n2, c5))))));
                 }
 #pragma unroll
-                for (int c = 0; c < 12; c++) acc[c] += (double)a[c];
+                for (int c = 0; c < 12; c++) acc[c] += (double)(a[c].x + a[c].y);
             }
             if (valid)
                 for (int c = 0; c < 12; c++) atomicAdd(&gnear[c * N + si], acc[c]);
@@ -1335,6 +1373,8 @@ extern "C" tc_status tc_adjoint(tc_ctx* ctx, const double* g, double* grad_f, do
 
     // near field: target side adds to adj_gt; source side writes adj_gnear
     const unsigned ngrid = (unsigned)((nbatch + kNearAdjWarps - 1) / kNearAdjWarps);
+    const int64_t ngroup = (nbatch + kNearAdjGroup - 1) / kNearAdjGroup;
+    const unsigned ngrid32 = (unsigned)((ngroup + kNearAdjWarps - 1) / kNearAdjWarps);
     if (ctx->precision == TC_FP64) {
         k_near_adj_target<double><<<ngrid, kNearAdjWarps * 32, 0, s>>>(
             ts, ptr<double>(ctx->adj_gs), M, ptr<int4>(ctx->node_topo), ptr<double>(ctx->xs), ptr<double>(ctx->ws), N,
@@ -1346,7 +1386,7 @@ extern "C" tc_status tc_adjoint(tc_ctx* ctx, const double* g, double* grad_f, do
             ptr<int32_t>(ctx->adj_nebatch), ctx->near_entries, ptr<double>(ctx->adj_gnear));
         note_launch();
     } else {
-        k_near_adj_target32<<<ngrid, kNearAdjWarps * 32, 0, s>>>(
+        k_near_adj_target32<<<ngrid32, kNearAdjWarps * 32, 0, s>>>(
             ts, ptr<double>(ctx->adj_gs), M, ptr<int4>(ctx->node_topo), ptr<float4>(ctx->spack),
             ptr<int64_t>(ctx->near_off), ptr<ListEntry>(ctx->near_list), ptr<double>(ctx->adj_gt));
         note_launch();

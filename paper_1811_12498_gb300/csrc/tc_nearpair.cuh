@@ -1,0 +1,212 @@
+// Packed FP32x2 near-field machinery shared by the forward near field
+// (tc_near.cu) and the target side of its adjoint (tc_adjoint.cu): the
+// staging of 32-source tiles as source pairs, and the walk of a group of
+// batches over the merge of their near lists with the targets of each leaf
+// packed into 32-lane streams.  See tc_near.cu for the design.
+#pragma once
+
+#include "tc_internal.cuh"
+
+namespace tc {
+namespace nearpair {
+
+// ---------------------------------------------------------------------------
+// mixed precision: packed FP32x2 arithmetic
+
+__device__ __forceinline__ float2 sub2(float2 a, float2 b)
+{
+    float2 r;
+    asm("{\n\t.reg .b64 ta, tb, td;\n\tmov.b64 ta, {%2, %3};\n\tmov.b64 tb, {%4, %5};\n\t"
+        "sub.rn.f32x2 td, ta, tb;\n\tmov.b64 {%0, %1}, td;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+
+// A source record is 16 FP32 fields: x_hi (3), f0, x_lo (3), f1, f2, h (3),
+// nu (3), pad.  The tile stores source pair q (sources 2q, 2q+1) as 8 float4,
+// float4 k = (y_2q.f_2k, y_2q+1.f_2k, y_2q.f_2k+1, y_2q+1.f_2k+1), with a
+// stride of 9 float4 per pair so that the staging stores are free of bank
+// conflicts.
+constexpr int kPairStride = 9;
+constexpr int kTileFloat4 = 16 * kPairStride;
+
+// Stage sources [base, base + cnt), cnt <= 32, into the tile.  Lanes past cnt
+// contribute a source at 1e30 with zero weights (its terms are exactly 0:
+// r^2 overflows to inf, 1/r = 0, and every weight is 0).
+__device__ inline void stage_pairs(const float4* __restrict__ spack, int64_t base, int cnt, float4* tw, int lane)
+{
+    float f[16];
+    if (lane < cnt) {
+        const float4* src = spack + 4 * (base + lane);
+        const float4 a = src[0], b = src[1], c = src[2], d = src[3];
+        f[0] = a.x, f[1] = a.y, f[2] = a.z, f[3] = a.w;
+        f[4] = b.x, f[5] = b.y, f[6] = b.z, f[7] = b.w;
+        f[8] = c.x, f[9] = c.y, f[10] = c.z, f[11] = c.w;
+        f[12] = d.x, f[13] = d.y, f[14] = d.z, f[15] = d.w;
+    } else {
+#pragma unroll
+        for (int k = 0; k < 16; k++) f[k] = k < 3 ? 1e30f : 0.0f;
+    }
+    const int par = lane & 1;
+    float recv[8];
+#pragma unroll
+    for (int k = 0; k < 8; k++) recv[k] = __shfl_xor_sync(0xffffffffu, par ? f[k] : f[8 + k], 1);
+    float4* dst = tw + (lane >> 1) * kPairStride;
+    if (!par) {
+#pragma unroll
+        for (int j = 0; j < 4; j++) dst[j] = make_float4(f[2 * j], recv[2 * j], f[2 * j + 1], recv[2 * j + 1]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+            dst[4 + j] = make_float4(recv[2 * j], f[8 + 2 * j], recv[2 * j + 1], f[9 + 2 * j]);
+    }
+}
+
+// Per-warp scratch of the compacted near kernel: the source tile, the
+// accumulators of the warp's G x 32 targets and the stream slot map.
+template <int G>
+struct NearScratch {
+    float4 tile[kTileFloat4];
+    double acc[G][3][32];
+    int slot[G * 32];
+};
+
+// Near field of batches G*B .. G*B+G-1 (the last ones may not exist) on one
+// warp, over the merge of their G near lists (all in tree order, so by the
+// leaf's first source).  For each leaf, the targets of the G batches that
+// need it (the union of the entries' lane masks, A of them) are packed
+// densely into ceil(A/32) streams of 32 lanes, so lanes whose target does not
+// need the leaf are not computed (lane use of single-batch lists at N = 1M:
+// 0.74); streams are evaluated two at a time, each sharing the staged tile,
+// and each result is added to its target's accumulator in shared memory.
+//
+// Op supplies the per-target record (Op::Tgt, Op::load), the pair terms of one
+// target against a staged source pair (Op::terms, three FP32x2 accumulators)
+// and whether the result is stored or added (Op::kAdd); gs is passed through
+// to Op::load (the adjoint's target weights g, unused by the forward field).
+template <int G, typename Op>
+__device__ inline void near_group(const double* __restrict__ ts, const double* __restrict__ gs, int64_t M,
+                                  const int4* __restrict__ topo, const float4* __restrict__ spack,
+                                  const int64_t* __restrict__ near_off, const ListEntry* __restrict__ near_list,
+                                  double* __restrict__ out, int64_t B, NearScratch<G>& sc, int lane)
+{
+    const int64_t nbatch = (M + kBatch - 1) / kBatch;
+    const int64_t b0 = (int64_t)G * B;
+    constexpr int kEnd = 0x7fffffff;
+    int64_t cur[G], end[G];
+    ListEntry le[G];
+    int key[G];
+#pragma unroll
+    for (int g = 0; g < G; g++) {
+        cur[g] = end[g] = 0;
+        if (b0 + g < nbatch) {
+            cur[g] = near_off[b0 + g];
+            end[g] = near_off[b0 + g + 1];
+        }
+        key[g] = kEnd;
+        le[g] = ListEntry{0, 0};
+        if (cur[g] < end[g]) {
+            le[g] = near_list[cur[g]];
+            key[g] = topo[le[g].node].x;
+        }
+#pragma unroll
+        for (int c = 0; c < 3; c++) sc.acc[g][c][lane] = 0.0;
+    }
+    const unsigned lt = (1u << lane) - 1u;
+    for (;;) {
+        int kmin = key[0];
+#pragma unroll
+        for (int g = 1; g < G; g++) kmin = min(kmin, key[g]);
+        if (kmin == kEnd) break;
+        // leaves are disjoint ranges, so equal first sources name one leaf
+        int node = 0;
+        unsigned m[G];
+        int A = 0, P[G];
+#pragma unroll
+        for (int g = G - 1; g >= 0; g--)
+            if (key[g] == kmin) node = le[g].node;
+#pragma unroll
+        for (int g = 0; g < G; g++) {
+            m[g] = key[g] == kmin ? le[g].mask : 0u;
+            P[g] = A;
+            A += __popc(m[g]);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int g = 0; g < G; g++)
+            if ((m[g] >> lane) & 1u) sc.slot[P[g] + __popc(m[g] & lt)] = g * 32 + lane;
+        __syncwarp();
+        const int4 t = topo[node];
+        const int S = (A + 31) >> 5;
+        for (int s = 0; s < S; s += 2) {
+            const bool two = s + 1 < S;
+            const int k1 = 32 * s + lane, k2 = k1 + 32;
+            const bool v1 = k1 < A, v2 = two && k2 < A;
+            const int id1 = v1 ? sc.slot[k1] : 0, id2 = v2 ? sc.slot[k2] : 0;
+            const typename Op::Tgt ta = Op::load(ts, gs, M, (b0 + (id1 >> 5)) * kBatch + (id1 & 31), v1);
+            const typename Op::Tgt tb = Op::load(ts, gs, M, (b0 + (id2 >> 5)) * kBatch + (id2 & 31), v2);
+            double a0 = 0, a1 = 0, a2 = 0, c0 = 0, c1 = 0, c2 = 0;
+            for (int base = t.x; base < t.x + t.y; base += 32) {
+                const int cnt = min(32, t.x + t.y - base);
+                __syncwarp();
+                stage_pairs(spack, base, cnt, sc.tile, lane);
+                __syncwarp();
+                const int npairs = (cnt + 1) >> 1;
+                float2 axa = make_float2(0.f, 0.f), aya = axa, aza = axa, axb = axa, ayb = axa, azb = axa;
+                if (two) {
+                    for (int q = 0; q < npairs; q++) {
+                        const float4* tp = sc.tile + q * kPairStride;
+                        Op::terms(ta, tp, axa, aya, aza);
+                        Op::terms(tb, tp, axb, ayb, azb);
+                    }
+                } else {
+                    for (int q = 0; q < npairs; q++) Op::terms(ta, sc.tile + q * kPairStride, axa, aya, aza);
+                }
+                a0 += (double)(axa.x + axa.y);
+                a1 += (double)(aya.x + aya.y);
+                a2 += (double)(aza.x + aza.y);
+                c0 += (double)(axb.x + axb.y);
+                c1 += (double)(ayb.x + ayb.y);
+                c2 += (double)(azb.x + azb.y);
+            }
+            // each (batch, lane) target holds one slot per leaf: no two lanes
+            // add to the same accumulator here
+            if (v1) {
+                sc.acc[id1 >> 5][0][id1 & 31] += a0;
+                sc.acc[id1 >> 5][1][id1 & 31] += a1;
+                sc.acc[id1 >> 5][2][id1 & 31] += a2;
+            }
+            if (v2) {
+                sc.acc[id2 >> 5][0][id2 & 31] += c0;
+                sc.acc[id2 >> 5][1][id2 & 31] += c1;
+                sc.acc[id2 >> 5][2][id2 & 31] += c2;
+            }
+        }
+#pragma unroll
+        for (int g = 0; g < G; g++)
+            if (key[g] == kmin) {
+                if (++cur[g] < end[g]) {
+                    le[g] = near_list[cur[g]];
+                    key[g] = topo[le[g].node].x;
+                } else {
+                    key[g] = kEnd;
+                }
+            }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int g = 0; g < G; g++) {
+        const int64_t mm = (b0 + g) * kBatch + lane;
+        if (mm < M)
+            for (int c = 0; c < 3; c++) {
+                if (Op::kAdd)
+                    out[c * M + mm] += sc.acc[g][c][lane];
+                else
+                    out[c * M + mm] = sc.acc[g][c][lane];
+            }
+    }
+}
+
+}  // namespace nearpair
+}  // namespace tc
