@@ -291,35 +291,7 @@ __global__ void __launch_bounds__(kNearAdjWarps * 32)
 
 // ------------------------------------------ near, mixed precision (FP32)
 // The same pair terms in FP32 on hi/lo positions (as the forward near field),
-// 1/r from rsqrtf, and every warp loop uniform: lanes outside an entry's mask
-// carry g = 0, which zeroes all their terms.
-
-struct NearPair32 {
-    float ri, st, c1, c3, c4, c5;
-};
-
-__device__ __forceinline__ NearPair32 near_pair32(float dx, float dy, float dz, float f0, float f1, float f2, float h0,
-                                                  float h1, float h2, float n0, float n1, float n2, float g0, float g1,
-                                                  float g2)
-{
-    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    const float ri = r2 > 0.f ? rsqrtf(r2) : 0.f;
-    const float ri2 = ri * ri, ri3 = ri2 * ri, ri5 = ri3 * ri2;
-    const float df = fmaf(dx, f0, fmaf(dy, f1, dz * f2));
-    const float dh = fmaf(dx, h0, fmaf(dy, h1, dz * h2));
-    const float dn = fmaf(dx, n0, fmaf(dy, n1, dz * n2));
-    const float gd = fmaf(dx, g0, fmaf(dy, g1, dz * g2));
-    const float gf = fmaf(g0, f0, fmaf(g1, f1, g2 * f2));
-    const float t5 = dh * dn * ri5;  // (d.h)(d.nu)/r^5
-    NearPair32 o;
-    o.ri = ri;
-    o.st = fmaf(df, ri3, t5);
-    o.c3 = gd * ri3;
-    o.c1 = -fmaf(gf, ri3, gd * ri2 * fmaf(3.f * df, ri3, 5.f * t5));
-    o.c4 = o.c3 * dn * ri2;
-    o.c5 = o.c3 * dh * ri2;
-    return o;
-}
+// 1/r from rsqrtf, packed FP32x2 arithmetic.
 
 // target side: the forward near field's group walk (tc_nearpair.cuh: four
 // batches per warp, the targets of each leaf packed into 32-lane streams, two
@@ -399,9 +371,11 @@ __global__ void __launch_bounds__(kNearAdjWarps * 32)
 // source side over the near entries sorted by leaf, in chunks of
 // kNearAdjChunk entries (a chunk can straddle leaves): for each leaf segment
 // of its chunk a block runs a warp per 32 of the leaf's sources over the
-// segment's entries; each entry's 32 targets (x_hi | g0, x_lo | g1, g2) are
-// staged and every lane runs over all 32 of them.  Per-segment sums are added
-// to the FP64 source gradients with atomics (gnear is zeroed first).
+// segment's entries; each entry's 32 targets are staged and every lane runs
+// over all of them, two per packed instruction (lanes outside the entry's
+// mask carry g = 0, which zeroes their terms, so the loop stays uniform).
+// Per-segment sums are added to the FP64 source gradients with atomics (gnear
+// is zeroed first).
 constexpr int kNearAdjChunk = 64;
 
 __global__ void __launch_bounds__(kNearAdjWarps * 32)

@@ -424,10 +424,8 @@ tc_status tc::eval_prepare(tc_ctx* ctx, const double* targets, int64_t M, double
     ctx->prepared = 0;
     ctx->adj_lists_ready = 0;
     const double* ts;
-    const int32_t* tperm;
     if (!targets) {
         ts = ptr<double>(ctx->xs);
-        tperm = ptr<int32_t>(ctx->perm);
         ctx->eval_self = 1;
     } else {
         int nrad = radix_blocks(M);
@@ -446,7 +444,6 @@ tc_status tc::eval_prepare(tc_ctx* ctx, const double* targets, int64_t M, double
         TC_CK(launch_gather3(targets, ptr<int32_t>(ctx->tperm), M, ptr<double>(ctx->ts), s), "gather targets");
         ph_end(ctx, TC_PH_TARGETS);
         ts = ptr<double>(ctx->ts);
-        tperm = ptr<int32_t>(ctx->tperm);
         ctx->eval_self = 0;
     }
     const int64_t nbatch = (M + kBatch - 1) / kBatch;
@@ -492,7 +489,6 @@ tc_status tc::eval_prepare(tc_ctx* ctx, const double* targets, int64_t M, double
     TC_CK(join_moments(ctx), "join moments");
     st = ensure_tables(ctx, p);
     if (st != TC_OK) return st;
-    (void)tperm;
     ctx->M = M;
     ctx->far_entries = tot[0];
     ctx->near_entries = tot[1];

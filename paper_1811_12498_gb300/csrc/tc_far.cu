@@ -202,23 +202,6 @@ __device__ inline void far_slots(unsigned char* smraw, int p, int w, double*& sl
 // ---------------------------------------------------------------------------
 // FP32, compile-time order: coefficients in registers
 
-__device__ __forceinline__ void contract12f(float c, const float4* __restrict__ t, float* tot)
-{
-    const float4 a = __ldg(t), b = __ldg(t + 1), d = __ldg(t + 2);
-    tot[0] = fmaf(c, a.x, tot[0]);
-    tot[1] = fmaf(c, a.y, tot[1]);
-    tot[2] = fmaf(c, a.z, tot[2]);
-    tot[3] = fmaf(c, a.w, tot[3]);
-    tot[4] = fmaf(c, b.x, tot[4]);
-    tot[5] = fmaf(c, b.y, tot[5]);
-    tot[6] = fmaf(c, b.z, tot[6]);
-    tot[7] = fmaf(c, b.w, tot[7]);
-    tot[8] = fmaf(c, d.x, tot[8]);
-    tot[9] = fmaf(c, d.y, tot[9]);
-    tot[10] = fmaf(c, d.z, tot[10]);
-    tot[11] = fmaf(c, d.w, tot[11]);
-}
-
 // A target as FP32 hi/lo splits of its FP64 coordinates.
 struct Tgt32 {
     float h0, h1, h2, l0, l1, l2;
