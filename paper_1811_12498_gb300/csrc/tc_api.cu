@@ -371,10 +371,9 @@ tc_status tc_moments(tc_ctx* ctx, const double* f, const double* h, const double
     return TC_OK;
 }
 
-static tc_status ensure_tables(tc_ctx* ctx, int p)
+static tc_status ensure_tables(tc_ctx* ctx, int p, cudaStream_t s)
 {
     if (ctx->ab_p == p) return TC_OK;
-    cudaStream_t s = ctx->stream;
     const int64_t n = ctx->nnodes * ncoef(p + 2) * 12;
     const int64_t nf = ctx->nnodes * (int64_t)(p + 3) * (p + 3) * 12;
     // FP64 full tables (always: they are the input of the folding), FP32 full
@@ -390,7 +389,7 @@ static tc_status ensure_tables(tc_ctx* ctx, int p)
     } else {
         TC_CK(ensure(ctx->abf64, (size_t)nf * 8), "alloc tables");
     }
-    ph_begin(ctx, TC_PH_TABLES);
+    ph_begin(ctx, TC_PH_TABLES, s);
     TC_CK(launch_ab_tables(ptr<double>(ctx->mom), ptr<double>(ctx->node_invrho), ctx->nnodes, ctx->p_mom, p,
                            ptr<double>(ctx->ab64), ab32, s),
           "tables");
@@ -400,7 +399,7 @@ static tc_status ensure_tables(tc_ctx* ctx, int p)
                              ptr<Geo>(ctx->node_geo), ptr<double>(ctx->node_invrho),
                              ctx->precision == TC_FP64 ? nullptr : ptr<float4>(ctx->geo32), s),
           "fold tables");
-    ph_end(ctx, TC_PH_TABLES);
+    ph_end(ctx, TC_PH_TABLES, s);
     ctx->ab_p = p;
     return TC_OK;
 }
@@ -484,11 +483,19 @@ tc_status tc::eval_prepare(tc_ctx* ctx, const double* targets, int64_t M, double
                        ptr<int64_t>(ctx->cnt_near), ptr<int32_t>(ctx->flags), s),
           "list write");
     ph_end(ctx, TC_PH_LISTS);
-    // the tables read the moments: join the moment passes here, after the
-    // traversal that ran beside them
-    TC_CK(join_moments(ctx), "join moments");
-    st = ensure_tables(ctx, p);
-    if (st != TC_OK) return st;
+    // The tables read the moments.  While the moment passes are still in
+    // flight on the second stream, the tables follow them there: the far
+    // field, which reads them, runs on that stream too, and the near field,
+    // which needs neither, starts on the first stream right after the lists.
+    // The moment event then marks the end of the tables.
+    if (ctx->mom_pending) {
+        st = ensure_tables(ctx, p, ctx->stream2);
+        if (st != TC_OK) return st;
+        TC_CK(cudaEventRecord(ctx->ev_mom, ctx->stream2), "tables done");
+    } else {
+        st = ensure_tables(ctx, p, s);
+        if (st != TC_OK) return st;
+    }
     ctx->M = M;
     ctx->far_entries = tot[0];
     ctx->near_entries = tot[1];
@@ -507,9 +514,11 @@ tc_status tc::eval_compute(tc_ctx* ctx, double* u)
     const double* ts = ctx->eval_self ? ptr<double>(ctx->xs) : ptr<double>(ctx->ts);
     const int32_t* tperm = ctx->eval_self ? ptr<int32_t>(ctx->perm) : ptr<int32_t>(ctx->tperm);
     // the far and near fields are independent: the far field runs on the
-    // context's second stream, forked from and joined back to the first
+    // context's second stream (after the moments and tables, when those are
+    // still in flight there), forked from and joined back to the first
     TC_CK(second_stream(ctx), "second stream");
     // profile mode 2: serialised, so that each phase time is one kernel's own
+    if (ctx->profile == 2) TC_CK(join_moments(ctx), "join moments");
     cudaStream_t s2 = ctx->profile == 2 ? s : ctx->stream2;
     TC_CK(cudaEventRecord(ctx->ev_fork, s), "fork");
     TC_CK(cudaStreamWaitEvent(s2, ctx->ev_fork, 0), "fork");
@@ -529,6 +538,9 @@ tc_status tc::eval_compute(tc_ctx* ctx, double* u)
           "near field");
     ph_end(ctx, TC_PH_NEAR);
     TC_CK(cudaStreamWaitEvent(s, ctx->ev_join, 0), "join");
+    // the join covers everything enqueued on the second stream, the moment
+    // passes and tables included
+    if (s2 == ctx->stream2) ctx->mom_pending = 0;
     ph_begin(ctx, TC_PH_FINAL);
     TC_CK(launch_finalize(ptr<double>(ctx->u_far), ptr<double>(ctx->u_near), tperm, M, u, s), "finalize");
     ph_end(ctx, TC_PH_FINAL);

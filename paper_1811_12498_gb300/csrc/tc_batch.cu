@@ -63,7 +63,7 @@ struct tc_batch {
     DevBuf d_off;                      // device copy of off
     DevBuf xseg, fseg, hseg, nuseg;    // per-system copies
     DevBuf desc;                       // SysDesc[nsys]
-    DevBuf item_off;                   // nsys + 1 item offsets (items: batches in FP64, batch pairs in mixed)
+    DevBuf item_off;                   // far item offsets (nsys + 1), then near item offsets (nsys + 1)
     DevBuf counters;                   // two queue counters
     std::vector<SysDesc> hdesc;
     std::vector<int64_t> hitem;
@@ -126,7 +126,8 @@ static void free_systems(tc_batch* b)
 }
 
 // far + near + finalize of all systems (stream-ordered; capturable)
-static tc_status launch_compute(tc_batch* b, const Shape& sh, int p, int64_t nitems, double* u, cudaStream_t s)
+static tc_status launch_compute(tc_batch* b, const Shape& sh, int p, int64_t nitems, int64_t nnear, double* u,
+                                cudaStream_t s)
 {
     unsigned long long* cnt = ptr<unsigned long long>(b->counters);
     TB_CK(cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), s), "reset queue");
@@ -135,7 +136,8 @@ static tc_status launch_compute(tc_batch* b, const Shape& sh, int p, int64_t nit
     TB_CK(launch_far_batched(b->cfg.precision, b->cfg.rec64, d, b->nsys, io, nitems, p, cnt, sh.far_warps,
                              sh.far_blocks, s),
           "batched far field");
-    TB_CK(launch_near_batched(b->cfg.precision, d, b->nsys, io, nitems, cnt + 1, sh.near_warps, sh.near_blocks, s),
+    TB_CK(launch_near_batched(b->cfg.precision, d, b->nsys, io + b->nsys + 1, nnear, cnt + 1, sh.near_warps,
+                              sh.near_blocks, s),
           "batched near field");
     TB_CK(launch_finalize_batched(d, b->nsys, ptr<int64_t>(b->d_off), b->ntot, u, b->ntot, s), "batched finalize");
     return TC_OK;
@@ -150,7 +152,7 @@ static int sm_count()
 }
 
 // Time each candidate shape of one kernel on the real work and keep the best.
-static tc_status tune(tc_batch* b, int p, int64_t nitems, double* u)
+static tc_status tune(tc_batch* b, int p, int64_t nitems, int64_t nnear, double* u)
 {
     cudaStream_t s = (cudaStream_t)b->cfg.stream;
     const int sms = sm_count();
@@ -193,7 +195,8 @@ static tc_status tune(tc_batch* b, int p, int64_t nitems, double* u)
             const int blocks = nb ? nb * sms : 0;
             cudaMemsetAsync(cnt + 1, 0, sizeof(unsigned long long), s);
             cudaEventRecord(e0, s);
-            cudaError_t e = launch_near_batched(b->cfg.precision, d, b->nsys, io, nitems, cnt + 1, nw, blocks, s);
+            cudaError_t e =
+                launch_near_batched(b->cfg.precision, d, b->nsys, io + b->nsys + 1, nnear, cnt + 1, nw, blocks, s);
             cudaEventRecord(e1, s);
             if (e != cudaSuccess) {
                 cudaGetLastError();
@@ -356,10 +359,14 @@ tc_status tc_batch_eval(tc_batch* b, double theta, int32_t p, double* u)
     for (int s = 0; s < b->nsys; s++) {
         tc_status r = eval_prepare(b->ctx[s], nullptr, b->off[s + 1] - b->off[s], theta, p);
         if (r != TC_OK) return from_ctx(b, b->ctx[s], r, s);
+        // the persistent kernels read every system's tables: join the
+        // system's second stream (moments, tables) into its first
+        TB_CK(join_moments(b->ctx[s]), "join moments");
     }
     // 2. descriptors and the item numbering
     b->hdesc.resize(b->nsys);
-    b->hitem.assign(b->nsys + 1, 0);
+    b->hitem.assign(2 * (b->nsys + 1), 0);
+    int64_t* hnear = b->hitem.data() + b->nsys + 1;
     for (int s = 0; s < b->nsys; s++) {
         tc_ctx* c = b->ctx[s];
         SysDesc& d = b->hdesc[s];
@@ -384,29 +391,30 @@ tc_status tc_batch_eval(tc_batch* b, double theta, int32_t p, double* u)
         d.out_off = b->off[s];
         const int64_t nb = (c->M + kBatch - 1) / kBatch;
         b->hitem[s + 1] = b->hitem[s] + (b->cfg.precision == TC_FP64 ? nb : (nb + 1) / 2);
+        hnear[s + 1] = hnear[s] + (b->cfg.precision == TC_FP64 ? nb : (nb + kNearGroupBatches - 1) / kNearGroupBatches);
     }
-    const int64_t nitems = b->hitem[b->nsys];
+    const int64_t nitems = b->hitem[b->nsys], nnear = hnear[b->nsys];
     TB_CK(ensure(b->desc, sizeof(SysDesc) * b->nsys), "alloc descriptors");
-    TB_CK(ensure(b->item_off, (size_t)(b->nsys + 1) * 8), "alloc items");
+    TB_CK(ensure(b->item_off, (size_t)(b->nsys + 1) * 16), "alloc items");
     TB_CK(cudaMemcpyAsync(b->desc.p, b->hdesc.data(), sizeof(SysDesc) * b->nsys, cudaMemcpyHostToDevice, st),
           "copy descriptors");
-    TB_CK(cudaMemcpyAsync(b->item_off.p, b->hitem.data(), (size_t)(b->nsys + 1) * 8, cudaMemcpyHostToDevice, st),
+    TB_CK(cudaMemcpyAsync(b->item_off.p, b->hitem.data(), (size_t)(b->nsys + 1) * 16, cudaMemcpyHostToDevice, st),
           "copy items");
     TB_CK(cudaStreamSynchronize(st), "descriptor sync");  // host arrays are reused next call
     // 3. launch shapes
     if (b->autotune && b->tuned_p != p) {
-        tc_status r = tune(b, p, nitems, u);
+        tc_status r = tune(b, p, nitems, nnear, u);
         if (r != TC_OK) return r;
     }
     // 4. compute phase: replay the captured graph, capturing it when stale
-    if (!b->use_graph) return launch_compute(b, b->shape, p, nitems, u, st);
+    if (!b->use_graph) return launch_compute(b, b->shape, p, nitems, nnear, u, st);
     const bool stale = !b->exec || b->graph_u != u || b->graph_p != p || b->graph_items != nitems ||
                        memcmp(&b->graph_shape, &b->shape, sizeof(Shape)) != 0 || !same_desc(b->graph_desc, b->hdesc);
     if (stale) {
         drop_graph(b);
         cudaGraph_t g = nullptr;
         TB_CK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
-        tc_status r = launch_compute(b, b->shape, p, nitems, u, b->cap);
+        tc_status r = launch_compute(b, b->shape, p, nitems, nnear, u, b->cap);
         cudaError_t e = cudaStreamEndCapture(b->cap, &g);
         if (r != TC_OK) {
             if (g) cudaGraphDestroy(g);

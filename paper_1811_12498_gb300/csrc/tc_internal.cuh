@@ -18,6 +18,7 @@ constexpr int kMaxDepth = 21;   // 21-bit quantised coordinates, 63-bit Morton k
 constexpr int kPMax = 12;       // largest Taylor order accepted
 constexpr int kQMax = kPMax + 2;  // far field needs Coulomb coefficients to p+2
 constexpr int kBatch = 32;      // targets per interaction list (one warp)
+constexpr int kNearGroupBatches = 4;  // batches per warp in the mixed-precision near kernels
 constexpr int kStack = 8 * (kMaxDepth + 1);  // traversal stack bound (7 siblings/level + 8)
 
 // number of multi-indices with ||k|| == n, and with ||k|| <= n

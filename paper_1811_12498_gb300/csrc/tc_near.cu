@@ -10,11 +10,12 @@
 // d = (x_hi - y_hi) + (x_lo - y_lo), so d keeps FP32 relative accuracy even
 // for close pairs; pair terms are FP32; each 32-source tile's partial sum
 // is added to an FP64 per-target accumulator.  One warp handles a group of
-// consecutive batches (four in the one-system kernel, two in the batched one)
-// and walks the merge of their near lists (all in tree order, i.e. by the
-// leaf's first source); for each leaf the targets that need it are packed
-// densely into 32-lane streams, and two streams share every staged tile, so
-// every broadcast source value feeds two targets.  The tile holds the sources
+// four consecutive batches (in both the one-system and the batched kernel)
+// and walks the merge of their near lists (all
+// in tree order, i.e. by the leaf's first source); for each leaf the targets
+// that need it are packed densely into 32-lane streams, and two streams share
+// every staged tile, so every broadcast source value feeds two targets.  The
+// tile holds the sources
 // in pairs, field by field ((y_2q.f, y_2q+1.f) adjacent), and the pair terms
 // run on packed FP32x2 arithmetic, two sources per instruction.
 //
@@ -26,7 +27,7 @@ namespace tc {
 namespace {
 
 constexpr int kNearWarps = 4;
-constexpr int kNearGroup = 4;     // batches per warp in the one-system kernel
+constexpr int kNearGroup = kNearGroupBatches;  // batches per warp (mixed precision)
 constexpr int kNearMaxWarps = 8;  // largest block the batched kernel accepts
 
 // ---------------------------------------------------------------------------
@@ -180,15 +181,15 @@ __global__ void __launch_bounds__(kNearWarps * 32)
 }
 
 // Persistent near-field kernel over many systems (see k_far32_batched).  An
-// item is a batch in FP64 mode and a pair of batches in mixed precision
-// (item_off counts accordingly).
+// item is a batch in FP64 mode and a group of four batches in mixed
+// precision (item_off counts accordingly).
 template <bool kFp64>
 __global__ void __launch_bounds__(kNearMaxWarps * 32)
     k_near_batched(const SysDesc* __restrict__ sys, int nsys, const int64_t* __restrict__ item_off, int64_t nitems,
                    unsigned long long* __restrict__ counter)
 {
     constexpr int kTileBytes =
-        12 * 32 * 8 > (int)sizeof(NearScratch<2>) ? 12 * 32 * 8 : (int)sizeof(NearScratch<2>);
+        12 * 32 * 8 > (int)sizeof(NearScratch<kNearGroup>) ? 12 * 32 * 8 : (int)sizeof(NearScratch<kNearGroup>);
     __shared__ __align__(16) double tile[kNearMaxWarps][kTileBytes / 8];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (;;) {
@@ -209,8 +210,9 @@ __global__ void __launch_bounds__(kNearMaxWarps * 32)
         if (kFp64)
             near_batch_fp64(d.ts, d.M, d.topo, d.xs, d.ws, d.N, d.near_off, d.near_list, d.u_near, b, tile[w], lane);
         else
-            nearpair::near_group<2, NearOpU>(d.ts, nullptr, d.M, d.topo, d.spack, d.near_off, d.near_list,
-                                             d.u_near, b, *reinterpret_cast<NearScratch<2>*>(tile[w]), lane);
+            nearpair::near_group<kNearGroup, NearOpU>(d.ts, nullptr, d.M, d.topo, d.spack, d.near_off,
+                                                      d.near_list, d.u_near, b,
+                                                      *reinterpret_cast<NearScratch<kNearGroup>*>(tile[w]), lane);
     }
 }
 
