@@ -140,18 +140,29 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
-def kernel_traffic(source, profile):
+# the files that hold each profiled kernel's code
+NEAR_SOURCES = ("tc_near.cu", "tc_nearpair.cuh")
+FAR_SOURCES = ("tc_far.cu", "tc_recurrence.cuh")
+
+
+def source_sha(sources):
+    """sha256 over the kernel's source files (csrc/), concatenated in order."""
+    hsh = hashlib.sha256()
+    for f in sources:
+        hsh.update(open(os.path.join(ROOT, "paper_1811_12498_gb300", "csrc", f), "rb").read())
+    return hsh.hexdigest()
+
+
+def kernel_traffic(sources, profile):
     """Per-launch DRAM bytes of a kernel from its committed ncu summary, if the
-    summary was taken on the current kernel source (sha256); else None."""
-    src = os.path.join(ROOT, "paper_1811_12498_gb300", "csrc", source)
+    summary was taken on the current kernel sources (source_sha); else None."""
     prof = os.path.join(ROOT, "profiles", profile)
     if not os.path.exists(prof):
         return None
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
     text = open(prof).read()
     m_sha = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
     m_b = re.search(r"dram_bytes_per_full_launch:\s*([0-9.eE+]+)", text)
-    if not m_sha or not m_b or m_sha.group(1) != sha:
+    if not m_sha or not m_b or m_sha.group(1) != source_sha(sources):
         return None
     return float(m_b.group(1))
 
@@ -286,6 +297,56 @@ def bench_sphere_sweep(flush, stream):
         tc.close()
     return {"workload": "Fibonacci sphere N=4000000, nu = outward normal, f, h ~ N(0,1), N0=2000, mixed",
             "E_samples": int(len(eidx)), "points": rows}
+
+
+def bench_table1(flush, stream):
+    """Test case 1 of the paper at its Table 1(b) size: Stokeslets and
+    stresslets at the N = 327680 centroids of a 7-times refined icosahedron
+    on the unit sphere, weights uniform in [-1, 1], shrunk clusters, N0 =
+    2000, theta in {0.2, 0.5, 0.8}, p in {0, 2, ..., 10}, mixed precision:
+    per point the time t of build + moments + eval, E over all targets
+    against the FP64 direct sum, and the speedup d/t over the mixed-precision
+    direct sum on the same GPU (the paper's d/t column is CPU against CPU)."""
+    import numpy as np
+    import torch
+
+    from paper_1811_12498_gb300 import api, inputs
+    x, f, h, nu = inputs.icosahedral_sphere(7, inputs.SEED_BASE + 101)
+    N, N0 = x.shape[0], 2000
+    d = [torch.from_numpy(np.ascontiguousarray(a.T)).cuda() for a in (x, f, h, nu)]
+    ud = api.direct(*d, precision="fp64", stream=stream)
+    u = torch.empty((3, N), dtype=torch.float64, device="cuda")
+    dms = []
+    for k in range(3):
+        flush.fill_(1)
+        e0, e1 = _events(stream)
+        api.direct(*d, precision="mixed", out=u, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        if k > 0:
+            dms.append(e0.elapsed_time(e1))
+    d_ms = statistics.mean(dms)
+    tc = api.Treecode("mixed", True, stream)
+    rows = []
+    for theta in (0.2, 0.5, 0.8):
+        for p in range(0, 11, 2):
+            times = []
+            for k in range(3):
+                flush.fill_(1)
+                e0, e1 = _events(stream)
+                tc.build(d[0], N0).moments(d[1], d[2], d[3], p)
+                tc.eval(theta, p, out=u)
+                e1.record(stream)
+                e1.synchronize()
+                if k > 0:
+                    times.append(e0.elapsed_time(e1))
+            E = float(torch.linalg.norm(u - ud) / torch.linalg.norm(ud))
+            ms = statistics.mean(times)
+            rows.append({"theta": theta, "p": p, "ms": ms, "d_over_t": d_ms / ms, "E": E})
+    tc.close()
+    return {"workload": "icosahedral sphere N=327680 (Table 1(b) size), f, h, nu uniform in [-1,1], N0=2000, "
+                        "shrink, mixed; E over all targets vs FP64 direct (mixed floor ~3e-7)",
+            "direct_mixed_ms": d_ms, "points": rows}
 
 
 def bench_batched(flush, stream, reps=3):
@@ -480,12 +541,12 @@ def main():
     if dominant_near:
         roof = {"bound": "alu", "kernel": near_kernel + " (near field, 43 flops per pair)", "achieved": near_tf,
                 "peak": peak, "unit": "TFLOP/s", "peak_kind": peak_kind, "frac": near_tf / peak,
-                "traffic": None if fp64 else kernel_traffic("tc_near.cu", "near_field_uniform_cube_524k.md"),
+                "traffic": None if fp64 else kernel_traffic(NEAR_SOURCES, "near_field_uniform_cube_524k.md"),
                 "flops_per_launch": near_flops, "launch_ms": near_ms}
     else:
         roof = {"bound": "alu", "kernel": "k_far (far field, folded recurrence + contraction)", "achieved": far_tf,
                 "peak": peak, "unit": "TFLOP/s", "peak_kind": peak_kind, "frac": far_tf / peak,
-                "traffic": None if fp64 else kernel_traffic("tc_far.cu", "far_field_uniform_cube_524k.md"),
+                "traffic": None if fp64 else kernel_traffic(FAR_SOURCES, "far_field_uniform_cube_524k.md"),
                 "flops_per_launch": rec_flops + con_flops, "launch_ms": far_ms}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -550,6 +611,7 @@ def main():
     if not args.no_extras:
         line["fwd_adjoint"] = bench_fwd_adjoint(flush, stream)
         line["batched"] = bench_batched(flush, stream)
+        line["table1_sphere"] = bench_table1(flush, stream)
         if not args.no_sweep:
             line["sphere_sweep"] = bench_sphere_sweep(flush, stream)
     print(json.dumps(line), flush=True)

@@ -224,6 +224,42 @@ tc_status tc_list_stats(tc_ctx* ctx, int64_t* far_entries, int64_t* near_entries
 tc_status tc_eval_counts(tc_ctx* ctx, int64_t* nfar, int64_t* nnear_pairs);
 
 /* ---------------------------------------------------------------------- */
+/* Parameters for a target accuracy.                                      */
+/* ---------------------------------------------------------------------- */
+/*
+ * The fastest (theta, p, N0) of a grid whose error reaches target_E on the
+ * caller's own system.  Section 6 of the paper closes with the remark that
+ * choosing these three for the accuracy wanted would make the method more
+ * efficient, and its Table 1 shows the best theta moving with the accuracy
+ * regime (0.8 for low, 0.5 for medium, 0.2 for high accuracy).
+ *
+ *  x, f, h, nu        : the system, FP64 SoA device arrays of N particles;
+ *                       the targets are the particles themselves
+ *  thetas, n_theta    : candidate MAC parameters, each in (0, 1)   (host)
+ *  orders, n_order    : candidate orders p, each in [0, 12]        (host)
+ *  leaf_sizes, n_leaf : candidate leaf sizes N0 >= 1                (host)
+ *  sample, n_sample   : indices in [0, N) of the particles at which
+ *                       the error is measured, 1 <= n_sample <= N   (host)
+ *  target_E           : the accuracy wanted, > 0
+ *  seconds, errors    : host outputs, one entry per candidate
+ *                       k = (i_leaf * n_order + i_order) * n_theta + i_theta:
+ *                       device time of tc_build + tc_moments + tc_eval (the
+ *                       second of two full runs, CUDA events on the context's
+ *                       stream), and E, the relative L2 error of Section 6
+ *                       over the sample, against the FP64 direct sum
+ *  best               : host output, the candidate of smallest time among
+ *                       those with E <= target_E, or -1 if there is none
+ *
+ * Runs in the context's precision mode; afterwards the context holds the tree,
+ * moments and lists of the last candidate.  Synchronises.  TC_EINVAL for a
+ * NULL pointer, an empty grid or a value out of range, before anything runs.
+ */
+tc_status tc_tune(tc_ctx* ctx, const double* x, const double* f, const double* h, const double* nu, int64_t N,
+                  const double* thetas, int32_t n_theta, const int32_t* orders, int32_t n_order,
+                  const int32_t* leaf_sizes, int32_t n_leaf, const int64_t* sample, int64_t n_sample,
+                  double target_E, double* seconds, double* errors, int32_t* best);
+
+/* ---------------------------------------------------------------------- */
 /* Batches of independent systems.                                        */
 /* ---------------------------------------------------------------------- */
 /*

@@ -26,6 +26,7 @@ SIGNATURES = {
     "tc_stats": (_i32, [_vp, _vp, _vp, _vp]),
     "tc_eval_counts": (_i32, [_vp, _vp, _vp]),
     "tc_list_stats": (_i32, [_vp, _vp, _vp, _vp]),
+    "tc_tune": (_i32, [_vp, _vp, _vp, _vp, _vp, _i64, _vp, _i32, _vp, _i32, _vp, _i32, _vp, _i64, _dbl, _vp, _vp, _vp]),
     "tc_tree_info": (_i32, [_vp, _vp, _vp, _vp, _vp]),
     "tc_tree_export": (_i32, [_vp] + [_vp] * 9),
     "tc_tree_order": (_i32, [_vp, _vp]),

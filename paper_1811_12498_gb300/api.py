@@ -170,6 +170,42 @@ class Treecode:
                     far_lane_use=st["far_interactions"] / max(1, 32 * fe.value),
                     near_lane_use=st["near_pairs"] / max(1, 32 * ns.value))
 
+    def tune(self, x, f, h, nu, thetas, orders, leaf_sizes, sample, target_E):
+        """Fastest (theta, p, N0) of the grid whose error E at the sampled
+        particles reaches target_E (tc_tune).  x, f, h, nu: (3, N) CUDA
+        tensors; thetas, orders, leaf_sizes: sequences; sample: indices in
+        [0, N).  Returns dict(best=(theta, p, N0) or None, table=[(theta, p,
+        N0, seconds, E), ...] in the candidate order of tc_tune)."""
+        import numpy as np
+        x = _vec3(x, "x")
+        N = x.shape[1]
+        f, h, nu = (_vec3(a, n, N) for a, n in ((f, "f"), (h, "h"), (nu, "nu")))
+        th = np.ascontiguousarray(thetas, dtype=np.float64)
+        ps = np.ascontiguousarray(orders, dtype=np.int32)
+        n0 = np.ascontiguousarray(leaf_sizes, dtype=np.int32)
+        smp = np.ascontiguousarray(sample, dtype=np.int64)
+        ncand = th.size * ps.size * n0.size
+        sec = np.zeros(max(ncand, 1), np.float64)
+        err = np.zeros(max(ncand, 1), np.float64)
+        best = ctypes.c_int32(-1)
+        vp = ctypes.c_void_p
+        self._chk(lib().tc_tune(self._h, _ptr(x), _ptr(f), _ptr(h), _ptr(nu), N, vp(th.ctypes.data), th.size,
+                                vp(ps.ctypes.data), ps.size, vp(n0.ctypes.data), n0.size, vp(smp.ctypes.data),
+                                smp.size, float(target_E), vp(sec.ctypes.data), vp(err.ctypes.data),
+                                ctypes.byref(best)))
+        table = []
+        k = 0
+        for nl in n0:
+            for p in ps:
+                for t in th:
+                    table.append((float(t), int(p), int(nl), float(sec[k]), float(err[k])))
+                    k += 1
+        self.N = N
+        self.p = int(ps[-1])
+        self._keep = (f, h, nu)
+        b = best.value
+        return dict(best=None if b < 0 else table[b][:3], table=table)
+
     def eval_counts(self):
         M = self.N if getattr(self, "_M", None) is None else self._M
         nf = torch.empty(M, dtype=torch.int64, device="cuda")

@@ -51,6 +51,9 @@ def test_host_argument_checks_without_gpu(lib):
     assert b"NULL" in lib.tc_last_error(None)
     assert lib.tc_destroy(None) == 0
     assert lib.tc_sync(None) == 1
+    assert lib.tc_tune(None, None, None, None, None, 10, None, 1, None, 1, None, 1, None, 1, 1e-3, None, None,
+                       None) == 1
+    assert b"ctx is NULL" in lib.tc_last_error(None)
 
 
 def test_oracle_and_library_share_no_code():

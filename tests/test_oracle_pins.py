@@ -427,18 +427,29 @@ def test_error_matches_paper_table2_cube():
         assert e / 2 < E[p] < e * 2, (p, E[p], e)
 
 
+def table1_E():
+    """Table 1 of the paper as printed: {(theta, p): (E at N=81920, E at N=327680)}."""
+    rows = np.loadtxt(os.path.join(GOLDEN, "table1_sphere_E.txt"), comments="#")
+    return {(float(r[0]), int(r[1])): (float(r[2]), float(r[3])) for r in rows}
+
+
 @pytest.mark.slow
 def test_error_matches_paper_table1_sphere():
     """Table 1(a): icosahedral sphere N = 81920, Stokeslets + stresslets,
-    clusters shrunk to their boxes, theta = 0.5: E = 1.2e-3 (p=2),
-    2.2e-4 (p=4), 5.2e-5 (p=6), 1.2e-5 (p=8), 2.9e-6 (p=10); agreement
-    within a factor 2 (600 sampled targets)."""
+    clusters shrunk to their boxes, every theta in {0.2, 0.5, 0.8} and p in
+    {0, 2, ..., 10}: E from 4.2e-11 to 2.3e-2.  E is a statistic of random
+    weights (600 sampled targets here), so agreement within a factor 1.5 is
+    required (measured: 0.87 to 1.18)."""
     x, f, h, nu = inputs.icosahedral_sphere(6, inputs.SEED_BASE + 101)
     assert x.shape[0] == 81920
-    paper = {2: 1.2e-3, 4: 2.2e-4, 6: 5.2e-5, 8: 1.2e-5, 10: 2.9e-6}
-    E = _sampled_E(x, f, h, nu, 2000, True, 0.5, list(paper), 600, 8)
-    for p, e in paper.items():
-        assert e / 2 < E[p] < e * 2, (p, E[p], e)
+    paper = table1_E()
+    idx = inputs.sample_indices(x.shape[0], 600, 8)
+    ud = oracle.direct(x, f, h, nu, targets=x[idx])
+    tree = oracle.Tree(x, 2000, True)
+    tree.set_moments(f, h, nu, 10)
+    for (theta, p), (e, _) in paper.items():
+        E = oracle.rel_l2(tree.treecode(x[idx], theta, p), ud)
+        assert e / 1.5 < E < e * 1.5, (theta, p, E, e)
 
 
 def test_frozen_structure_map_reduces_to_treecode_and_direct():
