@@ -527,7 +527,8 @@ tc_status tc::eval_compute(tc_ctx* ctx, double* u)
                      ptr<double>(ctx->node_invrho),
                      ptr<float4>(ctx->geo32), ptr<double>(ctx->abf64), ptr<float>(ctx->abf32), p,
                      ptr<int64_t>(ctx->far_off),
-                     ptr<ListEntry>(ctx->far_list), ptr<double>(ctx->u_far), s2),
+                     ptr<ListEntry>(ctx->far_list), ptr<double>(ctx->u_far),
+                     reinterpret_cast<unsigned*>(ptr<char>(ctx->flags) + 128), s2),
           "far field");
     ph_end(ctx, TC_PH_FAR, s2);
     TC_CK(cudaEventRecord(ctx->ev_join, s2), "join");

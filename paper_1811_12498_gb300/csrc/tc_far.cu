@@ -32,7 +32,10 @@
 //    per lane) and walks the merge of their far lists, so every table value
 //    the warp loads serves both targets of a lane wherever the lists share a
 //    cluster: the broadcast table loads, not the arithmetic, bound this
-//    kernel (4 B of L1 bandwidth per FMA at one target per lane).  The
+//    kernel (4 B of L1 bandwidth per FMA at one target per lane).  The grid
+//    is resident (one single-warp block per free slot) and its warps take
+//    batch pairs from a work queue, so a warp whose pairs have short lists
+//    takes more instead of idling while the last blocks run.  The
 //    contraction runs on packed FP32x2 FMAs over pairs of table columns,
 //    which halves the instructions of the fully unrolled body (its size, not
 //    only its arithmetic, limits the kernel: instruction fetch stalls).  d' is
@@ -405,16 +408,30 @@ __global__ void __launch_bounds__(32)
 }
 
 template <int P>
+__device__ __noinline__ void far_pair32_at(const double* ts, int64_t M, const int4* topo, const float4* geo32,
+                                           const float* ab, const int64_t* far_off, const ListEntry* far_list,
+                                           double* u_far, int64_t B, int lane)
+{
+    far_pair32<P>(ts, M, topo, geo32, ab, far_off, far_list, u_far, B, lane);
+}
+
+// One resident grid of single-warp blocks taking batch pairs from a work
+// queue (queue: a counter zeroed before the launch) until none is left.
+template <int P>
 __global__ void __launch_bounds__(32)
     k_far32(const double* __restrict__ ts, int64_t M, const int4* __restrict__ topo,
             const float4* __restrict__ geo32, const float* __restrict__ ab, const int64_t* __restrict__ far_off,
-            const ListEntry* __restrict__ far_list, double* __restrict__ u_far)
+            const ListEntry* __restrict__ far_list, double* __restrict__ u_far, unsigned* __restrict__ queue)
 {
     const int lane = threadIdx.x & 31;
     const int64_t nsuper = ((M + kBatch - 1) / kBatch + 1) / 2;
-    const int64_t B = blockIdx.x;
-    if (B >= nsuper) return;
-    far_pair32<P>(ts, M, topo, geo32, ab, far_off, far_list, u_far, B, lane);
+    for (;;) {
+        unsigned B = 0;
+        if (lane == 0) B = atomicAdd(queue, 1u);
+        B = __shfl_sync(0xffffffffu, B, 0);
+        if ((int64_t)B >= nsuper) break;
+        far_pair32_at<P>(ts, M, topo, geo32, ab, far_off, far_list, u_far, (int64_t)B, lane);
+    }
 }
 
 // Persistent far-field kernels over many systems: every warp repeatedly takes
@@ -517,10 +534,17 @@ cudaError_t persistent_grid(K kernel, int warps_per_block, size_t smem, int& blo
 
 template <int P>
 cudaError_t run_far32(const double* ts, int64_t M, const int4* topo, const float4* geo32, const float* ab,
-                      const int64_t* far_off, const ListEntry* far_list, double* u_far, cudaStream_t s)
+                      const int64_t* far_off, const ListEntry* far_list, double* u_far, unsigned* queue,
+                      cudaStream_t s)
 {
     const int64_t nsuper = ((M + kBatch - 1) / kBatch + 1) / 2;
-    k_far32<P><<<(unsigned)nsuper, 32, 0, s>>>(ts, M, topo, geo32, ab, far_off, far_list, u_far);
+    int blocks = 0;
+    cudaError_t e = persistent_grid(k_far32<P>, 1, 0, blocks);
+    if (e != cudaSuccess) return e;
+    if ((int64_t)blocks > nsuper) blocks = (int)nsuper;
+    e = cudaMemsetAsync(queue, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    k_far32<P><<<(unsigned)blocks, 32, 0, s>>>(ts, M, topo, geo32, ab, far_off, far_list, u_far, queue);
     note_launch();
     return cudaGetLastError();
 }
@@ -568,14 +592,15 @@ cudaError_t run_far64_batched(const SysDesc* sys, int nsys, const int64_t* item_
 
 cudaError_t launch_far(int precision, int rec64, const double* ts, int64_t M, const int4* topo, const Geo* geo,
                        const double* invrho, const float4* geo32, const double* ab64, const float* ab32, int p,
-                       const int64_t* far_off, const ListEntry* far_list, double* u_far, cudaStream_t s)
+                       const int64_t* far_off, const ListEntry* far_list, double* u_far, unsigned* queue,
+                       cudaStream_t s)
 {
     if (M <= 0) return cudaSuccess;
     if (precision == TC_FP64) return run_far64<double>(ts, M, geo, invrho, ab64, p, far_off, far_list, u_far, s);
     if (rec64 && p >= 8) return run_far64<float>(ts, M, geo, invrho, ab32, p, far_off, far_list, u_far, s);
     switch (p + 2) {
 #define TC_FAR32_CASE(P) \
-    case P: return run_far32<P>(ts, M, topo, geo32, ab32, far_off, far_list, u_far, s);
+    case P: return run_far32<P>(ts, M, topo, geo32, ab32, far_off, far_list, u_far, queue, s);
         TC_FAR32_CASE(2) TC_FAR32_CASE(3) TC_FAR32_CASE(4) TC_FAR32_CASE(5) TC_FAR32_CASE(6)
         TC_FAR32_CASE(7) TC_FAR32_CASE(8) TC_FAR32_CASE(9) TC_FAR32_CASE(10) TC_FAR32_CASE(11)
         TC_FAR32_CASE(12) TC_FAR32_CASE(13) TC_FAR32_CASE(14)

@@ -139,7 +139,7 @@ struct tc_ctx {
     tc::DevBuf far_list, near_list;     // ListEntry
     tc::DevBuf cnt_far, cnt_near;       // per sorted target counts (int64)
     tc::DevBuf u_far, u_near;           // 3*M FP64 sorted order
-    tc::DevBuf flags;                   // int32 device error flags
+    tc::DevBuf flags;                   // int32 device error flags at byte 0; far-field work-queue counter at byte 128
     int64_t far_entries = 0, near_entries = 0;  // list sizes of the last tc_eval
     int p_eval = -1;                            // order of the last tc_eval
     int prepared = 0;                           // lists ready for the far/near kernels
@@ -258,7 +258,8 @@ cudaError_t launch_sum_entry_sizes(const ListEntry* list, int64_t n, const int4*
 cudaError_t launch_far(int precision, int rec64, const double* ts, int64_t M, const int4* topo, const Geo* geo,
                        const double* invrho, const float4* geo32, const double* ab64, const float* ab32, int p,
                        const int64_t* far_off,
-                       const ListEntry* far_list, double* u_far, cudaStream_t s);
+                       const ListEntry* far_list, double* u_far, unsigned* queue,
+                       cudaStream_t s);
 
 cudaError_t launch_far_batched(int precision, int rec64, const SysDesc* sys, int nsys, const int64_t* item_off, int64_t nitems,
                                int p, unsigned long long* counter, int warps_per_block, int blocks, cudaStream_t s);
