@@ -39,6 +39,8 @@
 // their batch order).  The cluster-major far kernel accumulates per warp in
 // shared memory and flushes with FP64 atomics when the cluster changes, so
 // the source-side far gradient is reproducible only up to FP64 rounding.
+#include <algorithm>
+
 #include "tc_nearpair.cuh"
 #include "tc_recurrence.cuh"
 
@@ -703,17 +705,17 @@ __global__ void __launch_bounds__(32)
 // so the recurrence runs to level P + 1.  k + e_1 leaves the subset when
 // k1 = 1; Laplace's identity on level n+1 gives
 //   c^{(2,a,b)} = -[(a+2)(a+1) c^{(0,a+2,b)} + (b+2)(b+1) c^{(0,a,b+2)}] / 2.
-// One warp per batch, one target per lane, three levels in registers.
+// One warp per batch, one target per lane, three levels in registers; the
+// grid is resident and its warps take batches from a work queue (queue: a
+// counter zeroed before the launch), as in the forward far field.
 template <int P>
-__global__ void __launch_bounds__(32)
-    k_far_adj_target32(const double* __restrict__ ts, const double* __restrict__ gs, int64_t M,
-                       const float4* __restrict__ geo32, const float* __restrict__ ab,
-                       const int64_t* __restrict__ far_off, const ListEntry* __restrict__ far_list,
-                       double* __restrict__ gt)
+__device__ __noinline__ void far_adj_target32_batch(const double* __restrict__ ts, const double* __restrict__ gs,
+                                                    int64_t M, const float4* __restrict__ geo32,
+                                                    const float* __restrict__ ab, const int64_t* __restrict__ far_off,
+                                                    const ListEntry* __restrict__ far_list, double* __restrict__ gt,
+                                                    int64_t b, int lane)
 {
     constexpr int H = (P + 1) * (P + 1);
-    const int lane = threadIdx.x & 31;
-    const int64_t b = blockIdx.x;
     const int64_t m = b * kBatch + lane;
     const bool valid = m < M;
     float xh[3] = {0, 0, 0}, xl[3] = {0, 0, 0}, g[3] = {0, 0, 0};
@@ -800,6 +802,24 @@ __global__ void __launch_bounds__(32)
         gt[m] = G0;
         gt[M + m] = G1;
         gt[2 * M + m] = G2;
+    }
+}
+
+template <int P>
+__global__ void __launch_bounds__(32)
+    k_far_adj_target32(const double* __restrict__ ts, const double* __restrict__ gs, int64_t M,
+                       const float4* __restrict__ geo32, const float* __restrict__ ab,
+                       const int64_t* __restrict__ far_off, const ListEntry* __restrict__ far_list,
+                       double* __restrict__ gt, unsigned* __restrict__ queue)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nbatch = (M + kBatch - 1) / kBatch;
+    for (;;) {
+        unsigned b = 0;
+        if (lane == 0) b = atomicAdd(queue, 1u);
+        b = __shfl_sync(0xffffffffu, b, 0);
+        if ((int64_t)b >= nbatch) break;
+        far_adj_target32_batch<P>(ts, gs, M, geo32, ab, far_off, far_list, gt, (int64_t)b, lane);
     }
 }
 
@@ -1224,11 +1244,21 @@ cudaError_t run_far_adj32(tc_ctx* ctx, const double* ts, int64_t M, cudaStream_t
     const int64_t nbatch = (M + kBatch - 1) / kBatch;
     const int64_t nnodes = ctx->nnodes;
     const int H = hsize(P);
-    k_far_adj_target32<P><<<(unsigned)nbatch, 32, 0, s>>>(ts, ptr<double>(ctx->adj_gs), M, ptr<float4>(ctx->geo32),
-                                                          ptr<float>(ctx->abf32), ptr<int64_t>(ctx->far_off),
-                                                          ptr<ListEntry>(ctx->far_list), ptr<double>(ctx->adj_gt));
+    int per_sm = 0, sms = 0, dev = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_far_adj_target32<P>, 32, 0);
+    if (e != cudaSuccess) return e;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t grid = std::min<int64_t>(nbatch, (int64_t)std::max(per_sm, 1) * sms);
+    unsigned* queue = reinterpret_cast<unsigned*>(ptr<char>(ctx->flags) + 192);
+    e = cudaMemsetAsync(queue, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    k_far_adj_target32<P><<<(unsigned)grid, 32, 0, s>>>(ts, ptr<double>(ctx->adj_gs), M, ptr<float4>(ctx->geo32),
+                                                        ptr<float>(ctx->abf32), ptr<int64_t>(ctx->far_off),
+                                                        ptr<ListEntry>(ctx->far_list), ptr<double>(ctx->adj_gt),
+                                                        queue);
     note_launch();
-    cudaError_t e = ensure(ctx->adj_fbar, (size_t)nnodes * H * 12 * 8);
+    e = ensure(ctx->adj_fbar, (size_t)nnodes * H * 12 * 8);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(ctx->adj_fbar.p, 0, (size_t)nnodes * H * 12 * 8, s);
     if (e != cudaSuccess) return e;

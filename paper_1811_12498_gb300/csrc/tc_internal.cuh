@@ -139,7 +139,8 @@ struct tc_ctx {
     tc::DevBuf far_list, near_list;     // ListEntry
     tc::DevBuf cnt_far, cnt_near;       // per sorted target counts (int64)
     tc::DevBuf u_far, u_near;           // 3*M FP64 sorted order
-    tc::DevBuf flags;                   // int32 device error flags at byte 0; far-field work-queue counter at byte 128
+    tc::DevBuf flags;                   // int32 device error flags at byte 0; work-queue counters
+                                        // of the far field (byte 128) and its adjoint's target side (192)
     int64_t far_entries = 0, near_entries = 0;  // list sizes of the last tc_eval
     int p_eval = -1;                            // order of the last tc_eval
     int prepared = 0;                           // lists ready for the far/near kernels
