@@ -85,6 +85,23 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(value, dist, device):
+    """The largest of every rank's value (the slowest rank's time); dist is
+    torch.distributed or None for one process."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(n_per_rank, world, ms):
+    """Targets per second of the whole job: every rank evaluates its own
+    n_per_rank-particle replica in the slowest rank's time ms."""
+    return n_per_rank * world / (ms / 1e3)
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -459,12 +476,8 @@ def main():
     barrier()
     clk = clocks.stop()
     launches = api.kernel_launches() - launches0
-    ms = statistics.mean(times)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = N * world / (ms / 1e3)
+    ms = max_over_ranks(statistics.mean(times), dist, "cuda")
+    value = whole_job_value(N, world, ms)
     st = tc.stats()
     ls = tc.list_stats()
     ph_overlap = {k: statistics.mean(pp[k] for pp in phases if pp[k] is not None)
@@ -497,11 +510,7 @@ def main():
         e1.synchronize()
         if k > 0:
             e2e_times.append(e0.elapsed_time(e1))
-    e2e_ms = statistics.mean(e2e_times)
-    if dist is not None:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(statistics.mean(e2e_times), dist, "cuda")
 
     if rank != 0:
         tc.close()
