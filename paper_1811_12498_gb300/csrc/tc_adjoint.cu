@@ -411,9 +411,10 @@ __global__ void __launch_bounds__(kNearAdjWarps * 32)
             const float2 f0 = make_float2(A.w, A.w), f1 = make_float2(B.w, B.w), f2 = make_float2(C.x, C.x);
             const float2 h0 = make_float2(C.y, C.y), h1 = make_float2(C.z, C.z), h2 = make_float2(C.w, C.w);
             const float2 n0 = make_float2(D.x, D.x), n1 = make_float2(D.y, D.y), n2 = make_float2(D.z, D.z);
-            double acc[12];
+            // per-entry partial sums, accumulated by compensated FP32 summation
+            float acc[12], cmp[12];
 #pragma unroll
-            for (int c = 0; c < 12; c++) acc[c] = 0.0;
+            for (int c = 0; c < 12; c++) acc[c] = cmp[c] = 0.f;
             for (int64_t j = js; j < je; j++) {
                 const int32_t e = sidx[j];
                 const unsigned mask = near_list[e].mask;
@@ -482,10 +483,10 @@ __global__ void __launch_bounds__(kNearAdjWarps * 32)
                                                         __ffma2_rn(h2, c4, __fmul2_rn(n2, c5))))));
                 }
 #pragma unroll
-                for (int c = 0; c < 12; c++) acc[c] += (double)(a[c].x + a[c].y);
+                for (int c = 0; c < 12; c++) kahan_add(acc[c], cmp[c], a[c].x + a[c].y);
             }
             if (valid)
-                for (int c = 0; c < 12; c++) atomicAdd(&gnear[c * N + si], acc[c]);
+                for (int c = 0; c < 12; c++) atomicAdd(&gnear[c * N + si], (double)acc[c] - (double)cmp[c]);
         }
         js = je;
     }
@@ -726,7 +727,8 @@ __device__ __noinline__ void far_adj_target32_batch(const double* __restrict__ t
             xl[a] = __double2float_rn(v - (double)xh[a]);
             g[a] = __double2float_rn(gs[a * M + m]);
         }
-    double G0 = 0, G1 = 0, G2 = 0;
+    // per-entry contributions summed by compensated FP32 summation
+    float G[3] = {0.f, 0.f, 0.f}, K[3] = {0.f, 0.f, 0.f};
     for (int64_t e = far_off[b]; e < far_off[b + 1]; e++) {
         const ListEntry le = far_list[e];
         const bool in = (le.mask >> lane) & 1u;
@@ -793,15 +795,15 @@ __device__ __noinline__ void far_adj_target32_batch(const double* __restrict__ t
         }
         if (in) {
             const float s = iR * gh.w;  // 1/R' and d'/dx = 1/rho
-            G0 += (double)(a0 * s);
-            G1 += (double)(a1 * s);
-            G2 += (double)(a2 * s);
+            kahan_add(G[0], K[0], a0 * s);
+            kahan_add(G[1], K[1], a1 * s);
+            kahan_add(G[2], K[2], a2 * s);
         }
     }
     if (valid) {
-        gt[m] = G0;
-        gt[M + m] = G1;
-        gt[2 * M + m] = G2;
+        gt[m] = (double)G[0] - (double)K[0];
+        gt[M + m] = (double)G[1] - (double)K[1];
+        gt[2 * M + m] = (double)G[2] - (double)K[2];
     }
 }
 

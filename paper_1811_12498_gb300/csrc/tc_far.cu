@@ -42,10 +42,12 @@
 //    formed from FP32 hi/lo splits of the target and the cluster centre
 //    (x_hi - y_hi is computed with one rounding, so d' carries FP32 relative
 //    accuracy however close x and y_c are in absolute terms), with no FP64
-//    operation per entry except the FP64 accumulation of the three velocity
-//    components.  On the folded tables an FP32 recurrence is as accurate as
-//    an FP64 one (at p = 6, 8, 10 on a uniform cube the mixed result differs
-//    from FP64 by the same 1.8e-7, set by the FP32 near field).
+//    operation per entry: the per-entry velocities are summed by compensated
+//    (Kahan) FP32 summation, widened to FP64 once per target (an FP64
+//    accumulation stalled every entry's end on the slow FP64 pipe).  On the
+//    folded tables an FP32 recurrence is as accurate as an FP64 one (at
+//    p = 6, 8, 10 on a uniform cube the mixed result differs from FP64 by the
+//    same 1.8e-7, set by the FP32 near field).
 //  * FP64, any order at run time, one batch per warp: the coefficients live
 //    in a per-warp shared memory store of two slots laid out
 //    [slot][position][lane] (no bank conflicts); level n overwrites level n-2
@@ -316,7 +318,8 @@ __device__ __forceinline__ void far_pair32(const double* __restrict__ ts, int64_
     const int64_t ma = ba * kBatch + lane, mb = bb * kBatch + lane;
     const bool va = ma < M, vb = mb < M;
     const Tgt32 ta = load_tgt32(ts, M, ma, va), tb = load_tgt32(ts, M, mb, vb);
-    double ua0 = 0, ua1 = 0, ua2 = 0, ub0 = 0, ub1 = 0, ub2 = 0;
+    // per-entry contributions summed by compensated FP32 summation
+    float sa[3] = {0.f, 0.f, 0.f}, ka[3] = {0.f, 0.f, 0.f}, sb[3] = {0.f, 0.f, 0.f}, kb[3] = {0.f, 0.f, 0.f};
     int64_t ia = far_off[ba], ea = far_off[ba + 1], ib = 0, eb = 0;
     if (bb < nbatch) {
         ib = far_off[bb];
@@ -357,14 +360,14 @@ __device__ __forceinline__ void far_pair32(const double* __restrict__ ts, int64_
             float r[2][3];
             far_entry32<P, 2>(tg, in, gh, gl, tab, r);
             if (inA) {
-                ua0 += (double)r[0][0];
-                ua1 += (double)r[0][1];
-                ua2 += (double)r[0][2];
+                kahan_add(sa[0], ka[0], r[0][0]);
+                kahan_add(sa[1], ka[1], r[0][1]);
+                kahan_add(sa[2], ka[2], r[0][2]);
             }
             if (inB) {
-                ub0 += (double)r[1][0];
-                ub1 += (double)r[1][1];
-                ub2 += (double)r[1][2];
+                kahan_add(sb[0], kb[0], r[1][0]);
+                kahan_add(sb[1], kb[1], r[1][1]);
+                kahan_add(sb[2], kb[2], r[1][2]);
             }
         }
         if (takeA && ++ia < ea) {
@@ -377,14 +380,14 @@ __device__ __forceinline__ void far_pair32(const double* __restrict__ ts, int64_
         }
     }
     if (va) {
-        u_far[ma] = ua0;
-        u_far[M + ma] = ua1;
-        u_far[2 * M + ma] = ua2;
+        u_far[ma] = (double)sa[0] - (double)ka[0];
+        u_far[M + ma] = (double)sa[1] - (double)ka[1];
+        u_far[2 * M + ma] = (double)sa[2] - (double)ka[2];
     }
     if (vb) {
-        u_far[mb] = ub0;
-        u_far[M + mb] = ub1;
-        u_far[2 * M + mb] = ub2;
+        u_far[mb] = (double)sb[0] - (double)kb[0];
+        u_far[M + mb] = (double)sb[1] - (double)kb[1];
+        u_far[2 * M + mb] = (double)sb[2] - (double)kb[2];
     }
 }
 

@@ -34,6 +34,18 @@ __host__ __device__ inline int flat_index(int k1, int k2, int k3)
     return (n > 0 ? ncoef(n - 1) : 0) + a * (a + 1) / 2 + k3;
 }
 
+// Compensated (Kahan) FP32 summation: s accumulates, c carries the rounding
+// error of the last addition (s - c is the better estimate of the sum).
+// Written out so that no reassociation can cancel the compensation (the
+// library is built without fast-math).
+__device__ __forceinline__ void kahan_add(float& s, float& c, float b)
+{
+    const float y = b - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
 // Error flags raised by kernels (bit mask in device memory).
 enum DevFlag : int {
     kFlagStack = 1,     // traversal stack bound exceeded

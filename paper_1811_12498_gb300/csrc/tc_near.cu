@@ -8,14 +8,15 @@
 //
 // Mixed precision: positions are split as x = hi + lo (both FP32) and
 // d = (x_hi - y_hi) + (x_lo - y_lo), so d keeps FP32 relative accuracy even
-// for close pairs; pair terms are FP32; each 32-source tile's partial sum
-// is added to an FP64 per-target accumulator.  One warp handles a group of
-// four consecutive batches (in both the one-system and the batched kernel)
-// and walks the merge of their near lists (all
-// in tree order, i.e. by the leaf's first source); for each leaf the targets
-// that need it are packed densely into 32-lane streams, and two streams share
-// every staged tile, so every broadcast source value feeds two targets.  The
-// tile holds the sources
+// for close pairs; pair terms are FP32; the 32-source tiles' partial sums of
+// a leaf are accumulated by compensated (Kahan) FP32 summation and each
+// leaf's sum is added to an FP64 per-target accumulator (an FP64 addition per
+// tile stalled every tile's end on the slow FP64 pipe).  One warp handles a
+// group of four consecutive batches (in both the one-system and the batched
+// kernel) and walks the merge of their near lists (all in tree order, i.e. by
+// the leaf's first source); for each leaf the targets that need it are packed
+// densely into 32-lane streams, and two streams share every staged tile, so
+// every broadcast source value feeds two targets.  The tile holds the sources
 // in pairs, field by field ((y_2q.f, y_2q+1.f) adjacent), and the pair terms
 // run on packed FP32x2 arithmetic, two sources per instruction.
 //

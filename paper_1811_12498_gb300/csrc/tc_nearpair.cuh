@@ -146,7 +146,10 @@ __device__ inline void near_group(const double* __restrict__ ts, const double* _
             const int id1 = v1 ? sc.slot[k1] : 0, id2 = v2 ? sc.slot[k2] : 0;
             const typename Op::Tgt ta = Op::load(ts, gs, M, (b0 + (id1 >> 5)) * kBatch + (id1 & 31), v1);
             const typename Op::Tgt tb = Op::load(ts, gs, M, (b0 + (id2 >> 5)) * kBatch + (id2 & 31), v2);
-            double a0 = 0, a1 = 0, a2 = 0, c0 = 0, c1 = 0, c2 = 0;
+            // per-tile partial sums, accumulated over the leaf's tiles by
+            // compensated FP32 summation (sum, compensation per component)
+            float sa[3] = {0.f, 0.f, 0.f}, ka[3] = {0.f, 0.f, 0.f}, sb[3] = {0.f, 0.f, 0.f},
+                  kb[3] = {0.f, 0.f, 0.f};
             for (int base = t.x; base < t.x + t.y; base += 32) {
                 const int cnt = min(32, t.x + t.y - base);
                 __syncwarp();
@@ -163,13 +166,16 @@ __device__ inline void near_group(const double* __restrict__ ts, const double* _
                 } else {
                     for (int q = 0; q < npairs; q++) Op::terms(ta, sc.tile + q * kPairStride, axa, aya, aza);
                 }
-                a0 += (double)(axa.x + axa.y);
-                a1 += (double)(aya.x + aya.y);
-                a2 += (double)(aza.x + aza.y);
-                c0 += (double)(axb.x + axb.y);
-                c1 += (double)(ayb.x + ayb.y);
-                c2 += (double)(azb.x + azb.y);
+                kahan_add(sa[0], ka[0], axa.x + axa.y);
+                kahan_add(sa[1], ka[1], aya.x + aya.y);
+                kahan_add(sa[2], ka[2], aza.x + aza.y);
+                kahan_add(sb[0], kb[0], axb.x + axb.y);
+                kahan_add(sb[1], kb[1], ayb.x + ayb.y);
+                kahan_add(sb[2], kb[2], azb.x + azb.y);
             }
+            const double a0 = (double)sa[0] - (double)ka[0], a1 = (double)sa[1] - (double)ka[1],
+                         a2 = (double)sa[2] - (double)ka[2], c0 = (double)sb[0] - (double)kb[0],
+                         c1 = (double)sb[1] - (double)kb[1], c2 = (double)sb[2] - (double)kb[2];
             // each (batch, lane) target holds one slot per leaf: no two lanes
             // add to the same accumulator here
             if (v1) {
