@@ -580,7 +580,14 @@ def main():
                       "far_tflops_unfolded_count": unfolded_far_flops * n_far / (far_ms / 1e3) / 1e12,
                       "far_flops_per_interaction_unfolded": unfolded_far_flops,
                       "near_plus_far_frac_unfolded_count":
-                          (near_flops + unfolded_far_flops * n_far) / ((near_ms + far_ms) / 1e3) / 1e12 / peak},
+                          (near_flops + unfolded_far_flops * n_far) / ((near_ms + far_ms) / 1e3) / 1e12 / peak,
+                      # the whole timed step against the FP32 peak, counting the work per target as
+                      # 43 flops per near pair plus the unfolded FP32 contraction (24 C(p+5,3) + 18)
+                      # per far interaction, without and with the unfolded recurrence (11 C(p+5,3))
+                      "step_frac_fp32_count":
+                          (near_flops + (24 * ncoef(p + 2) + 18) * n_far) / (ms / 1e3) / 1e12 / peak,
+                      "step_frac_fp32_count_with_recurrence":
+                          (near_flops + unfolded_far_flops * n_far) / (ms / 1e3) / 1e12 / peak},
         "accuracy": {"E_vs_fp64_direct": E, "E_samples": int(len(eidx))},
     }
     if not args.no_fp64_compare and args.precision == "mixed":
