@@ -55,10 +55,11 @@ typedef enum {
     /* every stage in FP64 */
     TC_FP64 = 0,
     /* near field, far-field Coulomb-coefficient recurrence and contraction
-     * in FP32 (positions split into FP32 hi + lo parts, per-tile and
-     * per-cluster partial sums carried in FP64); cluster moments and
-     * contraction tables always built in FP64.  With tc_config.rec64 the
-     * recurrence runs in FP64 for p >= 8. */
+     * in FP32 (positions split into FP32 hi + lo parts; the FP32 partial
+     * sums per source tile and per cluster accumulated by compensated FP32
+     * summation and widened to FP64 per leaf and per target); cluster
+     * moments and contraction tables always built in FP64.  With
+     * tc_config.rec64 the recurrence runs in FP64 for p >= 8. */
     TC_MIXED = 1
 } tc_precision;
 
