@@ -88,3 +88,35 @@ def test_batch_rejects_bad_offsets():
     with pytest.raises(api.TCError):
         b.build(x, [0, 5, 5, 10], 4)  # empty system
     b.close()
+
+
+def test_full_size_64_systems_batched_equals_separate_and_oracle():
+    """The 64-system workload at full size (sizes log-uniform in [1e4, 5e5];
+    even systems uniform cubes, odd ones Fibonacci spheres; p = 6, theta = 0.6,
+    N0 = 2000; persistent kernels replayed from a CUDA graph with autotuned
+    shapes, as the benchmark times it): equal bit for bit to 64 separate
+    calls, and equal to the oracle on sampled targets of four systems."""
+    sizes = inputs.batch_sizes(64, inputs.SEED_BASE + 5)
+    parts = []
+    for k, n in enumerate(sizes):
+        gen = inputs.uniform_cube if k % 2 == 0 else inputs.fibonacci_sphere
+        parts.append(gen(int(n), inputs.SEED_BASE + 500 + k))
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    seg = [_seg([pp[c] for pp in parts]) for c in range(4)]
+    N0, p, theta = 2000, 6, 0.6
+    b = api.Batch("mixed", True).build(seg[0], off, N0).moments(seg[1], seg[2], seg[3], p)
+    u = b.eval(theta, p)
+    u = b.eval(theta, p, out=u)  # the replayed graph
+    sep = b.eval_separate(theta, p)
+    torch.cuda.synchronize()
+    uh = u.cpu().numpy()
+    for s in range(len(sizes)):
+        np.testing.assert_array_equal(uh[:, off[s]:off[s + 1]], sep[s].cpu().numpy())
+    for s in (0, 1, int(np.argmax(sizes)), int(np.argmin(sizes))):
+        x, f, h, nu = parts[s]
+        idx = inputs.sample_indices(x.shape[0], 16, 300 + s)
+        tree = oracle.Tree(x, N0, True)
+        tree.set_moments(f, h, nu, p)
+        ref = tree.treecode(x[idx], theta, p)
+        assert oracle.rel_l2(uh[:, off[s]:off[s + 1]].T[idx], ref) <= 1e-6, s
+    b.close()

@@ -330,3 +330,47 @@ def test_full_size_sampled_targets(million, prec):
     assert oracle.rel_l2(u[idx], ref) <= TOL[prec]
     # every target's far clusters and near leaves partition the sources
     assert st["near_pairs"] > 0 and st["far_interactions"] > 0
+
+
+@pytest.fixture(scope="module")
+def sphere4m():
+    x, f, h, nu = inputs.fibonacci_sphere(4_000_000, inputs.SEED_BASE + 3)
+    idx = inputs.sample_indices(x.shape[0], 24, 98)
+    tree = oracle.Tree(x, 2000, True)
+    tree.set_moments(f, h, nu, 10)
+    return x, f, h, nu, idx, tree
+
+
+# Mixed precision on a surface with nu = its normal: for y, x on the unit
+# sphere, d.nu_y = (x - y).y = -|d|^2 / 2, a sum of three O(|d|) products
+# that cancels to O(|d|^2), so FP32 resolves the stresslet factor d.nu only to
+# about eps32 / |d| relative (eps32 / r_nn = 3e-5 at the nearest-neighbour
+# distance r_nn = 1.8e-3 of 4M points).  Weighted over all pairs this gives
+# 1.6e-6 rel-L2, for the treecode and for the plain mixed direct sum alike,
+# at every p and theta; the bound below is that with a factor 3 of margin.
+TOL_MIXED_SURFACE = 5e-6
+
+
+@pytest.mark.parametrize("rec64", [False, True])
+def test_full_size_sphere_sweep_sampled(sphere4m, rec64):
+    """4M quasi-uniform points on the unit sphere (nu = outward normal, f, h
+    ~ N(0, 1)), N0 = 2000, p in {4, 6, 8, 10} x theta in {0.5, 0.7}, mixed
+    precision with the FP32 recurrence (and the FP64 one for p >= 8), built
+    and evaluated as the accuracy-against-time sweep runs it: sampled outputs
+    and their interaction counts against the oracle, one by one (tolerance:
+    TOL_MIXED_SURFACE, from the FP32 cancellation of d.nu above)."""
+    x, f, h, nu, idx, tree = sphere4m
+    tc = api.Treecode("mixed", True, rec64=rec64)
+    for p in (4, 6, 8, 10):
+        if rec64 and p < 8:
+            continue
+        tc.build(dev(x), 2000).moments(dev(f), dev(h), dev(nu), p)
+        for theta in (0.5, 0.7):
+            u = host(tc.eval(theta, p))
+            nf, nn = tc.eval_counts()
+            ref, cnt = tree.treecode(x[idx], theta, p, counts=True)
+            np.testing.assert_array_equal(nf.cpu().numpy()[idx], cnt["far"])
+            np.testing.assert_array_equal(nn.cpu().numpy()[idx], cnt["near_pairs"])
+            err = oracle.rel_l2(u[idx], ref)
+            assert err <= TOL_MIXED_SURFACE, (p, theta, err)
+    tc.close()
