@@ -304,6 +304,8 @@ struct NearOpG {
         float2 h0, h1, h2, l0, l1, l2, g0, g1, g2;
     };
     static constexpr bool kAdd = true;
+    // the guard-free variant measured slower here (more registers)
+    static constexpr bool kUnguarded = false;
     __device__ static Tgt load(const double* ts, const double* gs, int64_t M, int64_t m, bool valid)
     {
         float h[3] = {0, 0, 0}, l[3] = {0, 0, 0}, g[3] = {0, 0, 0};
@@ -321,6 +323,7 @@ struct NearOpG {
         return t;
     }
     // d(g.K)/dd_a = d_a c1 + g_a st + f_a c3 + h_a c4 + nu_a c5 for two sources
+    template <bool kGuard>
     __device__ static void terms(const Tgt& t, const float4* tp, float2& ax, float2& ay, float2& az)
     {
         using nearpair::sub2;
@@ -330,8 +333,13 @@ struct NearOpG {
         const float2 dz = __fadd2_rn(sub2(t.h2, make_float2(B.x, B.y)), sub2(t.l2, make_float2(D.x, D.y)));
         const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
         float2 ri;
-        ri.x = r2.x > 0.f ? rsqrtf(r2.x) : 0.f;
-        ri.y = r2.y > 0.f ? rsqrtf(r2.y) : 0.f;
+        if (kGuard) {
+            ri.x = r2.x > 0.f ? rsqrtf(r2.x) : 0.f;
+            ri.y = r2.y > 0.f ? rsqrtf(r2.y) : 0.f;
+        } else {
+            ri.x = rsqrtf(r2.x);
+            ri.y = rsqrtf(r2.y);
+        }
         const float2 ri2 = __fmul2_rn(ri, ri), ri3 = __fmul2_rn(ri2, ri), ri5 = __fmul2_rn(ri3, ri2);
         const float2 f0 = make_float2(B.z, B.w), f1 = make_float2(D.z, D.w), f2 = make_float2(E.x, E.y);
         const float2 h0 = make_float2(E.z, E.w), h1 = make_float2(F.x, F.y), h2 = make_float2(F.z, F.w);
@@ -360,14 +368,15 @@ __global__ void __launch_bounds__(kNearAdjWarps * 32)
     k_near_adj_target32(const double* __restrict__ ts, const double* __restrict__ gs, int64_t M,
                         const int4* __restrict__ topo, const float4* __restrict__ spack,
                         const int64_t* __restrict__ near_off, const ListEntry* __restrict__ near_list,
-                        double* __restrict__ gt)
+                        double* __restrict__ gt, int self)
 {
     __shared__ nearpair::NearScratch<kNearAdjGroup> sc[kNearAdjWarps];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t ngroup = ((M + kBatch - 1) / kBatch + kNearAdjGroup - 1) / kNearAdjGroup;
     const int64_t B = blockIdx.x * (int64_t)kNearAdjWarps + w;
     if (B >= ngroup) return;
-    nearpair::near_group<kNearAdjGroup, NearOpG>(ts, gs, M, topo, spack, near_off, near_list, gt, B, sc[w], lane);
+    nearpair::near_group<kNearAdjGroup, NearOpG>(ts, gs, M, topo, spack, near_off, near_list, gt, B, self, sc[w],
+                                                  lane);
 }
 
 // source side over the near entries sorted by leaf, in chunks of
@@ -1394,7 +1403,7 @@ extern "C" tc_status tc_adjoint(tc_ctx* ctx, const double* g, double* grad_f, do
     } else {
         k_near_adj_target32<<<ngrid32, kNearAdjWarps * 32, 0, s>>>(
             ts, ptr<double>(ctx->adj_gs), M, ptr<int4>(ctx->node_topo), ptr<float4>(ctx->spack),
-            ptr<int64_t>(ctx->near_off), ptr<ListEntry>(ctx->near_list), ptr<double>(ctx->adj_gt));
+            ptr<int64_t>(ctx->near_off), ptr<ListEntry>(ctx->near_list), ptr<double>(ctx->adj_gt), ctx->eval_self);
         note_launch();
         TC_CK(cudaMemsetAsync(ctx->adj_gnear.p, 0, (size_t)12 * N * 8, s), "zero near gradients");
         k_near_adj_source32<<<grid_for(ctx->near_entries, kNearAdjChunk), kNearAdjWarps * 32, 0, s>>>(

@@ -535,7 +535,7 @@ tc_status tc::eval_compute(tc_ctx* ctx, double* u)
     ph_begin(ctx, TC_PH_NEAR);
     TC_CK(launch_near(ctx->precision, ts, M, ptr<int4>(ctx->node_topo), ptr<double>(ctx->xs), ptr<double>(ctx->ws),
                       ptr<float4>(ctx->spack), ctx->N, ptr<int64_t>(ctx->near_off), ptr<ListEntry>(ctx->near_list),
-                      ptr<double>(ctx->u_near), s),
+                      ptr<double>(ctx->u_near), ctx->eval_self, s),
           "near field");
     ph_end(ctx, TC_PH_NEAR);
     TC_CK(cudaStreamWaitEvent(s, ctx->ev_join, 0), "join");

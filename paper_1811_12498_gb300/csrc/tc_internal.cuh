@@ -284,7 +284,8 @@ cudaError_t launch_finalize_batched(const SysDesc* sys, int nsys, const int64_t*
                                     int64_t ntot, cudaStream_t s);
 cudaError_t launch_near(int precision, const double* ts, int64_t M, const int4* topo,
                         const double* xs, const double* ws, const float4* spack, int64_t N,
-                        const int64_t* near_off, const ListEntry* near_list, double* u_near, cudaStream_t s);
+                        const int64_t* near_off, const ListEntry* near_list, double* u_near, int self,
+                        cudaStream_t s);
 cudaError_t launch_finalize(const double* u_far, const double* u_near, const int32_t* perm, int64_t M, double* u,
                             cudaStream_t s);
 cudaError_t launch_scatter_counts(const int64_t* cs, const int32_t* perm, int64_t M, int64_t* out,

@@ -61,7 +61,9 @@ __device__ inline Tgt2 load_target(const double* __restrict__ ts, int64_t M, int
 }
 
 // Stokeslet + stresslet terms of one target against source pair tp, both
-// sources at once
+// sources at once.  kGuard: a source may coincide with the target (r^2 = 0,
+// the pair is skipped); without it 1/r comes straight from rsqrt.
+template <bool kGuard>
 __device__ __forceinline__ void pair_terms(const Tgt2& t, const float4* tp, float2& ax, float2& ay, float2& az)
 {
     const float4 A = tp[0], B = tp[1], C = tp[2], D = tp[3], E = tp[4], F = tp[5], G = tp[6], Q = tp[7];
@@ -70,8 +72,13 @@ __device__ __forceinline__ void pair_terms(const Tgt2& t, const float4* tp, floa
     const float2 dz = __fadd2_rn(sub2(t.h2, make_float2(B.x, B.y)), sub2(t.l2, make_float2(D.x, D.y)));
     const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
     float2 ri;
-    ri.x = r2.x > 0.f ? rsqrtf(r2.x) : 0.f;
-    ri.y = r2.y > 0.f ? rsqrtf(r2.y) : 0.f;
+    if (kGuard) {
+        ri.x = r2.x > 0.f ? rsqrtf(r2.x) : 0.f;
+        ri.y = r2.y > 0.f ? rsqrtf(r2.y) : 0.f;
+    } else {
+        ri.x = rsqrtf(r2.x);
+        ri.y = rsqrtf(r2.y);
+    }
     const float2 ri2 = __fmul2_rn(ri, ri);
     const float2 f0 = make_float2(B.z, B.w), f1 = make_float2(D.z, D.w), f2 = make_float2(E.x, E.y);
     const float2 df = __ffma2_rn(dx, f0, __ffma2_rn(dy, f1, __fmul2_rn(dz, f2)));
@@ -90,13 +97,15 @@ __device__ __forceinline__ void pair_terms(const Tgt2& t, const float4* tp, floa
 struct NearOpU {
     using Tgt = Tgt2;
     static constexpr bool kAdd = false;
+    static constexpr bool kUnguarded = true;
     __device__ static Tgt load(const double* ts, const double*, int64_t M, int64_t m, bool valid)
     {
         return load_target(ts, M, m, valid);
     }
+    template <bool kGuard>
     __device__ static void terms(const Tgt& t, const float4* tp, float2& ax, float2& ay, float2& az)
     {
-        pair_terms(t, tp, ax, ay, az);
+        pair_terms<kGuard>(t, tp, ax, ay, az);
     }
 };
 
@@ -156,15 +165,15 @@ __device__ inline void near_batch_fp64(const double* __restrict__ ts, int64_t M,
 __global__ void __launch_bounds__(kNearWarps * 32)
     k_near_mixed(const double* __restrict__ ts, int64_t M, const int4* __restrict__ topo,
                  const float4* __restrict__ spack, const int64_t* __restrict__ near_off,
-                 const ListEntry* __restrict__ near_list, double* __restrict__ u_near)
+                 const ListEntry* __restrict__ near_list, double* __restrict__ u_near, int self)
 {
     __shared__ NearScratch<kNearGroup> sc[kNearWarps];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t ngroup = ((M + kBatch - 1) / kBatch + kNearGroup - 1) / kNearGroup;
     const int64_t B = blockIdx.x * (int64_t)kNearWarps + w;
     if (B >= ngroup) return;
-    nearpair::near_group<kNearGroup, NearOpU>(ts, nullptr, M, topo, spack, near_off, near_list, u_near, B, sc[w],
-                                             lane);
+    nearpair::near_group<kNearGroup, NearOpU>(ts, nullptr, M, topo, spack, near_off, near_list, u_near, B, self,
+                                             sc[w], lane);
 }
 
 __global__ void __launch_bounds__(kNearWarps * 32)
@@ -212,7 +221,7 @@ __global__ void __launch_bounds__(kNearMaxWarps * 32)
             near_batch_fp64(d.ts, d.M, d.topo, d.xs, d.ws, d.N, d.near_off, d.near_list, d.u_near, b, tile[w], lane);
         else
             nearpair::near_group<kNearGroup, NearOpU>(d.ts, nullptr, d.M, d.topo, d.spack, d.near_off,
-                                                      d.near_list, d.u_near, b,
+                                                      d.near_list, d.u_near, b, 1,
                                                       *reinterpret_cast<NearScratch<kNearGroup>*>(tile[w]), lane);
     }
 }
@@ -265,7 +274,8 @@ inline unsigned grid_for(int64_t n, int threads)
 
 cudaError_t launch_near(int precision, const double* ts, int64_t M, const int4* topo,
                         const double* xs, const double* ws, const float4* spack, int64_t N,
-                        const int64_t* near_off, const ListEntry* near_list, double* u_near, cudaStream_t s)
+                        const int64_t* near_off, const ListEntry* near_list, double* u_near, int self,
+                        cudaStream_t s)
 {
     if (M <= 0) return cudaSuccess;
     const int64_t nbatch = (M + kBatch - 1) / kBatch;
@@ -275,7 +285,7 @@ cudaError_t launch_near(int precision, const double* ts, int64_t M, const int4* 
     } else {
         const int64_t ngroup = (nbatch + kNearGroup - 1) / kNearGroup;
         const unsigned grid = (unsigned)((ngroup + kNearWarps - 1) / kNearWarps);
-        k_near_mixed<<<grid, kNearWarps * 32, 0, s>>>(ts, M, topo, spack, near_off, near_list, u_near);
+        k_near_mixed<<<grid, kNearWarps * 32, 0, s>>>(ts, M, topo, spack, near_off, near_list, u_near, self);
     }
     note_launch();
     return cudaGetLastError();

@@ -82,14 +82,16 @@ struct NearScratch {
 // and each result is added to its target's accumulator in shared memory.
 //
 // Op supplies the per-target record (Op::Tgt, Op::load), the pair terms of one
-// target against a staged source pair (Op::terms, three FP32x2 accumulators)
-// and whether the result is stored or added (Op::kAdd); gs is passed through
-// to Op::load (the adjoint's target weights g, unused by the forward field).
+// target against a staged source pair (Op::terms<kGuard>, three FP32x2
+// accumulators), whether the result is stored or added (Op::kAdd), and
+// whether its terms are also compiled without the r = 0 guard for leaves
+// that cannot hold a target (Op::kUnguarded); gs is passed through to
+// Op::load (the adjoint's target weights g, unused by the forward field).
 template <int G, typename Op>
 __device__ inline void near_group(const double* __restrict__ ts, const double* __restrict__ gs, int64_t M,
                                   const int4* __restrict__ topo, const float4* __restrict__ spack,
                                   const int64_t* __restrict__ near_off, const ListEntry* __restrict__ near_list,
-                                  double* __restrict__ out, int64_t B, NearScratch<G>& sc, int lane)
+                                  double* __restrict__ out, int64_t B, int self, NearScratch<G>& sc, int lane)
 {
     const int64_t nbatch = (M + kBatch - 1) / kBatch;
     const int64_t b0 = (int64_t)G * B;
@@ -144,8 +146,17 @@ __device__ inline void near_group(const double* __restrict__ ts, const double* _
             const int k1 = 32 * s + lane, k2 = k1 + 32;
             const bool v1 = k1 < A, v2 = two && k2 < A;
             const int id1 = v1 ? sc.slot[k1] : 0, id2 = v2 ? sc.slot[k2] : 0;
-            const typename Op::Tgt ta = Op::load(ts, gs, M, (b0 + (id1 >> 5)) * kBatch + (id1 & 31), v1);
-            const typename Op::Tgt tb = Op::load(ts, gs, M, (b0 + (id2 >> 5)) * kBatch + (id2 & 31), v2);
+            const int64_t m1 = (b0 + (id1 >> 5)) * kBatch + (id1 & 31), m2 = (b0 + (id2 >> 5)) * kBatch + (id2 & 31);
+            const typename Op::Tgt ta = Op::load(ts, gs, M, m1, v1);
+            const typename Op::Tgt tb = Op::load(ts, gs, M, m2, v2);
+            // r = 0 needs the target to coincide with a source of this leaf.
+            // With targets = sources (self) that is only possible for a
+            // target inside the leaf's own range (coincident points have
+            // one Morton key, so they share a leaf); otherwise (disjoint
+            // targets) every pair keeps the guard.
+            const bool guard = !Op::kUnguarded || !self ||
+                               __any_sync(0xffffffffu, (v1 && m1 >= t.x && m1 < (int64_t)t.x + t.y) ||
+                                                           (v2 && m2 >= t.x && m2 < (int64_t)t.x + t.y));
             // per-tile partial sums, accumulated over the leaf's tiles by
             // compensated FP32 summation (sum, compensation per component)
             float sa[3] = {0.f, 0.f, 0.f}, ka[3] = {0.f, 0.f, 0.f}, sb[3] = {0.f, 0.f, 0.f},
@@ -157,14 +168,24 @@ __device__ inline void near_group(const double* __restrict__ ts, const double* _
                 __syncwarp();
                 const int npairs = (cnt + 1) >> 1;
                 float2 axa = make_float2(0.f, 0.f), aya = axa, aza = axa, axb = axa, ayb = axa, azb = axa;
-                if (two) {
+                if (two && guard) {
                     for (int q = 0; q < npairs; q++) {
                         const float4* tp = sc.tile + q * kPairStride;
-                        Op::terms(ta, tp, axa, aya, aza);
-                        Op::terms(tb, tp, axb, ayb, azb);
+                        Op::template terms<true>(ta, tp, axa, aya, aza);
+                        Op::template terms<true>(tb, tp, axb, ayb, azb);
                     }
+                } else if (two) {
+                    for (int q = 0; q < npairs; q++) {
+                        const float4* tp = sc.tile + q * kPairStride;
+                        Op::template terms<false>(ta, tp, axa, aya, aza);
+                        Op::template terms<false>(tb, tp, axb, ayb, azb);
+                    }
+                } else if (guard) {
+                    for (int q = 0; q < npairs; q++)
+                        Op::template terms<true>(ta, sc.tile + q * kPairStride, axa, aya, aza);
                 } else {
-                    for (int q = 0; q < npairs; q++) Op::terms(ta, sc.tile + q * kPairStride, axa, aya, aza);
+                    for (int q = 0; q < npairs; q++)
+                        Op::template terms<false>(ta, sc.tile + q * kPairStride, axa, aya, aza);
                 }
                 kahan_add(sa[0], ka[0], axa.x + axa.y);
                 kahan_add(sa[1], ka[1], aya.x + aya.y);
