@@ -429,25 +429,34 @@ __global__ void __launch_bounds__(kNearAdjWarps * 32)
                 const unsigned mask = near_list[e].mask;
                 const int64_t m = (int64_t)ebatch[e] * kBatch + lane;
                 __syncwarp();
+                // the entry's targets (the lanes of its mask) are packed
+                // densely into the first A slots; slot A, when A is odd, holds
+                // a zero-weight target (written by the lowest lane outside the
+                // mask, whose record is all zeros) so that pairs stay whole
+                const int A = __popc(mask);
+                const int pad_lane = __ffs(~mask) - 1;  // -1 when all 32 are in
                 {
+                    const bool on = (mask >> lane) & 1u;
                     float v[9];
 #pragma unroll
                     for (int k = 0; k < 9; k++) v[k] = 0.f;
-                    if ((mask >> lane) & 1u)
+                    if (on)
                         for (int a = 0; a < 3; a++) {
                             const double x = ts[a * M + m];
                             v[a] = __double2float_rn(x);
                             v[3 + a] = __double2float_rn(x - (double)v[a]);
                             v[6 + a] = __double2float_rn(gs[a * M + m]);
                         }
+                    const int slot = on ? __popc(mask & ((1u << lane) - 1u)) : (lane == pad_lane ? A : -1);
+                    if (slot >= 0 && slot < 32)
 #pragma unroll
-                    for (int k = 0; k < 9; k++) tile[w][k][lane] = v[k];
+                        for (int k = 0; k < 9; k++) tile[w][k][slot] = v[k];
                 }
                 __syncwarp();
                 float2 a[12];
 #pragma unroll
                 for (int c = 0; c < 12; c++) a[c] = make_float2(0.f, 0.f);
-                for (int q = 0; q < 32; q += 2) {
+                for (int q = 0; q < A; q += 2) {
                     float2 T[9];
 #pragma unroll
                     for (int k = 0; k < 9; k++) T[k] = *reinterpret_cast<const float2*>(&tile[w][k][q]);
