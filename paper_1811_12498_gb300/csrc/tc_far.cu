@@ -36,9 +36,10 @@
 //    is resident (one single-warp block per free slot) and its warps take
 //    batch pairs from a work queue, so a warp whose pairs have short lists
 //    takes more instead of idling while the last blocks run.  The
-//    contraction runs on packed FP32x2 FMAs over pairs of table columns,
-//    which halves the instructions of the fully unrolled body (its size, not
-//    only its arithmetic, limits the kernel: instruction fetch stalls).  d' is
+//    contraction runs on packed FP32x2 FMAs over pairs of table columns and
+//    the two targets' recurrences on packed FP32x2 arithmetic side by side,
+//    which shrinks the fully unrolled body (its size, not only its
+//    arithmetic, limits the kernel: instruction fetch stalls).  d' is
 //    formed from FP32 hi/lo splits of the target and the cluster centre
 //    (x_hi - y_hi is computed with one rounding, so d' carries FP32 relative
 //    accuracy however close x and y_c are in absolute terms), with no FP64
@@ -227,56 +228,80 @@ __device__ inline Tgt32 load_tgt32(const double* __restrict__ ts, int64_t M, int
     return t;
 }
 
-// Far-field contribution of one cluster (folded FP32 tables tab, geometry
-// gh = (y_c hi, 1/rho), gl = (y_c lo, 0)) to NT targets held by this lane.
-// The NT recurrences run side by side and share every table load, so a
-// table value broadcast to the warp feeds NT x 32 products.  Lanes for which
-// in[t] is false get finite garbage, discarded by the caller.
-template <int P, int NT>
-__device__ __forceinline__ void far_entry32(const Tgt32 (&tg)[NT], const bool (&in)[NT], const float4 gh,
-                                            const float4 gl, const float4* __restrict__ tab, float (&res)[NT][3])
+// c^k of hcoef_r for the two targets of a lane at once, (target 0, target 1)
+// in the two halves of each FP32x2 register pair; nkap = -kappa_n / R'^2.
+__device__ __forceinline__ float2 hcoef_r2(const float2* R1, const float2* R2, int n, int h, float2 v0, float2 v1,
+                                           float2 v2, float2 nkap)
 {
-    float d0[NT], d1[NT], d2[NT], iR[NT], iR2[NT], v0[NT], v1[NT], v2[NT];
+    float2 s1 = make_float2(0.f, 0.f), s2 = make_float2(0.f, 0.f);
+    bool any1 = false, any2 = false;
+    if (h <= n) {
+        const int k3 = h, k2 = n - h;
+        if (k2 >= 1) s1 = __fmul2_rn(v1, R1[k3]), any1 = true;
+        if (k3 >= 1) s1 = any1 ? __ffma2_rn(v2, R1[k3 - 1], s1) : __fmul2_rn(v2, R1[k3 - 1]);
+        if (k2 >= 2) s2 = R2[k3], any2 = true;
+        if (k3 >= 2) s2 = any2 ? __fadd2_rn(s2, R2[k3 - 2]) : R2[k3 - 2], any2 = true;
+    } else {
+        const int k3 = h - n - 1, k2 = n - 1 - k3;
+        s1 = __fmul2_rn(v0, R1[k3]);
+        if (k2 >= 1) s1 = __ffma2_rn(v1, R1[n + k3], s1);
+        if (k3 >= 1) s1 = __ffma2_rn(v2, R1[n + k3 - 1], s1);
+        if (k2 >= 2) s2 = R2[n - 1 + k3], any2 = true;
+        if (k3 >= 2) s2 = any2 ? __fadd2_rn(s2, R2[n - 3 + k3]) : R2[n - 3 + k3], any2 = true;
+    }
+    return any2 ? __ffma2_rn(nkap, s2, s1) : s1;
+}
+
+// Far-field contribution of one cluster (folded FP32 tables tab, geometry
+// gh = (y_c hi, 1/rho), gl = (y_c lo, 0)) to the two targets held by this
+// lane.  Their recurrences run side by side on packed FP32x2 arithmetic and
+// share every table load, so a table value broadcast to the warp feeds
+// 2 x 32 products.  Lanes for which in[t] is false get finite garbage,
+// discarded by the caller.
+template <int P>
+__device__ __forceinline__ void far_entry32(const Tgt32 (&tg)[2], const bool (&in)[2], const float4 gh,
+                                            const float4 gl, const float4* __restrict__ tab, float (&res)[2][3])
+{
+    float d0[2], d1[2], d2[2], iR[2], iR2[2], v0[2], v1[2], v2[2];
 #pragma unroll
-    for (int t = 0; t < NT; t++) {
+    for (int t = 0; t < 2; t++) {
         d0[t] = ((tg[t].h0 - gh.x) + (tg[t].l0 - gl.x)) * gh.w;
         d1[t] = ((tg[t].h1 - gh.y) + (tg[t].l1 - gl.y)) * gh.w;
         d2[t] = ((tg[t].h2 - gh.z) + (tg[t].l2 - gl.z)) * gh.w;
         float R2 = fmaf(d0[t], d0[t], fmaf(d1[t], d1[t], d2[t] * d2[t]));
-        if (!in[t]) R2 = 1.0f;  // keep idle lanes finite
+        if (!in[t]) R2 = 1.0f;
         iR[t] = rsqrtf(R2);
         iR2[t] = iR[t] * iR[t];
         v0[t] = d0[t] * iR2[t];
         v1[t] = d1[t] * iR2[t];
         v2[t] = d2[t] * iR2[t];
     }
-    float2 tot[NT][6];
+    const float2 w0 = make_float2(v0[0], v0[1]), w1 = make_float2(v1[0], v1[1]), w2 = make_float2(v2[0], v2[1]);
+    float2 tot[2][6];
     {
-        const float4 a = __ldg(tab), b = __ldg(tab + 1), c = __ldg(tab + 2);  // level 0: c^0 = 1
+        const float4 a = __ldg(tab), b = __ldg(tab + 1), c = __ldg(tab + 2);
 #pragma unroll
-        for (int t = 0; t < NT; t++) {
+        for (int t = 0; t < 2; t++) {
             tot[t][0] = make_float2(a.x, a.y), tot[t][1] = make_float2(a.z, a.w);
             tot[t][2] = make_float2(b.x, b.y), tot[t][3] = make_float2(b.z, b.w);
             tot[t][4] = make_float2(c.x, c.y), tot[t][5] = make_float2(c.z, c.w);
         }
     }
-    float cs[NT][2][2 * P + 1];
-#pragma unroll
-    for (int t = 0; t < NT; t++) cs[t][0][0] = 1.0f;
+    float2 cs[2][2 * P + 1];
+    cs[0][0] = make_float2(1.0f, 1.0f);
 #pragma unroll
     for (int n = 1; n <= P; n++) {
-        float kap[NT];
-#pragma unroll
-        for (int t = 0; t < NT; t++) kap[t] = c_lev32.kappa[n] * iR2[t];
+        const float2 nkap = make_float2(-c_lev32.kappa[n] * iR2[0], -c_lev32.kappa[n] * iR2[1]);
 #pragma unroll
         for (int h = 2 * n; h >= 0; h--) {
             const float4* tl = tab + 3 * (n * n + h);
             const float4 a = __ldg(tl), b = __ldg(tl + 1), c = __ldg(tl + 2);
+            const float2 cf = hcoef_r2(cs[(n - 1) & 1], cs[n & 1], n, h, w0, w1, w2, nkap);
+            cs[n & 1][h] = cf;  // level n overwrites level n-2
 #pragma unroll
-            for (int t = 0; t < NT; t++) {
-                const float cf = hcoef_r(cs[t][(n - 1) & 1], cs[t][n & 1], n, h, v0[t], v1[t], v2[t], kap[t]);
-                cs[t][n & 1][h] = cf;  // level n overwrites level n-2
-                const float2 c2 = make_float2(cf, cf);
+            for (int t = 0; t < 2; t++) {
+                const float x = t == 0 ? cf.x : cf.y;
+                const float2 c2 = make_float2(x, x);
                 tot[t][0] = __ffma2_rn(c2, make_float2(a.x, a.y), tot[t][0]);
                 tot[t][1] = __ffma2_rn(c2, make_float2(a.z, a.w), tot[t][1]);
                 tot[t][2] = __ffma2_rn(c2, make_float2(b.x, b.y), tot[t][2]);
@@ -285,12 +310,12 @@ __device__ __forceinline__ void far_entry32(const Tgt32 (&tg)[NT], const bool (&
                 tot[t][5] = __ffma2_rn(c2, make_float2(c.z, c.w), tot[t][5]);
             }
             // keep the table loads of later coefficients from being hoisted
-            // here: with two targets per lane that would exhaust the registers
-            if (NT > 1) asm volatile("" ::: "memory");
+            // here: that would exhaust the registers
+            asm volatile("" ::: "memory");
         }
     }
 #pragma unroll
-    for (int t = 0; t < NT; t++) {
+    for (int t = 0; t < 2; t++) {
         const float T0 = tot[t][0].x, T1 = tot[t][0].y, T2 = tot[t][1].x, T3 = tot[t][1].y, T4 = tot[t][2].x,
                     T5 = tot[t][2].y, T6 = tot[t][3].x, T7 = tot[t][3].y, T8 = tot[t][4].x, T9 = tot[t][4].y,
                     T10 = tot[t][5].x, T11 = tot[t][5].y;
@@ -358,7 +383,7 @@ __device__ __forceinline__ void far_pair32(const double* __restrict__ ts, int64_
             const Tgt32 tg[2] = {ta, tb};
             const bool in[2] = {inA, inB};
             float r[2][3];
-            far_entry32<P, 2>(tg, in, gh, gl, tab, r);
+            far_entry32<P>(tg, in, gh, gl, tab, r);
             if (inA) {
                 kahan_add(sa[0], ka[0], r[0][0]);
                 kahan_add(sa[1], ka[1], r[0][1]);
