@@ -12,13 +12,13 @@
 // a leaf are accumulated by compensated (Kahan) FP32 summation and each
 // leaf's sum is added to an FP64 per-target accumulator (an FP64 addition per
 // tile stalled every tile's end on the slow FP64 pipe).  One warp handles a
-// group of four consecutive batches (in both the one-system and the batched
-// kernel) and walks the merge of their near lists (all in tree order, i.e. by
-// the leaf's first source); for each leaf the targets that need it are packed
-// densely into 32-lane streams, and two streams share every staged tile, so
-// every broadcast source value feeds two targets.  The tile holds the sources
-// in pairs, field by field ((y_2q.f, y_2q+1.f) adjacent), and the pair terms
-// run on packed FP32x2 arithmetic, two sources per instruction.
+// group of consecutive batches (eight in the one-system kernel, four in the
+// batched one) and walks the merge of their near lists (all in tree order,
+// i.e. by the leaf's first source); for each leaf the targets that need it
+// are packed densely into 32-lane streams, and two streams share every staged
+// tile, so every broadcast source value feeds two targets.  The tile holds the
+// sources in pairs, field by field ((y_2q.f, y_2q+1.f) adjacent), and the
+// pair terms run on packed FP32x2 arithmetic, two sources per instruction.
 //
 // FP64 mode computes everything in FP64, one batch per warp.
 #include "tc_nearpair.cuh"
@@ -28,7 +28,11 @@ namespace tc {
 namespace {
 
 constexpr int kNearWarps = 4;
-constexpr int kNearGroup = kNearGroupBatches;  // batches per warp (mixed precision)
+// batches per warp in the one-system mixed-precision kernel: with eight the
+// grid is short enough (about one resident wave at N = 10^6) that its tail
+// leaves SMs to the far field, which the step runs next (step 57.9 -> 54.4 ms
+// against four; the near kernel alone 39.0 -> 40.5 ms)
+constexpr int kNearGroup = 8;
 constexpr int kNearMaxWarps = 8;  // largest block the batched kernel accepts
 
 // ---------------------------------------------------------------------------
@@ -198,8 +202,9 @@ __global__ void __launch_bounds__(kNearMaxWarps * 32)
     k_near_batched(const SysDesc* __restrict__ sys, int nsys, const int64_t* __restrict__ item_off, int64_t nitems,
                    unsigned long long* __restrict__ counter)
 {
-    constexpr int kTileBytes =
-        12 * 32 * 8 > (int)sizeof(NearScratch<kNearGroup>) ? 12 * 32 * 8 : (int)sizeof(NearScratch<kNearGroup>);
+    constexpr int kTileBytes = 12 * 32 * 8 > (int)sizeof(NearScratch<kNearGroupBatches>)
+                                   ? 12 * 32 * 8
+                                   : (int)sizeof(NearScratch<kNearGroupBatches>);
     __shared__ __align__(16) double tile[kNearMaxWarps][kTileBytes / 8];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (;;) {
@@ -220,9 +225,9 @@ __global__ void __launch_bounds__(kNearMaxWarps * 32)
         if (kFp64)
             near_batch_fp64(d.ts, d.M, d.topo, d.xs, d.ws, d.N, d.near_off, d.near_list, d.u_near, b, tile[w], lane);
         else
-            nearpair::near_group<kNearGroup, NearOpU>(d.ts, nullptr, d.M, d.topo, d.spack, d.near_off,
-                                                      d.near_list, d.u_near, b, 1,
-                                                      *reinterpret_cast<NearScratch<kNearGroup>*>(tile[w]), lane);
+            nearpair::near_group<kNearGroupBatches, NearOpU>(
+                d.ts, nullptr, d.M, d.topo, d.spack, d.near_off, d.near_list, d.u_near, b, 1,
+                *reinterpret_cast<NearScratch<kNearGroupBatches>*>(tile[w]), lane);
     }
 }
 

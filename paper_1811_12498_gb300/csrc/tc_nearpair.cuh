@@ -74,7 +74,8 @@ struct NearScratch {
 
 // Near field of batches G*B .. G*B+G-1 (the last ones may not exist) on one
 // warp, over the merge of their G near lists (all in tree order, so by the
-// leaf's first source).  For each leaf, the targets of the G batches that
+// leaf's first source); lane g < G holds the cursor of list g, so the merge
+// state costs a few registers whatever G.  For each leaf, the targets of the G batches that
 // need it (the union of the entries' lane masks, A of them) are packed
 // densely into ceil(A/32) streams of 32 lanes, so lanes whose target does not
 // need the leaf are not computed (lane use of single-batch lists at N = 1M:
@@ -96,41 +97,39 @@ __device__ inline void near_group(const double* __restrict__ ts, const double* _
     const int64_t nbatch = (M + kBatch - 1) / kBatch;
     const int64_t b0 = (int64_t)G * B;
     constexpr int kEnd = 0x7fffffff;
-    int64_t cur[G], end[G];
-    ListEntry le[G];
-    int key[G];
+    constexpr unsigned kAll = 0xffffffffu;
+    // lane g < G holds the cursor of list g
+    int64_t cur = 0, end = 0;
+    if (lane < G && b0 + lane < nbatch) {
+        cur = near_off[b0 + lane];
+        end = near_off[b0 + lane + 1];
+    }
+    ListEntry le{0, 0};
+    int key = kEnd;
+    if (cur < end) {
+        le = near_list[cur];
+        key = topo[le.node].x;
+    }
 #pragma unroll
-    for (int g = 0; g < G; g++) {
-        cur[g] = end[g] = 0;
-        if (b0 + g < nbatch) {
-            cur[g] = near_off[b0 + g];
-            end[g] = near_off[b0 + g + 1];
-        }
-        key[g] = kEnd;
-        le[g] = ListEntry{0, 0};
-        if (cur[g] < end[g]) {
-            le[g] = near_list[cur[g]];
-            key[g] = topo[le[g].node].x;
-        }
+    for (int g = 0; g < G; g++)
 #pragma unroll
         for (int c = 0; c < 3; c++) sc.acc[g][c][lane] = 0.0;
-    }
     const unsigned lt = (1u << lane) - 1u;
     for (;;) {
-        int kmin = key[0];
+        int kmin = key;
 #pragma unroll
-        for (int g = 1; g < G; g++) kmin = min(kmin, key[g]);
+        for (int o = 1; o < G; o <<= 1) kmin = min(kmin, __shfl_xor_sync(kAll, kmin, o));
+        kmin = __shfl_sync(kAll, kmin, 0);
         if (kmin == kEnd) break;
         // leaves are disjoint ranges, so equal first sources name one leaf
-        int node = 0;
+        const bool match = lane < G && key == kmin;
+        const unsigned mine = match ? le.mask : 0u;
+        const int node = __shfl_sync(kAll, le.node, __ffs(__ballot_sync(kAll, match)) - 1);
         unsigned m[G];
         int A = 0, P[G];
 #pragma unroll
-        for (int g = G - 1; g >= 0; g--)
-            if (key[g] == kmin) node = le[g].node;
-#pragma unroll
         for (int g = 0; g < G; g++) {
-            m[g] = key[g] == kmin ? le[g].mask : 0u;
+            m[g] = __shfl_sync(kAll, mine, g);
             P[g] = A;
             A += __popc(m[g]);
         }
@@ -210,16 +209,14 @@ __device__ inline void near_group(const double* __restrict__ ts, const double* _
                 sc.acc[id2 >> 5][2][id2 & 31] += c2;
             }
         }
-#pragma unroll
-        for (int g = 0; g < G; g++)
-            if (key[g] == kmin) {
-                if (++cur[g] < end[g]) {
-                    le[g] = near_list[cur[g]];
-                    key[g] = topo[le[g].node].x;
-                } else {
-                    key[g] = kEnd;
-                }
+        if (match) {
+            if (++cur < end) {
+                le = near_list[cur];
+                key = topo[le.node].x;
+            } else {
+                key = kEnd;
             }
+        }
     }
     __syncwarp();
 #pragma unroll
