@@ -28,11 +28,15 @@ namespace tc {
 namespace {
 
 constexpr int kNearWarps = 4;
-// batches per warp in the one-system mixed-precision kernel: with eight the
-// grid is short enough (about one resident wave at N = 10^6) that its tail
-// leaves SMs to the far field, which the step runs next (step 57.9 -> 54.4 ms
-// against four; the near kernel alone 39.0 -> 40.5 ms)
-constexpr int kNearGroup = 8;
+// Batches per warp in the one-system mixed-precision kernel.  Eight when the
+// grid still fills the GPU (at least 0.6 of a resident wave of warps): the
+// grid is then short (about 1.3 waves at N = 10^6) and its tail leaves SMs to
+// the far field, which the step runs next (step 57.9 -> 54.4 ms against four,
+// though the near kernel alone goes 39.0 -> 40.5 ms); four otherwise, since a
+// grid of fewer warps than the GPU holds leaves it idle (N = 327680 on the
+// sphere: 36 ms with four, 64 ms with eight).
+constexpr int kNearGroupLarge = 8;
+constexpr double kNearWaveShare = 0.6;
 constexpr int kNearMaxWarps = 8;  // largest block the batched kernel accepts
 
 // ---------------------------------------------------------------------------
@@ -166,18 +170,45 @@ __device__ inline void near_batch_fp64(const double* __restrict__ ts, int64_t M,
     }
 }
 
+template <int G>
 __global__ void __launch_bounds__(kNearWarps * 32)
     k_near_mixed(const double* __restrict__ ts, int64_t M, const int4* __restrict__ topo,
                  const float4* __restrict__ spack, const int64_t* __restrict__ near_off,
                  const ListEntry* __restrict__ near_list, double* __restrict__ u_near, int self)
 {
-    __shared__ NearScratch<kNearGroup> sc[kNearWarps];
+    __shared__ NearScratch<G> sc[kNearWarps];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t ngroup = ((M + kBatch - 1) / kBatch + kNearGroup - 1) / kNearGroup;
+    const int64_t ngroup = ((M + kBatch - 1) / kBatch + G - 1) / G;
     const int64_t B = blockIdx.x * (int64_t)kNearWarps + w;
     if (B >= ngroup) return;
-    nearpair::near_group<kNearGroup, NearOpU>(ts, nullptr, M, topo, spack, near_off, near_list, u_near, B, self,
-                                             sc[w], lane);
+    nearpair::near_group<G, NearOpU>(ts, nullptr, M, topo, spack, near_off, near_list, u_near, B, self, sc[w], lane);
+}
+
+template <int G>
+cudaError_t run_near_mixed(const double* ts, int64_t M, const int4* topo, const float4* spack,
+                           const int64_t* near_off, const ListEntry* near_list, double* u_near, int self,
+                           cudaStream_t s)
+{
+    const int64_t ngroup = ((M + kBatch - 1) / kBatch + G - 1) / G;
+    const unsigned grid = (unsigned)((ngroup + kNearWarps - 1) / kNearWarps);
+    k_near_mixed<G><<<grid, kNearWarps * 32, 0, s>>>(ts, M, topo, spack, near_off, near_list, u_near, self);
+    return cudaGetLastError();
+}
+
+// warps of k_near_mixed<kNearGroupLarge> the GPU holds at once
+int near_resident_warps()
+{
+    static int warps = 0;
+    if (warps == 0) {
+        int per_sm = 0, dev = 0, sms = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_near_mixed<kNearGroupLarge>, kNearWarps * 32,
+                                                          0) != cudaSuccess)
+            per_sm = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        warps = (per_sm > 0 ? per_sm : 1) * kNearWarps * (sms > 0 ? sms : 1);
+    }
+    return warps;
 }
 
 __global__ void __launch_bounds__(kNearWarps * 32)
@@ -288,9 +319,14 @@ cudaError_t launch_near(int precision, const double* ts, int64_t M, const int4* 
         const unsigned grid = (unsigned)((nbatch + kNearWarps - 1) / kNearWarps);
         k_near_fp64<<<grid, kNearWarps * 32, 0, s>>>(ts, M, topo, xs, ws, N, near_off, near_list, u_near);
     } else {
-        const int64_t ngroup = (nbatch + kNearGroup - 1) / kNearGroup;
-        const unsigned grid = (unsigned)((ngroup + kNearWarps - 1) / kNearWarps);
-        k_near_mixed<<<grid, kNearWarps * 32, 0, s>>>(ts, M, topo, spack, near_off, near_list, u_near, self);
+        const bool large = (double)((nbatch + kNearGroupLarge - 1) / kNearGroupLarge) >=
+                           kNearWaveShare * near_resident_warps();
+        cudaError_t e = large ? run_near_mixed<kNearGroupLarge>(ts, M, topo, spack, near_off, near_list, u_near,
+                                                                  self, s)
+                              : run_near_mixed<kNearGroupBatches>(ts, M, topo, spack, near_off, near_list, u_near,
+                                                                  self, s);
+        note_launch();
+        return e;
     }
     note_launch();
     return cudaGetLastError();
