@@ -115,7 +115,8 @@ static void release_all(tc_ctx* c)
     DevBuf* bufs[] = {&c->root, &c->bbox_part, &c->keys, &c->keys_alt, &c->perm, &c->perm_alt, &c->hist, &c->xs,
                       &c->node_topo, &c->node_info, &c->node_key, &c->node_geo, &c->node_invrho, &c->node_geof, &c->geo_tmp,
                       &c->split_cnt,
-                      &c->split_off, &c->scan_tmp, &c->ws, &c->spack, &c->mom, &c->ab64, &c->ab32, &c->abf64,
+                      &c->split_off, &c->scan_tmp, &c->ws, &c->spack, &c->mom, &c->mom_tmp, &c->ab64, &c->ab32,
+                      &c->abf64,
                       &c->abf32, &c->geo32, &c->tkeys,
                       &c->tkeys_alt, &c->tperm, &c->tperm_alt, &c->ts, &c->nfar_e, &c->nnear_e,
                       &c->far_off, &c->near_off, &c->far_list, &c->near_list, &c->cnt_far, &c->cnt_near, &c->u_far,
@@ -336,6 +337,7 @@ tc_status tc_moments(tc_ctx* ctx, const double* f, const double* h, const double
     ctx->ab_p = -1;
     TC_CK(ensure(ctx->ws, (size_t)9 * N * 8), "alloc weights");
     TC_CK(ensure(ctx->mom, (size_t)ctx->nnodes * 12 * ncoef(p) * 8), "alloc moments");
+    TC_CK(ensure(ctx->mom_tmp, moments_scratch_bytes(N, ctx->nnodes, p)), "alloc moments");
     if (ctx->precision == TC_MIXED) TC_CK(ensure(ctx->spack, (size_t)N * 64), "alloc pack");
     ph_begin(ctx, TC_PH_MOMENTS);
     TC_CK(launch_gather_weights(f, h, nu, ptr<int32_t>(ctx->perm), N, ptr<double>(ctx->ws), s), "gather weights");
@@ -354,7 +356,7 @@ tc_status tc_moments(tc_ctx* ctx, const double* f, const double* h, const double
         TC_CK(cudaStreamWaitEvent(sm, ctx->ev_fork, 0), "fork");
     }
     TC_CK(launch_moments(ptr<int4>(ctx->node_topo), ptr<Geo>(ctx->node_geo), ptr<double>(ctx->xs),
-                         ptr<double>(ctx->ws), N, ctx->nnodes, p, ptr<double>(ctx->mom), sm),
+                         ptr<double>(ctx->ws), N, ctx->nnodes, p, ptr<double>(ctx->mom), ctx->mom_tmp.p, sm),
           "moments");
     // upward pass: level_begin holds the first node of each level and the end
     for (int L = (int)ctx->level_begin.size() - 3; L >= 0; L--)

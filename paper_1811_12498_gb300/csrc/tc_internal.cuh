@@ -135,6 +135,7 @@ struct tc_ctx {
     tc::DevBuf ws;                      // 9*N FP64 sorted weights: f(3) h(3) nu(3)
     tc::DevBuf spack;                   // MIXED source pack: 4 float4 per source
     tc::DevBuf mom;                     // FP64 [node][12][ncoef(p)]
+    tc::DevBuf mom_tmp;                 // leaf-pass scratch: item map and per-item partial moments
     int ab_p = -1;                      // order the contraction tables were built for
     tc::DevBuf ab64;                    // FP64 [node][ncoef(p+2)][12]
     tc::DevBuf ab32;                    // FP32 [node][ncoef(p+2)][12]
@@ -244,8 +245,10 @@ size_t geometry_scratch_bytes(int64_t nnodes);
 cudaError_t launch_gather_weights(const double* f, const double* h, const double* nu, const int32_t* perm,
                                   int64_t N, double* ws, cudaStream_t s);
 cudaError_t launch_source_pack(const double* xs, const double* ws, int64_t N, float4* pack, cudaStream_t s);
+// scratch bytes of launch_moments (item map and per-item partial moments)
+size_t moments_scratch_bytes(int64_t N, int64_t nnodes, int p);
 cudaError_t launch_moments(const int4* topo, const Geo* geo, const double* xs, const double* ws, int64_t N,
-                           int64_t nnodes, int p, double* mom, cudaStream_t s);
+                           int64_t nnodes, int p, double* mom, void* scratch, cudaStream_t s);
 cudaError_t launch_m2m(const int4* topo, const Geo* geo, int64_t lb, int64_t le, int p, double* mom, cudaStream_t s);
 cudaError_t launch_ab_tables(const double* mom, const double* invrho, int64_t nnodes, int pm, int p, double* ab64,
                              float* ab32, cudaStream_t s);

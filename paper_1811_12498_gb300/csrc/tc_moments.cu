@@ -82,21 +82,50 @@ constexpr int kMomThreads = 128;
 constexpr int kMomChunk = 32;
 constexpr int kMomSlots = (ncoef(kPMax) + kMomThreads - 1) / kMomThreads;
 
-// One block per leaf cluster (P2M, from the definition).  Particles are
-// staged in chunks: their powers of (y - y_c) per axis and their 12 weights;
-// each thread owns a few k.  Internal clusters are skipped here and
-// assembled from their children by k_m2m.
+constexpr int kMomItem = 256;  // particles of a leaf per block of the leaf pass
+
+// Leaf pass (P2M, from the definition), balanced: every leaf is cut into
+// items of at most kMomItem particles, one block per item, each writing its
+// partial moments to part[item]; k_moments_sum adds a leaf's partials in item
+// order (so the result does not depend on scheduling).  One block per leaf
+// left the GPU waiting on its largest leaves (N = 262144 in Gaussian
+// clusters: leaves of very different sizes).  Particles are staged in chunks:
+// their powers of (y - y_c) per axis and their 12 weights; each thread owns a
+// few k.  Internal clusters are assembled from their children by k_m2m.
+__global__ void k_mom_items(const int4* __restrict__ topo, int64_t nnodes, int32_t* __restrict__ cnt)
+{
+    const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (id >= nnodes) return;
+    const int4 t = topo[id];
+    cnt[id] = t.w == 0 ? (t.y + kMomItem - 1) / kMomItem : 0;
+}
+
 __global__ void __launch_bounds__(kMomThreads) k_moments(const int4* __restrict__ topo,
                                                          const Geo* __restrict__ geo,
                                                          const double* __restrict__ xs,
                                                          const double* __restrict__ ws, int64_t N, int p,
-                                                         double* __restrict__ mom)
+                                                         const int32_t* __restrict__ item_off,
+                                                         const int32_t* __restrict__ nitems, int64_t nnodes,
+                                                         double* __restrict__ part)
 {
     __shared__ double pw[3][kMomChunk][kPMax + 1];
     __shared__ double wt[kMomChunk][12];
-    int64_t node = blockIdx.x;
-    int4 t = topo[node];
-    if (t.w != 0) return;
+    const int item = blockIdx.x;
+    if (item >= *nitems) return;
+    int64_t lo = 0, hi = nnodes;  // item_off[lo] <= item < item_off[hi]
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (item_off[mid] <= item)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    // lo is the last node with item_off <= item; nodes without items (cnt 0)
+    // share their successor's offset and come before it, so lo owns the item
+    const int64_t node = lo;
+    const int4 t0 = topo[node];
+    const int first = t0.x + (item - item_off[node]) * kMomItem;
+    const int4 t = make_int4(first, min(kMomItem, t0.x + t0.y - first), 0, 0);
     Geo g = geo[node];
     const int C = ncoef(p);
     int kk[kMomSlots][3];
@@ -144,7 +173,23 @@ __global__ void __launch_bounds__(kMomThreads) k_moments(const int4* __restrict_
     for (int s = 0; s < kMomSlots; s++) {
         int idx = threadIdx.x + s * kMomThreads;
         if (idx >= C) break;
-        for (int c = 0; c < 12; c++) mom[(node * 12 + c) * C + idx] = acc[s][c];
+        for (int c = 0; c < 12; c++) part[((int64_t)item * 12 + c) * C + idx] = acc[s][c];
+    }
+}
+
+// mom[leaf] = sum of the leaf's item partials, in item order
+__global__ void k_moments_sum(const int4* __restrict__ topo, const int32_t* __restrict__ cnt,
+                              const int32_t* __restrict__ item_off, int64_t nnodes, int p,
+                              const double* __restrict__ part, double* __restrict__ mom)
+{
+    const int64_t node = blockIdx.x;
+    if (node >= nnodes || topo[node].w != 0) return;
+    const int C = ncoef(p);
+    const int i0 = item_off[node], ni = cnt[node];
+    for (int q = threadIdx.x; q < 12 * C; q += blockDim.x) {
+        double v = 0.0;
+        for (int k = 0; k < ni; k++) v += part[(int64_t)(i0 + k) * 12 * C + q];
+        mom[node * 12 * C + q] = v;
     }
 }
 
@@ -406,10 +451,30 @@ cudaError_t launch_source_pack(const double* xs, const double* ws, int64_t N, fl
     return cudaGetLastError();
 }
 
-cudaError_t launch_moments(const int4* topo, const Geo* geo, const double* xs, const double* ws, int64_t N,
-                           int64_t nnodes, int p, double* mom, cudaStream_t s)
+int64_t moments_item_bound(int64_t N, int64_t nnodes) { return nnodes + (N + kMomItem - 1) / kMomItem; }
+
+size_t moments_scratch_bytes(int64_t N, int64_t nnodes, int p)
 {
-    k_moments<<<(unsigned)nnodes, kMomThreads, 0, s>>>(topo, geo, xs, ws, N, p, mom);
+    return (size_t)(2 * nnodes + 1) * 4 + 16 + (size_t)moments_item_bound(N, nnodes) * 12 * ncoef(p) * 8;
+}
+
+cudaError_t launch_moments(const int4* topo, const Geo* geo, const double* xs, const double* ws, int64_t N,
+                           int64_t nnodes, int p, double* mom, void* scratch, cudaStream_t s)
+{
+    // scratch: cnt [nnodes] i32, item_off [nnodes] i32, nitems i32, then (16-byte aligned) the partials
+    int32_t* cnt = reinterpret_cast<int32_t*>(scratch);
+    int32_t* item_off = cnt + nnodes;
+    int32_t* nitems = item_off + nnodes;
+    const size_t head = ((size_t)(2 * nnodes + 1) * 4 + 15) & ~(size_t)15;
+    double* part = reinterpret_cast<double*>(reinterpret_cast<char*>(scratch) + head);
+    k_mom_items<<<(unsigned)((nnodes + 255) / 256), 256, 0, s>>>(topo, nnodes, cnt);
+    note_launch();
+    cudaError_t e = launch_scan_i32(cnt, item_off, nnodes, nitems, s);
+    if (e != cudaSuccess) return e;
+    k_moments<<<(unsigned)moments_item_bound(N, nnodes), kMomThreads, 0, s>>>(topo, geo, xs, ws, N, p, item_off,
+                                                                               nitems, nnodes, part);
+    note_launch();
+    k_moments_sum<<<(unsigned)nnodes, 128, 0, s>>>(topo, cnt, item_off, nnodes, p, part, mom);
     note_launch();
     return cudaGetLastError();
 }
