@@ -80,6 +80,8 @@ def parse():
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-sweep", action="store_true",
                     help="skip the accuracy-against-time sweep on the 4M-point sphere")
+    ap.add_argument("--only-extra", choices=["fwd_adjoint", "batched", "sphere_sweep", "table1_sphere"],
+                    help="run just this extra measurement and print it as one JSON line (for profiling runs)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the forward+adjoint (Gaussian clusters) and batched (64 systems) measurements")
     return ap.parse_args()
@@ -411,6 +413,17 @@ def bench_batched(flush, stream, reps=3):
             "identical_results": bool(same), "tuned_shape": info}
 
 
+def run_only_extra(name):
+    """One extra measurement alone (its JSON object on one line), so that a
+    profiler can be pointed at exactly that workload."""
+    import torch
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    fn = {"fwd_adjoint": bench_fwd_adjoint, "batched": bench_batched, "sphere_sweep": bench_sphere_sweep,
+          "table1_sphere": bench_table1}[name]
+    print(json.dumps({"extra": name, **fn(flush, stream)}), flush=True)
+
+
 def config(args):
     return {"workload": "uniform cube N=%d, Stokeslet+stresslet, p=%d, theta=%g, N0=%d, %s precision, "
                         "clusters shrunk to their boxes" % (args.N, args.p, args.theta, args.N0, args.precision),
@@ -422,6 +435,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.only_extra:
+        return run_only_extra(args.only_extra)
     import numpy as np
     import torch
 
