@@ -75,19 +75,22 @@ struct NearScratch {
 // Near field of batches G*B .. G*B+G-1 (the last ones may not exist) on one
 // warp, over the merge of their G near lists (all in tree order, so by the
 // leaf's first source); lane g < G holds the cursor of list g, so the merge
-// state costs a few registers whatever G.  For each leaf, the targets of the G batches that
-// need it (the union of the entries' lane masks, A of them) are packed
-// densely into ceil(A/32) streams of 32 lanes, so lanes whose target does not
-// need the leaf are not computed (lane use of single-batch lists at N = 1M:
-// 0.74); streams are evaluated two at a time, each sharing the staged tile,
-// and each result is added to its target's accumulator in shared memory.
+// state costs a few registers whatever G.  For each leaf, the targets of the
+// G batches that need it (the union of the entries' lane masks, A of them)
+// are packed densely into ceil(A/32) streams of 32 lanes, so lanes whose
+// target does not need the leaf are not computed (lane use of single-batch
+// lists at N = 1M: 0.74); streams are evaluated two at a time, each sharing
+// the staged tile, and each result is added to its target's accumulator in
+// shared memory.  self: the targets are the sources (sorted index = source
+// index), which lets leaves that cannot hold a stream's own target skip the
+// r = 0 guard.
 //
 // Op supplies the per-target record (Op::Tgt, Op::load), the pair terms of one
 // target against a staged source pair (Op::terms<kGuard>, three FP32x2
 // accumulators), whether the result is stored or added (Op::kAdd), and
-// whether its terms are also compiled without the r = 0 guard for leaves
-// that cannot hold a target (Op::kUnguarded); gs is passed through to
-// Op::load (the adjoint's target weights g, unused by the forward field).
+// whether its terms are also compiled without the r = 0 guard (Op::kUnguarded);
+// gs is passed through to Op::load (the adjoint's target weights g, unused by
+// the forward field).
 template <int G, typename Op>
 __device__ inline void near_group(const double* __restrict__ ts, const double* __restrict__ gs, int64_t M,
                                   const int4* __restrict__ topo, const float4* __restrict__ spack,
