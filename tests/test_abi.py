@@ -69,3 +69,25 @@ def test_oracle_and_library_share_no_code():
         if f.endswith(".py"):
             text = open(os.path.join(ROOT, "paper_1811_12498_gb300", f)).read()
             assert "import oracle" not in text and "from oracle" not in text, f
+
+
+def declared_parameter_counts():
+    """{entry point: number of parameters} from the prototypes in include/tc.h."""
+    src = open(os.path.join(ROOT, "include", "tc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"#define[^\n]*", "", src)
+    out = {}
+    for m in re.finditer(r"\b(tc_[a-z_0-9]+)\s*\(([^;{]*?)\)\s*;", src):
+        params = m.group(2).strip()
+        out[m.group(1)] = 0 if params in ("", "void") else params.count(",") + 1
+    return out
+
+
+def test_binding_signatures_match_the_header():
+    """The ctypes table marshals exactly as many arguments as each C
+    prototype declares (a mismatch would pass garbage through the ABI)."""
+    from paper_1811_12498_gb300._lib import SIGNATURES
+    counts = declared_parameter_counts()
+    assert set(counts) == set(SIGNATURES), set(counts) ^ set(SIGNATURES)
+    for name, n in counts.items():
+        assert len(SIGNATURES[name][1]) == n, (name, n, len(SIGNATURES[name][1]))
