@@ -45,6 +45,7 @@ def _load():
         "orc_stokeslet": (None, [_d, _d, _d]),
         "orc_stresslet": (None, [_d, _d, _d]),
         "orc_direct": (None, [_d, _d, _d, _d, c_i64, _d, c_i64, _d, c_int]),
+        "orc_direct_grad": (None, [_d, _d, _d, _d, c_i64, _d, _d, _d, _d, _d, c_int]),
         "orc_coulomb_coeffs": (None, [_d, c_int, _d]),
         "orc_taylor_stokeslet": (None, [_d, c_int, _d]),
         "orc_taylor_stresslet": (None, [_d, c_int, _d]),
@@ -107,6 +108,18 @@ def direct(x, f, h, nu, targets=None, nthreads=0):
     u = np.empty((t.shape[0], 3))
     _load().orc_direct(_ptr(x), _ptr(f), _ptr(h), _ptr(nu), x.shape[0], _ptr(t), t.shape[0], _ptr(u), nthreads)
     return u
+
+
+def direct_grad(x, f, h, nu, g, nthreads=0):
+    """Gradients of L = sum_m g_m . u_m (u the direct sum at the particles)
+    with respect to f, h, nu and x, each (N, 3), from the derivatives of S and
+    T as defined (FP64)."""
+    x, f, h, nu, g = (_c3(a) for a in (x, f, h, nu, g))
+    N = x.shape[0]
+    out = {k: np.empty((N, 3)) for k in ("f", "h", "nu", "x")}
+    _load().orc_direct_grad(_ptr(x), _ptr(f), _ptr(h), _ptr(nu), N, _ptr(g), _ptr(out["f"]), _ptr(out["h"]),
+                            _ptr(out["nu"]), _ptr(out["x"]), nthreads)
+    return out
 
 
 def coulomb_coeffs(d, P):

@@ -114,6 +114,92 @@ void orc_direct(const double* x, const double* f, const double* h, const double*
     }
 }
 
+/* Gradient of L = sum_m g_m . u_m, u the direct sum of eq. (1.3) (targets
+ * = sources, coincident pairs skipped), by differentiating S and T of
+ * eqs. (1.2a,b) as defined: with d = x_m - x_n, r = |d|,
+ *   dS_ij/dd_a = -delta_ij d_a / r^3 + (delta_ia d_j + d_i delta_ja) / r^3
+ *                - 3 d_i d_j d_a / r^5,
+ *   dT_ijl/dd_a = (delta_ia d_j d_l + d_i delta_ja d_l + d_i d_j delta_la) / r^5
+ *                 - 5 d_i d_j d_l d_a / r^7;
+ * dL/df_n = sum_m S(d)^T g_m, dL/dh_n,j = sum_m g_m,i T_ijl nu_n,l,
+ * dL/dnu_n,l = sum_m g_m,i T_ijl h_n,j, and dL/dx gets +dphi/dd at the
+ * target and -dphi/dd at the source of every pair.  Arrays are N x 3. */
+static void pair_dphi(const double* d, const double* g, const double* f, const double* h, const double* nu,
+                      double* out)
+{
+    const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    const double r = sqrt(r2), r3 = r2 * r, r5 = r3 * r2, r7 = r5 * r2;
+    for (int a = 0; a < 3; a++) {
+        double s = 0.0;
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) {
+                double dS = -((i == j) ? d[a] / r3 : 0.0) + (((i == a) ? d[j] : 0.0) + ((j == a) ? d[i] : 0.0)) / r3 -
+                            3.0 * d[i] * d[j] * d[a] / r5;
+                s += g[i] * dS * f[j];
+                for (int l = 0; l < 3; l++) {
+                    double dT = (((i == a) ? d[j] * d[l] : 0.0) + ((j == a) ? d[i] * d[l] : 0.0) +
+                                 ((l == a) ? d[i] * d[j] : 0.0)) / r5 -
+                                5.0 * d[i] * d[j] * d[l] * d[a] / r7;
+                    s += g[i] * dT * h[j] * nu[l];
+                }
+            }
+        out[a] = s;
+    }
+}
+
+void orc_direct_grad(const double* x, const double* f, const double* h, const double* nu, int64_t N,
+                     const double* g, double* gf, double* gh, double* gnu, double* gx, int nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+    (void)nthreads;
+    /* source side: the weights of n and the source part of dL/dx_n */
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t n = 0; n < N; n++) {
+        const double* yn = x + 3 * n;
+        double af[3] = {0, 0, 0}, ah[3] = {0, 0, 0}, an[3] = {0, 0, 0}, ax[3] = {0, 0, 0};
+        for (int64_t m = 0; m < N; m++) {
+            const double* xm = x + 3 * m;
+            if (xm[0] == yn[0] && xm[1] == yn[1] && xm[2] == yn[2]) continue;
+            double S[9], T[27], d[3] = {xm[0] - yn[0], xm[1] - yn[1], xm[2] - yn[2]}, dp[3];
+            orc_stokeslet(xm, yn, S);
+            orc_stresslet(xm, yn, T);
+            const double* gm = g + 3 * m;
+            for (int i = 0; i < 3; i++)
+                for (int j = 0; j < 3; j++) {
+                    af[j] += gm[i] * S[3 * i + j];
+                    for (int l = 0; l < 3; l++) {
+                        ah[j] += gm[i] * T[9 * i + 3 * j + l] * nu[3 * n + l];
+                        an[l] += gm[i] * T[9 * i + 3 * j + l] * h[3 * n + j];
+                    }
+                }
+            pair_dphi(d, gm, f + 3 * n, h + 3 * n, nu + 3 * n, dp);
+            for (int a = 0; a < 3; a++) ax[a] -= dp[a];
+        }
+        for (int a = 0; a < 3; a++) {
+            gf[3 * n + a] = af[a];
+            gh[3 * n + a] = ah[a];
+            gnu[3 * n + a] = an[a];
+            gx[3 * n + a] = ax[a];
+        }
+    }
+    /* target side: the target part of dL/dx_m */
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t m = 0; m < N; m++) {
+        const double* xm = x + 3 * m;
+        double ax[3] = {0, 0, 0};
+        for (int64_t n = 0; n < N; n++) {
+            const double* yn = x + 3 * n;
+            if (xm[0] == yn[0] && xm[1] == yn[1] && xm[2] == yn[2]) continue;
+            double d[3] = {xm[0] - yn[0], xm[1] - yn[1], xm[2] - yn[2]}, dp[3];
+            pair_dphi(d, g + 3 * m, f + 3 * n, h + 3 * n, nu + 3 * n, dp);
+            for (int a = 0; a < 3; a++) ax[a] += dp[a];
+        }
+        for (int a = 0; a < 3; a++) gx[3 * m + a] += ax[a];
+    }
+}
+
 /* ------------------------------------------------------------------ */
 /* Multi-index cube helpers.  A cube of order P holds entries          */
 /* (k1,k2,k3) with 0 <= k_a <= P; only ||k|| <= P are meaningful.      */

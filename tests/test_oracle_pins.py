@@ -464,3 +464,34 @@ def test_frozen_structure_map_reduces_to_treecode_and_direct():
     xe = x + 1e-3 * rng.standard_normal(x.shape)
     u = tree.treecode_frozen(xe, f, h, nu, 5, x, xe, 1e-9)
     np.testing.assert_allclose(u, oracle.direct(xe, f, h, nu), rtol=1e-12, atol=1e-12)
+
+
+def test_direct_gradient_matches_finite_differences():
+    """The oracle's gradient of L = sum_m g_m . u_m of the direct sum (the
+    derivatives of S and T as defined) against central differences of L:
+    f, h and nu enter L linearly (the differences are exact up to rounding),
+    x through the kernels (step 1e-5, truncation O(step^2))."""
+    rng = _rng(91)
+    N = 24
+    x = rng.random((N, 3))
+    f, h = rng.uniform(-1, 1, (N, 3)), rng.uniform(-1, 1, (N, 3))
+    nu = rng.standard_normal((N, 3))
+    nu /= np.linalg.norm(nu, axis=1, keepdims=True)
+    g = rng.standard_normal((N, 3))
+    gr = oracle.direct_grad(x, f, h, nu, g)
+    base = dict(x=x, f=f, h=h, nu=nu)
+
+    def L(**kw):
+        a = dict(base, **kw)
+        return float(np.sum(g * oracle.direct(a["x"], a["f"], a["h"], a["nu"])))
+
+    for key, eps, tol in (("f", 1e-3, 1e-9), ("h", 1e-3, 1e-9), ("nu", 1e-3, 1e-9), ("x", 1e-5, 1e-6)):
+        arr = base[key]
+        fd = np.zeros_like(arr)
+        for i in range(N):
+            for a in range(3):
+                ap, am = arr.copy(), arr.copy()
+                ap[i, a] += eps
+                am[i, a] -= eps
+                fd[i, a] = (L(**{key: ap}) - L(**{key: am})) / (2 * eps)
+        assert oracle.rel_l2(gr[key], fd) < tol, (key, oracle.rel_l2(gr[key], fd))
