@@ -184,11 +184,12 @@ def test_full_size_sampled_weight_gradient():
     assert abs(got - ref) <= 1e-6 * np.linalg.norm(gr["f"]) * np.linalg.norm(phi)
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("mixed", 1e-4)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("mixed", 1e-6)])
 def test_adjoint_is_the_direct_gradient_when_every_pair_is_direct(prec, tol):
     """theta -> 0: no cluster of more than one point passes the MAC, so the
     treecode is the direct sum and its adjoint must be the gradient of the
-    direct sum, which the oracle forms from the derivatives of S and T."""
+    direct sum, which the oracle forms from the derivatives of S and T
+    (measured: 4e-15 in FP64, 2.2e-7 in mixed precision)."""
     N = 1500
     x, f, h, nu = inputs.uniform_cube(N, inputs.SEED_BASE + 61)
     g = np.random.default_rng(62).standard_normal((N, 3))
