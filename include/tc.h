@@ -22,7 +22,13 @@
  *    interaction lists, scratch) and frees it in tc_destroy.
  *  - Work is enqueued on the context's CUDA stream (tc_config.stream,
  *    NULL = legacy default stream).  Calls that must size buffers
- *    (tc_build, tc_eval) synchronise that stream internally.
+ *    (tc_build, tc_eval) synchronise that stream internally.  Inside a
+ *    context some work also runs on a second, library-owned stream (the
+ *    moment passes, the contraction tables and the far field), forked from
+ *    and joined back to the context's stream by events: everything a call
+ *    reads from the caller's arrays is read on the context's stream, and
+ *    every result a call writes to them (u, the gradients) is complete in
+ *    the context's stream order.
  *  - No call aborts or prints.  Every failure returns a status; the message
  *    is available from tc_last_error.  Device-side failures (a bounded wait
  *    that ran out, an index check) are reported by the next call that
