@@ -162,6 +162,23 @@ tc_status tc_adjoint(tc_ctx* ctx, const double* g, double* grad_f, double* grad_
                      double* grad_t);
 
 /*
+ * Frozen-structure re-evaluation (for finite differences of the adjoint, or
+ * any caller that moves the particles slightly and wants the map tc_adjoint
+ * differentiates).  The paper has no counterpart.
+ * tc_update_positions: replace the particle positions (device, 3*N FP64
+ * SoA, caller's order) after a tc_eval with targets = NULL, keeping the
+ * tree's cells, cluster centres and radii and that tc_eval's interaction
+ * lists (its far/near decisions); the moments about the unchanged centres
+ * and the contraction tables are recomputed.  Enqueued only.
+ * tc_eval_frozen: the velocity at the (moved) particles with those lists,
+ * written to u (device, 3*N FP64 SoA, caller's order).  Coincident pairs are
+ * skipped by r = 0, as for disjoint targets.  The result equals Algorithm 1
+ * when no position moved.  tc_build starts afresh.
+ */
+tc_status tc_update_positions(tc_ctx* ctx, const double* x);
+tc_status tc_eval_frozen(tc_ctx* ctx, double* u);
+
+/*
  * Direct O(N*M) sum of eq. (1.3) (with the contraction of Section 4.1).
  *  x, f, h, nu : device, 3*N FP64 SoA.  targets: device 3*M SoA or NULL
  *  (targets = sources, M must equal N).  u: device 3*M FP64 SoA, written.

@@ -21,6 +21,8 @@ SIGNATURES = {
     "tc_moments": (_i32, [_vp, _vp, _vp, _vp, _i32]),
     "tc_eval": (_i32, [_vp, _vp, _i64, _dbl, _i32, _vp]),
     "tc_adjoint": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "tc_update_positions": (_i32, [_vp, _vp]),
+    "tc_eval_frozen": (_i32, [_vp, _vp]),
     "tc_direct": (_i32, [_vp, _vp, _vp, _vp, _i64, _vp, _i64, _i32, _vp, _vp]),
     "tc_direct_noalloc": (_i32, [_vp, _vp, _vp, _vp, _i64, _vp, _i64, _i32, _vp, _vp]),
     "tc_stats": (_i32, [_vp, _vp, _vp, _vp]),

@@ -123,6 +123,24 @@ class Treecode:
         self._keep_t = t
         return out
 
+    def update_positions(self, x):
+        """Move the particles (tc_update_positions): tree, centres, radii and
+        the last eval's lists stay; moments and tables are recomputed."""
+        x = _vec3(x, "x", self.N)
+        self._chk(lib().tc_update_positions(self._h, _ptr(x)))
+        self._keep_x = x
+        return self
+
+    def eval_frozen(self, out=None):
+        """Velocity at the moved particles with the last eval's lists
+        (tc_eval_frozen); (3, N)."""
+        if out is None:
+            with torch.cuda.stream(self.stream):
+                out = torch.empty((3, self.N), dtype=torch.float64, device="cuda")
+        _vec3(out, "out", self.N)
+        self._chk(lib().tc_eval_frozen(self._h, _ptr(out)))
+        return out
+
     def sync(self):
         self._chk(lib().tc_sync(self._h))
 

@@ -320,6 +320,7 @@ tc_status tc_build(tc_ctx* ctx, const double* x, int64_t N, int32_t N0)
           "geometry");
     ph_end(ctx, TC_PH_BUILD);
     ctx->built = 1;
+    ctx->moved = 0;
     return TC_OK;
 }
 
@@ -537,7 +538,7 @@ tc_status tc::eval_compute(tc_ctx* ctx, double* u)
     ph_begin(ctx, TC_PH_NEAR);
     TC_CK(launch_near(ctx->precision, ts, M, ptr<int4>(ctx->node_topo), ptr<double>(ctx->xs), ptr<double>(ctx->ws),
                       ptr<float4>(ctx->spack), ctx->N, ptr<int64_t>(ctx->near_off), ptr<ListEntry>(ctx->near_list),
-                      ptr<double>(ctx->u_near), ctx->eval_self, s),
+                      ptr<double>(ctx->u_near), ctx->eval_self && !ctx->moved, s),
           "near field");
     ph_end(ctx, TC_PH_NEAR);
     TC_CK(cudaStreamWaitEvent(s, ctx->ev_join, 0), "join");
@@ -552,6 +553,46 @@ tc_status tc::eval_compute(tc_ctx* ctx, double* u)
 }
 
 extern "C" {
+
+tc_status tc_update_positions(tc_ctx* ctx, const double* x)
+{
+    if (!ctx) return fail(nullptr, TC_EINVAL, "tc_update_positions: ctx is NULL");
+    if (!x) return fail(ctx, TC_EINVAL, "tc_update_positions: x is NULL");
+    if (!ctx->prepared || !ctx->have_moments)
+        return fail(ctx, TC_ESTATE, "tc_update_positions: call tc_eval (targets = NULL) first");
+    if (!ctx->eval_self)
+        return fail(ctx, TC_ESTATE, "tc_update_positions: the last tc_eval must have had targets = NULL");
+    TC_CK(join_moments(ctx), "tc_update_positions");
+    cudaStream_t s = ctx->stream;
+    const int64_t N = ctx->N;
+    // the new positions in the tree's order; cells, centres, radii and the
+    // interaction lists of the last tc_eval stay as they are
+    TC_CK(launch_gather3(x, ptr<int32_t>(ctx->perm), N, ptr<double>(ctx->xs), s), "gather x");
+    if (ctx->precision == TC_MIXED)
+        TC_CK(launch_source_pack(ptr<double>(ctx->xs), ptr<double>(ctx->ws), N, ptr<float4>(ctx->spack), s), "pack");
+    // moments of the moved particles about the unchanged centres, then the tables
+    TC_CK(launch_moments(ptr<int4>(ctx->node_topo), ptr<Geo>(ctx->node_geo), ptr<double>(ctx->xs),
+                         ptr<double>(ctx->ws), N, ctx->nnodes, ctx->p_mom, ptr<double>(ctx->mom), ctx->mom_tmp.p, s),
+          "moments");
+    for (int L = (int)ctx->level_begin.size() - 3; L >= 0; L--)
+        TC_CK(launch_m2m(ptr<int4>(ctx->node_topo), ptr<Geo>(ctx->node_geo), ctx->level_begin[L],
+                         ctx->level_begin[L + 1], ctx->p_mom, ptr<double>(ctx->mom), s),
+              "m2m");
+    ctx->ab_p = -1;
+    tc_status st = ensure_tables(ctx, ctx->p_eval, s);
+    if (st != TC_OK) return st;
+    ctx->moved = 1;
+    ctx->have_eval = 0;
+    return TC_OK;
+}
+
+tc_status tc_eval_frozen(tc_ctx* ctx, double* u)
+{
+    if (!ctx) return fail(nullptr, TC_EINVAL, "tc_eval_frozen: ctx is NULL");
+    if (!u) return fail(ctx, TC_EINVAL, "tc_eval_frozen: u is NULL");
+    if (!ctx->prepared) return fail(ctx, TC_ESTATE, "tc_eval_frozen: call tc_eval first");
+    return eval_compute(ctx, u);
+}
 
 tc_status tc_eval(tc_ctx* ctx, const double* targets, int64_t M, double theta, int32_t p, double* u)
 {

@@ -145,6 +145,7 @@ struct tc_ctx {
     // ---- evaluation (tc_eval)
     int64_t M = 0;
     int eval_self = 1;
+    int moved = 0;                      // positions replaced by tc_update_positions since tc_build
     tc::DevBuf tkeys, tkeys_alt, tperm, tperm_alt;  // disjoint targets
     tc::DevBuf ts;                      // 3*M FP64 sorted targets
     tc::DevBuf nfar_e, nnear_e;         // per batch entry counts (int32)

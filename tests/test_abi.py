@@ -54,6 +54,8 @@ def test_host_argument_checks_without_gpu(lib):
     assert lib.tc_tune(None, None, None, None, None, 10, None, 1, None, 1, None, 1, None, 1, 1e-3, None, None,
                        None) == 1
     assert b"ctx is NULL" in lib.tc_last_error(None)
+    assert lib.tc_update_positions(None, None) == 1
+    assert lib.tc_eval_frozen(None, None) == 1
 
 
 def test_oracle_and_library_share_no_code():

@@ -197,3 +197,25 @@ def test_adjoint_is_the_direct_gradient_when_every_pair_is_direct(prec, tol):
     ref = oracle.direct_grad(x, f, h, nu, g)
     for k in ("f", "h", "nu", "x"):
         assert oracle.rel_l2(gr[k], ref[k]) <= tol, (k, oracle.rel_l2(gr[k], ref[k]))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_update_positions_gives_the_frozen_structure_map(prec):
+    """tc_update_positions + tc_eval_frozen: the tree, centres, radii and the
+    far/near decisions of the last tc_eval stay, the particles move; the
+    result is the oracle's frozen-structure map (decisions at the old
+    positions, moments, direct sums and evaluation at the new ones), and with
+    the old positions it is the original evaluation again."""
+    N, N0, p, theta = 3000, 100, 5, 0.5
+    x, f, h, nu = inputs.uniform_cube(N, inputs.SEED_BASE + 63)
+    xe = x + 2e-3 * np.random.default_rng(64).standard_normal(x.shape)
+    tc = api.Treecode(prec, True).build(dev(x), N0).moments(dev(f), dev(h), dev(nu), p)
+    u0 = host(tc.eval(theta, p))
+    u = host(tc.update_positions(dev(xe)).eval_frozen())
+    tree = oracle.Tree(x, N0, True)
+    tree.set_moments(f, h, nu, p)
+    ref = tree.treecode_frozen(xe, f, h, nu, p, x, xe, theta)
+    assert oracle.rel_l2(u, ref) <= TOL_W[prec], oracle.rel_l2(u, ref)
+    back = host(tc.update_positions(dev(x)).eval_frozen())
+    np.testing.assert_allclose(back, u0, rtol=1e-13, atol=1e-13 * np.abs(u0).max())
+    tc.close()
