@@ -12,8 +12,6 @@ namespace tc {
 
 static thread_local std::string g_thread_err = "no error";
 
-void set_thread_error(const char* msg) { g_thread_err = msg; }
-
 tc_status fail(tc_ctx* ctx, tc_status st, const char* fmt, ...)
 {
     char buf[768];

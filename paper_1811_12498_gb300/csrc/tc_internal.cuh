@@ -211,7 +211,6 @@ tc_status eval_compute(tc_ctx* ctx, double* u);
 // error helpers (tc_api.cu)
 tc_status fail(tc_ctx* ctx, tc_status st, const char* fmt, ...);
 tc_status cuda_fail(tc_ctx* ctx, cudaError_t e, const char* where);
-void set_thread_error(const char* msg);
 
 // grow a device buffer to hold at least `bytes`; contents are not preserved
 cudaError_t ensure(DevBuf& b, size_t bytes);
