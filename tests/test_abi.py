@@ -93,3 +93,16 @@ def test_binding_signatures_match_the_header():
     assert set(counts) == set(SIGNATURES), set(counts) ^ set(SIGNATURES)
     for name, n in counts.items():
         assert len(SIGNATURES[name][1]) == n, (name, n, len(SIGNATURES[name][1]))
+
+
+def test_no_fallback_without_the_library_or_a_gpu(monkeypatch, tmp_path):
+    """The binding never computes on the host: a missing libtc.so raises, and
+    host (CPU) tensors are refused before any call reaches the library."""
+    import torch
+    from paper_1811_12498_gb300 import _lib, api
+    monkeypatch.setattr(_lib, "LIB_PATH", str(tmp_path / "libtc.so"))
+    monkeypatch.setattr(_lib, "_lib", None)
+    with pytest.raises(RuntimeError, match="not built"):
+        _lib.lib()
+    with pytest.raises(TypeError, match="CUDA tensor"):
+        api._vec3(torch.zeros(3, 4, dtype=torch.float64), "x", 4)
