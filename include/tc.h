@@ -53,7 +53,9 @@ typedef enum {
     TC_ENOMEM = 2,   /* a device or host allocation failed                      */
     TC_ECUDA = 3,    /* a CUDA runtime call failed (message has the CUDA error) */
     TC_ESTATE = 4,   /* calls out of order, e.g. tc_eval before tc_moments      */
-    TC_ETIMEOUT = 5, /* a bounded device-side wait ran out                      */
+    TC_ETIMEOUT = 5, /* reserved for a bounded device-side wait; no kernel here
+                      * waits on another block or a flag (work queues take
+                      * items by atomics only), so it is never returned      */
     TC_EDEVICE = 6   /* a device-side check failed (message says which)        */
 } tc_status;
 

@@ -216,7 +216,6 @@ static tc_status check_flags(tc_ctx* ctx)
     TC_CK(cudaMemcpyAsync(&f, ctx->flags.p, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream), "flags");
     TC_CK(cudaStreamSynchronize(ctx->stream), "flags sync");
     if (f & kFlagStack) return fail(ctx, TC_EDEVICE, "device check: traversal stack bound exceeded");
-    if (f & kFlagIndex) return fail(ctx, TC_EDEVICE, "device check: index out of range");
     if (f) return fail(ctx, TC_EDEVICE, "device check: flags 0x%x", f);
     return TC_OK;
 }

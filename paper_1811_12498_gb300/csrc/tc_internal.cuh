@@ -49,7 +49,6 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float b)
 // Error flags raised by kernels (bit mask in device memory).
 enum DevFlag : int {
     kFlagStack = 1,     // traversal stack bound exceeded
-    kFlagIndex = 2,     // an index check failed
 };
 
 struct DevBuf {
