@@ -116,6 +116,32 @@ def test_direct_sum_superposition_and_exclusion():
     del rng
 
 
+def test_direct_sum_rounding_against_extended_precision():
+    """eq. (1.3) at N = 1500: the oracle's FP64 sum is within FP64 rounding of
+    the same sum carried in extended precision (numpy longdouble with a
+    mantissa wider than FP64's), so no term is dropped or summed at lower precision."""
+    L = np.longdouble
+    if np.finfo(L).nmant <= 52:
+        pytest.skip("longdouble is no wider than float64 on this host")
+    N = 1500
+    x, f, h, nu = inputs.uniform_cube(N, 12)
+    u = oracle.direct(x, f, h, nu)
+    X, F, H, NU = (a.astype(L) for a in (x, f, h, nu))
+    ref = np.zeros((N, 3), L)
+    for m in range(N):
+        d = X[m] - X
+        d[m] = 1
+        r2 = (d * d).sum(axis=1)
+        ir = 1 / np.sqrt(r2)
+        ir[m] = 0
+        ir3 = ir * ir * ir
+        s = (d * F).sum(axis=1) * ir3
+        t = (d * H).sum(axis=1) * (d * NU).sum(axis=1) * ir3 * ir * ir
+        ref[m] = (F * ir[:, None] + d * (s + t)[:, None]).sum(axis=0)
+    err = np.sqrt(((u - ref.astype(np.float64)) ** 2).sum() / (ref.astype(np.float64) ** 2).sum())
+    assert err <= 1e-14, err
+
+
 # ---------------------------------------------------- Coulomb coefficients
 
 def test_coulomb_on_axis_closed_form():
