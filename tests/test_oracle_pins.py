@@ -385,6 +385,36 @@ def test_treecode_single_leaf_is_direct():
     assert np.all(cnt["far"] == 0)
 
 
+@pytest.mark.parametrize("theta", [0.3, 0.6, 0.9])
+def test_traversal_counts_match_a_plain_walk_of_algorithm_1(theta):
+    """Algorithm 1 with the MAC of eq. (5.1) walked here in plain Python over
+    the exported tree (root first, children in Morton order; a cluster is far
+    iff r_c^2 <= theta^2 R^2 with R > 0, a leaf that fails is summed
+    directly): the oracle's per-target far-cluster, near-leaf and near-pair
+    counts are the same numbers."""
+    x, f, h, nu = _system(2500, 54, "sphere")
+    tree = oracle.Tree(x, 40, True)
+    tree.set_moments(f, h, nu, 1)
+    nd = tree.nodes()
+    tg = np.concatenate([x[::41], x[:5] + 0.3])  # particles, and points off the sphere
+    _, cnt = tree.treecode(tg, theta, 1, counts=True)
+    for m, t in enumerate(tg):
+        far = leaves = pairs = 0
+        stack = [0]
+        while stack:
+            c = stack.pop()
+            d = t - nd["yc"][c]
+            R2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2]
+            if R2 > 0 and nd["rc2"][c] <= theta * theta * R2:
+                far += 1
+            elif nd["nchild"][c] == 0:
+                leaves += 1
+                pairs += nd["count"][c]
+            else:
+                stack.extend(reversed(nd["child"][c][:nd["nchild"][c]].tolist()))
+        assert (cnt["far"][m], cnt["near_leaves"][m], cnt["near_pairs"][m]) == (far, leaves, pairs), m
+
+
 @pytest.mark.parametrize("theta", [0.3, 0.5, 0.8])
 def test_far_and_near_partition_the_sources(theta):
     """Algorithm 1 visits every source exactly once per target: the far clusters
