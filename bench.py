@@ -172,10 +172,10 @@ def source_sha(sources):
     return hsh.hexdigest()
 
 
-def kernel_traffic(sources, profile):
+def kernel_traffic(sources, profile, profiles_dir=None):
     """Per-launch DRAM bytes of a kernel from its committed ncu summary, if the
     summary was taken on the current kernel sources (source_sha); else None."""
-    prof = os.path.join(ROOT, "profiles", profile)
+    prof = os.path.join(profiles_dir or os.path.join(ROOT, "profiles"), profile)
     if not os.path.exists(prof):
         return None
     text = open(prof).read()

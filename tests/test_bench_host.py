@@ -70,3 +70,19 @@ def test_reference_arm_prints_one_line_on_rank_0_only():
     r = _run_reference({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
     assert r.returncode == 0, r.stderr
     assert r.stdout.strip() == ""
+
+
+def test_traffic_is_taken_only_from_a_summary_of_the_current_source(tmp_path):
+    """roofline.traffic comes from a committed ncu summary only when the summary
+    names the sha256 of the kernel's current source files; otherwise null."""
+    import bench
+    sha = bench.source_sha(bench.NEAR_SOURCES)
+    (tmp_path / "near.md").write_text("source_sha256: %s\ndram_bytes_per_full_launch: 1.25e+08\n" % sha)
+    (tmp_path / "stale.md").write_text("source_sha256: %s\ndram_bytes_per_full_launch: 1.25e+08\n" % ("0" * 64))
+    (tmp_path / "no_bytes.md").write_text("source_sha256: %s\n" % sha)
+    d = str(tmp_path)
+    assert bench.kernel_traffic(bench.NEAR_SOURCES, "near.md", d) == 1.25e8
+    assert bench.kernel_traffic(bench.NEAR_SOURCES, "stale.md", d) is None
+    assert bench.kernel_traffic(bench.NEAR_SOURCES, "no_bytes.md", d) is None
+    assert bench.kernel_traffic(bench.NEAR_SOURCES, "missing.md", d) is None
+    assert bench.kernel_traffic(bench.FAR_SOURCES, "near.md", d) is None
