@@ -30,8 +30,8 @@
  *    every result a call writes to them (u, the gradients) is complete in
  *    the context's stream order.
  *  - No call aborts or prints.  Every failure returns a status; the message
- *    is available from tc_last_error.  Device-side failures (a bounded wait
- *    that ran out, an index check) are reported by the next call that
+ *    is available from tc_last_error.  A device-side failure (the MAC
+ *    traversal's stack bound, TC_EDEVICE) is reported by the next call that
  *    synchronises, or by tc_sync.
  *  - Pairs with |x - y| == 0 contribute nothing.  When targets are the
  *    sources this is the n != m exclusion of eq. (1.3).
