@@ -138,6 +138,24 @@ tc_status tc_moments(tc_ctx* ctx, const double* f, const double* h, const double
 tc_status tc_eval(tc_ctx* ctx, const double* targets, int64_t M, double theta, int32_t p, double* u);
 
 /*
+ * tc_build + tc_moments + tc_eval (targets = the particles) from HOST
+ * arrays, for callers without device memory of their own.
+ *  x, f, h, nu : host, 3*N FP64 SoA each, in the caller's particle order;
+ *                pinned (page-locked) memory gives asynchronous copies,
+ *                pageable memory works too.  Read during the call only.
+ *  N, N0, theta, p : as for tc_build, tc_moments and tc_eval; all checked
+ *                before anything is copied or enqueued.
+ *  u           : host, 3*N FP64 SoA, written.
+ * The inputs are copied into library-owned device buffers on the context's
+ * stream, the three calls run on them, u is copied back, and the stream is
+ * synchronised (u is complete on return; a device-side failure is reported
+ * as by tc_sync).  Afterwards the context holds the tree, moments and lists
+ * as after the three calls, so tc_adjoint (with device arrays) may follow.
+ */
+tc_status tc_velocity_host(tc_ctx* ctx, const double* x, const double* f, const double* h, const double* nu,
+                           int64_t N, int32_t N0, double theta, int32_t p, double* u);
+
+/*
  * Adjoint of the last tc_eval with its structure frozen.  For
  *   L = sum_m g^m . u(x^m)
  * it returns dL/df, dL/dh, dL/dnu, dL/dx and dL/dt while the tree (cluster

@@ -20,6 +20,7 @@ SIGNATURES = {
     "tc_build": (_i32, [_vp, _vp, _i64, _i32]),
     "tc_moments": (_i32, [_vp, _vp, _vp, _vp, _i32]),
     "tc_eval": (_i32, [_vp, _vp, _i64, _dbl, _i32, _vp]),
+    "tc_velocity_host": (_i32, [_vp, _vp, _vp, _vp, _vp, _i64, _i32, _dbl, _i32, _vp]),
     "tc_adjoint": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "tc_update_positions": (_i32, [_vp, _vp]),
     "tc_eval_frozen": (_i32, [_vp, _vp]),

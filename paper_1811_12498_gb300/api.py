@@ -58,6 +58,16 @@ def _vec3(a, name, count=None):
     return a
 
 
+def _host3(a, name, count=None):
+    if not isinstance(a, torch.Tensor) or a.is_cuda:
+        raise TypeError("%s must be a host (CPU) tensor" % name)
+    if a.dtype != torch.float64 or a.dim() != 2 or a.shape[0] != 3 or not a.is_contiguous():
+        raise ValueError("%s must be a contiguous float64 tensor of shape (3, n)" % name)
+    if count is not None and a.shape[1] != count:
+        raise ValueError("%s has %d entries, expected %d" % (name, a.shape[1], count))
+    return a
+
+
 def _ptr(a):
     return None if a is None else ctypes.c_void_p(a.data_ptr())
 
@@ -121,6 +131,23 @@ class Treecode:
         self._chk(lib().tc_eval(self._h, _ptr(t), M, float(theta), p, _ptr(out)))
         self._M = M
         self._keep_t = t
+        return out
+
+    def velocity_host(self, x, f, h, nu, N0, theta, p, out=None):
+        """build + moments + eval from HOST tensors (tc_velocity_host): x, f,
+        h, nu are (3, N) float64 CPU tensors (pinned memory copies
+        asynchronously); returns u as a (3, N) CPU tensor, complete on return
+        (pinned when x is)."""
+        x = _host3(x, "x")
+        N = x.shape[1]
+        f, h, nu = (_host3(a, n, N) for a, n in ((f, "f"), (h, "h"), (nu, "nu")))
+        if out is None:
+            out = torch.empty((3, N), dtype=torch.float64, pin_memory=x.is_pinned())
+        _host3(out, "out", N)
+        self._chk(lib().tc_velocity_host(self._h, _ptr(x), _ptr(f), _ptr(h), _ptr(nu), N, int(N0), float(theta),
+                                         int(p), _ptr(out)))
+        self.N, self.p, self._M = N, int(p), N
+        self._keep, self._keep_t = (), None
         return out
 
     def update_positions(self, x):

@@ -121,7 +121,7 @@ static void release_all(tc_ctx* c)
                       &c->u_near, &c->flags, &c->adj_fkeys, &c->adj_fkeys_alt, &c->adj_fidx, &c->adj_fidx_alt,
                       &c->adj_febatch, &c->adj_nkeys, &c->adj_nkeys_alt, &c->adj_nidx, &c->adj_nidx_alt,
                       &c->adj_nebatch, &c->adj_hist, &c->adj_gs, &c->adj_gt, &c->adj_abar, &c->adj_fbar, &c->adj_lam,
-                      &c->adj_lamacc, &c->adj_gfar, &c->adj_gnear};
+                      &c->adj_lamacc, &c->adj_gfar, &c->adj_gnear, &c->host_in, &c->host_u};
     for (DevBuf* b : bufs) release(*b);
 }
 
@@ -589,6 +589,34 @@ tc_status tc_eval_frozen(tc_ctx* ctx, double* u)
     if (!u) return fail(ctx, TC_EINVAL, "tc_eval_frozen: u is NULL");
     if (!ctx->prepared) return fail(ctx, TC_ESTATE, "tc_eval_frozen: call tc_eval first");
     return eval_compute(ctx, u);
+}
+
+tc_status tc_velocity_host(tc_ctx* ctx, const double* x, const double* f, const double* h, const double* nu,
+                           int64_t N, int32_t N0, double theta, int32_t p, double* u)
+{
+    if (!ctx) return fail(nullptr, TC_EINVAL, "tc_velocity_host: ctx is NULL");
+    if (!x || !f || !h || !nu || !u) return fail(ctx, TC_EINVAL, "tc_velocity_host: a host pointer is NULL");
+    if (N < 1 || N >= ((int64_t)1 << 31))
+        return fail(ctx, TC_EINVAL, "tc_velocity_host: N = %lld out of [1, 2^31)", (long long)N);
+    if (N0 < 1) return fail(ctx, TC_EINVAL, "tc_velocity_host: N0 = %d must be >= 1", N0);
+    if (!(theta > 0.0 && theta < 1.0)) return fail(ctx, TC_EINVAL, "tc_velocity_host: theta = %g out of (0, 1)", theta);
+    if (p < 0 || p > kPMax) return fail(ctx, TC_EINVAL, "tc_velocity_host: p = %d out of [0, %d]", p, kPMax);
+    // the staging buffers may still be read by moment passes of an earlier call
+    TC_CK(join_moments(ctx), "tc_velocity_host");
+    cudaStream_t s = ctx->stream;
+    const size_t b3 = (size_t)3 * N * sizeof(double);
+    TC_CK(ensure(ctx->host_in, 4 * b3), "alloc staging");
+    TC_CK(ensure(ctx->host_u, b3), "alloc staging");
+    double* d_in = ptr<double>(ctx->host_in);
+    const double* src[4] = {x, f, h, nu};
+    for (int a = 0; a < 4; a++)
+        TC_CK(cudaMemcpyAsync(d_in + (size_t)a * 3 * N, src[a], b3, cudaMemcpyHostToDevice, s), "copy in");
+    tc_status st = tc_build(ctx, d_in, N, N0);
+    if (st == TC_OK) st = tc_moments(ctx, d_in + 3 * N, d_in + 6 * N, d_in + 9 * N, p);
+    if (st == TC_OK) st = tc_eval(ctx, nullptr, N, theta, p, ptr<double>(ctx->host_u));
+    if (st != TC_OK) return st;
+    TC_CK(cudaMemcpyAsync(u, ctx->host_u.p, b3, cudaMemcpyDeviceToHost, s), "copy out");
+    return tc_sync(ctx);
 }
 
 tc_status tc_eval(tc_ctx* ctx, const double* targets, int64_t M, double theta, int32_t p, double* u)

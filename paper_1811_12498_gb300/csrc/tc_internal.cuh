@@ -147,6 +147,7 @@ struct tc_ctx {
     int moved = 0;                      // positions replaced by tc_update_positions since tc_build
     tc::DevBuf tkeys, tkeys_alt, tperm, tperm_alt;  // disjoint targets
     tc::DevBuf ts;                      // 3*M FP64 sorted targets
+    tc::DevBuf host_in, host_u;         // tc_velocity_host: device copies of x, f, h, nu (12*N) and of u (3*N)
     tc::DevBuf nfar_e, nnear_e;         // per batch entry counts (int32)
     tc::DevBuf far_off, near_off;       // per batch exclusive offsets (int64)
     tc::DevBuf far_list, near_list;     // ListEntry

@@ -55,6 +55,7 @@ def test_host_argument_checks_without_gpu(lib):
                        None) == 1
     assert b"ctx is NULL" in lib.tc_last_error(None)
     assert lib.tc_update_positions(None, None) == 1
+    assert lib.tc_velocity_host(None, None, None, None, None, 10, 2, 0.5, 4, None) == 1
     assert lib.tc_eval_frozen(None, None) == 1
 
 
@@ -106,3 +107,5 @@ def test_no_fallback_without_the_library_or_a_gpu(monkeypatch, tmp_path):
         _lib.lib()
     with pytest.raises(TypeError, match="CUDA tensor"):
         api._vec3(torch.zeros(3, 4, dtype=torch.float64), "x", 4)
+    with pytest.raises(TypeError, match="host"):
+        api._host3([[0.0] * 4] * 3, "x", 4)

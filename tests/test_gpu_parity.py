@@ -374,3 +374,28 @@ def test_full_size_sphere_sweep_sampled(sphere4m, rec64):
             err = oracle.rel_l2(u[idx], ref)
             assert err <= TOL_MIXED_SURFACE, (p, theta, err)
     tc.close()
+
+
+# ------------------------------------------------------------ host buffers
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_velocity_from_host_buffers(prec):
+    """tc_velocity_host (host arrays in and out, copies inside the call) gives
+    the device path's result bit for bit, from pinned and from pageable
+    memory, and that result is the oracle's treecode."""
+    N, N0, p, theta = 4000, 150, 6, 0.5
+    x, f, h, nu = inputs.uniform_cube(N, inputs.SEED_BASE + 71)
+    hx, hf, hh, hn = (torch.from_numpy(np.ascontiguousarray(a.T)) for a in (x, f, h, nu))
+    tc = api.Treecode(prec)
+    u_dev = tc.build(hx.cuda(), N0).moments(hf.cuda(), hh.cuda(), hn.cuda(), p).eval(theta, p).cpu()
+    tc.close()
+    tc = api.Treecode(prec)
+    u_pinned = tc.velocity_host(*(a.pin_memory() for a in (hx, hf, hh, hn)), N0, theta, p)
+    u_pageable = tc.velocity_host(hx, hf, hh, hn, N0, theta, p)
+    tc.close()
+    assert u_pinned.is_pinned() and not u_pageable.is_pinned()
+    assert torch.equal(u_pinned, u_dev) and torch.equal(u_pageable, u_dev)
+    tree = oracle.Tree(x, N0, True)
+    tree.set_moments(f, h, nu, p)
+    ref = tree.treecode(x, theta, p)
+    assert oracle.rel_l2(u_pinned.numpy().T, ref) <= TOL[prec]
