@@ -8,13 +8,29 @@ This module is a ctypes wrapper around ``oracle.c`` (plain C11 + OpenMP),
 which follows the paper step by step:
 
 * ``direct``            -- eq. (1.3), the velocity sum, from its definition;
+* ``direct_grad``       -- gradients of sum g.u of that sum (f, h, nu, x),
+                           from the derivatives of S and T;
 * ``coulomb_coeffs``    -- recurrence (3.2) for the Coulomb coefficients b^k;
 * ``taylor_stokeslet``  -- eq. (3.4), explicit a^k_ij;
 * ``taylor_stresslet``  -- eq. (3.7), explicit a~^k_ijl;
 * ``far_contracted``    -- eqs. (4.4) and (4.9), the contracted far field;
 * ``far_explicit``      -- eq. (2.9), sum of a^k M^k + a~^k M~^k;
 * ``moments``           -- the cluster moments of Section 2;
-* ``Tree``              -- the octree of Section 5 and Algorithm 1.
+* ``Tree``              -- the octree of Section 5 and Algorithm 1
+                           (``treecode``), the same walk with the structure
+                           frozen at other positions (``treecode_frozen``),
+                           and the far-field particle count per target
+                           (``far_mass``).
+
+Every function is pinned in ``tests/test_oracle_pins.py`` to something other
+than itself: hand-computed values and the Stokes equations (``direct``),
+finite differences (``direct_grad``), closed forms and the Legendre
+generating function (``coulomb_coeffs``), an independent power-series
+expansion (``taylor_*``), the explicit sum and the truncation rate against
+the direct sum (``far_*``), the binomial translation identity (``moments``),
+structural invariants, a plain walk of Algorithm 1, limits that reduce to the
+direct sum, exact scaling laws and the paper's Tables 1 and 2 (``Tree``).
+Parity unpinned: only the internal flattening order of the moments.
 
 Arrays are float64, row-major ``(count, 3)``.  Multi-index quantities use
 cubes of shape ``(P+1, P+1, P+1)`` (zero where ||k|| > P).
