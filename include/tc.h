@@ -193,7 +193,10 @@ tc_status tc_adjoint(tc_ctx* ctx, const double* g, double* grad_f, double* grad_
  * tc_eval_frozen: the velocity at the (moved) particles with those lists,
  * written to u (device, 3*N FP64 SoA, caller's order).  Coincident pairs are
  * skipped by r = 0, as for disjoint targets.  The result equals Algorithm 1
- * when no position moved.  tc_build starts afresh.
+ * when no position moved.  A later tc_eval makes new decisions at the moved
+ * positions but keeps the old centres and radii (a moved particle may lie
+ * outside its cluster's radius, which weakens the MAC's error bound);
+ * tc_build starts afresh.
  */
 tc_status tc_update_positions(tc_ctx* ctx, const double* x);
 tc_status tc_eval_frozen(tc_ctx* ctx, double* u);
