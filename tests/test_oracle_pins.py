@@ -462,6 +462,28 @@ def test_treecode_exact_power_of_two_scaling():
         np.testing.assert_array_equal(u2, u1 / 2.0 ** power)
 
 
+@pytest.mark.parametrize("perm", [(1, 2, 0), (2, 0, 1), (0, 2, 1)])
+def test_treecode_covariant_under_axis_permutation(perm):
+    """Relabelling the axes (x_a -> x_perm(a) for positions and all three
+    weight vectors) maps the root cube, the cells, the clusters and every MAC
+    decision onto themselves, and S, T are isotropic tensors (eqs. 1.2a,b):
+    the treecode velocity is the relabelled velocity.  A term that treats one
+    axis differently (a wrong index in the recurrence, the moments or the
+    contraction) breaks this."""
+    x, f, h, nu = _system(3000, 57)
+    P = list(perm)
+    t1 = oracle.Tree(x, 90, True)
+    t1.set_moments(f, h, nu, 6)
+    t2 = oracle.Tree(x[:, P], 90, True)
+    t2.set_moments(f[:, P], h[:, P], nu[:, P], 6)
+    tg = x[::7]
+    u1, c1 = t1.treecode(tg, 0.5, counts=True)
+    u2, c2 = t2.treecode(tg[:, P], 0.5, counts=True)
+    for k in ("far", "near_leaves", "near_pairs"):
+        np.testing.assert_array_equal(c1[k], c2[k])
+    assert oracle.rel_l2(u2, u1[:, P]) <= 1e-13
+
+
 def _sampled_E(x, f, h, nu, N0, shrink, theta, ps, nsamp, seed):
     idx = inputs.sample_indices(x.shape[0], nsamp, seed)
     ud = oracle.direct(x, f, h, nu, targets=x[idx])
