@@ -462,6 +462,28 @@ def test_treecode_exact_power_of_two_scaling():
         np.testing.assert_array_equal(u2, u1 / 2.0 ** power)
 
 
+@pytest.mark.parametrize("shrink", [True, False])
+def test_treecode_exactly_translation_invariant_on_a_dyadic_grid(shrink):
+    """Positions on the grid 2^-20 Z^3 moved by (3, -5, 7): every sum and
+    difference the method forms from positions is exact before and after, so
+    the root cube moves with the points, the cells, centres and radii follow,
+    and the velocity (a function of differences only, eq. 1.3) is the same to
+    the last bit.  Anything measured from the origin instead of the root
+    corner or the cluster centre breaks this."""
+    rng = _rng(58)
+    N = 2500
+    x = rng.integers(0, 2 ** 20, (N, 3)).astype(np.float64) / 2 ** 20
+    f, h = rng.uniform(-1, 1, (N, 3)), rng.uniform(-1, 1, (N, 3))
+    nu = rng.standard_normal((N, 3))
+    shift = np.array([3.0, -5.0, 7.0])
+    us = []
+    for pos in (x, x + shift):
+        tree = oracle.Tree(pos, 70, shrink)
+        tree.set_moments(f, h, nu, 5)
+        us.append(tree.treecode(pos[::9], 0.5))
+    np.testing.assert_array_equal(us[0], us[1])
+
+
 @pytest.mark.parametrize("perm", [(1, 2, 0), (2, 0, 1), (0, 2, 1)])
 def test_treecode_covariant_under_axis_permutation(perm):
     """Relabelling the axes (x_a -> x_perm(a) for positions and all three
