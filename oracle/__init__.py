@@ -16,10 +16,12 @@ which follows the paper step by step:
 * ``far_contracted``    -- eqs. (4.4) and (4.9), the contracted far field;
 * ``far_explicit``      -- eq. (2.9), sum of a^k M^k + a~^k M~^k;
 * ``moments``           -- the cluster moments of Section 2;
-* ``Tree``              -- the octree of Section 5 and Algorithm 1
-                           (``treecode``), the same walk with the structure
-                           frozen at other positions (``treecode_frozen``),
-                           and the far-field particle count per target
+* ``Tree``              -- the octree of Section 5; per target, the
+                           interaction list of the MAC (eq. 5.1) and its sum
+                           (``treecode``, Algorithm 1's result); the same
+                           lists decided at other positions with moved
+                           particles (``treecode_frozen``), and the
+                           far-field particle count per target
                            (``far_mass``).
 
 Every function is pinned in ``tests/test_oracle_pins.py`` to something other
@@ -250,7 +252,9 @@ class Tree:
         return Mf.reshape((3,) + (p + 1,) * 3), Mt.reshape((3, 3) + (p + 1,) * 3)
 
     def treecode(self, targets, theta, p=None, counts=False, nthreads=0):
-        """Algorithm 1 at each target; returns u (M,3) [and per-target counts]."""
+        """Treecode velocity (Algorithm 1's result) at each target: its
+        interaction list by the MAC of eq. (5.1), then the sum of that list;
+        returns u (M,3) [and per-target counts]."""
         p = self.p if p is None else int(p)
         t = _c3(targets)
         M = t.shape[0]

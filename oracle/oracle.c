@@ -11,10 +11,14 @@
  * The oracle is deliberately plain and slow:
  *   - the direct sum is the definition of eq. (1.3) ("StoStre") with the
  *     kernel tensors S_ij and T_ijl of eqs. (1.2a,b) formed explicitly;
- *   - the treecode follows Algorithm 1 recursively, target by target, with
- *     the cluster moments of Section 2 computed from their definition, the
- *     Coulomb coefficients from recurrence (3.2), and the far field from the
- *     contracted forms (4.4) ("S_final") and (4.9) ("T_final");
+ *   - the treecode decides, target by target, which clusters are taken in
+ *     the far field and which leaves are summed directly (the MAC of
+ *     eq. 5.1 over the octree of Section 5, Algorithm 1's decisions), by an
+ *     explicit-stack walk that records an interaction list, and then sums
+ *     that list: cluster moments of Section 2 from their definition, the
+ *     Coulomb coefficients from recurrence (3.2), the far field from the
+ *     contracted forms (4.4) ("S_final") and (4.9) ("T_final"), the leaves
+ *     by the contracted direct sum of Section 4.1;
  *   - the explicit Taylor coefficients a^k_ij (3.4) and a~^k_ijl (3.7) are
  *     provided as a cross-check of the contracted forms.
  * Multi-indices are held in plain (P+1)^3 cubes, zero outside ||k|| <= P.
@@ -646,20 +650,65 @@ void orc_tree_export_moments(const orc_tree* t, int64_t node, double* Mf, double
     memcpy(Mt, t->Mt + (size_t)node * 9 * n3, sizeof(double) * 9 * n3);
 }
 
-/* Direct sum of one leaf in the contracted form of Section 4.1:      */
-/* u_i += f_i/r + d_i (s + t), s = (d.f)/r^3, t = (d.h)(d.nu)/r^5.     */
-static void leaf_direct(const orc_tree* t, const orc_node* nd, const double* xm, double* u)
+/* ------------------------------------------------------------------ */
+/* Per-target interaction set (Section 5, MAC of eq. 5.1).             */
+/*                                                                     */
+/* Starting from the root, a cluster C is accepted for the far-field   */
+/* approximation when the target sees it under r/R <= theta; a leaf    */
+/* that is not accepted is summed directly; any other cluster that is  */
+/* not accepted is replaced by its children.  The walk below keeps the */
+/* clusters still to be examined on an explicit stack (children pushed */
+/* in reverse octant order, so they are examined in octant order) and  */
+/* records every decision in an interaction list, in the order the     */
+/* decisions are made.  The velocity is then the sum over that list.   */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    int64_t node;
+    int far; /* 1: far-field approximation, 0: direct sum over the leaf */
+} orc_entry;
+
+/* Interaction list of the target at xd.  list has room for every node;
+ * returns the number of entries. */
+static int64_t interaction_list(const orc_tree* t, const double* xd, double theta, orc_entry* list, int64_t* stack)
+{
+    int64_t nlist = 0, top = 0;
+    stack[top++] = 0;
+    while (top > 0) {
+        const int64_t c = stack[--top];
+        const orc_node* nd = &t->nodes[c];
+        double d[3] = {xd[0] - nd->yc[0], xd[1] - nd->yc[1], xd[2] - nd->yc[2]};
+        double R2 = (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2];
+        if ((R2 > 0.0) && (nd->rc2 <= (theta * theta) * R2)) {
+            list[nlist].node = c;
+            list[nlist].far = 1;
+            nlist++;
+        } else if (nd->nchild == 0) {
+            list[nlist].node = c;
+            list[nlist].far = 0;
+            nlist++;
+        } else {
+            for (int o = nd->nchild - 1; o >= 0; o--) stack[top++] = nd->child[o];
+        }
+    }
+    return nlist;
+}
+
+/* Direct sum of one leaf at xm in the contracted form of Section 4.1:
+ * u_i += f_i/r + d_i (s + t), s = (d.f)/r^3, t = (d.h)(d.nu)/r^5, with the
+ * leaf's sources at positions y (row-major), pairs with r == 0 skipped. */
+static void leaf_direct(const orc_tree* t, const orc_node* nd, const double* y_all, const double* f_all,
+                        const double* h_all, const double* nu_all, const double* xm, double* u)
 {
     for (int64_t q = 0; q < nd->count; q++) {
         int64_t n = t->order[nd->begin + q];
-        const double* y = t->x + 3 * n;
+        const double* y = y_all + 3 * n;
         double d[3] = {xm[0] - y[0], xm[1] - y[1], xm[2] - y[2]};
         double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
         if (r2 == 0.0) continue;
         double r = sqrt(r2);
-        const double* f = t->f + 3 * n;
-        const double* h = t->h + 3 * n;
-        const double* nu = t->nu + 3 * n;
+        const double* f = f_all + 3 * n;
+        const double* h = h_all + 3 * n;
+        const double* nu = nu_all + 3 * n;
         double s = (d[0] * f[0] + d[1] * f[1] + d[2] * f[2]) / (r * r2);
         double tt = (d[0] * h[0] + d[1] * h[1] + d[2] * h[2]) * (d[0] * nu[0] + d[1] * nu[1] + d[2] * nu[2]) /
                     (r2 * r2 * r);
@@ -667,60 +716,74 @@ static void leaf_direct(const orc_tree* t, const orc_node* nd, const double* xm,
     }
 }
 
+/* Far field of cluster moments stored at order P (cubes Mf: 3 x (P+1)^3,
+ * Mt: 9 x (P+1)^3), evaluated at order p <= P by eqs. (4.4) + (4.9). */
+static void far_at_order(const double* d, int p, int P, const double* MfP, const double* MtP, double* uf)
+{
+    if (p == P) {
+        orc_far_contracted(d, p, MfP, MtP, uf);
+        return;
+    }
+    int N3 = (P + 1) * (P + 1) * (P + 1), m3 = (p + 1) * (p + 1) * (p + 1);
+    double* Mf = (double*)malloc(sizeof(double) * 3 * m3);
+    double* Mt = (double*)malloc(sizeof(double) * 9 * m3);
+    for (int comp = 0; comp < 12; comp++)
+        for (int k1 = 0; k1 <= p; k1++)
+            for (int k2 = 0; k2 <= p; k2++)
+                for (int k3 = 0; k3 <= p; k3++) {
+                    double v = 0.0;
+                    if (k1 + k2 + k3 <= p)
+                        v = comp < 3 ? MfP[comp * N3 + cube_idx(P, k1, k2, k3)]
+                                     : MtP[(comp - 3) * N3 + cube_idx(P, k1, k2, k3)];
+                    if (comp < 3)
+                        Mf[comp * m3 + cube_idx(p, k1, k2, k3)] = v;
+                    else
+                        Mt[(comp - 3) * m3 + cube_idx(p, k1, k2, k3)] = v;
+                }
+    orc_far_contracted(d, p, Mf, Mt, uf);
+    free(Mf);
+    free(Mt);
+}
+
 typedef struct {
     int64_t nfar, nnear_leaves, nnear_pairs;
 } orc_counts;
 
-/* Algorithm 1, subroutine compute-velocity(x, C). */
-static void compute_velocity(const orc_tree* t, int64_t c, const double* xm, double theta, int p, double* u,
+/* What a sum over an interaction list reads: source positions and weights,
+ * per-node moments of order P about the nodes' centres, evaluation order p. */
+typedef struct {
+    const orc_tree* t;
+    const double *x, *f, *h, *nu;
+    const double *Mf, *Mt;
+    int P, p;
+} orc_sources;
+
+/* u at xm = sum over the interaction list, in list order: far entries by
+ * eqs. (4.4) + (4.9) at d = xm - y_c, near entries by Section 4.1. */
+static void sum_interactions(const orc_sources* s, const orc_entry* list, int64_t nlist, const double* xm, double* u,
                              orc_counts* cnt)
 {
-    const orc_node* nd = &t->nodes[c];
-    double d[3] = {xm[0] - nd->yc[0], xm[1] - nd->yc[1], xm[2] - nd->yc[2]};
-    double R2 = (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2];
-    int mac = (R2 > 0.0) && (nd->rc2 <= (theta * theta) * R2);
-    if (mac) {
-        int n3 = (t->p + 1) * (t->p + 1) * (t->p + 1);
-        double uf[3];
-        if (p == t->p) {
-            orc_far_contracted(d, p, t->Mf + (size_t)c * 3 * n3, t->Mt + (size_t)c * 9 * n3, uf);
+    const int64_t N3 = (int64_t)(s->P + 1) * (s->P + 1) * (s->P + 1);
+    for (int64_t e = 0; e < nlist; e++) {
+        const orc_node* nd = &s->t->nodes[list[e].node];
+        if (list[e].far) {
+            double d[3] = {xm[0] - nd->yc[0], xm[1] - nd->yc[1], xm[2] - nd->yc[2]}, uf[3];
+            far_at_order(d, s->p, s->P, s->Mf + (size_t)list[e].node * 3 * N3, s->Mt + (size_t)list[e].node * 9 * N3,
+                         uf);
+            for (int i = 0; i < 3; i++) u[i] += uf[i];
+            if (cnt) cnt->nfar++;
         } else {
-            /* evaluate at a lower order than stored: copy the needed part */
-            int m3 = (p + 1) * (p + 1) * (p + 1);
-            double* Mf = (double*)malloc(sizeof(double) * 3 * m3);
-            double* Mt = (double*)malloc(sizeof(double) * 9 * m3);
-            for (int comp = 0; comp < 12; comp++)
-                for (int k1 = 0; k1 <= p; k1++)
-                    for (int k2 = 0; k2 <= p; k2++)
-                        for (int k3 = 0; k3 <= p; k3++) {
-                            double v = (k1 + k2 + k3 <= p)
-                                           ? (comp < 3 ? t->Mf[(size_t)c * 3 * n3 + comp * n3 + cube_idx(t->p, k1, k2, k3)]
-                                                       : t->Mt[(size_t)c * 9 * n3 + (comp - 3) * n3 +
-                                                               cube_idx(t->p, k1, k2, k3)])
-                                           : 0.0;
-                            if (comp < 3)
-                                Mf[comp * m3 + cube_idx(p, k1, k2, k3)] = v;
-                            else
-                                Mt[(comp - 3) * m3 + cube_idx(p, k1, k2, k3)] = v;
-                        }
-            orc_far_contracted(d, p, Mf, Mt, uf);
-            free(Mf);
-            free(Mt);
+            leaf_direct(s->t, nd, s->x, s->f, s->h, s->nu, xm, u);
+            if (cnt) {
+                cnt->nnear_leaves++;
+                cnt->nnear_pairs += nd->count;
+            }
         }
-        for (int i = 0; i < 3; i++) u[i] += uf[i];
-        if (cnt) cnt->nfar++;
-    } else if (nd->nchild == 0) {
-        leaf_direct(t, nd, xm, u);
-        if (cnt) {
-            cnt->nnear_leaves++;
-            cnt->nnear_pairs += nd->count;
-        }
-    } else {
-        for (int o = 0; o < nd->nchild; o++) compute_velocity(t, nd->child[o], xm, theta, p, u, cnt);
     }
 }
 
-/* Treecode velocity at M targets tx (row-major (M,3)).  Requires moments of
+/* Treecode velocity at M targets tx (row-major (M,3)): the interaction list
+ * of each target (decided at the target), then its sum.  Requires moments of
  * order >= p.  Optional per-target counters (may be NULL). Returns 0 or -1. */
 int orc_treecode(const orc_tree* t, const double* tx, int64_t M, double theta, int p, double* u, int64_t* nfar,
                  int64_t* nnear_leaves, int64_t* nnear_pairs, int nthreads)
@@ -730,36 +793,46 @@ int orc_treecode(const orc_tree* t, const double* tx, int64_t M, double theta, i
     if (nthreads > 0) omp_set_num_threads(nthreads);
 #endif
     (void)nthreads;
-#pragma omp parallel for schedule(dynamic, 4)
-    for (int64_t m = 0; m < M; m++) {
-        double acc[3] = {0, 0, 0};
-        orc_counts cnt = {0, 0, 0};
-        compute_velocity(t, 0, tx + 3 * m, theta, p, acc, &cnt);
-        for (int i = 0; i < 3; i++) u[3 * m + i] = acc[i];
-        if (nfar) nfar[m] = cnt.nfar;
-        if (nnear_leaves) nnear_leaves[m] = cnt.nnear_leaves;
-        if (nnear_pairs) nnear_pairs[m] = cnt.nnear_pairs;
+    const orc_sources s = {t, t->x, t->f, t->h, t->nu, t->Mf, t->Mt, t->p, p};
+#pragma omp parallel
+    {
+        orc_entry* list = (orc_entry*)malloc(sizeof(orc_entry) * (size_t)t->nnodes);
+        int64_t* stack = (int64_t*)malloc(sizeof(int64_t) * (size_t)t->nnodes);
+#pragma omp for schedule(dynamic, 4)
+        for (int64_t m = 0; m < M; m++) {
+            double acc[3] = {0, 0, 0};
+            orc_counts cnt = {0, 0, 0};
+            const int64_t n = interaction_list(t, tx + 3 * m, theta, list, stack);
+            sum_interactions(&s, list, n, tx + 3 * m, acc, &cnt);
+            for (int i = 0; i < 3; i++) u[3 * m + i] = acc[i];
+            if (nfar) nfar[m] = cnt.nfar;
+            if (nnear_leaves) nnear_leaves[m] = cnt.nnear_leaves;
+            if (nnear_pairs) nnear_pairs[m] = cnt.nnear_pairs;
+        }
+        free(list);
+        free(stack);
     }
     return 0;
 }
 
-/* Sum of the counts of the far clusters of one target (partition check). */
-static int64_t far_mass_rec(const orc_tree* t, int64_t c, const double* xm, double theta)
-{
-    const orc_node* nd = &t->nodes[c];
-    double d[3] = {xm[0] - nd->yc[0], xm[1] - nd->yc[1], xm[2] - nd->yc[2]};
-    double R2 = (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2];
-    if ((R2 > 0.0) && (nd->rc2 <= (theta * theta) * R2)) return nd->count;
-    if (nd->nchild == 0) return 0;
-    int64_t s = 0;
-    for (int o = 0; o < nd->nchild; o++) s += far_mass_rec(t, nd->child[o], xm, theta);
-    return s;
-}
-
+/* Sum of the counts of the far clusters of each target (partition check). */
 void orc_far_mass(const orc_tree* t, const double* tx, int64_t M, double theta, int64_t* mass)
 {
-#pragma omp parallel for schedule(dynamic, 16)
-    for (int64_t m = 0; m < M; m++) mass[m] = far_mass_rec(t, 0, tx + 3 * m, theta);
+#pragma omp parallel
+    {
+        orc_entry* list = (orc_entry*)malloc(sizeof(orc_entry) * (size_t)t->nnodes);
+        int64_t* stack = (int64_t*)malloc(sizeof(int64_t) * (size_t)t->nnodes);
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t m = 0; m < M; m++) {
+            const int64_t n = interaction_list(t, tx + 3 * m, theta, list, stack);
+            int64_t s = 0;
+            for (int64_t e = 0; e < n; e++)
+                if (list[e].far) s += t->nodes[list[e].node].count;
+            mass[m] = s;
+        }
+        free(list);
+        free(stack);
+    }
 }
 
 int orc_max_threads(void)
@@ -774,54 +847,13 @@ int orc_max_threads(void)
 /* ------------------------------------------------------------------ */
 /* Frozen-structure evaluation, for finite-difference checks of the    */
 /* adjoint.  The tree built from the original positions keeps its      */
-/* cluster membership, centres y_c and radii; every target takes the   */
-/* MAC decisions of Algorithm 1 at its decision position td; the       */
+/* cluster membership, centres y_c and radii; every target's           */
+/* interaction list is decided at its decision position td; the        */
 /* moments (Section 2) and the direct sums (Section 4.1) use the moved  */
 /* source positions xe, and far fields and direct sums are evaluated   */
 /* at the moved target positions te.  With xe = x and td = te this is  */
 /* orc_treecode.                                                       */
 /* ------------------------------------------------------------------ */
-typedef struct {
-    const orc_tree* t;
-    const double *xe, *f, *h, *nu;
-    const double *Mf, *Mt; /* moments at xe, per node */
-    int p, n3;
-    double theta;
-} orc_frozen;
-
-static void compute_velocity_frozen(const orc_frozen* z, int64_t c, const double* xd, const double* xm, double* u)
-{
-    const orc_tree* t = z->t;
-    const orc_node* nd = &t->nodes[c];
-    double dd[3] = {xd[0] - nd->yc[0], xd[1] - nd->yc[1], xd[2] - nd->yc[2]};
-    double R2 = (dd[0] * dd[0] + dd[1] * dd[1]) + dd[2] * dd[2];
-    int mac = (R2 > 0.0) && (nd->rc2 <= (z->theta * z->theta) * R2);
-    if (mac) {
-        double d[3] = {xm[0] - nd->yc[0], xm[1] - nd->yc[1], xm[2] - nd->yc[2]};
-        double uf[3];
-        orc_far_contracted(d, z->p, z->Mf + (size_t)c * 3 * z->n3, z->Mt + (size_t)c * 9 * z->n3, uf);
-        for (int i = 0; i < 3; i++) u[i] += uf[i];
-    } else if (nd->nchild == 0) {
-        for (int64_t q = 0; q < nd->count; q++) {
-            int64_t n = t->order[nd->begin + q];
-            const double* y = z->xe + 3 * n;
-            double d[3] = {xm[0] - y[0], xm[1] - y[1], xm[2] - y[2]};
-            double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-            if (r2 == 0.0) continue;
-            double r = sqrt(r2);
-            const double* f = z->f + 3 * n;
-            const double* h = z->h + 3 * n;
-            const double* nu = z->nu + 3 * n;
-            double s = (d[0] * f[0] + d[1] * f[1] + d[2] * f[2]) / (r * r2);
-            double tt = (d[0] * h[0] + d[1] * h[1] + d[2] * h[2]) * (d[0] * nu[0] + d[1] * nu[1] + d[2] * nu[2]) /
-                        (r2 * r2 * r);
-            for (int i = 0; i < 3; i++) u[i] += f[i] / r + d[i] * (s + tt);
-        }
-    } else {
-        for (int o = 0; o < nd->nchild; o++) compute_velocity_frozen(z, nd->child[o], xd, xm, u);
-    }
-}
-
 int orc_treecode_frozen(const orc_tree* t, const double* xe, const double* f, const double* h, const double* nu, int p,
                         const double* td, const double* te, int64_t M, double theta, double* u, int nthreads)
 {
@@ -839,12 +871,20 @@ int orc_treecode_frozen(const orc_tree* t, const double* xe, const double* f, co
         orc_moments(xe, f, h, nu, t->order + nd->begin, nd->count, nd->yc, p, Mf + (size_t)c * 3 * n3,
                     Mt + (size_t)c * 9 * n3);
     }
-    orc_frozen z = {t, xe, f, h, nu, Mf, Mt, p, n3, theta};
-#pragma omp parallel for schedule(dynamic, 4)
-    for (int64_t m = 0; m < M; m++) {
-        double acc[3] = {0, 0, 0};
-        compute_velocity_frozen(&z, 0, td + 3 * m, te + 3 * m, acc);
-        for (int i = 0; i < 3; i++) u[3 * m + i] = acc[i];
+    const orc_sources s = {t, xe, f, h, nu, Mf, Mt, p, p};
+#pragma omp parallel
+    {
+        orc_entry* list = (orc_entry*)malloc(sizeof(orc_entry) * (size_t)t->nnodes);
+        int64_t* stack = (int64_t*)malloc(sizeof(int64_t) * (size_t)t->nnodes);
+#pragma omp for schedule(dynamic, 4)
+        for (int64_t m = 0; m < M; m++) {
+            double acc[3] = {0, 0, 0};
+            const int64_t n = interaction_list(t, td + 3 * m, theta, list, stack);
+            sum_interactions(&s, list, n, te + 3 * m, acc, NULL);
+            for (int i = 0; i < 3; i++) u[3 * m + i] = acc[i];
+        }
+        free(list);
+        free(stack);
     }
     free(Mf);
     free(Mt);

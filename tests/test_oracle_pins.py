@@ -595,3 +595,70 @@ def test_direct_gradient_matches_finite_differences():
                 am[i, a] -= eps
                 fd[i, a] = (L(**{key: ap}) - L(**{key: am})) / (2 * eps)
         assert oracle.rel_l2(gr[key], fd) < tol, (key, oracle.rel_l2(gr[key], fd))
+
+
+def _frozen_case():
+    x, f, h, nu = _system(1500, 57)
+    tree = oracle.Tree(x, 60, True)
+    xe = x + 5e-3 * _rng(59).standard_normal(x.shape)
+    return tree, x, xe, f, h, nu
+
+
+def test_frozen_map_with_moved_particles_converges_to_the_moved_direct_sum():
+    """Moved particles (xe = x + 5e-3 noise), lists decided at the original
+    positions, theta = 0.5: the far clusters' moments (Section 2) are sums
+    over the moved sources, and the far field (eqs. 4.4 + 4.9) is the Taylor
+    series of the kernels about the unmoved centre evaluated at the moved
+    target, so the map converges to the direct sum (eq. 1.3) at the moved
+    positions geometrically in p.  Moments taken at the unmoved sources, or
+    d formed from the decision position instead of the moved target, leave an
+    O(displacement) floor (about 2e-3 here) that no p removes."""
+    tree, x, xe, f, h, nu = _frozen_case()
+    ud = oracle.direct(xe, f, h, nu)
+    errs = [oracle.rel_l2(tree.treecode_frozen(xe, f, h, nu, p, x, xe, 0.5), ud) for p in (2, 4, 6, 8, 10)]
+    assert all(b < 0.5 * a for a, b in zip(errs, errs[1:])), errs
+    assert errs[-1] < 1e-4, errs
+
+
+def test_frozen_map_far_entries_are_the_moved_moments_at_the_moved_target():
+    """Each target's frozen velocity, rebuilt here from the oracle's
+    primitives: the clusters it takes in the far field and the leaves it sums
+    directly are decided at its original position (MAC of eq. 5.1, a plain
+    Python walk of the exported tree); each far cluster contributes the
+    contracted far field (4.4) + (4.9) at d = (moved target - y_c) of the
+    moments (Section 2) of its moved sources, each near leaf the direct sum
+    over its moved sources.  The rebuild equals the oracle to rounding; the
+    two plausible slips (moments of the unmoved sources, d from the unmoved
+    target) are shown to move the result by far more than that tolerance."""
+    tree, x, xe, f, h, nu = _frozen_case()
+    theta, p = 0.5, 6
+    nd, order = tree.nodes(), tree.order()
+
+    def rebuild(m, mom_pos, d_pos):
+        far, near, stack = [], [], [0]
+        while stack:
+            c = stack.pop()
+            d = x[m] - nd["yc"][c]
+            R2 = d @ d
+            if R2 > 0 and nd["rc2"][c] <= theta * theta * R2:
+                far.append(c)
+            elif nd["nchild"][c] == 0:
+                near.append(c)
+            else:
+                stack.extend(reversed(nd["child"][c][:nd["nchild"][c]].tolist()))
+        assert far and near
+        u = np.zeros(3)
+        for c in far:
+            idx = order[nd["begin"][c]:nd["begin"][c] + nd["count"][c]]
+            Mf, Mt = oracle.moments(mom_pos[idx], f[idx], h[idx], nu[idx], nd["yc"][c], p)
+            u += oracle.far_contracted(d_pos[m] - nd["yc"][c], p, Mf, Mt)
+        for c in near:
+            idx = order[nd["begin"][c]:nd["begin"][c] + nd["count"][c]]
+            u += oracle.direct(xe[idx], f[idx], h[idx], nu[idx], targets=xe[m][None])[0]
+        return u
+
+    ms = np.arange(0, 1500, 97)
+    u = tree.treecode_frozen(xe, f, h, nu, p, x, xe, theta)[ms]
+    assert oracle.rel_l2(np.array([rebuild(m, xe, xe) for m in ms]), u) < 1e-13
+    for slip in ((x, xe), (xe, x)):
+        assert oracle.rel_l2(np.array([rebuild(m, *slip) for m in ms]), u) > 1e-4
