@@ -32,7 +32,8 @@ METRIC = "targets/s at N=1M, p=8 (rel-L2<=1e-6 vs FP64 direct); fwd+adjoint s/st
 UNIT = "targets/s"
 L2_FLUSH_BYTES = 256 << 20
 # nominal GB300 arithmetic peaks (152 SMs at 2070 MHz): FP64 2 FMA/clk/SM,
-# FP32 128 FMA/clk/SM
+# FP32 128 FMA/clk/SM; the roofline fractions are taken against the peaks
+# measured in the run itself (tc_fma_peak) and reported beside these
 PEAK_FP64_TFLOPS = 1.25
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
@@ -62,6 +63,41 @@ def far_flops_per_interaction(p):
     return float(rec), float(con)
 
 
+def folded_coefficients(P):
+    """Coefficients with k1 <= 1 of orders 0..P (the harmonic subset the
+    folded tables keep): (P + 1)^2."""
+    return (P + 1) ** 2
+
+
+# Algorithmic flops of the adjoint's per-unit work (FMA = 2), from the
+# formulas of the adjoint (the header of csrc/tc_adjoint.cu):
+# near field, target side, per (target, source) pair: d 3, r^2 5, 1/r 1,
+# r^-2, r^-3, r^-5, r^-7 4, the dot products g.f, g.d, d.f, d.h, d.nu 25,
+# s and t 3 and their sum 1, c3, c4, c5 5, c1 8, the gradient
+# d c1 + g (s + t) + f c3 + h c4 + nu c5 27, its accumulation 3: 85;
+# near field, source side, per pair: the same 85 for dL/dy plus dL/df
+# (g / r + d c3: 9, accumulated 3), dL/dh (d c4: 3 + 3) and dL/dnu
+# (d c5: 3 + 3): 109;
+# far field, target side, per (target, cluster) interaction: the recurrence
+# one order further (to p + 3) and, per coefficient k, alpha^k = g.(A^k +
+# d' B^k) 30, beta_l^k = sum_i g_i B_il^k 18, the sums b^k beta^k 6 and
+# (k_l + 1) b^{k+e_l} alpha^k 9: 63.
+NEAR_ADJ_TARGET_FLOPS = 85.0
+NEAR_ADJ_SOURCE_FLOPS = 109.0
+FAR_ADJ_PER_COEF_FLOPS = 63.0
+
+
+def far_adj_target_flops(p):
+    """(folded, unfolded) flops of one far interaction of the adjoint's
+    target side: on the harmonic subset the kernel works on (recurrence as in
+    far_flops_per_interaction, one order further), and on the full set of
+    C(p+5, 3) coefficients with the unfolded recurrence 11 C(p+6, 3)."""
+    rec_next, _ = far_flops_per_interaction(p + 1)
+    folded = rec_next + FAR_ADJ_PER_COEF_FLOPS * folded_coefficients(p + 2)
+    unfolded = 11 * ncoef(p + 3) + FAR_ADJ_PER_COEF_FLOPS * ncoef(p + 2)
+    return float(folded), float(unfolded)
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -74,6 +110,8 @@ def parse():
     ap.add_argument("--theta", type=float, default=0.5)
     ap.add_argument("--N0", type=int, default=2000)
     ap.add_argument("--cpu-sample", type=int, default=16384, help="targets the oracle evaluates for cpu_baseline")
+    ap.add_argument("--cpu-sample-1t", type=int, default=1024,
+                    help="targets the oracle evaluates for the one-thread cpu_baseline")
     ap.add_argument("--ref-sample", type=int, default=2048, help="targets per step of the reference arm")
     ap.add_argument("--error-samples", type=int, default=10000, help="targets of the FP64 direct-sum error check")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -186,13 +224,16 @@ def kernel_traffic(sources, profile, profiles_dir=None):
     return float(m_b.group(1))
 
 
-def cpu_baseline(x, f, h, nu, args, sample):
-    """The oracle as it stands, on this host's cores: tree + moments over all
-    N particles, Algorithm 1 at `sample` seeded targets; eval time scaled to N."""
+def cpu_baseline(x, f, h, nu, args, sample, threads=0):
+    """The oracle as it stands, on this host's cores (threads = 0: all of
+    them): tree + moments over all N particles, the treecode at `sample`
+    seeded targets; the evaluation time extrapolated to N targets."""
     import oracle
     from paper_1811_12498_gb300 import inputs
     N = x.shape[0]
     idx = inputs.sample_indices(N, sample, 4242)
+    oracle.set_threads(threads)
+    cores = oracle.max_threads()
     t0 = time.perf_counter()
     tree = oracle.Tree(x, args.N0, True)
     t1 = time.perf_counter()
@@ -200,10 +241,12 @@ def cpu_baseline(x, f, h, nu, args, sample):
     t2 = time.perf_counter()
     u = tree.treecode(x[idx], args.theta, args.p)
     t3 = time.perf_counter()
+    oracle.set_threads(0)
     full = (t1 - t0) + (t2 - t1) + (t3 - t2) * N / len(idx)
-    return {"value": N / full, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
-            "sample": "oracle tree + order-%d moments over all %d particles (%.1f s), Algorithm 1 at %d seeded "
-                      "targets (%.1f s) scaled to %d targets" % (args.p, N, t2 - t0, len(idx), t3 - t2, N),
+    return {"value": N / full, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "oracle tree + order-%d moments over all %d particles (%.1f s), treecode at %d seeded "
+                      "targets (%.1f s), extrapolated to %d targets; %d thread(s)"
+                      % (args.p, N, t2 - t0, len(idx), t3 - t2, N, cores),
             "seconds": t3 - t0}, idx, u
 
 
@@ -221,10 +264,14 @@ def run_reference(args):
             vals.append(r)
     v = statistics.mean(r["value"] for r in vals)
     ms = args.N / v * 1e3
+    cfg = config(args)
+    cfg["reference_timing"] = ("extrapolated: each step times the oracle's tree and moments over all %d particles "
+                               "and its treecode at %d sampled targets, scaled to %d targets"
+                               % (args.N, args.ref_sample, args.N))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config(args),
+            "config": cfg,
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": vals[0]["cores"], "kind": "oracle",
                              "sample": vals[0]["sample"]},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -267,11 +314,41 @@ def bench_fwd_adjoint(flush, stream, steps=3):
         if k > 0:
             fwd.append(e0.elapsed_time(em))
             tot.append(e0.elapsed_time(e1))
+    # each adjoint kernel's own duration (phase events, one more step), and
+    # its counted work against the measured FP32 peak
+    tc.profile(True)
+    flush.fill_(1)
+    tc.build(d[0], N0).moments(d[1], d[2], d[3], p)
+    tc.eval(theta, p, out=u)
+    tc.adjoint(g)
+    ph = tc.phase_times()
+    tc.profile(False)
+    st = tc.stats()
     tc.close()
+    peak = api.fma_peak("mixed", stream)
+    far_f, far_u = far_adj_target_flops(p)
+
+    def roof(kernel, flops, ms_k, unit):
+        tf = flops / (ms_k / 1e3) / 1e12
+        return {"kernel": kernel, "bound": "alu", "achieved": tf, "peak": peak, "unit": "TFLOP/s", "frac": tf / peak,
+                "flops_per_launch": flops, "launch_ms": ms_k, "work_unit": unit}
+
+    rooflines = [
+        roof("k_near_adj_target32", NEAR_ADJ_TARGET_FLOPS * st["near_pairs"], ph["adj_near_target"],
+             "%g flops per near pair" % NEAR_ADJ_TARGET_FLOPS),
+        roof("k_near_adj_source32", NEAR_ADJ_SOURCE_FLOPS * st["near_pairs"], ph["adj_near_source"],
+             "%g flops per near pair" % NEAR_ADJ_SOURCE_FLOPS),
+        roof("k_far_adj_target32", far_f * st["far_interactions"], ph["adj_far_target"],
+             "%g flops per far interaction on the folded coefficients (%g on all C(p+5,3))" % (far_f, far_u)),
+    ]
     ms = statistics.mean(tot)
     return {"workload": "8 Gaussian clusters N=262144, sigma=0.05, p=8, theta=0.5, N0=2000, mixed",
             "s_per_step": ms / 1e3, "fwd_ms": statistics.mean(fwd), "adjoint_ms": ms - statistics.mean(fwd),
-            "steps": steps, "grads": "f, h, nu, x"}
+            "steps": steps, "grads": "f, h, nu, x",
+            "adjoint_phases_ms": {k: v for k, v in ph.items() if k.startswith("adj_")},
+            "interactions": {"near_pairs": st["near_pairs"], "far": st["far_interactions"]},
+            "roofline": rooflines,
+            "peak_kind": "measured FP32 FMA peak (tc_fma_peak)"}
 
 
 def bench_sphere_sweep(flush, stream):
@@ -470,6 +547,7 @@ def main():
     for _ in range(args.warmup):
         step(dx)
     torch.cuda.synchronize()
+    peaks = {"fp32": [api.fma_peak("mixed", stream)], "fp64": [api.fma_peak("fp64", stream)]}
     tc.profile(True)
     clocks = Clocks(local)
     barrier()
@@ -491,6 +569,8 @@ def main():
     barrier()
     clk = clocks.stop()
     launches = api.kernel_launches() - launches0
+    peaks["fp32"].append(api.fma_peak("mixed", stream))
+    peaks["fp64"].append(api.fma_peak("fp64", stream))
     ms = max_over_ranks(statistics.mean(times), dist, "cuda")
     value = whole_job_value(N, world, ms)
     st = tc.stats()
@@ -510,7 +590,9 @@ def main():
     ph = {k: statistics.mean(pp[k] for pp in serial if pp[k] is not None)
           for k in serial[0] if serial[0][k] is not None}
 
-    # end to end through the public API: pinned host inputs -> device -> step -> host u
+    # end to end through the C ABI's host-buffer call (tc_velocity_host): the
+    # pinned host inputs are copied in, the step runs, u is copied back to a
+    # pinned host array, all inside the one call and the timed region
     uh = torch.empty((3, N), dtype=torch.float64).pin_memory()
     e2e_times = []
     for k in range(args.steps + 1):
@@ -518,14 +600,13 @@ def main():
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        dd = [a.to("cuda", non_blocking=True) for a in hx]
-        step(dd)
-        uh.copy_(u, non_blocking=True)
+        tc.velocity_host(hx[0], hx[1], hx[2], hx[3], N0, theta, p, out=uh)
         e1.record(stream)
         e1.synchronize()
         if k > 0:
             e2e_times.append(e0.elapsed_time(e1))
     e2e_ms = max_over_ranks(statistics.mean(e2e_times), dist, "cuda")
+    e2e_same = bool(torch.equal(uh, u.cpu()))
 
     if rank != 0:
         tc.close()
@@ -548,9 +629,13 @@ def main():
     fp64 = args.precision == "fp64"
     far_ms = ph.get("far")
     near_ms = ph.get("near")
-    peak = PEAK_FP64_TFLOPS if fp64 else PEAK_FP32_TFLOPS
-    peak_kind = ("nominal FP64 (152 SMs x 2 FMA/clk x 2.07 GHz)" if fp64 else
-                 "nominal FP32 (152 SMs x 128 FMA/clk x 2.07 GHz)")
+    # measured peak of the run (best of the FMA-chain probes before and after
+    # the timed steps), the nominal one beside it
+    peak = max(peaks["fp64" if fp64 else "fp32"])
+    nominal = PEAK_FP64_TFLOPS if fp64 else PEAK_FP32_TFLOPS
+    peak_kind = ("measured FP64 FMA peak of this run (tc_fma_peak); nominal 1.25 (152 SMs x 2 FMA/clk x 2.07 GHz)"
+                 if fp64 else "measured FP32 FMA peak of this run (tc_fma_peak); nominal 80.5 (152 SMs x 128 "
+                              "FMA/clk x 2.07 GHz)")
     near_flops = 43.0 * st["near_pairs"]
     near_tf = near_flops / (near_ms / 1e3) / 1e12
     rec_unit, con_unit = far_flops_per_interaction(p)
@@ -565,11 +650,13 @@ def main():
     if dominant_near:
         roof = {"bound": "alu", "kernel": near_kernel + " (near field, 43 flops per pair)", "achieved": near_tf,
                 "peak": peak, "unit": "TFLOP/s", "peak_kind": peak_kind, "frac": near_tf / peak,
+                "nominal_peak": nominal, "frac_of_nominal": near_tf / nominal,
                 "traffic": None if fp64 else kernel_traffic(NEAR_SOURCES, "near_field_uniform_cube_524k.md"),
                 "flops_per_launch": near_flops, "launch_ms": near_ms}
     else:
         roof = {"bound": "alu", "kernel": "k_far (far field, folded recurrence + contraction)", "achieved": far_tf,
                 "peak": peak, "unit": "TFLOP/s", "peak_kind": peak_kind, "frac": far_tf / peak,
+                "nominal_peak": nominal, "frac_of_nominal": far_tf / nominal,
                 "traffic": None if fp64 else kernel_traffic(FAR_SOURCES, "far_field_uniform_cube_524k.md"),
                 "flops_per_launch": rec_flops + con_flops, "launch_ms": far_ms}
     line = {
@@ -579,7 +666,12 @@ def main():
         "config": config(args),
         "roofline": roof,
         "e2e": {"value": N / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(sum(a.numel() * 8 for a in hx)),
-                "d2h_bytes_per_step": int(uh.numel() * 8), "ms_per_step": e2e_ms},
+                "d2h_bytes_per_step": int(uh.numel() * 8), "ms_per_step": e2e_ms,
+                "call": "tc_velocity_host (pinned host arrays in and out, copies inside the call)",
+                "same_result_as_device_path": e2e_same},
+        "measured_peaks_tflops": {"fp32": peaks["fp32"], "fp64": peaks["fp64"],
+                                  "how": "tc_fma_peak before and after the timed steps (FMA chains, 8 blocks of 256 "
+                                         "threads per SM, best of 5 launches)"},
         "gpu_launches": int(launches),
         "clocks": clk,
         "phases_ms": ph,
@@ -637,6 +729,8 @@ def main():
     if not args.no_cpu_baseline:
         cb, idx, uo = cpu_baseline(x, f, h, nu, args, args.cpu_sample)
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        cb1, _, _ = cpu_baseline(x, f, h, nu, args, args.cpu_sample_1t, threads=1)
+        line["cpu_baseline"]["one_thread"] = {k: cb1[k] for k in ("value", "unit", "cores", "sample")}
         line["accuracy"]["vs_oracle_treecode"] = float(np.sqrt(np.sum((u_host[idx] - uo) ** 2) / np.sum(uo ** 2)))
         line["accuracy"]["oracle_samples"] = int(len(idx))
     if not args.no_extras:

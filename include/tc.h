@@ -362,7 +362,13 @@ typedef enum {
     TC_PH_FAR = 5,      /* tc_eval: far-field kernel                         */
     TC_PH_NEAR = 6,     /* tc_eval: near-field kernel                        */
     TC_PH_FINAL = 7,    /* tc_eval: sum and scatter to the caller's order    */
-    TC_NPHASES = 8
+    TC_PH_ADJ_FAR_T = 8,   /* tc_adjoint: far field, target side (dL/dx of targets)  */
+    TC_PH_ADJ_FAR_S = 9,   /* tc_adjoint: far field, source side (adjoint tables)    */
+    TC_PH_ADJ_NEAR_T = 10, /* tc_adjoint: near field, target side                    */
+    TC_PH_ADJ_NEAR_S = 11, /* tc_adjoint: near field, source side                    */
+    TC_PH_ADJ_REST = 12,   /* tc_adjoint: adjoint moments, downward pass, per-particle
+                            * evaluation and the final sums                       */
+    TC_NPHASES = 13
 } tc_phase;
 
 /* Enable (1) or disable (0) per-phase event timing on ctx.  Enabling resets
@@ -380,6 +386,30 @@ tc_status tc_phase_times(tc_ctx* ctx, double* ms);
 
 /* Number of kernels this library has launched in this process so far. */
 int64_t tc_kernel_launches(void);
+
+/*
+ * Measured arithmetic peak of the current device in TFLOP/s (an FMA counts
+ * as two flops), the denominator of a roofline fraction: every thread of a
+ * grid of 8 blocks of 256 threads per SM runs 8 independent FMA chains, timed
+ * with CUDA events on `stream` (cudaStream_t or NULL), best of 5 launches of
+ * about 1 ms after a warm-up, at whatever clock the device runs.
+ *  precision : TC_MIXED measures FP32 (the faster of scalar and packed
+ *              FP32x2 FMAs), TC_FP64 measures FP64.
+ *  tflops    : host output.
+ * Synchronises the stream.  The paper has no counterpart (it reports CPU
+ * seconds only).
+ */
+tc_status tc_fma_peak(int32_t precision, void* stream, double* tflops);
+
+/*
+ * Host-side fault injection for tests of the out-of-memory path: after
+ * `after` further device allocations by this library (across all contexts
+ * and threads), every allocation it attempts fails as if the device were out
+ * of memory, so the call that needed it returns TC_ENOMEM, until this is
+ * called again; after < 0 switches the injection off (the default).  Nothing
+ * is done on the device.
+ */
+void tc_fail_allocations(int64_t after);
 
 /* ---------------------------------------------------------------------- */
 /* Inspection of the tree (host outputs; for tests and tools).            */

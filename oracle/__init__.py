@@ -83,6 +83,7 @@ def _load():
         "orc_far_mass": (None, [vp, _d, c_i64, c_dbl, _i64]),
         "orc_treecode_frozen": (c_int, [vp, _d, _d, _d, _d, c_int, _d, _d, c_i64, c_dbl, _d, c_int]),
         "orc_max_threads": (c_int, []),
+        "orc_set_threads": (None, [c_int]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -103,6 +104,18 @@ def _c3(a):
 
 def max_threads():
     return _load().orc_max_threads()
+
+
+_all_threads = None
+
+
+def set_threads(n):
+    """Threads of every later oracle call (n <= 0: all of the host's)."""
+    global _all_threads
+    lib = _load()
+    if _all_threads is None:
+        _all_threads = lib.orc_max_threads()
+    lib.orc_set_threads(int(n) if n > 0 else _all_threads)
 
 
 def stokeslet(x, y):

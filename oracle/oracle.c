@@ -835,6 +835,15 @@ void orc_far_mass(const orc_tree* t, const double* tx, int64_t M, double theta, 
     }
 }
 
+/* Threads of every later parallel region (n >= 1). */
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+#endif
+    (void)n;
+}
+
 int orc_max_threads(void)
 {
 #ifdef _OPENMP

@@ -47,8 +47,11 @@ SIGNATURES = {
     "tc_profile": (_i32, [_vp, _i32]),
     "tc_phase_times": (_i32, [_vp, _vp]),
     "tc_kernel_launches": (_i64, []),
+    "tc_fma_peak": (_i32, [_i32, _vp, _vp]),
+    "tc_fail_allocations": (None, [_i64]),
 }
-PHASES = ("build", "moments", "tables", "targets", "lists", "far", "near", "final")
+PHASES = ("build", "moments", "tables", "targets", "lists", "far", "near", "final", "adj_far_target",
+          "adj_far_source", "adj_near_target", "adj_near_source", "adj_rest")
 
 
 class TCConfig(ctypes.Structure):

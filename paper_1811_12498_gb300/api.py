@@ -405,8 +405,12 @@ class StokesTreecode(torch.autograd.Function):
         return u
 
     @staticmethod
+    @torch.autograd.function.once_differentiable
     def backward(ctx, gu):
         tc = ctx.tc
+        if tc is None:
+            raise RuntimeError("StokesTreecode: backward ran twice on one forward pass; the adjoint releases the "
+                               "frozen tree and lists after its first run (use a fresh forward pass)")
         need = ctx.needs_input_grad
         gr = tc.adjoint(gu.contiguous(), f=need[1], h=need[2], nu=need[3], x=need[0])
         tc.sync()
@@ -423,6 +427,21 @@ def stokes_velocity(x, f, h, nu, theta, p, N0, precision="mixed", shrink=True):
 def kernel_launches():
     """Kernels launched by libtc.so in this process so far."""
     return int(lib().tc_kernel_launches())
+
+
+def fma_peak(precision="mixed", stream=None):
+    """Measured FP32 (precision "mixed") or FP64 FMA peak of the current
+    device in TFLOP/s (tc_fma_peak)."""
+    out = ctypes.c_double()
+    _check(lib().tc_fma_peak(_prec(precision), _stream_ptr(stream), ctypes.byref(out)))
+    return out.value
+
+
+def fail_allocations(after):
+    """Host-side injection: after `after` further device allocations by the
+    library every allocation fails as out of memory (TC_ENOMEM); after < 0
+    switches it off (tc_fail_allocations)."""
+    lib().tc_fail_allocations(int(after))
 
 
 def velocity(x, f, h, nu, theta, p, N0, precision="mixed", shrink=True, targets=None):

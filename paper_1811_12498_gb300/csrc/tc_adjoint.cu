@@ -1236,11 +1236,14 @@ cudaError_t run_far_adj(tc_ctx* ctx, const double* ts, int64_t M, int p, cudaStr
     cudaError_t e =
         cudaFuncSetAttribute(k_far_adj_target<TR, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
     if (e != cudaSuccess) return e;
+    ph_begin(ctx, TC_PH_ADJ_FAR_T);
     k_far_adj_target<TR, TC><<<(unsigned)nbatch, 32, sm1, s>>>(
         ts, ptr<double>(ctx->adj_gs), M, ptr<Geo>(ctx->node_geo), ptr<double>(ctx->node_invrho), ab, p,
         ptr<int64_t>(ctx->far_off), ptr<ListEntry>(ctx->far_list), ptr<double>(ctx->adj_gt));
     note_launch();
+    ph_end(ctx, TC_PH_ADJ_FAR_T);
     const int64_t nent = ctx->far_entries;
+    ph_begin(ctx, TC_PH_ADJ_FAR_S);
     if (nent > 0) {
         size_t sm2 = (size_t)(level_size(P) + level_size(P - 1)) * 32 * sizeof(TR) +
                      ((size_t)level_size(P) * 33 + 32 * 12 + (size_t)ncoef(P) * 12) * sizeof(TC);
@@ -1252,6 +1255,7 @@ cudaError_t run_far_adj(tc_ctx* ctx, const double* ts, int64_t M, int p, cudaStr
             ptr<int32_t>(ctx->adj_febatch), nent, kFarAdjChunk, ptr<double>(ctx->adj_abar));
         note_launch();
     }
+    ph_end(ctx, TC_PH_ADJ_FAR_S);
     return cudaGetLastError();
 }
 
@@ -1273,13 +1277,16 @@ cudaError_t run_far_adj32(tc_ctx* ctx, const double* ts, int64_t M, cudaStream_t
     unsigned* queue = reinterpret_cast<unsigned*>(ptr<char>(ctx->flags) + 192);
     e = cudaMemsetAsync(queue, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
+    ph_begin(ctx, TC_PH_ADJ_FAR_T);
     k_far_adj_target32<P><<<(unsigned)grid, 32, 0, s>>>(ts, ptr<double>(ctx->adj_gs), M, ptr<float4>(ctx->geo32),
                                                         ptr<float>(ctx->abf32), ptr<int64_t>(ctx->far_off),
                                                         ptr<ListEntry>(ctx->far_list), ptr<double>(ctx->adj_gt),
                                                         queue);
     note_launch();
+    ph_end(ctx, TC_PH_ADJ_FAR_T);
     e = ensure(ctx->adj_fbar, (size_t)nnodes * H * 12 * 8);
     if (e != cudaSuccess) return e;
+    ph_begin(ctx, TC_PH_ADJ_FAR_S);
     e = cudaMemsetAsync(ctx->adj_fbar.p, 0, (size_t)nnodes * H * 12 * 8, s);
     if (e != cudaSuccess) return e;
     const int64_t nent = ctx->far_entries;
@@ -1295,6 +1302,7 @@ cudaError_t run_far_adj32(tc_ctx* ctx, const double* ts, int64_t M, cudaStream_t
     if (e != cudaSuccess) return e;
     k_unfold_adj<<<(unsigned)nnodes, 128, smem, s>>>(ptr<double>(ctx->adj_fbar), nnodes, p, ptr<double>(ctx->adj_abar));
     note_launch();
+    ph_end(ctx, TC_PH_ADJ_FAR_S);
     return cudaGetLastError();
 }
 
@@ -1399,11 +1407,14 @@ extern "C" tc_status tc_adjoint(tc_ctx* ctx, const double* g, double* grad_f, do
     const unsigned ngrid = (unsigned)((nbatch + kNearAdjWarps - 1) / kNearAdjWarps);
     const int64_t ngroup = (nbatch + kNearAdjGroup - 1) / kNearAdjGroup;
     const unsigned ngrid32 = (unsigned)((ngroup + kNearAdjWarps - 1) / kNearAdjWarps);
+    ph_begin(ctx, TC_PH_ADJ_NEAR_T);
     if (ctx->precision == TC_FP64) {
         k_near_adj_target<double><<<ngrid, kNearAdjWarps * 32, 0, s>>>(
             ts, ptr<double>(ctx->adj_gs), M, ptr<int4>(ctx->node_topo), ptr<double>(ctx->xs), ptr<double>(ctx->ws), N,
             ptr<int64_t>(ctx->near_off), ptr<ListEntry>(ctx->near_list), ptr<double>(ctx->adj_gt));
         note_launch();
+        ph_end(ctx, TC_PH_ADJ_NEAR_T);
+        ph_begin(ctx, TC_PH_ADJ_NEAR_S);
         k_near_adj_source<double><<<(unsigned)nnodes, kNearAdjWarps * 32, 0, s>>>(
             ts, ptr<double>(ctx->adj_gs), M, ptr<int4>(ctx->node_topo), ptr<double>(ctx->xs), ptr<double>(ctx->ws), N,
             ptr<uint64_t>(ctx->adj_nkeys), ptr<int32_t>(ctx->adj_nidx), ptr<ListEntry>(ctx->near_list),
@@ -1414,6 +1425,8 @@ extern "C" tc_status tc_adjoint(tc_ctx* ctx, const double* g, double* grad_f, do
             ts, ptr<double>(ctx->adj_gs), M, ptr<int4>(ctx->node_topo), ptr<float4>(ctx->spack),
             ptr<int64_t>(ctx->near_off), ptr<ListEntry>(ctx->near_list), ptr<double>(ctx->adj_gt), ctx->eval_self);
         note_launch();
+        ph_end(ctx, TC_PH_ADJ_NEAR_T);
+        ph_begin(ctx, TC_PH_ADJ_NEAR_S);
         TC_CK(cudaMemsetAsync(ctx->adj_gnear.p, 0, (size_t)12 * N * 8, s), "zero near gradients");
         k_near_adj_source32<<<grid_for(ctx->near_entries, kNearAdjChunk), kNearAdjWarps * 32, 0, s>>>(
             ts, ptr<double>(ctx->adj_gs), M, ptr<int4>(ctx->node_topo), ptr<float4>(ctx->spack), N,
@@ -1421,9 +1434,11 @@ extern "C" tc_status tc_adjoint(tc_ctx* ctx, const double* g, double* grad_f, do
             ptr<int32_t>(ctx->adj_nebatch), ctx->near_entries, ptr<double>(ctx->adj_gnear));
         note_launch();
     }
+    ph_end(ctx, TC_PH_ADJ_NEAR_S);
     TC_CK(cudaGetLastError(), "near adjoint");
 
     // adjoint moments, downward pass, per-particle evaluation
+    ph_begin(ctx, TC_PH_ADJ_REST);
     size_t lsm = (size_t)12 * C * 8;
     TC_CK(cudaFuncSetAttribute(k_lambda, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm), "lambda attr");
     k_lambda<<<(unsigned)nnodes, 128, lsm, s>>>(ptr<double>(ctx->adj_abar), ptr<double>(ctx->node_invrho), p,
@@ -1449,6 +1464,7 @@ extern "C" tc_status tc_adjoint(tc_ctx* ctx, const double* g, double* grad_f, do
         k_scatter3<<<grid_for(M, 256), 256, 0, s>>>(ptr<double>(ctx->adj_gt), tperm, M, grad_t);
         note_launch();
     }
+    ph_end(ctx, TC_PH_ADJ_REST);
     TC_CK(cudaGetLastError(), "adjoint");
     return TC_OK;
 }

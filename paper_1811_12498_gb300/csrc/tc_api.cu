@@ -44,6 +44,7 @@ cudaError_t ensure(DevBuf& b, size_t bytes)
         if (e != cudaSuccess) return e;
     }
     size_t want = (bytes + 255) / 256 * 256;
+    if (alloc_should_fail()) return cudaErrorMemoryAllocation;
     cudaError_t e = cudaMalloc(&b.p, want);
     if (e != cudaSuccess) {
         b.p = nullptr;
@@ -59,6 +60,7 @@ static cudaError_t grow_keep(DevBuf& b, size_t bytes, size_t keep, cudaStream_t 
     if (b.p && b.cap >= bytes) return cudaSuccess;
     size_t want = (bytes + 255) / 256 * 256;
     void* np = nullptr;
+    if (alloc_should_fail()) return cudaErrorMemoryAllocation;
     cudaError_t e = cudaMalloc(&np, want);
     if (e != cudaSuccess) return e;
     if (b.p && keep) {
@@ -89,18 +91,16 @@ using namespace tc;
 static std::atomic<int64_t> g_launches{0};
 void tc::note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
-// phase timing: events around a phase when profiling is on
-static void ph_begin(tc_ctx* ctx, int ph, cudaStream_t s = nullptr)
+// allocations still allowed before injected failures start; -1 = no injection
+static std::atomic<int64_t> g_alloc_budget{-1};
+bool tc::alloc_should_fail()
 {
-    if (ctx->profile) cudaEventRecord(ctx->ev[2 * ph], s ? s : ctx->stream);
-}
-static void ph_end(tc_ctx* ctx, int ph, cudaStream_t s = nullptr)
-{
-    if (ctx->profile) {
-        cudaEventRecord(ctx->ev[2 * ph + 1], s ? s : ctx->stream);
-        ctx->ev_recorded[ph] = 1;
+    int64_t b = g_alloc_budget.load(std::memory_order_relaxed);
+    while (b > 0 && !g_alloc_budget.compare_exchange_weak(b, b - 1, std::memory_order_relaxed)) {
     }
+    return b == 0;
 }
+
 
 #define TC_CK(call, where)                                  \
     do {                                                    \
@@ -203,6 +203,31 @@ tc_status tc_phase_times(tc_ctx* ctx, double* ms)
 }
 
 int64_t tc_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+void tc_fail_allocations(int64_t after)
+{
+    g_alloc_budget.store(after < 0 ? -1 : after, std::memory_order_relaxed);
+}
+
+tc_status tc_fma_peak(int32_t precision, void* stream, double* tflops)
+{
+    if (!tflops) return fail(nullptr, TC_EINVAL, "tc_fma_peak: tflops is NULL");
+    if (precision != TC_FP64 && precision != TC_MIXED)
+        return fail(nullptr, TC_EINVAL, "tc_fma_peak: unknown precision %d", precision);
+    cudaStream_t s = (cudaStream_t)stream;
+    double r = 0.0, ms = 0.0;
+    tc_ctx* ctx = nullptr;
+    if (precision == TC_FP64) {
+        TC_CK(run_probe(2, s, &r, &ms), "tc_fma_peak");
+    } else {
+        double r2 = 0.0;
+        TC_CK(run_probe(0, s, &r, &ms), "tc_fma_peak");
+        TC_CK(run_probe(1, s, &r2, &ms), "tc_fma_peak");
+        r = r2 > r ? r2 : r;
+    }
+    *tflops = r;
+    return TC_OK;
+}
 
 const char* tc_last_error(const tc_ctx* ctx)
 {
@@ -641,7 +666,7 @@ tc_status tc_direct(const double* x, const double* f, const double* h, const dou
     cudaStream_t s = (cudaStream_t)stream;
     size_t bytes = direct_scratch_bytes(precision, N, M);
     void* scratch = nullptr;
-    TC_CK(cudaMallocAsync(&scratch, bytes, s), "tc_direct scratch");
+    TC_CK(alloc_should_fail() ? cudaErrorMemoryAllocation : cudaMallocAsync(&scratch, bytes, s), "tc_direct scratch");
     cudaError_t e = launch_direct(precision, x, f, h, nu, N, targets ? targets : x, M, u, scratch, bytes, s);
     cudaError_t e2 = cudaFreeAsync(scratch, s);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "tc_direct");

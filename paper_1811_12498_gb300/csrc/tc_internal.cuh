@@ -202,7 +202,23 @@ inline cudaError_t join_moments(tc_ctx* ctx)
 namespace tc {
 
 // count one kernel launch (process-wide counter read by tc_kernel_launches)
+// phase timing: events around a phase when profiling is on (tc_profile)
+inline void ph_begin(tc_ctx* ctx, int ph, cudaStream_t s = nullptr)
+{
+    if (ctx->profile) cudaEventRecord(ctx->ev[2 * ph], s ? s : ctx->stream);
+}
+inline void ph_end(tc_ctx* ctx, int ph, cudaStream_t s = nullptr)
+{
+    if (ctx->profile) {
+        cudaEventRecord(ctx->ev[2 * ph + 1], s ? s : ctx->stream);
+        ctx->ev_recorded[ph] = 1;
+    }
+}
 void note_launch();
+// host-side allocation-failure injection (tc_fail_allocations): true when the
+// next device allocation must fail as out of memory
+bool alloc_should_fail();
+cudaError_t run_probe(int kind, cudaStream_t s, double* tflops, double* ms_best);
 
 // tc_eval in two halves (tc_api.cu): lists, then far/near/finalize
 tc_status eval_prepare(tc_ctx* ctx, const double* targets, int64_t M, double theta, int p);

@@ -57,6 +57,10 @@ def test_host_argument_checks_without_gpu(lib):
     assert lib.tc_update_positions(None, None) == 1
     assert lib.tc_velocity_host(None, None, None, None, None, 10, 2, 0.5, 4, None) == 1
     assert lib.tc_eval_frozen(None, None) == 1
+    assert lib.tc_fma_peak(0, None, None) == 1
+    out = ctypes.c_double()
+    assert lib.tc_fma_peak(5, None, ctypes.byref(out)) == 1
+    assert b"precision" in lib.tc_last_error(None)
 
 
 def test_oracle_and_library_share_no_code():
