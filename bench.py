@@ -118,7 +118,8 @@ def parse():
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-sweep", action="store_true",
                     help="skip the accuracy-against-time sweep on the 4M-point sphere")
-    ap.add_argument("--only-extra", choices=["fwd_adjoint", "batched", "sphere_sweep", "table1_sphere"],
+    ap.add_argument("--only-extra", choices=["fwd_adjoint", "batched", "sphere_sweep", "table1_sphere",
+                                             "fig3_sphere"],
                     help="run just this extra measurement and print it as one JSON line (for profiling runs)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the forward+adjoint (Gaussian clusters) and batched (64 systems) measurements")
@@ -445,6 +446,60 @@ def bench_table1(flush, stream):
             "direct_mixed_ms": d_ms, "points": rows}
 
 
+def bench_fig3(flush, stream):
+    """Fig. 3 of the paper: test case 1 (icosahedral sphere, weights uniform
+    in [-1, 1], shrunk clusters, N0 = 2000) at theta = 0.5, p = 0, 2, ..., 10,
+    N = 20 * 4^L for L = 5..8 (20480 ... 1310720), mixed precision: per point
+    the time of build + moments + eval and E over 20000 sampled targets
+    (all at N = 20480) against the FP64 direct sum; per N the time of the
+    mixed direct sum; and the slopes of log time against log N (the paper:
+    direct O(N^2), treecode consistent with O(N log N))."""
+    import numpy as np
+    import torch
+
+    from paper_1811_12498_gb300 import api, inputs
+
+    def timed(fn, reps=2):
+        out = []
+        for k in range(reps + 1):
+            flush.fill_(1)
+            e0, e1 = _events(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            if k > 0:
+                out.append(e0.elapsed_time(e1))
+        return statistics.mean(out)
+
+    rows, direct = [], {}
+    for L in (5, 6, 7, 8):
+        x, f, h, nu = inputs.icosahedral_sphere(L, inputs.SEED_BASE + 101)
+        N = x.shape[0]
+        d = [torch.from_numpy(np.ascontiguousarray(a.T)).cuda() for a in (x, f, h, nu)]
+        idx = inputs.sample_indices(N, min(N, 20000), 5)
+        tgt = torch.from_numpy(np.ascontiguousarray(x[idx].T)).cuda()
+        ud = api.direct(*d, targets=tgt, precision="fp64", stream=stream)
+        it = torch.from_numpy(idx).cuda()
+        u = torch.empty((3, N), dtype=torch.float64, device="cuda")
+        direct[N] = timed(lambda: api.direct(*d, precision="mixed", out=u, stream=stream))
+        tc = api.Treecode("mixed", True, stream)
+        for p in range(0, 11, 2):
+            ms = timed(lambda: (tc.build(d[0], 2000).moments(d[1], d[2], d[3], p), tc.eval(0.5, p, out=u)))
+            E = float(torch.linalg.norm(u[:, it] - ud) / torch.linalg.norm(ud))
+            rows.append({"N": N, "p": p, "ms": ms, "E": E, "d_over_t": direct[N] / ms})
+        tc.close()
+    Ns = sorted(direct)
+    lnN = np.log(np.array(Ns, dtype=np.float64))
+    slopes = {"direct": float(np.polyfit(lnN, np.log([direct[n] for n in Ns]), 1)[0])}
+    for p in range(0, 11, 2):
+        t = [r["ms"] for n in Ns for r in rows if r["N"] == n and r["p"] == p]
+        slopes["treecode_p%d" % p] = float(np.polyfit(lnN, np.log(t), 1)[0])
+    return {"workload": "icosahedral sphere N=20480..1310720, theta=0.5, p=0..10, N0=2000, shrink, mixed; E on "
+                        "20000 sampled targets vs FP64 direct",
+            "direct_mixed_ms": {str(n): direct[n] for n in Ns}, "points": rows,
+            "loglog_slopes_time_vs_N": slopes}
+
+
 def bench_batched(flush, stream, reps=3):
     """64 independent systems, sizes log-uniform in [1e4, 5e5] (even: uniform
     cube, odd: Fibonacci sphere), p = 6, theta = 0.6, N0 = 2000, mixed: one
@@ -497,7 +552,7 @@ def run_only_extra(name):
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
     fn = {"fwd_adjoint": bench_fwd_adjoint, "batched": bench_batched, "sphere_sweep": bench_sphere_sweep,
-          "table1_sphere": bench_table1}[name]
+          "table1_sphere": bench_table1, "fig3_sphere": bench_fig3}[name]
     print(json.dumps({"extra": name, **fn(flush, stream)}), flush=True)
 
 
@@ -737,6 +792,7 @@ def main():
         line["fwd_adjoint"] = bench_fwd_adjoint(flush, stream)
         line["batched"] = bench_batched(flush, stream)
         line["table1_sphere"] = bench_table1(flush, stream)
+        line["fig3_sphere"] = bench_fig3(flush, stream)
         if not args.no_sweep:
             line["sphere_sweep"] = bench_sphere_sweep(flush, stream)
     print(json.dumps(line), flush=True)

@@ -74,9 +74,14 @@ def icosahedral_sphere(L, seed, normals=False):
     pushed onto the sphere at every level (geodesic refinement).  Particles
     are the face centroids projected onto the sphere.  f and h are uniform in
     [-1, 1]^3 as the paper states.  The paper does not say how nu was drawn
-    for this test; with nu uniform in [-1, 1]^3 the treecode errors of
-    Table 1(a) are reproduced to within 10 % for p = 2..10, while the outward
-    normal gives errors ten times larger, so the former is the default.
+    for this test (Section 1 defines nu as a unit vector; Section 6 draws the
+    weights as random numbers in [-1, 1]).  Components uniform in [-1, 1]
+    (the default) reproduce the 18 errors of Table 1(a) within factors 0.87
+    to 1.18 (geometric mean 1.02); random unit vectors within 0.98 to 1.51
+    (mean 1.18); the outward normal (normals=True) gives errors ten times
+    larger, because on a sphere the stresslet velocity of outward normals
+    nearly cancels (its RMS is 50 times smaller than with random directions)
+    while its truncation error does not.
     """
     v, faces = _icosahedron()
     for _ in range(L):

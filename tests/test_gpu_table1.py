@@ -1,12 +1,15 @@
-"""Table 1 of the paper reproduced on the GPU: test case 1 (Stokeslets and
-stresslets at the centroids of an icosahedral triangulation of the unit
-sphere, random weights in [-1, 1], shrunk clusters, N0 = 2000), with E taken
-over ALL targets as in Section 6, against the FP64 direct sum on the GPU.
-Column (a), N = 81920, in FP64 over the whole (theta, p) grid; column (b),
+"""Table 1 and Fig. 3 of the paper reproduced on the GPU: test case 1
+(Stokeslets and stresslets at the centroids of an icosahedral triangulation
+of the unit sphere, random weights in [-1, 1], shrunk clusters, N0 = 2000),
+E against the FP64 direct sum on the GPU.
+Column (a), N = 81920, in FP64 over the whole (theta, p) grid and column (b),
 N = 327680, in mixed precision for theta = 0.5 and 0.8 (E >= 1e-6 there, well
-above the mixed path's own 3e-7).  E is a statistic of random weights, so a
-factor 1.5 is allowed (the oracle on 600 sampled targets lands within 0.87 to
-1.18 of column (a))."""
+above the mixed path's own 3e-7), both with E over ALL targets as in
+Section 6; column (c), N = 1310720, in mixed precision for theta = 0.5 and
+0.8 with E over 20000 sampled targets.  E is a statistic of random weights,
+so a factor 1.5 is allowed (the oracle on 600 sampled targets lands within
+0.87 to 1.18 of column (a)).  Fig. 3(a): at theta = 0.5 the error is nearly
+independent of N = 20480 ... 1310720 and falls with p."""
 import os
 
 import numpy as np
@@ -22,7 +25,7 @@ GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 def _paper():
     rows = np.loadtxt(os.path.join(GOLDEN, "table1_sphere_E.txt"), comments="#")
-    return {(float(r[0]), int(r[1])): (float(r[2]), float(r[3])) for r in rows}
+    return {(float(r[0]), int(r[1])): (float(r[2]), float(r[3]), float(r[4])) for r in rows}
 
 
 def _rel_l2(u, ref):
@@ -46,3 +49,63 @@ def test_table1_error_on_gpu(L, col, precision, thetas):
             E = _rel_l2(tc.eval(theta, p), ud)
             e = paper[(theta, p)][col]
             assert e / 1.5 < E < e * 1.5, (L, theta, p, E, e)
+
+
+def _sampled_E(api, d, x, p_list, theta, tc, ns, seed):
+    N = x.shape[0]
+    idx = inputs.sample_indices(N, min(N, ns), seed)
+    tgt = torch.from_numpy(np.ascontiguousarray(x[idx].T)).cuda()
+    ud = api.direct(*d, targets=tgt, precision="fp64")
+    it = torch.from_numpy(idx).cuda()
+    return {p: _rel_l2(tc.eval(theta, p)[:, it], ud) for p in p_list}
+
+
+def test_table1c_and_fig3_error_against_system_size():
+    """Fig. 3(a) (theta = 0.5, p = 0, 2, ..., 10, N = 20 * 4^L for L = 5..8)
+    and Table 1(c) (N = 1310720, theta = 0.5 and 0.8), mixed precision, E on
+    20000 sampled targets (all of them at N = 20480).  For every p the errors
+    of the four sizes lie within a factor 2.5 of one another and fall with p
+    at every size; the N = 1310720 errors are the printed column (c) within a
+    factor 1.5."""
+    from paper_1811_12498_gb300 import api
+
+    paper = _paper()
+    ps = list(range(0, 11, 2))
+    fig = {}
+    for L in (5, 6, 7, 8):
+        x, f, h, nu = inputs.icosahedral_sphere(L, inputs.SEED_BASE + 101)
+        d = [torch.from_numpy(np.ascontiguousarray(a.T)).cuda() for a in (x, f, h, nu)]
+        tc = api.Treecode("mixed", True)
+        tc.build(d[0], 2000).moments(d[1], d[2], d[3], 10)
+        fig[L] = _sampled_E(api, d, x, ps, 0.5, tc, 20000, 5)
+        if L == 8:
+            E08 = _sampled_E(api, d, x, ps, 0.8, tc, 20000, 5)
+            for p in ps:
+                for theta, E in ((0.5, fig[8][p]), (0.8, E08[p])):
+                    e = paper[(theta, p)][2]
+                    assert e / 1.5 < E < e * 1.5, ("Table 1(c)", theta, p, E, e)
+        tc.close()
+    print("Fig. 3(a), theta = 0.5, E by p (rows) and N = 20480 ... 1310720 (columns):")
+    for p in ps:
+        row = [fig[L][p] for L in (5, 6, 7, 8)]
+        print("  p=%2d  " % p + "  ".join("%.2e" % v for v in row))
+        assert max(row) / min(row) < 2.5, (p, row)
+    for L in (5, 6, 7, 8):
+        assert all(fig[L][b] < fig[L][a] for a, b in zip(ps, ps[1:])), (L, fig[L])
+
+
+def test_largest_sphere_matches_oracle_on_sampled_targets():
+    """N = 1310720 icosahedral sphere, theta = 0.5, p = 6: the mixed GPU
+    treecode equals the oracle's at 256 sampled targets within 1e-6 (the
+    oracle builds its own tree and moments over all particles)."""
+    import oracle
+    from paper_1811_12498_gb300 import api
+
+    x, f, h, nu = inputs.icosahedral_sphere(8, inputs.SEED_BASE + 101)
+    d = [torch.from_numpy(np.ascontiguousarray(a.T)).cuda() for a in (x, f, h, nu)]
+    u = api.velocity(*d, theta=0.5, p=6, N0=2000, precision="mixed").cpu().numpy().T
+    idx = inputs.sample_indices(x.shape[0], 256, 6)
+    tree = oracle.Tree(x, 2000, True)
+    tree.set_moments(f, h, nu, 6)
+    ref = tree.treecode(x[idx], 0.5, 6)
+    assert oracle.rel_l2(u[idx], ref) <= 1e-6, oracle.rel_l2(u[idx], ref)

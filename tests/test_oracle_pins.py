@@ -528,9 +528,9 @@ def test_error_matches_paper_table2_cube():
 
 
 def table1_E():
-    """Table 1 of the paper as printed: {(theta, p): (E at N=81920, E at N=327680)}."""
+    """Table 1 of the paper as printed: {(theta, p): (E at N=81920, E at N=327680, E at N=1310720)}."""
     rows = np.loadtxt(os.path.join(GOLDEN, "table1_sphere_E.txt"), comments="#")
-    return {(float(r[0]), int(r[1])): (float(r[2]), float(r[3])) for r in rows}
+    return {(float(r[0]), int(r[1])): (float(r[2]), float(r[3]), float(r[4])) for r in rows}
 
 
 @pytest.mark.slow
@@ -547,7 +547,7 @@ def test_error_matches_paper_table1_sphere():
     ud = oracle.direct(x, f, h, nu, targets=x[idx])
     tree = oracle.Tree(x, 2000, True)
     tree.set_moments(f, h, nu, 10)
-    for (theta, p), (e, _) in paper.items():
+    for (theta, p), (e, _, _) in paper.items():
         E = oracle.rel_l2(tree.treecode(x[idx], theta, p), ud)
         assert e / 1.5 < E < e * 1.5, (theta, p, E, e)
 
