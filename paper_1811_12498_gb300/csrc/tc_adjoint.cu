@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(kNearAdjWarps * 32)
 
 // ------------------------------------------ near, mixed precision (FP32)
 // The same pair terms in FP32 on hi/lo positions (as the forward near field),
-// 1/r from rsqrtf, packed FP32x2 arithmetic.
+// 1/r from rsqrt_ftz, packed FP32x2 arithmetic.
 
 // target side: the forward near field's group walk (tc_nearpair.cuh: four
 // batches per warp, the targets of each leaf packed into 32-lane streams, two
@@ -334,11 +334,11 @@ struct NearOpG {
         const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
         float2 ri;
         if (kGuard) {
-            ri.x = r2.x > 0.f ? rsqrtf(r2.x) : 0.f;
-            ri.y = r2.y > 0.f ? rsqrtf(r2.y) : 0.f;
+            ri.x = r2.x > 0.f ? rsqrt_ftz(r2.x) : 0.f;
+            ri.y = r2.y > 0.f ? rsqrt_ftz(r2.y) : 0.f;
         } else {
-            ri.x = rsqrtf(r2.x);
-            ri.y = rsqrtf(r2.y);
+            ri.x = rsqrt_ftz(r2.x);
+            ri.y = rsqrt_ftz(r2.y);
         }
         const float2 ri2 = __fmul2_rn(ri, ri), ri3 = __fmul2_rn(ri2, ri), ri5 = __fmul2_rn(ri3, ri2);
         const float2 f0 = make_float2(B.z, B.w), f1 = make_float2(D.z, D.w), f2 = make_float2(E.x, E.y);
@@ -467,8 +467,8 @@ __global__ void __launch_bounds__(kNearAdjWarps * 32)
                     const float2 g0 = T[6], g1 = T[7], g2 = T[8];
                     const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
                     float2 ri;
-                    ri.x = r2.x > 0.f ? rsqrtf(r2.x) : 0.f;
-                    ri.y = r2.y > 0.f ? rsqrtf(r2.y) : 0.f;
+                    ri.x = r2.x > 0.f ? rsqrt_ftz(r2.x) : 0.f;
+                    ri.y = r2.y > 0.f ? rsqrt_ftz(r2.y) : 0.f;
                     const float2 ri2 = __fmul2_rn(ri, ri), ri3 = __fmul2_rn(ri2, ri), ri5 = __fmul2_rn(ri3, ri2);
                     const float2 df = __ffma2_rn(dx, f0, __ffma2_rn(dy, f1, __fmul2_rn(dz, f2)));
                     const float2 dh = __ffma2_rn(dx, h0, __ffma2_rn(dy, h1, __fmul2_rn(dz, h2)));

@@ -118,7 +118,7 @@ static void release_all(tc_ctx* c)
                       &c->abf32, &c->geo32, &c->tkeys,
                       &c->tkeys_alt, &c->tperm, &c->tperm_alt, &c->ts, &c->nfar_e, &c->nnear_e,
                       &c->far_off, &c->near_off, &c->far_list, &c->near_list, &c->cnt_far, &c->cnt_near, &c->u_far,
-                      &c->u_near, &c->flags, &c->adj_fkeys, &c->adj_fkeys_alt, &c->adj_fidx, &c->adj_fidx_alt,
+                      &c->u_near, &c->near_gkey, &c->near_gkey_alt, &c->near_gord, &c->near_gord_alt, &c->flags, &c->adj_fkeys, &c->adj_fkeys_alt, &c->adj_fidx, &c->adj_fidx_alt,
                       &c->adj_febatch, &c->adj_nkeys, &c->adj_nkeys_alt, &c->adj_nidx, &c->adj_nidx_alt,
                       &c->adj_nebatch, &c->adj_hist, &c->adj_gs, &c->adj_gt, &c->adj_abar, &c->adj_fbar, &c->adj_lam,
                       &c->adj_lamacc, &c->adj_gfar, &c->adj_gnear, &c->host_in, &c->host_u};
@@ -479,6 +479,12 @@ tc_status tc::eval_prepare(tc_ctx* ctx, const double* targets, int64_t M, double
     TC_CK(ensure(ctx->cnt_near, (size_t)M * 8), "alloc counts");
     TC_CK(ensure(ctx->u_far, (size_t)3 * M * 8), "alloc u");
     TC_CK(ensure(ctx->u_near, (size_t)3 * M * 8), "alloc u");
+    const int64_t ngmax = near_max_groups(M);
+    TC_CK(ensure(ctx->near_gkey, (size_t)ngmax * 8), "alloc near schedule");
+    TC_CK(ensure(ctx->near_gkey_alt, (size_t)ngmax * 8), "alloc near schedule");
+    TC_CK(ensure(ctx->near_gord, (size_t)ngmax * 4), "alloc near schedule");
+    TC_CK(ensure(ctx->near_gord_alt, (size_t)ngmax * 4), "alloc near schedule");
+    TC_CK(ensure(ctx->hist, (size_t)256 * radix_blocks(ngmax) * 4), "alloc near schedule");
     TC_CK(cudaMemsetAsync(ctx->flags.p, 0, 4, s), "flags");
     const int4* topo = ptr<int4>(ctx->node_topo);
     const Geo* geo = ptr<Geo>(ctx->node_geo);
@@ -558,9 +564,12 @@ tc_status tc::eval_compute(tc_ctx* ctx, double* u)
     ph_end(ctx, TC_PH_FAR, s2);
     TC_CK(cudaEventRecord(ctx->ev_join, s2), "join");
     ph_begin(ctx, TC_PH_NEAR);
+    const NearSched sched = {ptr<uint64_t>(ctx->near_gkey), ptr<uint64_t>(ctx->near_gkey_alt),
+                             ptr<int32_t>(ctx->near_gord), ptr<int32_t>(ctx->near_gord_alt), ptr<uint32_t>(ctx->hist),
+                             reinterpret_cast<unsigned*>(ptr<char>(ctx->flags) + 160)};
     TC_CK(launch_near(ctx->precision, ts, M, ptr<int4>(ctx->node_topo), ptr<double>(ctx->xs), ptr<double>(ctx->ws),
                       ptr<float4>(ctx->spack), ctx->N, ptr<int64_t>(ctx->near_off), ptr<ListEntry>(ctx->near_list),
-                      ptr<double>(ctx->u_near), ctx->eval_self && !ctx->moved, s),
+                      ptr<double>(ctx->u_near), ctx->eval_self && !ctx->moved, sched, s),
           "near field");
     ph_end(ctx, TC_PH_NEAR);
     TC_CK(cudaStreamWaitEvent(s, ctx->ev_join, 0), "join");

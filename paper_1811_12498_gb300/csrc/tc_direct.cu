@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(kDirWarps * 32)
             const float dy = (th[1] - p0.y) + (tl[1] - p1.y);
             const float dz = (th[2] - p0.z) + (tl[2] - p1.z);
             const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            const float ri = r2 > 0.f ? rsqrtf(r2) : 0.f;
+            const float ri = r2 > 0.f ? rsqrt_ftz(r2) : 0.f;
             const float ri2 = ri * ri;
             const float ri3 = ri2 * ri;
             const float df = fmaf(dx, p0.w, fmaf(dy, p1.w, dz * p2.x));

@@ -38,6 +38,18 @@ __host__ __device__ inline int flat_index(int k1, int k2, int k3)
 // error of the last addition (s - c is the better estimate of the sum).
 // Written out so that no reassociation can cancel the compensation (the
 // library is built without fast-math).
+// 1/sqrt(x) by the special-function unit with subnormal inputs and results
+// flushed to zero: the plain rsqrtf adds scaling steps for subnormals on the
+// FP32 pipe (12 % of the near field's FP32 instructions).  Pair distances
+// whose square is subnormal in FP32 (|d| < 1.1e-19) are out of range of the
+// FP32 pair terms anyway (their powers overflow).
+__device__ __forceinline__ float rsqrt_ftz(float x)
+{
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 __device__ __forceinline__ void kahan_add(float& s, float& c, float b)
 {
     const float y = b - c;
@@ -153,6 +165,7 @@ struct tc_ctx {
     tc::DevBuf far_list, near_list;     // ListEntry
     tc::DevBuf cnt_far, cnt_near;       // per sorted target counts (int64)
     tc::DevBuf u_far, u_near;           // 3*M FP64 sorted order
+    tc::DevBuf near_gkey, near_gkey_alt, near_gord, near_gord_alt;  // near-field group schedule (NearSched)
     tc::DevBuf flags;                   // int32 device error flags at byte 0; work-queue counters
                                         // of the far field (byte 128) and its adjoint's target side (192)
     int64_t far_entries = 0, near_entries = 0;  // list sizes of the last tc_eval
@@ -297,6 +310,19 @@ cudaError_t launch_far_batched(int precision, int rec64, const SysDesc* sys, int
                                int p, unsigned long long* counter, int warps_per_block, int blocks, cudaStream_t s);
 
 // tc_near.cu
+// Scratch of the one-system near field's schedule: the groups of batches are
+// taken from a queue in order of decreasing work (their pair counts, sorted
+// by radix sort), so the grid's tail is made of the smallest groups.
+struct NearSched {
+    uint64_t* keys;      // ngroup sort keys (and as many for the sort's second buffer)
+    uint64_t* keys_alt;
+    int32_t* order;      // ngroup group indices, sorted by decreasing work
+    int32_t* order_alt;
+    uint32_t* hist;      // radix histograms for ngroup keys
+    unsigned* queue;     // device counter
+};
+// groups the near field's schedule may need at most (the smallest group size)
+int64_t near_max_groups(int64_t M);
 cudaError_t launch_near_batched(int precision, const SysDesc* sys, int nsys, const int64_t* item_off, int64_t nitems,
                                 unsigned long long* counter, int warps_per_block, int blocks, cudaStream_t s);
 cudaError_t launch_finalize_batched(const SysDesc* sys, int nsys, const int64_t* moff, int64_t mtotal, double* u,
@@ -304,7 +330,7 @@ cudaError_t launch_finalize_batched(const SysDesc* sys, int nsys, const int64_t*
 cudaError_t launch_near(int precision, const double* ts, int64_t M, const int4* topo,
                         const double* xs, const double* ws, const float4* spack, int64_t N,
                         const int64_t* near_off, const ListEntry* near_list, double* u_near, int self,
-                        cudaStream_t s);
+                        const NearSched& sched, cudaStream_t s);
 cudaError_t launch_finalize(const double* u_far, const double* u_near, const int32_t* perm, int64_t M, double* u,
                             cudaStream_t s);
 cudaError_t launch_scatter_counts(const int64_t* cs, const int32_t* perm, int64_t M, int64_t* out,

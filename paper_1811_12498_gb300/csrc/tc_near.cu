@@ -21,6 +21,8 @@
 // pair terms run on packed FP32x2 arithmetic, two sources per instruction.
 //
 // FP64 mode computes everything in FP64, one batch per warp.
+#include <algorithm>
+
 #include "tc_nearpair.cuh"
 
 namespace tc {
@@ -28,12 +30,14 @@ namespace tc {
 namespace {
 
 constexpr int kNearWarps = 4;
-// Batches per warp in the one-system mixed-precision kernel.  Eight when the
-// grid still fills the GPU (at least 0.6 of a resident wave of warps): the
-// grid is then short (about 1.3 waves at N = 10^6) and its tail leaves SMs to
-// the far field, which the step runs next (step 57.9 -> 54.4 ms against four,
-// though the near kernel alone goes 39.0 -> 40.5 ms); four otherwise, since a
-// grid of fewer warps than the GPU holds leaves it idle (N = 327680 on the
+// Batches per warp in the one-system mixed-precision kernel.  The groups are
+// taken from a queue in order of decreasing work (k_group_work), so the end
+// of the kernel is made of the smallest groups.  Eight when the groups still
+// fill the GPU (at least 0.6 of a resident wave of warps): at N = 10^6 the
+// near kernel alone takes 37.8 ms with eight and 34.4 ms with four, but with
+// eight the far field, which the step runs on its own stream, fills the SMs
+// its end leaves free (step 53.2 against 54.4 ms); four otherwise, since
+// fewer groups than the GPU holds warps leave it idle (N = 327680 on the
 // sphere: 36 ms with four, 64 ms with eight).
 constexpr int kNearGroupLarge = 8;
 constexpr double kNearWaveShare = 0.6;
@@ -81,11 +85,11 @@ __device__ __forceinline__ void pair_terms(const Tgt2& t, const float4* tp, floa
     const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
     float2 ri;
     if (kGuard) {
-        ri.x = r2.x > 0.f ? rsqrtf(r2.x) : 0.f;
-        ri.y = r2.y > 0.f ? rsqrtf(r2.y) : 0.f;
+        ri.x = r2.x > 0.f ? rsqrt_ftz(r2.x) : 0.f;
+        ri.y = r2.y > 0.f ? rsqrt_ftz(r2.y) : 0.f;
     } else {
-        ri.x = rsqrtf(r2.x);
-        ri.y = rsqrtf(r2.y);
+        ri.x = rsqrt_ftz(r2.x);
+        ri.y = rsqrt_ftz(r2.y);
     }
     const float2 ri2 = __fmul2_rn(ri, ri);
     const float2 f0 = make_float2(B.z, B.w), f1 = make_float2(D.z, D.w), f2 = make_float2(E.x, E.y);
@@ -170,28 +174,75 @@ __device__ inline void near_batch_fp64(const double* __restrict__ ts, int64_t M,
     }
 }
 
+// Work of each group of G batches, its pair count (over its near entries, the
+// active targets times the leaf size), as a sort key that puts the groups
+// with the most work first; order receives the identity.
+template <int G>
+__global__ void k_group_work(const int64_t* __restrict__ near_off, const ListEntry* __restrict__ near_list,
+                             const int4* __restrict__ topo, int64_t nbatch, int64_t ngroup, uint64_t* __restrict__ keys,
+                             int32_t* __restrict__ order)
+{
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= ngroup) return;
+    const int64_t b0 = g * G, b1 = min(nbatch, b0 + G);
+    uint64_t w = 0;
+    for (int64_t e = near_off[b0]; e < near_off[b1]; e++) {
+        const ListEntry le = near_list[e];
+        w += (uint64_t)__popc(le.mask) * (uint64_t)topo[le.node].y;
+    }
+    keys[g] = 0xffffffffull - (w < 0xffffffffull ? w : 0xffffffffull);
+    order[g] = (int32_t)g;
+}
+
+// The one-system near field on a resident grid: each warp takes the next
+// group from the queue, in order of decreasing work.
 template <int G>
 __global__ void __launch_bounds__(kNearWarps * 32)
-    k_near_mixed(const double* __restrict__ ts, int64_t M, const int4* __restrict__ topo,
-                 const float4* __restrict__ spack, const int64_t* __restrict__ near_off,
-                 const ListEntry* __restrict__ near_list, double* __restrict__ u_near, int self)
+    k_near_mixed_q(const double* __restrict__ ts, int64_t M, const int4* __restrict__ topo,
+                   const float4* __restrict__ spack, const int64_t* __restrict__ near_off,
+                   const ListEntry* __restrict__ near_list, double* __restrict__ u_near, int self,
+                   const int32_t* __restrict__ order, int64_t ngroup, unsigned* __restrict__ queue)
 {
     __shared__ NearScratch<G> sc[kNearWarps];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t ngroup = ((M + kBatch - 1) / kBatch + G - 1) / G;
-    const int64_t B = blockIdx.x * (int64_t)kNearWarps + w;
-    if (B >= ngroup) return;
-    nearpair::near_group<G, NearOpU>(ts, nullptr, M, topo, spack, near_off, near_list, u_near, B, self, sc[w], lane);
+    for (;;) {
+        unsigned i = 0;
+        if (lane == 0) i = atomicAdd(queue, 1u);
+        i = __shfl_sync(0xffffffffu, i, 0);
+        if ((int64_t)i >= ngroup) break;
+        nearpair::near_group<G, NearOpU>(ts, nullptr, M, topo, spack, near_off, near_list, u_near, order[i], self,
+                                         sc[w], lane);
+    }
 }
 
 template <int G>
 cudaError_t run_near_mixed(const double* ts, int64_t M, const int4* topo, const float4* spack,
                            const int64_t* near_off, const ListEntry* near_list, double* u_near, int self,
-                           cudaStream_t s)
+                           const NearSched& sc, cudaStream_t s)
 {
-    const int64_t ngroup = ((M + kBatch - 1) / kBatch + G - 1) / G;
-    const unsigned grid = (unsigned)((ngroup + kNearWarps - 1) / kNearWarps);
-    k_near_mixed<G><<<grid, kNearWarps * 32, 0, s>>>(ts, M, topo, spack, near_off, near_list, u_near, self);
+    const int64_t nbatch = (M + kBatch - 1) / kBatch;
+    const int64_t ngroup = (nbatch + G - 1) / G;
+    k_group_work<G><<<(unsigned)((ngroup + 255) / 256), 256, 0, s>>>(near_off, near_list, topo, nbatch, ngroup,
+                                                                    sc.keys, sc.order);
+    note_launch();
+    cudaError_t e = radix_sort_bits(sc.keys, sc.order, sc.keys_alt, sc.order_alt, sc.hist, ngroup, 32, s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(sc.queue, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    static int per_sm[2] = {0, 0}, sms = 0;
+    int& ps = per_sm[G == kNearGroupLarge ? 1 : 0];
+    if (ps == 0) {
+        int dev = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, k_near_mixed_q<G>, kNearWarps * 32, 0) != cudaSuccess ||
+            ps < 1)
+            ps = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    }
+    const int64_t need = (ngroup + kNearWarps - 1) / kNearWarps;
+    const unsigned grid = (unsigned)std::min<int64_t>(need, (int64_t)ps * std::max(sms, 1));
+    k_near_mixed_q<G><<<grid, kNearWarps * 32, 0, s>>>(ts, M, topo, spack, near_off, near_list, u_near, self,
+                                                       sc.order, ngroup, sc.queue);
     return cudaGetLastError();
 }
 
@@ -201,7 +252,7 @@ int near_resident_warps()
     static int warps = 0;
     if (warps == 0) {
         int per_sm = 0, dev = 0, sms = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_near_mixed<kNearGroupLarge>, kNearWarps * 32,
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_near_mixed_q<kNearGroupLarge>, kNearWarps * 32,
                                                           0) != cudaSuccess)
             per_sm = 1;
         cudaGetDevice(&dev);
@@ -308,10 +359,16 @@ inline unsigned grid_for(int64_t n, int threads)
 
 }  // namespace
 
+int64_t near_max_groups(int64_t M)
+{
+    const int64_t nbatch = (M + kBatch - 1) / kBatch;
+    return (nbatch + kNearGroupBatches - 1) / kNearGroupBatches;
+}
+
 cudaError_t launch_near(int precision, const double* ts, int64_t M, const int4* topo,
                         const double* xs, const double* ws, const float4* spack, int64_t N,
                         const int64_t* near_off, const ListEntry* near_list, double* u_near, int self,
-                        cudaStream_t s)
+                        const NearSched& sched, cudaStream_t s)
 {
     if (M <= 0) return cudaSuccess;
     const int64_t nbatch = (M + kBatch - 1) / kBatch;
@@ -322,9 +379,9 @@ cudaError_t launch_near(int precision, const double* ts, int64_t M, const int4* 
         const bool large = (double)((nbatch + kNearGroupLarge - 1) / kNearGroupLarge) >=
                            kNearWaveShare * near_resident_warps();
         cudaError_t e = large ? run_near_mixed<kNearGroupLarge>(ts, M, topo, spack, near_off, near_list, u_near,
-                                                                  self, s)
+                                                                  self, sched, s)
                               : run_near_mixed<kNearGroupBatches>(ts, M, topo, spack, near_off, near_list, u_near,
-                                                                  self, s);
+                                                                  self, sched, s);
         note_launch();
         return e;
     }
