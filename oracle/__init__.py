@@ -83,6 +83,14 @@ def _load():
         "orc_far_mass": (None, [vp, _d, c_i64, c_dbl, _i64]),
         "orc_treecode_frozen": (c_int, [vp, _d, _d, _d, _d, c_int, _d, _d, c_i64, c_dbl, _d, c_int]),
         "orc_max_threads": (c_int, []),
+        "orc_stokeslet_reg": (None, [_d, _d, c_dbl, _d]),
+        "orc_stresslet_reg": (None, [_d, _d, c_dbl, _d]),
+        "orc_direct_reg": (None, [_d, _d, _d, _d, c_i64, _d, c_i64, c_dbl, _d, c_int]),
+        "orc_coeffs_nu": (None, [_d, c_dbl, c_int, c_int, _d]),
+        "orc_taylor_stokeslet_reg": (None, [_d, c_dbl, c_int, _d]),
+        "orc_taylor_stresslet_reg": (None, [_d, c_dbl, c_int, _d]),
+        "orc_far_reg": (None, [_d, c_dbl, c_int, _d, _d, _d]),
+        "orc_treecode_eps": (c_int, [vp, _d, c_i64, c_dbl, c_int, c_dbl, _d, vp, vp, vp, c_int]),
         "orc_set_threads": (None, [c_int]),
     }
     for name, (res, args) in sig.items():
@@ -151,6 +159,57 @@ def direct_grad(x, f, h, nu, g, nthreads=0):
     _load().orc_direct_grad(_ptr(x), _ptr(f), _ptr(h), _ptr(nu), N, _ptr(g), _ptr(out["f"]), _ptr(out["h"]),
                             _ptr(out["nu"]), _ptr(out["x"]), nthreads)
     return out
+
+
+def stokeslet_reg(x, y, eps):
+    """Regularized Stokeslet S^eps_ij(x, y) (oracle.c), 3x3."""
+    out = np.empty(9)
+    _load().orc_stokeslet_reg(_ptr(_c3(x)), _ptr(_c3(y)), float(eps), _ptr(out))
+    return out.reshape(3, 3)
+
+
+def stresslet_reg(x, y, eps):
+    """Regularized stresslet T^eps_ijl(x, y) (oracle.c), 3x3x3."""
+    out = np.empty(27)
+    _load().orc_stresslet_reg(_ptr(_c3(x)), _ptr(_c3(y)), float(eps), _ptr(out))
+    return out.reshape(3, 3, 3)
+
+
+def direct_reg(x, f, h, nu, eps, targets=None, nthreads=0):
+    """Velocity of eq. (1.3) with the regularized kernels, FP64."""
+    x, f, h, nu = (_c3(a) for a in (x, f, h, nu))
+    t = x if targets is None else _c3(targets)
+    u = np.empty((t.shape[0], 3))
+    _load().orc_direct_reg(_ptr(x), _ptr(f), _ptr(h), _ptr(nu), x.shape[0], _ptr(t), t.shape[0], float(eps), _ptr(u),
+                           nthreads)
+    return u
+
+
+def coeffs_nu(d, eps, two_nu, P):
+    """Taylor coefficients of (|x - y|^2 + eps^2)^(-two_nu/2) in y about y_c
+    for ||k|| <= P (the generalized recurrence); d = x - y_c."""
+    c = np.empty((P + 1,) * 3)
+    _load().orc_coeffs_nu(_ptr(_c3(d)), float(eps), int(two_nu), P, _ptr(c))
+    return c
+
+
+def taylor_stokeslet_reg(d, eps, p):
+    a = np.empty((9,) + (p + 1,) * 3)
+    _load().orc_taylor_stokeslet_reg(_ptr(_c3(d)), float(eps), p, _ptr(a))
+    return a.reshape((3, 3) + (p + 1,) * 3)
+
+
+def taylor_stresslet_reg(d, eps, p):
+    t = np.empty((27,) + (p + 1,) * 3)
+    _load().orc_taylor_stresslet_reg(_ptr(_c3(d)), float(eps), p, _ptr(t))
+    return t.reshape((3, 3, 3) + (p + 1,) * 3)
+
+
+def far_reg(d, eps, p, Mf, Mt):
+    """Regularized far field of one cluster (explicit Taylor coefficients)."""
+    u = np.empty(3)
+    _load().orc_far_reg(_ptr(_c3(d)), float(eps), p, _ptr(_c3(Mf)), _ptr(_c3(Mt)), _ptr(u))
+    return u
 
 
 def coulomb_coeffs(d, P):
@@ -281,6 +340,17 @@ class Tree:
             raise ValueError("oracle treecode needs moments of order >= p")
         if counts:
             return u, dict(far=nf, near_leaves=nl, near_pairs=npairs)
+        return u
+
+    def treecode_reg(self, targets, theta, eps, p=None, nthreads=0):
+        """The same lists summed with the regularized kernels (eps > 0)."""
+        p = self.p if p is None else int(p)
+        t = _c3(targets)
+        u = np.empty((t.shape[0], 3))
+        rc = _load().orc_treecode_eps(self._h, _ptr(t), t.shape[0], float(theta), p, float(eps), _ptr(u), None, None,
+                                      None, nthreads)
+        if rc != 0:
+            raise ValueError("oracle treecode needs moments of order >= p and eps >= 0")
         return u
 
     def treecode_frozen(self, xe, f, h, nu, p, td, te, theta, nthreads=0):

@@ -205,6 +205,76 @@ void orc_direct_grad(const double* x, const double* f, const double* h, const do
 }
 
 /* ------------------------------------------------------------------ */
+/* Regularized kernels.  The paper closes by naming regularized        */
+/* Stokeslets and stresslets as future work and gives neither kernel;  */
+/* these follow the blob of Cortez, Fauci and Medovikov (Phys. Fluids  */
+/* 17, 031504, 2005), phi(r) = 15 eps^4 / (8 pi (r^2 + eps^2)^(7/2)).  */
+/* With s = r^2 + eps^2 and the normalisation of eqs. (1.2a,b):        */
+/*   S^eps_ij = delta_ij (r^2 + 2 eps^2) / s^(3/2) + d_i d_j / s^(3/2), */
+/* the velocity of a regularized point force, and                      */
+/*   T^eps_ijl = [d_i d_j d_l + (eps^2/2)(delta_ij d_l + delta_jl d_i  */
+/*               + delta_il d_j)] / s^(5/2),                           */
+/* minus one sixth of that flow's stress, as T_ijl is of the singular  */
+/* Stokeslet's.  At eps = 0 they are eqs. (1.2a,b).                    */
+/* ------------------------------------------------------------------ */
+void orc_stokeslet_reg(const double* x, const double* y, double eps, double* S)
+{
+    double d[3] = {x[0] - y[0], x[1] - y[1], x[2] - y[2]};
+    double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    double e2 = eps * eps, s = r2 + e2, s32 = s * sqrt(s);
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) S[3 * i + j] = ((i == j ? r2 + 2.0 * e2 : 0.0) + d[i] * d[j]) / s32;
+}
+
+void orc_stresslet_reg(const double* x, const double* y, double eps, double* T)
+{
+    double d[3] = {x[0] - y[0], x[1] - y[1], x[2] - y[2]};
+    double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    double e2 = eps * eps, s = r2 + e2, s52 = s * s * sqrt(s);
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++)
+            for (int l = 0; l < 3; l++) {
+                double v = d[i] * d[j] * d[l];
+                v += 0.5 * e2 * ((i == j ? d[l] : 0.0) + (j == l ? d[i] : 0.0) + (i == l ? d[j] : 0.0));
+                T[9 * i + 3 * j + l] = v / s52;
+            }
+}
+
+/* eq. (1.3) with the regularized kernels; pairs with |x - y| == 0 are
+ * skipped as in orc_direct (the n != m exclusion). */
+void orc_direct_reg(const double* x, const double* f, const double* h, const double* nu, int64_t N,
+                    const double* tx, int64_t M, double eps, double* u, int nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+    (void)nthreads;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t m = 0; m < M; m++) {
+        const double* xm = tx + 3 * m;
+        double acc[3] = {0.0, 0.0, 0.0};
+        for (int64_t n = 0; n < N; n++) {
+            const double* yn = x + 3 * n;
+            if (xm[0] == yn[0] && xm[1] == yn[1] && xm[2] == yn[2]) continue;
+            double S[9], T[27];
+            orc_stokeslet_reg(xm, yn, eps, S);
+            orc_stresslet_reg(xm, yn, eps, T);
+            for (int i = 0; i < 3; i++) {
+                double sum = 0.0;
+                for (int j = 0; j < 3; j++) {
+                    sum += S[3 * i + j] * f[3 * n + j];
+                    for (int l = 0; l < 3; l++) sum += T[9 * i + 3 * j + l] * h[3 * n + j] * nu[3 * n + l];
+                }
+                acc[i] += sum;
+            }
+        }
+        u[3 * m + 0] = acc[0];
+        u[3 * m + 1] = acc[1];
+        u[3 * m + 2] = acc[2];
+    }
+}
+
+/* ------------------------------------------------------------------ */
 /* Multi-index cube helpers.  A cube of order P holds entries          */
 /* (k1,k2,k3) with 0 <= k_a <= P; only ||k|| <= P are meaningful.      */
 /* ------------------------------------------------------------------ */
@@ -387,6 +457,133 @@ void orc_far_explicit(const double* d, int p, const double* Mf, const double* Mt
             }
         }
         u[i] = s;
+    }
+    free(a);
+    free(t);
+}
+
+/* ------------------------------------------------------------------ */
+/* Taylor coefficients of G_nu(x, y) = (|x - y|^2 + eps^2)^(-nu) in y   */
+/* about y_c, ||k|| <= P, nu = two_nu / 2.  Recurrence (3.2) follows    */
+/* from R^2 D G = (x - y) G for G = 1/R; for G_nu, with                 */
+/* s = |x - y|^2 + eps^2, the identity is s D_y G_nu = 2 nu (x - y) G_nu. */
+/* Multiplying its Taylor series by t = y - y_c and summing over the    */
+/* axes (the Euler operator takes t^k to ||k|| t^k) gives, with         */
+/* d = x - y_c, n = ||k||, s_c = |d|^2 + eps^2:                         */
+/*   n s_c c^k - (2n + 2nu - 2) sum_i d_i c^{k-e_i}                    */
+/*                + (n + 2nu - 2) sum_i c^{k-2e_i} = 0,                 */
+/* c^0 = s_c^(-nu); at nu = 1/2, eps = 0 it is (3.2).                   */
+/* ------------------------------------------------------------------ */
+void orc_coeffs_nu(const double* d, double eps, int two_nu, int P, double* c)
+{
+    int n3 = (P + 1) * (P + 1) * (P + 1);
+    for (int i = 0; i < n3; i++) c[i] = 0.0;
+    double sc = d[0] * d[0] + d[1] * d[1] + d[2] * d[2] + eps * eps;
+    double nu2 = (double)two_nu;
+    c[cube_idx(P, 0, 0, 0)] = pow(sc, -0.5 * nu2);
+    for (int n = 1; n <= P; n++)
+        for (int k1 = n; k1 >= 0; k1--)
+            for (int k2 = n - k1; k2 >= 0; k2--) {
+                int k3 = n - k1 - k2;
+                double s1 = d[0] * cube_at(c, P, k1 - 1, k2, k3) + d[1] * cube_at(c, P, k1, k2 - 1, k3) +
+                            d[2] * cube_at(c, P, k1, k2, k3 - 1);
+                double s2 = cube_at(c, P, k1 - 2, k2, k3) + cube_at(c, P, k1, k2 - 2, k3) +
+                            cube_at(c, P, k1, k2, k3 - 2);
+                c[cube_idx(P, k1, k2, k3)] = ((2.0 * n + nu2 - 2.0) * s1 - (n + nu2 - 2.0) * s2) / (n * sc);
+            }
+}
+
+/* Coefficient of t^k in prod_{a in ax[0..na)} (d_a - t_a) g(t), from the
+ * coefficients g of g (product rule: every subset of the factors gives t). */
+static double prod_coef(const double* g, int P, const int* k, const double* d, const int* ax, int na)
+{
+    double v = 0.0;
+    for (int mask = 0; mask < (1 << na); mask++) {
+        int kk[3] = {k[0], k[1], k[2]};
+        double w = 1.0;
+        for (int q = 0; q < na; q++) {
+            if (mask & (1 << q)) {
+                kk[ax[q]] -= 1;
+                w = -w;
+            } else {
+                w *= d[ax[q]];
+            }
+        }
+        v += w * cube_at(g, P, kk[0], kk[1], kk[2]);
+    }
+    return v;
+}
+
+/* Explicit Taylor coefficients of S^eps (layout of orc_taylor_stokeslet)
+ * and T^eps (layout of orc_taylor_stresslet) in y about y_c, ||k|| <= p:
+ * S^eps = delta_ij (G_1 + eps^2 G_3) + d_i d_j G_3 and
+ * T^eps = d_i d_j d_l G_5 + (eps^2/2)(delta_ij d_l + delta_jl d_i + delta_il d_j) G_5,
+ * G_m = s^(-m/2), each factor d_a = x_a - y_a = d_a(y_c) - t_a. */
+void orc_taylor_stokeslet_reg(const double* d, double eps, int p, double* a)
+{
+    int n3 = (p + 1) * (p + 1) * (p + 1);
+    double* g1 = (double*)malloc(sizeof(double) * n3);
+    double* g3 = (double*)malloc(sizeof(double) * n3);
+    orc_coeffs_nu(d, eps, 1, p, g1);
+    orc_coeffs_nu(d, eps, 3, p, g3);
+    for (int c = 0; c < 9 * n3; c++) a[c] = 0.0;
+    for (int k1 = 0; k1 <= p; k1++)
+        for (int k2 = 0; k1 + k2 <= p; k2++)
+            for (int k3 = 0; k1 + k2 + k3 <= p; k3++) {
+                int k[3] = {k1, k2, k3}, ik = cube_idx(p, k1, k2, k3);
+                for (int i = 0; i < 3; i++)
+                    for (int j = 0; j < 3; j++) {
+                        int ax[2] = {i, j};
+                        double v = prod_coef(g3, p, k, d, ax, 2);
+                        if (i == j) v += g1[ik] + eps * eps * g3[ik];
+                        a[(3 * i + j) * n3 + ik] = v;
+                    }
+            }
+    free(g1);
+    free(g3);
+}
+
+void orc_taylor_stresslet_reg(const double* d, double eps, int p, double* t)
+{
+    int n3 = (p + 1) * (p + 1) * (p + 1);
+    double* g5 = (double*)malloc(sizeof(double) * n3);
+    orc_coeffs_nu(d, eps, 5, p, g5);
+    for (int c = 0; c < 27 * n3; c++) t[c] = 0.0;
+    for (int k1 = 0; k1 <= p; k1++)
+        for (int k2 = 0; k1 + k2 <= p; k2++)
+            for (int k3 = 0; k1 + k2 + k3 <= p; k3++) {
+                int k[3] = {k1, k2, k3}, ik = cube_idx(p, k1, k2, k3);
+                for (int i = 0; i < 3; i++)
+                    for (int j = 0; j < 3; j++)
+                        for (int l = 0; l < 3; l++) {
+                            int a3[3] = {i, j, l};
+                            double v = prod_coef(g5, p, k, d, a3, 3), w = 0.0;
+                            if (i == j) w += prod_coef(g5, p, k, d, &a3[2], 1);
+                            if (j == l) w += prod_coef(g5, p, k, d, &a3[0], 1);
+                            if (i == l) w += prod_coef(g5, p, k, d, &a3[1], 1);
+                            t[(9 * i + 3 * j + l) * n3 + ik] = v + 0.5 * eps * eps * w;
+                        }
+            }
+    free(g5);
+}
+
+/* Regularized particle-cluster far field: eq. (2.9) with the regularized
+ * kernels' Taylor coefficients, sum_k a^k_ij M_j^k + a~^k_ijl M~_jl^k. */
+void orc_far_reg(const double* d, double eps, int p, const double* Mf, const double* Mt, double* u)
+{
+    int n3 = (p + 1) * (p + 1) * (p + 1);
+    double* a = (double*)malloc(sizeof(double) * 9 * n3);
+    double* t = (double*)malloc(sizeof(double) * 27 * n3);
+    orc_taylor_stokeslet_reg(d, eps, p, a);
+    orc_taylor_stresslet_reg(d, eps, p, t);
+    for (int i = 0; i < 3; i++) {
+        double sum = 0.0;
+        for (int ik = 0; ik < n3; ik++)
+            for (int j = 0; j < 3; j++) {
+                sum += a[(3 * i + j) * n3 + ik] * Mf[j * n3 + ik];
+                for (int l = 0; l < 3; l++) sum += t[(9 * i + 3 * j + l) * n3 + ik] * Mt[(3 * j + l) * n3 + ik];
+            }
+        u[i] = sum;
     }
     free(a);
     free(t);
@@ -716,12 +913,37 @@ static void leaf_direct(const orc_tree* t, const orc_node* nd, const double* y_a
     }
 }
 
+/* Direct sum of one leaf at xm with the regularized kernels formed
+ * explicitly (orc_stokeslet_reg, orc_stresslet_reg), r == 0 skipped. */
+static void leaf_direct_reg(const orc_tree* t, const orc_node* nd, const double* y_all, const double* f_all,
+                            const double* h_all, const double* nu_all, double eps, const double* xm, double* u)
+{
+    for (int64_t q = 0; q < nd->count; q++) {
+        int64_t n = t->order[nd->begin + q];
+        const double* y = y_all + 3 * n;
+        if (xm[0] == y[0] && xm[1] == y[1] && xm[2] == y[2]) continue;
+        double S[9], T[27];
+        orc_stokeslet_reg(xm, y, eps, S);
+        orc_stresslet_reg(xm, y, eps, T);
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) {
+                u[i] += S[3 * i + j] * f_all[3 * n + j];
+                for (int l = 0; l < 3; l++) u[i] += T[9 * i + 3 * j + l] * h_all[3 * n + j] * nu_all[3 * n + l];
+            }
+    }
+}
+
 /* Far field of cluster moments stored at order P (cubes Mf: 3 x (P+1)^3,
- * Mt: 9 x (P+1)^3), evaluated at order p <= P by eqs. (4.4) + (4.9). */
-static void far_at_order(const double* d, int p, int P, const double* MfP, const double* MtP, double* uf)
+ * Mt: 9 x (P+1)^3), evaluated at order p <= P by eqs. (4.4) + (4.9), or
+ * for eps > 0 by the regularized expansion (orc_far_reg). */
+static void far_at_order(const double* d, int p, int P, const double* MfP, const double* MtP, double eps,
+                         double* uf)
 {
     if (p == P) {
-        orc_far_contracted(d, p, MfP, MtP, uf);
+        if (eps > 0.0)
+            orc_far_reg(d, eps, p, MfP, MtP, uf);
+        else
+            orc_far_contracted(d, p, MfP, MtP, uf);
         return;
     }
     int N3 = (P + 1) * (P + 1) * (P + 1), m3 = (p + 1) * (p + 1) * (p + 1);
@@ -740,7 +962,10 @@ static void far_at_order(const double* d, int p, int P, const double* MfP, const
                     else
                         Mt[(comp - 3) * m3 + cube_idx(p, k1, k2, k3)] = v;
                 }
-    orc_far_contracted(d, p, Mf, Mt, uf);
+    if (eps > 0.0)
+        orc_far_reg(d, eps, p, Mf, Mt, uf);
+    else
+        orc_far_contracted(d, p, Mf, Mt, uf);
     free(Mf);
     free(Mt);
 }
@@ -756,6 +981,7 @@ typedef struct {
     const double *x, *f, *h, *nu;
     const double *Mf, *Mt;
     int P, p;
+    double eps; /* > 0: regularized kernels */
 } orc_sources;
 
 /* u at xm = sum over the interaction list, in list order: far entries by
@@ -769,11 +995,14 @@ static void sum_interactions(const orc_sources* s, const orc_entry* list, int64_
         if (list[e].far) {
             double d[3] = {xm[0] - nd->yc[0], xm[1] - nd->yc[1], xm[2] - nd->yc[2]}, uf[3];
             far_at_order(d, s->p, s->P, s->Mf + (size_t)list[e].node * 3 * N3, s->Mt + (size_t)list[e].node * 9 * N3,
-                         uf);
+                         s->eps, uf);
             for (int i = 0; i < 3; i++) u[i] += uf[i];
             if (cnt) cnt->nfar++;
         } else {
-            leaf_direct(s->t, nd, s->x, s->f, s->h, s->nu, xm, u);
+            if (s->eps > 0.0)
+                leaf_direct_reg(s->t, nd, s->x, s->f, s->h, s->nu, s->eps, xm, u);
+            else
+                leaf_direct(s->t, nd, s->x, s->f, s->h, s->nu, xm, u);
             if (cnt) {
                 cnt->nnear_leaves++;
                 cnt->nnear_pairs += nd->count;
@@ -783,17 +1012,19 @@ static void sum_interactions(const orc_sources* s, const orc_entry* list, int64_
 }
 
 /* Treecode velocity at M targets tx (row-major (M,3)): the interaction list
- * of each target (decided at the target), then its sum.  Requires moments of
- * order >= p.  Optional per-target counters (may be NULL). Returns 0 or -1. */
-int orc_treecode(const orc_tree* t, const double* tx, int64_t M, double theta, int p, double* u, int64_t* nfar,
-                 int64_t* nnear_leaves, int64_t* nnear_pairs, int nthreads)
+ * of each target (decided at the target), then its sum, with the kernels of
+ * eqs. (1.2a,b) (eps = 0) or the regularized ones (eps > 0; same tree, MAC,
+ * moments and lists).  Requires moments of order >= p.  Optional per-target
+ * counters (may be NULL). Returns 0 or -1. */
+int orc_treecode_eps(const orc_tree* t, const double* tx, int64_t M, double theta, int p, double eps, double* u,
+                     int64_t* nfar, int64_t* nnear_leaves, int64_t* nnear_pairs, int nthreads)
 {
-    if (t->p < 0 || p > t->p || p < 0) return -1;
+    if (t->p < 0 || p > t->p || p < 0 || eps < 0.0) return -1;
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
 #endif
     (void)nthreads;
-    const orc_sources s = {t, t->x, t->f, t->h, t->nu, t->Mf, t->Mt, t->p, p};
+    const orc_sources s = {t, t->x, t->f, t->h, t->nu, t->Mf, t->Mt, t->p, p, eps};
 #pragma omp parallel
     {
         orc_entry* list = (orc_entry*)malloc(sizeof(orc_entry) * (size_t)t->nnodes);
@@ -813,6 +1044,12 @@ int orc_treecode(const orc_tree* t, const double* tx, int64_t M, double theta, i
         free(stack);
     }
     return 0;
+}
+
+int orc_treecode(const orc_tree* t, const double* tx, int64_t M, double theta, int p, double* u, int64_t* nfar,
+                 int64_t* nnear_leaves, int64_t* nnear_pairs, int nthreads)
+{
+    return orc_treecode_eps(t, tx, M, theta, p, 0.0, u, nfar, nnear_leaves, nnear_pairs, nthreads);
 }
 
 /* Sum of the counts of the far clusters of each target (partition check). */
@@ -880,7 +1117,7 @@ int orc_treecode_frozen(const orc_tree* t, const double* xe, const double* f, co
         orc_moments(xe, f, h, nu, t->order + nd->begin, nd->count, nd->yc, p, Mf + (size_t)c * 3 * n3,
                     Mt + (size_t)c * 9 * n3);
     }
-    const orc_sources s = {t, xe, f, h, nu, Mf, Mt, p, p};
+    const orc_sources s = {t, xe, f, h, nu, Mf, Mt, p, p, 0.0};
 #pragma omp parallel
     {
         orc_entry* list = (orc_entry*)malloc(sizeof(orc_entry) * (size_t)t->nnodes);

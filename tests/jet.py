@@ -65,8 +65,8 @@ class Jet:
 
     __rmul__ = __mul__
 
-    def rpow_half(self):
-        """self^(-1/2) for a jet with a positive constant term."""
+    def rpow(self, alpha):
+        """self^(-alpha) for a jet with a positive constant term (binomial series)."""
         P = self.P
         s0 = self.c[0, 0, 0]
         eps = Jet(P, self.c.copy())
@@ -76,10 +76,14 @@ class Jet:
         term = Jet.const(P, 1.0)
         coef = 1.0
         for n in range(1, P + 1):
-            coef *= (-0.5 - (n - 1)) / n  # binomial(-1/2, n)
+            coef *= (-alpha - (n - 1)) / n  # binomial(-alpha, n)
             term = term * eps
             out = out + term * coef
-        return out * (s0 ** -0.5)
+        return out * (s0 ** -alpha)
+
+    def rpow_half(self):
+        """self^(-1/2) for a jet with a positive constant term."""
+        return self.rpow(0.5)
 
 
 def kernel_jets(d, P):
@@ -93,3 +97,24 @@ def kernel_jets(d, P):
     S = [[(Jet.const(P, 1.0) * G if i == j else Jet(P)) + dm[i] * dm[j] * G3 for j in range(3)] for i in range(3)]
     T = [[[dm[i] * dm[j] * dm[l] * G5 for l in range(3)] for j in range(3)] for i in range(3)]
     return G, S, T
+
+
+def reg_kernel_jets(d, eps, P):
+    """Jets of the regularized kernels at y = y_c + t, d = x - y_c, straight
+    from their definitions: with s = |x - y|^2 + eps^2,
+    S^eps_ij = (delta_ij (|x - y|^2 + 2 eps^2) + (x - y)_i (x - y)_j) s^(-3/2),
+    T^eps_ijl = ((x - y)_i (x - y)_j (x - y)_l + (eps^2 / 2)(delta_ij (x - y)_l
+    + delta_jl (x - y)_i + delta_il (x - y)_j)) s^(-5/2)."""
+    t = [Jet.var(P, a) for a in range(3)]
+    dm = [t[a] * -1.0 + d[a] for a in range(3)]
+    r2 = dm[0] * dm[0] + dm[1] * dm[1] + dm[2] * dm[2]
+    s = r2 + eps * eps
+    s32 = s.rpow(1.5)
+    s52 = s.rpow(2.5)
+    e2 = eps * eps
+    S = [[((r2 + 2.0 * e2) if i == j else Jet(P)) * s32 + dm[i] * dm[j] * s32 for j in range(3)] for i in range(3)]
+    T = [[[(dm[i] * dm[j] * dm[l]
+            + ((dm[l] if i == j else Jet(P)) + (dm[i] if j == l else Jet(P)) + (dm[j] if i == l else Jet(P)))
+            * (0.5 * e2)) * s52
+           for l in range(3)] for j in range(3)] for i in range(3)]
+    return S, T
