@@ -81,6 +81,19 @@ typedef struct {
                         * p >= 8 (the contraction stays FP32); 0 = FP32, the
                         * default, as accurate on the folded tables          */
     int32_t reserved1; /* must be 0                                            */
+    double reg_eps;    /* 0: the kernels of eqs. (1.2a,b).  > 0: regularized
+                        * Stokeslet and stresslet with this eps (the blob of
+                        * Cortez, Fauci and Medovikov, Phys. Fluids 17, 2005;
+                        * the paper names regularized kernels as future work):
+                        * with s = r^2 + eps^2,
+                        *   S^eps_ij = (delta_ij (r^2 + 2 eps^2) + d_i d_j) / s^(3/2),
+                        *   T^eps_ijl = (d_i d_j d_l + (eps^2/2)(delta_ij d_l
+                        *               + delta_jl d_i + delta_il d_j)) / s^(5/2),
+                        * the same tree, MAC, moments and lists; the far field
+                        * is evaluated in FP64 in both precision modes (the
+                        * harmonic folding of the FP32 path does not hold for
+                        * eps > 0), the near field as the precision mode says.
+                        * Not available for tc_adjoint, tc_tune and batches.  */
 } tc_config;
 
 /* Create a context.  cfg may be NULL (TC_MIXED, shrink = 1, default stream).
@@ -212,6 +225,15 @@ tc_status tc_eval_frozen(tc_ctx* ctx, double* u);
  */
 tc_status tc_direct(const double* x, const double* f, const double* h, const double* nu, int64_t N,
                     const double* targets, int64_t M, int32_t precision, void* stream, double* u);
+
+/*
+ * tc_direct with the regularized kernels of tc_config.reg_eps (eps > 0,
+ * finite): the reference sum for the regularized treecode.  Pairs with
+ * |x - y| == 0 are skipped as in tc_direct.  Same arrays, precision modes,
+ * scratch and stream behaviour as tc_direct.
+ */
+tc_status tc_direct_reg(const double* x, const double* f, const double* h, const double* nu, int64_t N,
+                        const double* targets, int64_t M, double eps, int32_t precision, void* stream, double* u);
 
 /*
  * tc_direct without any device allocation.  The paper has no counterpart:

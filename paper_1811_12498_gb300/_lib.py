@@ -26,6 +26,7 @@ SIGNATURES = {
     "tc_eval_frozen": (_i32, [_vp, _vp]),
     "tc_direct": (_i32, [_vp, _vp, _vp, _vp, _i64, _vp, _i64, _i32, _vp, _vp]),
     "tc_direct_noalloc": (_i32, [_vp, _vp, _vp, _vp, _i64, _vp, _i64, _i32, _vp, _vp]),
+    "tc_direct_reg": (_i32, [_vp, _vp, _vp, _vp, _i64, _vp, _i64, _dbl, _i32, _vp, _vp]),
     "tc_stats": (_i32, [_vp, _vp, _vp, _vp]),
     "tc_eval_counts": (_i32, [_vp, _vp, _vp]),
     "tc_list_stats": (_i32, [_vp, _vp, _vp, _vp]),
@@ -55,7 +56,8 @@ PHASES = ("build", "moments", "tables", "targets", "lists", "far", "near", "fina
 
 
 class TCConfig(ctypes.Structure):
-    _fields_ = [("precision", _i32), ("shrink", _i32), ("stream", _vp), ("rec64", _i32), ("reserved1", _i32)]
+    _fields_ = [("precision", _i32), ("shrink", _i32), ("stream", _vp), ("rec64", _i32), ("reserved1", _i32),
+                ("reg_eps", _dbl)]
 
 
 _lib = None

@@ -80,12 +80,14 @@ def _stream_ptr(stream):
 class Treecode:
     """One treecode context (tc_ctx): tree, moments and interaction lists."""
 
-    def __init__(self, precision="mixed", shrink=True, stream=None, rec64=False):
+    def __init__(self, precision="mixed", shrink=True, stream=None, rec64=False, reg_eps=0.0):
         """rec64: in mixed precision, run the far-field recurrence in FP64 for
-        p >= 8 (tc_config.rec64)."""
+        p >= 8 (tc_config.rec64).  reg_eps > 0: the regularized Stokeslet and
+        stresslet with that eps (tc_config.reg_eps)."""
         self.precision = _prec(precision)
         self.stream = torch.cuda.current_stream() if stream is None else stream
-        cfg = TCConfig(self.precision, int(bool(shrink)), _stream_ptr(self.stream), int(bool(rec64)), 0)
+        cfg = TCConfig(self.precision, int(bool(shrink)), _stream_ptr(self.stream), int(bool(rec64)), 0,
+                       float(reg_eps))
         h = ctypes.c_void_p()
         _check(lib().tc_create(ctypes.byref(h), ctypes.byref(cfg)))
         self._h = h
@@ -303,6 +305,21 @@ def direct(x, f, h, nu, targets=None, precision="fp64", out=None, stream=None):
     _vec3(out, "out", M)
     _check(lib().tc_direct(_ptr(x), _ptr(f), _ptr(h), _ptr(nu), N, _ptr(t), M, _prec(precision),
                            _stream_ptr(stream), _ptr(out)))
+    return out
+
+
+def direct_reg(x, f, h, nu, eps, targets=None, precision="fp64", out=None, stream=None):
+    """O(N M) sum of eq. (1.3) with the regularized kernels (tc_direct_reg)."""
+    x = _vec3(x, "x")
+    N = x.shape[1]
+    f, h, nu = (_vec3(a, n, N) for a, n in ((f, "f"), (h, "h"), (nu, "nu")))
+    t = _vec3(targets, "targets")
+    M = N if t is None else t.shape[1]
+    if out is None:
+        out = torch.empty((3, M), dtype=torch.float64, device="cuda")
+    _vec3(out, "out", M)
+    _check(lib().tc_direct_reg(_ptr(x), _ptr(f), _ptr(h), _ptr(nu), N, _ptr(t), M, float(eps), _prec(precision),
+                               _stream_ptr(stream), _ptr(out)))
     return out
 
 

@@ -306,7 +306,7 @@ struct NearOpG {
     static constexpr bool kAdd = true;
     // the guard-free variant measured slower here (more registers)
     static constexpr bool kUnguarded = false;
-    __device__ static Tgt load(const double* ts, const double* gs, int64_t M, int64_t m, bool valid)
+    __device__ static Tgt load(const double* ts, const double* gs, int64_t M, int64_t m, bool valid, float)
     {
         float h[3] = {0, 0, 0}, l[3] = {0, 0, 0}, g[3] = {0, 0, 0};
         if (valid)
@@ -375,7 +375,7 @@ __global__ void __launch_bounds__(kNearAdjWarps * 32)
     const int64_t ngroup = ((M + kBatch - 1) / kBatch + kNearAdjGroup - 1) / kNearAdjGroup;
     const int64_t B = blockIdx.x * (int64_t)kNearAdjWarps + w;
     if (B >= ngroup) return;
-    nearpair::near_group<kNearAdjGroup, NearOpG>(ts, gs, M, topo, spack, near_off, near_list, gt, B, self, sc[w],
+    nearpair::near_group<kNearAdjGroup, NearOpG>(ts, gs, M, topo, spack, near_off, near_list, gt, B, self, 0.0f, sc[w],
                                                   lane);
 }
 
@@ -1360,6 +1360,7 @@ extern "C" tc_status tc_adjoint(tc_ctx* ctx, const double* g, double* grad_f, do
 {
     if (!ctx) return fail(nullptr, TC_EINVAL, "tc_adjoint: ctx is NULL");
     if (!ctx->have_eval) return fail(ctx, TC_ESTATE, "tc_adjoint: call tc_eval first");
+    if (ctx->reg_eps > 0.0) return fail(ctx, TC_EINVAL, "tc_adjoint: not available for the regularized kernels");
     if (!g) return fail(ctx, TC_EINVAL, "tc_adjoint: g is NULL");
     if (ctx->eval_self && grad_t)
         return fail(ctx, TC_EINVAL, "tc_adjoint: grad_t must be NULL when targets are the sources (use grad_x)");

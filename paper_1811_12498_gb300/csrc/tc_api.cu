@@ -115,7 +115,7 @@ static void release_all(tc_ctx* c)
                       &c->split_cnt,
                       &c->split_off, &c->scan_tmp, &c->ws, &c->spack, &c->mom, &c->mom_tmp, &c->ab64, &c->ab32,
                       &c->abf64,
-                      &c->abf32, &c->geo32, &c->tkeys,
+                      &c->abf32, &c->geo32, &c->reg_et, &c->tkeys,
                       &c->tkeys_alt, &c->tperm, &c->tperm_alt, &c->ts, &c->nfar_e, &c->nnear_e,
                       &c->far_off, &c->near_off, &c->far_list, &c->near_list, &c->cnt_far, &c->cnt_near, &c->u_far,
                       &c->u_near, &c->near_gkey, &c->near_gkey_alt, &c->near_gord, &c->near_gord_alt, &c->flags, &c->adj_fkeys, &c->adj_fkeys_alt, &c->adj_fidx, &c->adj_fidx_alt,
@@ -132,8 +132,10 @@ tc_status tc_create(tc_ctx** out, const tc_config* cfg)
     tc_ctx* ctx = nullptr;
     if (!out) return fail(nullptr, TC_EINVAL, "tc_create: out is NULL");
     *out = nullptr;
-    tc_config c = {TC_MIXED, 1, nullptr, 0, 0};
+    tc_config c = {TC_MIXED, 1, nullptr, 0, 0, 0.0};
     if (cfg) c = *cfg;
+    if (!(c.reg_eps >= 0.0) || !std::isfinite(c.reg_eps))
+        return fail(nullptr, TC_EINVAL, "tc_create: reg_eps = %g must be >= 0 and finite", c.reg_eps);
     if (c.precision != TC_FP64 && c.precision != TC_MIXED)
         return fail(nullptr, TC_EINVAL, "tc_create: unknown precision %d", c.precision);
     if (c.shrink != 0 && c.shrink != 1) return fail(nullptr, TC_EINVAL, "tc_create: shrink must be 0 or 1");
@@ -155,6 +157,7 @@ tc_status tc_create(tc_ctx** out, const tc_config* cfg)
     ctx->precision = c.precision;
     ctx->rec64 = c.precision == TC_MIXED ? c.rec64 : 0;
     ctx->shrink = c.shrink;
+    ctx->reg_eps = c.reg_eps;
     ctx->stream = (cudaStream_t)c.stream;
     ctx->err = "no error";
     *out = ctx;
@@ -424,6 +427,12 @@ static tc_status ensure_tables(tc_ctx* ctx, int p, cudaStream_t s)
                              ptr<Geo>(ctx->node_geo), ptr<double>(ctx->node_invrho),
                              ctx->precision == TC_FP64 ? nullptr : ptr<float4>(ctx->geo32), s),
           "fold tables");
+    if (ctx->reg_eps > 0.0) {
+        TC_CK(ensure(ctx->reg_et, (size_t)ctx->nnodes * ncoef(p + 1) * 3 * 8), "alloc tables");
+        TC_CK(launch_eps_table(ptr<double>(ctx->mom), ptr<double>(ctx->node_invrho), ctx->nnodes, ctx->p_mom, p,
+                               ctx->reg_eps, ptr<double>(ctx->reg_et), s),
+              "eps table");
+    }
     ph_end(ctx, TC_PH_TABLES, s);
     ctx->ab_p = p;
     return TC_OK;
@@ -554,13 +563,19 @@ tc_status tc::eval_compute(tc_ctx* ctx, double* u)
     TC_CK(cudaEventRecord(ctx->ev_fork, s), "fork");
     TC_CK(cudaStreamWaitEvent(s2, ctx->ev_fork, 0), "fork");
     ph_begin(ctx, TC_PH_FAR, s2);
-    TC_CK(launch_far(ctx->precision, ctx->rec64, ts, M, ptr<int4>(ctx->node_topo), ptr<Geo>(ctx->node_geo),
-                     ptr<double>(ctx->node_invrho),
-                     ptr<float4>(ctx->geo32), ptr<double>(ctx->abf64), ptr<float>(ctx->abf32), p,
-                     ptr<int64_t>(ctx->far_off),
-                     ptr<ListEntry>(ctx->far_list), ptr<double>(ctx->u_far),
-                     reinterpret_cast<unsigned*>(ptr<char>(ctx->flags) + 128), s2),
-          "far field");
+    if (ctx->reg_eps > 0.0)
+        TC_CK(launch_far_reg(ts, M, ptr<Geo>(ctx->node_geo), ptr<double>(ctx->node_invrho), ptr<double>(ctx->ab64),
+                             ptr<double>(ctx->reg_et), p, ctx->reg_eps, ptr<int64_t>(ctx->far_off),
+                             ptr<ListEntry>(ctx->far_list), ptr<double>(ctx->u_far), s2),
+              "far field");
+    else
+        TC_CK(launch_far(ctx->precision, ctx->rec64, ts, M, ptr<int4>(ctx->node_topo), ptr<Geo>(ctx->node_geo),
+                         ptr<double>(ctx->node_invrho),
+                         ptr<float4>(ctx->geo32), ptr<double>(ctx->abf64), ptr<float>(ctx->abf32), p,
+                         ptr<int64_t>(ctx->far_off),
+                         ptr<ListEntry>(ctx->far_list), ptr<double>(ctx->u_far),
+                         reinterpret_cast<unsigned*>(ptr<char>(ctx->flags) + 128), s2),
+              "far field");
     ph_end(ctx, TC_PH_FAR, s2);
     TC_CK(cudaEventRecord(ctx->ev_join, s2), "join");
     ph_begin(ctx, TC_PH_NEAR);
@@ -569,7 +584,7 @@ tc_status tc::eval_compute(tc_ctx* ctx, double* u)
                              reinterpret_cast<unsigned*>(ptr<char>(ctx->flags) + 160)};
     TC_CK(launch_near(ctx->precision, ts, M, ptr<int4>(ctx->node_topo), ptr<double>(ctx->xs), ptr<double>(ctx->ws),
                       ptr<float4>(ctx->spack), ctx->N, ptr<int64_t>(ctx->near_off), ptr<ListEntry>(ctx->near_list),
-                      ptr<double>(ctx->u_near), ctx->eval_self && !ctx->moved, sched, s),
+                      ptr<double>(ctx->u_near), ctx->eval_self && !ctx->moved, sched, ctx->reg_eps, s),
           "near field");
     ph_end(ctx, TC_PH_NEAR);
     TC_CK(cudaStreamWaitEvent(s, ctx->ev_join, 0), "join");
@@ -663,24 +678,39 @@ tc_status tc_eval(tc_ctx* ctx, const double* targets, int64_t M, double theta, i
     return eval_compute(ctx, u);
 }
 
-tc_status tc_direct(const double* x, const double* f, const double* h, const double* nu, int64_t N,
-                    const double* targets, int64_t M, int32_t precision, void* stream, double* u)
+static tc_status direct_impl(const char* name, const double* x, const double* f, const double* h, const double* nu,
+                             int64_t N, const double* targets, int64_t M, double eps, int32_t precision, void* stream,
+                             double* u)
 {
     tc_ctx* ctx = nullptr;
-    if (!x || !f || !h || !nu || !u) return fail(nullptr, TC_EINVAL, "tc_direct: a pointer is NULL");
-    if (N < 1 || N >= ((int64_t)1 << 31)) return fail(nullptr, TC_EINVAL, "tc_direct: N out of range");
-    if (!targets && M != N) return fail(nullptr, TC_EINVAL, "tc_direct: targets = NULL requires M = N");
-    if (M < 1 || M >= ((int64_t)1 << 31)) return fail(nullptr, TC_EINVAL, "tc_direct: M out of range");
-    if (precision != TC_FP64 && precision != TC_MIXED) return fail(nullptr, TC_EINVAL, "tc_direct: unknown precision");
+    if (!x || !f || !h || !nu || !u) return fail(nullptr, TC_EINVAL, "%s: a pointer is NULL", name);
+    if (N < 1 || N >= ((int64_t)1 << 31)) return fail(nullptr, TC_EINVAL, "%s: N out of range", name);
+    if (!targets && M != N) return fail(nullptr, TC_EINVAL, "%s: targets = NULL requires M = N", name);
+    if (M < 1 || M >= ((int64_t)1 << 31)) return fail(nullptr, TC_EINVAL, "%s: M out of range", name);
+    if (precision != TC_FP64 && precision != TC_MIXED) return fail(nullptr, TC_EINVAL, "%s: unknown precision", name);
     cudaStream_t s = (cudaStream_t)stream;
     size_t bytes = direct_scratch_bytes(precision, N, M);
     void* scratch = nullptr;
-    TC_CK(alloc_should_fail() ? cudaErrorMemoryAllocation : cudaMallocAsync(&scratch, bytes, s), "tc_direct scratch");
-    cudaError_t e = launch_direct(precision, x, f, h, nu, N, targets ? targets : x, M, u, scratch, bytes, s);
+    TC_CK(alloc_should_fail() ? cudaErrorMemoryAllocation : cudaMallocAsync(&scratch, bytes, s), "direct scratch");
+    cudaError_t e = launch_direct(precision, x, f, h, nu, N, targets ? targets : x, M, u, scratch, bytes, eps, s);
     cudaError_t e2 = cudaFreeAsync(scratch, s);
-    if (e != cudaSuccess) return cuda_fail(nullptr, e, "tc_direct");
-    if (e2 != cudaSuccess) return cuda_fail(nullptr, e2, "tc_direct free");
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, name);
+    if (e2 != cudaSuccess) return cuda_fail(nullptr, e2, "direct free");
     return TC_OK;
+}
+
+tc_status tc_direct(const double* x, const double* f, const double* h, const double* nu, int64_t N,
+                    const double* targets, int64_t M, int32_t precision, void* stream, double* u)
+{
+    return direct_impl("tc_direct", x, f, h, nu, N, targets, M, 0.0, precision, stream, u);
+}
+
+tc_status tc_direct_reg(const double* x, const double* f, const double* h, const double* nu, int64_t N,
+                        const double* targets, int64_t M, double eps, int32_t precision, void* stream, double* u)
+{
+    if (!(eps > 0.0) || !std::isfinite(eps))
+        return fail(nullptr, TC_EINVAL, "tc_direct_reg: eps = %g must be positive and finite", eps);
+    return direct_impl("tc_direct_reg", x, f, h, nu, N, targets, M, eps, precision, stream, u);
 }
 
 tc_status tc_stats(tc_ctx* ctx, int64_t* near_pairs, int64_t* far_interactions, int64_t* clusters)

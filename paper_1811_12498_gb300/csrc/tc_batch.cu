@@ -236,10 +236,11 @@ tc_status tc_batch_create(tc_batch** out, const tc_config* cfg)
 {
     if (!out) return fail(nullptr, TC_EINVAL, "tc_batch_create: out is NULL");
     *out = nullptr;
-    tc_config c = {TC_MIXED, 1, nullptr, 0, 0};
+    tc_config c = {TC_MIXED, 1, nullptr, 0, 0, 0.0};
     if (cfg) c = *cfg;
     if (c.precision != TC_FP64 && c.precision != TC_MIXED)
         return fail(nullptr, TC_EINVAL, "tc_batch_create: unknown precision %d", c.precision);
+    if (c.reg_eps != 0.0) return fail(nullptr, TC_EINVAL, "tc_batch_create: batches use the kernels of eqs. (1.2a,b)");
     if (c.shrink != 0 && c.shrink != 1) return fail(nullptr, TC_EINVAL, "tc_batch_create: shrink must be 0 or 1");
     if (c.rec64 != 0 && c.rec64 != 1) return fail(nullptr, TC_EINVAL, "tc_batch_create: rec64 must be 0 or 1");
     tc_batch* b = new (std::nothrow) tc_batch();

@@ -1,5 +1,9 @@
 // Direct O(N*M) evaluation of eq. (1.3) in the contracted form of
-// Section 4.1 (the reference u^d of eq. 6.1 for the error E).
+// Section 4.1 (the reference u^d of eq. 6.1 for the error E), and of the same
+// sum with the regularized kernels (kReg; the blob of Cortez, Fauci and
+// Medovikov, s = r^2 + eps^2, q = s^-1/2):
+//   u_i += f_i q (1 + eps^2 q^2) + d_i q^3 ((d.f) + q^2 ((d.h)(d.nu) + (eps^2/2)(h.nu)))
+//          + (eps^2/2) q^5 (h_i (d.nu) + nu_i (d.h)).
 //
 // Warps own 32 targets; the source range is split into `nsplit` chunks along
 // gridDim.y so that few targets (e.g. 10^4 sampled targets against 10^6
@@ -29,13 +33,17 @@ __global__ void k_direct_pack(const double* __restrict__ x, const double* __rest
     pack[4 * i + 0] = make_float4(hi[0], hi[1], hi[2], (float)f[i]);
     pack[4 * i + 1] = make_float4(lo[0], lo[1], lo[2], (float)f[N + i]);
     pack[4 * i + 2] = make_float4((float)f[2 * N + i], (float)h[i], (float)h[N + i], (float)h[2 * N + i]);
-    pack[4 * i + 3] = make_float4((float)nu[i], (float)nu[N + i], (float)nu[2 * N + i], 0.0f);
+    // the fourth slot holds h.nu, which only the regularized pair terms read
+    const double hn = h[i] * nu[i] + h[N + i] * nu[N + i] + h[2 * N + i] * nu[2 * N + i];
+    pack[4 * i + 3] = make_float4((float)nu[i], (float)nu[N + i], (float)nu[2 * N + i], (float)hn);
 }
 
+template <bool kReg>
 __global__ void __launch_bounds__(kDirWarps * 32)
     k_direct_mixed(const double* __restrict__ t, int64_t M, const float4* __restrict__ pack, int64_t N, int64_t chunk,
-                   double* __restrict__ part)
+                   double* __restrict__ part, float e2)
 {
+    const float e2h = 0.5f * e2;
     __shared__ float4 tile[kDirWarps][32][4];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t nbatch = (M + 31) / 32;
@@ -70,16 +78,28 @@ __global__ void __launch_bounds__(kDirWarps * 32)
             const float dy = (th[1] - p0.y) + (tl[1] - p1.y);
             const float dz = (th[2] - p0.z) + (tl[2] - p1.z);
             const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            const float ri = r2 > 0.f ? rsqrt_ftz(r2) : 0.f;
-            const float ri2 = ri * ri;
-            const float ri3 = ri2 * ri;
             const float df = fmaf(dx, p0.w, fmaf(dy, p1.w, dz * p2.x));
             const float dh = fmaf(dx, p2.y, fmaf(dy, p2.z, dz * p2.w));
             const float dn = fmaf(dx, p3.x, fmaf(dy, p3.y, dz * p3.z));
-            const float st = ri3 * fmaf(dh * dn, ri2, df);
-            ax = fmaf(p0.w, ri, fmaf(dx, st, ax));
-            ay = fmaf(p1.w, ri, fmaf(dy, st, ay));
-            az = fmaf(p2.x, ri, fmaf(dz, st, az));
+            if (kReg) {
+                const float q = r2 > 0.f ? rsqrt_ftz(r2 + e2) : 0.f;
+                const float q2 = q * q;
+                const float a1 = q * fmaf(e2, q2, 1.0f);
+                const float qs = q * q2 * fmaf(q2, fmaf(dh, dn, e2h * p3.w), df);
+                const float w = e2h * q * q2 * q2;
+                const float wn = w * dn, wh = w * dh;
+                ax = fmaf(p0.w, a1, fmaf(dx, qs, fmaf(p2.y, wn, fmaf(p3.x, wh, ax))));
+                ay = fmaf(p1.w, a1, fmaf(dy, qs, fmaf(p2.z, wn, fmaf(p3.y, wh, ay))));
+                az = fmaf(p2.x, a1, fmaf(dz, qs, fmaf(p2.w, wn, fmaf(p3.z, wh, az))));
+            } else {
+                const float ri = r2 > 0.f ? rsqrt_ftz(r2) : 0.f;
+                const float ri2 = ri * ri;
+                const float ri3 = ri2 * ri;
+                const float st = ri3 * fmaf(dh * dn, ri2, df);
+                ax = fmaf(p0.w, ri, fmaf(dx, st, ax));
+                ay = fmaf(p1.w, ri, fmaf(dy, st, ay));
+                az = fmaf(p2.x, ri, fmaf(dz, st, az));
+            }
         }
         ux += (double)ax;
         uy += (double)ay;
@@ -93,11 +113,13 @@ __global__ void __launch_bounds__(kDirWarps * 32)
     }
 }
 
+template <bool kReg>
 __global__ void __launch_bounds__(kDirWarps * 32)
     k_direct_fp64(const double* __restrict__ t, int64_t M, const double* __restrict__ x, const double* __restrict__ f,
                   const double* __restrict__ h, const double* __restrict__ nu, int64_t N, int64_t chunk,
-                  double* __restrict__ part)
+                  double* __restrict__ part, double e2)
 {
+    const double e2h = 0.5 * e2;
     __shared__ double tile[kDirWarps][12][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t nbatch = (M + 31) / 32;
@@ -126,16 +148,29 @@ __global__ void __launch_bounds__(kDirWarps * 32)
         for (int j = 0; j < cnt; j++) {
             const double dx = tx[0] - tile[w][0][j], dy = tx[1] - tile[w][1][j], dz = tx[2] - tile[w][2][j];
             const double r2 = dx * dx + dy * dy + dz * dz;
-            const double ri = r2 > 0.0 ? rsqrt(r2) : 0.0;
-            const double ri2 = ri * ri, ri3 = ri2 * ri;
             const double f0 = tile[w][3][j], f1 = tile[w][4][j], f2 = tile[w][5][j];
             const double df = dx * f0 + dy * f1 + dz * f2;
             const double dh = dx * tile[w][6][j] + dy * tile[w][7][j] + dz * tile[w][8][j];
             const double dn = dx * tile[w][9][j] + dy * tile[w][10][j] + dz * tile[w][11][j];
-            const double st = ri3 * (df + dh * dn * ri2);
-            ux += f0 * ri + dx * st;
-            uy += f1 * ri + dy * st;
-            uz += f2 * ri + dz * st;
+            if (kReg) {
+                if (!(r2 > 0.0)) continue;
+                const double hn = tile[w][6][j] * tile[w][9][j] + tile[w][7][j] * tile[w][10][j] +
+                                  tile[w][8][j] * tile[w][11][j];
+                const double q = rsqrt(r2 + e2), q2 = q * q;
+                const double a1 = q * (1.0 + e2 * q2);
+                const double qs = q * q2 * (df + q2 * (dh * dn + e2h * hn));
+                const double wq = e2h * q * q2 * q2;
+                ux += f0 * a1 + dx * qs + wq * (tile[w][6][j] * dn + tile[w][9][j] * dh);
+                uy += f1 * a1 + dy * qs + wq * (tile[w][7][j] * dn + tile[w][10][j] * dh);
+                uz += f2 * a1 + dz * qs + wq * (tile[w][8][j] * dn + tile[w][11][j] * dh);
+            } else {
+                const double ri = r2 > 0.0 ? rsqrt(r2) : 0.0;
+                const double ri2 = ri * ri, ri3 = ri2 * ri;
+                const double st = ri3 * (df + dh * dn * ri2);
+                ux += f0 * ri + dx * st;
+                uy += f1 * ri + dy * st;
+                uz += f2 * ri + dz * st;
+            }
         }
     }
     if (valid) {
@@ -195,7 +230,7 @@ size_t direct_scratch_bytes(int precision, int64_t N, int64_t M)
 
 cudaError_t launch_direct(int precision, const double* x, const double* f, const double* h, const double* nu,
                           int64_t N, const double* t, int64_t M, double* u, void* scratch, size_t scratch_bytes,
-                          cudaStream_t s)
+                          double eps, cudaStream_t s)
 {
     DirectPlan pl = plan_direct(precision, N, M);
     size_t pack_off = ((pl.pack_bytes + 255) / 256) * 256;
@@ -204,13 +239,20 @@ cudaError_t launch_direct(int precision, const double* x, const double* f, const
     double* part = reinterpret_cast<double*>(reinterpret_cast<char*>(scratch) + pack_off);
     int64_t nbatch = (M + 31) / 32;
     dim3 grid((unsigned)((nbatch + kDirWarps - 1) / kDirWarps), (unsigned)pl.nsplit);
+    const double e2 = eps * eps;
     if (precision == TC_FP64) {
-        k_direct_fp64<<<grid, kDirWarps * 32, 0, s>>>(t, M, x, f, h, nu, N, pl.chunk, part);
+        if (eps > 0.0)
+            k_direct_fp64<true><<<grid, kDirWarps * 32, 0, s>>>(t, M, x, f, h, nu, N, pl.chunk, part, e2);
+        else
+            k_direct_fp64<false><<<grid, kDirWarps * 32, 0, s>>>(t, M, x, f, h, nu, N, pl.chunk, part, 0.0);
         note_launch();
     } else {
         k_direct_pack<<<grid_for(N, 256), 256, 0, s>>>(x, f, h, nu, N, pack);
         note_launch();
-        k_direct_mixed<<<grid, kDirWarps * 32, 0, s>>>(t, M, pack, N, pl.chunk, part);
+        if (eps > 0.0)
+            k_direct_mixed<true><<<grid, kDirWarps * 32, 0, s>>>(t, M, pack, N, pl.chunk, part, (float)e2);
+        else
+            k_direct_mixed<false><<<grid, kDirWarps * 32, 0, s>>>(t, M, pack, N, pl.chunk, part, 0.0f);
         note_launch();
     }
     k_direct_reduce<<<grid_for(3 * M, 256), 256, 0, s>>>(part, pl.nsplit, M, u);
@@ -299,12 +341,12 @@ extern "C" tc_status tc_direct_noalloc(const double* x, const double* f, const d
     // every scratch word read below is first written by this call: the pack by
     // k_direct_pack, each split's partial block by its own k_direct_* launch
     if (precision == TC_FP64) {
-        k_direct_fp64<<<grid, kDirWarps * 32, 0, s>>>(t, M, x, f, h, nu, N, pl.chunk, part);
+        k_direct_fp64<false><<<grid, kDirWarps * 32, 0, s>>>(t, M, x, f, h, nu, N, pl.chunk, part, 0.0);
         note_launch();
     } else {
         k_direct_pack<<<grid_for(N, 256), 256, 0, s>>>(x, f, h, nu, N, pack);
         note_launch();
-        k_direct_mixed<<<grid, kDirWarps * 32, 0, s>>>(t, M, pack, N, pl.chunk, part);
+        k_direct_mixed<false><<<grid, kDirWarps * 32, 0, s>>>(t, M, pack, N, pl.chunk, part, 0.0f);
         note_launch();
     }
     k_direct_reduce<<<grid_for(3 * M, 256), 256, 0, s>>>(part, pl.nsplit, M, u);

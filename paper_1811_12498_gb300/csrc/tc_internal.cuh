@@ -152,6 +152,8 @@ struct tc_ctx {
     tc::DevBuf ab32;                    // FP32 [node][ncoef(p+2)][12]
     tc::DevBuf abf64, abf32;            // folded tables [node][(p+3)^2][12], level n times lambda_n
     tc::DevBuf geo32;                   // mixed: per node (y_c hi, 1/rho), (y_c lo, 0) as float4
+    tc::DevBuf reg_et;                  // regularized kernels: FP64 [node][ncoef(p+1)][3] eps^2 table
+    double reg_eps = 0.0;               // > 0: regularized kernels (tc_config.reg_eps)
 
     // ---- evaluation (tc_eval)
     int64_t M = 0;
@@ -281,6 +283,8 @@ cudaError_t launch_moments(const int4* topo, const Geo* geo, const double* xs, c
 cudaError_t launch_m2m(const int4* topo, const Geo* geo, int64_t lb, int64_t le, int p, double* mom, cudaStream_t s);
 cudaError_t launch_ab_tables(const double* mom, const double* invrho, int64_t nnodes, int pm, int p, double* ab64,
                              float* ab32, cudaStream_t s);
+cudaError_t launch_eps_table(const double* mom, const double* invrho, int64_t nnodes, int pm, int p, double eps,
+                             double* et, cudaStream_t s);
 cudaError_t launch_fold_tables(const double* ab64, int64_t nnodes, int p, double* abf64, float* abf32,
                                const Geo* geo, const double* invrho, float4* geo32, cudaStream_t s);
 
@@ -330,16 +334,22 @@ cudaError_t launch_finalize_batched(const SysDesc* sys, int nsys, const int64_t*
 cudaError_t launch_near(int precision, const double* ts, int64_t M, const int4* topo,
                         const double* xs, const double* ws, const float4* spack, int64_t N,
                         const int64_t* near_off, const ListEntry* near_list, double* u_near, int self,
-                        const NearSched& sched, cudaStream_t s);
+                        const NearSched& sched, double eps, cudaStream_t s);
+// tc_reg.cu: far field of the regularized kernels (eps > 0), FP64, on the
+// FP64 contraction tables ab64 and the eps^2 table et of launch_eps_table
+cudaError_t launch_far_reg(const double* ts, int64_t M, const Geo* geo, const double* invrho, const double* ab64,
+                           const double* et, int p, double eps, const int64_t* far_off, const ListEntry* far_list,
+                           double* u_far, cudaStream_t s);
 cudaError_t launch_finalize(const double* u_far, const double* u_near, const int32_t* perm, int64_t M, double* u,
                             cudaStream_t s);
 cudaError_t launch_scatter_counts(const int64_t* cs, const int32_t* perm, int64_t M, int64_t* out,
                                   cudaStream_t s);
 
 // tc_direct.cu
+// eps > 0: the regularized kernels
 cudaError_t launch_direct(int precision, const double* x, const double* f, const double* h, const double* nu,
                           int64_t N, const double* t, int64_t M, double* u, void* scratch, size_t scratch_bytes,
-                          cudaStream_t s);
+                          double eps, cudaStream_t s);
 size_t direct_scratch_bytes(int precision, int64_t N, int64_t M);
 
 }  // namespace tc

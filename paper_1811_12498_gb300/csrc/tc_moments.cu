@@ -75,7 +75,9 @@ __global__ void k_source_pack(const double* __restrict__ xs, const double* __res
     pack[4 * i + 0] = make_float4(hi[0], hi[1], hi[2], w[0]);
     pack[4 * i + 1] = make_float4(lo[0], lo[1], lo[2], w[1]);
     pack[4 * i + 2] = make_float4(w[2], w[3], w[4], w[5]);
-    pack[4 * i + 3] = make_float4(w[6], w[7], w[8], 0.0f);
+    // the last slot holds h.nu, which only the regularized pair terms read
+    const double hn = ws[3 * N + i] * ws[6 * N + i] + ws[4 * N + i] * ws[7 * N + i] + ws[5 * N + i] * ws[8 * N + i];
+    pack[4 * i + 3] = make_float4(w[6], w[7], w[8], (float)hn);
 }
 
 constexpr int kMomThreads = 128;
@@ -353,6 +355,50 @@ __global__ void k_ab_tables(const double* __restrict__ mom, const double* __rest
         for (int c = 0; c < 12; c++) ab32[o + c] = (float)out[c];
 }
 
+// Regularized kernels.  With G_m = (|x - y|^2 + eps^2)^(-m/2) the
+// regularized Stokeslet is delta_ij G_1 + (x_j - y_j) D_{y_i} G_1 + eps^2
+// delta_ij G_3 and the regularized stresslet is
+// (1/3)[(x_l - y_l) D_{y_i} D_{y_j} G_1 + delta_ij D_{y_l} G_1]
+// + (eps^2/6)(delta_ij D_{y_l} G_3 + delta_jl D_{y_i} G_3 + delta_il D_{y_j} G_3):
+// the G_1 parts have the structure of eqs. (4.4)/(4.9), so the tables above
+// apply with the Coulomb coefficients replaced by those of G_1; the eps^2
+// parts contract the Taylor coefficients c^k of G_3 against
+//   E_i^k = eps^2 M_i^k + (eps^2/6)[sum_l k_l M~_il^{k-e_l}
+//           + k_i sum_j M~_jj^{k-e_i} + sum_j k_j M~_ji^{k-e_j}],  ||k|| <= p + 1,
+// stored scaled by rho^-(n+3) (n = ||k||; the coefficients are then taken at
+// d' = (x - y_c)/rho and eps' = eps/rho).  One thread per (cluster, k),
+// layout [node][flat(k)][3].
+__global__ void k_eps_table(const double* __restrict__ mom, const double* __restrict__ invrho, int64_t nnodes,
+                            int pm, int p, double eps, double* __restrict__ et)
+{
+    const int C = ncoef(pm), C1 = ncoef(p + 1);
+    const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (gid >= nnodes * C1) return;
+    const int64_t node = gid / C1;
+    int k[3];
+    unflatten((int)(gid - node * C1), k[0], k[1], k[2]);
+    const int n = k[0] + k[1] + k[2];
+    const double* m = mom + node * 12 * C;
+    const double e2 = eps * eps;
+    double tr = 0.0;  // sum_j M~_jj shifted per i below
+    double sc = invrho[node] * invrho[node] * invrho[node];
+    for (int q = 0; q < n; q++) sc *= invrho[node];
+    for (int i = 0; i < 3; i++) {
+        int ei[3] = {i == 0, i == 1, i == 2};
+        double v = e2 * mget(m, C, p, i, k[0], k[1], k[2]);
+        double t = 0.0;
+        for (int l = 0; l < 3; l++) {
+            int el[3] = {l == 0, l == 1, l == 2};
+            t += k[l] * mget(m, C, p, 3 + 3 * i + l, k[0] - el[0], k[1] - el[1], k[2] - el[2]);
+            t += k[l] * mget(m, C, p, 3 + 3 * l + i, k[0] - el[0], k[1] - el[1], k[2] - el[2]);
+        }
+        tr = 0.0;
+        for (int j = 0; j < 3; j++) tr += mget(m, C, p, 3 + 4 * j, k[0] - ei[0], k[1] - ei[1], k[2] - ei[2]);
+        t += k[i] * tr;
+        et[gid * 3 + i] = (v + e2 / 6.0 * t) * sc;
+    }
+}
+
 // Harmonic folding of the tables.  The b^k are the Taylor coefficients of
 // 1/|d - t| in t, a harmonic function, so (Laplace's equation)
 //   sum_i (k_i + 2)(k_i + 1) b^{k + 2 e_i} = 0,
@@ -497,6 +543,15 @@ cudaError_t launch_fold_tables(const double* ab64, int64_t nnodes, int p, double
     cudaError_t e = cudaFuncSetAttribute(k_fold_tables, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_fold_tables<<<(unsigned)nnodes, 128, smem, s>>>(ab64, nnodes, p, abf64, abf32, geo, invrho, geo32);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_eps_table(const double* mom, const double* invrho, int64_t nnodes, int pm, int p, double eps,
+                             double* et, cudaStream_t s)
+{
+    const int64_t total = nnodes * ncoef(p + 1);
+    k_eps_table<<<grid_for(total, 128), 128, 0, s>>>(mom, invrho, nnodes, pm, p, eps, et);
     note_launch();
     return cudaGetLastError();
 }

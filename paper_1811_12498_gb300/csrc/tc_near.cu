@@ -110,7 +110,7 @@ struct NearOpU {
     using Tgt = Tgt2;
     static constexpr bool kAdd = false;
     static constexpr bool kUnguarded = true;
-    __device__ static Tgt load(const double* ts, const double*, int64_t M, int64_t m, bool valid)
+    __device__ static Tgt load(const double* ts, const double*, int64_t M, int64_t m, bool valid, float)
     {
         return load_target(ts, M, m, valid);
     }
@@ -121,14 +121,82 @@ struct NearOpU {
     }
 };
 
+// Regularized kernels (the blob of Cortez, Fauci and Medovikov), s = r^2 +
+// eps^2, q = s^-1/2:
+//   u_i += f_i q (1 + eps^2 q^2) + d_i q^3 ((d.f) + q^2 ((d.h)(d.nu) + (eps^2/2)(h.nu)))
+//          + (eps^2/2) q^5 (h_i (d.nu) + nu_i (d.h)),
+// h.nu from the last field of the source record; coincident pairs skipped as
+// for the paper's kernels.
+struct TgtReg {
+    Tgt2 p;
+    float2 e2, e2h;
+};
+
+template <bool kGuard>
+__device__ __forceinline__ void pair_terms_reg(const TgtReg& T, const float4* tp, float2& ax, float2& ay, float2& az)
+{
+    const Tgt2& t = T.p;
+    const float4 A = tp[0], B = tp[1], C = tp[2], D = tp[3], E = tp[4], F = tp[5], G = tp[6], Q = tp[7];
+    const float2 dx = __fadd2_rn(sub2(t.h0, make_float2(A.x, A.y)), sub2(t.l0, make_float2(C.x, C.y)));
+    const float2 dy = __fadd2_rn(sub2(t.h1, make_float2(A.z, A.w)), sub2(t.l1, make_float2(C.z, C.w)));
+    const float2 dz = __fadd2_rn(sub2(t.h2, make_float2(B.x, B.y)), sub2(t.l2, make_float2(D.x, D.y)));
+    const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+    const float2 sr = __fadd2_rn(r2, T.e2);
+    float2 q;
+    if (kGuard) {
+        q.x = r2.x > 0.f ? rsqrt_ftz(sr.x) : 0.f;
+        q.y = r2.y > 0.f ? rsqrt_ftz(sr.y) : 0.f;
+    } else {
+        q.x = rsqrt_ftz(sr.x);
+        q.y = rsqrt_ftz(sr.y);
+    }
+    const float2 q2 = __fmul2_rn(q, q);
+    const float2 f0 = make_float2(B.z, B.w), f1 = make_float2(D.z, D.w), f2 = make_float2(E.x, E.y);
+    const float2 h0 = make_float2(E.z, E.w), h1 = make_float2(F.x, F.y), h2 = make_float2(F.z, F.w);
+    const float2 n0 = make_float2(G.x, G.y), n1 = make_float2(G.z, G.w), n2 = make_float2(Q.x, Q.y);
+    const float2 df = __ffma2_rn(dx, f0, __ffma2_rn(dy, f1, __fmul2_rn(dz, f2)));
+    const float2 dh = __ffma2_rn(dx, h0, __ffma2_rn(dy, h1, __fmul2_rn(dz, h2)));
+    const float2 dn = __ffma2_rn(dx, n0, __ffma2_rn(dy, n1, __fmul2_rn(dz, n2)));
+    const float2 one = make_float2(1.f, 1.f);
+    const float2 a1 = __fmul2_rn(q, __ffma2_rn(T.e2, q2, one));
+    const float2 t1 = __ffma2_rn(dh, dn, __fmul2_rn(T.e2h, make_float2(Q.z, Q.w)));
+    const float2 qs = __fmul2_rn(__fmul2_rn(q, q2), __ffma2_rn(q2, t1, df));
+    const float2 w = __fmul2_rn(__fmul2_rn(T.e2h, q), __fmul2_rn(q2, q2));
+    const float2 wn = __fmul2_rn(w, dn), wh = __fmul2_rn(w, dh);
+    ax = __ffma2_rn(f0, a1, __ffma2_rn(dx, qs, __ffma2_rn(h0, wn, __ffma2_rn(n0, wh, ax))));
+    ay = __ffma2_rn(f1, a1, __ffma2_rn(dy, qs, __ffma2_rn(h1, wn, __ffma2_rn(n1, wh, ay))));
+    az = __ffma2_rn(f2, a1, __ffma2_rn(dz, qs, __ffma2_rn(h2, wn, __ffma2_rn(n2, wh, az))));
+}
+
+struct NearOpReg {
+    using Tgt = TgtReg;
+    static constexpr bool kAdd = false;
+    static constexpr bool kUnguarded = true;
+    __device__ static Tgt load(const double* ts, const double*, int64_t M, int64_t m, bool valid, float e2)
+    {
+        TgtReg t;
+        t.p = load_target(ts, M, m, valid);
+        t.e2 = make_float2(e2, e2);
+        t.e2h = make_float2(0.5f * e2, 0.5f * e2);
+        return t;
+    }
+    template <bool kGuard>
+    __device__ static void terms(const Tgt& t, const float4* tp, float2& ax, float2& ay, float2& az)
+    {
+        pair_terms_reg<kGuard>(t, tp, ax, ay, az);
+    }
+};
+
 // ---------------------------------------------------------------------------
 // FP64
 
 // FP64 near field of batch b on one warp; tw is the warp's tile [12][32].
+// kReg: the regularized kernels with e2 = eps^2 (formula at NearOpReg).
+template <bool kReg = false>
 __device__ inline void near_batch_fp64(const double* __restrict__ ts, int64_t M, const int4* __restrict__ topo,
                                        const double* __restrict__ xs, const double* __restrict__ ws, int64_t N,
                                        const int64_t* __restrict__ near_off, const ListEntry* __restrict__ near_list,
-                                       double* __restrict__ u_near, int64_t b, double* tw, int lane)
+                                       double* __restrict__ u_near, int64_t b, double* tw, int lane, double e2 = 0.0)
 {
     const int64_t m = b * kBatch + lane;
     const bool valid = m < M;
@@ -151,7 +219,25 @@ __device__ inline void near_batch_fp64(const double* __restrict__ ts, int64_t M,
             }
             __syncwarp();
             if (!in) continue;
-            for (int j = 0; j < cnt; j++) {
+            for (int j = 0; j < cnt && kReg; j++) {
+                const double dx = tx[0] - tw[j], dy = tx[1] - tw[32 + j], dz = tx[2] - tw[64 + j];
+                const double r2 = dx * dx + dy * dy + dz * dz;
+                if (!(r2 > 0.0)) continue;
+                const double f0 = tw[96 + j], f1 = tw[128 + j], f2 = tw[160 + j];
+                const double h0 = tw[192 + j], h1 = tw[224 + j], h2 = tw[256 + j];
+                const double n0 = tw[288 + j], n1 = tw[320 + j], n2 = tw[352 + j];
+                const double df = dx * f0 + dy * f1 + dz * f2;
+                const double dh = dx * h0 + dy * h1 + dz * h2;
+                const double dn = dx * n0 + dy * n1 + dz * n2;
+                const double q = rsqrt(r2 + e2), q2 = q * q;
+                const double a1 = q * (1.0 + e2 * q2);
+                const double qs = q * q2 * (df + q2 * (dh * dn + 0.5 * e2 * (h0 * n0 + h1 * n1 + h2 * n2)));
+                const double w = 0.5 * e2 * q * q2 * q2;
+                ux += f0 * a1 + dx * qs + w * (h0 * dn + n0 * dh);
+                uy += f1 * a1 + dy * qs + w * (h1 * dn + n1 * dh);
+                uz += f2 * a1 + dz * qs + w * (h2 * dn + n2 * dh);
+            }
+            for (int j = 0; j < cnt && !kReg; j++) {
                 const double dx = tx[0] - tw[j], dy = tx[1] - tw[32 + j], dz = tx[2] - tw[64 + j];
                 const double r2 = dx * dx + dy * dy + dz * dz;
                 const double ri = r2 > 0.0 ? rsqrt(r2) : 0.0;
@@ -196,12 +282,12 @@ __global__ void k_group_work(const int64_t* __restrict__ near_off, const ListEnt
 
 // The one-system near field on a resident grid: each warp takes the next
 // group from the queue, in order of decreasing work.
-template <int G>
+template <int G, typename Op>
 __global__ void __launch_bounds__(kNearWarps * 32)
     k_near_mixed_q(const double* __restrict__ ts, int64_t M, const int4* __restrict__ topo,
                    const float4* __restrict__ spack, const int64_t* __restrict__ near_off,
                    const ListEntry* __restrict__ near_list, double* __restrict__ u_near, int self,
-                   const int32_t* __restrict__ order, int64_t ngroup, unsigned* __restrict__ queue)
+                   const int32_t* __restrict__ order, int64_t ngroup, unsigned* __restrict__ queue, float prm)
 {
     __shared__ NearScratch<G> sc[kNearWarps];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -210,15 +296,15 @@ __global__ void __launch_bounds__(kNearWarps * 32)
         if (lane == 0) i = atomicAdd(queue, 1u);
         i = __shfl_sync(0xffffffffu, i, 0);
         if ((int64_t)i >= ngroup) break;
-        nearpair::near_group<G, NearOpU>(ts, nullptr, M, topo, spack, near_off, near_list, u_near, order[i], self,
-                                         sc[w], lane);
+        nearpair::near_group<G, Op>(ts, nullptr, M, topo, spack, near_off, near_list, u_near, order[i], self, prm,
+                                    sc[w], lane);
     }
 }
 
-template <int G>
+template <int G, typename Op = NearOpU>
 cudaError_t run_near_mixed(const double* ts, int64_t M, const int4* topo, const float4* spack,
                            const int64_t* near_off, const ListEntry* near_list, double* u_near, int self,
-                           const NearSched& sc, cudaStream_t s)
+                           const NearSched& sc, cudaStream_t s, float prm = 0.0f)
 {
     const int64_t nbatch = (M + kBatch - 1) / kBatch;
     const int64_t ngroup = (nbatch + G - 1) / G;
@@ -229,11 +315,11 @@ cudaError_t run_near_mixed(const double* ts, int64_t M, const int4* topo, const 
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(sc.queue, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
-    static int per_sm[2] = {0, 0}, sms = 0;
-    int& ps = per_sm[G == kNearGroupLarge ? 1 : 0];
+    static int ps = 0, sms = 0;
     if (ps == 0) {
         int dev = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, k_near_mixed_q<G>, kNearWarps * 32, 0) != cudaSuccess ||
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, k_near_mixed_q<G, Op>, kNearWarps * 32, 0) !=
+                cudaSuccess ||
             ps < 1)
             ps = 1;
         cudaGetDevice(&dev);
@@ -241,8 +327,8 @@ cudaError_t run_near_mixed(const double* ts, int64_t M, const int4* topo, const 
     }
     const int64_t need = (ngroup + kNearWarps - 1) / kNearWarps;
     const unsigned grid = (unsigned)std::min<int64_t>(need, (int64_t)ps * std::max(sms, 1));
-    k_near_mixed_q<G><<<grid, kNearWarps * 32, 0, s>>>(ts, M, topo, spack, near_off, near_list, u_near, self,
-                                                       sc.order, ngroup, sc.queue);
+    k_near_mixed_q<G, Op><<<grid, kNearWarps * 32, 0, s>>>(ts, M, topo, spack, near_off, near_list, u_near, self,
+                                                           sc.order, ngroup, sc.queue, prm);
     return cudaGetLastError();
 }
 
@@ -252,7 +338,7 @@ int near_resident_warps()
     static int warps = 0;
     if (warps == 0) {
         int per_sm = 0, dev = 0, sms = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_near_mixed_q<kNearGroupLarge>, kNearWarps * 32,
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_near_mixed_q<kNearGroupLarge, NearOpU>, kNearWarps * 32,
                                                           0) != cudaSuccess)
             per_sm = 1;
         cudaGetDevice(&dev);
@@ -262,18 +348,19 @@ int near_resident_warps()
     return warps;
 }
 
+template <bool kReg>
 __global__ void __launch_bounds__(kNearWarps * 32)
     k_near_fp64(const double* __restrict__ ts, int64_t M, const int4* __restrict__ topo,
                 const double* __restrict__ xs, const double* __restrict__ ws, int64_t N,
                 const int64_t* __restrict__ near_off, const ListEntry* __restrict__ near_list,
-                double* __restrict__ u_near)
+                double* __restrict__ u_near, double e2)
 {
     __shared__ double tile[kNearWarps][12 * 32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t nbatch = (M + kBatch - 1) / kBatch;
     const int64_t b = blockIdx.x * (int64_t)kNearWarps + w;
     if (b >= nbatch) return;
-    near_batch_fp64(ts, M, topo, xs, ws, N, near_off, near_list, u_near, b, tile[w], lane);
+    near_batch_fp64<kReg>(ts, M, topo, xs, ws, N, near_off, near_list, u_near, b, tile[w], lane, e2);
 }
 
 // Persistent near-field kernel over many systems (see k_far32_batched).  An
@@ -308,7 +395,7 @@ __global__ void __launch_bounds__(kNearMaxWarps * 32)
             near_batch_fp64(d.ts, d.M, d.topo, d.xs, d.ws, d.N, d.near_off, d.near_list, d.u_near, b, tile[w], lane);
         else
             nearpair::near_group<kNearGroupBatches, NearOpU>(
-                d.ts, nullptr, d.M, d.topo, d.spack, d.near_off, d.near_list, d.u_near, b, 1,
+                d.ts, nullptr, d.M, d.topo, d.spack, d.near_off, d.near_list, d.u_near, b, 1, 0.0f,
                 *reinterpret_cast<NearScratch<kNearGroupBatches>*>(tile[w]), lane);
     }
 }
@@ -368,13 +455,24 @@ int64_t near_max_groups(int64_t M)
 cudaError_t launch_near(int precision, const double* ts, int64_t M, const int4* topo,
                         const double* xs, const double* ws, const float4* spack, int64_t N,
                         const int64_t* near_off, const ListEntry* near_list, double* u_near, int self,
-                        const NearSched& sched, cudaStream_t s)
+                        const NearSched& sched, double eps, cudaStream_t s)
 {
     if (M <= 0) return cudaSuccess;
     const int64_t nbatch = (M + kBatch - 1) / kBatch;
+    const double e2 = eps * eps;
     if (precision == TC_FP64) {
         const unsigned grid = (unsigned)((nbatch + kNearWarps - 1) / kNearWarps);
-        k_near_fp64<<<grid, kNearWarps * 32, 0, s>>>(ts, M, topo, xs, ws, N, near_off, near_list, u_near);
+        if (eps > 0.0)
+            k_near_fp64<true><<<grid, kNearWarps * 32, 0, s>>>(ts, M, topo, xs, ws, N, near_off, near_list, u_near, e2);
+        else
+            k_near_fp64<false><<<grid, kNearWarps * 32, 0, s>>>(ts, M, topo, xs, ws, N, near_off, near_list, u_near,
+                                                                0.0);
+    } else if (eps > 0.0) {
+        // the regularized kernels: groups of four (no tuning for this path)
+        cudaError_t e = run_near_mixed<kNearGroupBatches, NearOpReg>(ts, M, topo, spack, near_off, near_list, u_near,
+                                                                     self, sched, s, (float)e2);
+        note_launch();
+        return e;
     } else {
         const bool large = (double)((nbatch + kNearGroupLarge - 1) / kNearGroupLarge) >=
                            kNearWaveShare * near_resident_warps();

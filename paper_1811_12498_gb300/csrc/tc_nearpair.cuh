@@ -89,13 +89,14 @@ struct NearScratch {
 // target against a staged source pair (Op::terms<kGuard>, three FP32x2
 // accumulators), whether the result is stored or added (Op::kAdd), and
 // whether its terms are also compiled without the r = 0 guard (Op::kUnguarded);
-// gs is passed through to Op::load (the adjoint's target weights g, unused by
-// the forward field).
+// gs and prm are passed through to Op::load (the adjoint's target weights g,
+// unused by the forward field; prm: eps^2 of the regularized kernels).
 template <int G, typename Op>
 __device__ inline void near_group(const double* __restrict__ ts, const double* __restrict__ gs, int64_t M,
                                   const int4* __restrict__ topo, const float4* __restrict__ spack,
                                   const int64_t* __restrict__ near_off, const ListEntry* __restrict__ near_list,
-                                  double* __restrict__ out, int64_t B, int self, NearScratch<G>& sc, int lane)
+                                  double* __restrict__ out, int64_t B, int self, float prm, NearScratch<G>& sc,
+                                  int lane)
 {
     const int64_t nbatch = (M + kBatch - 1) / kBatch;
     const int64_t b0 = (int64_t)G * B;
@@ -149,8 +150,8 @@ __device__ inline void near_group(const double* __restrict__ ts, const double* _
             const bool v1 = k1 < A, v2 = two && k2 < A;
             const int id1 = v1 ? sc.slot[k1] : 0, id2 = v2 ? sc.slot[k2] : 0;
             const int64_t m1 = (b0 + (id1 >> 5)) * kBatch + (id1 & 31), m2 = (b0 + (id2 >> 5)) * kBatch + (id2 & 31);
-            const typename Op::Tgt ta = Op::load(ts, gs, M, m1, v1);
-            const typename Op::Tgt tb = Op::load(ts, gs, M, m2, v2);
+            const typename Op::Tgt ta = Op::load(ts, gs, M, m1, v1, prm);
+            const typename Op::Tgt tb = Op::load(ts, gs, M, m2, v2, prm);
             // r = 0 needs the target to coincide with a source of this leaf.
             // With targets = sources (self) that is only possible for a
             // target inside the leaf's own range (coincident points have

@@ -1,0 +1,124 @@
+// Far field of the regularized Stokeslet and stresslet (the blob of Cortez,
+// Fauci and Medovikov; the paper lists regularized kernels as future work).
+//
+// With G_nu = (|x - y|^2 + eps^2)^(-nu), the regularized kernels are the
+// structure of eqs. (4.4)/(4.9) built on G_1/2 plus eps^2 terms in G_3/2
+// (tc_moments.cu, k_eps_table), so per (target, cluster):
+//   u_i = sum_{||k|| <= p+2} c_{1/2}^k (Â_i^k + d'_l B̂_il^k)
+//       + sum_{||k|| <= p+1} c_{3/2}^k Ê_i^k,
+// d' = (x - y_c)/rho, with the contraction tables of the paper's kernels
+// (k_ab_tables) and the eps^2 table Ê.  The Taylor coefficients c_nu^k of
+// G_nu at (d', eps' = eps/rho) follow the recurrence that generalizes (3.2):
+// from s D_y G_nu = 2 nu (x - y) G_nu (s = |x - y|^2 + eps^2),
+//   n s' c^k = (2n + 2nu - 2) sum_i d'_i c^{k-e_i} - (n + 2nu - 2) sum_i c^{k-2e_i},
+//   c^0 = s'^-nu,  s' = |d'|^2 + eps'^2,  n = ||k||.
+// G_1/2 is not harmonic when eps > 0, so the harmonic folding of the
+// paper's kernels does not apply: the full index set is formed, in FP64 in
+// both precision modes.  One batch of 32 targets per warp; the coefficients
+// of two levels live in a per-warp shared-memory store [slot][position][lane]
+// (level n overwrites level n-2 in place, positions running downward).
+#include "tc_recurrence.cuh"
+
+namespace tc {
+
+namespace {
+
+// one coefficient pass: the recurrence for G_nu (two_nu = 2 nu) up to order
+// P, each coefficient contracted against W table values at once
+template <int W>
+__device__ inline void reg_pass(double* slot0, double* slot1, int P, double two_nu, double sp, double d0, double d1,
+                                double d2, const double* __restrict__ tab, double* tot, int lane)
+{
+    double c0 = rsqrt(sp);
+    if (two_nu > 1.5) c0 = c0 * c0 * c0;  // nu = 3/2
+    slot0[lane] = c0;
+#pragma unroll
+    for (int q = 0; q < W; q++) tot[q] = fma(c0, tab[q], tot[q]);
+    const double isp = 1.0 / sp;
+    for (int n = 1; n <= P; n++) {
+        double* Rn = (n & 1) ? slot1 : slot0;  // also holds level n-2
+        const double* R1 = (n & 1) ? slot0 : slot1;
+        const double al = (2.0 * n + two_nu - 2.0) * isp / n, be = (n + two_nu - 2.0) * isp / n;
+        const double w0 = al * d0, w1 = al * d1, w2 = al * d2;
+        const double* tl = tab + (int64_t)ncoef(n - 1) * W;
+        __syncwarp();
+        for (int a = n; a >= 0; a--) {
+            const int k1 = n - a, base = a * (a + 1) / 2;
+            for (int k3 = a; k3 >= 0; k3--) {
+                const int pos = base + k3;
+                const double ck = coef<double>(R1, Rn, pos, a, k1, a - k3, k3, w0, w1, w2, be, lane);
+                Rn[pos * 32 + lane] = ck;
+                const double* t = tl + pos * W;
+#pragma unroll
+                for (int q = 0; q < W; q++) tot[q] = fma(ck, t[q], tot[q]);
+            }
+        }
+    }
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(32)
+    k_far_reg(const double* __restrict__ ts, int64_t M, const Geo* __restrict__ geo, const double* __restrict__ invrho,
+              const double* __restrict__ ab64, const double* __restrict__ et, int p, double eps,
+              const int64_t* __restrict__ far_off, const ListEntry* __restrict__ far_list, double* __restrict__ u_far)
+{
+    extern __shared__ double store[];
+    const int lane = threadIdx.x & 31;
+    const int64_t b = blockIdx.x;
+    const int64_t nbatch = (M + kBatch - 1) / kBatch;
+    if (b >= nbatch) return;
+    const int L = (p + 3) * (p + 4) / 2;  // largest level, order p + 2
+    double* slot0 = store;
+    double* slot1 = store + (size_t)L * 32;
+    const int64_t m = b * kBatch + lane;
+    const bool valid = m < M;
+    double x0 = 0, x1 = 0, x2 = 0;
+    if (valid) {
+        x0 = ts[m];
+        x1 = ts[M + m];
+        x2 = ts[2 * M + m];
+    }
+    const int C2 = ncoef(p + 2), C1 = ncoef(p + 1);
+    double ux = 0.0, uy = 0.0, uz = 0.0;
+    for (int64_t e = far_off[b]; e < far_off[b + 1]; e++) {
+        const ListEntry le = far_list[e];
+        const bool in = (le.mask >> lane) & 1u;
+        const Geo g = geo[le.node];
+        const double ir = invrho[le.node];
+        double d0 = (x0 - g.x) * ir, d1 = (x1 - g.y) * ir, d2 = (x2 - g.z) * ir;
+        if (!in) d0 = 2.0, d1 = 0.0, d2 = 0.0;  // keep idle lanes finite
+        const double ep = eps * ir;
+        const double sp = d0 * d0 + d1 * d1 + d2 * d2 + ep * ep;
+        double t12[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0}, t3[3] = {0, 0, 0};
+        reg_pass<12>(slot0, slot1, p + 2, 1.0, sp, d0, d1, d2, ab64 + (int64_t)le.node * C2 * 12, t12, lane);
+        reg_pass<3>(slot0, slot1, p + 1, 3.0, sp, d0, d1, d2, et + (int64_t)le.node * C1 * 3, t3, lane);
+        if (in) {
+            ux += t12[0] + d0 * t12[3] + d1 * t12[4] + d2 * t12[5] + t3[0];
+            uy += t12[1] + d0 * t12[6] + d1 * t12[7] + d2 * t12[8] + t3[1];
+            uz += t12[2] + d0 * t12[9] + d1 * t12[10] + d2 * t12[11] + t3[2];
+        }
+    }
+    if (valid) {
+        u_far[m] = ux;
+        u_far[M + m] = uy;
+        u_far[2 * M + m] = uz;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_far_reg(const double* ts, int64_t M, const Geo* geo, const double* invrho, const double* ab64,
+                           const double* et, int p, double eps, const int64_t* far_off, const ListEntry* far_list,
+                           double* u_far, cudaStream_t s)
+{
+    if (M <= 0) return cudaSuccess;
+    const int64_t nbatch = (M + kBatch - 1) / kBatch;
+    const size_t smem = (size_t)2 * ((p + 3) * (p + 4) / 2) * 32 * sizeof(double);
+    cudaError_t e = cudaFuncSetAttribute(k_far_reg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_far_reg<<<(unsigned)nbatch, 32, smem, s>>>(ts, M, geo, invrho, ab64, et, p, eps, far_off, far_list, u_far);
+    note_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace tc

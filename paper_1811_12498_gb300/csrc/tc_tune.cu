@@ -83,6 +83,7 @@ extern "C" tc_status tc_tune(tc_ctx* ctx, const double* x, const double* f, cons
                              double target_E, double* seconds, double* errors, int32_t* best)
 {
     if (!ctx) return fail(nullptr, TC_EINVAL, "tc_tune: ctx is NULL");
+    if (ctx->reg_eps > 0.0) return fail(ctx, TC_EINVAL, "tc_tune: not available for the regularized kernels");
     if (!x || !f || !h || !nu) return fail(ctx, TC_EINVAL, "tc_tune: a particle array is NULL");
     if (!thetas || !orders || !leaf_sizes || !sample || !seconds || !errors || !best)
         return fail(ctx, TC_EINVAL, "tc_tune: a host array is NULL");

@@ -57,6 +57,13 @@ def test_host_argument_checks_without_gpu(lib):
     assert lib.tc_update_positions(None, None) == 1
     assert lib.tc_velocity_host(None, None, None, None, None, 10, 2, 0.5, 4, None) == 1
     assert lib.tc_eval_frozen(None, None) == 1
+    assert lib.tc_direct_reg(None, None, None, None, 10, None, 10, 0.1, 0, None, None) == 1
+    one = ctypes.c_void_p(1)
+    assert lib.tc_direct_reg(one, one, one, one, 10, None, 10, 0.0, 0, None, one) == 1
+    assert b"eps" in lib.tc_last_error(None)
+    bad = TCConfig(0, 1, None, 0, 0, -1.0)
+    assert lib.tc_create(ctypes.byref(h), ctypes.byref(bad)) == 1
+    assert b"reg_eps" in lib.tc_last_error(None)
     assert lib.tc_fma_peak(0, None, None) == 1
     out = ctypes.c_double()
     assert lib.tc_fma_peak(5, None, ctypes.byref(out)) == 1
