@@ -119,7 +119,7 @@ def parse():
     ap.add_argument("--no-sweep", action="store_true",
                     help="skip the accuracy-against-time sweep on the 4M-point sphere")
     ap.add_argument("--only-extra", choices=["fwd_adjoint", "batched", "sphere_sweep", "table1_sphere",
-                                             "fig3_sphere"],
+                                             "fig3_sphere", "regularized"],
                     help="run just this extra measurement and print it as one JSON line (for profiling runs)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the forward+adjoint (Gaussian clusters) and batched (64 systems) measurements")
@@ -500,6 +500,52 @@ def bench_fig3(flush, stream):
             "loglog_slopes_time_vs_N": slopes}
 
 
+def bench_regularized(flush, stream):
+    """Regularized Stokeslet and stresslet (tc_config.reg_eps) on the headline
+    workload: N = 1,000,000 uniform in the unit cube, p = 8, theta = 0.5,
+    N0 = 2000, eps = 1e-3 (a tenth of the mean spacing), mixed precision (the
+    regularized far field runs in FP64): time of build + moments + eval, the
+    far and near phases alone, and E against the FP64 regularized direct sum
+    on 2000 sampled targets."""
+    import numpy as np
+    import torch
+
+    from paper_1811_12498_gb300 import api, inputs
+    N, N0, p, theta, eps = 1_000_000, 2000, 8, 0.5, 1e-3
+    x, f, h, nu = inputs.uniform_cube(N, inputs.SEED_BASE + 1)
+    d = [torch.from_numpy(np.ascontiguousarray(a.T)).cuda() for a in (x, f, h, nu)]
+    tc = api.Treecode("mixed", True, stream, reg_eps=eps)
+    u = torch.empty((3, N), dtype=torch.float64, device="cuda")
+    times = []
+    for k in range(3):
+        flush.fill_(1)
+        e0, e1 = _events(stream)
+        tc.build(d[0], N0).moments(d[1], d[2], d[3], p)
+        tc.eval(theta, p, out=u)
+        e1.record(stream)
+        e1.synchronize()
+        if k > 0:
+            times.append(e0.elapsed_time(e1))
+    tc.profile(2)
+    tc.build(d[0], N0).moments(d[1], d[2], d[3], p)
+    tc.eval(theta, p, out=u)
+    ph = tc.phase_times()
+    tc.profile(False)
+    st = tc.stats()
+    tc.close()
+    idx = inputs.sample_indices(N, 2000, 983)
+    tgt = torch.from_numpy(np.ascontiguousarray(x[idx].T)).cuda()
+    ud = api.direct_reg(*d, eps, targets=tgt, precision="fp64", stream=stream)
+    it = torch.from_numpy(idx).cuda()
+    E = float(torch.linalg.norm(u[:, it] - ud) / torch.linalg.norm(ud))
+    ms = statistics.mean(times)
+    return {"workload": "regularized kernels, eps=1e-3, uniform cube N=1000000, p=8, theta=0.5, N0=2000, mixed "
+                        "(FP64 far field)",
+            "ms_per_step": ms, "targets_per_s": N / (ms / 1e3), "far_ms": ph["far"], "near_ms": ph["near"],
+            "far_interactions": st["far_interactions"], "near_pairs": st["near_pairs"],
+            "E_vs_fp64_regularized_direct": E, "E_samples": int(len(idx))}
+
+
 def bench_batched(flush, stream, reps=3):
     """64 independent systems, sizes log-uniform in [1e4, 5e5] (even: uniform
     cube, odd: Fibonacci sphere), p = 6, theta = 0.6, N0 = 2000, mixed: one
@@ -552,7 +598,7 @@ def run_only_extra(name):
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
     fn = {"fwd_adjoint": bench_fwd_adjoint, "batched": bench_batched, "sphere_sweep": bench_sphere_sweep,
-          "table1_sphere": bench_table1, "fig3_sphere": bench_fig3}[name]
+          "table1_sphere": bench_table1, "fig3_sphere": bench_fig3, "regularized": bench_regularized}[name]
     print(json.dumps({"extra": name, **fn(flush, stream)}), flush=True)
 
 
@@ -793,6 +839,7 @@ def main():
         line["batched"] = bench_batched(flush, stream)
         line["table1_sphere"] = bench_table1(flush, stream)
         line["fig3_sphere"] = bench_fig3(flush, stream)
+        line["regularized"] = bench_regularized(flush, stream)
         if not args.no_sweep:
             line["sphere_sweep"] = bench_sphere_sweep(flush, stream)
     print(json.dumps(line), flush=True)

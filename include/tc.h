@@ -30,9 +30,11 @@
  *    every result a call writes to them (u, the gradients) is complete in
  *    the context's stream order.
  *  - No call aborts or prints.  Every failure returns a status; the message
- *    is available from tc_last_error.  A device-side failure (the MAC
- *    traversal's stack bound, TC_EDEVICE) is reported by the next call that
- *    synchronises, or by tc_sync.
+ *    is available from tc_last_error.  Kernels report through a device flag
+ *    word that the next synchronising call (or tc_sync) reads (TC_EDEVICE).
+ *    The one check that writes it, the MAC traversal's stack bound (176
+ *    entries), is a guard only: a walk of a tree of depth <= 21 holds at
+ *    most 7 * 21 + 8 = 155 entries, so no input reaches it.
  *  - Pairs with |x - y| == 0 contribute nothing.  When targets are the
  *    sources this is the n != m exclusion of eq. (1.3).
  */
@@ -256,7 +258,10 @@ tc_status tc_direct_reg(const double* x, const double* f, const double* h, const
  * No cudaMalloc, cudaFree or other allocating routine is called.  The first
  * call on a device looks up the array's device address once for that device
  * (with that device current); make that first call before any stream
- * capture.  All calls on a device share the one array and it keeps the last
+ * capture.  The address is kept for the life of the process: a
+ * cudaDeviceReset (or any other destruction of the device's primary context)
+ * unloads the library's device image and makes it stale, so do not call
+ * tc_direct_noalloc on a device after resetting it in the same process.  All calls on a device share the one array and it keeps the last
  * call's contents; every scratch word a call reads is first written by the
  * same call, so nothing needs clearing, but calls whose kernels overlap on
  * the GPU (different streams, no ordering between them) race on the array

@@ -19,7 +19,11 @@ constexpr int kPMax = 12;       // largest Taylor order accepted
 constexpr int kQMax = kPMax + 2;  // far field needs Coulomb coefficients to p+2
 constexpr int kBatch = 32;      // targets per interaction list (one warp)
 constexpr int kNearGroupBatches = 4;  // batches per warp in the mixed-precision near kernels
-constexpr int kStack = 8 * (kMaxDepth + 1);  // traversal stack bound (7 siblings/level + 8)
+// traversal stack: a preorder walk keeps at most 7 siblings per level plus
+// the children of the deepest node, 7 * kMaxDepth + 8 = 155 entries, so the
+// kernels' bound check on this size is a guard that no tree of this library
+// reaches
+constexpr int kStack = 8 * (kMaxDepth + 1);
 
 // number of multi-indices with ||k|| == n, and with ||k|| <= n
 __host__ __device__ constexpr int level_size(int n) { return (n + 1) * (n + 2) / 2; }

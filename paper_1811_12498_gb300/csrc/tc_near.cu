@@ -281,7 +281,8 @@ __global__ void k_group_work(const int64_t* __restrict__ near_off, const ListEnt
 }
 
 // The one-system near field on a resident grid: each warp takes the next
-// group from the queue, in order of decreasing work.
+// group from the queue, in order of decreasing work (order), or in index
+// order (order = NULL) when the grid holds every group at once.
 template <int G, typename Op>
 __global__ void __launch_bounds__(kNearWarps * 32)
     k_near_mixed_q(const double* __restrict__ ts, int64_t M, const int4* __restrict__ topo,
@@ -296,8 +297,8 @@ __global__ void __launch_bounds__(kNearWarps * 32)
         if (lane == 0) i = atomicAdd(queue, 1u);
         i = __shfl_sync(0xffffffffu, i, 0);
         if ((int64_t)i >= ngroup) break;
-        nearpair::near_group<G, Op>(ts, nullptr, M, topo, spack, near_off, near_list, u_near, order[i], self, prm,
-                                    sc[w], lane);
+        nearpair::near_group<G, Op>(ts, nullptr, M, topo, spack, near_off, near_list, u_near, order ? order[i] : i,
+                                    self, prm, sc[w], lane);
     }
 }
 
@@ -308,13 +309,6 @@ cudaError_t run_near_mixed(const double* ts, int64_t M, const int4* topo, const 
 {
     const int64_t nbatch = (M + kBatch - 1) / kBatch;
     const int64_t ngroup = (nbatch + G - 1) / G;
-    k_group_work<G><<<(unsigned)((ngroup + 255) / 256), 256, 0, s>>>(near_off, near_list, topo, nbatch, ngroup,
-                                                                    sc.keys, sc.order);
-    note_launch();
-    cudaError_t e = radix_sort_bits(sc.keys, sc.order, sc.keys_alt, sc.order_alt, sc.hist, ngroup, 32, s);
-    if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(sc.queue, 0, sizeof(unsigned), s);
-    if (e != cudaSuccess) return e;
     static int ps = 0, sms = 0;
     if (ps == 0) {
         int dev = 0;
@@ -326,9 +320,22 @@ cudaError_t run_near_mixed(const double* ts, int64_t M, const int4* topo, const 
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     }
     const int64_t need = (ngroup + kNearWarps - 1) / kNearWarps;
-    const unsigned grid = (unsigned)std::min<int64_t>(need, (int64_t)ps * std::max(sms, 1));
+    const int64_t resident = (int64_t)ps * std::max(sms, 1);
+    const unsigned grid = (unsigned)std::min<int64_t>(need, resident);
+    // the order matters only when some warps take more than one group
+    const int32_t* order = nullptr;
+    if (need > resident) {
+        k_group_work<G><<<(unsigned)((ngroup + 255) / 256), 256, 0, s>>>(near_off, near_list, topo, nbatch, ngroup,
+                                                                        sc.keys, sc.order);
+        note_launch();
+        cudaError_t e = radix_sort_bits(sc.keys, sc.order, sc.keys_alt, sc.order_alt, sc.hist, ngroup, 32, s);
+        if (e != cudaSuccess) return e;
+        order = sc.order;
+    }
+    cudaError_t e = cudaMemsetAsync(sc.queue, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
     k_near_mixed_q<G, Op><<<grid, kNearWarps * 32, 0, s>>>(ts, M, topo, spack, near_off, near_list, u_near, self,
-                                                           sc.order, ngroup, sc.queue, prm);
+                                                           order, ngroup, sc.queue, prm);
     return cudaGetLastError();
 }
 
