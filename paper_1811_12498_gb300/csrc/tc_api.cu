@@ -176,6 +176,7 @@ tc_status tc_destroy(tc_ctx* ctx)
     if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
     if (ctx->ev_mom) cudaEventDestroy(ctx->ev_mom);
     if (ctx->stream2) cudaStreamDestroy(ctx->stream2);
+    if (ctx->host_words) cudaFreeHost(ctx->host_words);
     delete ctx;
     return TC_OK;
 }
@@ -444,6 +445,19 @@ static tc_status ensure_tables(tc_ctx* ctx, int p, cudaStream_t s)
 // interaction lists (synchronises once to size the lists).
 tc_status tc::eval_prepare(tc_ctx* ctx, const double* targets, int64_t M, double theta, int p)
 {
+    tc_status st = eval_prepare_count(ctx, targets, M, theta, p);
+    if (st != TC_OK) return st;
+    TC_CK(cudaStreamSynchronize(ctx->stream), "list totals");
+    return eval_prepare_finish(ctx);
+}
+
+// The part of eval_prepare before the host needs the list sizes: target
+// ordering, the counting pass of the traversal and its scans, and the copy of
+// the two totals and the device flags into the context's pinned host words.
+// Nothing here waits for the device; eval_prepare_finish must follow after
+// the context's stream has been synchronised.
+tc_status tc::eval_prepare_count(tc_ctx* ctx, const double* targets, int64_t M, double theta, int p)
+{
     if (!ctx->have_moments) return fail(ctx, TC_ESTATE, "tc_eval: call tc_build and tc_moments first");
     if (!(theta > 0.0 && theta < 1.0)) return fail(ctx, TC_EINVAL, "tc_eval: theta = %g out of (0, 1)", theta);
     if (p < 0 || p > ctx->p_mom)
@@ -511,11 +525,44 @@ tc_status tc::eval_prepare(tc_ctx* ctx, const double* targets, int64_t M, double
     int64_t* near_off = ptr<int64_t>(ctx->near_off);
     TC_CK(launch_scan_i32_to_i64(ptr<int32_t>(ctx->nfar_e), far_off, nbatch, far_off + nbatch, s), "far scan");
     TC_CK(launch_scan_i32_to_i64(ptr<int32_t>(ctx->nnear_e), near_off, nbatch, near_off + nbatch, s), "near scan");
-    int64_t tot[2];
-    TC_CK(cudaMemcpyAsync(&tot[0], far_off + nbatch, 8, cudaMemcpyDeviceToHost, s), "list totals");
-    TC_CK(cudaMemcpyAsync(&tot[1], near_off + nbatch, 8, cudaMemcpyDeviceToHost, s), "list totals");
-    st = check_flags(ctx);  // synchronises
-    if (st != TC_OK) return st;
+    if (!ctx->host_words) TC_CK(cudaMallocHost((void**)&ctx->host_words, 4 * sizeof(int64_t)), "host words");
+    TC_CK(cudaMemcpyAsync(&ctx->host_words[0], far_off + nbatch, 8, cudaMemcpyDeviceToHost, s), "list totals");
+    TC_CK(cudaMemcpyAsync(&ctx->host_words[1], near_off + nbatch, 8, cudaMemcpyDeviceToHost, s), "list totals");
+    ctx->host_words[2] = 0;
+    TC_CK(cudaMemcpyAsync(&ctx->host_words[2], ctx->flags.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "flags");
+    ctx->pending_theta = theta;
+    ctx->pending_p = p;
+    ctx->pending_ts = ts;
+    ctx->pending_M = M;
+    ctx->counted = 1;
+    return TC_OK;
+}
+
+// The rest of eval_prepare once the totals are on the host: the write pass of
+// the traversal and the contraction tables.
+tc_status tc::eval_prepare_finish(tc_ctx* ctx)
+{
+    if (!ctx->counted) return fail(ctx, TC_ESTATE, "tc_eval: lists were not counted");
+    ctx->counted = 0;
+    tc_status st = TC_OK;
+    cudaStream_t s = ctx->stream;
+    const int64_t M = ctx->pending_M;
+    const int p = ctx->pending_p;
+    const double theta = ctx->pending_theta;
+    const double* ts = ctx->pending_ts;
+    const int64_t nbatch = (M + kBatch - 1) / kBatch;
+    const int32_t f = (int32_t)ctx->host_words[2];
+    if (f & kFlagStack) return fail(ctx, TC_EDEVICE, "device check: traversal stack bound exceeded");
+    if (f) return fail(ctx, TC_EDEVICE, "device check: flags 0x%x", f);
+    const int64_t tot[2] = {ctx->host_words[0], ctx->host_words[1]};
+    const int4* topo = ptr<int4>(ctx->node_topo);
+    const Geo* geo = ptr<Geo>(ctx->node_geo);
+    const float4* geof = ptr<float4>(ctx->node_geof);
+    double S = 0.0;
+    for (int a = 0; a < 3; a++) S = std::max(S, std::max(std::fabs(ctx->lo[a]), std::fabs(ctx->lo[a] + ctx->side)));
+    const float scale2 = (float)(S * S);
+    int64_t* far_off = ptr<int64_t>(ctx->far_off);
+    int64_t* near_off = ptr<int64_t>(ctx->near_off);
     TC_CK(ensure(ctx->far_list, (size_t)(tot[0] > 0 ? tot[0] : 1) * sizeof(ListEntry)), "alloc far list");
     TC_CK(ensure(ctx->near_list, (size_t)(tot[1] > 0 ? tot[1] : 1) * sizeof(ListEntry)), "alloc near list");
     TC_CK(launch_lists(ts, M, topo, geo, geof, scale2, theta, 1, nullptr, nullptr, far_off, near_off,

@@ -356,9 +356,16 @@ tc_status tc_batch_eval(tc_batch* b, double theta, int32_t p, double* u)
     if (b->nsys < 1) return bfail(b, TC_ESTATE, "tc_batch_eval: call tc_batch_build first");
     if (!u) return bfail(b, TC_EINVAL, "tc_batch_eval: u is NULL");
     cudaStream_t st = (cudaStream_t)b->cfg.stream;
-    // 1. every system's tables and interaction lists
+    // 1. every system's tables and interaction lists: the counting passes of
+    // all systems, one synchronisation for all their list sizes, then the
+    // write passes and tables
     for (int s = 0; s < b->nsys; s++) {
-        tc_status r = eval_prepare(b->ctx[s], nullptr, b->off[s + 1] - b->off[s], theta, p);
+        tc_status r = eval_prepare_count(b->ctx[s], nullptr, b->off[s + 1] - b->off[s], theta, p);
+        if (r != TC_OK) return from_ctx(b, b->ctx[s], r, s);
+    }
+    TB_CK(cudaStreamSynchronize(st), "list sizes");
+    for (int s = 0; s < b->nsys; s++) {
+        tc_status r = eval_prepare_finish(b->ctx[s]);
         if (r != TC_OK) return from_ctx(b, b->ctx[s], r, s);
         // the persistent kernels read every system's tables: join the
         // system's second stream (moments, tables) into its first

@@ -158,6 +158,12 @@ struct tc_ctx {
     tc::DevBuf geo32;                   // mixed: per node (y_c hi, 1/rho), (y_c lo, 0) as float4
     tc::DevBuf reg_et;                  // regularized kernels: FP64 [node][ncoef(p+1)][3] eps^2 table
     double reg_eps = 0.0;               // > 0: regularized kernels (tc_config.reg_eps)
+    int64_t* host_words = nullptr;      // pinned: far and near list totals, device flags
+    int counted = 0;                    // eval_prepare_count done, finish pending
+    double pending_theta = 0.0;
+    int pending_p = 0;
+    const double* pending_ts = nullptr;
+    int64_t pending_M = 0;
 
     // ---- evaluation (tc_eval)
     int64_t M = 0;
@@ -241,6 +247,10 @@ cudaError_t run_probe(int kind, cudaStream_t s, double* tflops, double* ms_best)
 
 // tc_eval in two halves (tc_api.cu): lists, then far/near/finalize
 tc_status eval_prepare(tc_ctx* ctx, const double* targets, int64_t M, double theta, int p);
+// eval_prepare in two halves around the one synchronisation it needs (a batch
+// counts every system's lists, synchronises once, then finishes them all)
+tc_status eval_prepare_count(tc_ctx* ctx, const double* targets, int64_t M, double theta, int p);
+tc_status eval_prepare_finish(tc_ctx* ctx);
 tc_status eval_compute(tc_ctx* ctx, double* u);
 
 // error helpers (tc_api.cu)
