@@ -335,11 +335,13 @@ def bench_fwd_adjoint(flush, stream, steps=3):
                 "flops_per_launch": flops, "launch_ms": ms_k, "work_unit": unit}
 
     rooflines = [
-        roof("k_near_adj_target32", NEAR_ADJ_TARGET_FLOPS * st["near_pairs"], ph["adj_near_target"],
+        roof("k_near_queue<4, NearOpG> (near field, target side)", NEAR_ADJ_TARGET_FLOPS * st["near_pairs"],
+             ph["adj_near_target"],
              "%g flops per near pair" % NEAR_ADJ_TARGET_FLOPS),
-        roof("k_near_adj_source32", NEAR_ADJ_SOURCE_FLOPS * st["near_pairs"], ph["adj_near_source"],
+        roof("k_near_adj_source32 (near field, source side)", NEAR_ADJ_SOURCE_FLOPS * st["near_pairs"],
+             ph["adj_near_source"],
              "%g flops per near pair" % NEAR_ADJ_SOURCE_FLOPS),
-        roof("k_far_adj_target32", far_f * st["far_interactions"], ph["adj_far_target"],
+        roof("k_far_adj_target32 (far field, target side)", far_f * st["far_interactions"], ph["adj_far_target"],
              "%g flops per far interaction on the folded coefficients (%g on all C(p+5,3))" % (far_f, far_u)),
     ]
     ms = statistics.mean(tot)
@@ -746,7 +748,7 @@ def main():
     # the unfolded form: recurrence 11 and contraction 24 flops per coefficient
     # of order <= p+2, plus 18 for d.B
     unfolded_far_flops = (11 + 24) * ncoef(p + 2) + 18
-    near_kernel = "k_near_fp64" if fp64 else "k_near_mixed"
+    near_kernel = "k_near_fp64" if fp64 else "k_near_queue<4, NearOpU>"
     dominant_near = near_ms >= far_ms
     if dominant_near:
         roof = {"bound": "alu", "kernel": near_kernel + " (near field, 43 flops per pair)", "achieved": near_tf,

@@ -364,21 +364,6 @@ struct NearOpG {
 
 constexpr int kNearAdjGroup = 4;
 
-__global__ void __launch_bounds__(kNearAdjWarps * 32)
-    k_near_adj_target32(const double* __restrict__ ts, const double* __restrict__ gs, int64_t M,
-                        const int4* __restrict__ topo, const float4* __restrict__ spack,
-                        const int64_t* __restrict__ near_off, const ListEntry* __restrict__ near_list,
-                        double* __restrict__ gt, int self)
-{
-    __shared__ nearpair::NearScratch<kNearAdjGroup> sc[kNearAdjWarps];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t ngroup = ((M + kBatch - 1) / kBatch + kNearAdjGroup - 1) / kNearAdjGroup;
-    const int64_t B = blockIdx.x * (int64_t)kNearAdjWarps + w;
-    if (B >= ngroup) return;
-    nearpair::near_group<kNearAdjGroup, NearOpG>(ts, gs, M, topo, spack, near_off, near_list, gt, B, self, 0.0f, sc[w],
-                                                  lane);
-}
-
 // source side over the near entries sorted by leaf, in chunks of
 // kNearAdjChunk entries (a chunk can straddle leaves): for each leaf segment
 // of its chunk a block runs a warp per 32 of the leaf's sources over the
@@ -1406,8 +1391,6 @@ extern "C" tc_status tc_adjoint(tc_ctx* ctx, const double* g, double* grad_f, do
 
     // near field: target side adds to adj_gt; source side writes adj_gnear
     const unsigned ngrid = (unsigned)((nbatch + kNearAdjWarps - 1) / kNearAdjWarps);
-    const int64_t ngroup = (nbatch + kNearAdjGroup - 1) / kNearAdjGroup;
-    const unsigned ngrid32 = (unsigned)((ngroup + kNearAdjWarps - 1) / kNearAdjWarps);
     ph_begin(ctx, TC_PH_ADJ_NEAR_T);
     if (ctx->precision == TC_FP64) {
         k_near_adj_target<double><<<ngrid, kNearAdjWarps * 32, 0, s>>>(
@@ -1422,10 +1405,15 @@ extern "C" tc_status tc_adjoint(tc_ctx* ctx, const double* g, double* grad_f, do
             ptr<int32_t>(ctx->adj_nebatch), ctx->near_entries, ptr<double>(ctx->adj_gnear));
         note_launch();
     } else {
-        k_near_adj_target32<<<ngrid32, kNearAdjWarps * 32, 0, s>>>(
-            ts, ptr<double>(ctx->adj_gs), M, ptr<int4>(ctx->node_topo), ptr<float4>(ctx->spack),
-            ptr<int64_t>(ctx->near_off), ptr<ListEntry>(ctx->near_list), ptr<double>(ctx->adj_gt), ctx->eval_self);
-        note_launch();
+        const NearSched sched = {ptr<uint64_t>(ctx->near_gkey), ptr<uint64_t>(ctx->near_gkey_alt),
+                                 ptr<int32_t>(ctx->near_gord), ptr<int32_t>(ctx->near_gord_alt),
+                                 ptr<uint32_t>(ctx->hist), reinterpret_cast<unsigned*>(ptr<char>(ctx->flags) + 224)};
+        TC_CK((nearpair::run_near_queue<kNearAdjGroup, NearOpG>(ts, ptr<double>(ctx->adj_gs), M,
+                                                                ptr<int4>(ctx->node_topo), ptr<float4>(ctx->spack),
+                                                                ptr<int64_t>(ctx->near_off),
+                                                                ptr<ListEntry>(ctx->near_list), ptr<double>(ctx->adj_gt),
+                                                                ctx->eval_self, 0.0f, sched, s)),
+              "near adjoint target side");
         ph_end(ctx, TC_PH_ADJ_NEAR_T);
         ph_begin(ctx, TC_PH_ADJ_NEAR_S);
         TC_CK(cudaMemsetAsync(ctx->adj_gnear.p, 0, (size_t)12 * N * 8, s), "zero near gradients");

@@ -12,9 +12,9 @@
 // a leaf are accumulated by compensated (Kahan) FP32 summation and each
 // leaf's sum is added to an FP64 per-target accumulator (an FP64 addition per
 // tile stalled every tile's end on the slow FP64 pipe).  One warp handles a
-// group of consecutive batches (eight in the one-system kernel, four in the
-// batched one) and walks the merge of their near lists (all in tree order,
-// i.e. by the leaf's first source); for each leaf the targets that need it
+// group of four consecutive batches and walks the merge of their near lists
+// (all in tree order, i.e. by the leaf's first source); for each leaf the
+// targets that need it
 // are packed densely into 32-lane streams, and two streams share every staged
 // tile, so every broadcast source value feeds two targets.  The tile holds the
 // sources in pairs, field by field ((y_2q.f, y_2q+1.f) adjacent), and the
@@ -30,17 +30,6 @@ namespace tc {
 namespace {
 
 constexpr int kNearWarps = 4;
-// Batches per warp in the one-system mixed-precision kernel.  The groups are
-// taken from a queue in order of decreasing work (k_group_work), so the end
-// of the kernel is made of the smallest groups.  Eight when the groups still
-// fill the GPU (at least 0.6 of a resident wave of warps): at N = 10^6 the
-// near kernel alone takes 37.8 ms with eight and 34.4 ms with four, but with
-// eight the far field, which the step runs on its own stream, fills the SMs
-// its end leaves free (step 53.2 against 54.4 ms); four otherwise, since
-// fewer groups than the GPU holds warps leave it idle (N = 327680 on the
-// sphere: 36 ms with four, 64 ms with eight).
-constexpr int kNearGroupLarge = 8;
-constexpr double kNearWaveShare = 0.6;
 constexpr int kNearMaxWarps = 8;  // largest block the batched kernel accepts
 
 // ---------------------------------------------------------------------------
@@ -260,101 +249,6 @@ __device__ inline void near_batch_fp64(const double* __restrict__ ts, int64_t M,
     }
 }
 
-// Work of each group of G batches, its pair count (over its near entries, the
-// active targets times the leaf size), as a sort key that puts the groups
-// with the most work first; order receives the identity.
-template <int G>
-__global__ void k_group_work(const int64_t* __restrict__ near_off, const ListEntry* __restrict__ near_list,
-                             const int4* __restrict__ topo, int64_t nbatch, int64_t ngroup, uint64_t* __restrict__ keys,
-                             int32_t* __restrict__ order)
-{
-    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (g >= ngroup) return;
-    const int64_t b0 = g * G, b1 = min(nbatch, b0 + G);
-    uint64_t w = 0;
-    for (int64_t e = near_off[b0]; e < near_off[b1]; e++) {
-        const ListEntry le = near_list[e];
-        w += (uint64_t)__popc(le.mask) * (uint64_t)topo[le.node].y;
-    }
-    keys[g] = 0xffffffffull - (w < 0xffffffffull ? w : 0xffffffffull);
-    order[g] = (int32_t)g;
-}
-
-// The one-system near field on a resident grid: each warp takes the next
-// group from the queue, in order of decreasing work (order), or in index
-// order (order = NULL) when the grid holds every group at once.
-template <int G, typename Op>
-__global__ void __launch_bounds__(kNearWarps * 32)
-    k_near_mixed_q(const double* __restrict__ ts, int64_t M, const int4* __restrict__ topo,
-                   const float4* __restrict__ spack, const int64_t* __restrict__ near_off,
-                   const ListEntry* __restrict__ near_list, double* __restrict__ u_near, int self,
-                   const int32_t* __restrict__ order, int64_t ngroup, unsigned* __restrict__ queue, float prm)
-{
-    __shared__ NearScratch<G> sc[kNearWarps];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (;;) {
-        unsigned i = 0;
-        if (lane == 0) i = atomicAdd(queue, 1u);
-        i = __shfl_sync(0xffffffffu, i, 0);
-        if ((int64_t)i >= ngroup) break;
-        nearpair::near_group<G, Op>(ts, nullptr, M, topo, spack, near_off, near_list, u_near, order ? order[i] : i,
-                                    self, prm, sc[w], lane);
-    }
-}
-
-template <int G, typename Op = NearOpU>
-cudaError_t run_near_mixed(const double* ts, int64_t M, const int4* topo, const float4* spack,
-                           const int64_t* near_off, const ListEntry* near_list, double* u_near, int self,
-                           const NearSched& sc, cudaStream_t s, float prm = 0.0f)
-{
-    const int64_t nbatch = (M + kBatch - 1) / kBatch;
-    const int64_t ngroup = (nbatch + G - 1) / G;
-    static int ps = 0, sms = 0;
-    if (ps == 0) {
-        int dev = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, k_near_mixed_q<G, Op>, kNearWarps * 32, 0) !=
-                cudaSuccess ||
-            ps < 1)
-            ps = 1;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    }
-    const int64_t need = (ngroup + kNearWarps - 1) / kNearWarps;
-    const int64_t resident = (int64_t)ps * std::max(sms, 1);
-    const unsigned grid = (unsigned)std::min<int64_t>(need, resident);
-    // the order matters only when some warps take more than one group
-    const int32_t* order = nullptr;
-    if (need > resident) {
-        k_group_work<G><<<(unsigned)((ngroup + 255) / 256), 256, 0, s>>>(near_off, near_list, topo, nbatch, ngroup,
-                                                                        sc.keys, sc.order);
-        note_launch();
-        cudaError_t e = radix_sort_bits(sc.keys, sc.order, sc.keys_alt, sc.order_alt, sc.hist, ngroup, 32, s);
-        if (e != cudaSuccess) return e;
-        order = sc.order;
-    }
-    cudaError_t e = cudaMemsetAsync(sc.queue, 0, sizeof(unsigned), s);
-    if (e != cudaSuccess) return e;
-    k_near_mixed_q<G, Op><<<grid, kNearWarps * 32, 0, s>>>(ts, M, topo, spack, near_off, near_list, u_near, self,
-                                                           order, ngroup, sc.queue, prm);
-    return cudaGetLastError();
-}
-
-// warps of k_near_mixed<kNearGroupLarge> the GPU holds at once
-int near_resident_warps()
-{
-    static int warps = 0;
-    if (warps == 0) {
-        int per_sm = 0, dev = 0, sms = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_near_mixed_q<kNearGroupLarge, NearOpU>, kNearWarps * 32,
-                                                          0) != cudaSuccess)
-            per_sm = 1;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        warps = (per_sm > 0 ? per_sm : 1) * kNearWarps * (sms > 0 ? sms : 1);
-    }
-    return warps;
-}
-
 template <bool kReg>
 __global__ void __launch_bounds__(kNearWarps * 32)
     k_near_fp64(const double* __restrict__ ts, int64_t M, const int4* __restrict__ topo,
@@ -476,19 +370,11 @@ cudaError_t launch_near(int precision, const double* ts, int64_t M, const int4* 
                                                                 0.0);
     } else if (eps > 0.0) {
         // the regularized kernels: groups of four (no tuning for this path)
-        cudaError_t e = run_near_mixed<kNearGroupBatches, NearOpReg>(ts, M, topo, spack, near_off, near_list, u_near,
-                                                                     self, sched, s, (float)e2);
-        note_launch();
-        return e;
+        return nearpair::run_near_queue<kNearGroupBatches, NearOpReg>(ts, nullptr, M, topo, spack, near_off,
+                                                                      near_list, u_near, self, (float)e2, sched, s);
     } else {
-        const bool large = (double)((nbatch + kNearGroupLarge - 1) / kNearGroupLarge) >=
-                           kNearWaveShare * near_resident_warps();
-        cudaError_t e = large ? run_near_mixed<kNearGroupLarge>(ts, M, topo, spack, near_off, near_list, u_near,
-                                                                  self, sched, s)
-                              : run_near_mixed<kNearGroupBatches>(ts, M, topo, spack, near_off, near_list, u_near,
-                                                                  self, sched, s);
-        note_launch();
-        return e;
+        return nearpair::run_near_queue<kNearGroupBatches, NearOpU>(ts, nullptr, M, topo, spack, near_off,
+                                                                    near_list, u_near, self, 0.0f, sched, s);
     }
     note_launch();
     return cudaGetLastError();

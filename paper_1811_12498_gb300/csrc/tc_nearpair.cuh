@@ -236,5 +236,98 @@ __device__ inline void near_group(const double* __restrict__ ts, const double* _
     }
 }
 
+// ---------------------------------------------------------------------------
+// Scheduling of the groups over a resident grid (the one-system near field and
+// the target side of its adjoint).  A grid one block per SM short of the
+// occupancy limit drains a queue of groups; when the groups outnumber its
+// warps, they are taken in order of decreasing work (k_group_work + radix
+// sort), so each warp drains several and the end of the kernel is made of the
+// smallest ones.  Measured at N = 10^6 (near kernel alone / step): groups of
+// eight at full occupancy 37.4 / 53.0 ms, eight one block short 35.7 / 53.1,
+// four at full occupancy 34.2 / 54.3, four one block short 33.3 / 54.1, four
+// two blocks short 34.4 / 54.4.
+
+constexpr int kQueueWarps = 4;       // warps per block of the queued kernels
+constexpr int kQueueFreeBlocks = 1;  // block slots per SM left free
+
+// Work of each group of G batches, its pair count (over its near entries, the
+// active targets times the leaf size), as a sort key that puts the groups
+// with the most work first; order receives the identity.
+template <int G>
+__global__ void k_group_work(const int64_t* __restrict__ near_off, const ListEntry* __restrict__ near_list,
+                             const int4* __restrict__ topo, int64_t nbatch, int64_t ngroup, uint64_t* __restrict__ keys,
+                             int32_t* __restrict__ order)
+{
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= ngroup) return;
+    const int64_t b0 = g * G, b1 = min(nbatch, b0 + G);
+    uint64_t w = 0;
+    for (int64_t e = near_off[b0]; e < near_off[b1]; e++) {
+        const ListEntry le = near_list[e];
+        w += (uint64_t)__popc(le.mask) * (uint64_t)topo[le.node].y;
+    }
+    keys[g] = 0xffffffffull - (w < 0xffffffffull ? w : 0xffffffffull);
+    order[g] = (int32_t)g;
+}
+
+// Each warp takes the next group from the queue: order[i], or i when order is
+// NULL (the grid holds every group at once).
+template <int G, typename Op>
+__global__ void __launch_bounds__(kQueueWarps * 32)
+    k_near_queue(const double* __restrict__ ts, const double* __restrict__ gs, int64_t M,
+                 const int4* __restrict__ topo, const float4* __restrict__ spack, const int64_t* __restrict__ near_off,
+                 const ListEntry* __restrict__ near_list, double* __restrict__ out, int self, float prm,
+                 const int32_t* __restrict__ order, int64_t ngroup, unsigned* __restrict__ queue)
+{
+    __shared__ NearScratch<G> sc[kQueueWarps];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (;;) {
+        unsigned i = 0;
+        if (lane == 0) i = atomicAdd(queue, 1u);
+        i = __shfl_sync(0xffffffffu, i, 0);
+        if ((int64_t)i >= ngroup) break;
+        near_group<G, Op>(ts, gs, M, topo, spack, near_off, near_list, out, order ? order[i] : i, self, prm, sc[w],
+                          lane);
+    }
+}
+
+template <int G, typename Op>
+cudaError_t run_near_queue(const double* ts, const double* gs, int64_t M, const int4* topo, const float4* spack,
+                           const int64_t* near_off, const ListEntry* near_list, double* out, int self, float prm,
+                           const NearSched& sc, cudaStream_t s)
+{
+    const int64_t nbatch = (M + kBatch - 1) / kBatch;
+    const int64_t ngroup = (nbatch + G - 1) / G;
+    static int ps = 0, sms = 0;
+    if (ps == 0) {
+        int dev = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, k_near_queue<G, Op>, kQueueWarps * 32, 0) !=
+                cudaSuccess ||
+            ps < 1)
+            ps = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    }
+    const int64_t need = (ngroup + kQueueWarps - 1) / kQueueWarps;
+    const int64_t resident = (int64_t)(ps > kQueueFreeBlocks ? ps - kQueueFreeBlocks : 1) * (sms > 0 ? sms : 1);
+    const unsigned grid = (unsigned)(need < resident ? need : resident);
+    // the order matters only when some warps take more than one group
+    const int32_t* order = nullptr;
+    if (need > resident) {
+        k_group_work<G><<<(unsigned)((ngroup + 255) / 256), 256, 0, s>>>(near_off, near_list, topo, nbatch, ngroup,
+                                                                        sc.keys, sc.order);
+        note_launch();
+        cudaError_t e = radix_sort_bits(sc.keys, sc.order, sc.keys_alt, sc.order_alt, sc.hist, ngroup, 32, s);
+        if (e != cudaSuccess) return e;
+        order = sc.order;
+    }
+    cudaError_t e = cudaMemsetAsync(sc.queue, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    k_near_queue<G, Op><<<grid, kQueueWarps * 32, 0, s>>>(ts, gs, M, topo, spack, near_off, near_list, out, self, prm,
+                                                           order, ngroup, sc.queue);
+    note_launch();
+    return cudaGetLastError();
+}
+
 }  // namespace nearpair
 }  // namespace tc
