@@ -80,8 +80,9 @@ struct NearScratch {
 // are packed densely into ceil(A/32) streams of 32 lanes, so lanes whose
 // target does not need the leaf are not computed (lane use of single-batch
 // lists at N = 1M: 0.74); streams are evaluated two at a time, each sharing
-// the staged tile, and each result is added to its target's accumulator in
-// shared memory.  self: the targets are the sources (sorted index = source
+// the staged tile (a stream left alone runs the two halves of each tile on
+// the two chains of its lanes instead), and each result is added to its
+// target's accumulator in shared memory.  self: the targets are the sources (sorted index = source
 // index), which lets leaves that cannot hold a stream's own target skip the
 // r = 0 guard.
 //
@@ -183,12 +184,23 @@ __device__ inline void near_group(const double* __restrict__ ts, const double* _
                         Op::template terms<false>(ta, tp, axa, aya, aza);
                         Op::template terms<false>(tb, tp, axb, ayb, azb);
                     }
-                } else if (guard) {
-                    for (int q = 0; q < npairs; q++)
-                        Op::template terms<true>(ta, sc.tile + q * kPairStride, axa, aya, aza);
                 } else {
-                    for (int q = 0; q < npairs; q++)
-                        Op::template terms<false>(ta, sc.tile + q * kPairStride, axa, aya, aza);
+                    // one stream: the lane's two chains take the two halves of
+                    // the tile (the b sums are added to the a sums below)
+                    const int h2 = npairs >> 1, h1 = npairs - h2;
+                    if (guard) {
+                        for (int q = 0; q < h2; q++) {
+                            Op::template terms<true>(ta, sc.tile + q * kPairStride, axa, aya, aza);
+                            Op::template terms<true>(ta, sc.tile + (q + h1) * kPairStride, axb, ayb, azb);
+                        }
+                        if (h1 > h2) Op::template terms<true>(ta, sc.tile + h2 * kPairStride, axa, aya, aza);
+                    } else {
+                        for (int q = 0; q < h2; q++) {
+                            Op::template terms<false>(ta, sc.tile + q * kPairStride, axa, aya, aza);
+                            Op::template terms<false>(ta, sc.tile + (q + h1) * kPairStride, axb, ayb, azb);
+                        }
+                        if (h1 > h2) Op::template terms<false>(ta, sc.tile + h2 * kPairStride, axa, aya, aza);
+                    }
                 }
                 kahan_add(sa[0], ka[0], axa.x + axa.y);
                 kahan_add(sa[1], ka[1], aya.x + aya.y);
@@ -197,9 +209,15 @@ __device__ inline void near_group(const double* __restrict__ ts, const double* _
                 kahan_add(sb[1], kb[1], ayb.x + ayb.y);
                 kahan_add(sb[2], kb[2], azb.x + azb.y);
             }
-            const double a0 = (double)sa[0] - (double)ka[0], a1 = (double)sa[1] - (double)ka[1],
-                         a2 = (double)sa[2] - (double)ka[2], c0 = (double)sb[0] - (double)kb[0],
-                         c1 = (double)sb[1] - (double)kb[1], c2 = (double)sb[2] - (double)kb[2];
+            double a0 = (double)sa[0] - (double)ka[0], a1 = (double)sa[1] - (double)ka[1],
+                   a2 = (double)sa[2] - (double)ka[2];
+            const double c0 = (double)sb[0] - (double)kb[0], c1 = (double)sb[1] - (double)kb[1],
+                         c2 = (double)sb[2] - (double)kb[2];
+            if (!two) {  // the second half of a one-stream pass
+                a0 += c0;
+                a1 += c1;
+                a2 += c2;
+            }
             // each (batch, lane) target holds one slot per leaf: no two lanes
             // add to the same accumulator here
             if (v1) {

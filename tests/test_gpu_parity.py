@@ -399,3 +399,22 @@ def test_velocity_from_host_buffers(prec):
     tree.set_moments(f, h, nu, p)
     ref = tree.treecode(x, theta, p)
     assert oracle.rel_l2(u_pinned.numpy().T, ref) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec,p", [("mixed", 10), ("mixed", 12), ("fp64", 12)])
+def test_deep_tree_high_order_matches_oracle(prec, p):
+    """Gaussian clusters (sigma 0.05, a deep tree: the smallest clusters are
+    about 1e-3 across) at the highest orders, where the far field's
+    coefficients span the widest range (|b^k| ~ R^-(n+1)): the scale-free
+    FP32 recurrence on folded tables stays within the mixed tolerance."""
+    x, f, h, nu = inputs.gaussian_clusters(40000, 4043)
+    tc = api.Treecode(prec, True).build(dev(x), 64).moments(dev(f), dev(h), dev(nu), p)
+    u = host(tc.eval(0.5, p))
+    tc.close()
+    tree = oracle.Tree(x, 64, True)
+    tree.set_moments(f, h, nu, p)
+    idx = inputs.sample_indices(40000, 3000, 4044)
+    ref = tree.treecode(x[idx], 0.5, p)
+    err = oracle.rel_l2(u[idx], ref)
+    print("deep tree p=%d %s: %.3e" % (p, prec, err))
+    assert err <= TOL[prec], err
