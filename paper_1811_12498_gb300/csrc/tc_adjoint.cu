@@ -362,7 +362,6 @@ struct NearOpG {
     }
 };
 
-constexpr int kNearAdjGroup = 4;
 
 // source side over the near entries sorted by leaf, in chunks of
 // kNearAdjChunk entries (a chunk can straddle leaves): for each leaf segment
@@ -1408,7 +1407,7 @@ extern "C" tc_status tc_adjoint(tc_ctx* ctx, const double* g, double* grad_f, do
         const NearSched sched = {ptr<uint64_t>(ctx->near_gkey), ptr<uint64_t>(ctx->near_gkey_alt),
                                  ptr<int32_t>(ctx->near_gord), ptr<int32_t>(ctx->near_gord_alt),
                                  ptr<uint32_t>(ctx->hist), reinterpret_cast<unsigned*>(ptr<char>(ctx->flags) + 224)};
-        TC_CK((nearpair::run_near_queue<kNearAdjGroup, NearOpG>(ts, ptr<double>(ctx->adj_gs), M,
+        TC_CK((nearpair::run_near_auto<NearOpG>(ts, ptr<double>(ctx->adj_gs), M,
                                                                 ptr<int4>(ctx->node_topo), ptr<float4>(ctx->spack),
                                                                 ptr<int64_t>(ctx->near_off),
                                                                 ptr<ListEntry>(ctx->near_list), ptr<double>(ctx->adj_gt),

@@ -350,7 +350,7 @@ inline unsigned grid_for(int64_t n, int threads)
 int64_t near_max_groups(int64_t M)
 {
     const int64_t nbatch = (M + kBatch - 1) / kBatch;
-    return (nbatch + kNearGroupBatches - 1) / kNearGroupBatches;
+    return (nbatch + 1) / 2;  // the smallest groups of the queue (two batches)
 }
 
 cudaError_t launch_near(int precision, const double* ts, int64_t M, const int4* topo,
@@ -370,11 +370,11 @@ cudaError_t launch_near(int precision, const double* ts, int64_t M, const int4* 
                                                                 0.0);
     } else if (eps > 0.0) {
         // the regularized kernels: groups of four (no tuning for this path)
-        return nearpair::run_near_queue<kNearGroupBatches, NearOpReg>(ts, nullptr, M, topo, spack, near_off,
-                                                                      near_list, u_near, self, (float)e2, sched, s);
+        return nearpair::run_near_auto<NearOpReg>(ts, nullptr, M, topo, spack, near_off, near_list, u_near, self,
+                                                  (float)e2, sched, s);
     } else {
-        return nearpair::run_near_queue<kNearGroupBatches, NearOpU>(ts, nullptr, M, topo, spack, near_off,
-                                                                    near_list, u_near, self, 0.0f, sched, s);
+        return nearpair::run_near_auto<NearOpU>(ts, nullptr, M, topo, spack, near_off, near_list, u_near, self,
+                                                0.0f, sched, s);
     }
     note_launch();
     return cudaGetLastError();

@@ -80,9 +80,9 @@ struct NearScratch {
 // are packed densely into ceil(A/32) streams of 32 lanes, so lanes whose
 // target does not need the leaf are not computed (lane use of single-batch
 // lists at N = 1M: 0.74); streams are evaluated two at a time, each sharing
-// the staged tile (a stream left alone runs the two halves of each tile on
-// the two chains of its lanes instead), and each result is added to its
-// target's accumulator in shared memory.  self: the targets are the sources (sorted index = source
+// the staged tile, and each result is added to its target's accumulator in
+// shared memory.  A target's arithmetic does not depend on which stream or
+// lane it is packed into, so any group size gives the same bits.  self: the targets are the sources (sorted index = source
 // index), which lets leaves that cannot hold a stream's own target skip the
 // r = 0 guard.
 //
@@ -184,23 +184,12 @@ __device__ inline void near_group(const double* __restrict__ ts, const double* _
                         Op::template terms<false>(ta, tp, axa, aya, aza);
                         Op::template terms<false>(tb, tp, axb, ayb, azb);
                     }
+                } else if (guard) {
+                    for (int q = 0; q < npairs; q++)
+                        Op::template terms<true>(ta, sc.tile + q * kPairStride, axa, aya, aza);
                 } else {
-                    // one stream: the lane's two chains take the two halves of
-                    // the tile (the b sums are added to the a sums below)
-                    const int h2 = npairs >> 1, h1 = npairs - h2;
-                    if (guard) {
-                        for (int q = 0; q < h2; q++) {
-                            Op::template terms<true>(ta, sc.tile + q * kPairStride, axa, aya, aza);
-                            Op::template terms<true>(ta, sc.tile + (q + h1) * kPairStride, axb, ayb, azb);
-                        }
-                        if (h1 > h2) Op::template terms<true>(ta, sc.tile + h2 * kPairStride, axa, aya, aza);
-                    } else {
-                        for (int q = 0; q < h2; q++) {
-                            Op::template terms<false>(ta, sc.tile + q * kPairStride, axa, aya, aza);
-                            Op::template terms<false>(ta, sc.tile + (q + h1) * kPairStride, axb, ayb, azb);
-                        }
-                        if (h1 > h2) Op::template terms<false>(ta, sc.tile + h2 * kPairStride, axa, aya, aza);
-                    }
+                    for (int q = 0; q < npairs; q++)
+                        Op::template terms<false>(ta, sc.tile + q * kPairStride, axa, aya, aza);
                 }
                 kahan_add(sa[0], ka[0], axa.x + axa.y);
                 kahan_add(sa[1], ka[1], aya.x + aya.y);
@@ -209,15 +198,9 @@ __device__ inline void near_group(const double* __restrict__ ts, const double* _
                 kahan_add(sb[1], kb[1], ayb.x + ayb.y);
                 kahan_add(sb[2], kb[2], azb.x + azb.y);
             }
-            double a0 = (double)sa[0] - (double)ka[0], a1 = (double)sa[1] - (double)ka[1],
-                   a2 = (double)sa[2] - (double)ka[2];
-            const double c0 = (double)sb[0] - (double)kb[0], c1 = (double)sb[1] - (double)kb[1],
-                         c2 = (double)sb[2] - (double)kb[2];
-            if (!two) {  // the second half of a one-stream pass
-                a0 += c0;
-                a1 += c1;
-                a2 += c2;
-            }
+            const double a0 = (double)sa[0] - (double)ka[0], a1 = (double)sa[1] - (double)ka[1],
+                         a2 = (double)sa[2] - (double)ka[2], c0 = (double)sb[0] - (double)kb[0],
+                         c1 = (double)sb[1] - (double)kb[1], c2 = (double)sb[2] - (double)kb[2];
             // each (batch, lane) target holds one slot per leaf: no two lanes
             // add to the same accumulator here
             if (v1) {
@@ -309,13 +292,11 @@ __global__ void __launch_bounds__(kQueueWarps * 32)
     }
 }
 
+// blocks of k_near_queue<G, Op> the grid takes: the occupancy limit less
+// kQueueFreeBlocks per SM, times the SMs
 template <int G, typename Op>
-cudaError_t run_near_queue(const double* ts, const double* gs, int64_t M, const int4* topo, const float4* spack,
-                           const int64_t* near_off, const ListEntry* near_list, double* out, int self, float prm,
-                           const NearSched& sc, cudaStream_t s)
+int64_t queue_resident_blocks()
 {
-    const int64_t nbatch = (M + kBatch - 1) / kBatch;
-    const int64_t ngroup = (nbatch + G - 1) / G;
     static int ps = 0, sms = 0;
     if (ps == 0) {
         int dev = 0;
@@ -326,8 +307,18 @@ cudaError_t run_near_queue(const double* ts, const double* gs, int64_t M, const 
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     }
+    return (int64_t)(ps > kQueueFreeBlocks ? ps - kQueueFreeBlocks : 1) * (sms > 0 ? sms : 1);
+}
+
+template <int G, typename Op>
+cudaError_t run_near_queue(const double* ts, const double* gs, int64_t M, const int4* topo, const float4* spack,
+                           const int64_t* near_off, const ListEntry* near_list, double* out, int self, float prm,
+                           const NearSched& sc, cudaStream_t s)
+{
+    const int64_t nbatch = (M + kBatch - 1) / kBatch;
+    const int64_t ngroup = (nbatch + G - 1) / G;
     const int64_t need = (ngroup + kQueueWarps - 1) / kQueueWarps;
-    const int64_t resident = (int64_t)(ps > kQueueFreeBlocks ? ps - kQueueFreeBlocks : 1) * (sms > 0 ? sms : 1);
+    const int64_t resident = queue_resident_blocks<G, Op>();
     const unsigned grid = (unsigned)(need < resident ? need : resident);
     // the order matters only when some warps take more than one group
     const int32_t* order = nullptr;
@@ -345,6 +336,22 @@ cudaError_t run_near_queue(const double* ts, const double* gs, int64_t M, const 
                                                            order, ngroup, sc.queue);
     note_launch();
     return cudaGetLastError();
+}
+
+// Groups of four batches when there are at least kQueueMinGroups of them per
+// warp of the grid, else groups of two (more, smaller groups, so that the
+// queue can still balance the warps of a smaller or more uneven problem).
+constexpr int kQueueMinGroups = 2;
+
+template <typename Op>
+cudaError_t run_near_auto(const double* ts, const double* gs, int64_t M, const int4* topo, const float4* spack,
+                          const int64_t* near_off, const ListEntry* near_list, double* out, int self, float prm,
+                          const NearSched& sc, cudaStream_t s)
+{
+    const int64_t nbatch = (M + kBatch - 1) / kBatch;
+    if ((nbatch + 3) / 4 >= kQueueMinGroups * kQueueWarps * queue_resident_blocks<4, Op>())
+        return run_near_queue<4, Op>(ts, gs, M, topo, spack, near_off, near_list, out, self, prm, sc, s);
+    return run_near_queue<2, Op>(ts, gs, M, topo, spack, near_off, near_list, out, self, prm, sc, s);
 }
 
 }  // namespace nearpair
