@@ -754,7 +754,7 @@ def main():
         roof = {"bound": "alu", "kernel": near_kernel + " (near field, 43 flops per pair)", "achieved": near_tf,
                 "peak": peak, "unit": "TFLOP/s", "peak_kind": peak_kind, "frac": near_tf / peak,
                 "nominal_peak": nominal, "frac_of_nominal": near_tf / nominal,
-                "traffic": None if fp64 else kernel_traffic(NEAR_SOURCES, "near_field_uniform_cube_524k.md"),
+                "traffic": None if fp64 else kernel_traffic(NEAR_SOURCES, "near_field_uniform_cube_1M.md"),
                 "flops_per_launch": near_flops, "launch_ms": near_ms}
     else:
         roof = {"bound": "alu", "kernel": "k_far (far field, folded recurrence + contraction)", "achieved": far_tf,
