@@ -82,6 +82,11 @@ def folded_coefficients(P):
 # one order further (to p + 3) and, per coefficient k, alpha^k = g.(A^k +
 # d' B^k) 30, beta_l^k = sum_i g_i B_il^k 18, the sums b^k beta^k 6 and
 # (k_l + 1) b^{k+e_l} alpha^k 9: 63.
+# regularized pair terms per (target, source) pair: d 3, r^2 5, s 1, 1/sqrt(s)
+# 1, q^2 1, d.f, d.h, d.nu 15, f coefficient q (1 + eps^2 q^2) 3, (d.h)(d.nu)
+# + (eps^2/2)(h.nu) 3, the d coefficient 4, the h and nu coefficient 5, the
+# three components (f, d, h, nu terms) 24: 65
+REG_NEAR_PAIR_FLOPS = 65
 NEAR_ADJ_TARGET_FLOPS = 85.0
 NEAR_ADJ_SOURCE_FLOPS = 109.0
 FAR_ADJ_PER_COEF_FLOPS = 63.0
@@ -541,11 +546,25 @@ def bench_regularized(flush, stream):
     it = torch.from_numpy(idx).cuda()
     E = float(torch.linalg.norm(u[:, it] - ud) / torch.linalg.norm(ud))
     ms = statistics.mean(times)
+    peak64 = api.fma_peak("fp64", stream)
+    peak32 = api.fma_peak("mixed", stream)
+    # FP64 far field per interaction: the recurrences of G_1/2 (orders <= p+2)
+    # and G_3/2 (orders <= p+1) at 11 flops per coefficient, the contractions
+    # at 24 and 6 flops per coefficient, d'.B 18
+    far_unit = 35 * ncoef(p + 2) + 17 * ncoef(p + 1) + 18
+    far_tf = far_unit * st["far_interactions"] / (ph["far"] / 1e3) / 1e12
+    near_tf = REG_NEAR_PAIR_FLOPS * st["near_pairs"] / (ph["near"] / 1e3) / 1e12
     return {"workload": "regularized kernels, eps=1e-3, uniform cube N=1000000, p=8, theta=0.5, N0=2000, mixed "
                         "(FP64 far field)",
             "ms_per_step": ms, "targets_per_s": N / (ms / 1e3), "far_ms": ph["far"], "near_ms": ph["near"],
             "far_interactions": st["far_interactions"], "near_pairs": st["near_pairs"],
-            "E_vs_fp64_regularized_direct": E, "E_samples": int(len(idx))}
+            "E_vs_fp64_regularized_direct": E, "E_samples": int(len(idx)),
+            "roofline": [
+                {"kernel": "k_far_reg (FP64)", "bound": "alu", "achieved": far_tf, "peak": peak64, "unit": "TFLOP/s",
+                 "frac": far_tf / peak64, "work_unit": "%d FP64 flops per far interaction" % far_unit},
+                {"kernel": "k_near_queue<G, NearOpReg>", "bound": "alu", "achieved": near_tf, "peak": peak32,
+                 "unit": "TFLOP/s", "frac": near_tf / peak32,
+                 "work_unit": "%d flops per near pair" % REG_NEAR_PAIR_FLOPS}]}
 
 
 def bench_batched(flush, stream, reps=3):
