@@ -340,7 +340,7 @@ def bench_fwd_adjoint(flush, stream, steps=3):
                 "flops_per_launch": flops, "launch_ms": ms_k, "work_unit": unit}
 
     rooflines = [
-        roof("k_near_queue<4, NearOpG> (near field, target side)", NEAR_ADJ_TARGET_FLOPS * st["near_pairs"],
+        roof("k_near_leaf<NearOpG> (near field, target side)", NEAR_ADJ_TARGET_FLOPS * st["near_pairs"],
              ph["adj_near_target"],
              "%g flops per near pair" % NEAR_ADJ_TARGET_FLOPS),
         roof("k_near_adj_source32 (near field, source side)", NEAR_ADJ_SOURCE_FLOPS * st["near_pairs"],
@@ -562,7 +562,7 @@ def bench_regularized(flush, stream):
             "roofline": [
                 {"kernel": "k_far_reg (FP64)", "bound": "alu", "achieved": far_tf, "peak": peak64, "unit": "TFLOP/s",
                  "frac": far_tf / peak64, "work_unit": "%d FP64 flops per far interaction" % far_unit},
-                {"kernel": "k_near_queue<G, NearOpReg>", "bound": "alu", "achieved": near_tf, "peak": peak32,
+                {"kernel": "k_near_leaf<NearOpReg>", "bound": "alu", "achieved": near_tf, "peak": peak32,
                  "unit": "TFLOP/s", "frac": near_tf / peak32,
                  "work_unit": "%d flops per near pair" % REG_NEAR_PAIR_FLOPS}]}
 
@@ -767,7 +767,7 @@ def main():
     # the unfolded form: recurrence 11 and contraction 24 flops per coefficient
     # of order <= p+2, plus 18 for d.B
     unfolded_far_flops = (11 + 24) * ncoef(p + 2) + 18
-    near_kernel = "k_near_fp64" if fp64 else "k_near_queue<4, NearOpU>"
+    near_kernel = "k_near_fp64" if fp64 else "k_near_leaf<NearOpU>"
     dominant_near = near_ms >= far_ms
     if dominant_near:
         roof = {"bound": "alu", "kernel": near_kernel + " (near field, 43 flops per pair)", "achieved": near_tf,

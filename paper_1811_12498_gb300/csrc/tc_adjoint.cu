@@ -69,32 +69,6 @@ __device__ inline void unflatten(int idx, int& k1, int& k2, int& k3)
     k1 = n - a;
 }
 
-// ------------------------------------------------------------ list helpers
-__global__ void k_entry_keys(const ListEntry* __restrict__ list, int64_t n, uint64_t* __restrict__ keys,
-                             int32_t* __restrict__ idx)
-{
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    keys[i] = (uint64_t)(uint32_t)list[i].node;
-    idx[i] = (int32_t)i;
-}
-
-// batch of each list entry: largest b with off[b] <= e
-__global__ void k_entry_batch(const int64_t* __restrict__ off, int64_t nbatch, int64_t n, int32_t* __restrict__ eb)
-{
-    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e >= n) return;
-    int64_t lo = 0, hi = nbatch;  // off[lo] <= e < off[hi]
-    while (hi - lo > 1) {
-        int64_t mid = (lo + hi) >> 1;
-        if (off[mid] <= e)
-            lo = mid;
-        else
-            hi = mid;
-    }
-    eb[e] = (int32_t)lo;
-}
-
 __global__ void k_gather_g(const double* __restrict__ g, const int32_t* __restrict__ perm, int64_t M,
                            double* __restrict__ gs)
 {
@@ -1303,31 +1277,6 @@ cudaError_t launch_far_adj32(tc_ctx* ctx, const double* ts, int64_t M, int p, cu
     }
 }
 
-// Sort one of the forward lists by cluster: keys/idx sorted, batch per entry.
-cudaError_t sort_entries(const ListEntry* list, int64_t n, const int64_t* off, int64_t nbatch, int64_t nnodes,
-                         DevBuf& keys, DevBuf& keys_alt, DevBuf& idx, DevBuf& idx_alt, DevBuf& eb, DevBuf& hist,
-                         cudaStream_t s)
-{
-    cudaError_t e;
-    if ((e = ensure(keys, (size_t)n * 8)) != cudaSuccess) return e;
-    if ((e = ensure(keys_alt, (size_t)n * 8)) != cudaSuccess) return e;
-    if ((e = ensure(idx, (size_t)n * 4)) != cudaSuccess) return e;
-    if ((e = ensure(idx_alt, (size_t)n * 4)) != cudaSuccess) return e;
-    if ((e = ensure(eb, (size_t)n * 4)) != cudaSuccess) return e;
-    if ((e = ensure(hist, (size_t)256 * radix_blocks(n) * 4)) != cudaSuccess) return e;
-    if (n == 0) return cudaSuccess;
-    k_entry_keys<<<grid_for(n, 256), 256, 0, s>>>(list, n, ptr<uint64_t>(keys), ptr<int32_t>(idx));
-    note_launch();
-    int bits = 1;
-    while (bits < 32 && ((int64_t)1 << bits) < nnodes) bits++;
-    e = radix_sort_bits(ptr<uint64_t>(keys), ptr<int32_t>(idx), ptr<uint64_t>(keys_alt), ptr<int32_t>(idx_alt),
-                        ptr<uint32_t>(hist), n, bits, s);
-    if (e != cudaSuccess) return e;
-    k_entry_batch<<<grid_for(n, 256), 256, 0, s>>>(off, nbatch, n, ptr<int32_t>(eb));
-    note_launch();
-    return cudaGetLastError();
-}
-
 }  // namespace
 }  // namespace tc
 
@@ -1366,16 +1315,17 @@ extern "C" tc_status tc_adjoint(tc_ctx* ctx, const double* g, double* grad_f, do
     TC_CK(ensure(ctx->adj_gnear, (size_t)12 * N * 8), "alloc adjoint");
 
     if (!ctx->adj_lists_ready) {
-        TC_CK(sort_entries(ptr<ListEntry>(ctx->far_list), ctx->far_entries, ptr<int64_t>(ctx->far_off), nbatch, nnodes,
-                           ctx->adj_fkeys, ctx->adj_fkeys_alt, ctx->adj_fidx, ctx->adj_fidx_alt, ctx->adj_febatch,
-                           ctx->adj_hist, s),
+        TC_CK(sort_list_entries(ptr<ListEntry>(ctx->far_list), ctx->far_entries, ptr<int64_t>(ctx->far_off), nbatch,
+                                nnodes, ctx->adj_fkeys, ctx->adj_fkeys_alt, ctx->adj_fidx, ctx->adj_fidx_alt,
+                                ctx->adj_febatch, ctx->adj_hist, s),
               "sort far entries");
-        TC_CK(sort_entries(ptr<ListEntry>(ctx->near_list), ctx->near_entries, ptr<int64_t>(ctx->near_off), nbatch,
-                           nnodes, ctx->adj_nkeys, ctx->adj_nkeys_alt, ctx->adj_nidx, ctx->adj_nidx_alt,
-                           ctx->adj_nebatch, ctx->adj_hist, s),
-              "sort near entries");
         ctx->adj_lists_ready = 1;
     }
+    // the near entries sorted by leaf (source side); in mixed precision the
+    // whole leaf-major schedule (target side), shared with the forward field
+    NearSched sched;
+    TC_CK(near_schedule(ctx, ctx->precision != TC_FP64, sched, s), "near schedule");
+    sched.queue = reinterpret_cast<unsigned*>(ptr<char>(ctx->flags) + 224);
     k_gather_g<<<grid_for(M, 256), 256, 0, s>>>(g, tperm, M, ptr<double>(ctx->adj_gs));
     note_launch();
     TC_CK(cudaMemsetAsync(ctx->adj_abar.p, 0, (size_t)nnodes * C2 * 12 * 8, s), "zero adjoint tables");
@@ -1400,26 +1350,22 @@ extern "C" tc_status tc_adjoint(tc_ctx* ctx, const double* g, double* grad_f, do
         ph_begin(ctx, TC_PH_ADJ_NEAR_S);
         k_near_adj_source<double><<<(unsigned)nnodes, kNearAdjWarps * 32, 0, s>>>(
             ts, ptr<double>(ctx->adj_gs), M, ptr<int4>(ctx->node_topo), ptr<double>(ctx->xs), ptr<double>(ctx->ws), N,
-            ptr<uint64_t>(ctx->adj_nkeys), ptr<int32_t>(ctx->adj_nidx), ptr<ListEntry>(ctx->near_list),
-            ptr<int32_t>(ctx->adj_nebatch), ctx->near_entries, ptr<double>(ctx->adj_gnear));
+            ptr<uint64_t>(ctx->nl_keys), ptr<int32_t>(ctx->nl_idx), ptr<ListEntry>(ctx->near_list),
+            ptr<int32_t>(ctx->nl_eb), ctx->near_entries, ptr<double>(ctx->adj_gnear));
         note_launch();
     } else {
-        const NearSched sched = {ptr<uint64_t>(ctx->near_gkey), ptr<uint64_t>(ctx->near_gkey_alt),
-                                 ptr<int32_t>(ctx->near_gord), ptr<int32_t>(ctx->near_gord_alt),
-                                 ptr<uint32_t>(ctx->hist), reinterpret_cast<unsigned*>(ptr<char>(ctx->flags) + 224)};
-        TC_CK((nearpair::run_near_auto<NearOpG>(ts, ptr<double>(ctx->adj_gs), M,
-                                                                ptr<int4>(ctx->node_topo), ptr<float4>(ctx->spack),
-                                                                ptr<int64_t>(ctx->near_off),
-                                                                ptr<ListEntry>(ctx->near_list), ptr<double>(ctx->adj_gt),
-                                                                ctx->eval_self, 0.0f, sched, s)),
+        TC_CK((nearpair::run_near_leaf<NearOpG>(ts, ptr<double>(ctx->adj_gs), M, ptr<int4>(ctx->node_topo),
+                                                ptr<float4>(ctx->spack), ptr<int64_t>(ctx->near_off),
+                                                ptr<ListEntry>(ctx->near_list), ptr<double>(ctx->adj_gt),
+                                                ctx->eval_self, 0.0f, sched, s)),
               "near adjoint target side");
         ph_end(ctx, TC_PH_ADJ_NEAR_T);
         ph_begin(ctx, TC_PH_ADJ_NEAR_S);
         TC_CK(cudaMemsetAsync(ctx->adj_gnear.p, 0, (size_t)12 * N * 8, s), "zero near gradients");
         k_near_adj_source32<<<grid_for(ctx->near_entries, kNearAdjChunk), kNearAdjWarps * 32, 0, s>>>(
             ts, ptr<double>(ctx->adj_gs), M, ptr<int4>(ctx->node_topo), ptr<float4>(ctx->spack), N,
-            ptr<uint64_t>(ctx->adj_nkeys), ptr<int32_t>(ctx->adj_nidx), ptr<ListEntry>(ctx->near_list),
-            ptr<int32_t>(ctx->adj_nebatch), ctx->near_entries, ptr<double>(ctx->adj_gnear));
+            ptr<uint64_t>(ctx->nl_keys), ptr<int32_t>(ctx->nl_idx), ptr<ListEntry>(ctx->near_list),
+            ptr<int32_t>(ctx->nl_eb), ctx->near_entries, ptr<double>(ctx->adj_gnear));
         note_launch();
     }
     ph_end(ctx, TC_PH_ADJ_NEAR_S);

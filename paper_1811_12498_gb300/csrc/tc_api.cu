@@ -118,9 +118,11 @@ static void release_all(tc_ctx* c)
                       &c->abf32, &c->geo32, &c->reg_et, &c->tkeys,
                       &c->tkeys_alt, &c->tperm, &c->tperm_alt, &c->ts, &c->nfar_e, &c->nnear_e,
                       &c->far_off, &c->near_off, &c->far_list, &c->near_list, &c->cnt_far, &c->cnt_near, &c->u_far,
-                      &c->u_near, &c->near_gkey, &c->near_gkey_alt, &c->near_gord, &c->near_gord_alt, &c->flags, &c->adj_fkeys, &c->adj_fkeys_alt, &c->adj_fidx, &c->adj_fidx_alt,
-                      &c->adj_febatch, &c->adj_nkeys, &c->adj_nkeys_alt, &c->adj_nidx, &c->adj_nidx_alt,
-                      &c->adj_nebatch, &c->adj_hist, &c->adj_gs, &c->adj_gt, &c->adj_abar, &c->adj_fbar, &c->adj_lam,
+                      &c->u_near, &c->nl_keys, &c->nl_keys_alt, &c->nl_idx, &c->nl_idx_alt, &c->nl_eb, &c->nl_hist,
+                      &c->nl_cnt, &c->nl_inc0, &c->nl_k0, &c->nl_k1, &c->nl_ninc0, &c->nl_nA, &c->nl_nkey,
+                      &c->nl_nkey_alt, &c->nl_nord, &c->nl_nord_alt, &c->nl_ucnt, &c->nl_uoff, &c->nl_units,
+                      &c->nl_inc_m, &c->nl_inc_e, &c->nl_slots, &c->flags, &c->adj_fkeys, &c->adj_fkeys_alt,
+                      &c->adj_fidx, &c->adj_fidx_alt, &c->adj_febatch, &c->adj_hist, &c->adj_gs, &c->adj_gt, &c->adj_abar, &c->adj_fbar, &c->adj_lam,
                       &c->adj_lamacc, &c->adj_gfar, &c->adj_gnear, &c->host_in, &c->host_u};
     for (DevBuf* b : bufs) release(*b);
 }
@@ -470,6 +472,7 @@ tc_status tc::eval_prepare_count(tc_ctx* ctx, const double* targets, int64_t M, 
     ctx->have_eval = 0;
     ctx->prepared = 0;
     ctx->adj_lists_ready = 0;
+    ctx->near_sched_ready = 0;
     const double* ts;
     if (!targets) {
         ts = ptr<double>(ctx->xs);
@@ -502,12 +505,6 @@ tc_status tc::eval_prepare_count(tc_ctx* ctx, const double* targets, int64_t M, 
     TC_CK(ensure(ctx->cnt_near, (size_t)M * 8), "alloc counts");
     TC_CK(ensure(ctx->u_far, (size_t)3 * M * 8), "alloc u");
     TC_CK(ensure(ctx->u_near, (size_t)3 * M * 8), "alloc u");
-    const int64_t ngmax = near_max_groups(M);
-    TC_CK(ensure(ctx->near_gkey, (size_t)ngmax * 8), "alloc near schedule");
-    TC_CK(ensure(ctx->near_gkey_alt, (size_t)ngmax * 8), "alloc near schedule");
-    TC_CK(ensure(ctx->near_gord, (size_t)ngmax * 4), "alloc near schedule");
-    TC_CK(ensure(ctx->near_gord_alt, (size_t)ngmax * 4), "alloc near schedule");
-    TC_CK(ensure(ctx->hist, (size_t)256 * radix_blocks(ngmax) * 4), "alloc near schedule");
     TC_CK(cudaMemsetAsync(ctx->flags.p, 0, 4, s), "flags");
     const int4* topo = ptr<int4>(ctx->node_topo);
     const Geo* geo = ptr<Geo>(ctx->node_geo);
@@ -626,9 +623,9 @@ tc_status tc::eval_compute(tc_ctx* ctx, double* u)
     ph_end(ctx, TC_PH_FAR, s2);
     TC_CK(cudaEventRecord(ctx->ev_join, s2), "join");
     ph_begin(ctx, TC_PH_NEAR);
-    const NearSched sched = {ptr<uint64_t>(ctx->near_gkey), ptr<uint64_t>(ctx->near_gkey_alt),
-                             ptr<int32_t>(ctx->near_gord), ptr<int32_t>(ctx->near_gord_alt), ptr<uint32_t>(ctx->hist),
-                             reinterpret_cast<unsigned*>(ptr<char>(ctx->flags) + 160)};
+    NearSched sched{};
+    if (ctx->precision == TC_MIXED) TC_CK(near_schedule(ctx, 1, sched, s), "near schedule");
+    sched.queue = reinterpret_cast<unsigned*>(ptr<char>(ctx->flags) + 160);
     TC_CK(launch_near(ctx->precision, ts, M, ptr<int4>(ctx->node_topo), ptr<double>(ctx->xs), ptr<double>(ctx->ws),
                       ptr<float4>(ctx->spack), ctx->N, ptr<int64_t>(ctx->near_off), ptr<ListEntry>(ctx->near_list),
                       ptr<double>(ctx->u_near), ctx->eval_self && !ctx->moved, sched, ctx->reg_eps, s),

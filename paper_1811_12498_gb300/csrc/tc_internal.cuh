@@ -177,7 +177,15 @@ struct tc_ctx {
     tc::DevBuf far_list, near_list;     // ListEntry
     tc::DevBuf cnt_far, cnt_near;       // per sorted target counts (int64)
     tc::DevBuf u_far, u_near;           // 3*M FP64 sorted order
-    tc::DevBuf near_gkey, near_gkey_alt, near_gord, near_gord_alt;  // near-field group schedule (NearSched)
+    // leaf-major near-field schedule (near_schedule): near entries sorted by
+    // leaf (keys, entry index, batch of each entry), per sorted entry its
+    // incidence count and first incidence, per node its range of sorted
+    // entries, first incidence, incidence count and sort key/order, the units,
+    // per incidence target and entry, and the slots of the leaf sums
+    tc::DevBuf nl_keys, nl_keys_alt, nl_idx, nl_idx_alt, nl_eb, nl_hist;
+    tc::DevBuf nl_cnt, nl_inc0, nl_k0, nl_k1, nl_ninc0, nl_nA, nl_nkey, nl_nkey_alt, nl_nord, nl_nord_alt;
+    tc::DevBuf nl_ucnt, nl_uoff, nl_units, nl_inc_m, nl_inc_e, nl_slots;
+    int near_sched_ready = 0;  // 0: none, 1: entries sorted, 2: full schedule (for the lists of the last tc_eval)
     tc::DevBuf flags;                   // int32 device error flags at byte 0; work-queue counters
                                         // of the far field (byte 128) and its adjoint's target side (192)
     int64_t far_entries = 0, near_entries = 0;  // list sizes of the last tc_eval
@@ -187,7 +195,6 @@ struct tc_ctx {
 
     // ---- adjoint (tc_adjoint)
     tc::DevBuf adj_fkeys, adj_fkeys_alt, adj_fidx, adj_fidx_alt, adj_febatch;  // far entries sorted by cluster
-    tc::DevBuf adj_nkeys, adj_nkeys_alt, adj_nidx, adj_nidx_alt, adj_nebatch;  // near entries sorted by leaf
     tc::DevBuf adj_hist;
     tc::DevBuf adj_gs, adj_gt;            // 3*M sorted g and target-position gradient
     tc::DevBuf adj_abar;                  // FP64 [node][ncoef(p+2)][12] adjoint of the tables
@@ -316,6 +323,11 @@ cudaError_t launch_scan_i32_to_i64(const int32_t* in, int64_t* out_excl, int64_t
                                    cudaStream_t s);
 cudaError_t launch_sum_i64(const int64_t* in, int64_t n, int64_t* out, cudaStream_t s);
 cudaError_t launch_sum_entry_sizes(const ListEntry* list, int64_t n, const int4* topo, int64_t* out, cudaStream_t s);
+// Sort the n entries of a list by cluster (stable): keys = cluster, idx =
+// entry index, in sorted order; eb = batch of each entry, by entry index.
+cudaError_t sort_list_entries(const ListEntry* list, int64_t n, const int64_t* off, int64_t nbatch, int64_t nnodes,
+                              DevBuf& keys, DevBuf& keys_alt, DevBuf& idx, DevBuf& idx_alt, DevBuf& eb,
+                              DevBuf& hist, cudaStream_t s);
 
 // tc_far.cu
 cudaError_t launch_far(int precision, int rec64, const double* ts, int64_t M, const int4* topo, const Geo* geo,
@@ -328,19 +340,25 @@ cudaError_t launch_far_batched(int precision, int rec64, const SysDesc* sys, int
                                int p, unsigned long long* counter, int warps_per_block, int blocks, cudaStream_t s);
 
 // tc_near.cu
-// Scratch of the one-system near field's schedule: the groups of batches are
-// taken from a queue in order of decreasing work (their pair counts, sorted
-// by radix sort), so the grid's tail is made of the smallest groups.
+// The leaf-major schedule of the one-system near field, built once per set
+// of near lists by near_schedule: the near entries sorted by leaf, the
+// targets of each leaf's entries (its incidences) in that order, and the units
+// of work, (leaf, pair of 32-target streams), in order of decreasing leaf size.
 struct NearSched {
-    uint64_t* keys;      // ngroup sort keys (and as many for the sort's second buffer)
-    uint64_t* keys_alt;
-    int32_t* order;      // ngroup group indices, sorted by decreasing work
-    int32_t* order_alt;
-    uint32_t* hist;      // radix histograms for ngroup keys
-    unsigned* queue;     // device counter
+    const int64_t* node_inc0;  // per node: its first incidence
+    const int32_t* node_A;     // per node: its incidences (0 for a node in no near list)
+    const int2* units;         // per unit: (node, stream pair)
+    const int32_t* nunits;     // device word: the number of units
+    const int32_t* inc_m;      // per incidence: sorted target index
+    const int32_t* inc_e;      // per incidence: its near-list entry
+    double* slots;             // 96 per near entry: leaf sums per (entry, component, lane)
+    int64_t E;                 // near entries
+    int64_t max_units;         // bound on the number of units
+    unsigned* queue;           // device word: the work-queue counter (the caller's)
 };
-// groups the near field's schedule may need at most (the smallest group size)
-int64_t near_max_groups(int64_t M);
+// Build the schedule for the lists of the last tc_eval, unless built already;
+// full = 0: only sort the near entries by leaf (nl_keys, nl_idx, nl_eb).
+cudaError_t near_schedule(tc_ctx* ctx, int full, NearSched& sc, cudaStream_t s);
 cudaError_t launch_near_batched(int precision, const SysDesc* sys, int nsys, const int64_t* item_off, int64_t nitems,
                                 unsigned long long* counter, int warps_per_block, int blocks, cudaStream_t s);
 cudaError_t launch_finalize_batched(const SysDesc* sys, int nsys, const int64_t* moff, int64_t mtotal, double* u,

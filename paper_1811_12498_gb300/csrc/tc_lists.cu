@@ -182,7 +182,63 @@ __global__ void k_sum_entry_sizes(const ListEntry* __restrict__ list, int64_t n,
     if (threadIdx.x == 0) *out = part[0];
 }
 
+// cluster of each list entry as its sort key, and the identity
+__global__ void k_entry_keys(const ListEntry* __restrict__ list, int64_t n, uint64_t* __restrict__ keys,
+                             int32_t* __restrict__ idx)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    keys[i] = (uint64_t)(uint32_t)list[i].node;
+    idx[i] = (int32_t)i;
+}
+
+// batch of each list entry: largest b with off[b] <= e
+__global__ void k_entry_batch(const int64_t* __restrict__ off, int64_t nbatch, int64_t n, int32_t* __restrict__ eb)
+{
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    int64_t lo = 0, hi = nbatch;  // off[lo] <= e < off[hi]
+    while (hi - lo > 1) {
+        int64_t mid = (lo + hi) >> 1;
+        if (off[mid] <= e)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    eb[e] = (int32_t)lo;
+}
+
+inline unsigned grid_for(int64_t n, int threads)
+{
+    int64_t g = (n + threads - 1) / threads;
+    return (unsigned)(g > 0 ? g : 1);
+}
+
 }  // namespace
+
+cudaError_t sort_list_entries(const ListEntry* list, int64_t n, const int64_t* off, int64_t nbatch, int64_t nnodes,
+                              DevBuf& keys, DevBuf& keys_alt, DevBuf& idx, DevBuf& idx_alt, DevBuf& eb,
+                              DevBuf& hist, cudaStream_t s)
+{
+    cudaError_t e;
+    if ((e = ensure(keys, (size_t)n * 8)) != cudaSuccess) return e;
+    if ((e = ensure(keys_alt, (size_t)n * 8)) != cudaSuccess) return e;
+    if ((e = ensure(idx, (size_t)n * 4)) != cudaSuccess) return e;
+    if ((e = ensure(idx_alt, (size_t)n * 4)) != cudaSuccess) return e;
+    if ((e = ensure(eb, (size_t)n * 4)) != cudaSuccess) return e;
+    if ((e = ensure(hist, (size_t)256 * radix_blocks(n) * 4)) != cudaSuccess) return e;
+    if (n == 0) return cudaSuccess;
+    k_entry_keys<<<grid_for(n, 256), 256, 0, s>>>(list, n, ptr<uint64_t>(keys), ptr<int32_t>(idx));
+    note_launch();
+    int bits = 1;
+    while (bits < 32 && ((int64_t)1 << bits) < nnodes) bits++;
+    e = radix_sort_bits(ptr<uint64_t>(keys), ptr<int32_t>(idx), ptr<uint64_t>(keys_alt), ptr<int32_t>(idx_alt),
+                        ptr<uint32_t>(hist), n, bits, s);
+    if (e != cudaSuccess) return e;
+    k_entry_batch<<<grid_for(n, 256), 256, 0, s>>>(off, nbatch, n, ptr<int32_t>(eb));
+    note_launch();
+    return cudaGetLastError();
+}
 
 cudaError_t launch_sum_entry_sizes(const ListEntry* list, int64_t n, const int4* topo, int64_t* out, cudaStream_t s)
 {

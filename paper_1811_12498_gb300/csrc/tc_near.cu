@@ -345,12 +345,169 @@ inline unsigned grid_for(int64_t n, int threads)
     return (unsigned)(g > 0 ? g : 1);
 }
 
+// ---------------------------------------------------------------------------
+// leaf-major schedule (near_schedule)
+
+// incidences of each sorted near entry
+__global__ void k_inc_count(const ListEntry* __restrict__ list, const int32_t* __restrict__ sidx, int64_t E,
+                            int32_t* __restrict__ cnt)
+{
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k < E) cnt[k] = __popc(list[sidx[k]].mask);
+}
+
+// each node's range [k0, k1) of sorted entries (both left 0 for a node in no
+// near list)
+__global__ void k_leaf_bounds(const uint64_t* __restrict__ skeys, int64_t E, int32_t* __restrict__ k0,
+                              int32_t* __restrict__ k1)
+{
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= E) return;
+    const uint64_t node = skeys[k];
+    if (k == 0 || skeys[k - 1] != node) k0[node] = (int32_t)k;
+    if (k == E - 1 || skeys[k + 1] != node) k1[node] = (int32_t)(k + 1);
+}
+
+// sort key of a node in no near list; the others' keys, below it, put the
+// largest leaves first
+constexpr uint64_t kLeafKeyNone = 0xffff;
+constexpr int kLeafKeyBits = 16;
+
+// per node: first incidence, incidence count and sort key; ord = identity
+__global__ void k_leaf_units(const int4* __restrict__ topo, int64_t nnodes, const int32_t* __restrict__ k0,
+                             const int32_t* __restrict__ k1, const int64_t* __restrict__ inc0,
+                             int64_t* __restrict__ node_inc0, int32_t* __restrict__ node_A,
+                             uint64_t* __restrict__ key, int32_t* __restrict__ ord)
+{
+    const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (n >= nnodes) return;
+    const int64_t i0 = inc0[k0[n]], A = inc0[k1[n]] - i0;
+    node_inc0[n] = i0;
+    node_A[n] = (int32_t)A;
+    const uint64_t size = (uint64_t)topo[n].y;
+    key[n] = A > 0 ? kLeafKeyNone - 1 - (size < kLeafKeyNone - 1 ? size : kLeafKeyNone - 1) : kLeafKeyNone;
+    ord[n] = (int32_t)n;
+}
+
+// units (pairs of 32-target streams) of the node at sorted position j
+__global__ void k_unit_count(const int32_t* __restrict__ ord, const int32_t* __restrict__ node_A, int64_t nnodes,
+                             int32_t* __restrict__ ucnt)
+{
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j < nnodes) ucnt[j] = (node_A[ord[j]] + 63) / 64;
+}
+
+__global__ void k_unit_fill(const int32_t* __restrict__ ord, const int32_t* __restrict__ ucnt,
+                            const int32_t* __restrict__ uoff, int64_t nnodes, int2* __restrict__ units)
+{
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= nnodes) return;
+    const int node = ord[j], c = ucnt[j];
+    int2* u = units + uoff[j];
+    for (int q = 0; q < c; q++) u[q] = make_int2(node, q);
+}
+
+// per incidence its sorted target and its entry: one warp per sorted entry,
+// lane l for the batch's target l
+__global__ void k_inc_fill(const ListEntry* __restrict__ list, const int32_t* __restrict__ sidx,
+                           const int32_t* __restrict__ eb, const int64_t* __restrict__ inc0, int64_t E,
+                           int32_t* __restrict__ inc_m, int32_t* __restrict__ inc_e)
+{
+    const int64_t k = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (k >= E) return;
+    const int e = sidx[k];
+    const unsigned mask = list[e].mask;
+    if ((mask >> lane) & 1u) {
+        const int64_t pos = inc0[k] + __popc(mask & ((1u << lane) - 1u));
+        inc_m[pos] = eb[e] * kBatch + lane;
+        inc_e[pos] = e;
+    }
+}
+
 }  // namespace
 
-int64_t near_max_groups(int64_t M)
+cudaError_t near_schedule(tc_ctx* ctx, int full, NearSched& sc, cudaStream_t s)
 {
-    const int64_t nbatch = (M + kBatch - 1) / kBatch;
-    return (nbatch + 1) / 2;  // the smallest groups of the queue (two batches)
+    const int64_t E = ctx->near_entries, nnodes = ctx->nnodes;
+    const int64_t nbatch = (ctx->M + kBatch - 1) / kBatch;
+    const ListEntry* list = ptr<ListEntry>(ctx->near_list);
+    cudaError_t e;
+    // one histogram buffer for both sorts (entries, nodes), sized before either runs
+    if ((e = ensure(ctx->nl_hist, (size_t)256 * radix_blocks(std::max(E, nnodes)) * 4)) != cudaSuccess) return e;
+    if (ctx->near_sched_ready < 1) {
+        e = sort_list_entries(list, E, ptr<int64_t>(ctx->near_off), nbatch, nnodes, ctx->nl_keys, ctx->nl_keys_alt,
+                              ctx->nl_idx, ctx->nl_idx_alt, ctx->nl_eb, ctx->nl_hist, s);
+        if (e != cudaSuccess) return e;
+        ctx->near_sched_ready = 1;
+    }
+    // sum over leaves of ceil(A / 64) <= 32 E / 64 + the leaves
+    const int64_t max_units = E / 2 + nnodes + 1;
+    if (full && ctx->near_sched_ready < 2) {
+        if ((e = ensure(ctx->nl_cnt, (size_t)(E + 1) * 4)) != cudaSuccess) return e;
+        if ((e = ensure(ctx->nl_inc0, (size_t)(E + 1) * 8)) != cudaSuccess) return e;
+        if ((e = ensure(ctx->nl_k0, (size_t)nnodes * 4)) != cudaSuccess) return e;
+        if ((e = ensure(ctx->nl_k1, (size_t)nnodes * 4)) != cudaSuccess) return e;
+        if ((e = ensure(ctx->nl_ninc0, (size_t)nnodes * 8)) != cudaSuccess) return e;
+        if ((e = ensure(ctx->nl_nA, (size_t)nnodes * 4)) != cudaSuccess) return e;
+        if ((e = ensure(ctx->nl_nkey, (size_t)nnodes * 8)) != cudaSuccess) return e;
+        if ((e = ensure(ctx->nl_nkey_alt, (size_t)nnodes * 8)) != cudaSuccess) return e;
+        if ((e = ensure(ctx->nl_nord, (size_t)nnodes * 4)) != cudaSuccess) return e;
+        if ((e = ensure(ctx->nl_nord_alt, (size_t)nnodes * 4)) != cudaSuccess) return e;
+        if ((e = ensure(ctx->nl_ucnt, (size_t)nnodes * 4)) != cudaSuccess) return e;
+        if ((e = ensure(ctx->nl_uoff, (size_t)(nnodes + 1) * 4)) != cudaSuccess) return e;
+        if ((e = ensure(ctx->nl_units, (size_t)max_units * 8)) != cudaSuccess) return e;
+        if ((e = ensure(ctx->nl_inc_m, (size_t)E * 32 * 4)) != cudaSuccess) return e;
+        if ((e = ensure(ctx->nl_inc_e, (size_t)E * 32 * 4)) != cudaSuccess) return e;
+        if ((e = ensure(ctx->nl_slots, (size_t)E * 96 * 8)) != cudaSuccess) return e;
+        if (E > 0) {
+            const int32_t* sidx = ptr<int32_t>(ctx->nl_idx);
+            int64_t* inc0 = ptr<int64_t>(ctx->nl_inc0);
+            k_inc_count<<<grid_for(E, 256), 256, 0, s>>>(list, sidx, E, ptr<int32_t>(ctx->nl_cnt));
+            note_launch();
+            if ((e = launch_scan_i32_to_i64(ptr<int32_t>(ctx->nl_cnt), inc0, E, inc0 + E, s)) != cudaSuccess)
+                return e;
+            if ((e = cudaMemsetAsync(ctx->nl_k0.p, 0, (size_t)nnodes * 4, s)) != cudaSuccess) return e;
+            if ((e = cudaMemsetAsync(ctx->nl_k1.p, 0, (size_t)nnodes * 4, s)) != cudaSuccess) return e;
+            k_leaf_bounds<<<grid_for(E, 256), 256, 0, s>>>(ptr<uint64_t>(ctx->nl_keys), E, ptr<int32_t>(ctx->nl_k0),
+                                                           ptr<int32_t>(ctx->nl_k1));
+            note_launch();
+            k_leaf_units<<<grid_for(nnodes, 256), 256, 0, s>>>(
+                ptr<int4>(ctx->node_topo), nnodes, ptr<int32_t>(ctx->nl_k0), ptr<int32_t>(ctx->nl_k1), inc0,
+                ptr<int64_t>(ctx->nl_ninc0), ptr<int32_t>(ctx->nl_nA), ptr<uint64_t>(ctx->nl_nkey),
+                ptr<int32_t>(ctx->nl_nord));
+            note_launch();
+            if ((e = radix_sort_bits(ptr<uint64_t>(ctx->nl_nkey), ptr<int32_t>(ctx->nl_nord),
+                                     ptr<uint64_t>(ctx->nl_nkey_alt), ptr<int32_t>(ctx->nl_nord_alt),
+                                     ptr<uint32_t>(ctx->nl_hist), nnodes, kLeafKeyBits, s)) != cudaSuccess)
+                return e;
+            k_unit_count<<<grid_for(nnodes, 256), 256, 0, s>>>(ptr<int32_t>(ctx->nl_nord), ptr<int32_t>(ctx->nl_nA),
+                                                               nnodes, ptr<int32_t>(ctx->nl_ucnt));
+            note_launch();
+            int32_t* uoff = ptr<int32_t>(ctx->nl_uoff);
+            if ((e = launch_scan_i32(ptr<int32_t>(ctx->nl_ucnt), uoff, nnodes, uoff + nnodes, s)) != cudaSuccess)
+                return e;
+            k_unit_fill<<<grid_for(nnodes, 256), 256, 0, s>>>(ptr<int32_t>(ctx->nl_nord), ptr<int32_t>(ctx->nl_ucnt),
+                                                              uoff, nnodes, ptr<int2>(ctx->nl_units));
+            note_launch();
+            k_inc_fill<<<grid_for(E * 32, 256), 256, 0, s>>>(list, sidx, ptr<int32_t>(ctx->nl_eb), inc0, E,
+                                                             ptr<int32_t>(ctx->nl_inc_m), ptr<int32_t>(ctx->nl_inc_e));
+            note_launch();
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+        ctx->near_sched_ready = 2;
+    }
+    sc.node_inc0 = ptr<int64_t>(ctx->nl_ninc0);
+    sc.node_A = ptr<int32_t>(ctx->nl_nA);
+    sc.units = ptr<int2>(ctx->nl_units);
+    sc.nunits = ptr<int32_t>(ctx->nl_uoff) + nnodes;
+    sc.inc_m = ptr<int32_t>(ctx->nl_inc_m);
+    sc.inc_e = ptr<int32_t>(ctx->nl_inc_e);
+    sc.slots = ptr<double>(ctx->nl_slots);
+    sc.E = E;
+    sc.max_units = max_units;
+    sc.queue = nullptr;
+    return cudaSuccess;
 }
 
 cudaError_t launch_near(int precision, const double* ts, int64_t M, const int4* topo,
@@ -369,11 +526,10 @@ cudaError_t launch_near(int precision, const double* ts, int64_t M, const int4* 
             k_near_fp64<false><<<grid, kNearWarps * 32, 0, s>>>(ts, M, topo, xs, ws, N, near_off, near_list, u_near,
                                                                 0.0);
     } else if (eps > 0.0) {
-        // the regularized kernels: groups of four (no tuning for this path)
-        return nearpair::run_near_auto<NearOpReg>(ts, nullptr, M, topo, spack, near_off, near_list, u_near, self,
+        return nearpair::run_near_leaf<NearOpReg>(ts, nullptr, M, topo, spack, near_off, near_list, u_near, self,
                                                   (float)e2, sched, s);
     } else {
-        return nearpair::run_near_auto<NearOpU>(ts, nullptr, M, topo, spack, near_off, near_list, u_near, self,
+        return nearpair::run_near_leaf<NearOpU>(ts, nullptr, M, topo, spack, near_off, near_list, u_near, self,
                                                 0.0f, sched, s);
     }
     note_launch();

@@ -72,6 +72,58 @@ struct NearScratch {
     int slot[G * 32];
 };
 
+// The near field of one leaf (sources first .. first + count - 1) at the
+// targets of one or two streams (ta, and tb when two), on the warp's tile:
+// per 32-source tile the packed pair sums of each target, accumulated over
+// the leaf's tiles by compensated FP32 summation (sum, compensation per
+// component) and returned in FP64 as sum less compensation (ra for ta, rb for
+// tb).  guard: a source of the leaf may coincide with a target.  Every
+// schedule of the near field computes a leaf's sums here, so a target's sums
+// do not depend on the schedule.
+template <typename Op>
+__device__ __forceinline__ void leaf_sums(const typename Op::Tgt& ta, const typename Op::Tgt& tb, bool two,
+                                          bool guard, int first, int count, const float4* __restrict__ spack,
+                                          float4* tile, int lane, double (&ra)[3], double (&rb)[3])
+{
+    float sa[3] = {0.f, 0.f, 0.f}, ka[3] = {0.f, 0.f, 0.f}, sb[3] = {0.f, 0.f, 0.f}, kb[3] = {0.f, 0.f, 0.f};
+    for (int base = first; base < first + count; base += 32) {
+        const int cnt = min(32, first + count - base);
+        __syncwarp();
+        stage_pairs(spack, base, cnt, tile, lane);
+        __syncwarp();
+        const int npairs = (cnt + 1) >> 1;
+        float2 axa = make_float2(0.f, 0.f), aya = axa, aza = axa, axb = axa, ayb = axa, azb = axa;
+        if (two && guard) {
+            for (int q = 0; q < npairs; q++) {
+                const float4* tp = tile + q * kPairStride;
+                Op::template terms<true>(ta, tp, axa, aya, aza);
+                Op::template terms<true>(tb, tp, axb, ayb, azb);
+            }
+        } else if (two) {
+            for (int q = 0; q < npairs; q++) {
+                const float4* tp = tile + q * kPairStride;
+                Op::template terms<false>(ta, tp, axa, aya, aza);
+                Op::template terms<false>(tb, tp, axb, ayb, azb);
+            }
+        } else if (guard) {
+            for (int q = 0; q < npairs; q++) Op::template terms<true>(ta, tile + q * kPairStride, axa, aya, aza);
+        } else {
+            for (int q = 0; q < npairs; q++) Op::template terms<false>(ta, tile + q * kPairStride, axa, aya, aza);
+        }
+        kahan_add(sa[0], ka[0], axa.x + axa.y);
+        kahan_add(sa[1], ka[1], aya.x + aya.y);
+        kahan_add(sa[2], ka[2], aza.x + aza.y);
+        kahan_add(sb[0], kb[0], axb.x + axb.y);
+        kahan_add(sb[1], kb[1], ayb.x + ayb.y);
+        kahan_add(sb[2], kb[2], azb.x + azb.y);
+    }
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        ra[k] = (double)sa[k] - (double)ka[k];
+        rb[k] = (double)sb[k] - (double)kb[k];
+    }
+}
+
 // Near field of batches G*B .. G*B+G-1 (the last ones may not exist) on one
 // warp, over the merge of their G near lists (all in tree order, so by the
 // leaf's first source); lane g < G holds the cursor of list g, so the merge
@@ -161,58 +213,16 @@ __device__ inline void near_group(const double* __restrict__ ts, const double* _
             const bool guard = !Op::kUnguarded || !self ||
                                __any_sync(0xffffffffu, (v1 && m1 >= t.x && m1 < (int64_t)t.x + t.y) ||
                                                            (v2 && m2 >= t.x && m2 < (int64_t)t.x + t.y));
-            // per-tile partial sums, accumulated over the leaf's tiles by
-            // compensated FP32 summation (sum, compensation per component)
-            float sa[3] = {0.f, 0.f, 0.f}, ka[3] = {0.f, 0.f, 0.f}, sb[3] = {0.f, 0.f, 0.f},
-                  kb[3] = {0.f, 0.f, 0.f};
-            for (int base = t.x; base < t.x + t.y; base += 32) {
-                const int cnt = min(32, t.x + t.y - base);
-                __syncwarp();
-                stage_pairs(spack, base, cnt, sc.tile, lane);
-                __syncwarp();
-                const int npairs = (cnt + 1) >> 1;
-                float2 axa = make_float2(0.f, 0.f), aya = axa, aza = axa, axb = axa, ayb = axa, azb = axa;
-                if (two && guard) {
-                    for (int q = 0; q < npairs; q++) {
-                        const float4* tp = sc.tile + q * kPairStride;
-                        Op::template terms<true>(ta, tp, axa, aya, aza);
-                        Op::template terms<true>(tb, tp, axb, ayb, azb);
-                    }
-                } else if (two) {
-                    for (int q = 0; q < npairs; q++) {
-                        const float4* tp = sc.tile + q * kPairStride;
-                        Op::template terms<false>(ta, tp, axa, aya, aza);
-                        Op::template terms<false>(tb, tp, axb, ayb, azb);
-                    }
-                } else if (guard) {
-                    for (int q = 0; q < npairs; q++)
-                        Op::template terms<true>(ta, sc.tile + q * kPairStride, axa, aya, aza);
-                } else {
-                    for (int q = 0; q < npairs; q++)
-                        Op::template terms<false>(ta, sc.tile + q * kPairStride, axa, aya, aza);
-                }
-                kahan_add(sa[0], ka[0], axa.x + axa.y);
-                kahan_add(sa[1], ka[1], aya.x + aya.y);
-                kahan_add(sa[2], ka[2], aza.x + aza.y);
-                kahan_add(sb[0], kb[0], axb.x + axb.y);
-                kahan_add(sb[1], kb[1], ayb.x + ayb.y);
-                kahan_add(sb[2], kb[2], azb.x + azb.y);
-            }
-            const double a0 = (double)sa[0] - (double)ka[0], a1 = (double)sa[1] - (double)ka[1],
-                         a2 = (double)sa[2] - (double)ka[2], c0 = (double)sb[0] - (double)kb[0],
-                         c1 = (double)sb[1] - (double)kb[1], c2 = (double)sb[2] - (double)kb[2];
+            double a[3], c[3];
+            leaf_sums<Op>(ta, tb, two, guard, t.x, t.y, spack, sc.tile, lane, a, c);
             // each (batch, lane) target holds one slot per leaf: no two lanes
             // add to the same accumulator here
-            if (v1) {
-                sc.acc[id1 >> 5][0][id1 & 31] += a0;
-                sc.acc[id1 >> 5][1][id1 & 31] += a1;
-                sc.acc[id1 >> 5][2][id1 & 31] += a2;
-            }
-            if (v2) {
-                sc.acc[id2 >> 5][0][id2 & 31] += c0;
-                sc.acc[id2 >> 5][1][id2 & 31] += c1;
-                sc.acc[id2 >> 5][2][id2 & 31] += c2;
-            }
+            if (v1)
+#pragma unroll
+                for (int k = 0; k < 3; k++) sc.acc[id1 >> 5][k][id1 & 31] += a[k];
+            if (v2)
+#pragma unroll
+                for (int k = 0; k < 3; k++) sc.acc[id2 >> 5][k][id2 & 31] += c[k];
         }
         if (match) {
             if (++cur < end) {
@@ -238,120 +248,137 @@ __device__ inline void near_group(const double* __restrict__ ts, const double* _
 }
 
 // ---------------------------------------------------------------------------
-// Scheduling of the groups over a resident grid (the one-system near field and
-// the target side of its adjoint).  A grid one block per SM short of the
-// occupancy limit drains a queue of groups; when the groups outnumber its
-// warps, they are taken in order of decreasing work (k_group_work + radix
-// sort), so each warp drains several and the end of the kernel is made of the
-// smallest ones.  Measured at N = 10^6 (near kernel alone / step): groups of
-// eight at full occupancy 37.4 / 53.0 ms, eight one block short 35.7 / 53.1,
-// four at full occupancy 34.2 / 54.3, four one block short 33.3 / 54.1, four
-// two blocks short 34.4 / 54.4.
+// Leaf-major schedule of the one-system near field and of the target side of
+// its adjoint.  The near entries are sorted by leaf (near_schedule); the
+// targets of all entries of a leaf, its incidences, are packed densely into
+// 32-lane streams, so that only a leaf's last stream is partial, and the
+// units of work, (leaf, pair of streams), are drained by a resident grid in
+// order of decreasing leaf size.  A unit writes each of its targets' leaf sums
+// to the slot of its (entry, lane); k_near_reduce then adds each target's
+// slots in list order, the order in which near_group adds its leaves, so both
+// schedules give the same bits.
+constexpr int kLeafWarps = 4;       // warps per block of k_near_leaf
+constexpr int kLeafFreeBlocks = 1;  // block slots per SM left free (for the far field on the second stream)
 
-constexpr int kQueueWarps = 4;       // warps per block of the queued kernels
-constexpr int kQueueFreeBlocks = 1;  // block slots per SM left free
-
-// Work of each group of G batches, its pair count (over its near entries, the
-// active targets times the leaf size), as a sort key that puts the groups
-// with the most work first; order receives the identity.
-template <int G>
-__global__ void k_group_work(const int64_t* __restrict__ near_off, const ListEntry* __restrict__ near_list,
-                             const int4* __restrict__ topo, int64_t nbatch, int64_t ngroup, uint64_t* __restrict__ keys,
-                             int32_t* __restrict__ order)
+template <typename Op>
+__global__ void __launch_bounds__(kLeafWarps * 32)
+    k_near_leaf(const double* __restrict__ ts, const double* __restrict__ gs, int64_t M,
+                const int4* __restrict__ topo, const float4* __restrict__ spack, const int2* __restrict__ units,
+                const int32_t* __restrict__ nunits, const int64_t* __restrict__ node_inc0,
+                const int32_t* __restrict__ node_A, const int32_t* __restrict__ inc_m,
+                const int32_t* __restrict__ inc_e, double* __restrict__ slots, int self, float prm,
+                unsigned* __restrict__ queue)
 {
-    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (g >= ngroup) return;
-    const int64_t b0 = g * G, b1 = min(nbatch, b0 + G);
-    uint64_t w = 0;
-    for (int64_t e = near_off[b0]; e < near_off[b1]; e++) {
-        const ListEntry le = near_list[e];
-        w += (uint64_t)__popc(le.mask) * (uint64_t)topo[le.node].y;
-    }
-    keys[g] = 0xffffffffull - (w < 0xffffffffull ? w : 0xffffffffull);
-    order[g] = (int32_t)g;
-}
-
-// Each warp takes the next group from the queue: order[i], or i when order is
-// NULL (the grid holds every group at once).
-template <int G, typename Op>
-__global__ void __launch_bounds__(kQueueWarps * 32)
-    k_near_queue(const double* __restrict__ ts, const double* __restrict__ gs, int64_t M,
-                 const int4* __restrict__ topo, const float4* __restrict__ spack, const int64_t* __restrict__ near_off,
-                 const ListEntry* __restrict__ near_list, double* __restrict__ out, int self, float prm,
-                 const int32_t* __restrict__ order, int64_t ngroup, unsigned* __restrict__ queue)
-{
-    __shared__ NearScratch<G> sc[kQueueWarps];
+    __shared__ float4 tile[kLeafWarps][kTileFloat4];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned nu = (unsigned)*nunits;
     for (;;) {
         unsigned i = 0;
         if (lane == 0) i = atomicAdd(queue, 1u);
         i = __shfl_sync(0xffffffffu, i, 0);
-        if ((int64_t)i >= ngroup) break;
-        near_group<G, Op>(ts, gs, M, topo, spack, near_off, near_list, out, order ? order[i] : i, self, prm, sc[w],
-                          lane);
+        if (i >= nu) break;
+        const int2 un = units[i];
+        const int node = un.x;
+        const int64_t I0 = node_inc0[node];
+        const int A = node_A[node];
+        const int k1 = 64 * un.y + lane, k2 = k1 + 32;
+        const bool two = 64 * un.y + 32 < A;
+        const bool v1 = k1 < A, v2 = k2 < A;
+        const int m1 = v1 ? inc_m[I0 + k1] : 0, m2 = v2 ? inc_m[I0 + k2] : 0;
+        const typename Op::Tgt ta = Op::load(ts, gs, M, m1, v1, prm);
+        const typename Op::Tgt tb = Op::load(ts, gs, M, m2, v2, prm);
+        const int4 t = topo[node];
+        // as in near_group: with targets = sources only a target inside the
+        // leaf's own range can coincide with one of its sources
+        const bool guard = !Op::kUnguarded || !self ||
+                           __any_sync(0xffffffffu, (v1 && m1 >= t.x && m1 < t.x + t.y) ||
+                                                       (v2 && m2 >= t.x && m2 < t.x + t.y));
+        double a[3], c[3];
+        leaf_sums<Op>(ta, tb, two, guard, t.x, t.y, spack, tile[w], lane, a, c);
+        // slot of (entry e, component k, lane l): 96 e + 32 k + l
+        if (v1) {
+            double* q = slots + (int64_t)inc_e[I0 + k1] * 96 + (m1 & 31);
+            q[0] = a[0], q[32] = a[1], q[64] = a[2];
+        }
+        if (v2) {
+            double* q = slots + (int64_t)inc_e[I0 + k2] * 96 + (m2 & 31);
+            q[0] = c[0], q[32] = c[1], q[64] = c[2];
+        }
     }
 }
 
-// blocks of k_near_queue<G, Op> the grid takes: the occupancy limit less
-// kQueueFreeBlocks per SM, times the SMs
-template <int G, typename Op>
-int64_t queue_resident_blocks()
+// One warp per batch: each lane adds its target's slots over the batch's near
+// entries, in list order, starting from zero, and stores (or, kAdd, adds) the
+// sum.
+template <bool kAdd>
+__global__ void k_near_reduce(const int64_t* __restrict__ near_off, const ListEntry* __restrict__ near_list,
+                              int64_t M, const double* __restrict__ slots, double* __restrict__ out)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t b = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (b >= (M + kBatch - 1) / kBatch) return;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    const int64_t e1 = near_off[b + 1];
+    for (int64_t e = near_off[b]; e < e1; e++)
+        if ((near_list[e].mask >> lane) & 1u) {
+            const double* q = slots + e * 96 + lane;
+            a0 += q[0];
+            a1 += q[32];
+            a2 += q[64];
+        }
+    const int64_t m = b * kBatch + lane;
+    if (m < M) {
+        if (kAdd) {
+            out[m] += a0;
+            out[M + m] += a1;
+            out[2 * M + m] += a2;
+        } else {
+            out[m] = a0;
+            out[M + m] = a1;
+            out[2 * M + m] = a2;
+        }
+    }
+}
+
+// blocks of k_near_leaf<Op> the grid takes: the occupancy limit less
+// kLeafFreeBlocks per SM, times the SMs
+template <typename Op>
+int64_t leaf_resident_blocks()
 {
     static int ps = 0, sms = 0;
     if (ps == 0) {
         int dev = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, k_near_queue<G, Op>, kQueueWarps * 32, 0) !=
-                cudaSuccess ||
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, k_near_leaf<Op>, kLeafWarps * 32, 0) != cudaSuccess ||
             ps < 1)
             ps = 1;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     }
-    return (int64_t)(ps > kQueueFreeBlocks ? ps - kQueueFreeBlocks : 1) * (sms > 0 ? sms : 1);
+    return (int64_t)(ps > kLeafFreeBlocks ? ps - kLeafFreeBlocks : 1) * (sms > 0 ? sms : 1);
 }
 
-template <int G, typename Op>
-cudaError_t run_near_queue(const double* ts, const double* gs, int64_t M, const int4* topo, const float4* spack,
-                           const int64_t* near_off, const ListEntry* near_list, double* out, int self, float prm,
-                           const NearSched& sc, cudaStream_t s)
-{
-    const int64_t nbatch = (M + kBatch - 1) / kBatch;
-    const int64_t ngroup = (nbatch + G - 1) / G;
-    const int64_t need = (ngroup + kQueueWarps - 1) / kQueueWarps;
-    const int64_t resident = queue_resident_blocks<G, Op>();
-    const unsigned grid = (unsigned)(need < resident ? need : resident);
-    // the order matters only when some warps take more than one group
-    const int32_t* order = nullptr;
-    if (need > resident) {
-        k_group_work<G><<<(unsigned)((ngroup + 255) / 256), 256, 0, s>>>(near_off, near_list, topo, nbatch, ngroup,
-                                                                        sc.keys, sc.order);
-        note_launch();
-        cudaError_t e = radix_sort_bits(sc.keys, sc.order, sc.keys_alt, sc.order_alt, sc.hist, ngroup, 32, s);
-        if (e != cudaSuccess) return e;
-        order = sc.order;
-    }
-    cudaError_t e = cudaMemsetAsync(sc.queue, 0, sizeof(unsigned), s);
-    if (e != cudaSuccess) return e;
-    k_near_queue<G, Op><<<grid, kQueueWarps * 32, 0, s>>>(ts, gs, M, topo, spack, near_off, near_list, out, self, prm,
-                                                           order, ngroup, sc.queue);
-    note_launch();
-    return cudaGetLastError();
-}
-
-// Groups of four batches when there are at least kQueueMinGroups of them per
-// warp of the grid, else groups of two (more, smaller groups, so that the
-// queue can still balance the warps of a smaller or more uneven problem).
-constexpr int kQueueMinGroups = 2;
-
+// The near field of Op over the schedule sc (near_schedule): the units, then
+// the sums per target into out.
 template <typename Op>
-cudaError_t run_near_auto(const double* ts, const double* gs, int64_t M, const int4* topo, const float4* spack,
+cudaError_t run_near_leaf(const double* ts, const double* gs, int64_t M, const int4* topo, const float4* spack,
                           const int64_t* near_off, const ListEntry* near_list, double* out, int self, float prm,
                           const NearSched& sc, cudaStream_t s)
 {
+    if (sc.E > 0) {
+        // at most one unit per warp of the grid when every entry had its own unit
+        const int64_t resident = leaf_resident_blocks<Op>();
+        const int64_t need = (sc.max_units + kLeafWarps - 1) / kLeafWarps;
+        const unsigned grid = (unsigned)(need < resident ? (need > 0 ? need : 1) : resident);
+        cudaError_t e = cudaMemsetAsync(sc.queue, 0, sizeof(unsigned), s);
+        if (e != cudaSuccess) return e;
+        k_near_leaf<Op><<<grid, kLeafWarps * 32, 0, s>>>(ts, gs, M, topo, spack, sc.units, sc.nunits, sc.node_inc0,
+                                                         sc.node_A, sc.inc_m, sc.inc_e, sc.slots, self, prm, sc.queue);
+        note_launch();
+    }
     const int64_t nbatch = (M + kBatch - 1) / kBatch;
-    if ((nbatch + 3) / 4 >= kQueueMinGroups * kQueueWarps * queue_resident_blocks<4, Op>())
-        return run_near_queue<4, Op>(ts, gs, M, topo, spack, near_off, near_list, out, self, prm, sc, s);
-    return run_near_queue<2, Op>(ts, gs, M, topo, spack, near_off, near_list, out, self, prm, sc, s);
+    k_near_reduce<Op::kAdd><<<(unsigned)((nbatch + 7) / 8), 256, 0, s>>>(near_off, near_list, M, sc.slots, out);
+    note_launch();
+    return cudaGetLastError();
 }
 
 }  // namespace nearpair
