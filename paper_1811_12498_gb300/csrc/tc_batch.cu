@@ -5,11 +5,13 @@
 // ordinary build and moments.  tc_batch_eval prepares every system's
 // interaction lists, then runs the far field, near field and the final sum of
 // ALL systems as one far and one near persistent kernel (each warp takes
-// (system, batch) items from a device counter until the queue is empty) plus
-// one batched finalize, captured once into a CUDA graph and replayed.  The
-// launch shapes of the two persistent kernels come from a small autotuner
-// that times candidate shapes on the first evaluation of each (order,
-// precision) and keeps the fastest.
+// items from a device counter until the queue is empty: (system, batch) items
+// in the far field, the units of the systems' leaf-major schedules in the
+// near field, whose builds run beside the far field on a second stream) plus
+// the batched sums and finalize, captured once into a CUDA graph and
+// replayed.  The launch shapes of the two persistent kernels come from a
+// small autotuner that times candidate shapes on the first evaluation of each
+// (order, precision) and keeps the fastest.
 #include <algorithm>
 #include <new>
 
@@ -60,10 +62,16 @@ struct tc_batch {
     int64_t ntot = 0;
     std::vector<int64_t> off;          // nsys + 1 host offsets
     std::vector<tc_ctx*> ctx;
+    // each system's context works on a stream of its own, forked from and
+    // joined back to the batch's stream, so that the small launches of many
+    // systems' preparation run side by side
+    std::vector<cudaStream_t> sys_stream;
+    std::vector<cudaEvent_t> sys_ev;
     DevBuf d_off;                      // device copy of off
     DevBuf xseg, fseg, hseg, nuseg;    // per-system copies
     DevBuf desc;                       // SysDesc[nsys]
-    DevBuf item_off;                   // far item offsets (nsys + 1), then near item offsets (nsys + 1)
+    DevBuf item_off;                   // far item offsets (nsys + 1), then batch offsets (nsys + 1)
+    DevBuf unit_off;                   // the systems' first near-field units (nsys + 1)
     DevBuf counters;                   // two queue counters
     std::vector<SysDesc> hdesc;
     std::vector<int64_t> hitem;
@@ -84,6 +92,9 @@ struct tc_batch {
     // caller's stream by events
     cudaStream_t cap = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    // second stream of the compute phase: the near-field schedules' builds
+    cudaStream_t cap2 = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 static tc_status bfail(tc_batch* b, tc_status st, const char* msg, cudaError_t e = cudaSuccess)
@@ -123,9 +134,43 @@ static void free_systems(tc_batch* b)
 {
     for (tc_ctx* c : b->ctx) tc_destroy(c);
     b->ctx.clear();
+    for (cudaStream_t q : b->sys_stream) cudaStreamDestroy(q);
+    for (cudaEvent_t e : b->sys_ev) cudaEventDestroy(e);
+    b->sys_stream.clear();
+    b->sys_ev.clear();
 }
 
-// far + near + finalize of all systems (stream-ordered; capturable)
+// order systems [s0, s1)'s streams after the work enqueued so far on st
+static cudaError_t fork_systems(tc_batch* b, cudaStream_t st, int s0, int s1)
+{
+    cudaError_t e = cudaEventRecord(b->ev_in, st);
+    for (int s = s0; s < s1 && e == cudaSuccess; s++) e = cudaStreamWaitEvent(b->sys_stream[s], b->ev_in, 0);
+    return e;
+}
+
+// order st after everything enqueued on systems [s0, s1)'s streams (their
+// moment passes included)
+static cudaError_t join_systems(tc_batch* b, cudaStream_t st, int s0, int s1)
+{
+    cudaError_t e = cudaSuccess;
+    for (int s = s0; s < s1 && e == cudaSuccess; s++) {
+        e = join_moments(b->ctx[s]);
+        if (e == cudaSuccess) e = cudaEventRecord(b->sys_ev[s], b->sys_stream[s]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, b->sys_ev[s], 0);
+    }
+    return e;
+}
+
+// the near-field schedules of all systems (mixed precision; no allocation)
+static tc_status build_schedules(tc_batch* b, cudaStream_t s)
+{
+    for (int i = 0; i < b->nsys; i++) TB_CK(near_schedule_build(b->ctx[i], 1, s), "near schedule");
+    return TC_OK;
+}
+
+// far + near + finalize of all systems (stream-ordered; capturable).  In
+// mixed precision the near field runs on the second stream, after its
+// schedules' builds and beside the far field, as in tc_eval.
 static tc_status launch_compute(tc_batch* b, const Shape& sh, int p, int64_t nitems, int64_t nnear, double* u,
                                 cudaStream_t s)
 {
@@ -133,12 +178,25 @@ static tc_status launch_compute(tc_batch* b, const Shape& sh, int p, int64_t nit
     TB_CK(cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), s), "reset queue");
     const SysDesc* d = ptr<SysDesc>(b->desc);
     const int64_t* io = ptr<int64_t>(b->item_off);
+    const bool mixed = b->cfg.precision == TC_MIXED;
+    cudaStream_t sn = s;
+    if (mixed) {
+        sn = b->cap2;
+        TB_CK(cudaEventRecord(b->ev_fork, s), "fork");
+        TB_CK(cudaStreamWaitEvent(sn, b->ev_fork, 0), "fork");
+        tc_status r = build_schedules(b, sn);
+        if (r != TC_OK) return r;
+    }
     TB_CK(launch_far_batched(b->cfg.precision, b->cfg.rec64, d, b->nsys, io, nitems, p, cnt, sh.far_warps,
                              sh.far_blocks, s),
           "batched far field");
-    TB_CK(launch_near_batched(b->cfg.precision, d, b->nsys, io + b->nsys + 1, nnear, cnt + 1, sh.near_warps,
-                              sh.near_blocks, s),
+    TB_CK(launch_near_batched(b->cfg.precision, d, b->nsys, io + b->nsys + 1, nnear, ptr<int64_t>(b->unit_off),
+                              cnt + 1, sh.near_warps, sh.near_blocks, sn),
           "batched near field");
+    if (mixed) {
+        TB_CK(cudaEventRecord(b->ev_join, sn), "join");
+        TB_CK(cudaStreamWaitEvent(s, b->ev_join, 0), "join");
+    }
     TB_CK(launch_finalize_batched(d, b->nsys, ptr<int64_t>(b->d_off), b->ntot, u, b->ntot, s), "batched finalize");
     return TC_OK;
 }
@@ -195,8 +253,8 @@ static tc_status tune(tc_batch* b, int p, int64_t nitems, int64_t nnear, double*
             const int blocks = nb ? nb * sms : 0;
             cudaMemsetAsync(cnt + 1, 0, sizeof(unsigned long long), s);
             cudaEventRecord(e0, s);
-            cudaError_t e =
-                launch_near_batched(b->cfg.precision, d, b->nsys, io + b->nsys + 1, nnear, cnt + 1, nw, blocks, s);
+            cudaError_t e = launch_near_batched(b->cfg.precision, d, b->nsys, io + b->nsys + 1, nnear,
+                                                ptr<int64_t>(b->unit_off), cnt + 1, nw, blocks, s);
             cudaEventRecord(e1, s);
             if (e != cudaSuccess) {
                 cudaGetLastError();
@@ -252,6 +310,9 @@ tc_status tc_batch_create(tc_batch** out, const tc_config* cfg)
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap2, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         tc_batch_destroy(b);
         return fail(nullptr, TC_ECUDA, "tc_batch_create: %s", cudaGetErrorString(e));
@@ -266,11 +327,15 @@ tc_status tc_batch_destroy(tc_batch* b)
     cudaStreamSynchronize((cudaStream_t)b->cfg.stream);
     drop_graph(b);
     free_systems(b);
-    DevBuf* bufs[] = {&b->d_off, &b->xseg, &b->fseg, &b->hseg, &b->nuseg, &b->desc, &b->item_off, &b->counters};
+    DevBuf* bufs[] = {&b->d_off, &b->xseg,     &b->fseg,     &b->hseg,    &b->nuseg,
+                      &b->desc,  &b->item_off, &b->unit_off, &b->counters};
     for (DevBuf* d : bufs) release(*d);
     if (b->cap) cudaStreamDestroy(b->cap);
+    if (b->cap2) cudaStreamDestroy(b->cap2);
     if (b->ev_in) cudaEventDestroy(b->ev_in);
     if (b->ev_out) cudaEventDestroy(b->ev_out);
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->ev_join) cudaEventDestroy(b->ev_join);
     delete b;
     return TC_OK;
 }
@@ -299,8 +364,20 @@ tc_status tc_batch_build(tc_batch* b, const double* x, int32_t nsys, const int64
     if ((int)b->ctx.size() != nsys) {
         free_systems(b);
         for (int s = 0; s < nsys; s++) {
+            cudaStream_t q = nullptr;
+            cudaEvent_t ev = nullptr;
+            cudaError_t e = cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking);
+            if (e == cudaSuccess) b->sys_stream.push_back(q);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+            if (e == cudaSuccess) b->sys_ev.push_back(ev);
+            if (e != cudaSuccess) {
+                free_systems(b);
+                return bfail(b, TC_ECUDA, "system stream", e);
+            }
+            tc_config cs = b->cfg;
+            cs.stream = q;
             tc_ctx* c = nullptr;
-            tc_status r = tc_create(&c, &b->cfg);
+            tc_status r = tc_create(&c, &cs);
             if (r != TC_OK) {
                 free_systems(b);
                 return bfail(b, r, tc_last_error(nullptr));
@@ -318,10 +395,12 @@ tc_status tc_batch_build(tc_batch* b, const double* x, int32_t nsys, const int64
                                                               ptr<double>(b->xseg));
     note_launch();
     TB_CK(cudaGetLastError(), "split positions");
+    TB_CK(fork_systems(b, st, 0, nsys), "fork systems");
     for (int s = 0; s < nsys; s++) {
         tc_status r = tc_build(b->ctx[s], ptr<double>(b->xseg) + 3 * offsets[s], offsets[s + 1] - offsets[s], N0);
         if (r != TC_OK) return from_ctx(b, b->ctx[s], r, s);
     }
+    TB_CK(join_systems(b, st, 0, nsys), "join systems");
     b->tuned_p = -1;
     return TC_OK;
 }
@@ -341,12 +420,14 @@ tc_status tc_batch_moments(tc_batch* b, const double* f, const double* h, const 
         note_launch();
     }
     TB_CK(cudaGetLastError(), "split weights");
+    TB_CK(fork_systems(b, st, 0, b->nsys), "fork systems");
     for (int s = 0; s < b->nsys; s++) {
         const int64_t o = 3 * b->off[s];
         tc_status r = tc_moments(b->ctx[s], ptr<double>(b->fseg) + o, ptr<double>(b->hseg) + o,
                                  ptr<double>(b->nuseg) + o, p);
         if (r != TC_OK) return from_ctx(b, b->ctx[s], r, s);
     }
+    TB_CK(join_systems(b, st, 0, b->nsys), "join systems");
     return TC_OK;
 }
 
@@ -356,21 +437,27 @@ tc_status tc_batch_eval(tc_batch* b, double theta, int32_t p, double* u)
     if (b->nsys < 1) return bfail(b, TC_ESTATE, "tc_batch_eval: call tc_batch_build first");
     if (!u) return bfail(b, TC_EINVAL, "tc_batch_eval: u is NULL");
     cudaStream_t st = (cudaStream_t)b->cfg.stream;
-    // 1. every system's tables and interaction lists: the counting passes of
-    // all systems, one synchronisation for all their list sizes, then the
-    // write passes and tables
+    // 1. every system's tables and interaction lists, each on its system's
+    // stream: the counting passes of all systems, one wait for all their
+    // list sizes, then the write passes and tables
+    TB_CK(fork_systems(b, st, 0, b->nsys), "fork systems");
     for (int s = 0; s < b->nsys; s++) {
         tc_status r = eval_prepare_count(b->ctx[s], nullptr, b->off[s + 1] - b->off[s], theta, p);
         if (r != TC_OK) return from_ctx(b, b->ctx[s], r, s);
     }
-    TB_CK(cudaStreamSynchronize(st), "list sizes");
+    for (int s = 0; s < b->nsys; s++) TB_CK(cudaStreamSynchronize(b->sys_stream[s]), "list sizes");
     for (int s = 0; s < b->nsys; s++) {
         tc_status r = eval_prepare_finish(b->ctx[s]);
         if (r != TC_OK) return from_ctx(b, b->ctx[s], r, s);
-        // the persistent kernels read every system's tables: join the
-        // system's second stream (moments, tables) into its first
-        TB_CK(join_moments(b->ctx[s]), "join moments");
+        // the buffers of its near-field schedule (built in the compute phase)
+        if (b->cfg.precision == TC_MIXED) {
+            cudaError_t e = near_schedule_alloc(b->ctx[s], 1);
+            if (e != cudaSuccess) return bfail(b, TC_ECUDA, "near schedule", e);
+            b->ctx[s]->near_sched_ready = 0;  // its work is enqueued by the batch
+        }
     }
+    // the persistent kernels read every system's lists and tables
+    TB_CK(join_systems(b, st, 0, b->nsys), "join systems");
     // 2. descriptors and the item numbering
     b->hdesc.resize(b->nsys);
     b->hitem.assign(2 * (b->nsys + 1), 0);
@@ -397,13 +484,24 @@ tc_status tc_batch_eval(tc_batch* b, double theta, int32_t p, double* u)
         d.u_near = ptr<double>(c->u_near);
         d.tperm = ptr<int32_t>(c->perm);
         d.out_off = b->off[s];
+        const NearSched sc = near_schedule_desc(c);
+        d.units = sc.units;
+        d.nunits = sc.nunits;
+        d.node_inc0 = sc.node_inc0;
+        d.node_A = sc.node_A;
+        d.inc_m = sc.inc_m;
+        d.inc_e = sc.inc_e;
+        d.slots = sc.slots;
+        d.near_entries = c->near_entries;
+        d.nnodes = c->nnodes;
         const int64_t nb = (c->M + kBatch - 1) / kBatch;
         b->hitem[s + 1] = b->hitem[s] + (b->cfg.precision == TC_FP64 ? nb : (nb + 1) / 2);
-        hnear[s + 1] = hnear[s] + (b->cfg.precision == TC_FP64 ? nb : (nb + kNearGroupBatches - 1) / kNearGroupBatches);
+        hnear[s + 1] = hnear[s] + nb;
     }
     const int64_t nitems = b->hitem[b->nsys], nnear = hnear[b->nsys];
     TB_CK(ensure(b->desc, sizeof(SysDesc) * b->nsys), "alloc descriptors");
     TB_CK(ensure(b->item_off, (size_t)(b->nsys + 1) * 16), "alloc items");
+    TB_CK(ensure(b->unit_off, (size_t)(b->nsys + 1) * 8), "alloc units");
     TB_CK(cudaMemcpyAsync(b->desc.p, b->hdesc.data(), sizeof(SysDesc) * b->nsys, cudaMemcpyHostToDevice, st),
           "copy descriptors");
     TB_CK(cudaMemcpyAsync(b->item_off.p, b->hitem.data(), (size_t)(b->nsys + 1) * 16, cudaMemcpyHostToDevice, st),
@@ -411,6 +509,11 @@ tc_status tc_batch_eval(tc_batch* b, double theta, int32_t p, double* u)
     TB_CK(cudaStreamSynchronize(st), "descriptor sync");  // host arrays are reused next call
     // 3. launch shapes
     if (b->autotune && b->tuned_p != p) {
+        // the near kernel reads the schedules: build them for the timing runs
+        if (b->cfg.precision == TC_MIXED) {
+            tc_status r = build_schedules(b, st);
+            if (r != TC_OK) return r;
+        }
         tc_status r = tune(b, p, nitems, nnear, u);
         if (r != TC_OK) return r;
     }
@@ -454,9 +557,13 @@ tc_status tc_batch_eval_separate(tc_batch* b, double theta, int32_t p, double* c
     if (!b) return fail(nullptr, TC_EINVAL, "tc_batch_eval_separate: batch is NULL");
     if (b->nsys < 1) return bfail(b, TC_ESTATE, "tc_batch_eval_separate: call tc_batch_build first");
     if (!u_sys) return bfail(b, TC_EINVAL, "tc_batch_eval_separate: u is NULL");
+    // one system after the other, each ordered after the last on the batch's stream
+    cudaStream_t st = (cudaStream_t)b->cfg.stream;
     for (int s = 0; s < b->nsys; s++) {
+        TB_CK(fork_systems(b, st, s, s + 1), "fork system");
         tc_status r = tc_eval(b->ctx[s], nullptr, b->off[s + 1] - b->off[s], theta, p, u_sys[s]);
         if (r != TC_OK) return from_ctx(b, b->ctx[s], r, s);
+        TB_CK(join_systems(b, st, s, s + 1), "join system");
     }
     return TC_OK;
 }

@@ -18,7 +18,6 @@ constexpr int kMaxDepth = 21;   // 21-bit quantised coordinates, 63-bit Morton k
 constexpr int kPMax = 12;       // largest Taylor order accepted
 constexpr int kQMax = kPMax + 2;  // far field needs Coulomb coefficients to p+2
 constexpr int kBatch = 32;      // targets per interaction list (one warp)
-constexpr int kNearGroupBatches = 4;  // batches per warp in the mixed-precision near kernels
 // traversal stack: a preorder walk keeps at most 7 siblings per level plus
 // the children of the deepest node, 7 * kMaxDepth + 8 = 155 entries, so the
 // kernels' bound check on this size is a guard that no tree of this library
@@ -105,6 +104,16 @@ struct SysDesc {
     double* u_near;
     const int32_t* tperm;      // sorted target -> caller's target index
     int64_t out_off;           // first column of this system in the batched output
+    // leaf-major near-field schedule (mixed precision; NearSched)
+    const int2* units;
+    const int32_t* nunits;
+    const int64_t* node_inc0;
+    const int32_t* node_A;
+    const int32_t* inc_m;
+    const int32_t* inc_e;
+    double* slots;
+    int64_t near_entries;      // sizes the schedule's work was enqueued for
+    int64_t nnodes;
 };
 
 }  // namespace tc
@@ -359,8 +368,19 @@ struct NearSched {
 // Build the schedule for the lists of the last tc_eval, unless built already;
 // full = 0: only sort the near entries by leaf (nl_keys, nl_idx, nl_eb).
 cudaError_t near_schedule(tc_ctx* ctx, int full, NearSched& sc, cudaStream_t s);
-cudaError_t launch_near_batched(int precision, const SysDesc* sys, int nsys, const int64_t* item_off, int64_t nitems,
-                                unsigned long long* counter, int warps_per_block, int blocks, cudaStream_t s);
+// Its two halves, for a caller that captures the work in a graph: the
+// buffers (host side, nothing enqueued), then the work (no allocation).
+cudaError_t near_schedule_alloc(tc_ctx* ctx, int full);
+cudaError_t near_schedule_build(tc_ctx* ctx, int full, cudaStream_t s);
+NearSched near_schedule_desc(tc_ctx* ctx);
+// Near field of many systems: FP64, one persistent kernel over the (system,
+// batch) items; mixed, the systems' first units (unit_off, nsys + 1, written
+// here), one persistent kernel over all units of their schedules (built
+// beforehand), and the sums per target of every system.  batch_off: nsys + 1
+// offsets of the systems' batches, nbatches in all.
+cudaError_t launch_near_batched(int precision, const SysDesc* sys, int nsys, const int64_t* batch_off,
+                                int64_t nbatches, int64_t* unit_off, unsigned long long* counter, int warps_per_block,
+                                int blocks, cudaStream_t s);
 cudaError_t launch_finalize_batched(const SysDesc* sys, int nsys, const int64_t* moff, int64_t mtotal, double* u,
                                     int64_t ntot, cudaStream_t s);
 cudaError_t launch_near(int precision, const double* ts, int64_t M, const int4* topo,

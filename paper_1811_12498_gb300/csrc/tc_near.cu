@@ -11,14 +11,14 @@
 // for close pairs; pair terms are FP32; the 32-source tiles' partial sums of
 // a leaf are accumulated by compensated (Kahan) FP32 summation and each
 // leaf's sum is added to an FP64 per-target accumulator (an FP64 addition per
-// tile stalled every tile's end on the slow FP64 pipe).  One warp handles a
-// group of four consecutive batches and walks the merge of their near lists
-// (all in tree order, i.e. by the leaf's first source); for each leaf the
-// targets that need it
-// are packed densely into 32-lane streams, and two streams share every staged
-// tile, so every broadcast source value feeds two targets.  The tile holds the
-// sources in pairs, field by field ((y_2q.f, y_2q+1.f) adjacent), and the
-// pair terms run on packed FP32x2 arithmetic, two sources per instruction.
+// tile stalled every tile's end on the slow FP64 pipe).  Work is scheduled
+// leaf by leaf (tc_nearpair.cuh): the near entries are sorted by leaf, the
+// targets that need a leaf are packed densely into 32-lane streams, and two
+// streams share every staged tile, so every broadcast source value feeds two
+// targets.  The tile holds the sources in pairs, field by field
+// ((y_2q.f, y_2q+1.f) adjacent), and the pair terms run on packed FP32x2
+// arithmetic, two sources per instruction.  Each leaf's sums go to a slot
+// per (near entry, lane), added per target in list order by a second kernel.
 //
 // FP64 mode computes everything in FP64, one batch per warp.
 #include <algorithm>
@@ -37,7 +37,6 @@ constexpr int kNearMaxWarps = 8;  // largest block the batched kernel accepts
 // in tc_nearpair.cuh)
 
 using nearpair::sub2;
-using nearpair::NearScratch;
 using nearpair::kPairStride;
 using nearpair::kTileFloat4;
 
@@ -264,41 +263,82 @@ __global__ void __launch_bounds__(kNearWarps * 32)
     near_batch_fp64<kReg>(ts, M, topo, xs, ws, N, near_off, near_list, u_near, b, tile[w], lane, e2);
 }
 
-// Persistent near-field kernel over many systems (see k_far32_batched).  An
-// item is a batch in FP64 mode and a group of four batches in mixed
-// precision (item_off counts accordingly).
-template <bool kFp64>
-__global__ void __launch_bounds__(kNearMaxWarps * 32)
-    k_near_batched(const SysDesc* __restrict__ sys, int nsys, const int64_t* __restrict__ item_off, int64_t nitems,
-                   unsigned long long* __restrict__ counter)
+// system of a global item: the largest s with off[s] <= item (off: the
+// systems' nsys + 1 first items; systems without items are passed over)
+__device__ __forceinline__ int find_system(const int64_t* __restrict__ off, int nsys, int64_t item)
 {
-    constexpr int kTileBytes = 12 * 32 * 8 > (int)sizeof(NearScratch<kNearGroupBatches>)
-                                   ? 12 * 32 * 8
-                                   : (int)sizeof(NearScratch<kNearGroupBatches>);
-    __shared__ __align__(16) double tile[kNearMaxWarps][kTileBytes / 8];
+    int lo = 0, hi = nsys;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (off[mid] <= item)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+// Persistent FP64 near-field kernel over many systems (see k_far32_batched):
+// an item is a (system, batch).
+__global__ void __launch_bounds__(kNearMaxWarps * 32)
+    k_near_batched_fp64(const SysDesc* __restrict__ sys, int nsys, const int64_t* __restrict__ item_off,
+                        int64_t nitems, unsigned long long* __restrict__ counter)
+{
+    __shared__ __align__(16) double tile[kNearMaxWarps][12 * 32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (;;) {
         unsigned long long item = 0;
         if (lane == 0) item = atomicAdd(counter, 1ull);
         item = __shfl_sync(0xffffffffu, item, 0);
         if ((int64_t)item >= nitems) break;
-        int lo = 0, hi = nsys;
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (item_off[mid] <= (int64_t)item)
-                lo = mid;
-            else
-                hi = mid;
-        }
-        const SysDesc& d = sys[lo];
-        const int64_t b = (int64_t)item - item_off[lo];
-        if (kFp64)
-            near_batch_fp64(d.ts, d.M, d.topo, d.xs, d.ws, d.N, d.near_off, d.near_list, d.u_near, b, tile[w], lane);
-        else
-            nearpair::near_group<kNearGroupBatches, NearOpU>(
-                d.ts, nullptr, d.M, d.topo, d.spack, d.near_off, d.near_list, d.u_near, b, 1, 0.0f,
-                *reinterpret_cast<NearScratch<kNearGroupBatches>*>(tile[w]), lane);
+        const int s = find_system(item_off, nsys, (int64_t)item);
+        const SysDesc& d = sys[s];
+        near_batch_fp64(d.ts, d.M, d.topo, d.xs, d.ws, d.N, d.near_off, d.near_list, d.u_near,
+                        (int64_t)item - item_off[s], tile[w], lane);
     }
+}
+
+// first unit of each system's schedule (one thread; nsys + 1 offsets)
+__global__ void k_unit_offsets(const SysDesc* __restrict__ sys, int nsys, int64_t* __restrict__ uoff)
+{
+    int64_t run = 0;
+    for (int s = 0; s < nsys; s++) {
+        uoff[s] = run;
+        run += *sys[s].nunits;
+    }
+    uoff[nsys] = run;
+}
+
+// Persistent leaf-major near field over the units of many systems' schedules
+// (mixed precision; targets = sources in every system).
+__global__ void __launch_bounds__(kNearMaxWarps * 32)
+    k_near_leaf_batched(const SysDesc* __restrict__ sys, int nsys, const int64_t* __restrict__ uoff,
+                        unsigned long long* __restrict__ counter)
+{
+    __shared__ float4 tile[kNearMaxWarps][kTileFloat4];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t nitems = uoff[nsys];
+    for (;;) {
+        unsigned long long item = 0;
+        if (lane == 0) item = atomicAdd(counter, 1ull);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if ((int64_t)item >= nitems) break;
+        const int s = find_system(uoff, nsys, (int64_t)item);
+        const SysDesc& d = sys[s];
+        nearpair::leaf_unit<NearOpU>(d.ts, nullptr, d.M, d.topo, d.spack, d.units, d.node_inc0, d.node_A, d.inc_m,
+                                     d.inc_e, d.slots, 1, 0.0f, (int64_t)item - uoff[s], tile[w], lane);
+    }
+}
+
+// the sums per target of every system: one warp per (system, batch)
+__global__ void k_near_reduce_batched(const SysDesc* __restrict__ sys, int nsys, const int64_t* __restrict__ boff,
+                                      int64_t nbatches)
+{
+    const int64_t item = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (item >= nbatches) return;
+    const int s = find_system(boff, nsys, item);
+    const SysDesc& d = sys[s];
+    nearpair::reduce_batch<false>(d.near_off, d.near_list, d.M, d.slots, d.u_near, item - boff[s], threadIdx.x & 31);
 }
 
 __global__ void k_finalize(const double* __restrict__ uf, const double* __restrict__ un,
@@ -427,86 +467,108 @@ __global__ void k_inc_fill(const ListEntry* __restrict__ list, const int32_t* __
 
 }  // namespace
 
-cudaError_t near_schedule(tc_ctx* ctx, int full, NearSched& sc, cudaStream_t s)
+// bound on the units of a schedule: sum over leaves of ceil(A / 64) <= 32 E / 64 + the leaves
+static int64_t schedule_max_units(const tc_ctx* ctx) { return ctx->near_entries / 2 + ctx->nnodes + 1; }
+
+cudaError_t near_schedule_alloc(tc_ctx* ctx, int full)
+{
+    const int64_t E = ctx->near_entries, nnodes = ctx->nnodes;
+    cudaError_t e;
+    // one histogram buffer for both sorts (entries, nodes)
+    if ((e = ensure(ctx->nl_hist, (size_t)256 * radix_blocks(std::max(E, nnodes)) * 4)) != cudaSuccess) return e;
+    if ((e = ensure(ctx->nl_keys, (size_t)E * 8)) != cudaSuccess) return e;
+    if ((e = ensure(ctx->nl_keys_alt, (size_t)E * 8)) != cudaSuccess) return e;
+    if ((e = ensure(ctx->nl_idx, (size_t)E * 4)) != cudaSuccess) return e;
+    if ((e = ensure(ctx->nl_idx_alt, (size_t)E * 4)) != cudaSuccess) return e;
+    if ((e = ensure(ctx->nl_eb, (size_t)E * 4)) != cudaSuccess) return e;
+    if (!full) return cudaSuccess;
+    if ((e = ensure(ctx->nl_cnt, (size_t)(E + 1) * 4)) != cudaSuccess) return e;
+    if ((e = ensure(ctx->nl_inc0, (size_t)(E + 1) * 8)) != cudaSuccess) return e;
+    if ((e = ensure(ctx->nl_k0, (size_t)nnodes * 4)) != cudaSuccess) return e;
+    if ((e = ensure(ctx->nl_k1, (size_t)nnodes * 4)) != cudaSuccess) return e;
+    if ((e = ensure(ctx->nl_ninc0, (size_t)nnodes * 8)) != cudaSuccess) return e;
+    if ((e = ensure(ctx->nl_nA, (size_t)nnodes * 4)) != cudaSuccess) return e;
+    if ((e = ensure(ctx->nl_nkey, (size_t)nnodes * 8)) != cudaSuccess) return e;
+    if ((e = ensure(ctx->nl_nkey_alt, (size_t)nnodes * 8)) != cudaSuccess) return e;
+    if ((e = ensure(ctx->nl_nord, (size_t)nnodes * 4)) != cudaSuccess) return e;
+    if ((e = ensure(ctx->nl_nord_alt, (size_t)nnodes * 4)) != cudaSuccess) return e;
+    if ((e = ensure(ctx->nl_ucnt, (size_t)nnodes * 4)) != cudaSuccess) return e;
+    if ((e = ensure(ctx->nl_uoff, (size_t)(nnodes + 1) * 4)) != cudaSuccess) return e;
+    if ((e = ensure(ctx->nl_units, (size_t)schedule_max_units(ctx) * 8)) != cudaSuccess) return e;
+    if ((e = ensure(ctx->nl_inc_m, (size_t)E * 32 * 4)) != cudaSuccess) return e;
+    if ((e = ensure(ctx->nl_inc_e, (size_t)E * 32 * 4)) != cudaSuccess) return e;
+    if ((e = ensure(ctx->nl_slots, (size_t)E * 96 * 8)) != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
+cudaError_t near_schedule_build(tc_ctx* ctx, int full, cudaStream_t s)
 {
     const int64_t E = ctx->near_entries, nnodes = ctx->nnodes;
     const int64_t nbatch = (ctx->M + kBatch - 1) / kBatch;
     const ListEntry* list = ptr<ListEntry>(ctx->near_list);
-    cudaError_t e;
-    // one histogram buffer for both sorts (entries, nodes), sized before either runs
-    if ((e = ensure(ctx->nl_hist, (size_t)256 * radix_blocks(std::max(E, nnodes)) * 4)) != cudaSuccess) return e;
-    if (ctx->near_sched_ready < 1) {
-        e = sort_list_entries(list, E, ptr<int64_t>(ctx->near_off), nbatch, nnodes, ctx->nl_keys, ctx->nl_keys_alt,
-                              ctx->nl_idx, ctx->nl_idx_alt, ctx->nl_eb, ctx->nl_hist, s);
-        if (e != cudaSuccess) return e;
-        ctx->near_sched_ready = 1;
-    }
-    // sum over leaves of ceil(A / 64) <= 32 E / 64 + the leaves
-    const int64_t max_units = E / 2 + nnodes + 1;
-    if (full && ctx->near_sched_ready < 2) {
-        if ((e = ensure(ctx->nl_cnt, (size_t)(E + 1) * 4)) != cudaSuccess) return e;
-        if ((e = ensure(ctx->nl_inc0, (size_t)(E + 1) * 8)) != cudaSuccess) return e;
-        if ((e = ensure(ctx->nl_k0, (size_t)nnodes * 4)) != cudaSuccess) return e;
-        if ((e = ensure(ctx->nl_k1, (size_t)nnodes * 4)) != cudaSuccess) return e;
-        if ((e = ensure(ctx->nl_ninc0, (size_t)nnodes * 8)) != cudaSuccess) return e;
-        if ((e = ensure(ctx->nl_nA, (size_t)nnodes * 4)) != cudaSuccess) return e;
-        if ((e = ensure(ctx->nl_nkey, (size_t)nnodes * 8)) != cudaSuccess) return e;
-        if ((e = ensure(ctx->nl_nkey_alt, (size_t)nnodes * 8)) != cudaSuccess) return e;
-        if ((e = ensure(ctx->nl_nord, (size_t)nnodes * 4)) != cudaSuccess) return e;
-        if ((e = ensure(ctx->nl_nord_alt, (size_t)nnodes * 4)) != cudaSuccess) return e;
-        if ((e = ensure(ctx->nl_ucnt, (size_t)nnodes * 4)) != cudaSuccess) return e;
-        if ((e = ensure(ctx->nl_uoff, (size_t)(nnodes + 1) * 4)) != cudaSuccess) return e;
-        if ((e = ensure(ctx->nl_units, (size_t)max_units * 8)) != cudaSuccess) return e;
-        if ((e = ensure(ctx->nl_inc_m, (size_t)E * 32 * 4)) != cudaSuccess) return e;
-        if ((e = ensure(ctx->nl_inc_e, (size_t)E * 32 * 4)) != cudaSuccess) return e;
-        if ((e = ensure(ctx->nl_slots, (size_t)E * 96 * 8)) != cudaSuccess) return e;
-        if (E > 0) {
-            const int32_t* sidx = ptr<int32_t>(ctx->nl_idx);
-            int64_t* inc0 = ptr<int64_t>(ctx->nl_inc0);
-            k_inc_count<<<grid_for(E, 256), 256, 0, s>>>(list, sidx, E, ptr<int32_t>(ctx->nl_cnt));
-            note_launch();
-            if ((e = launch_scan_i32_to_i64(ptr<int32_t>(ctx->nl_cnt), inc0, E, inc0 + E, s)) != cudaSuccess)
-                return e;
-            if ((e = cudaMemsetAsync(ctx->nl_k0.p, 0, (size_t)nnodes * 4, s)) != cudaSuccess) return e;
-            if ((e = cudaMemsetAsync(ctx->nl_k1.p, 0, (size_t)nnodes * 4, s)) != cudaSuccess) return e;
-            k_leaf_bounds<<<grid_for(E, 256), 256, 0, s>>>(ptr<uint64_t>(ctx->nl_keys), E, ptr<int32_t>(ctx->nl_k0),
-                                                           ptr<int32_t>(ctx->nl_k1));
-            note_launch();
-            k_leaf_units<<<grid_for(nnodes, 256), 256, 0, s>>>(
-                ptr<int4>(ctx->node_topo), nnodes, ptr<int32_t>(ctx->nl_k0), ptr<int32_t>(ctx->nl_k1), inc0,
-                ptr<int64_t>(ctx->nl_ninc0), ptr<int32_t>(ctx->nl_nA), ptr<uint64_t>(ctx->nl_nkey),
-                ptr<int32_t>(ctx->nl_nord));
-            note_launch();
-            if ((e = radix_sort_bits(ptr<uint64_t>(ctx->nl_nkey), ptr<int32_t>(ctx->nl_nord),
-                                     ptr<uint64_t>(ctx->nl_nkey_alt), ptr<int32_t>(ctx->nl_nord_alt),
-                                     ptr<uint32_t>(ctx->nl_hist), nnodes, kLeafKeyBits, s)) != cudaSuccess)
-                return e;
-            k_unit_count<<<grid_for(nnodes, 256), 256, 0, s>>>(ptr<int32_t>(ctx->nl_nord), ptr<int32_t>(ctx->nl_nA),
-                                                               nnodes, ptr<int32_t>(ctx->nl_ucnt));
-            note_launch();
-            int32_t* uoff = ptr<int32_t>(ctx->nl_uoff);
-            if ((e = launch_scan_i32(ptr<int32_t>(ctx->nl_ucnt), uoff, nnodes, uoff + nnodes, s)) != cudaSuccess)
-                return e;
-            k_unit_fill<<<grid_for(nnodes, 256), 256, 0, s>>>(ptr<int32_t>(ctx->nl_nord), ptr<int32_t>(ctx->nl_ucnt),
-                                                              uoff, nnodes, ptr<int2>(ctx->nl_units));
-            note_launch();
-            k_inc_fill<<<grid_for(E * 32, 256), 256, 0, s>>>(list, sidx, ptr<int32_t>(ctx->nl_eb), inc0, E,
-                                                             ptr<int32_t>(ctx->nl_inc_m), ptr<int32_t>(ctx->nl_inc_e));
-            note_launch();
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        }
-        ctx->near_sched_ready = 2;
-    }
+    cudaError_t e = sort_list_entries(list, E, ptr<int64_t>(ctx->near_off), nbatch, nnodes, ctx->nl_keys,
+                                      ctx->nl_keys_alt, ctx->nl_idx, ctx->nl_idx_alt, ctx->nl_eb, ctx->nl_hist, s);
+    if (e != cudaSuccess || !full) return e;
+    int32_t* uoff = ptr<int32_t>(ctx->nl_uoff);
+    if (E == 0) return cudaMemsetAsync(uoff + nnodes, 0, 4, s);
+    const int32_t* sidx = ptr<int32_t>(ctx->nl_idx);
+    int64_t* inc0 = ptr<int64_t>(ctx->nl_inc0);
+    k_inc_count<<<grid_for(E, 256), 256, 0, s>>>(list, sidx, E, ptr<int32_t>(ctx->nl_cnt));
+    note_launch();
+    if ((e = launch_scan_i32_to_i64(ptr<int32_t>(ctx->nl_cnt), inc0, E, inc0 + E, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(ctx->nl_k0.p, 0, (size_t)nnodes * 4, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(ctx->nl_k1.p, 0, (size_t)nnodes * 4, s)) != cudaSuccess) return e;
+    k_leaf_bounds<<<grid_for(E, 256), 256, 0, s>>>(ptr<uint64_t>(ctx->nl_keys), E, ptr<int32_t>(ctx->nl_k0),
+                                                   ptr<int32_t>(ctx->nl_k1));
+    note_launch();
+    k_leaf_units<<<grid_for(nnodes, 256), 256, 0, s>>>(ptr<int4>(ctx->node_topo), nnodes, ptr<int32_t>(ctx->nl_k0),
+                                                       ptr<int32_t>(ctx->nl_k1), inc0, ptr<int64_t>(ctx->nl_ninc0),
+                                                       ptr<int32_t>(ctx->nl_nA), ptr<uint64_t>(ctx->nl_nkey),
+                                                       ptr<int32_t>(ctx->nl_nord));
+    note_launch();
+    if ((e = radix_sort_bits(ptr<uint64_t>(ctx->nl_nkey), ptr<int32_t>(ctx->nl_nord), ptr<uint64_t>(ctx->nl_nkey_alt),
+                             ptr<int32_t>(ctx->nl_nord_alt), ptr<uint32_t>(ctx->nl_hist), nnodes, kLeafKeyBits, s)) !=
+        cudaSuccess)
+        return e;
+    k_unit_count<<<grid_for(nnodes, 256), 256, 0, s>>>(ptr<int32_t>(ctx->nl_nord), ptr<int32_t>(ctx->nl_nA), nnodes,
+                                                       ptr<int32_t>(ctx->nl_ucnt));
+    note_launch();
+    if ((e = launch_scan_i32(ptr<int32_t>(ctx->nl_ucnt), uoff, nnodes, uoff + nnodes, s)) != cudaSuccess) return e;
+    k_unit_fill<<<grid_for(nnodes, 256), 256, 0, s>>>(ptr<int32_t>(ctx->nl_nord), ptr<int32_t>(ctx->nl_ucnt), uoff,
+                                                      nnodes, ptr<int2>(ctx->nl_units));
+    note_launch();
+    k_inc_fill<<<grid_for(E * 32, 256), 256, 0, s>>>(list, sidx, ptr<int32_t>(ctx->nl_eb), inc0, E,
+                                                     ptr<int32_t>(ctx->nl_inc_m), ptr<int32_t>(ctx->nl_inc_e));
+    note_launch();
+    return cudaGetLastError();
+}
+
+NearSched near_schedule_desc(tc_ctx* ctx)
+{
+    NearSched sc;
     sc.node_inc0 = ptr<int64_t>(ctx->nl_ninc0);
     sc.node_A = ptr<int32_t>(ctx->nl_nA);
     sc.units = ptr<int2>(ctx->nl_units);
-    sc.nunits = ptr<int32_t>(ctx->nl_uoff) + nnodes;
+    sc.nunits = ptr<int32_t>(ctx->nl_uoff) + ctx->nnodes;
     sc.inc_m = ptr<int32_t>(ctx->nl_inc_m);
     sc.inc_e = ptr<int32_t>(ctx->nl_inc_e);
     sc.slots = ptr<double>(ctx->nl_slots);
-    sc.E = E;
-    sc.max_units = max_units;
+    sc.E = ctx->near_entries;
+    sc.max_units = schedule_max_units(ctx);
     sc.queue = nullptr;
+    return sc;
+}
+
+cudaError_t near_schedule(tc_ctx* ctx, int full, NearSched& sc, cudaStream_t s)
+{
+    const int want = full ? 2 : 1;
+    if (ctx->near_sched_ready < want) {
+        cudaError_t e = near_schedule_alloc(ctx, full);
+        if (e == cudaSuccess) e = near_schedule_build(ctx, full, s);
+        if (e != cudaSuccess) return e;
+        ctx->near_sched_ready = want;
+    }
+    sc = near_schedule_desc(ctx);
     return cudaSuccess;
 }
 
@@ -536,11 +598,12 @@ cudaError_t launch_near(int precision, const double* ts, int64_t M, const int4* 
     return cudaGetLastError();
 }
 
-cudaError_t launch_near_batched(int precision, const SysDesc* sys, int nsys, const int64_t* item_off, int64_t nitems,
-                                unsigned long long* counter, int warps_per_block, int blocks, cudaStream_t s)
+cudaError_t launch_near_batched(int precision, const SysDesc* sys, int nsys, const int64_t* batch_off,
+                                int64_t nbatches, int64_t* unit_off, unsigned long long* counter, int warps_per_block,
+                                int blocks, cudaStream_t s)
 {
     if (warps_per_block < 1 || warps_per_block > kNearMaxWarps) return cudaErrorInvalidValue;
-    const void* fn = precision == TC_FP64 ? (const void*)k_near_batched<true> : (const void*)k_near_batched<false>;
+    const void* fn = precision == TC_FP64 ? (const void*)k_near_batched_fp64 : (const void*)k_near_leaf_batched;
     cudaError_t e;
     if (blocks <= 0) {
         int per_sm = 0, dev = 0, sms = 0;
@@ -550,10 +613,16 @@ cudaError_t launch_near_batched(int precision, const SysDesc* sys, int nsys, con
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         blocks = (per_sm > 0 ? per_sm : 1) * sms;
     }
-    if (precision == TC_FP64)
-        k_near_batched<true><<<blocks, warps_per_block * 32, 0, s>>>(sys, nsys, item_off, nitems, counter);
-    else
-        k_near_batched<false><<<blocks, warps_per_block * 32, 0, s>>>(sys, nsys, item_off, nitems, counter);
+    if (precision == TC_FP64) {
+        k_near_batched_fp64<<<blocks, warps_per_block * 32, 0, s>>>(sys, nsys, batch_off, nbatches, counter);
+        note_launch();
+        return cudaGetLastError();
+    }
+    k_unit_offsets<<<1, 1, 0, s>>>(sys, nsys, unit_off);
+    note_launch();
+    k_near_leaf_batched<<<blocks, warps_per_block * 32, 0, s>>>(sys, nsys, unit_off, counter);
+    note_launch();
+    k_near_reduce_batched<<<grid_for(nbatches * 32, 256), 256, 0, s>>>(sys, nsys, batch_off, nbatches);
     note_launch();
     return cudaGetLastError();
 }

@@ -1,8 +1,8 @@
 // Packed FP32x2 near-field machinery shared by the forward near field
 // (tc_near.cu) and the target side of its adjoint (tc_adjoint.cu): the
-// staging of 32-source tiles as source pairs, and the walk of a group of
-// batches over the merge of their near lists with the targets of each leaf
-// packed into 32-lane streams.  See tc_near.cu for the design.
+// staging of 32-source tiles as source pairs, the sums of one leaf at one or
+// two 32-target streams, and the leaf-major schedule that packs the targets
+// of each leaf into full streams.  See tc_near.cu for the design.
 #pragma once
 
 #include "tc_internal.cuh"
@@ -63,15 +63,6 @@ __device__ inline void stage_pairs(const float4* __restrict__ spack, int64_t bas
     }
 }
 
-// Per-warp scratch of the compacted near kernel: the source tile, the
-// accumulators of the warp's G x 32 targets and the stream slot map.
-template <int G>
-struct NearScratch {
-    float4 tile[kTileFloat4];
-    double acc[G][3][32];
-    int slot[G * 32];
-};
-
 // The near field of one leaf (sources first .. first + count - 1) at the
 // targets of one or two streams (ta, and tb when two), on the warp's tile:
 // per 32-source tile the packed pair sums of each target, accumulated over
@@ -124,141 +115,60 @@ __device__ __forceinline__ void leaf_sums(const typename Op::Tgt& ta, const type
     }
 }
 
-// Near field of batches G*B .. G*B+G-1 (the last ones may not exist) on one
-// warp, over the merge of their G near lists (all in tree order, so by the
-// leaf's first source); lane g < G holds the cursor of list g, so the merge
-// state costs a few registers whatever G.  For each leaf, the targets of the
-// G batches that need it (the union of the entries' lane masks, A of them)
-// are packed densely into ceil(A/32) streams of 32 lanes, so lanes whose
-// target does not need the leaf are not computed (lane use of single-batch
-// lists at N = 1M: 0.74); streams are evaluated two at a time, each sharing
-// the staged tile, and each result is added to its target's accumulator in
-// shared memory.  A target's arithmetic does not depend on which stream or
-// lane it is packed into, so any group size gives the same bits.  self: the targets are the sources (sorted index = source
-// index), which lets leaves that cannot hold a stream's own target skip the
-// r = 0 guard.
-//
-// Op supplies the per-target record (Op::Tgt, Op::load), the pair terms of one
-// target against a staged source pair (Op::terms<kGuard>, three FP32x2
-// accumulators), whether the result is stored or added (Op::kAdd), and
-// whether its terms are also compiled without the r = 0 guard (Op::kUnguarded);
-// gs and prm are passed through to Op::load (the adjoint's target weights g,
-// unused by the forward field; prm: eps^2 of the regularized kernels).
-template <int G, typename Op>
-__device__ inline void near_group(const double* __restrict__ ts, const double* __restrict__ gs, int64_t M,
-                                  const int4* __restrict__ topo, const float4* __restrict__ spack,
-                                  const int64_t* __restrict__ near_off, const ListEntry* __restrict__ near_list,
-                                  double* __restrict__ out, int64_t B, int self, float prm, NearScratch<G>& sc,
-                                  int lane)
-{
-    const int64_t nbatch = (M + kBatch - 1) / kBatch;
-    const int64_t b0 = (int64_t)G * B;
-    constexpr int kEnd = 0x7fffffff;
-    constexpr unsigned kAll = 0xffffffffu;
-    // lane g < G holds the cursor of list g
-    int64_t cur = 0, end = 0;
-    if (lane < G && b0 + lane < nbatch) {
-        cur = near_off[b0 + lane];
-        end = near_off[b0 + lane + 1];
-    }
-    ListEntry le{0, 0};
-    int key = kEnd;
-    if (cur < end) {
-        le = near_list[cur];
-        key = topo[le.node].x;
-    }
-#pragma unroll
-    for (int g = 0; g < G; g++)
-#pragma unroll
-        for (int c = 0; c < 3; c++) sc.acc[g][c][lane] = 0.0;
-    const unsigned lt = (1u << lane) - 1u;
-    for (;;) {
-        int kmin = key;
-#pragma unroll
-        for (int o = 1; o < G; o <<= 1) kmin = min(kmin, __shfl_xor_sync(kAll, kmin, o));
-        kmin = __shfl_sync(kAll, kmin, 0);
-        if (kmin == kEnd) break;
-        // leaves are disjoint ranges, so equal first sources name one leaf
-        const bool match = lane < G && key == kmin;
-        const unsigned mine = match ? le.mask : 0u;
-        const int node = __shfl_sync(kAll, le.node, __ffs(__ballot_sync(kAll, match)) - 1);
-        unsigned m[G];
-        int A = 0, P[G];
-#pragma unroll
-        for (int g = 0; g < G; g++) {
-            m[g] = __shfl_sync(kAll, mine, g);
-            P[g] = A;
-            A += __popc(m[g]);
-        }
-        __syncwarp();
-#pragma unroll
-        for (int g = 0; g < G; g++)
-            if ((m[g] >> lane) & 1u) sc.slot[P[g] + __popc(m[g] & lt)] = g * 32 + lane;
-        __syncwarp();
-        const int4 t = topo[node];
-        const int S = (A + 31) >> 5;
-        for (int s = 0; s < S; s += 2) {
-            const bool two = s + 1 < S;
-            const int k1 = 32 * s + lane, k2 = k1 + 32;
-            const bool v1 = k1 < A, v2 = two && k2 < A;
-            const int id1 = v1 ? sc.slot[k1] : 0, id2 = v2 ? sc.slot[k2] : 0;
-            const int64_t m1 = (b0 + (id1 >> 5)) * kBatch + (id1 & 31), m2 = (b0 + (id2 >> 5)) * kBatch + (id2 & 31);
-            const typename Op::Tgt ta = Op::load(ts, gs, M, m1, v1, prm);
-            const typename Op::Tgt tb = Op::load(ts, gs, M, m2, v2, prm);
-            // r = 0 needs the target to coincide with a source of this leaf.
-            // With targets = sources (self) that is only possible for a
-            // target inside the leaf's own range (coincident points have
-            // one Morton key, so they share a leaf); otherwise (disjoint
-            // targets) every pair keeps the guard.
-            const bool guard = !Op::kUnguarded || !self ||
-                               __any_sync(0xffffffffu, (v1 && m1 >= t.x && m1 < (int64_t)t.x + t.y) ||
-                                                           (v2 && m2 >= t.x && m2 < (int64_t)t.x + t.y));
-            double a[3], c[3];
-            leaf_sums<Op>(ta, tb, two, guard, t.x, t.y, spack, sc.tile, lane, a, c);
-            // each (batch, lane) target holds one slot per leaf: no two lanes
-            // add to the same accumulator here
-            if (v1)
-#pragma unroll
-                for (int k = 0; k < 3; k++) sc.acc[id1 >> 5][k][id1 & 31] += a[k];
-            if (v2)
-#pragma unroll
-                for (int k = 0; k < 3; k++) sc.acc[id2 >> 5][k][id2 & 31] += c[k];
-        }
-        if (match) {
-            if (++cur < end) {
-                le = near_list[cur];
-                key = topo[le.node].x;
-            } else {
-                key = kEnd;
-            }
-        }
-    }
-    __syncwarp();
-#pragma unroll
-    for (int g = 0; g < G; g++) {
-        const int64_t mm = (b0 + g) * kBatch + lane;
-        if (mm < M)
-            for (int c = 0; c < 3; c++) {
-                if (Op::kAdd)
-                    out[c * M + mm] += sc.acc[g][c][lane];
-                else
-                    out[c * M + mm] = sc.acc[g][c][lane];
-            }
-    }
-}
-
 // ---------------------------------------------------------------------------
-// Leaf-major schedule of the one-system near field and of the target side of
-// its adjoint.  The near entries are sorted by leaf (near_schedule); the
-// targets of all entries of a leaf, its incidences, are packed densely into
-// 32-lane streams, so that only a leaf's last stream is partial, and the
-// units of work, (leaf, pair of streams), are drained by a resident grid in
-// order of decreasing leaf size.  A unit writes each of its targets' leaf sums
-// to the slot of its (entry, lane); k_near_reduce then adds each target's
-// slots in list order, the order in which near_group adds its leaves, so both
-// schedules give the same bits.
+// Leaf-major schedule of the near field and of the target side of its
+// adjoint.  The near entries are sorted by leaf (near_schedule); the targets
+// of all entries of a leaf, its incidences, are packed densely into 32-lane
+// streams, so that only a leaf's last stream is partial, and the units of
+// work, (leaf, pair of streams), are drained by a resident grid in order of
+// decreasing leaf size.  A unit writes each of its targets' leaf sums to the
+// slot of its (entry, lane); k_near_reduce then adds each target's slots in
+// list order (tree order), starting from zero.  A target's sums do not depend
+// on which stream or lane it is packed into, nor on the order of the units,
+// so the result is the same whatever the packing, the grid or the number of
+// systems in a batch.
 constexpr int kLeafWarps = 4;       // warps per block of k_near_leaf
 constexpr int kLeafFreeBlocks = 1;  // block slots per SM left free (for the far field on the second stream)
+
+// Unit i of a schedule on one warp (tile: the warp's source tile).
+template <typename Op>
+__device__ __forceinline__ void leaf_unit(const double* __restrict__ ts, const double* __restrict__ gs, int64_t M,
+                                          const int4* __restrict__ topo, const float4* __restrict__ spack,
+                                          const int2* __restrict__ units, const int64_t* __restrict__ node_inc0,
+                                          const int32_t* __restrict__ node_A, const int32_t* __restrict__ inc_m,
+                                          const int32_t* __restrict__ inc_e, double* __restrict__ slots, int self,
+                                          float prm, int64_t i, float4* tile, int lane)
+{
+    const int2 un = units[i];
+    const int node = un.x;
+    const int64_t I0 = node_inc0[node];
+    const int A = node_A[node];
+    const int k1 = 64 * un.y + lane, k2 = k1 + 32;
+    const bool two = 64 * un.y + 32 < A;
+    const bool v1 = k1 < A, v2 = k2 < A;
+    const int m1 = v1 ? inc_m[I0 + k1] : 0, m2 = v2 ? inc_m[I0 + k2] : 0;
+    const typename Op::Tgt ta = Op::load(ts, gs, M, m1, v1, prm);
+    const typename Op::Tgt tb = Op::load(ts, gs, M, m2, v2, prm);
+    const int4 t = topo[node];
+    // r = 0 needs the target to coincide with a source of this leaf.  With
+    // targets = sources (self) that is only possible for a target inside the
+    // leaf's own range (coincident points have one Morton key, so they share
+    // a leaf); otherwise (disjoint targets) every pair keeps the guard.
+    const bool guard = !Op::kUnguarded || !self ||
+                       __any_sync(0xffffffffu, (v1 && m1 >= t.x && m1 < t.x + t.y) ||
+                                                   (v2 && m2 >= t.x && m2 < t.x + t.y));
+    double a[3], c[3];
+    leaf_sums<Op>(ta, tb, two, guard, t.x, t.y, spack, tile, lane, a, c);
+    // slot of (entry e, component k, lane l): 96 e + 32 k + l
+    if (v1) {
+        double* q = slots + (int64_t)inc_e[I0 + k1] * 96 + (m1 & 31);
+        q[0] = a[0], q[32] = a[1], q[64] = a[2];
+    }
+    if (v2) {
+        double* q = slots + (int64_t)inc_e[I0 + k2] * 96 + (m2 & 31);
+        q[0] = c[0], q[32] = c[1], q[64] = c[2];
+    }
+}
 
 template <typename Op>
 __global__ void __launch_bounds__(kLeafWarps * 32)
@@ -277,33 +187,8 @@ __global__ void __launch_bounds__(kLeafWarps * 32)
         if (lane == 0) i = atomicAdd(queue, 1u);
         i = __shfl_sync(0xffffffffu, i, 0);
         if (i >= nu) break;
-        const int2 un = units[i];
-        const int node = un.x;
-        const int64_t I0 = node_inc0[node];
-        const int A = node_A[node];
-        const int k1 = 64 * un.y + lane, k2 = k1 + 32;
-        const bool two = 64 * un.y + 32 < A;
-        const bool v1 = k1 < A, v2 = k2 < A;
-        const int m1 = v1 ? inc_m[I0 + k1] : 0, m2 = v2 ? inc_m[I0 + k2] : 0;
-        const typename Op::Tgt ta = Op::load(ts, gs, M, m1, v1, prm);
-        const typename Op::Tgt tb = Op::load(ts, gs, M, m2, v2, prm);
-        const int4 t = topo[node];
-        // as in near_group: with targets = sources only a target inside the
-        // leaf's own range can coincide with one of its sources
-        const bool guard = !Op::kUnguarded || !self ||
-                           __any_sync(0xffffffffu, (v1 && m1 >= t.x && m1 < t.x + t.y) ||
-                                                       (v2 && m2 >= t.x && m2 < t.x + t.y));
-        double a[3], c[3];
-        leaf_sums<Op>(ta, tb, two, guard, t.x, t.y, spack, tile[w], lane, a, c);
-        // slot of (entry e, component k, lane l): 96 e + 32 k + l
-        if (v1) {
-            double* q = slots + (int64_t)inc_e[I0 + k1] * 96 + (m1 & 31);
-            q[0] = a[0], q[32] = a[1], q[64] = a[2];
-        }
-        if (v2) {
-            double* q = slots + (int64_t)inc_e[I0 + k2] * 96 + (m2 & 31);
-            q[0] = c[0], q[32] = c[1], q[64] = c[2];
-        }
+        leaf_unit<Op>(ts, gs, M, topo, spack, units, node_inc0, node_A, inc_m, inc_e, slots, self, prm, i, tile[w],
+                      lane);
     }
 }
 
@@ -311,12 +196,11 @@ __global__ void __launch_bounds__(kLeafWarps * 32)
 // entries, in list order, starting from zero, and stores (or, kAdd, adds) the
 // sum.
 template <bool kAdd>
-__global__ void k_near_reduce(const int64_t* __restrict__ near_off, const ListEntry* __restrict__ near_list,
-                              int64_t M, const double* __restrict__ slots, double* __restrict__ out)
+__device__ __forceinline__ void reduce_batch(const int64_t* __restrict__ near_off,
+                                             const ListEntry* __restrict__ near_list, int64_t M,
+                                             const double* __restrict__ slots, double* __restrict__ out, int64_t b,
+                                             int lane)
 {
-    const int lane = threadIdx.x & 31;
-    const int64_t b = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    if (b >= (M + kBatch - 1) / kBatch) return;
     double a0 = 0.0, a1 = 0.0, a2 = 0.0;
     const int64_t e1 = near_off[b + 1];
     for (int64_t e = near_off[b]; e < e1; e++)
@@ -338,6 +222,15 @@ __global__ void k_near_reduce(const int64_t* __restrict__ near_off, const ListEn
             out[2 * M + m] = a2;
         }
     }
+}
+
+template <bool kAdd>
+__global__ void k_near_reduce(const int64_t* __restrict__ near_off, const ListEntry* __restrict__ near_list,
+                              int64_t M, const double* __restrict__ slots, double* __restrict__ out)
+{
+    const int64_t b = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (b >= (M + kBatch - 1) / kBatch) return;
+    reduce_batch<kAdd>(near_off, near_list, M, slots, out, b, threadIdx.x & 31);
 }
 
 // blocks of k_near_leaf<Op> the grid takes: the occupancy limit less
