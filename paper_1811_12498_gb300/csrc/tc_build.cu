@@ -176,51 +176,6 @@ __global__ void k_radix_hist(const uint64_t* __restrict__ keys, int64_t N, int s
     hist[(int64_t)threadIdx.x * gridDim.x + blockIdx.x] = cnt[threadIdx.x];
 }
 
-// Single-block exclusive scan of n uint32 values in place.  Each thread owns
-// a contiguous chunk (a multiple of 4 values, so whole uint4 loads) and reads
-// it with independent vector loads, so the chunk's latency is paid a few
-// times rather than once per element.
-__global__ void __launch_bounds__(1024) k_scan_u32_inplace(uint32_t* __restrict__ a, int64_t n)
-{
-    __shared__ uint32_t part[1024];
-    const int t = threadIdx.x;
-    int64_t chunk = (n + blockDim.x - 1) / blockDim.x;
-    chunk = (chunk + 3) & ~(int64_t)3;
-    const int64_t b = t * chunk, e = b + chunk < n ? b + chunk : n;
-    const int64_t e4 = b + ((e > b ? e - b : 0) & ~(int64_t)3);  // end of the whole uint4 loads
-    uint32_t s = 0;
-#pragma unroll 4
-    for (int64_t i = b; i < e4; i += 4) {
-        const uint4 v = *reinterpret_cast<const uint4*>(a + i);
-        s += v.x + v.y + v.z + v.w;
-    }
-    for (int64_t i = e4; i < e; i++) s += a[i];
-    part[t] = s;
-    __syncthreads();
-    for (int o = 1; o < (int)blockDim.x; o <<= 1) {
-        uint32_t v = t >= o ? part[t - o] : 0;
-        __syncthreads();
-        part[t] += v;
-        __syncthreads();
-    }
-    uint32_t run = part[t] - s;
-#pragma unroll 4
-    for (int64_t i = b; i < e4; i += 4) {
-        const uint4 v = *reinterpret_cast<const uint4*>(a + i);
-        uint4 o;
-        o.x = run;
-        o.y = run + v.x;
-        o.z = o.y + v.y;
-        o.w = o.z + v.z;
-        run = o.w + v.w;
-        *reinterpret_cast<uint4*>(a + i) = o;
-    }
-    for (int64_t i = e4; i < e; i++) {
-        const uint32_t v = a[i];
-        a[i] = run;
-        run += v;
-    }
-}
 
 __global__ void k_radix_scatter(const uint64_t* __restrict__ kin, const int32_t* __restrict__ vin,
                                 uint64_t* __restrict__ kout, int32_t* __restrict__ vout, int64_t N, int shift,
@@ -562,7 +517,7 @@ cudaError_t radix_sort_bits(uint64_t* keys, int32_t* vals, uint64_t* keys_alt, i
         int shift = 8 * pass;
         k_radix_hist<<<nblk, kRadixThreads, 0, s>>>(ki, N, shift, hist);
         note_launch();
-        k_scan_u32_inplace<<<1, 1024, 0, s>>>(hist, (int64_t)256 * nblk);
+        k_scan_tiles<uint32_t, uint32_t><<<1, 1024, 0, s>>>(hist, hist, (int64_t)256 * nblk, nullptr);
         note_launch();
         k_radix_scatter<<<nblk, kRadixThreads, 0, s>>>(ki, vi, ko, vo, N, shift, hist);
         note_launch();
@@ -598,37 +553,9 @@ cudaError_t launch_split_count(const int4* topo, const int4* info, const uint64_
     return cudaGetLastError();
 }
 
-namespace {
-__global__ void k_scan_i32(const int32_t* __restrict__ in, int32_t* __restrict__ out, int64_t n,
-                           int32_t* __restrict__ total)
-{
-    __shared__ int32_t part[1024];
-    int t = threadIdx.x;
-    int64_t chunk = (n + blockDim.x - 1) / blockDim.x;
-    int64_t b = t * chunk, e = b + chunk < n ? b + chunk : n;
-    int32_t s = 0;
-    for (int64_t i = b; i < e; i++) s += in[i];
-    part[t] = s;
-    __syncthreads();
-    for (int o = 1; o < (int)blockDim.x; o <<= 1) {
-        int32_t v = t >= o ? part[t - o] : 0;
-        __syncthreads();
-        part[t] += v;
-        __syncthreads();
-    }
-    int32_t run = part[t] - s;
-    for (int64_t i = b; i < e; i++) {
-        int32_t v = in[i];
-        out[i] = run;
-        run += v;
-    }
-    if (t == (int)blockDim.x - 1) *total = part[t];
-}
-}  // namespace
-
 cudaError_t launch_scan_i32(const int32_t* in, int32_t* out_excl, int64_t n, int32_t* total, cudaStream_t s)
 {
-    k_scan_i32<<<1, 1024, 0, s>>>(in, out_excl, n, total);
+    k_scan_tiles<int32_t, int32_t><<<1, 1024, 0, s>>>(in, out_excl, n, total);
     note_launch();
     return cudaGetLastError();
 }

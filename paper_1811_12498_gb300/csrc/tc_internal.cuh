@@ -269,6 +269,61 @@ tc_status eval_prepare_count(tc_ctx* ctx, const double* targets, int64_t M, doub
 tc_status eval_prepare_finish(tc_ctx* ctx);
 tc_status eval_compute(tc_ctx* ctx, double* u);
 
+// Exclusive scan of n values with one block of 1024 threads (in and out may
+// be the same array): tiles of 1024 x kScanPer values, each thread summing
+// its kScanPer consecutive values, the lane sums scanned by warp shuffles,
+// the 32 warp sums by warp 0, and the tiles chained by a running carry.  All
+// of a tile's loads are independent, so its latency is paid once per tile.
+// total (may be NULL) receives the sum of all n values.
+constexpr int kScanPer = 16;
+template <typename Tin, typename Tout>
+__global__ void __launch_bounds__(1024) k_scan_tiles(const Tin* in, Tout* out, int64_t n, Tout* total)
+{
+    constexpr int64_t kTile = 1024 * kScanPer;
+    __shared__ Tout wex[32];
+    __shared__ Tout ttot;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    Tout carry = 0;
+    for (int64_t base = 0; base < n; base += kTile) {
+        const int64_t b0 = base + (int64_t)threadIdx.x * kScanPer;
+        Tin v[kScanPer];
+#pragma unroll
+        for (int k = 0; k < kScanPer; k++) v[k] = b0 + k < n ? in[b0 + k] : (Tin)0;
+        Tout sum = 0;
+#pragma unroll
+        for (int k = 0; k < kScanPer; k++) sum += (Tout)v[k];
+        Tout x = sum;  // inclusive scan of the lane sums
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const Tout y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wex[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            const Tout t0 = wex[lane];
+            Tout y = t0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const Tout z = __shfl_up_sync(0xffffffffu, y, o);
+                if (lane >= o) y += z;
+            }
+            wex[lane] = y - t0;
+            if (lane == 31) ttot = y;
+        }
+        __syncthreads();
+        Tout run = carry + wex[w] + (x - sum);
+#pragma unroll
+        for (int k = 0; k < kScanPer; k++) {
+            if (b0 + k < n) out[b0 + k] = run;
+            run += (Tout)v[k];
+        }
+        carry += ttot;
+        __syncthreads();  // wex and ttot are rewritten by the next tile
+    }
+    if (threadIdx.x == 0 && total) *total = carry;
+}
+
 // error helpers (tc_api.cu)
 tc_status fail(tc_ctx* ctx, tc_status st, const char* fmt, ...);
 tc_status cuda_fail(tc_ctx* ctx, cudaError_t e, const char* where);

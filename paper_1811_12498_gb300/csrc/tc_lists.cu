@@ -126,31 +126,6 @@ __global__ void __launch_bounds__(kListWarps * 32, 12)
     }
 }
 
-__global__ void k_scan_i32_to_i64(const int32_t* __restrict__ in, int64_t* __restrict__ out, int64_t n,
-                                  int64_t* __restrict__ total)
-{
-    __shared__ int64_t part[1024];
-    int t = threadIdx.x;
-    int64_t chunk = (n + blockDim.x - 1) / blockDim.x;
-    int64_t b = t * chunk, e = b + chunk < n ? b + chunk : n;
-    int64_t s = 0;
-    for (int64_t i = b; i < e; i++) s += in[i];
-    part[t] = s;
-    __syncthreads();
-    for (int o = 1; o < (int)blockDim.x; o <<= 1) {
-        int64_t v = t >= o ? part[t - o] : 0;
-        __syncthreads();
-        part[t] += v;
-        __syncthreads();
-    }
-    int64_t run = part[t] - s;
-    for (int64_t i = b; i < e; i++) {
-        int64_t v = in[i];
-        out[i] = run;
-        run += v;
-    }
-    if (t == (int)blockDim.x - 1) *total = part[t];
-}
 
 __global__ void k_sum_i64(const int64_t* __restrict__ in, int64_t n, int64_t* __restrict__ out)
 {
@@ -267,7 +242,7 @@ cudaError_t launch_lists(const double* ts, int64_t M, const int4* topo, const Ge
 cudaError_t launch_scan_i32_to_i64(const int32_t* in, int64_t* out_excl, int64_t n, int64_t* total,
                                    cudaStream_t s)
 {
-    k_scan_i32_to_i64<<<1, 1024, 0, s>>>(in, out_excl, n, total);
+    k_scan_tiles<int32_t, int64_t><<<1, 1024, 0, s>>>(in, out_excl, n, total);
     note_launch();
     return cudaGetLastError();
 }
