@@ -270,35 +270,43 @@ tc_status eval_prepare_finish(tc_ctx* ctx);
 tc_status eval_compute(tc_ctx* ctx, double* u);
 
 // Exclusive scan of n values with one block of 1024 threads (in and out may
-// be the same array): tiles of 1024 x kScanPer values, each thread summing
-// its kScanPer consecutive values, the lane sums scanned by warp shuffles,
-// the 32 warp sums by warp 0, and the tiles chained by a running carry.  All
-// of a tile's loads are independent, so its latency is paid once per tile.
-// total (may be NULL) receives the sum of all n values.
-constexpr int kScanPer = 16;
+// be the same array).  A tile is 32 warps x kScanRows rows of 32 values; each
+// warp reads its rows with coalesced loads (all of a tile's loads are
+// independent, so its latency is paid once per tile), scans each row by
+// shuffles with a running carry, the 32 warp sums are scanned by warp 0, and
+// the tiles are chained by a running carry.  total (may be NULL) receives the
+// sum of all n values.
+constexpr int kScanRows = 8;
 template <typename Tin, typename Tout>
 __global__ void __launch_bounds__(1024) k_scan_tiles(const Tin* in, Tout* out, int64_t n, Tout* total)
 {
-    constexpr int64_t kTile = 1024 * kScanPer;
+    constexpr int64_t kTile = 1024 * kScanRows;
     __shared__ Tout wex[32];
     __shared__ Tout ttot;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     Tout carry = 0;
     for (int64_t base = 0; base < n; base += kTile) {
-        const int64_t b0 = base + (int64_t)threadIdx.x * kScanPer;
-        Tin v[kScanPer];
+        const int64_t wb = base + (int64_t)w * (32 * kScanRows);
+        Tin v[kScanRows];
 #pragma unroll
-        for (int k = 0; k < kScanPer; k++) v[k] = b0 + k < n ? in[b0 + k] : (Tin)0;
-        Tout sum = 0;
-#pragma unroll
-        for (int k = 0; k < kScanPer; k++) sum += (Tout)v[k];
-        Tout x = sum;  // inclusive scan of the lane sums
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const Tout y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
+        for (int r = 0; r < kScanRows; r++) {
+            const int64_t i = wb + r * 32 + lane;
+            v[r] = i < n ? in[i] : (Tin)0;
         }
-        if (lane == 31) wex[w] = x;
+        Tout ex[kScanRows];  // exclusive prefix inside the warp's rows
+        Tout run = 0;
+#pragma unroll
+        for (int r = 0; r < kScanRows; r++) {
+            Tout x = (Tout)v[r];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const Tout y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            ex[r] = run + x - (Tout)v[r];
+            run += __shfl_sync(0xffffffffu, x, 31);
+        }
+        if (lane == 0) wex[w] = run;
         __syncthreads();
         if (w == 0) {
             const Tout t0 = wex[lane];
@@ -312,11 +320,11 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(const Tin* in, Tout* out, i
             if (lane == 31) ttot = y;
         }
         __syncthreads();
-        Tout run = carry + wex[w] + (x - sum);
+        const Tout off = carry + wex[w];
 #pragma unroll
-        for (int k = 0; k < kScanPer; k++) {
-            if (b0 + k < n) out[b0 + k] = run;
-            run += (Tout)v[k];
+        for (int r = 0; r < kScanRows; r++) {
+            const int64_t i = wb + r * 32 + lane;
+            if (i < n) out[i] = off + ex[r];
         }
         carry += ttot;
         __syncthreads();  // wex and ttot are rewritten by the next tile
