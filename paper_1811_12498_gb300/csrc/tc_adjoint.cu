@@ -1322,9 +1322,10 @@ extern "C" tc_status tc_adjoint(tc_ctx* ctx, const double* g, double* grad_f, do
         ctx->adj_lists_ready = 1;
     }
     // the near entries sorted by leaf (source side); in mixed precision the
-    // whole leaf-major schedule (target side), shared with the forward field
+    // leaf-major schedule too (target side), shared with the forward field
     NearSched sched;
-    TC_CK(near_schedule(ctx, ctx->precision != TC_FP64, sched, s), "near schedule");
+    TC_CK(near_schedule(ctx, 0, sched, s), "near schedule");
+    if (ctx->precision != TC_FP64) TC_CK(near_schedule(ctx, 1, sched, s), "near schedule");
     sched.queue = reinterpret_cast<unsigned*>(ptr<char>(ctx->flags) + 224);
     k_gather_g<<<grid_for(M, 256), 256, 0, s>>>(g, tperm, M, ptr<double>(ctx->adj_gs));
     note_launch();

@@ -119,8 +119,8 @@ static void release_all(tc_ctx* c)
                       &c->tkeys_alt, &c->tperm, &c->tperm_alt, &c->ts, &c->nfar_e, &c->nnear_e,
                       &c->far_off, &c->near_off, &c->far_list, &c->near_list, &c->cnt_far, &c->cnt_near, &c->u_far,
                       &c->u_near, &c->nl_keys, &c->nl_keys_alt, &c->nl_idx, &c->nl_idx_alt, &c->nl_eb, &c->nl_hist,
-                      &c->nl_cnt, &c->nl_inc0, &c->nl_k0, &c->nl_k1, &c->nl_ninc0, &c->nl_nA, &c->nl_nkey,
-                      &c->nl_nkey_alt, &c->nl_nord, &c->nl_nord_alt, &c->nl_ucnt, &c->nl_uoff, &c->nl_units,
+                      &c->nl_nA, &c->nl_nkey, &c->nl_nkey_alt, &c->nl_nord, &c->nl_nord_alt, &c->nl_sA,
+                      &c->nl_inc0s, &c->nl_ninc0, &c->nl_cur, &c->nl_ucnt, &c->nl_uoff, &c->nl_units,
                       &c->nl_inc_m, &c->nl_inc_e, &c->nl_slots, &c->flags, &c->adj_fkeys, &c->adj_fkeys_alt,
                       &c->adj_fidx, &c->adj_fidx_alt, &c->adj_febatch, &c->adj_hist, &c->adj_gs, &c->adj_gt, &c->adj_abar, &c->adj_fbar, &c->adj_lam,
                       &c->adj_lamacc, &c->adj_gfar, &c->adj_gnear, &c->host_in, &c->host_u};

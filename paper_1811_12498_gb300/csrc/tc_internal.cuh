@@ -186,15 +186,16 @@ struct tc_ctx {
     tc::DevBuf far_list, near_list;     // ListEntry
     tc::DevBuf cnt_far, cnt_near;       // per sorted target counts (int64)
     tc::DevBuf u_far, u_near;           // 3*M FP64 sorted order
-    // leaf-major near-field schedule (near_schedule): near entries sorted by
-    // leaf (keys, entry index, batch of each entry), per sorted entry its
-    // incidence count and first incidence, per node its range of sorted
-    // entries, first incidence, incidence count and sort key/order, the units,
-    // per incidence target and entry, and the slots of the leaf sums
+    // near entries sorted by leaf (keys, entry index, batch of each entry;
+    // the adjoint's source side), and the leaf-major near-field schedule
+    // (near_schedule): per node its incidence count, sort key and order, the
+    // counts and first incidences in that order, its first incidence and fill
+    // cursor, units per node and their offsets, the units, per incidence target
+    // and entry, and the slots of the leaf sums
     tc::DevBuf nl_keys, nl_keys_alt, nl_idx, nl_idx_alt, nl_eb, nl_hist;
-    tc::DevBuf nl_cnt, nl_inc0, nl_k0, nl_k1, nl_ninc0, nl_nA, nl_nkey, nl_nkey_alt, nl_nord, nl_nord_alt;
+    tc::DevBuf nl_nA, nl_nkey, nl_nkey_alt, nl_nord, nl_nord_alt, nl_sA, nl_inc0s, nl_ninc0, nl_cur;
     tc::DevBuf nl_ucnt, nl_uoff, nl_units, nl_inc_m, nl_inc_e, nl_slots;
-    int near_sched_ready = 0;  // 0: none, 1: entries sorted, 2: full schedule (for the lists of the last tc_eval)
+    int near_sched_ready = 0;  // bit 1: entries sorted, bit 2: schedule built (for the lists of the last tc_eval)
     tc::DevBuf flags;                   // int32 device error flags at byte 0; work-queue counters
                                         // of the far field (byte 128) and its adjoint's target side (192)
     int64_t far_entries = 0, near_entries = 0;  // list sizes of the last tc_eval
@@ -429,7 +430,7 @@ struct NearSched {
     unsigned* queue;           // device word: the work-queue counter (the caller's)
 };
 // Build the schedule for the lists of the last tc_eval, unless built already;
-// full = 0: only sort the near entries by leaf (nl_keys, nl_idx, nl_eb).
+// full = 0: sort the near entries by leaf instead (nl_keys, nl_idx, nl_eb).
 cudaError_t near_schedule(tc_ctx* ctx, int full, NearSched& sc, cudaStream_t s);
 // Its two halves, for a caller that captures the work in a graph: the
 // buffers (host side, nothing enqueued), then the work (no allocation).

@@ -388,24 +388,14 @@ inline unsigned grid_for(int64_t n, int threads)
 // ---------------------------------------------------------------------------
 // leaf-major schedule (near_schedule)
 
-// incidences of each sorted near entry
-__global__ void k_inc_count(const ListEntry* __restrict__ list, const int32_t* __restrict__ sidx, int64_t E,
-                            int32_t* __restrict__ cnt)
+// incidences per leaf (nA zeroed before)
+__global__ void k_leaf_count(const ListEntry* __restrict__ list, int64_t E, int32_t* __restrict__ nA)
 {
-    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (k < E) cnt[k] = __popc(list[sidx[k]].mask);
-}
-
-// each node's range [k0, k1) of sorted entries (both left 0 for a node in no
-// near list)
-__global__ void k_leaf_bounds(const uint64_t* __restrict__ skeys, int64_t E, int32_t* __restrict__ k0,
-                              int32_t* __restrict__ k1)
-{
-    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (k >= E) return;
-    const uint64_t node = skeys[k];
-    if (k == 0 || skeys[k - 1] != node) k0[node] = (int32_t)k;
-    if (k == E - 1 || skeys[k + 1] != node) k1[node] = (int32_t)(k + 1);
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e < E) {
+        const ListEntry le = list[e];
+        atomicAdd(nA + le.node, __popc(le.mask));
+    }
 }
 
 // sort key of a node in no near list; the others' keys, below it, put the
@@ -413,55 +403,77 @@ __global__ void k_leaf_bounds(const uint64_t* __restrict__ skeys, int64_t E, int
 constexpr uint64_t kLeafKeyNone = 0xffff;
 constexpr int kLeafKeyBits = 16;
 
-// per node: first incidence, incidence count and sort key; ord = identity
-__global__ void k_leaf_units(const int4* __restrict__ topo, int64_t nnodes, const int32_t* __restrict__ k0,
-                             const int32_t* __restrict__ k1, const int64_t* __restrict__ inc0,
-                             int64_t* __restrict__ node_inc0, int32_t* __restrict__ node_A,
-                             uint64_t* __restrict__ key, int32_t* __restrict__ ord)
+// per node its sort key; ord = identity
+__global__ void k_leaf_keys(const int4* __restrict__ topo, int64_t nnodes, const int32_t* __restrict__ nA,
+                            uint64_t* __restrict__ key, int32_t* __restrict__ ord)
 {
     const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (n >= nnodes) return;
-    const int64_t i0 = inc0[k0[n]], A = inc0[k1[n]] - i0;
-    node_inc0[n] = i0;
-    node_A[n] = (int32_t)A;
     const uint64_t size = (uint64_t)topo[n].y;
-    key[n] = A > 0 ? kLeafKeyNone - 1 - (size < kLeafKeyNone - 1 ? size : kLeafKeyNone - 1) : kLeafKeyNone;
+    key[n] = nA[n] > 0 ? kLeafKeyNone - 1 - (size < kLeafKeyNone - 1 ? size : kLeafKeyNone - 1) : kLeafKeyNone;
     ord[n] = (int32_t)n;
 }
 
-// units (pairs of 32-target streams) of the node at sorted position j
-__global__ void k_unit_count(const int32_t* __restrict__ ord, const int32_t* __restrict__ node_A, int64_t nnodes,
-                             int32_t* __restrict__ ucnt)
+// the node at sorted position j: its incidences and its units (pairs of
+// 32-target streams)
+__global__ void k_unit_count(const int32_t* __restrict__ ord, const int32_t* __restrict__ nA, int64_t nnodes,
+                             int32_t* __restrict__ sA, int32_t* __restrict__ ucnt)
 {
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (j < nnodes) ucnt[j] = (node_A[ord[j]] + 63) / 64;
+    if (j >= nnodes) return;
+    const int32_t A = nA[ord[j]];
+    sA[j] = A;
+    ucnt[j] = (A + 63) / 64;
 }
 
+// per node its first incidence (incidences numbered in the sorted node
+// order) and the cursor of the fill; the unit list
 __global__ void k_unit_fill(const int32_t* __restrict__ ord, const int32_t* __restrict__ ucnt,
-                            const int32_t* __restrict__ uoff, int64_t nnodes, int2* __restrict__ units)
+                            const int32_t* __restrict__ uoff, const int64_t* __restrict__ inc0s, int64_t nnodes,
+                            int64_t* __restrict__ node_inc0, unsigned long long* __restrict__ cur,
+                            int2* __restrict__ units)
 {
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (j >= nnodes) return;
     const int node = ord[j], c = ucnt[j];
+    node_inc0[node] = inc0s[j];
+    cur[node] = (unsigned long long)inc0s[j];
     int2* u = units + uoff[j];
     for (int q = 0; q < c; q++) u[q] = make_int2(node, q);
 }
 
-// per incidence its sorted target and its entry: one warp per sorted entry,
-// lane l for the batch's target l
-__global__ void k_inc_fill(const ListEntry* __restrict__ list, const int32_t* __restrict__ sidx,
-                           const int32_t* __restrict__ eb, const int64_t* __restrict__ inc0, int64_t E,
-                           int32_t* __restrict__ inc_m, int32_t* __restrict__ inc_e)
+// Incidences of every entry at its leaf's cursor: one warp per batch, its
+// entries 32 at a time (lane j reserves entry j's places), then entry by
+// entry the lanes of its mask write their target and the entry.  The order of
+// the incidences inside a leaf depends on the order of the atomics, which
+// changes nothing: a target's sums do not depend on its stream.
+__global__ void k_inc_fill(const int64_t* __restrict__ near_off, const ListEntry* __restrict__ list, int64_t nbatch,
+                           unsigned long long* __restrict__ cur, int32_t* __restrict__ inc_m,
+                           int32_t* __restrict__ inc_e)
 {
-    const int64_t k = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t b = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (k >= E) return;
-    const int e = sidx[k];
-    const unsigned mask = list[e].mask;
-    if ((mask >> lane) & 1u) {
-        const int64_t pos = inc0[k] + __popc(mask & ((1u << lane) - 1u));
-        inc_m[pos] = eb[e] * kBatch + lane;
-        inc_e[pos] = e;
+    if (b >= nbatch) return;
+    const unsigned lt = (1u << lane) - 1u;
+    const int64_t e0 = near_off[b], e1 = near_off[b + 1];
+    for (int64_t base = e0; base < e1; base += 32) {
+        const int64_t e = base + lane;
+        ListEntry le{0, 0};
+        unsigned long long pos = 0;
+        if (e < e1) {
+            le = list[e];
+            pos = atomicAdd(cur + le.node, (unsigned long long)__popc(le.mask));
+        }
+        const int cnt = (int)min((int64_t)32, e1 - base);
+        for (int j = 0; j < cnt; j++) {
+            const unsigned mj = __shfl_sync(0xffffffffu, le.mask, j);
+            const unsigned long long pj = __shfl_sync(0xffffffffu, pos, j);
+            if ((mj >> lane) & 1u) {
+                const unsigned long long q = pj + __popc(mj & lt);
+                inc_m[q] = (int32_t)(b * kBatch + lane);
+                inc_e[q] = (int32_t)(base + j);
+            }
+        }
     }
 }
 
@@ -476,18 +488,18 @@ cudaError_t near_schedule_alloc(tc_ctx* ctx, int full)
     cudaError_t e;
     // one histogram buffer for both sorts (entries, nodes)
     if ((e = ensure(ctx->nl_hist, (size_t)256 * radix_blocks(std::max(E, nnodes)) * 4)) != cudaSuccess) return e;
-    if ((e = ensure(ctx->nl_keys, (size_t)E * 8)) != cudaSuccess) return e;
-    if ((e = ensure(ctx->nl_keys_alt, (size_t)E * 8)) != cudaSuccess) return e;
-    if ((e = ensure(ctx->nl_idx, (size_t)E * 4)) != cudaSuccess) return e;
-    if ((e = ensure(ctx->nl_idx_alt, (size_t)E * 4)) != cudaSuccess) return e;
-    if ((e = ensure(ctx->nl_eb, (size_t)E * 4)) != cudaSuccess) return e;
-    if (!full) return cudaSuccess;
-    if ((e = ensure(ctx->nl_cnt, (size_t)(E + 1) * 4)) != cudaSuccess) return e;
-    if ((e = ensure(ctx->nl_inc0, (size_t)(E + 1) * 8)) != cudaSuccess) return e;
-    if ((e = ensure(ctx->nl_k0, (size_t)nnodes * 4)) != cudaSuccess) return e;
-    if ((e = ensure(ctx->nl_k1, (size_t)nnodes * 4)) != cudaSuccess) return e;
-    if ((e = ensure(ctx->nl_ninc0, (size_t)nnodes * 8)) != cudaSuccess) return e;
+    if (!full) {
+        if ((e = ensure(ctx->nl_keys, (size_t)E * 8)) != cudaSuccess) return e;
+        if ((e = ensure(ctx->nl_keys_alt, (size_t)E * 8)) != cudaSuccess) return e;
+        if ((e = ensure(ctx->nl_idx, (size_t)E * 4)) != cudaSuccess) return e;
+        if ((e = ensure(ctx->nl_idx_alt, (size_t)E * 4)) != cudaSuccess) return e;
+        return ensure(ctx->nl_eb, (size_t)E * 4);
+    }
     if ((e = ensure(ctx->nl_nA, (size_t)nnodes * 4)) != cudaSuccess) return e;
+    if ((e = ensure(ctx->nl_sA, (size_t)nnodes * 4)) != cudaSuccess) return e;
+    if ((e = ensure(ctx->nl_inc0s, (size_t)(nnodes + 1) * 8)) != cudaSuccess) return e;
+    if ((e = ensure(ctx->nl_ninc0, (size_t)nnodes * 8)) != cudaSuccess) return e;
+    if ((e = ensure(ctx->nl_cur, (size_t)nnodes * 8)) != cudaSuccess) return e;
     if ((e = ensure(ctx->nl_nkey, (size_t)nnodes * 8)) != cudaSuccess) return e;
     if ((e = ensure(ctx->nl_nkey_alt, (size_t)nnodes * 8)) != cudaSuccess) return e;
     if ((e = ensure(ctx->nl_nord, (size_t)nnodes * 4)) != cudaSuccess) return e;
@@ -497,8 +509,7 @@ cudaError_t near_schedule_alloc(tc_ctx* ctx, int full)
     if ((e = ensure(ctx->nl_units, (size_t)schedule_max_units(ctx) * 8)) != cudaSuccess) return e;
     if ((e = ensure(ctx->nl_inc_m, (size_t)E * 32 * 4)) != cudaSuccess) return e;
     if ((e = ensure(ctx->nl_inc_e, (size_t)E * 32 * 4)) != cudaSuccess) return e;
-    if ((e = ensure(ctx->nl_slots, (size_t)E * 96 * 8)) != cudaSuccess) return e;
-    return cudaSuccess;
+    return ensure(ctx->nl_slots, (size_t)E * 96 * 8);
 }
 
 cudaError_t near_schedule_build(tc_ctx* ctx, int full, cudaStream_t s)
@@ -506,39 +517,37 @@ cudaError_t near_schedule_build(tc_ctx* ctx, int full, cudaStream_t s)
     const int64_t E = ctx->near_entries, nnodes = ctx->nnodes;
     const int64_t nbatch = (ctx->M + kBatch - 1) / kBatch;
     const ListEntry* list = ptr<ListEntry>(ctx->near_list);
-    cudaError_t e = sort_list_entries(list, E, ptr<int64_t>(ctx->near_off), nbatch, nnodes, ctx->nl_keys,
-                                      ctx->nl_keys_alt, ctx->nl_idx, ctx->nl_idx_alt, ctx->nl_eb, ctx->nl_hist, s);
-    if (e != cudaSuccess || !full) return e;
+    cudaError_t e;
+    if (!full)  // the entries sorted by leaf
+        return sort_list_entries(list, E, ptr<int64_t>(ctx->near_off), nbatch, nnodes, ctx->nl_keys, ctx->nl_keys_alt,
+                                 ctx->nl_idx, ctx->nl_idx_alt, ctx->nl_eb, ctx->nl_hist, s);
     int32_t* uoff = ptr<int32_t>(ctx->nl_uoff);
     if (E == 0) return cudaMemsetAsync(uoff + nnodes, 0, 4, s);
-    const int32_t* sidx = ptr<int32_t>(ctx->nl_idx);
-    int64_t* inc0 = ptr<int64_t>(ctx->nl_inc0);
-    k_inc_count<<<grid_for(E, 256), 256, 0, s>>>(list, sidx, E, ptr<int32_t>(ctx->nl_cnt));
+    int32_t* nA = ptr<int32_t>(ctx->nl_nA);
+    int64_t* inc0s = ptr<int64_t>(ctx->nl_inc0s);
+    if ((e = cudaMemsetAsync(nA, 0, (size_t)nnodes * 4, s)) != cudaSuccess) return e;
+    k_leaf_count<<<grid_for(E, 256), 256, 0, s>>>(list, E, nA);
     note_launch();
-    if ((e = launch_scan_i32_to_i64(ptr<int32_t>(ctx->nl_cnt), inc0, E, inc0 + E, s)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(ctx->nl_k0.p, 0, (size_t)nnodes * 4, s)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(ctx->nl_k1.p, 0, (size_t)nnodes * 4, s)) != cudaSuccess) return e;
-    k_leaf_bounds<<<grid_for(E, 256), 256, 0, s>>>(ptr<uint64_t>(ctx->nl_keys), E, ptr<int32_t>(ctx->nl_k0),
-                                                   ptr<int32_t>(ctx->nl_k1));
-    note_launch();
-    k_leaf_units<<<grid_for(nnodes, 256), 256, 0, s>>>(ptr<int4>(ctx->node_topo), nnodes, ptr<int32_t>(ctx->nl_k0),
-                                                       ptr<int32_t>(ctx->nl_k1), inc0, ptr<int64_t>(ctx->nl_ninc0),
-                                                       ptr<int32_t>(ctx->nl_nA), ptr<uint64_t>(ctx->nl_nkey),
-                                                       ptr<int32_t>(ctx->nl_nord));
+    k_leaf_keys<<<grid_for(nnodes, 256), 256, 0, s>>>(ptr<int4>(ctx->node_topo), nnodes, nA,
+                                                      ptr<uint64_t>(ctx->nl_nkey), ptr<int32_t>(ctx->nl_nord));
     note_launch();
     if ((e = radix_sort_bits(ptr<uint64_t>(ctx->nl_nkey), ptr<int32_t>(ctx->nl_nord), ptr<uint64_t>(ctx->nl_nkey_alt),
                              ptr<int32_t>(ctx->nl_nord_alt), ptr<uint32_t>(ctx->nl_hist), nnodes, kLeafKeyBits, s)) !=
         cudaSuccess)
         return e;
-    k_unit_count<<<grid_for(nnodes, 256), 256, 0, s>>>(ptr<int32_t>(ctx->nl_nord), ptr<int32_t>(ctx->nl_nA), nnodes,
-                                                       ptr<int32_t>(ctx->nl_ucnt));
+    k_unit_count<<<grid_for(nnodes, 256), 256, 0, s>>>(ptr<int32_t>(ctx->nl_nord), nA, nnodes,
+                                                       ptr<int32_t>(ctx->nl_sA), ptr<int32_t>(ctx->nl_ucnt));
     note_launch();
+    if ((e = launch_scan_i32_to_i64(ptr<int32_t>(ctx->nl_sA), inc0s, nnodes, inc0s + nnodes, s)) != cudaSuccess)
+        return e;
     if ((e = launch_scan_i32(ptr<int32_t>(ctx->nl_ucnt), uoff, nnodes, uoff + nnodes, s)) != cudaSuccess) return e;
     k_unit_fill<<<grid_for(nnodes, 256), 256, 0, s>>>(ptr<int32_t>(ctx->nl_nord), ptr<int32_t>(ctx->nl_ucnt), uoff,
-                                                      nnodes, ptr<int2>(ctx->nl_units));
+                                                      inc0s, nnodes, ptr<int64_t>(ctx->nl_ninc0),
+                                                      ptr<unsigned long long>(ctx->nl_cur), ptr<int2>(ctx->nl_units));
     note_launch();
-    k_inc_fill<<<grid_for(E * 32, 256), 256, 0, s>>>(list, sidx, ptr<int32_t>(ctx->nl_eb), inc0, E,
-                                                     ptr<int32_t>(ctx->nl_inc_m), ptr<int32_t>(ctx->nl_inc_e));
+    k_inc_fill<<<grid_for(nbatch * 32, 256), 256, 0, s>>>(ptr<int64_t>(ctx->near_off), list, nbatch,
+                                                          ptr<unsigned long long>(ctx->nl_cur),
+                                                          ptr<int32_t>(ctx->nl_inc_m), ptr<int32_t>(ctx->nl_inc_e));
     note_launch();
     return cudaGetLastError();
 }
@@ -561,12 +570,12 @@ NearSched near_schedule_desc(tc_ctx* ctx)
 
 cudaError_t near_schedule(tc_ctx* ctx, int full, NearSched& sc, cudaStream_t s)
 {
-    const int want = full ? 2 : 1;
-    if (ctx->near_sched_ready < want) {
+    const int want = full ? 2 : 1;  // bit 1: entries sorted, bit 2: schedule built
+    if (!(ctx->near_sched_ready & want)) {
         cudaError_t e = near_schedule_alloc(ctx, full);
         if (e == cudaSuccess) e = near_schedule_build(ctx, full, s);
         if (e != cudaSuccess) return e;
-        ctx->near_sched_ready = want;
+        ctx->near_sched_ready |= want;
     }
     sc = near_schedule_desc(ctx);
     return cudaSuccess;
