@@ -225,6 +225,29 @@ def test_treecode_disjoint_targets(prec):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_targets_with_no_near_field(prec):
+    # every target far from the sources: the root cluster passes the MAC for
+    # all of them, so the near lists are empty (no near entries at all) and the
+    # near field must give exactly zero; then one target inside the cube among
+    # them (one batch with near entries)
+    x, f, h, nu = inputs.uniform_cube(3000, 71)
+    t = np.random.default_rng(72).uniform(5.0, 6.0, (1000, 3))
+    u, nf, nn, _ = _run(prec, x, f, h, nu, 64, 5, 0.5, targets=t)
+    tree = oracle.Tree(x, 64, True)
+    tree.set_moments(f, h, nu, 5)
+    ref, cnt = tree.treecode(t, 0.5, 5, counts=True)
+    assert nn.sum() == 0
+    np.testing.assert_array_equal(nf, cnt["far"])
+    assert oracle.rel_l2(u, ref) <= TOL[prec]
+    t[500] = [0.5, 0.5, 0.5]
+    u, nf, nn, _ = _run(prec, x, f, h, nu, 64, 5, 0.5, targets=t)
+    ref, cnt = tree.treecode(t, 0.5, 5, counts=True)
+    np.testing.assert_array_equal(nn, cnt["near_pairs"])
+    assert nn.sum() == cnt["near_pairs"][500] > 0
+    assert oracle.rel_l2(u, ref) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_offset_and_duplicated_points(prec):
     # coordinates far from the origin (FP32 keeps only ~1e-4 absolute there)
     # and exact duplicates: every coincident pair must still be skipped and
