@@ -343,7 +343,7 @@ def bench_fwd_adjoint(flush, stream, steps=3):
         roof("k_near_leaf<NearOpG> (near field, target side)", NEAR_ADJ_TARGET_FLOPS * st["near_pairs"],
              ph["adj_near_target"],
              "%g flops per near pair" % NEAR_ADJ_TARGET_FLOPS),
-        roof("k_near_adj_source32 (near field, source side)", NEAR_ADJ_SOURCE_FLOPS * st["near_pairs"],
+        roof("k_near_adj_source_units (near field, source side)", NEAR_ADJ_SOURCE_FLOPS * st["near_pairs"],
              ph["adj_near_source"],
              "%g flops per near pair" % NEAR_ADJ_SOURCE_FLOPS),
         roof("k_far_adj_target32 (far field, target side)", far_f * st["far_interactions"], ph["adj_far_target"],

@@ -51,6 +51,14 @@ namespace {
 __constant__ LevelConst c_lev = make_level_const();
 __constant__ LevelConst32 c_lev32 = make_level_const32();
 
+inline int sm_count_adj()
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+}
+
 inline unsigned grid_for(int64_t n, int threads)
 {
     int64_t g = (n + threads - 1) / threads;
@@ -337,134 +345,156 @@ struct NearOpG {
 };
 
 
-// source side over the near entries sorted by leaf, in chunks of
-// kNearAdjChunk entries (a chunk can straddle leaves): for each leaf segment
-// of its chunk a block runs a warp per 32 of the leaf's sources over the
-// segment's entries; each entry's 32 targets are staged and every lane runs
-// over all of them, two per packed instruction (lanes outside the entry's
-// mask carry g = 0, which zeroes their terms, so the loop stays uniform).
-// Per-segment sums are added to the FP64 source gradients with atomics (gnear
-// is zeroed first).
-constexpr int kNearAdjChunk = 64;
+// Source side, on the leaf-major schedule of the forward near field: a unit
+// is (leaf, tile of 32 of its sources, segment of kAdjSeg of its incidences);
+// a warp holds one source per lane and runs over the segment's targets in
+// chunks of 32, staged in shared memory (positions as FP32 hi/lo, g), two
+// targets per packed instruction; a chunk's terms are summed by compensated
+// FP32 summation and a unit's sums added to the FP64 source gradients with
+// atomics (gnear is zeroed first).  The units of a leaf are numbered from
+// its first unit soff[leaf] (k_adj_src_count + scan), tile-minor.
+constexpr int kAdjSeg = 1024;
+constexpr int kAdjSrcWarps = 4;
 
-__global__ void __launch_bounds__(kNearAdjWarps * 32)
-    k_near_adj_source32(const double* __restrict__ ts, const double* __restrict__ gs, int64_t M,
-                        const int4* __restrict__ topo, const float4* __restrict__ spack, int64_t N,
-                        const uint64_t* __restrict__ skeys, const int32_t* __restrict__ sidx,
-                        const ListEntry* __restrict__ near_list, const int32_t* __restrict__ ebatch, int64_t nent,
-                        double* __restrict__ gnear)
+// units of each node: tiles of 32 sources x segments of its incidences
+__global__ void k_adj_src_count(const int4* __restrict__ topo, const int32_t* __restrict__ node_A, int64_t nnodes,
+                                int32_t* __restrict__ cnt)
+{
+    const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (n >= nnodes) return;
+    const int A = node_A[n];
+    cnt[n] = A > 0 ? ((topo[n].y + 31) / 32) * ((A + kAdjSeg - 1) / kAdjSeg) : 0;
+}
+
+// The source-side terms of the lane's source (sh/sl: position hi/lo; f, h,
+// nu) against staged targets q, q+1 (T: their 9 fields as pairs), added to
+// a[12]: dL/df (3), dL/dh (3), dL/dnu (3), dL/dy (3).
+__device__ __forceinline__ void adj_src_pair(const float2 (&T)[9], const float2 (&sh)[3], const float2 (&sl)[3],
+                                             const float2 (&f)[3], const float2 (&h)[3], const float2 (&n)[3],
+                                             float2 (&a)[12])
+{
+    using nearpair::sub2;
+    const float2 dx = __fadd2_rn(sub2(T[0], sh[0]), sub2(T[3], sl[0]));
+    const float2 dy = __fadd2_rn(sub2(T[1], sh[1]), sub2(T[4], sl[1]));
+    const float2 dz = __fadd2_rn(sub2(T[2], sh[2]), sub2(T[5], sl[2]));
+    const float2 g0 = T[6], g1 = T[7], g2 = T[8];
+    const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+    float2 ri;
+    ri.x = r2.x > 0.f ? rsqrt_ftz(r2.x) : 0.f;
+    ri.y = r2.y > 0.f ? rsqrt_ftz(r2.y) : 0.f;
+    const float2 ri2 = __fmul2_rn(ri, ri), ri3 = __fmul2_rn(ri2, ri), ri5 = __fmul2_rn(ri3, ri2);
+    const float2 df = __ffma2_rn(dx, f[0], __ffma2_rn(dy, f[1], __fmul2_rn(dz, f[2])));
+    const float2 dh = __ffma2_rn(dx, h[0], __ffma2_rn(dy, h[1], __fmul2_rn(dz, h[2])));
+    const float2 dn = __ffma2_rn(dx, n[0], __ffma2_rn(dy, n[1], __fmul2_rn(dz, n[2])));
+    const float2 gd = __ffma2_rn(dx, g0, __ffma2_rn(dy, g1, __fmul2_rn(dz, g2)));
+    const float2 gf = __ffma2_rn(g0, f[0], __ffma2_rn(g1, f[1], __fmul2_rn(g2, f[2])));
+    const float2 t5 = __fmul2_rn(__fmul2_rn(dh, dn), ri5);
+    const float2 st = __ffma2_rn(df, ri3, t5);
+    const float2 c3 = __fmul2_rn(gd, ri3);
+    const float2 inner =
+        __ffma2_rn(__fmul2_rn(make_float2(3.f, 3.f), df), ri3, __fmul2_rn(make_float2(5.f, 5.f), t5));
+    const float2 c1n = __ffma2_rn(gf, ri3, __fmul2_rn(__fmul2_rn(gd, ri2), inner));  // -c1
+    const float2 c4 = __fmul2_rn(__fmul2_rn(c3, dn), ri2);
+    const float2 c5 = __fmul2_rn(__fmul2_rn(c3, dh), ri2);
+    a[0] = __ffma2_rn(g0, ri, __ffma2_rn(dx, c3, a[0]));
+    a[1] = __ffma2_rn(g1, ri, __ffma2_rn(dy, c3, a[1]));
+    a[2] = __ffma2_rn(g2, ri, __ffma2_rn(dz, c3, a[2]));
+    a[3] = __ffma2_rn(dx, c4, a[3]);
+    a[4] = __ffma2_rn(dy, c4, a[4]);
+    a[5] = __ffma2_rn(dz, c4, a[5]);
+    a[6] = __ffma2_rn(dx, c5, a[6]);
+    a[7] = __ffma2_rn(dy, c5, a[7]);
+    a[8] = __ffma2_rn(dz, c5, a[8]);
+    // dL/dy = -d(g.K)/dd = -(d c1 + g st + f c3 + h c4 + nu c5)
+    a[9] = __ffma2_rn(dx, c1n, sub2(a[9], __ffma2_rn(g0, st, __ffma2_rn(f[0], c3,
+                                       __ffma2_rn(h[0], c4, __fmul2_rn(n[0], c5))))));
+    a[10] = __ffma2_rn(dy, c1n, sub2(a[10], __ffma2_rn(g1, st, __ffma2_rn(f[1], c3,
+                                        __ffma2_rn(h[1], c4, __fmul2_rn(n[1], c5))))));
+    a[11] = __ffma2_rn(dz, c1n, sub2(a[11], __ffma2_rn(g2, st, __ffma2_rn(f[2], c3,
+                                        __ffma2_rn(h[2], c4, __fmul2_rn(n[2], c5))))));
+}
+
+__global__ void __launch_bounds__(kAdjSrcWarps * 32)
+    k_near_adj_source_units(const double* __restrict__ ts, const double* __restrict__ gs, int64_t M,
+                            const int4* __restrict__ topo, const float4* __restrict__ spack, int64_t N,
+                            int64_t nnodes, const int64_t* __restrict__ soff, const int64_t* __restrict__ node_inc0,
+                            const int32_t* __restrict__ node_A, const int32_t* __restrict__ inc_m,
+                            double* __restrict__ gnear, unsigned long long* __restrict__ queue)
 {
     // staged targets, field-major: x_hi (3), x_lo (3), g (3); targets q, q+1
     // are read together as one float2 per field
-    __shared__ __align__(8) float tile[kNearAdjWarps][9][32];
+    __shared__ __align__(8) float tile[kAdjSrcWarps][9][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t c0 = (int64_t)blockIdx.x * kNearAdjChunk;
-    const int64_t c1 = min(nent, c0 + kNearAdjChunk);
-    for (int64_t js = c0; js < c1;) {
-        const uint64_t node = skeys[js];
-        const int64_t je = min(c1, lower_key(skeys, nent, node + 1));
-        const int4 t = topo[node];
-        for (int tile0 = w * 32; tile0 < t.y; tile0 += kNearAdjWarps * 32) {
-            const int64_t si = t.x + tile0 + lane;
-            const bool valid = tile0 + lane < t.y;
-            float4 A = make_float4(0, 0, 0, 0), B = A, C = A, D = A;
-            if (valid) {
-                const float4* src = spack + 4 * si;
-                A = src[0], B = src[1], C = src[2], D = src[3];
-            }
-            // this lane's source, replicated into both halves of each pair
-            const float2 sh0 = make_float2(A.x, A.x), sh1 = make_float2(A.y, A.y), sh2 = make_float2(A.z, A.z);
-            const float2 sl0 = make_float2(B.x, B.x), sl1 = make_float2(B.y, B.y), sl2 = make_float2(B.z, B.z);
-            const float2 f0 = make_float2(A.w, A.w), f1 = make_float2(B.w, B.w), f2 = make_float2(C.x, C.x);
-            const float2 h0 = make_float2(C.y, C.y), h1 = make_float2(C.z, C.z), h2 = make_float2(C.w, C.w);
-            const float2 n0 = make_float2(D.x, D.x), n1 = make_float2(D.y, D.y), n2 = make_float2(D.z, D.z);
-            // per-entry partial sums, accumulated by compensated FP32 summation
-            float acc[12], cmp[12];
-#pragma unroll
-            for (int c = 0; c < 12; c++) acc[c] = cmp[c] = 0.f;
-            for (int64_t j = js; j < je; j++) {
-                const int32_t e = sidx[j];
-                const unsigned mask = near_list[e].mask;
-                const int64_t m = (int64_t)ebatch[e] * kBatch + lane;
-                __syncwarp();
-                // the entry's targets (the lanes of its mask) are packed
-                // densely into the first A slots; slot A, when A is odd, holds
-                // a zero-weight target (written by the lowest lane outside the
-                // mask, whose record is all zeros) so that pairs stay whole
-                const int A = __popc(mask);
-                const int pad_lane = __ffs(~mask) - 1;  // -1 when all 32 are in
-                {
-                    const bool on = (mask >> lane) & 1u;
-                    float v[9];
-#pragma unroll
-                    for (int k = 0; k < 9; k++) v[k] = 0.f;
-                    if (on)
-                        for (int a = 0; a < 3; a++) {
-                            const double x = ts[a * M + m];
-                            v[a] = __double2float_rn(x);
-                            v[3 + a] = __double2float_rn(x - (double)v[a]);
-                            v[6 + a] = __double2float_rn(gs[a * M + m]);
-                        }
-                    const int slot = on ? __popc(mask & ((1u << lane) - 1u)) : (lane == pad_lane ? A : -1);
-                    if (slot >= 0 && slot < 32)
-#pragma unroll
-                        for (int k = 0; k < 9; k++) tile[w][k][slot] = v[k];
-                }
-                __syncwarp();
-                float2 a[12];
-#pragma unroll
-                for (int c = 0; c < 12; c++) a[c] = make_float2(0.f, 0.f);
-                for (int q = 0; q < A; q += 2) {
-                    float2 T[9];
-#pragma unroll
-                    for (int k = 0; k < 9; k++) T[k] = *reinterpret_cast<const float2*>(&tile[w][k][q]);
-                    using nearpair::sub2;
-                    const float2 dx = __fadd2_rn(sub2(T[0], sh0), sub2(T[3], sl0));
-                    const float2 dy = __fadd2_rn(sub2(T[1], sh1), sub2(T[4], sl1));
-                    const float2 dz = __fadd2_rn(sub2(T[2], sh2), sub2(T[5], sl2));
-                    const float2 g0 = T[6], g1 = T[7], g2 = T[8];
-                    const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
-                    float2 ri;
-                    ri.x = r2.x > 0.f ? rsqrt_ftz(r2.x) : 0.f;
-                    ri.y = r2.y > 0.f ? rsqrt_ftz(r2.y) : 0.f;
-                    const float2 ri2 = __fmul2_rn(ri, ri), ri3 = __fmul2_rn(ri2, ri), ri5 = __fmul2_rn(ri3, ri2);
-                    const float2 df = __ffma2_rn(dx, f0, __ffma2_rn(dy, f1, __fmul2_rn(dz, f2)));
-                    const float2 dh = __ffma2_rn(dx, h0, __ffma2_rn(dy, h1, __fmul2_rn(dz, h2)));
-                    const float2 dn = __ffma2_rn(dx, n0, __ffma2_rn(dy, n1, __fmul2_rn(dz, n2)));
-                    const float2 gd = __ffma2_rn(dx, g0, __ffma2_rn(dy, g1, __fmul2_rn(dz, g2)));
-                    const float2 gf = __ffma2_rn(g0, f0, __ffma2_rn(g1, f1, __fmul2_rn(g2, f2)));
-                    const float2 t5 = __fmul2_rn(__fmul2_rn(dh, dn), ri5);
-                    const float2 st = __ffma2_rn(df, ri3, t5);
-                    const float2 c3 = __fmul2_rn(gd, ri3);
-                    const float2 inner =
-                        __ffma2_rn(__fmul2_rn(make_float2(3.f, 3.f), df), ri3, __fmul2_rn(make_float2(5.f, 5.f), t5));
-                    const float2 c1n = __ffma2_rn(gf, ri3, __fmul2_rn(__fmul2_rn(gd, ri2), inner));  // -c1
-                    const float2 c4 = __fmul2_rn(__fmul2_rn(c3, dn), ri2);
-                    const float2 c5 = __fmul2_rn(__fmul2_rn(c3, dh), ri2);
-                    a[0] = __ffma2_rn(g0, ri, __ffma2_rn(dx, c3, a[0]));
-                    a[1] = __ffma2_rn(g1, ri, __ffma2_rn(dy, c3, a[1]));
-                    a[2] = __ffma2_rn(g2, ri, __ffma2_rn(dz, c3, a[2]));
-                    a[3] = __ffma2_rn(dx, c4, a[3]);
-                    a[4] = __ffma2_rn(dy, c4, a[4]);
-                    a[5] = __ffma2_rn(dz, c4, a[5]);
-                    a[6] = __ffma2_rn(dx, c5, a[6]);
-                    a[7] = __ffma2_rn(dy, c5, a[7]);
-                    a[8] = __ffma2_rn(dz, c5, a[8]);
-                    // dL/dy = -d(g.K)/dd = -(d c1 + g st + f c3 + h c4 + nu c5)
-                    a[9] = __ffma2_rn(dx, c1n, sub2(a[9], __ffma2_rn(g0, st, __ffma2_rn(f0, c3,
-                                                       __ffma2_rn(h0, c4, __fmul2_rn(n0, c5))))));
-                    a[10] = __ffma2_rn(dy, c1n, sub2(a[10], __ffma2_rn(g1, st, __ffma2_rn(f1, c3,
-                                                        __ffma2_rn(h1, c4, __fmul2_rn(n1, c5))))));
-                    a[11] = __ffma2_rn(dz, c1n, sub2(a[11], __ffma2_rn(g2, st, __ffma2_rn(f2, c3,
-                                                        __ffma2_rn(h2, c4, __fmul2_rn(n2, c5))))));
-                }
-#pragma unroll
-                for (int c = 0; c < 12; c++) kahan_add(acc[c], cmp[c], a[c].x + a[c].y);
-            }
-            if (valid)
-                for (int c = 0; c < 12; c++) atomicAdd(&gnear[c * N + si], (double)acc[c] - (double)cmp[c]);
+    const int64_t nunits = soff[nnodes];
+    for (;;) {
+        unsigned long long u = 0;
+        if (lane == 0) u = atomicAdd(queue, 1ull);
+        u = __shfl_sync(0xffffffffu, u, 0);
+        if ((int64_t)u >= nunits) break;
+        int64_t lo = 0, hi = nnodes;  // soff[lo] <= u < soff[hi]; nodes without units share offsets
+        while (hi - lo > 1) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (soff[mid] <= (int64_t)u)
+                lo = mid;
+            else
+                hi = mid;
         }
-        js = je;
+        const int4 t = topo[lo];
+        const int S = (t.y + 31) / 32;
+        const int64_t r = (int64_t)u - soff[lo];
+        const int tile_s = (int)(r % S), seg = (int)(r / S);
+        const int64_t I0 = node_inc0[lo];
+        const int k0 = seg * kAdjSeg, k1 = min(node_A[lo], k0 + kAdjSeg);
+        const int64_t si = t.x + 32 * tile_s + lane;
+        const bool valid = 32 * tile_s + lane < t.y;
+        float4 A = make_float4(0, 0, 0, 0), B = A, C = A, D = A;
+        if (valid) {
+            const float4* src = spack + 4 * si;
+            A = src[0], B = src[1], C = src[2], D = src[3];
+        }
+        // this lane's source, replicated into both halves of each pair
+        const float2 sh[3] = {make_float2(A.x, A.x), make_float2(A.y, A.y), make_float2(A.z, A.z)};
+        const float2 sl[3] = {make_float2(B.x, B.x), make_float2(B.y, B.y), make_float2(B.z, B.z)};
+        const float2 f[3] = {make_float2(A.w, A.w), make_float2(B.w, B.w), make_float2(C.x, C.x)};
+        const float2 h[3] = {make_float2(C.y, C.y), make_float2(C.z, C.z), make_float2(C.w, C.w)};
+        const float2 n[3] = {make_float2(D.x, D.x), make_float2(D.y, D.y), make_float2(D.z, D.z)};
+        float acc[12], cmp[12];
+#pragma unroll
+        for (int c = 0; c < 12; c++) acc[c] = cmp[c] = 0.f;
+        for (int kc = k0; kc < k1; kc += 32) {
+            const int cnt = min(32, k1 - kc);
+            __syncwarp();
+            {
+                float v[9];
+#pragma unroll
+                for (int k = 0; k < 9; k++) v[k] = 0.f;  // past cnt: a zero-weight target, zero terms
+                if (lane < cnt) {
+                    const int64_t m = inc_m[I0 + kc + lane];
+                    for (int a = 0; a < 3; a++) {
+                        const double x = ts[a * M + m];
+                        v[a] = __double2float_rn(x);
+                        v[3 + a] = __double2float_rn(x - (double)v[a]);
+                        v[6 + a] = __double2float_rn(gs[a * M + m]);
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < 9; k++) tile[w][k][lane] = v[k];
+            }
+            __syncwarp();
+            float2 a[12];
+#pragma unroll
+            for (int c = 0; c < 12; c++) a[c] = make_float2(0.f, 0.f);
+            for (int q = 0; q < cnt; q += 2) {
+                float2 T[9];
+#pragma unroll
+                for (int k = 0; k < 9; k++) T[k] = *reinterpret_cast<const float2*>(&tile[w][k][q]);
+                adj_src_pair(T, sh, sl, f, h, n, a);
+            }
+#pragma unroll
+            for (int c = 0; c < 12; c++) kahan_add(acc[c], cmp[c], a[c].x + a[c].y);
+        }
+        if (valid)
+            for (int c = 0; c < 12; c++) atomicAdd(&gnear[c * N + si], (double)acc[c] - (double)cmp[c]);
     }
 }
 
@@ -1363,10 +1393,25 @@ extern "C" tc_status tc_adjoint(tc_ctx* ctx, const double* g, double* grad_f, do
         ph_end(ctx, TC_PH_ADJ_NEAR_T);
         ph_begin(ctx, TC_PH_ADJ_NEAR_S);
         TC_CK(cudaMemsetAsync(ctx->adj_gnear.p, 0, (size_t)12 * N * 8, s), "zero near gradients");
-        k_near_adj_source32<<<grid_for(ctx->near_entries, kNearAdjChunk), kNearAdjWarps * 32, 0, s>>>(
-            ts, ptr<double>(ctx->adj_gs), M, ptr<int4>(ctx->node_topo), ptr<float4>(ctx->spack), N,
-            ptr<uint64_t>(ctx->nl_keys), ptr<int32_t>(ctx->nl_idx), ptr<ListEntry>(ctx->near_list),
-            ptr<int32_t>(ctx->nl_eb), ctx->near_entries, ptr<double>(ctx->adj_gnear));
+        TC_CK(ensure(ctx->adj_scnt, (size_t)nnodes * 4), "alloc adjoint");
+        TC_CK(ensure(ctx->adj_soff, (size_t)(nnodes + 1) * 8), "alloc adjoint");
+        int64_t* soff = ptr<int64_t>(ctx->adj_soff);
+        k_adj_src_count<<<grid_for(nnodes, 256), 256, 0, s>>>(ptr<int4>(ctx->node_topo), sched.node_A, nnodes,
+                                                              ptr<int32_t>(ctx->adj_scnt));
+        note_launch();
+        TC_CK(launch_scan_i32_to_i64(ptr<int32_t>(ctx->adj_scnt), soff, nnodes, soff + nnodes, s), "source units");
+        unsigned long long* squeue = reinterpret_cast<unsigned long long*>(ptr<char>(ctx->flags) + 240);
+        TC_CK(cudaMemsetAsync(squeue, 0, sizeof(unsigned long long), s), "source queue");
+        static int src_blocks = 0;
+        if (src_blocks == 0) {
+            int per_sm = 0;
+            TC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_near_adj_source_units, kAdjSrcWarps * 32, 0),
+                  "source grid");
+            src_blocks = (per_sm > 0 ? per_sm : 1) * sm_count_adj();
+        }
+        k_near_adj_source_units<<<(unsigned)src_blocks, kAdjSrcWarps * 32, 0, s>>>(
+            ts, ptr<double>(ctx->adj_gs), M, ptr<int4>(ctx->node_topo), ptr<float4>(ctx->spack), N, nnodes, soff,
+            sched.node_inc0, sched.node_A, sched.inc_m, ptr<double>(ctx->adj_gnear), squeue);
         note_launch();
     }
     ph_end(ctx, TC_PH_ADJ_NEAR_S);

@@ -122,7 +122,7 @@ static void release_all(tc_ctx* c)
                       &c->nl_nA, &c->nl_nkey, &c->nl_nkey_alt, &c->nl_nord, &c->nl_nord_alt, &c->nl_sA,
                       &c->nl_inc0s, &c->nl_ninc0, &c->nl_cur, &c->nl_ucnt, &c->nl_uoff, &c->nl_units,
                       &c->nl_inc_m, &c->nl_inc_e, &c->nl_slots, &c->flags, &c->adj_fkeys, &c->adj_fkeys_alt,
-                      &c->adj_fidx, &c->adj_fidx_alt, &c->adj_febatch, &c->adj_hist, &c->adj_gs, &c->adj_gt, &c->adj_abar, &c->adj_fbar, &c->adj_lam,
+                      &c->adj_fidx, &c->adj_fidx_alt, &c->adj_febatch, &c->adj_hist, &c->adj_scnt, &c->adj_soff, &c->adj_gs, &c->adj_gt, &c->adj_abar, &c->adj_fbar, &c->adj_lam,
                       &c->adj_lamacc, &c->adj_gfar, &c->adj_gnear, &c->host_in, &c->host_u};
     for (DevBuf* b : bufs) release(*b);
 }

@@ -206,6 +206,7 @@ struct tc_ctx {
     // ---- adjoint (tc_adjoint)
     tc::DevBuf adj_fkeys, adj_fkeys_alt, adj_fidx, adj_fidx_alt, adj_febatch;  // far entries sorted by cluster
     tc::DevBuf adj_hist;
+    tc::DevBuf adj_scnt, adj_soff;        // near source side: units per leaf and their offsets
     tc::DevBuf adj_gs, adj_gt;            // 3*M sorted g and target-position gradient
     tc::DevBuf adj_abar;                  // FP64 [node][ncoef(p+2)][12] adjoint of the tables
     tc::DevBuf adj_fbar;                  // FP64 [node][(p+3)^2][12] adjoint of the folded tables (mixed)
