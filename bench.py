@@ -510,10 +510,10 @@ def bench_fig3(flush, stream):
 def bench_regularized(flush, stream):
     """Regularized Stokeslet and stresslet (tc_config.reg_eps) on the headline
     workload: N = 1,000,000 uniform in the unit cube, p = 8, theta = 0.5,
-    N0 = 2000, eps = 1e-3 (a tenth of the mean spacing), mixed precision (the
-    regularized far field runs in FP64): time of build + moments + eval, the
-    far and near phases alone, and E against the FP64 regularized direct sum
-    on 2000 sampled targets."""
+    N0 = 2000, eps = 1e-3 (a tenth of the mean spacing), mixed precision (FP32
+    far and near fields): time of build + moments + eval, the far and near
+    phases alone, and E against the FP64 regularized direct sum on 2000
+    sampled targets."""
     import numpy as np
     import torch
 
@@ -546,22 +546,21 @@ def bench_regularized(flush, stream):
     it = torch.from_numpy(idx).cuda()
     E = float(torch.linalg.norm(u[:, it] - ud) / torch.linalg.norm(ud))
     ms = statistics.mean(times)
-    peak64 = api.fma_peak("fp64", stream)
     peak32 = api.fma_peak("mixed", stream)
-    # FP64 far field per interaction: the recurrences of G_1/2 (orders <= p+2)
-    # and G_3/2 (orders <= p+1) at 11 flops per coefficient, the contractions
-    # at 24 and 6 flops per coefficient, d'.B 18
+    # far field per interaction: the recurrences of G_1/2 (orders <= p+2) and
+    # G_3/2 (orders <= p+1) at 11 flops per coefficient, the contractions at
+    # 24 and 6 flops per coefficient, d'.B 18
     far_unit = 35 * ncoef(p + 2) + 17 * ncoef(p + 1) + 18
     far_tf = far_unit * st["far_interactions"] / (ph["far"] / 1e3) / 1e12
     near_tf = REG_NEAR_PAIR_FLOPS * st["near_pairs"] / (ph["near"] / 1e3) / 1e12
     return {"workload": "regularized kernels, eps=1e-3, uniform cube N=1000000, p=8, theta=0.5, N0=2000, mixed "
-                        "(FP64 far field)",
+                        "(FP32 far and near fields)",
             "ms_per_step": ms, "targets_per_s": N / (ms / 1e3), "far_ms": ph["far"], "near_ms": ph["near"],
             "far_interactions": st["far_interactions"], "near_pairs": st["near_pairs"],
             "E_vs_fp64_regularized_direct": E, "E_samples": int(len(idx)),
             "roofline": [
-                {"kernel": "k_far_reg (FP64)", "bound": "alu", "achieved": far_tf, "peak": peak64, "unit": "TFLOP/s",
-                 "frac": far_tf / peak64, "work_unit": "%d FP64 flops per far interaction" % far_unit},
+                {"kernel": "k_far_reg32", "bound": "alu", "achieved": far_tf, "peak": peak32, "unit": "TFLOP/s",
+                 "frac": far_tf / peak32, "work_unit": "%d flops per far interaction" % far_unit},
                 {"kernel": "k_near_leaf<NearOpReg>", "bound": "alu", "achieved": near_tf, "peak": peak32,
                  "unit": "TFLOP/s", "frac": near_tf / peak32,
                  "work_unit": "%d flops per near pair" % REG_NEAR_PAIR_FLOPS}]}

@@ -115,7 +115,7 @@ static void release_all(tc_ctx* c)
                       &c->split_cnt,
                       &c->split_off, &c->scan_tmp, &c->ws, &c->spack, &c->mom, &c->mom_tmp, &c->ab64, &c->ab32,
                       &c->abf64,
-                      &c->abf32, &c->geo32, &c->reg_et, &c->tkeys,
+                      &c->abf32, &c->geo32, &c->reg_et, &c->reg_et32, &c->tkeys,
                       &c->tkeys_alt, &c->tperm, &c->tperm_alt, &c->ts, &c->nfar_e, &c->nnear_e,
                       &c->far_off, &c->near_off, &c->far_list, &c->near_list, &c->cnt_far, &c->cnt_near, &c->u_far,
                       &c->u_near, &c->nl_keys, &c->nl_keys_alt, &c->nl_idx, &c->nl_idx_alt, &c->nl_eb, &c->nl_hist,
@@ -435,6 +435,11 @@ static tc_status ensure_tables(tc_ctx* ctx, int p, cudaStream_t s)
         TC_CK(launch_eps_table(ptr<double>(ctx->mom), ptr<double>(ctx->node_invrho), ctx->nnodes, ctx->p_mom, p,
                                ctx->reg_eps, ptr<double>(ctx->reg_et), s),
               "eps table");
+        if (ctx->precision == TC_MIXED) {
+            const int64_t ne = ctx->nnodes * ncoef(p + 1) * 3;
+            TC_CK(ensure(ctx->reg_et32, (size_t)ne * 4), "alloc tables");
+            TC_CK(launch_narrow_table(ptr<double>(ctx->reg_et), ne, ptr<float>(ctx->reg_et32), s), "eps table");
+        }
     }
     ph_end(ctx, TC_PH_TABLES, s);
     ctx->ab_p = p;
@@ -607,7 +612,12 @@ tc_status tc::eval_compute(tc_ctx* ctx, double* u)
     TC_CK(cudaEventRecord(ctx->ev_fork, s), "fork");
     TC_CK(cudaStreamWaitEvent(s2, ctx->ev_fork, 0), "fork");
     ph_begin(ctx, TC_PH_FAR, s2);
-    if (ctx->reg_eps > 0.0)
+    if (ctx->reg_eps > 0.0 && ctx->precision == TC_MIXED && !(ctx->rec64 && p >= 8))
+        TC_CK(launch_far_reg32(ts, M, ptr<float4>(ctx->geo32), ptr<float>(ctx->ab32), ptr<float>(ctx->reg_et32), p,
+                               ctx->reg_eps, ptr<int64_t>(ctx->far_off), ptr<ListEntry>(ctx->far_list),
+                               ptr<double>(ctx->u_far), s2),
+              "far field");
+    else if (ctx->reg_eps > 0.0)
         TC_CK(launch_far_reg(ts, M, ptr<Geo>(ctx->node_geo), ptr<double>(ctx->node_invrho), ptr<double>(ctx->ab64),
                              ptr<double>(ctx->reg_et), p, ctx->reg_eps, ptr<int64_t>(ctx->far_off),
                              ptr<ListEntry>(ctx->far_list), ptr<double>(ctx->u_far), s2),

@@ -166,6 +166,7 @@ struct tc_ctx {
     tc::DevBuf abf64, abf32;            // folded tables [node][(p+3)^2][12], level n times lambda_n
     tc::DevBuf geo32;                   // mixed: per node (y_c hi, 1/rho), (y_c lo, 0) as float4
     tc::DevBuf reg_et;                  // regularized kernels: FP64 [node][ncoef(p+1)][3] eps^2 table
+    tc::DevBuf reg_et32;                // its FP32 copy (mixed precision)
     double reg_eps = 0.0;               // > 0: regularized kernels (tc_config.reg_eps)
     int64_t* host_words = nullptr;      // pinned: far and near list totals, device flags
     int counted = 0;                    // eval_prepare_count done, finish pending
@@ -457,6 +458,12 @@ cudaError_t launch_near(int precision, const double* ts, int64_t M, const int4* 
 cudaError_t launch_far_reg(const double* ts, int64_t M, const Geo* geo, const double* invrho, const double* ab64,
                            const double* et, int p, double eps, const int64_t* far_off, const ListEntry* far_list,
                            double* u_far, cudaStream_t s);
+// the same in FP32 (mixed precision) on the FP32 tables ab32 and et32
+cudaError_t launch_far_reg32(const double* ts, int64_t M, const float4* geo32, const float* ab32, const float* et32,
+                             int p, double eps, const int64_t* far_off, const ListEntry* far_list, double* u_far,
+                             cudaStream_t s);
+// dst = the FP32 rounding of the n FP64 values src (as the FP32 contraction tables are rounded)
+cudaError_t launch_narrow_table(const double* src, int64_t n, float* dst, cudaStream_t s);
 cudaError_t launch_finalize(const double* u_far, const double* u_near, const int32_t* perm, int64_t M, double* u,
                             cudaStream_t s);
 cudaError_t launch_scatter_counts(const int64_t* cs, const int32_t* perm, int64_t M, int64_t* out,
