@@ -559,7 +559,7 @@ def bench_regularized(flush, stream):
             "far_interactions": st["far_interactions"], "near_pairs": st["near_pairs"],
             "E_vs_fp64_regularized_direct": E, "E_samples": int(len(idx)),
             "roofline": [
-                {"kernel": "k_far_reg32", "bound": "alu", "achieved": far_tf, "peak": peak32, "unit": "TFLOP/s",
+                {"kernel": "k_far_reg32r<10>", "bound": "alu", "achieved": far_tf, "peak": peak32, "unit": "TFLOP/s",
                  "frac": far_tf / peak32, "work_unit": "%d flops per far interaction" % far_unit},
                 {"kernel": "k_near_leaf<NearOpReg>", "bound": "alu", "achieved": near_tf, "peak": peak32,
                  "unit": "TFLOP/s", "frac": near_tf / peak32,

@@ -194,6 +194,120 @@ __global__ void __launch_bounds__(32)
     }
 }
 
+// FP32, compile-time order P (p + 2 <= 10; above, the shared-memory store
+// of k_far_reg32): both live levels of the coefficients in registers (the
+// recurrence fully unrolled, level n overwriting level n-2 in place,
+// positions running downward), the tables read as float4 when W = 12.
+// NU2 = 2 nu.
+
+template <int P, int W, int NU2>
+__device__ __forceinline__ void reg_pass_r(float sp, float d0, float d1, float d2, const float* __restrict__ tab,
+                                           float (&tot)[W])
+{
+    constexpr int L = (P + 1) * (P + 2) / 2;  // level P, the largest
+    float cs[2][L];
+    float c0 = rsqrtf(sp);
+    if (NU2 == 3) c0 = c0 * c0 * c0;
+    cs[0][0] = c0;
+    if (W == 12) {
+        const float4* t4 = reinterpret_cast<const float4*>(tab);
+        const float4 a = __ldg(t4), b = __ldg(t4 + 1), c = __ldg(t4 + 2);
+        const float t[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
+#pragma unroll
+        for (int q = 0; q < W; q++) tot[q] = fmaf(c0, t[q % 12], tot[q]);
+    } else {
+#pragma unroll
+        for (int q = 0; q < W; q++) tot[q] = fmaf(c0, __ldg(tab + q), tot[q]);
+    }
+    const float isp = 1.0f / sp;
+#pragma unroll
+    for (int n = 1; n <= P; n++) {
+        const float al = ((float)(2 * n + NU2 - 2) / (float)n) * isp, be = ((float)(n + NU2 - 2) / (float)n) * isp;
+        const float w0 = al * d0, w1 = al * d1, w2 = al * d2;
+        float* Rn = cs[n & 1];  // also holds level n-2
+        const float* R1 = cs[(n - 1) & 1];
+#pragma unroll
+        for (int a = n; a >= 0; a--) {
+            const int k1 = n - a, base = a * (a + 1) / 2;
+#pragma unroll
+            for (int k3 = a; k3 >= 0; k3--) {
+                const int k2 = a - k3, pos = base + k3;
+                float s1 = 0.f, s2 = 0.f;
+                if (k1 >= 1) s1 = w0 * R1[pos];
+                if (k2 >= 1) s1 = fmaf(w1, R1[pos - a], s1);
+                if (k3 >= 1) s1 = fmaf(w2, R1[pos - a - 1], s1);
+                if (k1 >= 2) s2 = Rn[pos];
+                if (k2 >= 2) s2 += Rn[pos - 2 * a + 1];
+                if (k3 >= 2) s2 += Rn[pos - 2 * a - 1];
+                const float ck = fmaf(-be, s2, s1);
+                Rn[pos] = ck;
+                const float* t = tab + (int64_t)(ncoef(n - 1) + pos) * W;
+                if (W == 12) {
+                    const float4* t4 = reinterpret_cast<const float4*>(t);
+                    const float4 x = __ldg(t4), y = __ldg(t4 + 1), z = __ldg(t4 + 2);
+                    const float tv[12] = {x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w, z.x, z.y, z.z, z.w};
+#pragma unroll
+                    for (int q = 0; q < W; q++) tot[q] = fmaf(ck, tv[q % 12], tot[q]);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < W; q++) tot[q] = fmaf(ck, __ldg(t + q), tot[q]);
+                }
+                // keep the table loads of later coefficients from being
+                // hoisted here: that would exhaust the registers
+                asm volatile("" ::: "memory");
+            }
+        }
+    }
+}
+
+template <int P>
+__global__ void __launch_bounds__(32)
+    k_far_reg32r(const double* __restrict__ ts, int64_t M, const float4* __restrict__ geo32,
+                 const float* __restrict__ ab32, const float* __restrict__ et32, float eps,
+                 const int64_t* __restrict__ far_off, const ListEntry* __restrict__ far_list,
+                 double* __restrict__ u_far)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t b = blockIdx.x;
+    const int64_t nbatch = (M + kBatch - 1) / kBatch;
+    if (b >= nbatch) return;
+    const int64_t m = b * kBatch + lane;
+    const bool valid = m < M;
+    float xh[3] = {0, 0, 0}, xl[3] = {0, 0, 0};
+    if (valid)
+        for (int a = 0; a < 3; a++) {
+            const double v = ts[a * M + m];
+            xh[a] = __double2float_rn(v);
+            xl[a] = __double2float_rn(v - (double)xh[a]);
+        }
+    constexpr int C2 = (P + 1) * (P + 2) * (P + 3) / 6, C1 = P * (P + 1) * (P + 2) / 6;
+    float su[3] = {0.f, 0.f, 0.f}, ku[3] = {0.f, 0.f, 0.f};
+    for (int64_t e = far_off[b]; e < far_off[b + 1]; e++) {
+        const ListEntry le = far_list[e];
+        const bool in = (le.mask >> lane) & 1u;
+        const float4 gh = __ldg(geo32 + 2 * (int64_t)le.node), gl = __ldg(geo32 + 2 * (int64_t)le.node + 1);
+        float d0 = ((xh[0] - gh.x) + (xl[0] - gl.x)) * gh.w;
+        float d1 = ((xh[1] - gh.y) + (xl[1] - gl.y)) * gh.w;
+        float d2 = ((xh[2] - gh.z) + (xl[2] - gl.z)) * gh.w;
+        if (!in) d0 = 2.0f, d1 = 0.0f, d2 = 0.0f;  // keep idle lanes finite
+        const float ep = eps * gh.w;
+        const float sp = fmaf(d0, d0, fmaf(d1, d1, fmaf(d2, d2, ep * ep)));
+        float t12[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0}, t3[3] = {0, 0, 0};
+        reg_pass_r<P, 12, 1>(sp, d0, d1, d2, ab32 + (int64_t)le.node * C2 * 12, t12);
+        reg_pass_r<P - 1, 3, 3>(sp, d0, d1, d2, et32 + (int64_t)le.node * C1 * 3, t3);
+        if (in) {
+            kahan_add(su[0], ku[0], t12[0] + d0 * t12[3] + d1 * t12[4] + d2 * t12[5] + t3[0]);
+            kahan_add(su[1], ku[1], t12[1] + d0 * t12[6] + d1 * t12[7] + d2 * t12[8] + t3[1]);
+            kahan_add(su[2], ku[2], t12[2] + d0 * t12[9] + d1 * t12[10] + d2 * t12[11] + t3[2]);
+        }
+    }
+    if (valid) {
+        u_far[m] = (double)su[0] - (double)ku[0];
+        u_far[M + m] = (double)su[1] - (double)ku[1];
+        u_far[2 * M + m] = (double)su[2] - (double)ku[2];
+    }
+}
+
 // FP32 copy of an FP64 table, rounded as the contraction tables are (narrow)
 __global__ void k_narrow_table(const double* __restrict__ src, int64_t n, float* __restrict__ dst)
 {
@@ -223,6 +337,18 @@ cudaError_t launch_far_reg32(const double* ts, int64_t M, const float4* geo32, c
 {
     if (M <= 0) return cudaSuccess;
     const int64_t nbatch = (M + kBatch - 1) / kBatch;
+    switch (p + 2) {
+#define TC_REG32R_CASE(P)                                                                                          \
+    case P:                                                                                                        \
+        k_far_reg32r<P><<<(unsigned)nbatch, 32, 0, s>>>(ts, M, geo32, ab32, et32, (float)eps, far_off, far_list, \
+                                                        u_far);                                                   \
+        note_launch();                                                                                             \
+        return cudaGetLastError();
+        TC_REG32R_CASE(2) TC_REG32R_CASE(3) TC_REG32R_CASE(4) TC_REG32R_CASE(5) TC_REG32R_CASE(6)
+        TC_REG32R_CASE(7) TC_REG32R_CASE(8) TC_REG32R_CASE(9) TC_REG32R_CASE(10)
+#undef TC_REG32R_CASE
+    default: break;  // higher orders: the shared-memory store
+    }
     const size_t smem = (size_t)2 * ((p + 3) * (p + 4) / 2) * 32 * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(k_far_reg32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
