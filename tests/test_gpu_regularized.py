@@ -63,6 +63,22 @@ def test_regularized_treecode_matches_oracle(prec, kind, N, N0, p, theta, eps):
     assert E < 1e-2, E
 
 
+@pytest.mark.parametrize("p,rec64", [(9, False), (11, False), (8, True), (10, True)])
+def test_regularized_mixed_far_field_variants(p, rec64):
+    """Mixed precision above the register-resident order (p = 9, 11: the
+    FP32 far field with its coefficients in shared memory) and with the FP64
+    far field kept by rec64 at p >= 8: the oracle's regularized treecode
+    within 1e-6."""
+    x, f, h, nu = inputs.gaussian_clusters(9000, 991)
+    tc = api.Treecode("mixed", True, rec64=rec64, reg_eps=0.004).build(dev(x), 100).moments(dev(f), dev(h), dev(nu), p)
+    u = host(tc.eval(0.5, p))
+    tc.close()
+    tree = oracle.Tree(x, 100, True)
+    tree.set_moments(f, h, nu, p)
+    ref = tree.treecode_reg(x, 0.5, 0.004, p)
+    assert oracle.rel_l2(u, ref) <= TOL["mixed"], oracle.rel_l2(u, ref)
+
+
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_regularized_treecode_disjoint_targets(prec):
     x, f, h, nu = inputs.uniform_cube(8000, 951)
