@@ -1185,6 +1185,69 @@ __global__ void k_leaf_eval(const int4* __restrict__ topo, const Geo* __restrict
     }
 }
 
+// Mixed precision: the same evaluation in FP32 (the polynomial is the far
+// field's adjoint expanded about the leaf centre, a convergent Taylor sum
+// led by its low orders, so FP32 terms leave about 1e-7 relative error), the
+// leaf's coefficients rounded to FP32 in shared memory.
+__global__ void k_leaf_eval32(const int4* __restrict__ topo, const Geo* __restrict__ geo,
+                              const double* __restrict__ xs, const double* __restrict__ ws, int64_t N, int p,
+                              const double* __restrict__ lamacc, double* __restrict__ gfar)
+{
+    extern __shared__ float llf[];
+    const int64_t node = blockIdx.x;
+    const int4 t = topo[node];
+    if (t.w != 0) return;
+    const int C = ncoef(p);
+    for (int q = threadIdx.x; q < 12 * C; q += blockDim.x) llf[q] = (float)lamacc[node * 12 * C + q];
+    __syncthreads();
+    const Geo gc = geo[node];
+    for (int i = t.x + blockIdx.y * blockDim.x + threadIdx.x; i < t.x + t.y; i += gridDim.y * blockDim.x) {
+        const float dl[3] = {(float)(xs[i] - gc.x), (float)(xs[N + i] - gc.y), (float)(xs[2 * N + i] - gc.z)};
+        float w[12];
+        for (int c = 0; c < 3; c++) w[c] = (float)ws[c * N + i];
+        for (int j = 0; j < 3; j++)
+            for (int l = 0; l < 3; l++) w[3 + 3 * j + l] = (float)(ws[(3 + j) * N + i] * ws[(6 + l) * N + i]);
+        float Qv[12], gx[3] = {0.f, 0.f, 0.f};
+        for (int c = 0; c < 12; c++) Qv[c] = 0.f;
+        float p1 = 1.f, p1m = 0.f;
+        for (int k1 = 0; k1 <= p; k1++) {
+            float p2 = 1.f, p2m = 0.f;
+            for (int k2 = 0; k1 + k2 <= p; k2++) {
+                float p3 = 1.f, p3m = 0.f;
+                for (int k3 = 0; k1 + k2 + k3 <= p; k3++) {
+                    const int kidx = flat_index(k1, k2, k3);
+                    const float mono = p1 * p2 * p3;
+                    float R = 0.f;
+#pragma unroll
+                    for (int c = 0; c < 12; c++) {
+                        const float L = llf[c * C + kidx];
+                        Qv[c] = fmaf(L, mono, Qv[c]);
+                        R = fmaf(w[c], L, R);
+                    }
+                    gx[0] = fmaf(R, (float)k1 * p1m * p2 * p3, gx[0]);
+                    gx[1] = fmaf(R, (float)k2 * p1 * p2m * p3, gx[1]);
+                    gx[2] = fmaf(R, (float)k3 * p1 * p2 * p3m, gx[2]);
+                    p3m = p3;
+                    p3 *= dl[2];
+                }
+                p2m = p2;
+                p2 *= dl[1];
+            }
+            p1m = p1;
+            p1 *= dl[0];
+        }
+        for (int a = 0; a < 3; a++) {
+            gfar[a * N + i] = Qv[a];
+            double gh = 0.0, gn = 0.0;
+            for (int l = 0; l < 3; l++) gh += ws[(6 + l) * N + i] * (double)Qv[3 + 3 * a + l];
+            for (int j = 0; j < 3; j++) gn += ws[(3 + j) * N + i] * (double)Qv[3 + 3 * j + a];
+            gfar[(3 + a) * N + i] = gh;
+            gfar[(6 + a) * N + i] = gn;
+            gfar[(9 + a) * N + i] = gx[a];
+        }
+    }
+}
+
 // Sum the parts and scatter from Morton order to the caller's order.
 __global__ void k_adj_final(const double* __restrict__ gfar, const double* __restrict__ gnear,
                             const double* __restrict__ gt, const int32_t* __restrict__ perm, int64_t N, int self,
@@ -1431,10 +1494,19 @@ extern "C" tc_status tc_adjoint(tc_ctx* ctx, const double* g, double* grad_f, do
                                                   ptr<double>(ctx->adj_lam), ptr<double>(ctx->adj_lamacc));
         note_launch();
     }
-    TC_CK(cudaFuncSetAttribute(k_leaf_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm), "leaf attr");
-    k_leaf_eval<<<dim3((unsigned)nnodes, kLeafEvalSplit), 128, lsm, s>>>(
-        ptr<int4>(ctx->node_topo), ptr<Geo>(ctx->node_geo), ptr<double>(ctx->xs), ptr<double>(ctx->ws), N, p,
-        ptr<double>(ctx->adj_lamacc), ptr<double>(ctx->adj_gfar));
+    if (ctx->precision == TC_FP64) {
+        TC_CK(cudaFuncSetAttribute(k_leaf_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm), "leaf attr");
+        k_leaf_eval<<<dim3((unsigned)nnodes, kLeafEvalSplit), 128, lsm, s>>>(
+            ptr<int4>(ctx->node_topo), ptr<Geo>(ctx->node_geo), ptr<double>(ctx->xs), ptr<double>(ctx->ws), N, p,
+            ptr<double>(ctx->adj_lamacc), ptr<double>(ctx->adj_gfar));
+    } else {
+        const size_t lsm32 = (size_t)12 * C * 4;
+        TC_CK(cudaFuncSetAttribute(k_leaf_eval32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm32),
+              "leaf attr");
+        k_leaf_eval32<<<dim3((unsigned)nnodes, kLeafEvalSplit), 128, lsm32, s>>>(
+            ptr<int4>(ctx->node_topo), ptr<Geo>(ctx->node_geo), ptr<double>(ctx->xs), ptr<double>(ctx->ws), N, p,
+            ptr<double>(ctx->adj_lamacc), ptr<double>(ctx->adj_gfar));
+    }
     note_launch();
     k_adj_final<<<grid_for(N, 256), 256, 0, s>>>(ptr<double>(ctx->adj_gfar), ptr<double>(ctx->adj_gnear),
                                                  ptr<double>(ctx->adj_gt), ptr<int32_t>(ctx->perm), N, ctx->eval_self,
