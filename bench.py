@@ -346,7 +346,7 @@ def bench_fwd_adjoint(flush, stream, steps=3):
         roof("k_near_adj_source_units (near field, source side)", NEAR_ADJ_SOURCE_FLOPS * st["near_pairs"],
              ph["adj_near_source"],
              "%g flops per near pair" % NEAR_ADJ_SOURCE_FLOPS),
-        roof("k_far_adj_target32 (far field, target side)", far_f * st["far_interactions"], ph["adj_far_target"],
+        roof("k_far_adj_target32p<10> (far field, target side)", far_f * st["far_interactions"], ph["adj_far_target"],
              "%g flops per far interaction on the folded coefficients (%g on all C(p+5,3))" % (far_f, far_u)),
     ]
     ms = statistics.mean(tot)

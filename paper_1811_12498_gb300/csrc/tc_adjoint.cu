@@ -813,6 +813,209 @@ __device__ __noinline__ void far_adj_target32_batch(const double* __restrict__ t
     }
 }
 
+// c^k of hcoef_r for the two targets of a lane at once (target a, target b
+// in the two halves of each FP32x2 register pair); nkap = -kappa_n / R'^2.
+__device__ __forceinline__ float2 hcoef_pair(const float2* R1, const float2* R2, int n, int h, float2 v0, float2 v1,
+                                             float2 v2, float2 nkap)
+{
+    float2 s1 = make_float2(0.f, 0.f), s2 = make_float2(0.f, 0.f);
+    bool any1 = false, any2 = false;
+    if (h <= n) {
+        const int k3 = h, k2 = n - h;
+        if (k2 >= 1) s1 = __fmul2_rn(v1, R1[k3]), any1 = true;
+        if (k3 >= 1) s1 = any1 ? __ffma2_rn(v2, R1[k3 - 1], s1) : __fmul2_rn(v2, R1[k3 - 1]);
+        if (k2 >= 2) s2 = R2[k3], any2 = true;
+        if (k3 >= 2) s2 = any2 ? __fadd2_rn(s2, R2[k3 - 2]) : R2[k3 - 2], any2 = true;
+    } else {
+        const int k3 = h - n - 1, k2 = n - 1 - k3;
+        s1 = __fmul2_rn(v0, R1[k3]);
+        if (k2 >= 1) s1 = __ffma2_rn(v1, R1[n + k3], s1);
+        if (k3 >= 1) s1 = __ffma2_rn(v2, R1[n + k3 - 1], s1);
+        if (k2 >= 2) s2 = R2[n - 1 + k3], any2 = true;
+        if (k3 >= 2) s2 = any2 ? __fadd2_rn(s2, R2[n - 3 + k3]) : R2[n - 3 + k3], any2 = true;
+    }
+    return any2 ? __ffma2_rn(nkap, s2, s1) : s1;
+}
+
+__device__ __forceinline__ float2 f2(float x) { return make_float2(x, x); }
+
+constexpr int kFarAdjPairMaxP = 10;  // largest P of the two-target form (register budget)
+
+// The target side for batches 2B and 2B+1 (the second may not exist) on one
+// warp, two targets per lane, over the merge of their far lists (tree
+// preorder; a cluster in both lists is evaluated once for both): the
+// arithmetic of far_adj_target32_batch on packed FP32x2 operations, every
+// table value loaded once for both targets.  Levels n - 1 and n + 1 share a
+// slot (level n + 1 overwrites level n - 1 in place, positions running
+// downward: a coefficient reads level n - 1 only at positions <= its own).
+template <int P>
+__device__ __noinline__ void far_adj_target32_pair(const double* __restrict__ ts, const double* __restrict__ gs,
+                                                   int64_t M, const int4* __restrict__ topo,
+                                                   const float4* __restrict__ geo32, const float* __restrict__ ab,
+                                                   const int64_t* __restrict__ far_off,
+                                                   const ListEntry* __restrict__ far_list, double* __restrict__ gt,
+                                                   int64_t B, int lane)
+{
+    constexpr int H = (P + 1) * (P + 1);
+    const int64_t nbatch = (M + kBatch - 1) / kBatch;
+    const int64_t ba = 2 * B, bb = 2 * B + 1;
+    const int64_t ma = ba * kBatch + lane, mb = bb * kBatch + lane;
+    const bool va = ma < M, vb = mb < M;
+    float2 xh[3], xl[3], g[3];
+    for (int a = 0; a < 3; a++) {
+        const double xa = va ? ts[a * M + ma] : 0.0, xb = vb ? ts[a * M + mb] : 0.0;
+        const float ha = __double2float_rn(xa), hb = __double2float_rn(xb);
+        xh[a] = make_float2(ha, hb);
+        xl[a] = make_float2(__double2float_rn(xa - (double)ha), __double2float_rn(xb - (double)hb));
+        g[a] = make_float2(va ? __double2float_rn(gs[a * M + ma]) : 0.f, vb ? __double2float_rn(gs[a * M + mb]) : 0.f);
+    }
+    // per-entry contributions summed by compensated FP32 summation
+    float Ga[3] = {0.f, 0.f, 0.f}, Ka[3] = {0.f, 0.f, 0.f}, Gb[3] = {0.f, 0.f, 0.f}, Kb[3] = {0.f, 0.f, 0.f};
+    int64_t ia = far_off[ba], ea = far_off[ba + 1], ib = 0, eb = 0;
+    if (bb < nbatch) {
+        ib = far_off[bb];
+        eb = far_off[bb + 1];
+    }
+    ListEntry la{0, 0}, lb{0, 0};
+    int4 qa = make_int4(0, 0, 0, 0), qb = make_int4(0, 0, 0, 0);
+    if (ia < ea) {
+        la = far_list[ia];
+        qa = topo[la.node];
+    }
+    if (ib < eb) {
+        lb = far_list[ib];
+        qb = topo[lb.node];
+    }
+    while (ia < ea || ib < eb) {
+        bool takeA, takeB;
+        if (ia >= ea) {
+            takeA = false, takeB = true;
+        } else if (ib >= eb) {
+            takeA = true, takeB = false;
+        } else if (la.node == lb.node) {
+            takeA = takeB = true;
+        } else {
+            takeA = qa.x < qb.x || (qa.x == qb.x && (qa.y > qb.y || (qa.y == qb.y && la.node < lb.node)));
+            takeB = !takeA;
+        }
+        const int node = takeA ? la.node : lb.node;
+        const bool inA = takeA && ((la.mask >> lane) & 1u), inB = takeB && ((lb.mask >> lane) & 1u);
+        const float4 gh = __ldg(geo32 + 2 * (int64_t)node), gl = __ldg(geo32 + 2 * (int64_t)node + 1);
+        using nearpair::sub2;
+        const float2 d0 = __fmul2_rn(__fadd2_rn(sub2(xh[0], f2(gh.x)), sub2(xl[0], f2(gl.x))), f2(gh.w));
+        const float2 d1 = __fmul2_rn(__fadd2_rn(sub2(xh[1], f2(gh.y)), sub2(xl[1], f2(gl.y))), f2(gh.w));
+        const float2 d2 = __fmul2_rn(__fadd2_rn(sub2(xh[2], f2(gh.z)), sub2(xl[2], f2(gl.z))), f2(gh.w));
+        float2 R2 = __ffma2_rn(d0, d0, __ffma2_rn(d1, d1, __fmul2_rn(d2, d2)));
+        if (!inA) R2.x = 1.0f;
+        if (!inB) R2.y = 1.0f;
+        const float2 iR = make_float2(rsqrtf(R2.x), rsqrtf(R2.y)), iR2 = __fmul2_rn(iR, iR);
+        const float2 v0 = __fmul2_rn(d0, iR2), v1 = __fmul2_rn(d1, iR2), v2 = __fmul2_rn(d2, iR2);
+        float2 wb[9];  // g_i d'_q
+        wb[0] = __fmul2_rn(g[0], d0), wb[1] = __fmul2_rn(g[0], d1), wb[2] = __fmul2_rn(g[0], d2);
+        wb[3] = __fmul2_rn(g[1], d0), wb[4] = __fmul2_rn(g[1], d1), wb[5] = __fmul2_rn(g[1], d2);
+        wb[6] = __fmul2_rn(g[2], d0), wb[7] = __fmul2_rn(g[2], d1), wb[8] = __fmul2_rn(g[2], d2);
+        const float4* __restrict__ tab = reinterpret_cast<const float4*>(ab + (int64_t)node * H * 12);
+        float2 cs[2][2 * P + 3];  // level n in slot n & 1
+        cs[0][0] = f2(1.0f);
+        cs[1][0] = v1, cs[1][1] = v2, cs[1][2] = v0;  // level 1: (0,1,0), (0,0,1), (1,0,0)
+        float2 a0 = f2(0.f), a1 = f2(0.f), a2 = f2(0.f);
+#pragma unroll
+        for (int n = 0; n <= P; n++) {
+            if (n >= 1) {  // level n + 1 from levels n and n - 1, over level n - 1
+                const float2 nkap = make_float2(-c_lev32.kappa[n + 1] * iR2.x, -c_lev32.kappa[n + 1] * iR2.y);
+#pragma unroll
+                for (int h = 2 * n + 2; h >= 0; h--)
+                    cs[(n + 1) & 1][h] = hcoef_pair(cs[n & 1], cs[(n + 1) & 1], n + 1, h, v0, v1, v2, nkap);
+            }
+            const float rn = (float)(2 * n + 1) / (float)(n + 1);
+            const float2* C1 = cs[(n + 1) & 1];
+#pragma unroll
+            for (int h = 0; h <= 2 * n; h++) {
+                const float4 ta = __ldg(tab + 3 * (n * n + h)), tb = __ldg(tab + 3 * (n * n + h) + 1),
+                             tc = __ldg(tab + 3 * (n * n + h) + 2);
+                const float2 gB0 = __ffma2_rn(g[0], f2(ta.w), __ffma2_rn(g[1], f2(tb.z), __fmul2_rn(g[2], f2(tc.y))));
+                const float2 gB1 = __ffma2_rn(g[0], f2(tb.x), __ffma2_rn(g[1], f2(tb.w), __fmul2_rn(g[2], f2(tc.z))));
+                const float2 gB2 = __ffma2_rn(g[0], f2(tb.y), __ffma2_rn(g[1], f2(tc.x), __fmul2_rn(g[2], f2(tc.w))));
+                float2 al = __ffma2_rn(g[0], f2(ta.x), __ffma2_rn(g[1], f2(ta.y), __fmul2_rn(g[2], f2(ta.z))));
+                al = __ffma2_rn(wb[0], f2(ta.w), __ffma2_rn(wb[1], f2(tb.x), __ffma2_rn(wb[2], f2(tb.y), al)));
+                al = __ffma2_rn(wb[3], f2(tb.z), __ffma2_rn(wb[4], f2(tb.w), __ffma2_rn(wb[5], f2(tc.x), al)));
+                al = __ffma2_rn(wb[6], f2(tc.y), __ffma2_rn(wb[7], f2(tc.z), __ffma2_rn(wb[8], f2(tc.w), al)));
+                const float2 c = cs[n & 1][h];
+                a0 = __ffma2_rn(c, gB0, a0);
+                a1 = __ffma2_rn(c, gB1, a1);
+                a2 = __ffma2_rn(c, gB2, a2);
+                float2 e0, e1, e2;  // (k_m + 1) r_n c^{k+e_m}
+                if (h <= n) {       // k = (0, n-h, h)
+                    const int k2 = n - h, k3 = h;
+                    e0 = __fmul2_rn(f2(rn), C1[n + 2 + h]);
+                    e1 = __fmul2_rn(f2((float)(k2 + 1) * rn), C1[h]);
+                    e2 = __fmul2_rn(f2((float)(k3 + 1) * rn), C1[h + 1]);
+                } else {  // k = (1, a, b)
+                    const int bq = h - n - 1, aq = n - 1 - bq;
+                    e0 = __fmul2_rn(f2(-rn), __ffma2_rn(f2((float)((aq + 2) * (aq + 1))), C1[bq],
+                                                       __fmul2_rn(f2((float)((bq + 2) * (bq + 1))), C1[bq + 2])));
+                    e1 = __fmul2_rn(f2((float)(aq + 1) * rn), C1[h + 1]);
+                    e2 = __fmul2_rn(f2((float)(bq + 1) * rn), C1[h + 2]);
+                }
+                a0 = __ffma2_rn(make_float2(-e0.x, -e0.y), al, a0);
+                a1 = __ffma2_rn(make_float2(-e1.x, -e1.y), al, a1);
+                a2 = __ffma2_rn(make_float2(-e2.x, -e2.y), al, a2);
+                // keep the table loads of later coefficients from being
+                // hoisted here: that would exhaust the registers
+                asm volatile("" ::: "memory");
+            }
+        }
+        const float2 sc = __fmul2_rn(iR, f2(gh.w));  // 1/R' and d'/dx = 1/rho
+        if (inA) {
+            kahan_add(Ga[0], Ka[0], a0.x * sc.x);
+            kahan_add(Ga[1], Ka[1], a1.x * sc.x);
+            kahan_add(Ga[2], Ka[2], a2.x * sc.x);
+        }
+        if (inB) {
+            kahan_add(Gb[0], Kb[0], a0.y * sc.y);
+            kahan_add(Gb[1], Kb[1], a1.y * sc.y);
+            kahan_add(Gb[2], Kb[2], a2.y * sc.y);
+        }
+        if (takeA && ++ia < ea) {
+            la = far_list[ia];
+            qa = topo[la.node];
+        }
+        if (takeB && ++ib < eb) {
+            lb = far_list[ib];
+            qb = topo[lb.node];
+        }
+    }
+    if (va) {
+        gt[ma] = (double)Ga[0] - (double)Ka[0];
+        gt[M + ma] = (double)Ga[1] - (double)Ka[1];
+        gt[2 * M + ma] = (double)Ga[2] - (double)Ka[2];
+    }
+    if (vb) {
+        gt[mb] = (double)Gb[0] - (double)Kb[0];
+        gt[M + mb] = (double)Gb[1] - (double)Kb[1];
+        gt[2 * M + mb] = (double)Gb[2] - (double)Kb[2];
+    }
+}
+
+// One resident grid of single-warp blocks taking batch pairs from a queue.
+template <int P>
+__global__ void __launch_bounds__(32)
+    k_far_adj_target32p(const double* __restrict__ ts, const double* __restrict__ gs, int64_t M,
+                        const int4* __restrict__ topo, const float4* __restrict__ geo32, const float* __restrict__ ab,
+                        const int64_t* __restrict__ far_off, const ListEntry* __restrict__ far_list,
+                        double* __restrict__ gt, unsigned* __restrict__ queue)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nsuper = ((M + kBatch - 1) / kBatch + 1) / 2;
+    for (;;) {
+        unsigned B = 0;
+        if (lane == 0) B = atomicAdd(queue, 1u);
+        B = __shfl_sync(0xffffffffu, B, 0);
+        if ((int64_t)B >= nsuper) break;
+        far_adj_target32_pair<P>(ts, gs, M, topo, geo32, ab, far_off, far_list, gt, (int64_t)B, lane);
+    }
+}
+
 template <int P>
 __global__ void __launch_bounds__(32)
     k_far_adj_target32(const double* __restrict__ ts, const double* __restrict__ gs, int64_t M,
@@ -1320,19 +1523,32 @@ cudaError_t run_far_adj32(tc_ctx* ctx, const double* ts, int64_t M, cudaStream_t
     const int64_t nnodes = ctx->nnodes;
     const int H = hsize(P);
     int per_sm = 0, sms = 0, dev = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_far_adj_target32<P>, 32, 0);
-    if (e != cudaSuccess) return e;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int64_t grid = std::min<int64_t>(nbatch, (int64_t)std::max(per_sm, 1) * sms);
     unsigned* queue = reinterpret_cast<unsigned*>(ptr<char>(ctx->flags) + 192);
-    e = cudaMemsetAsync(queue, 0, sizeof(unsigned), s);
+    cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
     ph_begin(ctx, TC_PH_ADJ_FAR_T);
-    k_far_adj_target32<P><<<(unsigned)grid, 32, 0, s>>>(ts, ptr<double>(ctx->adj_gs), M, ptr<float4>(ctx->geo32),
-                                                        ptr<float>(ctx->abf32), ptr<int64_t>(ctx->far_off),
-                                                        ptr<ListEntry>(ctx->far_list), ptr<double>(ctx->adj_gt),
-                                                        queue);
+    // two targets per lane up to P = 10 (p = 8); above, the packed form runs
+    // out of registers and the one-target form is used
+    if constexpr (P <= kFarAdjPairMaxP) {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_far_adj_target32p<P>, 32, 0);
+        if (e != cudaSuccess) return e;
+        const int64_t grid = std::min<int64_t>((nbatch + 1) / 2, (int64_t)std::max(per_sm, 1) * sms);
+        k_far_adj_target32p<P><<<(unsigned)grid, 32, 0, s>>>(ts, ptr<double>(ctx->adj_gs), M,
+                                                             ptr<int4>(ctx->node_topo), ptr<float4>(ctx->geo32),
+                                                             ptr<float>(ctx->abf32), ptr<int64_t>(ctx->far_off),
+                                                             ptr<ListEntry>(ctx->far_list), ptr<double>(ctx->adj_gt),
+                                                             queue);
+    } else {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_far_adj_target32<P>, 32, 0);
+        if (e != cudaSuccess) return e;
+        const int64_t grid = std::min<int64_t>(nbatch, (int64_t)std::max(per_sm, 1) * sms);
+        k_far_adj_target32<P><<<(unsigned)grid, 32, 0, s>>>(ts, ptr<double>(ctx->adj_gs), M,
+                                                            ptr<float4>(ctx->geo32), ptr<float>(ctx->abf32),
+                                                            ptr<int64_t>(ctx->far_off), ptr<ListEntry>(ctx->far_list),
+                                                            ptr<double>(ctx->adj_gt), queue);
+    }
     note_launch();
     ph_end(ctx, TC_PH_ADJ_FAR_T);
     e = ensure(ctx->adj_fbar, (size_t)nnodes * H * 12 * 8);
