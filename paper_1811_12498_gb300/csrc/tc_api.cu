@@ -113,7 +113,7 @@ static void release_all(tc_ctx* c)
     DevBuf* bufs[] = {&c->root, &c->bbox_part, &c->keys, &c->keys_alt, &c->perm, &c->perm_alt, &c->hist, &c->xs,
                       &c->node_topo, &c->node_info, &c->node_key, &c->node_geo, &c->node_invrho, &c->node_geof, &c->geo_tmp,
                       &c->split_cnt,
-                      &c->split_off, &c->scan_tmp, &c->ws, &c->spack, &c->mom, &c->mom_tmp, &c->ab64, &c->ab32,
+                      &c->split_off, &c->scan_tmp, &c->ws, &c->spack, &c->mom, &c->mom_tmp, &c->m2m_tmp, &c->ab64, &c->ab32,
                       &c->abf64,
                       &c->abf32, &c->geo32, &c->reg_et, &c->reg_et32, &c->tkeys,
                       &c->tkeys_alt, &c->tperm, &c->tperm_alt, &c->ts, &c->nfar_e, &c->nnear_e,
@@ -367,6 +367,13 @@ tc_status tc_moments(tc_ctx* ctx, const double* f, const double* h, const double
     TC_CK(ensure(ctx->ws, (size_t)9 * N * 8), "alloc weights");
     TC_CK(ensure(ctx->mom, (size_t)ctx->nnodes * 12 * ncoef(p) * 8), "alloc moments");
     TC_CK(ensure(ctx->mom_tmp, moments_scratch_bytes(N, ctx->nnodes, p)), "alloc moments");
+    {
+        // upward-pass scratch: one slot of moments per node of the widest level
+        int64_t widest = 1;
+        for (size_t L = 0; L + 1 < ctx->level_begin.size(); L++)
+            widest = std::max<int64_t>(widest, ctx->level_begin[L + 1] - ctx->level_begin[L]);
+        TC_CK(ensure(ctx->m2m_tmp, (size_t)widest * 12 * ncoef(p) * 8), "alloc moments");
+    }
     if (ctx->precision == TC_MIXED) TC_CK(ensure(ctx->spack, (size_t)N * 64), "alloc pack");
     ph_begin(ctx, TC_PH_MOMENTS);
     TC_CK(launch_gather_weights(f, h, nu, ptr<int32_t>(ctx->perm), N, ptr<double>(ctx->ws), s), "gather weights");
@@ -390,7 +397,8 @@ tc_status tc_moments(tc_ctx* ctx, const double* f, const double* h, const double
     // upward pass: level_begin holds the first node of each level and the end
     for (int L = (int)ctx->level_begin.size() - 3; L >= 0; L--)
         TC_CK(launch_m2m(ptr<int4>(ctx->node_topo), ptr<Geo>(ctx->node_geo), ctx->level_begin[L],
-                         ctx->level_begin[L + 1], p, ptr<double>(ctx->mom), sm),
+                         ctx->level_begin[L + 1], ctx->level_begin[L + 1], p, ptr<double>(ctx->mom),
+                         ptr<double>(ctx->m2m_tmp), sm),
               "m2m");
     ph_end(ctx, TC_PH_MOMENTS, sm);
     if (async) {
@@ -676,7 +684,8 @@ tc_status tc_update_positions(tc_ctx* ctx, const double* x)
           "moments");
     for (int L = (int)ctx->level_begin.size() - 3; L >= 0; L--)
         TC_CK(launch_m2m(ptr<int4>(ctx->node_topo), ptr<Geo>(ctx->node_geo), ctx->level_begin[L],
-                         ctx->level_begin[L + 1], ctx->p_mom, ptr<double>(ctx->mom), s),
+                         ctx->level_begin[L + 1], ctx->level_begin[L + 1], ctx->p_mom, ptr<double>(ctx->mom),
+                         ptr<double>(ctx->m2m_tmp), s),
               "m2m");
     ctx->ab_p = -1;
     tc_status st = ensure_tables(ctx, ctx->p_eval, s);

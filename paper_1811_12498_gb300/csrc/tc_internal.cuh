@@ -160,6 +160,7 @@ struct tc_ctx {
     tc::DevBuf spack;                   // MIXED source pack: 4 float4 per source
     tc::DevBuf mom;                     // FP64 [node][12][ncoef(p)]
     tc::DevBuf mom_tmp;                 // leaf-pass scratch: item map and per-item partial moments
+    tc::DevBuf m2m_tmp;                 // upward-pass scratch: shifted moments per child of one level
     int ab_p = -1;                      // order the contraction tables were built for
     tc::DevBuf ab64;                    // FP64 [node][ncoef(p+2)][12]
     tc::DevBuf ab32;                    // FP32 [node][ncoef(p+2)][12]
@@ -376,7 +377,10 @@ cudaError_t launch_source_pack(const double* xs, const double* ws, int64_t N, fl
 size_t moments_scratch_bytes(int64_t N, int64_t nnodes, int p);
 cudaError_t launch_moments(const int4* topo, const Geo* geo, const double* xs, const double* ws, int64_t N,
                            int64_t nnodes, int p, double* mom, void* scratch, cudaStream_t s);
-cudaError_t launch_m2m(const int4* topo, const Geo* geo, int64_t lb, int64_t le, int p, double* mom, cudaStream_t s);
+// upward pass of one level [lb, le) whose children start at cb; shifted:
+// scratch of m2m_scratch_bytes (one slot of moments per child of the level)
+cudaError_t launch_m2m(const int4* topo, const Geo* geo, int64_t lb, int64_t le, int64_t cb, int p, double* mom,
+                       double* shifted, cudaStream_t s);
 cudaError_t launch_ab_tables(const double* mom, const double* invrho, int64_t nnodes, int pm, int p, double* ab64,
                              float* ab32, cudaStream_t s);
 cudaError_t launch_eps_table(const double* mom, const double* invrho, int64_t nnodes, int pm, int p, double eps,

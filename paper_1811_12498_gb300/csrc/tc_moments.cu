@@ -216,10 +216,14 @@ __constant__ Binom c_binom = make_binom();
 // the same for all 12 components.  The shift factorises over the axes, so
 // each child's moments are shifted along x, then y, then z: three passes of
 // at most p+1 terms per coefficient instead of one of prod_a (k_a + 1).  One
-// block per internal cluster of one level, the three working arrays [C][12]
-// in shared memory; levels are processed from the deepest up.
-__global__ void __launch_bounds__(kMomThreads) k_m2m(const int4* __restrict__ topo, const Geo* __restrict__ geo,
-                                                     int64_t lb, int64_t le, int p, double* __restrict__ mom)
+// block per (internal cluster of one level, child), the two working arrays
+// [C][12] in shared memory, the shifted moments to a scratch slot per child;
+// then k_m2m_sum adds each cluster's children in order.  Levels are
+// processed from the deepest up.
+__global__ void __launch_bounds__(kMomThreads) k_m2m_shift(const int4* __restrict__ topo, const Geo* __restrict__ geo,
+                                                           int64_t lb, int64_t le, int64_t cb, int p,
+                                                           const double* __restrict__ mom,
+                                                           double* __restrict__ shifted)
 {
     extern __shared__ double m2m_sh[];
     __shared__ double sp[3][kPMax + 1];
@@ -227,7 +231,8 @@ __global__ void __launch_bounds__(kMomThreads) k_m2m(const int4* __restrict__ to
     const int64_t node = lb + blockIdx.x;
     if (node >= le) return;
     const int4 t = topo[node];
-    if (t.w == 0) return;
+    const int ci = blockIdx.y;
+    if (ci >= t.w) return;
     const Geo gp = geo[node];
     const int C = ncoef(p), W = C * 12;
     for (int k = threadIdx.x; k < C; k += blockDim.x) {
@@ -237,43 +242,54 @@ __global__ void __launch_bounds__(kMomThreads) k_m2m(const int4* __restrict__ to
     }
     double* A = m2m_sh;
     double* B = A + W;
-    double* acc = B + W;
-    for (int i = threadIdx.x; i < W; i += blockDim.x) acc[i] = 0.0;
-    for (int ci = 0; ci < t.w; ci++) {
-        const int64_t child = t.z + ci;
-        const Geo gc = geo[child];
-        const double* mc = mom + child * 12 * C;
-        __syncthreads();
-        if (threadIdx.x < 3) {
-            const double sh = threadIdx.x == 0 ? gc.x - gp.x : (threadIdx.x == 1 ? gc.y - gp.y : gc.z - gp.z);
-            double v = 1.0;
-            sp[threadIdx.x][0] = 1.0;
-            for (int k = 1; k <= p; k++) {
-                v *= sh;
-                sp[threadIdx.x][k] = v;
-            }
-        }
-        for (int i = threadIdx.x; i < W; i += blockDim.x) A[i] = mc[(i % 12) * C + i / 12];
-        __syncthreads();
-#pragma unroll
-        for (int ax = 0; ax < 3; ax++) {
-            const double* src = ax == 1 ? B : A;
-            double* dst = ax == 0 ? B : (ax == 1 ? A : acc);
-            for (int i = threadIdx.x; i < W; i += blockDim.x) {
-                const int k = i / 12, c = i % 12;
-                int kk[3] = {kidx[k][0], kidx[k][1], kidx[k][2]};
-                const int ka = kk[ax];
-                double v = 0.0;
-                for (int m = 0; m <= ka; m++) {
-                    kk[ax] = m;
-                    v = fma(c_binom.v[ka][m] * sp[ax][ka - m], src[flat_index(kk[0], kk[1], kk[2]) * 12 + c], v);
-                }
-                dst[i] = ax == 2 ? dst[i] + v : v;
-            }
-            __syncthreads();
+    const int64_t child = t.z + ci;
+    const Geo gc = geo[child];
+    const double* mc = mom + child * 12 * C;
+    double* out = shifted + (child - cb) * (int64_t)W;
+    if (threadIdx.x < 3) {
+        const double sh = threadIdx.x == 0 ? gc.x - gp.x : (threadIdx.x == 1 ? gc.y - gp.y : gc.z - gp.z);
+        double v = 1.0;
+        sp[threadIdx.x][0] = 1.0;
+        for (int k = 1; k <= p; k++) {
+            v *= sh;
+            sp[threadIdx.x][k] = v;
         }
     }
-    for (int i = threadIdx.x; i < W; i += blockDim.x) mom[(node * 12 + i % 12) * C + i / 12] = acc[i];
+    for (int i = threadIdx.x; i < W; i += blockDim.x) A[i] = mc[(i % 12) * C + i / 12];
+    __syncthreads();
+#pragma unroll
+    for (int ax = 0; ax < 3; ax++) {
+        const double* src = ax == 1 ? B : A;
+        double* dst = ax == 0 ? B : (ax == 1 ? A : out);
+        for (int i = threadIdx.x; i < W; i += blockDim.x) {
+            const int k = i / 12, c = i % 12;
+            int kk[3] = {kidx[k][0], kidx[k][1], kidx[k][2]};
+            const int ka = kk[ax];
+            double v = 0.0;
+            for (int m = 0; m <= ka; m++) {
+                kk[ax] = m;
+                v = fma(c_binom.v[ka][m] * sp[ax][ka - m], src[flat_index(kk[0], kk[1], kk[2]) * 12 + c], v);
+            }
+            dst[i] = v;
+        }
+        __syncthreads();
+    }
+}
+
+// mom[cluster] = sum of its children's shifted moments, in child order
+__global__ void k_m2m_sum(const int4* __restrict__ topo, int64_t lb, int64_t le, int64_t cb, int p,
+                          const double* __restrict__ shifted, double* __restrict__ mom)
+{
+    const int64_t node = lb + blockIdx.x;
+    if (node >= le) return;
+    const int4 t = topo[node];
+    if (t.w == 0) return;
+    const int C = ncoef(p), W = C * 12;
+    for (int i = threadIdx.x; i < W; i += blockDim.x) {
+        double acc = 0.0;
+        for (int ci = 0; ci < t.w; ci++) acc += shifted[(t.z + ci - cb) * (int64_t)W + i];
+        mom[(node * 12 + i % 12) * C + i / 12] = acc;
+    }
 }
 
 // moment of component c at multi-index (k1,k2,k3); 0 outside 0 <= k, ||k|| <= p
@@ -525,13 +541,16 @@ cudaError_t launch_moments(const int4* topo, const Geo* geo, const double* xs, c
     return cudaGetLastError();
 }
 
-cudaError_t launch_m2m(const int4* topo, const Geo* geo, int64_t lb, int64_t le, int p, double* mom, cudaStream_t s)
+cudaError_t launch_m2m(const int4* topo, const Geo* geo, int64_t lb, int64_t le, int64_t cb, int p, double* mom,
+                       double* shifted, cudaStream_t s)
 {
     if (le <= lb) return cudaSuccess;
-    const size_t smem = (size_t)3 * ncoef(p) * 12 * sizeof(double);
-    cudaError_t e = cudaFuncSetAttribute(k_m2m, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = (size_t)2 * ncoef(p) * 12 * sizeof(double);
+    cudaError_t e = cudaFuncSetAttribute(k_m2m_shift, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_m2m<<<(unsigned)(le - lb), kMomThreads, smem, s>>>(topo, geo, lb, le, p, mom);
+    k_m2m_shift<<<dim3((unsigned)(le - lb), 8), kMomThreads, smem, s>>>(topo, geo, lb, le, cb, p, mom, shifted);
+    note_launch();
+    k_m2m_sum<<<(unsigned)(le - lb), 256, 0, s>>>(topo, lb, le, cb, p, shifted, mom);
     note_launch();
     return cudaGetLastError();
 }

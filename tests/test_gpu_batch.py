@@ -82,6 +82,31 @@ def test_batch_without_graph_or_tuning_gives_the_same_result():
     np.testing.assert_array_equal(res[0], res[2])
 
 
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_batch_with_tiny_systems_and_changing_order(prec):
+    # systems of 1, 2 and 40 particles among larger ones (one near entry, one
+    # leaf), evaluated at one order, replayed, then at another order and with
+    # new weights (the graph is captured again): every system equals its own
+    # tc_eval bit for bit and the oracle within the tolerance
+    sizes = [1, 2, 1700, 40, 2600]
+    xs, fs, hs, ns, off = _systems(sizes, 760)
+    b = api.Batch(prec, True).build(_seg(xs), off, 64)
+    tol = 1e-6 if prec == "mixed" else 1e-10
+    for p, scale in ((4, 1.0), (4, 1.0), (7, -0.5)):
+        b.moments(_seg([scale * f for f in fs]), _seg(hs), _seg(ns), p)
+        u = b.eval(0.5, p).cpu().numpy()
+        sep = b.eval_separate(0.5, p)
+        assert np.all(u[:, 0] == 0.0)  # a single particle has nothing to sum
+        for s in range(len(sizes)):
+            us = u[:, off[s]:off[s + 1]]
+            np.testing.assert_array_equal(us, sep[s].cpu().numpy())
+            if sizes[s] > 2:
+                tree = oracle.Tree(xs[s], 64, True)
+                tree.set_moments(scale * fs[s], hs[s], ns[s], p)
+                assert oracle.rel_l2(us.T, tree.treecode(xs[s], 0.5, p)) <= tol
+    b.close()
+
+
 def test_batch_rejects_bad_offsets():
     x = torch.zeros((3, 10), dtype=torch.float64, device="cuda")
     b = api.Batch("mixed")
