@@ -91,10 +91,11 @@ typedef struct {
                         *   S^eps_ij = (delta_ij (r^2 + 2 eps^2) + d_i d_j) / s^(3/2),
                         *   T^eps_ijl = (d_i d_j d_l + (eps^2/2)(delta_ij d_l
                         *               + delta_jl d_i + delta_il d_j)) / s^(5/2),
-                        * the same tree, MAC, moments and lists; the far field
-                        * is evaluated in FP64 in both precision modes (the
-                        * harmonic folding of the FP32 path does not hold for
-                        * eps > 0), the near field as the precision mode says.
+                        * the same tree, MAC, moments and lists; far and near
+                        * fields as the precision mode says, the far field on
+                        * the full (unfolded) tables, since the harmonic
+                        * folding does not hold for eps > 0 (TC_MIXED with
+                        * rec64 at p >= 8: far field in FP64).
                         * Not available for tc_adjoint, tc_tune and batches.  */
 } tc_config;
 
