@@ -441,3 +441,34 @@ def test_deep_tree_high_order_matches_oracle(prec, p):
     err = oracle.rel_l2(u[idx], ref)
     print("deep tree p=%d %s: %.3e" % (p, prec, err))
     assert err <= TOL[prec], err
+
+
+@pytest.mark.parametrize("case", range(12))
+def test_random_configurations_match_oracle(case):
+    """Seeded random configurations (size, distribution, leaf size, order,
+    theta, shrink, precision, disjoint targets or not) against the oracle's
+    treecode: the interaction counts exactly, the velocities within the
+    precision's tolerance.  Covers small and ragged schedules (leaves with a
+    few incidences, single-stream units, batches of one target)."""
+    rng = np.random.default_rng(1000 + case)
+    N = int(rng.integers(50, 6000))
+    kind = ["cube", "clusters", "sphere"][case % 3]
+    gen = {"cube": inputs.uniform_cube, "clusters": inputs.gaussian_clusters, "sphere": inputs.fibonacci_sphere}[kind]
+    x, f, h, nu = gen(N, 2000 + case)
+    N0 = int(rng.integers(8, 300))
+    p = int(rng.integers(0, 11))
+    theta = float(rng.uniform(0.3, 0.8))
+    shrink = bool(case % 2)
+    prec = "mixed" if case % 4 < 3 else "fp64"
+    targets = None
+    if case % 5 == 4:
+        targets = np.concatenate([rng.uniform(-0.5, 1.5, (int(rng.integers(1, 700)), 3)), x[: int(rng.integers(0, 40))]])
+    u, nf, nn, _ = _run(prec, x, f, h, nu, N0, p, theta, shrink=shrink, targets=targets)
+    tree = oracle.Tree(x, N0, shrink)
+    tree.set_moments(f, h, nu, p)
+    ref, cnt = tree.treecode(x if targets is None else targets, theta, p, counts=True)
+    np.testing.assert_array_equal(nf, cnt["far"])
+    np.testing.assert_array_equal(nn, cnt["near_pairs"])
+    # the sphere's outward normals: the FP32 d.nu limit of TOL_MIXED_SURFACE
+    tol = TOL_MIXED_SURFACE if (prec == "mixed" and kind == "sphere") else TOL[prec]
+    assert oracle.rel_l2(u, ref) <= tol, (kind, N, N0, p, theta, shrink, prec, oracle.rel_l2(u, ref))
