@@ -1280,6 +1280,8 @@ __constant__ Binom c_binom = make_binom();
 // Downward pass: the adjoint polynomial of the parent, sum_k L^k (y - y_P)^k,
 // re-expanded about the child centre (y - y_P = (y - y_C) + s, s = y_C - y_P):
 //   L'^j = sum_{k >= j} binom(k, j) s^(k-j) L^k,  added to the child's own.
+// Grid (nodes of one level, 3): each block takes 4 of the 12 components, so
+// that the upper levels, with few nodes, still spread over the GPU.
 __global__ void k_l2l(const int4* __restrict__ info, const Geo* __restrict__ geo, int64_t lb, int64_t le, int p,
                       const double* __restrict__ lam, double* __restrict__ lamacc)
 {
@@ -1288,8 +1290,10 @@ __global__ void k_l2l(const int4* __restrict__ info, const Geo* __restrict__ geo
     if (node >= le) return;
     const int C = ncoef(p);
     const int64_t parent = info[node].y;
+    const int c0 = 4 * blockIdx.y;  // this block's components c0 .. c0 + 3
     if (parent < 0) {
-        for (int q = threadIdx.x; q < 12 * C; q += blockDim.x) lamacc[node * 12 * C + q] = lam[node * 12 * C + q];
+        for (int q = threadIdx.x; q < 4 * C; q += blockDim.x)
+            lamacc[node * 12 * C + c0 * C + q] = lam[node * 12 * C + c0 * C + q];
         return;
     }
     const Geo gc = geo[node], gp = geo[parent];
@@ -1307,8 +1311,8 @@ __global__ void k_l2l(const int4* __restrict__ info, const Geo* __restrict__ geo
     for (int jdx = threadIdx.x; jdx < C; jdx += blockDim.x) {
         int j1, j2, j3;
         unflatten(jdx, j1, j2, j3);
-        double acc[12];
-        for (int c = 0; c < 12; c++) acc[c] = lam[(node * 12 + c) * C + jdx];
+        double acc[4];
+        for (int c = 0; c < 4; c++) acc[c] = lam[(node * 12 + c0 + c) * C + jdx];
         for (int k1 = j1; k1 <= p; k1++) {
             const double w1 = c_binom.v[k1][j1] * sp[0][k1 - j1];
             for (int k2 = j2; k1 + k2 <= p; k2++) {
@@ -1316,11 +1320,11 @@ __global__ void k_l2l(const int4* __restrict__ info, const Geo* __restrict__ geo
                 for (int k3 = j3; k1 + k2 + k3 <= p; k3++) {
                     const double wk = w12 * c_binom.v[k3][j3] * sp[2][k3 - j3];
                     const int kidx = flat_index(k1, k2, k3);
-                    for (int c = 0; c < 12; c++) acc[c] = fma(wk, lp[c * C + kidx], acc[c]);
+                    for (int c = 0; c < 4; c++) acc[c] = fma(wk, lp[(c0 + c) * C + kidx], acc[c]);
                 }
             }
         }
-        for (int c = 0; c < 12; c++) lamacc[(node * 12 + c) * C + jdx] = acc[c];
+        for (int c = 0; c < 4; c++) lamacc[(node * 12 + c0 + c) * C + jdx] = acc[c];
     }
 }
 
@@ -1706,8 +1710,8 @@ extern "C" tc_status tc_adjoint(tc_ctx* ctx, const double* g, double* grad_f, do
     for (size_t L = 0; L + 1 < ctx->level_begin.size(); L++) {
         const int64_t lb = ctx->level_begin[L], le = ctx->level_begin[L + 1];
         if (le <= lb) continue;
-        k_l2l<<<(unsigned)(le - lb), 128, 0, s>>>(ptr<int4>(ctx->node_info), ptr<Geo>(ctx->node_geo), lb, le, p,
-                                                  ptr<double>(ctx->adj_lam), ptr<double>(ctx->adj_lamacc));
+        k_l2l<<<dim3((unsigned)(le - lb), 3), 128, 0, s>>>(ptr<int4>(ctx->node_info), ptr<Geo>(ctx->node_geo), lb, le,
+                                                           p, ptr<double>(ctx->adj_lam), ptr<double>(ctx->adj_lamacc));
         note_launch();
     }
     if (ctx->precision == TC_FP64) {
