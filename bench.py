@@ -89,7 +89,7 @@ def folded_coefficients(P):
 REG_NEAR_PAIR_FLOPS = 65
 NEAR_ADJ_TARGET_FLOPS = 85.0
 NEAR_ADJ_SOURCE_FLOPS = 109.0
-FAR_ADJ_PER_COEF_FLOPS = 63.0
+FAR_ADJ_PER_COEF_FLOPS = 45.0
 
 
 def far_adj_target_flops(p):

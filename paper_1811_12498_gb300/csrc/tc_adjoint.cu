@@ -746,10 +746,6 @@ __device__ __noinline__ void far_adj_target32_batch(const double* __restrict__ t
         if (!in) R2 = 1.0f;
         const float iR = rsqrtf(R2), iR2 = iR * iR;
         const float v0 = d0 * iR2, v1 = d1 * iR2, v2 = d2 * iR2;
-        float wb[9];  // g_i d'_q
-        wb[0] = g[0] * d0, wb[1] = g[0] * d1, wb[2] = g[0] * d2;
-        wb[3] = g[1] * d0, wb[4] = g[1] * d1, wb[5] = g[1] * d2;
-        wb[6] = g[2] * d0, wb[7] = g[2] * d1, wb[8] = g[2] * d2;
         const float4* __restrict__ tab = reinterpret_cast<const float4*>(ab + (int64_t)le.node * H * 12);
         float cs[3][2 * P + 3];  // levels n-1, n, n+1 (slot = level mod 3)
         cs[0][0] = 1.0f;
@@ -774,10 +770,9 @@ __device__ __noinline__ void far_adj_target32_batch(const double* __restrict__ t
                 const float gB0 = fmaf(g[0], ta.w, fmaf(g[1], tb.z, g[2] * tc.y));
                 const float gB1 = fmaf(g[0], tb.x, fmaf(g[1], tb.w, g[2] * tc.z));
                 const float gB2 = fmaf(g[0], tb.y, fmaf(g[1], tc.x, g[2] * tc.w));
+                // alpha^k = g.T_0..2 + sum_q d'_q gB_q  (sum_iq g_i d'_q T_{3+3i+q} regrouped)
                 float al = fmaf(g[0], ta.x, fmaf(g[1], ta.y, g[2] * ta.z));
-                al = fmaf(wb[0], ta.w, fmaf(wb[1], tb.x, fmaf(wb[2], tb.y, al)));
-                al = fmaf(wb[3], tb.z, fmaf(wb[4], tb.w, fmaf(wb[5], tc.x, al)));
-                al = fmaf(wb[6], tc.y, fmaf(wb[7], tc.z, fmaf(wb[8], tc.w, al)));
+                al = fmaf(d0, gB0, fmaf(d1, gB1, fmaf(d2, gB2, al)));
                 const float c = cs[n % 3][h];
                 a0 = fmaf(c, gB0, a0);
                 a1 = fmaf(c, gB1, a1);
@@ -910,10 +905,6 @@ __device__ __noinline__ void far_adj_target32_pair(const double* __restrict__ ts
         if (!inB) R2.y = 1.0f;
         const float2 iR = make_float2(rsqrtf(R2.x), rsqrtf(R2.y)), iR2 = __fmul2_rn(iR, iR);
         const float2 v0 = __fmul2_rn(d0, iR2), v1 = __fmul2_rn(d1, iR2), v2 = __fmul2_rn(d2, iR2);
-        float2 wb[9];  // g_i d'_q
-        wb[0] = __fmul2_rn(g[0], d0), wb[1] = __fmul2_rn(g[0], d1), wb[2] = __fmul2_rn(g[0], d2);
-        wb[3] = __fmul2_rn(g[1], d0), wb[4] = __fmul2_rn(g[1], d1), wb[5] = __fmul2_rn(g[1], d2);
-        wb[6] = __fmul2_rn(g[2], d0), wb[7] = __fmul2_rn(g[2], d1), wb[8] = __fmul2_rn(g[2], d2);
         const float4* __restrict__ tab = reinterpret_cast<const float4*>(ab + (int64_t)node * H * 12);
         float2 cs[2][2 * P + 3];  // level n in slot n & 1
         cs[0][0] = f2(1.0f);
@@ -936,10 +927,9 @@ __device__ __noinline__ void far_adj_target32_pair(const double* __restrict__ ts
                 const float2 gB0 = __ffma2_rn(g[0], f2(ta.w), __ffma2_rn(g[1], f2(tb.z), __fmul2_rn(g[2], f2(tc.y))));
                 const float2 gB1 = __ffma2_rn(g[0], f2(tb.x), __ffma2_rn(g[1], f2(tb.w), __fmul2_rn(g[2], f2(tc.z))));
                 const float2 gB2 = __ffma2_rn(g[0], f2(tb.y), __ffma2_rn(g[1], f2(tc.x), __fmul2_rn(g[2], f2(tc.w))));
+                // alpha^k = g.T_0..2 + sum_q d'_q gB_q  (sum_iq g_i d'_q T_{3+3i+q} regrouped)
                 float2 al = __ffma2_rn(g[0], f2(ta.x), __ffma2_rn(g[1], f2(ta.y), __fmul2_rn(g[2], f2(ta.z))));
-                al = __ffma2_rn(wb[0], f2(ta.w), __ffma2_rn(wb[1], f2(tb.x), __ffma2_rn(wb[2], f2(tb.y), al)));
-                al = __ffma2_rn(wb[3], f2(tb.z), __ffma2_rn(wb[4], f2(tb.w), __ffma2_rn(wb[5], f2(tc.x), al)));
-                al = __ffma2_rn(wb[6], f2(tc.y), __ffma2_rn(wb[7], f2(tc.z), __ffma2_rn(wb[8], f2(tc.w), al)));
+                al = __ffma2_rn(d0, gB0, __ffma2_rn(d1, gB1, __ffma2_rn(d2, gB2, al)));
                 const float2 c = cs[n & 1][h];
                 a0 = __ffma2_rn(c, gB0, a0);
                 a1 = __ffma2_rn(c, gB1, a1);
