@@ -1047,11 +1047,11 @@ __global__ void __launch_bounds__(32)
     const int64_t j0 = (int64_t)blockIdx.x * chunk;
     if (j0 >= nent) return;
     const int64_t j1 = min(nent, j0 + chunk);
-    float acc[NPL][12];
+    float2 acc[NPL][6];  // components (2c, 2c+1) packed
 #pragma unroll
     for (int q = 0; q < NPL; q++)
 #pragma unroll
-        for (int c = 0; c < 12; c++) acc[q][c] = 0.f;
+        for (int c = 0; c < 6; c++) acc[q][c] = make_float2(0.f, 0.f);
     int64_t cur = -1;
     for (int64_t j = j0; j <= j1; j++) {
         const int64_t node = j < j1 ? (int64_t)skeys[j] : -2;
@@ -1061,13 +1061,16 @@ __global__ void __launch_bounds__(32)
                 for (int q = 0; q < NPL; q++) {
                     const int h = lane + 32 * q;
                     if (h < H)
-                        for (int c = 0; c < 12; c++) atomicAdd(&fbar[(cur * H + h) * 12 + c], (double)acc[q][c]);
+                        for (int c = 0; c < 6; c++) {
+                            atomicAdd(&fbar[(cur * H + h) * 12 + 2 * c], (double)acc[q][c].x);
+                            atomicAdd(&fbar[(cur * H + h) * 12 + 2 * c + 1], (double)acc[q][c].y);
+                        }
                 }
             }
 #pragma unroll
             for (int q = 0; q < NPL; q++)
 #pragma unroll
-                for (int c = 0; c < 12; c++) acc[q][c] = 0.f;
+                for (int c = 0; c < 6; c++) acc[q][c] = make_float2(0.f, 0.f);
             cur = node;
         }
         if (j == j1) break;
@@ -1116,22 +1119,19 @@ __global__ void __launch_bounds__(32)
         for (int t = 0; t < 32; t++) {
             const float4* w4 = reinterpret_cast<const float4*>(wt[t]);
             const float4 wa = w4[0], wb = w4[1], wc = w4[2];
+            const float2 w01 = make_float2(wa.x, wa.y), w23 = make_float2(wa.z, wa.w), w45 = make_float2(wb.x, wb.y),
+                         w67 = make_float2(wb.z, wb.w), w89 = make_float2(wc.x, wc.y), wab = make_float2(wc.z, wc.w);
 #pragma unroll
             for (int q = 0; q < NPL; q++) {
                 const int h = lane + 32 * q;
-                const float s = h < H ? sc[h < H ? h : 0][t] : 0.f;
-                acc[q][0] = fmaf(s, wa.x, acc[q][0]);
-                acc[q][1] = fmaf(s, wa.y, acc[q][1]);
-                acc[q][2] = fmaf(s, wa.z, acc[q][2]);
-                acc[q][3] = fmaf(s, wa.w, acc[q][3]);
-                acc[q][4] = fmaf(s, wb.x, acc[q][4]);
-                acc[q][5] = fmaf(s, wb.y, acc[q][5]);
-                acc[q][6] = fmaf(s, wb.z, acc[q][6]);
-                acc[q][7] = fmaf(s, wb.w, acc[q][7]);
-                acc[q][8] = fmaf(s, wc.x, acc[q][8]);
-                acc[q][9] = fmaf(s, wc.y, acc[q][9]);
-                acc[q][10] = fmaf(s, wc.z, acc[q][10]);
-                acc[q][11] = fmaf(s, wc.w, acc[q][11]);
+                const float sv = h < H ? sc[h < H ? h : 0][t] : 0.f;
+                const float2 s2 = make_float2(sv, sv);
+                acc[q][0] = __ffma2_rn(s2, w01, acc[q][0]);
+                acc[q][1] = __ffma2_rn(s2, w23, acc[q][1]);
+                acc[q][2] = __ffma2_rn(s2, w45, acc[q][2]);
+                acc[q][3] = __ffma2_rn(s2, w67, acc[q][3]);
+                acc[q][4] = __ffma2_rn(s2, w89, acc[q][4]);
+                acc[q][5] = __ffma2_rn(s2, wab, acc[q][5]);
             }
         }
     }
