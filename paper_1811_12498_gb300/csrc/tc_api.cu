@@ -382,8 +382,9 @@ tc_status tc_moments(tc_ctx* ctx, const double* f, const double* h, const double
     }
     // The caller's weights are consumed above; the moment passes read only the
     // library's sorted copies, so they run on the second stream, overlapping
-    // the list traversal of the next tc_eval (FP64 pipe against FP32 and
-    // memory latency), and are joined before anything reads the moments.
+    // the list traversal and the near field of the next tc_eval (FP64 pipe
+    // against FP32 and memory latency), and are joined before anything reads
+    // the moments.
     // Profile mode 2 keeps them on the first stream.
     const bool async = ctx->profile != 2;
     cudaStream_t sm = async ? ctx->stream2 : s;
@@ -391,8 +392,16 @@ tc_status tc_moments(tc_ctx* ctx, const double* f, const double* h, const double
         TC_CK(cudaEventRecord(ctx->ev_fork, s), "fork");
         TC_CK(cudaStreamWaitEvent(sm, ctx->ev_fork, 0), "fork");
     }
+    // In mixed precision the near field of the Stokeslet + stresslet kernel
+    // takes most of the step and needs no moments: the leaf pass then runs
+    // one block per SM beside it, and the far field follows.  Where the far
+    // field, which waits for the moments, takes most of the step (the
+    // regularized kernels) or the near field runs on the FP64 pipe too, the
+    // leaf pass fills the SMs.
+    const int mom_blocks = ctx->precision == TC_MIXED && ctx->reg_eps == 0.0 ? 1 : 0;
     TC_CK(launch_moments(ptr<int4>(ctx->node_topo), ptr<Geo>(ctx->node_geo), ptr<double>(ctx->xs),
-                         ptr<double>(ctx->ws), N, ctx->nnodes, p, ptr<double>(ctx->mom), ctx->mom_tmp.p, sm),
+                         ptr<double>(ctx->ws), N, ctx->nnodes, p, ptr<double>(ctx->mom), ctx->mom_tmp.p, mom_blocks,
+                         sm),
           "moments");
     // upward pass: level_begin holds the first node of each level and the end
     for (int L = (int)ctx->level_begin.size() - 3; L >= 0; L--)
@@ -680,7 +689,7 @@ tc_status tc_update_positions(tc_ctx* ctx, const double* x)
         TC_CK(launch_source_pack(ptr<double>(ctx->xs), ptr<double>(ctx->ws), N, ptr<float4>(ctx->spack), s), "pack");
     // moments of the moved particles about the unchanged centres, then the tables
     TC_CK(launch_moments(ptr<int4>(ctx->node_topo), ptr<Geo>(ctx->node_geo), ptr<double>(ctx->xs),
-                         ptr<double>(ctx->ws), N, ctx->nnodes, ctx->p_mom, ptr<double>(ctx->mom), ctx->mom_tmp.p, s),
+                         ptr<double>(ctx->ws), N, ctx->nnodes, ctx->p_mom, ptr<double>(ctx->mom), ctx->mom_tmp.p, 0, s),
           "moments");
     for (int L = (int)ctx->level_begin.size() - 3; L >= 0; L--)
         TC_CK(launch_m2m(ptr<int4>(ctx->node_topo), ptr<Geo>(ctx->node_geo), ctx->level_begin[L],

@@ -375,8 +375,10 @@ cudaError_t launch_gather_weights(const double* f, const double* h, const double
 cudaError_t launch_source_pack(const double* xs, const double* ws, int64_t N, float4* pack, cudaStream_t s);
 // scratch bytes of launch_moments (item map and per-item partial moments)
 size_t moments_scratch_bytes(int64_t N, int64_t nnodes, int p);
+// leaf moments of every leaf; blocks_per_sm sizes the leaf pass's resident
+// grid (0: as many as fit)
 cudaError_t launch_moments(const int4* topo, const Geo* geo, const double* xs, const double* ws, int64_t N,
-                           int64_t nnodes, int p, double* mom, void* scratch, cudaStream_t s);
+                           int64_t nnodes, int p, double* mom, void* scratch, int blocks_per_sm, cudaStream_t s);
 // upward pass of one level [lb, le) whose children start at cb; shifted:
 // scratch of m2m_scratch_bytes (one slot of moments per child of the level)
 cudaError_t launch_m2m(const int4* topo, const Geo* geo, int64_t lb, int64_t le, int64_t cb, int p, double* mom,

@@ -82,18 +82,25 @@ __global__ void k_source_pack(const double* __restrict__ xs, const double* __res
 
 constexpr int kMomThreads = 128;
 constexpr int kMomChunk = 32;
-constexpr int kMomSlots = (ncoef(kPMax) + kMomThreads - 1) / kMomThreads;
+constexpr int kLeafMomThreads = 192;  // threads of a leaf-pass block
+constexpr int kLeafMomSlots = (ncoef(kPMax) + kLeafMomThreads - 1) / kLeafMomThreads;
 
-constexpr int kMomItem = 256;  // particles of a leaf per block of the leaf pass
+constexpr int kMomItem = 256;       // particles of a leaf per item of the leaf pass
 
 // Leaf pass (P2M, from the definition), balanced: every leaf is cut into
-// items of at most kMomItem particles, one block per item, each writing its
-// partial moments to part[item]; k_moments_sum adds a leaf's partials in item
-// order (so the result does not depend on scheduling).  One block per leaf
-// left the GPU waiting on its largest leaves (N = 262144 in Gaussian
-// clusters: leaves of very different sizes).  Particles are staged in chunks:
-// their powers of (y - y_c) per axis and their 12 weights; each thread owns a
-// few k.  Internal clusters are assembled from their children by k_m2m.
+// items of at most kMomItem particles, each writing its partial moments to
+// part[item]; k_moments_sum adds a leaf's partials in item order (so the
+// result does not depend on scheduling).  One block per leaf left the GPU
+// waiting on its largest leaves (N = 262144 in Gaussian clusters: leaves of
+// very different sizes).  Particles are staged in chunks: their powers of
+// (y - y_c) per axis and their 12 weights; each thread owns S = C / 192
+// (rounded up) of the k, so the accumulators take 24 S registers.  A
+// resident grid walks the items.  Beside the near field (launched while the
+// moments are still in flight) it is one block per SM: the pass is bound by
+// the FP64 pipe, which the near field's FP32 work leaves free, and at S = 1
+// (p <= 8) a block takes 192 x 64 registers, which fits in what the near
+// field's resident blocks leave; alone it fills the SMs.  Internal clusters
+// are assembled from their children by k_m2m.
 __global__ void k_mom_items(const int4* __restrict__ topo, int64_t nnodes, int32_t* __restrict__ cnt)
 {
     const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -102,80 +109,80 @@ __global__ void k_mom_items(const int4* __restrict__ topo, int64_t nnodes, int32
     cnt[id] = t.w == 0 ? (t.y + kMomItem - 1) / kMomItem : 0;
 }
 
-__global__ void __launch_bounds__(kMomThreads) k_moments(const int4* __restrict__ topo,
-                                                         const Geo* __restrict__ geo,
-                                                         const double* __restrict__ xs,
-                                                         const double* __restrict__ ws, int64_t N, int p,
-                                                         const int32_t* __restrict__ item_off,
-                                                         const int32_t* __restrict__ nitems, int64_t nnodes,
-                                                         double* __restrict__ part)
+template <int S>
+__global__ void __launch_bounds__(kLeafMomThreads, S * kLeafMomThreads <= 256 ? 5 : 1)
+    k_moments(const int4* __restrict__ topo, const Geo* __restrict__ geo, const double* __restrict__ xs,
+              const double* __restrict__ ws, int64_t N, int p, const int32_t* __restrict__ item_off,
+              const int32_t* __restrict__ nitems, int64_t nnodes, double* __restrict__ part)
 {
     __shared__ double pw[3][kMomChunk][kPMax + 1];
     __shared__ double wt[kMomChunk][12];
-    const int item = blockIdx.x;
-    if (item >= *nitems) return;
-    int64_t lo = 0, hi = nnodes;  // item_off[lo] <= item < item_off[hi]
-    while (hi - lo > 1) {
-        const int64_t mid = (lo + hi) >> 1;
-        if (item_off[mid] <= item)
-            lo = mid;
-        else
-            hi = mid;
-    }
-    // lo is the last node with item_off <= item; nodes without items (cnt 0)
-    // share their successor's offset and come before it, so lo owns the item
-    const int64_t node = lo;
-    const int4 t0 = topo[node];
-    const int first = t0.x + (item - item_off[node]) * kMomItem;
-    const int4 t = make_int4(first, min(kMomItem, t0.x + t0.y - first), 0, 0);
-    Geo g = geo[node];
     const int C = ncoef(p);
-    int kk[kMomSlots][3];
-    double acc[kMomSlots][12];
-    for (int s = 0; s < kMomSlots; s++) {
-        int idx = threadIdx.x + s * kMomThreads;
+    int kk[S][3];
+    for (int s = 0; s < S; s++) {
+        const int idx = threadIdx.x + s * kLeafMomThreads;
         if (idx < C)
             unflatten(idx, kk[s][0], kk[s][1], kk[s][2]);
         else
             kk[s][0] = kk[s][1] = kk[s][2] = 0;
-        for (int c = 0; c < 12; c++) acc[s][c] = 0.0;
     }
-    for (int base = t.x; base < t.x + t.y; base += kMomChunk) {
-        int nq = min(kMomChunk, t.x + t.y - base);
-        __syncthreads();
-        if (threadIdx.x < nq) {
-            int i = base + threadIdx.x;
-            double d[3] = {xs[i] - g.x, xs[N + i] - g.y, xs[2 * N + i] - g.z};
-            for (int a = 0; a < 3; a++) {
-                double v = 1.0;
-                pw[a][threadIdx.x][0] = 1.0;
-                for (int k = 1; k <= p; k++) {
-                    v *= d[a];
-                    pw[a][threadIdx.x][k] = v;
+    const int items = *nitems;
+    for (int item = blockIdx.x; item < items; item += gridDim.x) {
+        int64_t lo = 0, hi = nnodes;  // item_off[lo] <= item < item_off[hi]
+        while (hi - lo > 1) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (item_off[mid] <= item)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        // lo is the last node with item_off <= item; nodes without items
+        // (cnt 0) share their successor's offset and come before it, so lo
+        // owns the item
+        const int64_t node = lo;
+        const int4 t0 = topo[node];
+        const int first = t0.x + (item - item_off[node]) * kMomItem;
+        const int end = first + min(kMomItem, t0.x + t0.y - first);
+        const Geo g = geo[node];
+        double acc[S][12];
+        for (int s = 0; s < S; s++)
+            for (int c = 0; c < 12; c++) acc[s][c] = 0.0;
+        for (int base = first; base < end; base += kMomChunk) {
+            const int nq = min(kMomChunk, end - base);
+            __syncthreads();
+            if (threadIdx.x < nq) {
+                const int i = base + threadIdx.x;
+                const double d[3] = {xs[i] - g.x, xs[N + i] - g.y, xs[2 * N + i] - g.z};
+                for (int a = 0; a < 3; a++) {
+                    double v = 1.0;
+                    pw[a][threadIdx.x][0] = 1.0;
+                    for (int k = 1; k <= p; k++) {
+                        v *= d[a];
+                        pw[a][threadIdx.x][k] = v;
+                    }
+                }
+                const double h[3] = {ws[3 * N + i], ws[4 * N + i], ws[5 * N + i]};
+                const double nu[3] = {ws[6 * N + i], ws[7 * N + i], ws[8 * N + i]};
+                wt[threadIdx.x][0] = ws[i];
+                wt[threadIdx.x][1] = ws[N + i];
+                wt[threadIdx.x][2] = ws[2 * N + i];
+                for (int j = 0; j < 3; j++)
+                    for (int l = 0; l < 3; l++) wt[threadIdx.x][3 + 3 * j + l] = h[j] * nu[l];
+            }
+            __syncthreads();
+            for (int s = 0; s < S; s++) {
+                if (threadIdx.x + s * kLeafMomThreads >= C) break;
+                for (int q = 0; q < nq; q++) {
+                    const double mono = pw[0][q][kk[s][0]] * pw[1][q][kk[s][1]] * pw[2][q][kk[s][2]];
+                    for (int c = 0; c < 12; c++) acc[s][c] = fma(mono, wt[q][c], acc[s][c]);
                 }
             }
-            double f0 = ws[i], f1 = ws[N + i], f2 = ws[2 * N + i];
-            double h[3] = {ws[3 * N + i], ws[4 * N + i], ws[5 * N + i]};
-            double nu[3] = {ws[6 * N + i], ws[7 * N + i], ws[8 * N + i]};
-            wt[threadIdx.x][0] = f0;
-            wt[threadIdx.x][1] = f1;
-            wt[threadIdx.x][2] = f2;
-            for (int j = 0; j < 3; j++)
-                for (int l = 0; l < 3; l++) wt[threadIdx.x][3 + 3 * j + l] = h[j] * nu[l];
         }
-        __syncthreads();
-        for (int s = 0; s < kMomSlots; s++) {
-            if (threadIdx.x + s * kMomThreads >= C) break;
-            for (int q = 0; q < nq; q++) {
-                double mono = pw[0][q][kk[s][0]] * pw[1][q][kk[s][1]] * pw[2][q][kk[s][2]];
-                for (int c = 0; c < 12; c++) acc[s][c] = fma(mono, wt[q][c], acc[s][c]);
-            }
+        for (int s = 0; s < S; s++) {
+            const int idx = threadIdx.x + s * kLeafMomThreads;
+            if (idx >= C) break;
+            for (int c = 0; c < 12; c++) part[((int64_t)item * 12 + c) * C + idx] = acc[s][c];
         }
-    }
-    for (int s = 0; s < kMomSlots; s++) {
-        int idx = threadIdx.x + s * kMomThreads;
-        if (idx >= C) break;
-        for (int c = 0; c < 12; c++) part[((int64_t)item * 12 + c) * C + idx] = acc[s][c];
     }
 }
 
@@ -520,8 +527,21 @@ size_t moments_scratch_bytes(int64_t N, int64_t nnodes, int p)
     return (size_t)(2 * nnodes + 1) * 4 + 16 + (size_t)moments_item_bound(N, nnodes) * 12 * ncoef(p) * 8;
 }
 
+template <int S>
+unsigned moments_grid(int blocks_per_sm, int64_t bound)
+{
+    int dev = 0, sms = 0, fit = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (blocks_per_sm <= 0 &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_moments<S>, kLeafMomThreads, 0) == cudaSuccess)
+        blocks_per_sm = fit;
+    const int64_t want = (int64_t)(blocks_per_sm > 0 ? blocks_per_sm : 1) * (sms > 0 ? sms : 1);
+    return (unsigned)(bound < want ? bound : want);
+}
+
 cudaError_t launch_moments(const int4* topo, const Geo* geo, const double* xs, const double* ws, int64_t N,
-                           int64_t nnodes, int p, double* mom, void* scratch, cudaStream_t s)
+                           int64_t nnodes, int p, double* mom, void* scratch, int blocks_per_sm, cudaStream_t s)
 {
     // scratch: cnt [nnodes] i32, item_off [nnodes] i32, nitems i32, then (16-byte aligned) the partials
     int32_t* cnt = reinterpret_cast<int32_t*>(scratch);
@@ -533,8 +553,18 @@ cudaError_t launch_moments(const int4* topo, const Geo* geo, const double* xs, c
     note_launch();
     cudaError_t e = launch_scan_i32(cnt, item_off, nnodes, nitems, s);
     if (e != cudaSuccess) return e;
-    k_moments<<<(unsigned)moments_item_bound(N, nnodes), kMomThreads, 0, s>>>(topo, geo, xs, ws, N, p, item_off,
-                                                                               nitems, nnodes, part);
+    // the item count stays on the device: the grid walks the items up to it
+    const int64_t bound = moments_item_bound(N, nnodes);
+    const int S = (ncoef(p) + kLeafMomThreads - 1) / kLeafMomThreads;
+    if (S == 1)
+        k_moments<1><<<moments_grid<1>(blocks_per_sm, bound), kLeafMomThreads, 0, s>>>(
+            topo, geo, xs, ws, N, p, item_off, nitems, nnodes, part);
+    else if (S == 2)
+        k_moments<2><<<moments_grid<2>(blocks_per_sm, bound), kLeafMomThreads, 0, s>>>(
+            topo, geo, xs, ws, N, p, item_off, nitems, nnodes, part);
+    else
+        k_moments<kLeafMomSlots><<<moments_grid<kLeafMomSlots>(blocks_per_sm, bound), kLeafMomThreads, 0, s>>>(
+            topo, geo, xs, ws, N, p, item_off, nitems, nnodes, part);
     note_launch();
     k_moments_sum<<<(unsigned)nnodes, 128, 0, s>>>(topo, cnt, item_off, nnodes, p, part, mom);
     note_launch();
