@@ -396,8 +396,9 @@ tc_status tc_moments(tc_ctx* ctx, const double* f, const double* h, const double
     // takes most of the step and needs no moments: the leaf pass then runs
     // one block per SM beside it, and the far field follows.  Where the far
     // field, which waits for the moments, takes most of the step (the
-    // regularized kernels) or the near field runs on the FP64 pipe too, the
-    // leaf pass fills the SMs.
+    // regularized kernels: there it gains from sharing the SMs with the near
+    // field) or the near field runs on the FP64 pipe too, the leaf pass runs
+    // one block per item and ends first.
     const int mom_blocks = ctx->precision == TC_MIXED && ctx->reg_eps == 0.0 ? 1 : 0;
     TC_CK(launch_moments(ptr<int4>(ctx->node_topo), ptr<Geo>(ctx->node_geo), ptr<double>(ctx->xs),
                          ptr<double>(ctx->ws), N, ctx->nnodes, p, ptr<double>(ctx->mom), ctx->mom_tmp.p, mom_blocks,

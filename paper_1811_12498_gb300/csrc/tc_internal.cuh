@@ -376,7 +376,7 @@ cudaError_t launch_source_pack(const double* xs, const double* ws, int64_t N, fl
 // scratch bytes of launch_moments (item map and per-item partial moments)
 size_t moments_scratch_bytes(int64_t N, int64_t nnodes, int p);
 // leaf moments of every leaf; blocks_per_sm sizes the leaf pass's resident
-// grid (0: as many as fit)
+// grid (0: one block per item)
 cudaError_t launch_moments(const int4* topo, const Geo* geo, const double* xs, const double* ws, int64_t N,
                            int64_t nnodes, int p, double* mom, void* scratch, int blocks_per_sm, cudaStream_t s);
 // upward pass of one level [lb, le) whose children start at cb; shifted:

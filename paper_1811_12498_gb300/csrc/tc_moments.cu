@@ -94,13 +94,15 @@ constexpr int kMomItem = 256;       // particles of a leaf per item of the leaf 
 // waiting on its largest leaves (N = 262144 in Gaussian clusters: leaves of
 // very different sizes).  Particles are staged in chunks: their powers of
 // (y - y_c) per axis and their 12 weights; each thread owns S = C / 192
-// (rounded up) of the k, so the accumulators take 24 S registers.  A
-// resident grid walks the items.  Beside the near field (launched while the
-// moments are still in flight) it is one block per SM: the pass is bound by
-// the FP64 pipe, which the near field's FP32 work leaves free, and at S = 1
-// (p <= 8) a block takes 192 x 64 registers, which fits in what the near
-// field's resident blocks leave; alone it fills the SMs.  Internal clusters
-// are assembled from their children by k_m2m.
+// (rounded up) of the k, so the accumulators take 24 S registers.  The
+// blocks walk the items.  Beside the near field (launched while the moments
+// are still in flight) the grid is one resident block per SM: the pass is
+// bound by the FP64 pipe, which the near field's FP32 work leaves free, and
+// at S = 1 (p <= 8) a block takes 192 x 64 registers, which fits in what
+// the near field's resident blocks leave.  Otherwise it is one block per
+// item, whose blocks come and go, so kernels launched after it on other
+// streams start as soon as blocks retire.  Internal clusters are assembled
+// from their children by k_m2m.
 __global__ void k_mom_items(const int4* __restrict__ topo, int64_t nnodes, int32_t* __restrict__ cnt)
 {
     const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -527,16 +529,14 @@ size_t moments_scratch_bytes(int64_t N, int64_t nnodes, int p)
     return (size_t)(2 * nnodes + 1) * 4 + 16 + (size_t)moments_item_bound(N, nnodes) * 12 * ncoef(p) * 8;
 }
 
-template <int S>
-unsigned moments_grid(int blocks_per_sm, int64_t bound)
+// One block per item, or a resident grid of blocks_per_sm blocks per SM
+static unsigned moments_grid(int blocks_per_sm, int64_t bound)
 {
-    int dev = 0, sms = 0, fit = 0;
+    if (blocks_per_sm <= 0) return (unsigned)bound;
+    int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (blocks_per_sm <= 0 &&
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_moments<S>, kLeafMomThreads, 0) == cudaSuccess)
-        blocks_per_sm = fit;
-    const int64_t want = (int64_t)(blocks_per_sm > 0 ? blocks_per_sm : 1) * (sms > 0 ? sms : 1);
+    const int64_t want = (int64_t)blocks_per_sm * (sms > 0 ? sms : 1);
     return (unsigned)(bound < want ? bound : want);
 }
 
@@ -554,17 +554,15 @@ cudaError_t launch_moments(const int4* topo, const Geo* geo, const double* xs, c
     cudaError_t e = launch_scan_i32(cnt, item_off, nnodes, nitems, s);
     if (e != cudaSuccess) return e;
     // the item count stays on the device: the grid walks the items up to it
-    const int64_t bound = moments_item_bound(N, nnodes);
+    const unsigned grid = moments_grid(blocks_per_sm, moments_item_bound(N, nnodes));
     const int S = (ncoef(p) + kLeafMomThreads - 1) / kLeafMomThreads;
     if (S == 1)
-        k_moments<1><<<moments_grid<1>(blocks_per_sm, bound), kLeafMomThreads, 0, s>>>(
-            topo, geo, xs, ws, N, p, item_off, nitems, nnodes, part);
+        k_moments<1><<<grid, kLeafMomThreads, 0, s>>>(topo, geo, xs, ws, N, p, item_off, nitems, nnodes, part);
     else if (S == 2)
-        k_moments<2><<<moments_grid<2>(blocks_per_sm, bound), kLeafMomThreads, 0, s>>>(
-            topo, geo, xs, ws, N, p, item_off, nitems, nnodes, part);
+        k_moments<2><<<grid, kLeafMomThreads, 0, s>>>(topo, geo, xs, ws, N, p, item_off, nitems, nnodes, part);
     else
-        k_moments<kLeafMomSlots><<<moments_grid<kLeafMomSlots>(blocks_per_sm, bound), kLeafMomThreads, 0, s>>>(
-            topo, geo, xs, ws, N, p, item_off, nitems, nnodes, part);
+        k_moments<kLeafMomSlots><<<grid, kLeafMomThreads, 0, s>>>(topo, geo, xs, ws, N, p, item_off, nitems, nnodes,
+                                                                   part);
     note_launch();
     k_moments_sum<<<(unsigned)nnodes, 128, 0, s>>>(topo, cnt, item_off, nnodes, p, part, mom);
     note_launch();
