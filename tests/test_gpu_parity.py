@@ -145,6 +145,39 @@ def test_moments_match_oracle(p):
     tc.close()
 
 
+@pytest.mark.parametrize("p", [3, 8, 10, 12])
+def test_moments_same_bits_on_both_leaf_pass_grids(p):
+    """The leaf pass runs one resident block per SM in mixed precision (beside
+    the near field) and one block per item in FP64 and regularized contexts;
+    each item's partial moments and their sums in item order are the same in
+    both, so the exported moments agree bit for bit, and the mixed ones equal
+    the oracle's.  p = 3, 8, 10, 12 take one, one, two and three coefficients
+    per thread; Gaussian clusters give leaves cut into many items."""
+    x, f, h, nu = inputs.gaussian_clusters(9000, 37)
+    d = [dev(a) for a in (x, f, h, nu)]
+    ctxs = [api.Treecode(prec, True, reg_eps=eps).build(d[0], 400).moments(d[1], d[2], d[3], p)
+            for prec, eps in (("mixed", 0.0), ("fp64", 0.0), ("mixed", 0.01))]
+    g = ctxs[0].tree_export()
+    for c in ctxs[1:]:
+        for k, v in c.tree_export().items():
+            np.testing.assert_array_equal(v, g[k])
+    ot = oracle.Tree(x, 400, True)
+    ot.set_moments(f, h, nu, p)
+    om = _node_map(ot.nodes()["level"], ot.nodes()["cell"])
+    for key, gi in _node_map(g["level"], g["cell"]).items():
+        Mf, Mt = ctxs[0].moments_export(gi)
+        for c in ctxs[1:]:
+            Mf2, Mt2 = c.moments_export(gi)
+            np.testing.assert_array_equal(Mf2, Mf)
+            np.testing.assert_array_equal(Mt2, Mt)
+        rf, rt = ot.node_moments(om[key])
+        scale = max(np.abs(rf).max(), np.abs(rt).max())
+        np.testing.assert_allclose(Mf, rf, rtol=1e-11, atol=1e-13 * scale)
+        np.testing.assert_allclose(Mt, rt, rtol=1e-11, atol=1e-13 * scale)
+    for c in ctxs:
+        c.close()
+
+
 # ---------------------------------------------------------------- treecode
 
 def _run(prec, x, f, h, nu, N0, p, theta, shrink=True, targets=None, pm=None):
