@@ -320,9 +320,10 @@ def bench_fwd_adjoint(flush, stream, steps=3):
         if k > 0:
             fwd.append(e0.elapsed_time(em))
             tot.append(e0.elapsed_time(e1))
-    # each adjoint kernel's own duration (phase events, one more step), and
-    # its counted work against the measured FP32 peak
-    tc.profile(True)
+    # each adjoint kernel's own duration (phase events, one more step with
+    # everything serialised), and its counted work against the measured FP32
+    # peak
+    tc.profile(2)
     flush.fill_(1)
     tc.build(d[0], N0).moments(d[1], d[2], d[3], p)
     tc.eval(theta, p, out=u)

@@ -394,17 +394,20 @@ typedef enum {
     TC_PH_ADJ_FAR_S = 9,   /* tc_adjoint: far field, source side (adjoint tables)    */
     TC_PH_ADJ_NEAR_T = 10, /* tc_adjoint: near field, target side                    */
     TC_PH_ADJ_NEAR_S = 11, /* tc_adjoint: near field, source side                    */
-    TC_PH_ADJ_REST = 12,   /* tc_adjoint: adjoint moments, downward pass, per-particle
-                            * evaluation and the final sums                       */
+    TC_PH_ADJ_REST = 12,   /* tc_adjoint: adjoint moments, downward pass and
+                            * per-particle evaluation (second stream)            */
     TC_NPHASES = 13
 } tc_phase;
 
 /* Enable (1) or disable (0) per-phase event timing on ctx.  Enabling resets
- * the recorded phases.  Costs two event records per phase.  tc_eval runs the
- * far field concurrently with the near field (second stream), so their phase
- * times overlap; enable = 2 times them with the two kernels serialised, so
- * that each phase time is that kernel's own duration (the result is the
- * same). */
+ * the recorded phases.  Costs two event records per phase.  Some phases run
+ * on the context's second stream beside others: the moment passes of
+ * tc_moments and the far field of tc_eval beside the near field, and the
+ * adjoint's moments, downward pass and per-particle evaluation
+ * (TC_PH_ADJ_REST) beside its near-field phases; their phase times then
+ * overlap.  enable = 2 runs everything on one stream, one phase after the
+ * other, so that each phase time is that work's own duration (the result is
+ * the same). */
 tc_status tc_profile(tc_ctx* ctx, int32_t enable);
 
 /* Durations in ms of the most recent run of each phase (host array of

@@ -1642,6 +1642,48 @@ extern "C" tc_status tc_adjoint(tc_ctx* ctx, const double* g, double* grad_f, do
         e = launch_far_adj32(ctx, ts, M, p, s);
     TC_CK(e, "far adjoint");
 
+    // Adjoint moments, downward pass (FP64) and per-particle evaluation:
+    // they read only the far field's adjoint tables and write only the far
+    // gradients, so they run on the second stream beside the near field
+    // (FP32 pipe), which reads and writes none of that, and join before the
+    // final sums.  Profile mode 2 keeps them on the first stream.
+    TC_CK(second_stream(ctx), "second stream");
+    cudaStream_t sr = ctx->profile == 2 ? s : ctx->stream2;
+    if (sr != s) {
+        TC_CK(cudaEventRecord(ctx->ev_fork, s), "fork");
+        TC_CK(cudaStreamWaitEvent(sr, ctx->ev_fork, 0), "fork");
+    }
+    ph_begin(ctx, TC_PH_ADJ_REST, sr);
+    size_t lsm = (size_t)12 * C * 8;
+    TC_CK(cudaFuncSetAttribute(k_lambda, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm), "lambda attr");
+    k_lambda<<<(unsigned)nnodes, 128, lsm, sr>>>(ptr<double>(ctx->adj_abar), ptr<double>(ctx->node_invrho), p,
+                                               ptr<double>(ctx->adj_lam));
+    note_launch();
+    for (size_t L = 0; L + 1 < ctx->level_begin.size(); L++) {
+        const int64_t lb = ctx->level_begin[L], le = ctx->level_begin[L + 1];
+        if (le <= lb) continue;
+        k_l2l<<<dim3((unsigned)(le - lb), 3), 128, 0, sr>>>(ptr<int4>(ctx->node_info), ptr<Geo>(ctx->node_geo), lb,
+                                                            le, p, ptr<double>(ctx->adj_lam),
+                                                            ptr<double>(ctx->adj_lamacc));
+        note_launch();
+    }
+    if (ctx->precision == TC_FP64) {
+        TC_CK(cudaFuncSetAttribute(k_leaf_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm), "leaf attr");
+        k_leaf_eval<<<dim3((unsigned)nnodes, kLeafEvalSplit), 128, lsm, sr>>>(
+            ptr<int4>(ctx->node_topo), ptr<Geo>(ctx->node_geo), ptr<double>(ctx->xs), ptr<double>(ctx->ws), N, p,
+            ptr<double>(ctx->adj_lamacc), ptr<double>(ctx->adj_gfar));
+    } else {
+        const size_t lsm32 = (size_t)12 * C * 4;
+        TC_CK(cudaFuncSetAttribute(k_leaf_eval32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm32),
+              "leaf attr");
+        k_leaf_eval32<<<dim3((unsigned)nnodes, kLeafEvalSplit), 128, lsm32, sr>>>(
+            ptr<int4>(ctx->node_topo), ptr<Geo>(ctx->node_geo), ptr<double>(ctx->xs), ptr<double>(ctx->ws), N, p,
+            ptr<double>(ctx->adj_lamacc), ptr<double>(ctx->adj_gfar));
+    }
+    note_launch();
+    ph_end(ctx, TC_PH_ADJ_REST, sr);
+    if (sr != s) TC_CK(cudaEventRecord(ctx->ev_join, sr), "join");
+
     // near field: target side adds to adj_gt; source side writes adj_gnear
     const unsigned ngrid = (unsigned)((nbatch + kNearAdjWarps - 1) / kNearAdjWarps);
     ph_begin(ctx, TC_PH_ADJ_NEAR_T);
@@ -1690,34 +1732,7 @@ extern "C" tc_status tc_adjoint(tc_ctx* ctx, const double* g, double* grad_f, do
     ph_end(ctx, TC_PH_ADJ_NEAR_S);
     TC_CK(cudaGetLastError(), "near adjoint");
 
-    // adjoint moments, downward pass, per-particle evaluation
-    ph_begin(ctx, TC_PH_ADJ_REST);
-    size_t lsm = (size_t)12 * C * 8;
-    TC_CK(cudaFuncSetAttribute(k_lambda, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm), "lambda attr");
-    k_lambda<<<(unsigned)nnodes, 128, lsm, s>>>(ptr<double>(ctx->adj_abar), ptr<double>(ctx->node_invrho), p,
-                                              ptr<double>(ctx->adj_lam));
-    note_launch();
-    for (size_t L = 0; L + 1 < ctx->level_begin.size(); L++) {
-        const int64_t lb = ctx->level_begin[L], le = ctx->level_begin[L + 1];
-        if (le <= lb) continue;
-        k_l2l<<<dim3((unsigned)(le - lb), 3), 128, 0, s>>>(ptr<int4>(ctx->node_info), ptr<Geo>(ctx->node_geo), lb, le,
-                                                           p, ptr<double>(ctx->adj_lam), ptr<double>(ctx->adj_lamacc));
-        note_launch();
-    }
-    if (ctx->precision == TC_FP64) {
-        TC_CK(cudaFuncSetAttribute(k_leaf_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm), "leaf attr");
-        k_leaf_eval<<<dim3((unsigned)nnodes, kLeafEvalSplit), 128, lsm, s>>>(
-            ptr<int4>(ctx->node_topo), ptr<Geo>(ctx->node_geo), ptr<double>(ctx->xs), ptr<double>(ctx->ws), N, p,
-            ptr<double>(ctx->adj_lamacc), ptr<double>(ctx->adj_gfar));
-    } else {
-        const size_t lsm32 = (size_t)12 * C * 4;
-        TC_CK(cudaFuncSetAttribute(k_leaf_eval32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm32),
-              "leaf attr");
-        k_leaf_eval32<<<dim3((unsigned)nnodes, kLeafEvalSplit), 128, lsm32, s>>>(
-            ptr<int4>(ctx->node_topo), ptr<Geo>(ctx->node_geo), ptr<double>(ctx->xs), ptr<double>(ctx->ws), N, p,
-            ptr<double>(ctx->adj_lamacc), ptr<double>(ctx->adj_gfar));
-    }
-    note_launch();
+    if (sr != s) TC_CK(cudaStreamWaitEvent(s, ctx->ev_join, 0), "join");
     k_adj_final<<<grid_for(N, 256), 256, 0, s>>>(ptr<double>(ctx->adj_gfar), ptr<double>(ctx->adj_gnear),
                                                  ptr<double>(ctx->adj_gt), ptr<int32_t>(ctx->perm), N, ctx->eval_self,
                                                  grad_f, grad_h, grad_nu, grad_x);
@@ -1726,7 +1741,6 @@ extern "C" tc_status tc_adjoint(tc_ctx* ctx, const double* g, double* grad_f, do
         k_scatter3<<<grid_for(M, 256), 256, 0, s>>>(ptr<double>(ctx->adj_gt), tperm, M, grad_t);
         note_launch();
     }
-    ph_end(ctx, TC_PH_ADJ_REST);
     TC_CK(cudaGetLastError(), "adjoint");
     return TC_OK;
 }
