@@ -192,8 +192,10 @@ class Treecode:
 
     def profile(self, enable=True):
         """Enable per-phase CUDA-event timing (see phase_times).  enable=2
-        serialises the far and near fields so that their phase times are each
-        kernel's own duration (by default they run concurrently)."""
+        runs every phase on one stream, one after the other, so that each
+        phase time is that work's own duration (by default the moment passes,
+        the far field and the adjoint's far-gradient passes run beside the
+        near field)."""
         self._chk(lib().tc_profile(self._h, int(enable) if enable in (0, 1, 2) else int(bool(enable))))
 
     def phase_times(self):
