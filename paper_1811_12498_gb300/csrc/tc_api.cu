@@ -490,7 +490,6 @@ tc_status tc::eval_prepare_count(tc_ctx* ctx, const double* targets, int64_t M, 
     if (!targets && M != ctx->N)
         return fail(ctx, TC_EINVAL, "tc_eval: targets = NULL requires M = N (%lld)", (long long)ctx->N);
     if (M < 1 || M >= ((int64_t)1 << 31)) return fail(ctx, TC_EINVAL, "tc_eval: M = %lld out of range", (long long)M);
-    tc_status st = TC_OK;
     cudaStream_t s = ctx->stream;
     ctx->have_eval = 0;
     ctx->prepared = 0;
@@ -570,7 +569,6 @@ tc_status tc::eval_prepare_finish(tc_ctx* ctx)
     const int p = ctx->pending_p;
     const double theta = ctx->pending_theta;
     const double* ts = ctx->pending_ts;
-    const int64_t nbatch = (M + kBatch - 1) / kBatch;
     const int32_t f = (int32_t)ctx->host_words[2];
     if (f & kFlagStack) return fail(ctx, TC_EDEVICE, "device check: traversal stack bound exceeded");
     if (f) return fail(ctx, TC_EDEVICE, "device check: flags 0x%x", f);
