@@ -128,7 +128,7 @@ __device__ __forceinline__ void leaf_sums(const typename Op::Tgt& ta, const type
 // so the result is the same whatever the packing, the grid or the number of
 // systems in a batch.
 constexpr int kLeafWarps = 4;       // warps per block of k_near_leaf
-constexpr int kLeafFreeBlocks = 1;  // block slots per SM left free (for the leaf moment pass, then the far field)
+constexpr int kLeafFreeBlocks = 1;  // block slots per SM left free (for the far field on the second stream)
 
 // Unit i of a schedule on one warp (tile: the warp's source tile).
 template <typename Op>
